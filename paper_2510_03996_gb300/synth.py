@@ -1,0 +1,77 @@
+"""Seeded synthetic workloads: parameter sets and inputs, no scheme arithmetic.
+
+This module is the only thing the CPU oracle and the CUDA library both see in
+a test: it draws message vectors, integer polynomials, images and weights from
+numpy's PCG64 with fixed seeds, and it names the parameter sets.  Every random
+number the scheme itself draws (keys, encryption noise) comes from each
+side's own ChaCha20 stream instead.
+
+Workloads (shapes and distributions of the paper's experiments; MNIST- and
+CIFAR-shaped tensors stand in for the datasets, which are not used):
+  * conv_n13     - one encrypted 5x5 conv layer, N=2^13, Q={60,40,40} bits,
+                   P={60}, dnum=3, scale 2^40, input 1x28x28 ~ U[0,1],
+                   kernel ~ N(0, 0.1^2), stride 1, pad 2.
+  * rot_n16      - batched rotations, N=2^16, 24 x 50-bit Q + 4 x 60-bit P,
+                   dnum=6, 256 ciphertexts at levels ~ U{4..24}, rotation
+                   amounts ~ U[1, 2^15).
+"""
+import numpy as np
+
+SEED_BASE = 0xF4E00000
+
+
+def params(name):
+    """Parameter set by workload name: dict(logN, qbits, pbits, dnum, scale, seed)."""
+    if name == "conv_n13":
+        return dict(logN=13, qbits=[60, 40, 40], pbits=[60], dnum=3, scale=2.0 ** 40, seed=SEED_BASE + 0)
+    if name == "rot_n16":
+        return dict(logN=16, qbits=[50] * 24, pbits=[60] * 4, dnum=6, scale=2.0 ** 40, seed=SEED_BASE + 1)
+    if name == "tiny":  # test-sized: several limbs, two digits, two P limbs
+        return dict(logN=6, qbits=[50, 40, 40, 40], pbits=[58, 58], dnum=2, scale=2.0 ** 30, seed=SEED_BASE + 7)
+    if name == "small_n12":  # test-sized, spans several NTT tiles
+        return dict(logN=12, qbits=[55, 45, 45, 45, 45], pbits=[60, 60], dnum=3, scale=2.0 ** 40, seed=SEED_BASE + 8)
+    raise KeyError(name)
+
+
+def rng(seed, stream=0):
+    return np.random.Generator(np.random.PCG64([int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream)]))
+
+
+def uniform_slots(seed, stream, n, lo=-1.0, hi=1.0, complex_=False):
+    g = rng(seed, stream)
+    z = g.uniform(lo, hi, n)
+    if complex_:
+        z = z + 1j * g.uniform(lo, hi, n)
+    return z
+
+
+def small_int_poly(seed, stream, N, bound):
+    """Integer polynomial with coefficients uniform in [-bound, bound]."""
+    return rng(seed, stream).integers(-bound, bound + 1, N, dtype=np.int64)
+
+
+def residues_poly(seed, stream, moduli, N):
+    """uint64[len(moduli)][N] with limb i uniform in [0, moduli[i])."""
+    g = rng(seed, stream)
+    return np.stack([g.integers(0, int(q), N, dtype=np.uint64) for q in moduli])
+
+
+def image(seed, stream, shape, dist="uniform01"):
+    g = rng(seed, stream)
+    if dist == "uniform01":
+        return g.uniform(0.0, 1.0, shape)
+    if dist == "normal":
+        return g.standard_normal(shape)
+    raise KeyError(dist)
+
+
+def conv_kernel(seed, stream, shape, std=0.1):
+    return rng(seed, stream).normal(0.0, std, shape)
+
+
+def rotation_workload(seed, n_ct=256, lmin=4, lmax=24, rmax=1 << 15):
+    """Levels ~ U{lmin..lmax} and rotation amounts ~ U[1, rmax) for n_ct ciphertexts."""
+    g = rng(seed, 99)
+    levels = g.integers(lmin, lmax + 1, n_ct)
+    steps = g.integers(1, rmax, n_ct)
+    return [int(x) for x in levels], [int(x) for x in steps]
