@@ -1,0 +1,330 @@
+"""Benchmark: HE rotations/sec at N=2^16 (batched rotation workload).
+
+Workload (one "step"): 256 CKKS ciphertexts at N = 2^16 over 24 x 50-bit Q
+limbs + 4 x 60-bit P limbs, dnum 6, each at a level ~ U{4..24}, each rotated
+by its own amount ~ U[1, 2^15) with its own resident rotation key (one key per
+distinct amount, ~45 GB of keys), all in one fheon_rotate_batch call.  Inputs
+are fresh encryptions of U[-1, 1] slot vectors (synthetic, seeded).  Keys and
+ciphertexts (> 45 GB) exceed the 129 MB L2, so no flush is needed.
+
+Arms:
+  default          the CUDA library; prints one JSON line with roofline,
+                   cpu_baseline, e2e, clocks, gpu_launches.
+  --impl reference the CPU oracle (test infrastructure) timed on this host's
+                   cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_03996_gb300 import synth  # noqa: E402
+
+METRIC = "HE rotations/sec at N=2^16"
+UNIT = "rotations/s"
+WORKLOAD = "rot_n16"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic_costs(N, L, K, alpha, level):
+    """Per-rotation algorithmic work at `level` (see the design notes):
+    bytes that must cross HBM at least once, and 64-bit modular multiplies."""
+    beta = (level + alpha - 1) // alpha
+    limb = 8 * N
+    key_bytes = 2 * beta * (level + K) * limb
+    ct_bytes = 4 * level * limb  # read (c0, c1), write (c0', c1')
+    logN = N.bit_length() - 1
+    ntt_limbs = level + (beta * (level + K) - level) + 2 * K + 2 * level
+    butterflies = ntt_limbs * (N // 2) * logN
+    return dict(bytes=key_bytes + ct_bytes, key_bytes=key_bytes, ntt_limbs=ntt_limbs, butterflies=butterflies,
+                ip_bytes=key_bytes + (beta * (level + K)) * limb + 2 * (level + K) * limb)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def barrier_max(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle timing
+class OracleRunner:
+    """The CPU oracle (single thread) set up once on the workload's parameters.
+    One rotation key serves every sample: the work does not depend on which key."""
+
+    def __init__(self, P, step):
+        import oracle.ckks as O
+        N = 1 << P["logN"]
+        L = len(P["qbits"])
+        mods = O.gen_primes(N, P["qbits"] + P["pbits"])
+        self.oc = O.Ctx(N, mods[:L], mods[L:], P["dnum"], P["seed"])
+        _, se = self.oc.keygen_sk()
+        pk = self.oc.keygen_pk(se)
+        self.g = O.galois_elt(step, N)
+        self.key = self.oc.rotkey(se, self.g)
+        self.ct = self.oc.encrypt(pk, synth.small_int_poly(P["seed"], 5, N, 1 << 40), 1)
+
+    def rotate_seconds(self, level):
+        c = self.oc.drop_level(self.ct, level)
+        t0 = time.perf_counter()
+        self.oc.rotate(c, self.g, self.key)
+        return time.perf_counter() - t0
+
+    def rate(self, levels, budget_s):
+        done, t_total, used = 0, 0.0, []
+        for lv in levels:
+            t_total += self.rotate_seconds(lv)
+            done += 1
+            used.append(lv)
+            if t_total > budget_s:
+                break
+        return done / t_total, done, t_total, used
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    P = synth.params(WORKLOAD)
+    levels, steps = synth.rotation_workload(P["seed"])
+    runner = OracleRunner(P, steps[0])
+    # each step rotates the next workload item on the oracle
+    for k in range(args.warmup):
+        runner.rotate_seconds(levels[k % len(levels)])
+    t_steps, per_step = [], []
+    for k in range(args.steps):
+        lv = levels[(args.warmup + k) % len(levels)]
+        t_steps.append(runner.rotate_seconds(lv))
+        per_step.append(lv)
+    value = len(t_steps) / sum(t_steps)
+    ms = 1e3 * sum(t_steps) / len(t_steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched rotation, N=2^16, 24x50-bit Q + 4x60-bit P, dnum 6, levels U{4..24}, "
+                                   "steps U[1,2^15); reference steps rotate one ciphertext each",
+                       "levels_sampled": per_step, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "one rotation per step at the workload's item levels %s" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ CUDA arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2510_03996_gb300 import fheon as F
+
+    F.use_torch_allocator()
+    P = synth.params(WORKLOAD)
+    N = 1 << P["logN"]
+    stream = torch.cuda.current_stream()
+    ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                    stream=stream.cuda_stream)
+    levels, steps = synth.rotation_workload(P["seed"], n_ct=args.n_ct)
+    sk, pk = ctx.keygen()
+    t0 = time.time()
+    ctx.rotkeygen(sk, sorted(set(steps)))
+    ctx.sync()
+    nkeys, kbytes = ctx.key_stats()
+    t_keys = time.time() - t0
+    z = synth.uniform_slots(P["seed"], 3, N // 2)
+    pt = ctx.encode(z, ctx.L, P["scale"])
+    ins, outs = [], []
+    for i, lv in enumerate(levels):
+        ct = ctx.encrypt(pk, pt, nonce=i)
+        ins.append(ctx.drop_level(ct, lv))
+        outs.append(ctx.ct_create(lv, P["scale"]))
+        del ct
+    ctx.sync()
+
+    def step():
+        ctx.rotate_batch(ins, outs, steps)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        ctx.profile_begin()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        prof = ctx.profile_end()
+        torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = barrier_max(ms_total, world)
+    ms_step = ms_total / args.steps
+    value = world * len(levels) * args.steps / (ms_total / 1e3)
+
+    # e2e: host buffers (pinned) -> upload -> batched rotation -> download, every step
+    host_in = [torch.empty((2, lv, N), dtype=torch.int64, pin_memory=True) for lv in levels]
+    host_out = [torch.empty((2, lv, N), dtype=torch.int64, pin_memory=True) for lv in levels]
+    for h, c in zip(host_in, ins):
+        ctx.ct_download_ptr(c, h.data_ptr())
+    h2d = sum(h.numel() * 8 for h in host_in)
+    d2h = sum(h.numel() * 8 for h in host_out)
+
+    def e2e_step():
+        for h, c in zip(host_in, ins):
+            ctx.ct_upload_ptr(c, h.data_ptr())
+        ctx.rotate_batch(ins, outs, steps)
+        for h, c in zip(host_out, outs):
+            ctx.ct_download_ptr(c, h.data_ptr())
+
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = barrier_max(time.perf_counter() - t0, world)
+    e2e_value = world * len(levels) * e2e_steps / e2e_s
+
+    # roofline of the dominant kernel, from the live per-launch events
+    pk_, src = peaks()
+    launches = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    costs = [algorithmic_costs(N, ctx.L, ctx.K, ctx.alpha, lv) for lv in levels]
+    dom_name, (dom_n, dom_ms) = dom
+    if dom_name.startswith("ntt"):
+        # one pass = half of the log2(N) butterfly stages over every transformed limb
+        tot_bfly = sum(c["butterflies"] for c in costs) * args.steps / 2
+        achieved = tot_bfly / (dom_ms / 1e3) / 1e12
+        imad_peak = 152 * 64 * float(pk_.get("sm_max_mhz", 2070.0)) * 1e6
+        peak = imad_peak / 10 / 1e12   # 10 IMAD per Shoup product (butterfly)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tbutterfly/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom_name, "launches": dom_n,
+                "avg_launch_ms": dom_ms / dom_n, "peak_source": "derived: 152 SM x 64 IMAD/clk x max clock / 10"}
+    else:
+        tot_bytes = sum(c["ip_bytes"] if dom_name == "ks_inner" else c["bytes"] for c in costs) * args.steps
+        achieved = tot_bytes / (dom_ms / 1e3) / 1e9
+        peak = float(pk_["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom_name, "launches": dom_n, "avg_launch_ms": dom_ms / dom_n,
+                "peak_source": src}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, done, secs, used = OracleRunner(P, steps[0]).rate(levels, budget_s=args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d rotations of the workload's first items (levels %s) on one host core, %.1f s" %
+                         (done, used, secs)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": "batched rotation, N=2^16, 24x50-bit Q + 4x60-bit P, dnum 6, %d ciphertexts "
+                                       "at levels U{4..24}, steps U[1,2^15), one key per step" % len(levels),
+                           "keys": nkeys, "key_bytes": kbytes, "keygen_s": round(t_keys, 2),
+                           "mean_level": float(np.mean(levels)), "parallelism": "replicas" if world > 1 else "none",
+                           "l2": "inputs larger than L2 (keys %.1f GB)" % (kbytes / 1e9)},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fheon", choices=["fheon", "reference"])
+    ap.add_argument("--n-ct", type=int, default=256)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,284 @@
+/*
+ * fheon.h -- C ABI of the GB300 (sm_103a) RNS-CKKS rotation library behind
+ * FHEON's encrypted CNN layers (arxiv 2510.03996).
+ *
+ * FHEON (paper Sec. 5, "Support Functions") exposes context generation,
+ * key generation and key management, an encryption layer, the secure CNN
+ * layers of Sec. 4 and bootstrapping on top of RNS-CKKS (Sec. 2.2).  This
+ * library is the GPU arithmetic under those calls: the homomorphic rotation
+ * (Galois automorphism + hybrid key switching) and the plaintext-multiply,
+ * add and rescale steps around it, plus the packed special convolution of
+ * Sec. 4.3.
+ *
+ * Conventions shared by every call
+ *  - Every call returns int: FHEON_OK (0) or a negative FHEON_ERR_* code;
+ *    fheon_last_error() gives a message for the last failing call on a
+ *    context.  No call aborts the process.
+ *  - Results are returned through out-parameters.  Every handle (context,
+ *    keys, plaintext, ciphertext, layer) is owned by the caller and freed
+ *    with its matching *_destroy; destroying NULL is a no-op.
+ *  - Device memory comes from the allocator installed by
+ *    fheon_set_allocator() (default: cudaMalloc/cudaFree).  All device
+ *    work of a context is enqueued on its stream (a cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) and is asynchronous, except
+ *    the calls documented as blocking (downloads, decode, fheon_sync).
+ *  - Polynomials live on the device limb-major: u64[limbs][N], residues in
+ *    [0, m_i), in the evaluation (NTT) domain, slot j holding
+ *    a(psi_i^(2*brv(j)+1)) for the smallest primitive 2N-th root psi_i of
+ *    m_i.  A ciphertext at level l is u64[2][l][N] over q_0..q_{l-1}.
+ *    Host arrays passed to upload/download use the same layout.
+ *  - Slot i of a plaintext is the evaluation at zeta^(5^i mod 2N),
+ *    zeta = exp(i*pi/N); rotating by r moves slot i+r to slot i (r > 0 is
+ *    a left rotation), Galois element 5^r mod 2N.
+ *  - Supported sizes: N = 2^10 .. 2^17; primes of at most 61 bits with
+ *    q = 1 (mod 2N); digit count, digit size and P count each at most 16.
+ */
+#ifndef FHEON_H
+#define FHEON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Errors                                                             */
+/* ------------------------------------------------------------------ */
+#define FHEON_OK 0
+#define FHEON_ERR_ARG (-1)           /* bad argument, size or handle */
+#define FHEON_ERR_OOM (-2)           /* the allocator returned NULL */
+#define FHEON_ERR_NO_KEY (-3)        /* rotation key for that step missing */
+#define FHEON_ERR_LEVEL (-4)         /* operand levels incompatible */
+#define FHEON_ERR_SCALE (-5)         /* operand scales incompatible */
+#define FHEON_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
+#define FHEON_ERR_CUDA (-7)          /* a CUDA runtime call failed */
+#define FHEON_ERR_UNIMPLEMENTED (-8) /* not available in this build */
+
+typedef struct fheon_ctx fheon_ctx;
+typedef struct fheon_sk fheon_sk;
+typedef struct fheon_pk fheon_pk;
+typedef struct fheon_pt fheon_pt;
+typedef struct fheon_ct fheon_ct;
+typedef struct fheon_layer fheon_layer;
+
+/* Message for an error code (static storage). */
+const char *fheon_error_string(int code);
+/* Message of the last failing call on ctx (valid until the next call). */
+const char *fheon_last_error(const fheon_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Device memory                                                      */
+/* ------------------------------------------------------------------ */
+/* Allocation hook: returns device memory of `bytes` usable on `stream`,
+ * or NULL (the calling API function then fails with FHEON_ERR_OOM). */
+typedef void *(*fheon_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*fheon_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+/* Install the process-wide allocator used for every later allocation
+ * (NULL, NULL restores cudaMalloc/cudaFree).  Memory is freed through the
+ * hook that allocated it. */
+int fheon_set_allocator(fheon_alloc_fn alloc, fheon_free_fn free_fn, void *user);
+
+/* ------------------------------------------------------------------ */
+/* Context (paper Sec. 5, context generation)                         */
+/* ------------------------------------------------------------------ */
+/* Create a context for ring degree N with ciphertext moduli q[0..nq) and
+ * special moduli p[0..np), hybrid key switching with `dnum` digits
+ * (paper Sec. 6: "4 digits"; digit j = limbs [j*alpha, (j+1)*alpha) of Q,
+ * alpha = ceil(nq/dnum)), default scale `scale` and master seed `seed`
+ * (every random draw is ChaCha20 on (seed, purpose, index)).  Moduli must
+ * be distinct primes = 1 mod 2N.  Uploads all constant tables on `stream`.
+ * Errors: FHEON_ERR_ARG for unsupported sizes or non-NTT-friendly moduli. */
+int fheon_ctx_create(uint32_t N, const uint64_t *q, uint32_t nq, const uint64_t *p, uint32_t np,
+                     uint32_t dnum, double scale, uint64_t seed, void *stream, fheon_ctx **out);
+/* As fheon_ctx_create, choosing the moduli from bit sizes: for each size in
+ * the order qbits then pbits, the largest unused prime q < 2^bits with
+ * q = 1 (mod 2N). */
+int fheon_ctx_create_bits(uint32_t N, const uint32_t *qbits, uint32_t nq, const uint32_t *pbits,
+                          uint32_t np, uint32_t dnum, double scale, uint64_t seed, void *stream,
+                          fheon_ctx **out);
+int fheon_ctx_destroy(fheon_ctx *ctx);
+/* N, L (= nq), K (= np), alpha (limbs per digit), beta (digits at level L). */
+int fheon_ctx_info(const fheon_ctx *ctx, uint32_t *N, uint32_t *L, uint32_t *K, uint32_t *alpha,
+                   uint32_t *beta);
+/* The L+K moduli, Q first, into out[L+K]. */
+int fheon_ctx_moduli(const fheon_ctx *ctx, uint64_t *out);
+int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream);
+/* Block until all work enqueued on the context's stream is done. */
+int fheon_sync(fheon_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* Keys (paper Sec. 5, key generation and evaluation-key management)  */
+/* ------------------------------------------------------------------ */
+/* Secret key s (ternary, stream (seed, 1, 0)) and public key
+ * (b, a) = (-a*s + e, a) over Q_L; a uniform in the evaluation domain
+ * (stream (seed, 2, limb)), e discrete Gaussian sigma = 3.2 tail 20
+ * (stream (seed, 3, 0)).  Generated on the device. */
+int fheon_keygen(fheon_ctx *ctx, fheon_sk **sk, fheon_pk **pk);
+int fheon_sk_destroy(fheon_sk *sk);
+int fheon_pk_destroy(fheon_pk *pk);
+/* Blocking copy of s (evaluation form over all L+K moduli, u64[L+K][N]). */
+int fheon_sk_download(fheon_ctx *ctx, const fheon_sk *sk, uint64_t *host);
+/* Blocking copy of pk, u64[2][L][N] (b then a), canonical residues. */
+int fheon_pk_download(fheon_ctx *ctx, const fheon_pk *pk, uint64_t *host);
+
+/* Rotation keys for slot rotations steps[0..n) (Galois elements 5^r mod 2N;
+ * paper Sec. 5: the rotation indices each layer needs).  A key for g is
+ * beta digits of (b_j, a_j) over Q_L u P with
+ *   b_j = -a_j*s + e_j + [limb in digit j] * P * sigma_g(s),
+ * a_j uniform (stream (seed, 4, g<<32 | j<<16 | limb)), e_j Gaussian
+ * (stream (seed, 5, g<<32 | j<<16)).  Keys stay resident on the device;
+ * existing keys are kept. */
+int fheon_rotkeygen(fheon_ctx *ctx, const fheon_sk *sk, const int32_t *steps, uint32_t n);
+/* Same, by Galois element (odd g < 2N; 2N-1 is complex conjugation). */
+int fheon_galois_keygen(fheon_ctx *ctx, const fheon_sk *sk, const uint64_t *galois, uint32_t n);
+/* Drop the key of Galois element g (paper Sec. 5: keys loaded and cleared
+ * per block); FHEON_ERR_NO_KEY if absent. */
+int fheon_key_erase(fheon_ctx *ctx, uint64_t galois);
+/* Number of resident rotation keys and their device bytes. */
+int fheon_key_stats(const fheon_ctx *ctx, uint32_t *count, uint64_t *bytes);
+/* Blocking copy of the key of Galois element g, canonical residues,
+ * u64[beta][2][L+K][N] (component 0 = b, 1 = a). */
+int fheon_key_download(fheon_ctx *ctx, uint64_t galois, uint64_t *host);
+/* Galois element of a slot rotation by r (negative r allowed). */
+uint64_t fheon_galois_elt(const fheon_ctx *ctx, int32_t r);
+
+/* ------------------------------------------------------------------ */
+/* Plaintexts (paper Sec. 2.2, encoding C^{N/2} -> R)                 */
+/* ------------------------------------------------------------------ */
+/* Encode n <= N/2 complex slots (re, im; im may be NULL) at `scale` into a
+ * plaintext over Q_level: coefficients m_k = round(scale * tau^-1(z)_k)
+ * (FP64 special FFT on the device, round half away from zero), then RNS
+ * reduction and NTT.  Errors: FHEON_ERR_ARG if a coefficient exceeds 2^62. */
+int fheon_encode_plain(fheon_ctx *ctx, const double *re, const double *im, uint32_t n, uint32_t level,
+                       double scale, fheon_pt **out);
+/* Plaintext from N integer coefficients (host), over Q_level, tagged with
+ * `scale`. */
+int fheon_plain_from_coeffs(fheon_ctx *ctx, const int64_t *coeffs, uint32_t level, double scale,
+                            fheon_pt **out);
+/* Blocking: the integer coefficients the device encoder produces for z
+ * (same arithmetic as fheon_encode_plain, before RNS reduction). */
+int fheon_encode_coeffs(fheon_ctx *ctx, const double *re, const double *im, uint32_t n, double scale,
+                        int64_t *coeffs);
+/* Blocking decode of a plaintext into n slots (re, im; im may be NULL):
+ * INTT, centred lift from the lowest two limbs (exact while |m| < q0*q1/2),
+ * FP64 FFT, division by the plaintext's scale. */
+int fheon_decode(fheon_ctx *ctx, const fheon_pt *pt, double *re, double *im, uint32_t n);
+int fheon_pt_info(const fheon_pt *pt, uint32_t *level, double *scale);
+int fheon_pt_download(fheon_ctx *ctx, const fheon_pt *pt, uint64_t *host);
+int fheon_pt_destroy(fheon_pt *pt);
+
+/* ------------------------------------------------------------------ */
+/* Ciphertexts (paper Sec. 5, encryption layer)                       */
+/* ------------------------------------------------------------------ */
+/* Public-key encryption of pt (must be at level L):
+ * ct = (v*b + e0 + m, v*a + e1), v ternary, e0, e1 Gaussian, drawn from
+ * streams (seed, 6|7|8, nonce).  fheon_encrypt uses a per-context counter
+ * as the nonce. */
+int fheon_encrypt(fheon_ctx *ctx, const fheon_pk *pk, const fheon_pt *pt, fheon_ct **out);
+int fheon_encrypt_seeded(fheon_ctx *ctx, const fheon_pk *pk, const fheon_pt *pt, uint64_t nonce,
+                         fheon_ct **out);
+/* m = c0 + c1*s over Q_level, as a plaintext with the ciphertext's scale. */
+int fheon_decrypt(fheon_ctx *ctx, const fheon_sk *sk, const fheon_ct *ct, fheon_pt **out);
+/* Zero ciphertext at `level` with `scale`, for use as an output buffer. */
+int fheon_ct_create(fheon_ctx *ctx, uint32_t level, double scale, fheon_ct **out);
+int fheon_ct_destroy(fheon_ct *ct);
+int fheon_ct_info(const fheon_ct *ct, uint32_t *level, double *scale);
+/* Copy u64[2][level][N] residues from / to host memory on the context's
+ * stream.  Upload is asynchronous when `host` is pinned, else it blocks;
+ * download blocks.  Residues are not range-checked on upload. */
+int fheon_ct_upload(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host);
+int fheon_ct_download(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host);
+/* Device address of the ciphertext's u64[2][level][N] array. */
+int fheon_ct_device_ptr(const fheon_ct *ct, void **dptr);
+
+/* ------------------------------------------------------------------ */
+/* Homomorphic evaluation                                             */
+/* ------------------------------------------------------------------ */
+/* Rotation by `step` slots (paper Sec. 2.2 rotation; Alg. 1 Rot_k):
+ *   (c0, c1) -> (sigma_g(c0), sigma_g(c1)) in the evaluation domain, then
+ *   hybrid key switching of sigma_g(c1) from sigma_g(s) to s: INTT, ModUp
+ *   of each digit by fast base conversion, NTT, inner product with the
+ *   key, ModDown by P; out = (sigma_g(c0) + ks0, ks1).
+ * out is resized to in's level and takes its scale; out may equal in.
+ * Errors: FHEON_ERR_NO_KEY if no key for 5^step. */
+int fheon_rotate(fheon_ctx *ctx, const fheon_ct *in, int32_t step, fheon_ct *out);
+int fheon_rotate_galois(fheon_ctx *ctx, const fheon_ct *in, uint64_t galois, fheon_ct *out);
+
+/* One batched rotation request: rotate `in` by `step` into `out`. */
+typedef struct fheon_rot_item {
+    const fheon_ct *in;
+    fheon_ct *out;
+    int32_t step;
+} fheon_rot_item;
+/* Rotate many ciphertexts, at any mix of levels and steps, with one launch
+ * per pipeline stage over a device work list (instead of one launch
+ * sequence per ciphertext).  Bit-identical to n calls of fheon_rotate.
+ * Outputs must be distinct from every input of the batch. */
+int fheon_rotate_batch(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
+
+/* out = ct * pt slot-wise (paper Sec. 4.1, kernel-vector products); levels
+ * must match (the plaintext may be at a higher level: its lowest limbs are
+ * used); scale(out) = scale(ct) * scale(pt). */
+int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheon_ct *out);
+/* out = a + b; equal levels, scales equal to 1e-9 relative, else
+ * FHEON_ERR_LEVEL / FHEON_ERR_SCALE. */
+int fheon_add(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out);
+/* out = ct + pt (c0 only). */
+int fheon_add_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheon_ct *out);
+/* Floor rescale by the last prime q_t (paper Sec. 6, depth and rescaling):
+ * out_i = (x_i - [x]_{q_t}) * q_t^-1 mod q_i, level - 1, scale / q_t. */
+int fheon_rescale(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
+/* Keep the lowest `level` limbs (level <= in's level). */
+int fheon_drop_level(fheon_ctx *ctx, const fheon_ct *in, uint32_t level, fheon_ct *out);
+
+/* ------------------------------------------------------------------ */
+/* Secure layers (paper Sec. 4)                                       */
+/* ------------------------------------------------------------------ */
+/* Rotation steps a special ("same", stride 1) k x k convolution on a
+ * W-wide input needs: di*W + dj for every non-zero tap (di, dj) in
+ * [-(k-1)/2, (k-1)/2]^2, plus H*W for channel summation when in_ch > 1
+ * (paper Sec. 4.3 and Sec. 5 rotation-index analysis).  Writes at most
+ * *n entries, sets *n to the count. */
+int fheon_conv2d_rotation_steps(uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w, int32_t *out,
+                                uint32_t *n);
+/* Prepare a special convolution (paper Sec. 4.3, Alg. 1-3 generalised to
+ * odd k): one output channel per layer call, in_ch input channels packed
+ * at slot c*H*W + h*W + w, weights w[in_ch][k][k], optional bias.  The
+ * tap vectors (weight x boundary mask of Alg. 2/3) are encoded at scale
+ * q_{level-1} so that one rescale restores the input scale.
+ * stride must be 1 and pad (k-1)/2 (FHEON_ERR_UNIMPLEMENTED otherwise). */
+int fheon_conv2d_prepare(fheon_ctx *ctx, uint32_t in_ch, uint32_t k, uint32_t stride, uint32_t pad,
+                         uint32_t in_h, uint32_t in_w, const double *w, const double *bias,
+                         uint32_t level, double in_scale, fheon_layer **out);
+/* Prepare from caller-made tap plaintexts (k*k of them, taps row-major,
+ * each over Q_level) and an optional bias plaintext (level-1). */
+int fheon_conv2d_prepare_plain(fheon_ctx *ctx, uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w,
+                               uint32_t level, const fheon_pt *const *taps, const fheon_pt *bias,
+                               fheon_layer **out);
+/* Apply: for each tap, Rot_{di*W+dj}(in) * tap plaintext, summed, one
+ * rescale, channel sum by Rot_{H*W} (in_ch > 1), bias added. */
+int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
+/* prepare + apply + destroy in one call. */
+int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k, uint32_t stride,
+                 uint32_t pad, uint32_t in_h, uint32_t in_w, const double *w, const double *bias,
+                 fheon_ct *out);
+int fheon_layer_destroy(fheon_layer *layer);
+
+/* ------------------------------------------------------------------ */
+/* Instrumentation (no counterpart in the paper)                      */
+/* ------------------------------------------------------------------ */
+/* Start recording a CUDA event after every kernel this library launches on
+ * the context's stream (one open profile per process). */
+int fheon_profile_begin(fheon_ctx *ctx);
+/* Stop, synchronise, and write into out[cap] a JSON object
+ * {"kernel name": [launches, total device ms], ...}; the time of a launch is
+ * the gap between its event and the previous one on the stream.
+ * FHEON_ERR_ARG if cap is too small. */
+int fheon_profile_end(fheon_ctx *ctx, char *out, size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FHEON_H */

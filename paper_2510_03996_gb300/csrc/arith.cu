@@ -1,0 +1,204 @@
+// arith.cu -- slot-wise ciphertext arithmetic around the rotation: plaintext
+// products and sums (paper Sec. 4.1, kernel-vector products and their sum),
+// decryption, and floor rescaling by the last prime (paper Sec. 6, depth).
+// All are HBM-bound streams over u64[2][l][N]; each thread handles two
+// adjacent coefficients with 16-byte accesses.
+#include "jobs.cuh"
+
+namespace fheon {
+
+namespace {
+constexpr int TPB = 256;
+
+__device__ __forceinline__ u32 limb_of(u64 idx, u32 level, u32 logN) { return (u32)((idx >> logN) % level); }
+
+// out[b][i][n] = ct[b][i][n] * pt[i][n]
+__global__ void __launch_bounds__(TPB) mul_plain_kernel(const u64 *__restrict__ ct, const u64 *__restrict__ pt,
+                                                        u64 *__restrict__ out, u32 level, u32 logN,
+                                                        const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= 2 * per) return;
+    const u64 w = idx % per;
+    const ModConst m = mc[(u32)(w >> logN)];
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
+    const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(pt + w);
+    *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(mulmod_plain(x.x, y.x, m), mulmod_plain(x.y, y.y, m));
+}
+
+// out = a + b over `ncomp` components of `level` limbs
+__global__ void __launch_bounds__(TPB) add_kernel(const u64 *__restrict__ a, const u64 *__restrict__ b,
+                                                  u64 *__restrict__ out, u32 level, u32 ncomp, u32 logN,
+                                                  const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    if (idx >= ((u64)ncomp * level << logN)) return;
+    const u64 q = mc[limb_of(idx, level, logN)].q;
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a + idx);
+    const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b + idx);
+    *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(addmod(x.x, y.x, q), addmod(x.y, y.y, q));
+}
+
+// out = (c0 + pt, c1)
+__global__ void __launch_bounds__(TPB) add_plain_kernel(const u64 *__restrict__ ct, const u64 *__restrict__ pt,
+                                                        u64 *__restrict__ out, u32 level, u32 logN,
+                                                        const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= 2 * per) return;
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
+    ulonglong2 r = x;
+    if (idx < per) {
+        const u64 q = mc[(u32)(idx >> logN)].q;
+        const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(pt + idx);
+        r = make_ulonglong2(addmod(x.x, y.x, q), addmod(x.y, y.y, q));
+    }
+    *reinterpret_cast<ulonglong2 *>(out + idx) = r;
+}
+
+// m = c0 + c1 * s
+__global__ void __launch_bounds__(TPB) decrypt_kernel(const u64 *__restrict__ ct, const u64 *__restrict__ s,
+                                                      u64 *__restrict__ m, u32 level, u32 logN,
+                                                      const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= per) return;
+    const ModConst c = mc[(u32)(idx >> logN)];
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(ct + idx);
+    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(ct + per + idx);
+    const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(s + idx);
+    *reinterpret_cast<ulonglong2 *>(m + idx) =
+        make_ulonglong2(addmod(a.x, mulmod_plain(b.x, k.x, c), c.q), addmod(a.y, mulmod_plain(b.y, k.y, c), c.q));
+}
+
+// out[b][i] = (x[b][i] - y[b][i]) * q_t^-1 mod q_i, i < level-1 (x over `level` limbs)
+__global__ void __launch_bounds__(TPB) rescale_combine_kernel(const u64 *__restrict__ x, const u64 *__restrict__ y,
+                                                              u64 *__restrict__ out, u32 level, u32 logN, u32 L,
+                                                              const ulonglong2 *__restrict__ rinv,
+                                                              const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u32 lo = level - 1;
+    const u64 per = (u64)lo << logN;
+    if (idx >= 2 * per) return;
+    const u32 b = (u32)(idx / per);
+    const u64 w = idx % per;
+    const u32 i = (u32)(w >> logN);
+    const u64 q = mc[i].q;
+    const ulonglong2 f = rinv[(u64)lo * L + i];
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(x + (u64)b * ((u64)level << logN) + w);
+    const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(y + idx);
+    *reinterpret_cast<ulonglong2 *>(out + idx) =
+        make_ulonglong2(shoup(a.x + q - c.x, f.x, f.y, q), shoup(a.y + q - c.y, f.x, f.y, q));
+}
+
+// Forward NTT of [x]_{q_t} reduced into each q_i: limb position p of polynomial
+// b reads the coefficients of b's last limb (any value < 2^64 reduces exactly:
+// REDC(x * (2^64 mod q)) = x mod q).
+struct ReduceLoadJob : MapJob {
+    using Params = MapParams;
+    __device__ ReduceLoadJob(const MapParams &P, u32 job) : MapJob(P, job)
+    {
+        in = P.in + (job / P.per_poly) * P.in_poly_stride; // same source limb for every i
+    }
+    template <bool INV> __device__ u64 load_first(u32 J) const
+    {
+        const ModConst m = p.tp.mc[midx];
+        const u64 v = in[J];
+        return redc(__umul64hi(v, m.r1), v * m.r1, m.q, m.qneg_inv);
+    }
+};
+
+inline unsigned blocks2(u64 elems) { return (unsigned)((elems / 2 + TPB - 1) / TPB); }
+} // namespace
+
+cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level, u32)
+{
+    mul_plain_kernel<<<blocks2((u64)2 * level * ctx->N), TPB, 0, ctx->stream>>>(ct, pt, out, level, ctx->logN,
+                                                                                ctx->tab.mc.as<ModConst>());
+    prof_mark(ctx->stream, "mul_plain");
+    return cudaGetLastError();
+}
+cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 level, u32 ncomp)
+{
+    add_kernel<<<blocks2((u64)ncomp * level * ctx->N), TPB, 0, ctx->stream>>>(a, b, out, level, ncomp, ctx->logN,
+                                                                              ctx->tab.mc.as<ModConst>());
+    prof_mark(ctx->stream, "add");
+    return cudaGetLastError();
+}
+cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level)
+{
+    add_plain_kernel<<<blocks2((u64)2 * level * ctx->N), TPB, 0, ctx->stream>>>(ct, pt, out, level, ctx->logN,
+                                                                                ctx->tab.mc.as<ModConst>());
+    prof_mark(ctx->stream, "add_plain");
+    return cudaGetLastError();
+}
+cudaError_t k_decrypt(fheon_ctx *ctx, const u64 *ct, const u64 *s, u64 *m, u32 level)
+{
+    decrypt_kernel<<<blocks2((u64)level * ctx->N), TPB, 0, ctx->stream>>>(ct, s, m, level, ctx->logN,
+                                                                          ctx->tab.mc.as<ModConst>());
+    return cudaGetLastError();
+}
+
+cudaError_t ntt_fwd_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 level, u32 first_limb, cudaStream_t st)
+{
+    MapParams mp = map_params(ctx, in, out, n, first_limb, level);
+    return ntt::launch<false, MapJob>(ctx->logN, mp, n, st);
+}
+cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 level, u32 first_limb, cudaStream_t st)
+{
+    MapParams mp = map_params(ctx, in, out, n, first_limb, level);
+    return ntt::launch<true, MapJob>(ctx->logN, mp, n, st);
+}
+
+int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)
+{
+    const u32 l = in->level, N = ctx->N, t = l - 1;
+    const size_t need = 2 + (size_t)2 * t + 2 * (size_t)t; // last-limb coeffs, y, staging
+    int rc = ensure_workspace(ctx, need > ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L
+                                       ? need
+                                       : ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L);
+    if (rc) return rc;
+    cudaStream_t st = ctx->stream;
+    u64 *xl = ctx->ws.as<u64>();       // [2][N] coefficients of the last limb
+    u64 *y = xl + (u64)2 * N;          // [2][t][N]
+    u64 *stage = y + (u64)2 * t * N;   // [2][t][N]
+    // INTT of the last limb of c0 and c1 (modulus q_t)
+    {
+        MapParams mp = map_params(ctx, in->c0() + (u64)t * N, xl, 1, t, l);
+        mp.in_poly_stride = (u64)l * N;
+        mp.out_poly_stride = N;
+        FHEON_CUDA(ctx, (ntt::launch<true, MapJob>(ctx->logN, mp, 2, st)));
+    }
+    // [x]_{q_t} into every q_i, i < t, forward NTT
+    {
+        MapParams mp = map_params(ctx, xl, y, t, 0, t);
+        mp.in_poly_stride = N;
+        mp.out_poly_stride = (u64)t * N;
+        FHEON_CUDA(ctx, (ntt::launch<false, ReduceLoadJob>(ctx->logN, mp, 2 * t, st)));
+    }
+    const bool inplace = (out == in);
+    u64 *dst = stage;
+    if (!inplace) {
+        rc = ct_reshape(ctx, out, t);
+        if (rc) return rc;
+        dst = out->c0();
+    }
+    const double sc = in->scale / (double)ctx->mod[t];
+    rescale_combine_kernel<<<blocks2((u64)2 * t * N), TPB, 0, st>>>(in->c0(), y, dst, l, ctx->logN, ctx->L,
+                                                                     ctx->tab.rescale_inv.as<ulonglong2>(),
+                                                                     ctx->tab.mc.as<ModConst>());
+    prof_mark(st, "rescale_combine");
+    FHEON_CUDA(ctx, cudaGetLastError());
+    if (inplace) {
+        FHEON_CUDA(ctx, cudaMemcpyAsync(out->c0(), stage, (size_t)2 * t * ctx->limb_bytes(), cudaMemcpyDeviceToDevice, st));
+        out->level = t;
+    }
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+} // namespace fheon

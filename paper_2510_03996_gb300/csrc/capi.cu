@@ -1,0 +1,664 @@
+// capi.cu -- the extern "C" surface of libfheon: allocator hook, errors,
+// context creation (constant tables), handles, and dispatch to the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+using namespace fheon;
+
+// ------------------------------------------------------------------ allocator
+namespace {
+std::mutex g_alloc_mu;
+fheon_alloc_fn g_alloc = nullptr;
+fheon_free_fn g_free = nullptr;
+void *g_alloc_user = nullptr;
+}
+
+namespace fheon {
+void *dev_alloc(size_t bytes, cudaStream_t st)
+{
+    fheon_alloc_fn a;
+    void *u;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        u = g_alloc_user;
+    }
+    if (a) return a(bytes, (void *)st, u);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void dev_free(void *p, size_t bytes, cudaStream_t st)
+{
+    fheon_free_fn f;
+    void *u;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_free;
+        u = g_alloc_user;
+    }
+    if (f) f(p, bytes, (void *)st, u);
+    else cudaFree(p);
+}
+
+int fail(fheon_ctx *ctx, int code, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return code;
+}
+int cuda_fail(fheon_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, e == cudaErrorMemoryAllocation ? FHEON_ERR_OOM : FHEON_ERR_CUDA, "%s: %s", where,
+                cudaGetErrorString(e));
+}
+
+int ct_reshape(fheon_ctx *ctx, fheon_ct *ct, u32 level)
+{
+    if (ct->cap >= level && ct->c.p) {
+        ct->level = level;
+        return FHEON_OK;
+    }
+    if (!ct->c.alloc((size_t)2 * level * ctx->N * 8, ctx->stream))
+        return fail(ctx, FHEON_ERR_OOM, "ciphertext allocation of %u limbs failed", 2 * level);
+    ct->cap = level;
+    ct->level = level;
+    return FHEON_OK;
+}
+
+int ensure_workspace(fheon_ctx *ctx, size_t limbs)
+{
+    if (ctx->ws_limbs >= limbs) return FHEON_OK;
+    if (!ctx->ws.alloc(limbs * ctx->limb_bytes(), ctx->stream))
+        return fail(ctx, FHEON_ERR_OOM, "workspace of %zu limbs failed", limbs);
+    ctx->ws_limbs = limbs;
+    return FHEON_OK;
+}
+} // namespace fheon
+
+size_t fheon_ctx::ks_ws_limbs(u32 l) const
+{
+    const size_t b = beta_at(l);
+    return (size_t)l + b * (l + K) + 2 * (size_t)(l + K) + 2 * (size_t)K + 2 * (size_t)l;
+}
+
+extern "C" {
+
+const char *fheon_error_string(int code)
+{
+    switch (code) {
+    case FHEON_OK: return "ok";
+    case FHEON_ERR_ARG: return "invalid argument";
+    case FHEON_ERR_OOM: return "device allocation failed";
+    case FHEON_ERR_NO_KEY: return "rotation key missing";
+    case FHEON_ERR_LEVEL: return "level mismatch";
+    case FHEON_ERR_SCALE: return "scale mismatch";
+    case FHEON_ERR_TIMEOUT: return "device wait timed out";
+    case FHEON_ERR_CUDA: return "CUDA runtime error";
+    case FHEON_ERR_UNIMPLEMENTED: return "not implemented";
+    default: return "unknown error";
+    }
+}
+
+const char *fheon_last_error(const fheon_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+int fheon_set_allocator(fheon_alloc_fn alloc, fheon_free_fn free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return FHEON_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = user;
+    return FHEON_OK;
+}
+
+// ------------------------------------------------------------------ context
+static int upload(fheon_ctx *ctx, DevMem &m, const void *host, size_t bytes)
+{
+    if (!m.alloc(bytes, ctx->stream)) return fail(ctx, FHEON_ERR_OOM, "table allocation failed");
+    FHEON_CUDA(ctx, cudaMemcpyAsync(m.p, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream)); // host staging buffers are freed on return
+    return FHEON_OK;
+}
+
+static int build_tables(fheon_ctx *ctx)
+{
+    const u32 N = ctx->N, L = ctx->L, K = ctx->K, A = ctx->alpha, B = ctx->beta, n = L + K;
+    const u64 *m = ctx->mod.data();
+    int rc;
+    // NTT twiddles
+    std::vector<ulonglong2> fw((size_t)n * N), iv((size_t)n * N);
+    std::vector<ulonglong2> ninv(n);
+    std::vector<u64> pw(N), pwi(N);
+    for (u32 i = 0; i < n; i++) {
+        const u64 q = m[i], psi = h_min_root(q, N), psii = h_invmod(psi, q);
+        pw[0] = pwi[0] = 1;
+        for (u32 e = 1; e < N; e++) {
+            pw[e] = h_mulmod(pw[e - 1], psi, q);
+            pwi[e] = h_mulmod(pwi[e - 1], psii, q);
+        }
+        for (u32 k = 0; k < N; k++) {
+            u32 r = 0;
+            for (u32 b = 0; b < ctx->logN; b++) r |= ((k >> b) & 1u) << (ctx->logN - 1 - b);
+            fw[(size_t)i * N + k] = make_ulonglong2(pw[r], h_shoup(pw[r], q));
+            iv[(size_t)i * N + k] = make_ulonglong2(pwi[r], h_shoup(pwi[r], q));
+        }
+        const u64 ni = h_invmod(N % q, q);
+        ninv[i] = make_ulonglong2(ni, h_shoup(ni, q));
+    }
+    if ((rc = upload(ctx, ctx->tab.mc, ctx->mc.data(), sizeof(ModConst) * n))) return rc;
+    if ((rc = upload(ctx, ctx->tab.tw_fwd, fw.data(), fw.size() * sizeof(ulonglong2)))) return rc;
+    if ((rc = upload(ctx, ctx->tab.tw_inv, iv.data(), iv.size() * sizeof(ulonglong2)))) return rc;
+    if ((rc = upload(ctx, ctx->tab.ninv, ninv.data(), ninv.size() * sizeof(ulonglong2)))) return rc;
+
+    auto mont = [&](u64 x, u32 t) { return h_mulmod(x % m[t], ctx->mc[t].r1, m[t]); };
+    // ModUp: digit j of size d (its limbs j*A .. j*A+d-1)
+    std::vector<ulonglong2> us((size_t)B * A * A, make_ulonglong2(0, 0));
+    std::vector<u64> uc((size_t)B * A * A * n, 0);
+    for (u32 j = 0; j < B; j++)
+        for (u32 d = 1; d <= A; d++) {
+            if (j * A + d > L) break;
+            for (u32 il = 0; il < d; il++) {
+                const u32 i = j * A + il;
+                u64 dh = 1;
+                for (u32 k = 0; k < d; k++)
+                    if (k != il) dh = h_mulmod(dh, m[j * A + k] % m[i], m[i]);
+                const u64 sc = h_mulmod(h_invmod(dh, m[i]), ninv[i].x, m[i]);
+                us[((size_t)j * A + (d - 1)) * A + il] = make_ulonglong2(sc, h_shoup(sc, m[i]));
+                for (u32 t = 0; t < n; t++) {
+                    u64 v = 1;
+                    for (u32 k = 0; k < d; k++)
+                        if (k != il) v = h_mulmod(v, m[j * A + k] % m[t], m[t]);
+                    uc[(((size_t)j * A + (d - 1)) * A + il) * n + t] = mont(v, t);
+                }
+            }
+        }
+    if ((rc = upload(ctx, ctx->tab.modup_scale, us.data(), us.size() * sizeof(ulonglong2)))) return rc;
+    if ((rc = upload(ctx, ctx->tab.modup_conv, uc.data(), uc.size() * sizeof(u64)))) return rc;
+
+    // ModDown
+    std::vector<ulonglong2> ds(K), pinv(L), pmod(n);
+    std::vector<u64> dc((size_t)K * L);
+    for (u32 k = 0; k < K; k++) {
+        const u32 pk = L + k;
+        u64 ph = 1;
+        for (u32 k2 = 0; k2 < K; k2++)
+            if (k2 != k) ph = h_mulmod(ph, m[L + k2] % m[pk], m[pk]);
+        const u64 sc = h_mulmod(h_invmod(ph, m[pk]), ninv[pk].x, m[pk]);
+        ds[k] = make_ulonglong2(sc, h_shoup(sc, m[pk]));
+        for (u32 i = 0; i < L; i++) {
+            u64 v = 1;
+            for (u32 k2 = 0; k2 < K; k2++)
+                if (k2 != k) v = h_mulmod(v, m[L + k2] % m[i], m[i]);
+            dc[(size_t)k * L + i] = mont(v, i);
+        }
+    }
+    for (u32 t = 0; t < n; t++) {
+        u64 P = 1;
+        for (u32 k = 0; k < K; k++) P = h_mulmod(P, m[L + k] % m[t], m[t]);
+        pmod[t] = make_ulonglong2(P, h_shoup(P, m[t]));
+        if (t < L) {
+            const u64 pi = h_invmod(P, m[t]);
+            pinv[t] = make_ulonglong2(pi, h_shoup(pi, m[t]));
+        }
+    }
+    if ((rc = upload(ctx, ctx->tab.moddown_scale, ds.data(), ds.size() * sizeof(ulonglong2)))) return rc;
+    if ((rc = upload(ctx, ctx->tab.moddown_conv, dc.data(), dc.size() * sizeof(u64)))) return rc;
+    if ((rc = upload(ctx, ctx->tab.pinv, pinv.data(), pinv.size() * sizeof(ulonglong2)))) return rc;
+    if ((rc = upload(ctx, ctx->tab.pmod, pmod.data(), pmod.size() * sizeof(ulonglong2)))) return rc;
+
+    // rescale: [t][i] = q_t^-1 mod q_i
+    std::vector<ulonglong2> ri((size_t)L * L, make_ulonglong2(0, 0));
+    for (u32 t = 1; t < L; t++)
+        for (u32 i = 0; i < t; i++) {
+            const u64 v = h_invmod(m[t] % m[i], m[i]);
+            ri[(size_t)t * L + i] = make_ulonglong2(v, h_shoup(v, m[i]));
+        }
+    if ((rc = upload(ctx, ctx->tab.rescale_inv, ri.data(), ri.size() * sizeof(ulonglong2)))) return rc;
+
+    u64 cdt[41];
+    h_cdt_table(3.2, 20, cdt);
+    if ((rc = upload(ctx, ctx->tab.cdt, cdt, sizeof cdt))) return rc;
+    return build_fft_tables(ctx);
+}
+
+static int ctx_create_impl(u32 N, std::vector<u64> mods, u32 nq, u32 np, u32 dnum, double scale, u64 seed,
+                           void *stream, fheon_ctx **out)
+{
+    if (!out) return FHEON_ERR_ARG;
+    *out = nullptr;
+    u32 logN = 0;
+    while ((1u << logN) < N) logN++;
+    if ((1u << logN) != N || logN < 10 || logN > 17) return FHEON_ERR_ARG;
+    if (nq < 1 || np < 1 || np > 16 || dnum < 1 || dnum > nq) return FHEON_ERR_ARG;
+    const u32 alpha = (nq + dnum - 1) / dnum, beta = (nq + alpha - 1) / alpha;
+    if (alpha > 16 || beta > 16) return FHEON_ERR_ARG;
+    u64 qmax = 0;
+    for (size_t i = 0; i < mods.size(); i++) {
+        const u64 q = mods[i];
+        if (q >= (1ull << 61) || q % (2ull * N) != 1 || !h_is_prime(q)) return FHEON_ERR_ARG;
+        for (size_t k = 0; k < i; k++)
+            if (mods[k] == q) return FHEON_ERR_ARG;
+        qmax = q > qmax ? q : qmax;
+    }
+    // lazy accumulations of up to 16 products of residues < qmax reduce by one REDC
+    if ((unsigned __int128)qmax * 16 >= ((unsigned __int128)1 << 64)) return FHEON_ERR_ARG;
+    fheon_ctx *ctx = new fheon_ctx();
+    ctx->N = N;
+    ctx->logN = logN;
+    ctx->L = nq;
+    ctx->K = np;
+    ctx->dnum = dnum;
+    ctx->alpha = alpha;
+    ctx->beta = beta;
+    ctx->scale = scale;
+    ctx->seed = seed;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->mod = mods;
+    for (u64 q : mods) ctx->mc.push_back(h_modconst(q));
+    int rc = build_tables(ctx);
+    if (rc) {
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return FHEON_OK;
+}
+
+int fheon_ctx_create(uint32_t N, const uint64_t *q, uint32_t nq, const uint64_t *p, uint32_t np, uint32_t dnum,
+                     double scale, uint64_t seed, void *stream, fheon_ctx **out)
+{
+    if (!q || !p) return FHEON_ERR_ARG;
+    std::vector<u64> mods(q, q + nq);
+    mods.insert(mods.end(), p, p + np);
+    return ctx_create_impl(N, mods, nq, np, dnum, scale, seed, stream, out);
+}
+
+int fheon_ctx_create_bits(uint32_t N, const uint32_t *qbits, uint32_t nq, const uint32_t *pbits, uint32_t np,
+                          uint32_t dnum, double scale, uint64_t seed, void *stream, fheon_ctx **out)
+{
+    if (!qbits || !pbits || N < 1024 || N > (1u << 17)) return FHEON_ERR_ARG;
+    std::vector<u32> bits(qbits, qbits + nq);
+    bits.insert(bits.end(), pbits, pbits + np);
+    std::vector<u64> mods;
+    if (!h_pick_primes(N, bits, mods)) return FHEON_ERR_ARG;
+    return ctx_create_impl(N, mods, nq, np, dnum, scale, seed, stream, out);
+}
+
+int fheon_ctx_destroy(fheon_ctx *ctx)
+{
+    if (!ctx) return FHEON_OK;
+    cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    return FHEON_OK;
+}
+
+int fheon_ctx_info(const fheon_ctx *ctx, uint32_t *N, uint32_t *L, uint32_t *K, uint32_t *alpha, uint32_t *beta)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    if (N) *N = ctx->N;
+    if (L) *L = ctx->L;
+    if (K) *K = ctx->K;
+    if (alpha) *alpha = ctx->alpha;
+    if (beta) *beta = ctx->beta;
+    return FHEON_OK;
+}
+
+int fheon_ctx_moduli(const fheon_ctx *ctx, uint64_t *out)
+{
+    if (!ctx || !out) return FHEON_ERR_ARG;
+    memcpy(out, ctx->mod.data(), ctx->mod.size() * sizeof(u64));
+    return FHEON_OK;
+}
+
+int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return FHEON_OK;
+}
+
+int fheon_sync(fheon_ctx *ctx)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FHEON_OK;
+}
+
+// ------------------------------------------------------------------ keys
+int fheon_keygen(fheon_ctx *ctx, fheon_sk **sk, fheon_pk **pk)
+{
+    if (!ctx || !sk || !pk) return FHEON_ERR_ARG;
+    fheon_sk *s = new fheon_sk();
+    fheon_pk *p = new fheon_pk();
+    int rc = keygen_dev(ctx, s, p);
+    if (rc) {
+        delete s;
+        delete p;
+        return rc;
+    }
+    *sk = s;
+    *pk = p;
+    return FHEON_OK;
+}
+int fheon_sk_destroy(fheon_sk *sk) { delete sk; return FHEON_OK; }
+int fheon_pk_destroy(fheon_pk *pk) { delete pk; return FHEON_OK; }
+
+static int download(fheon_ctx *ctx, const void *dev, void *host, size_t bytes)
+{
+    FHEON_CUDA(ctx, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return FHEON_OK;
+}
+
+int fheon_sk_download(fheon_ctx *ctx, const fheon_sk *sk, uint64_t *host)
+{
+    if (!ctx || !sk || !host) return FHEON_ERR_ARG;
+    return download(ctx, sk->s.p, host, (size_t)(ctx->L + ctx->K) * ctx->limb_bytes());
+}
+int fheon_pk_download(fheon_ctx *ctx, const fheon_pk *pk, uint64_t *host)
+{
+    if (!ctx || !pk || !host) return FHEON_ERR_ARG;
+    return download(ctx, pk->b.p, host, (size_t)2 * ctx->L * ctx->limb_bytes());
+}
+
+uint64_t fheon_galois_elt(const fheon_ctx *ctx, int32_t r)
+{
+    if (!ctx) return 0;
+    const int64_t n = ctx->N / 2;
+    int64_t e = ((int64_t)r % n + n) % n;
+    return h_powmod(5, (u64)e, 2ull * ctx->N);
+}
+
+int fheon_galois_keygen(fheon_ctx *ctx, const fheon_sk *sk, const uint64_t *galois, uint32_t n)
+{
+    if (!ctx || !sk || (n && !galois)) return FHEON_ERR_ARG;
+    for (u32 i = 0; i < n; i++) {
+        const u64 g = galois[i];
+        if ((g & 1) == 0 || g >= 2ull * ctx->N) return fail(ctx, FHEON_ERR_ARG, "bad Galois element %llu", g);
+        if (ctx->keys.count(g)) continue;
+        RotKey key;
+        int rc = galois_key_dev(ctx, sk, g, key);
+        if (rc) return rc;
+        ctx->keys.emplace(g, std::move(key));
+    }
+    return FHEON_OK;
+}
+
+int fheon_rotkeygen(fheon_ctx *ctx, const fheon_sk *sk, const int32_t *steps, uint32_t n)
+{
+    if (!ctx || !sk || (n && !steps)) return FHEON_ERR_ARG;
+    std::vector<uint64_t> gs(n);
+    for (u32 i = 0; i < n; i++) gs[i] = fheon_galois_elt(ctx, steps[i]);
+    return fheon_galois_keygen(ctx, sk, gs.data(), n);
+}
+
+int fheon_key_erase(fheon_ctx *ctx, uint64_t galois)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    auto it = ctx->keys.find(galois);
+    if (it == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "no key for Galois element %llu", galois);
+    cudaStreamSynchronize(ctx->stream); // the key may be in use by queued work
+    ctx->keys.erase(it);
+    return FHEON_OK;
+}
+
+int fheon_key_stats(const fheon_ctx *ctx, uint32_t *count, uint64_t *bytes)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    u64 b = 0;
+    for (auto &kv : ctx->keys) b += kv.second.mem.bytes;
+    if (count) *count = (u32)ctx->keys.size();
+    if (bytes) *bytes = b;
+    return FHEON_OK;
+}
+
+int fheon_key_download(fheon_ctx *ctx, uint64_t galois, uint64_t *host)
+{
+    if (!ctx || !host) return FHEON_ERR_ARG;
+    auto it = ctx->keys.find(galois);
+    if (it == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "no key for Galois element %llu", galois);
+    const size_t per = (size_t)(ctx->L + ctx->K);
+    DevMem tmp;
+    if (!tmp.alloc(it->second.mem.bytes, ctx->stream)) return fail(ctx, FHEON_ERR_OOM, "key download buffer");
+    FHEON_CUDA(ctx, key_from_mont(ctx, it->second.mem.as<u64>(), tmp.as<u64>(), per, 2 * ctx->beta));
+    return download(ctx, tmp.p, host, it->second.mem.bytes);
+}
+
+// ------------------------------------------------------------------ plaintexts
+int fheon_plain_from_coeffs(fheon_ctx *ctx, const int64_t *coeffs, uint32_t level, double scale, fheon_pt **out)
+{
+    if (!ctx || !coeffs || !out || level < 1 || level > ctx->L) return FHEON_ERR_ARG;
+    fheon_pt *pt = new fheon_pt();
+    pt->level = level;
+    pt->scale = scale;
+    int rc = plain_from_coeffs_dev(ctx, coeffs, level, pt);
+    if (rc) { delete pt; return rc; }
+    *out = pt;
+    return FHEON_OK;
+}
+
+int fheon_encode_plain(fheon_ctx *ctx, const double *re, const double *im, uint32_t n, uint32_t level,
+                       double scale, fheon_pt **out)
+{
+    if (!ctx || !re || !out || n > ctx->N / 2 || level < 1 || level > ctx->L || !(scale > 0)) return FHEON_ERR_ARG;
+    fheon_pt *pt = new fheon_pt();
+    pt->level = level;
+    pt->scale = scale;
+    int rc = encode_dev(ctx, re, im, n, scale, level, pt, nullptr);
+    if (rc) { delete pt; return rc; }
+    *out = pt;
+    return FHEON_OK;
+}
+
+int fheon_encode_coeffs(fheon_ctx *ctx, const double *re, const double *im, uint32_t n, double scale,
+                        int64_t *coeffs)
+{
+    if (!ctx || !re || !coeffs || n > ctx->N / 2 || !(scale > 0)) return FHEON_ERR_ARG;
+    return encode_dev(ctx, re, im, n, scale, 0, nullptr, coeffs);
+}
+
+int fheon_decode(fheon_ctx *ctx, const fheon_pt *pt, double *re, double *im, uint32_t n)
+{
+    if (!ctx || !pt || !re || n > ctx->N / 2) return FHEON_ERR_ARG;
+    return decode_dev(ctx, pt, re, im, n);
+}
+
+int fheon_pt_info(const fheon_pt *pt, uint32_t *level, double *scale)
+{
+    if (!pt) return FHEON_ERR_ARG;
+    if (level) *level = pt->level;
+    if (scale) *scale = pt->scale;
+    return FHEON_OK;
+}
+int fheon_pt_download(fheon_ctx *ctx, const fheon_pt *pt, uint64_t *host)
+{
+    if (!ctx || !pt || !host) return FHEON_ERR_ARG;
+    return download(ctx, pt->m.p, host, (size_t)pt->level * ctx->limb_bytes());
+}
+int fheon_pt_destroy(fheon_pt *pt) { delete pt; return FHEON_OK; }
+
+// ------------------------------------------------------------------ ciphertexts
+int fheon_encrypt_seeded(fheon_ctx *ctx, const fheon_pk *pk, const fheon_pt *pt, uint64_t nonce, fheon_ct **out)
+{
+    if (!ctx || !pk || !pt || !out) return FHEON_ERR_ARG;
+    if (pt->level != ctx->L) return fail(ctx, FHEON_ERR_LEVEL, "encrypt needs a plaintext at level L");
+    fheon_ct *ct = new fheon_ct();
+    int rc = encrypt_dev(ctx, pk, pt, nonce, ct);
+    if (rc) { delete ct; return rc; }
+    ct->scale = pt->scale;
+    *out = ct;
+    return FHEON_OK;
+}
+int fheon_encrypt(fheon_ctx *ctx, const fheon_pk *pk, const fheon_pt *pt, fheon_ct **out)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    return fheon_encrypt_seeded(ctx, pk, pt, (1ull << 63) | ctx->enc_counter++, out);
+}
+
+int fheon_decrypt(fheon_ctx *ctx, const fheon_sk *sk, const fheon_ct *ct, fheon_pt **out)
+{
+    if (!ctx || !sk || !ct || !out) return FHEON_ERR_ARG;
+    fheon_pt *pt = new fheon_pt();
+    pt->level = ct->level;
+    pt->scale = ct->scale;
+    if (!pt->m.alloc((size_t)ct->level * ctx->limb_bytes(), ctx->stream)) {
+        delete pt;
+        return fail(ctx, FHEON_ERR_OOM, "plaintext allocation");
+    }
+    cudaError_t e = k_decrypt(ctx, ct->c0(), sk->s.as<u64>(), pt->m.as<u64>(), ct->level);
+    if (e != cudaSuccess) { delete pt; return cuda_fail(ctx, e, "decrypt"); }
+    *out = pt;
+    return FHEON_OK;
+}
+
+int fheon_ct_create(fheon_ctx *ctx, uint32_t level, double scale, fheon_ct **out)
+{
+    if (!ctx || !out || level < 1 || level > ctx->L) return FHEON_ERR_ARG;
+    fheon_ct *ct = new fheon_ct();
+    int rc = ct_reshape(ctx, ct, level);
+    if (rc) { delete ct; return rc; }
+    ct->scale = scale;
+    cudaError_t e = cudaMemsetAsync(ct->c.p, 0, (size_t)2 * level * ctx->limb_bytes(), ctx->stream);
+    if (e != cudaSuccess) { delete ct; return cuda_fail(ctx, e, "memset"); }
+    *out = ct;
+    return FHEON_OK;
+}
+int fheon_ct_destroy(fheon_ct *ct) { delete ct; return FHEON_OK; }
+int fheon_ct_info(const fheon_ct *ct, uint32_t *level, double *scale)
+{
+    if (!ct) return FHEON_ERR_ARG;
+    if (level) *level = ct->level;
+    if (scale) *scale = ct->scale;
+    return FHEON_OK;
+}
+int fheon_ct_upload(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host)
+{
+    if (!ctx || !ct || !host) return FHEON_ERR_ARG;
+    FHEON_CUDA(ctx, cudaMemcpyAsync(ct->c.p, host, (size_t)2 * ct->level * ctx->limb_bytes(),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+    return FHEON_OK;
+}
+int fheon_ct_download(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host)
+{
+    if (!ctx || !ct || !host) return FHEON_ERR_ARG;
+    return download(ctx, ct->c.p, host, (size_t)2 * ct->level * ctx->limb_bytes());
+}
+int fheon_ct_device_ptr(const fheon_ct *ct, void **dptr)
+{
+    if (!ct || !dptr) return FHEON_ERR_ARG;
+    *dptr = ct->c.p;
+    return FHEON_OK;
+}
+
+// ------------------------------------------------------------------ evaluation
+int fheon_rotate_galois(fheon_ctx *ctx, const fheon_ct *in, uint64_t galois, fheon_ct *out)
+{
+    if (!ctx || !in || !out) return FHEON_ERR_ARG;
+    if ((galois & 1) == 0 || galois >= 2ull * ctx->N) return fail(ctx, FHEON_ERR_ARG, "bad Galois element");
+    return rotate_one(ctx, in, galois, out);
+}
+int fheon_rotate(fheon_ctx *ctx, const fheon_ct *in, int32_t step, fheon_ct *out)
+{
+    if (!ctx) return FHEON_ERR_ARG;
+    return fheon_rotate_galois(ctx, in, fheon_galois_elt(ctx, step), out);
+}
+int fheon_rotate_batch(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
+{
+    if (!ctx || (n && !items)) return FHEON_ERR_ARG;
+    return rotate_many(ctx, items, n);
+}
+
+static bool scales_match(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
+
+int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheon_ct *out)
+{
+    if (!ctx || !ct || !pt || !out) return FHEON_ERR_ARG;
+    if (pt->level < ct->level) return fail(ctx, FHEON_ERR_LEVEL, "plaintext level %u < ciphertext level %u", pt->level, ct->level);
+    const u32 l = ct->level;
+    const double sc = ct->scale * pt->scale;
+    if (out != ct) {
+        int rc = ct_reshape(ctx, out, l);
+        if (rc) return rc;
+    }
+    FHEON_CUDA(ctx, k_mul_plain(ctx, ct->c0(), pt->m.as<u64>(), out->c0(), l, 0));
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_add(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out)
+{
+    if (!ctx || !a || !b || !out) return FHEON_ERR_ARG;
+    if (a->level != b->level) return fail(ctx, FHEON_ERR_LEVEL, "add: levels %u and %u", a->level, b->level);
+    if (!scales_match(a->scale, b->scale)) return fail(ctx, FHEON_ERR_SCALE, "add: scales differ");
+    const u32 l = a->level;
+    const double sc = a->scale;
+    if (out != a && out != b) {
+        int rc = ct_reshape(ctx, out, l);
+        if (rc) return rc;
+    }
+    FHEON_CUDA(ctx, k_add(ctx, a->c0(), b->c0(), out->c0(), l, 2));
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_add_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheon_ct *out)
+{
+    if (!ctx || !ct || !pt || !out) return FHEON_ERR_ARG;
+    if (pt->level < ct->level) return fail(ctx, FHEON_ERR_LEVEL, "add_plain: plaintext level too low");
+    if (!scales_match(ct->scale, pt->scale)) return fail(ctx, FHEON_ERR_SCALE, "add_plain: scales differ");
+    const u32 l = ct->level;
+    const double sc = ct->scale;
+    if (out != ct) {
+        int rc = ct_reshape(ctx, out, l);
+        if (rc) return rc;
+    }
+    FHEON_CUDA(ctx, k_add_plain(ctx, ct->c0(), pt->m.as<u64>(), out->c0(), l));
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_rescale(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !in || !out) return FHEON_ERR_ARG;
+    if (in->level < 2) return fail(ctx, FHEON_ERR_LEVEL, "rescale needs level >= 2");
+    return rescale_ct(ctx, in, out);
+}
+
+int fheon_drop_level(fheon_ctx *ctx, const fheon_ct *in, uint32_t level, fheon_ct *out)
+{
+    if (!ctx || !in || !out || level < 1 || level > in->level) return FHEON_ERR_ARG;
+    const size_t lb = ctx->limb_bytes();
+    if (out == in) {
+        // move c1's lowest limbs down next to c0's, one limb at a time so that
+        // no copy overlaps itself and no source limb is overwritten first
+        u64 *c1 = in->c1(ctx->N);
+        for (u32 i = 0; i < level && level < in->level; i++)
+            FHEON_CUDA(ctx, cudaMemcpyAsync(in->c0() + (size_t)(level + i) * ctx->N, c1 + (size_t)i * ctx->N, lb,
+                                            cudaMemcpyDeviceToDevice, ctx->stream));
+        out->level = level;
+        return FHEON_OK;
+    }
+    int rc = ct_reshape(ctx, out, level);
+    if (rc) return rc;
+    FHEON_CUDA(ctx, cudaMemcpyAsync(out->c0(), in->c0(), level * lb, cudaMemcpyDeviceToDevice, ctx->stream));
+    FHEON_CUDA(ctx, cudaMemcpyAsync(out->c1(ctx->N), in->c1(ctx->N), level * lb, cudaMemcpyDeviceToDevice, ctx->stream));
+    out->scale = in->scale;
+    return FHEON_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,175 @@
+// internal.h -- context, handles and device tables of libfheon.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fheon.h"
+#include "modarith.cuh"
+
+namespace fheon {
+
+// ------------------------------------------------------------ allocation
+void *dev_alloc(size_t bytes, cudaStream_t st);
+void dev_free(void *p, size_t bytes, cudaStream_t st);
+
+struct DevMem {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    DevMem() = default;
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes), st(o.st) { o.p = nullptr; o.bytes = 0; }
+    DevMem &operator=(DevMem &&o) noexcept
+    {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; st = o.st; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevMem() { release(); }
+    bool alloc(size_t n, cudaStream_t s)
+    {
+        release();
+        st = s;
+        if (n == 0) return true;
+        p = dev_alloc(n, s);
+        if (!p) return false;
+        bytes = n;
+        return true;
+    }
+    void release()
+    {
+        if (p) dev_free(p, bytes, st);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ------------------------------------------------------------ host math
+u64 h_mulmod(u64 a, u64 b, u64 m);
+u64 h_powmod(u64 b, u64 e, u64 m);
+u64 h_invmod(u64 a, u64 m);
+bool h_is_prime(u64 n);
+u64 h_min_root(u64 q, u32 N);
+u64 h_shoup(u64 w, u64 q);                 // floor(w * 2^64 / q)
+ModConst h_modconst(u64 q);
+bool h_pick_primes(u32 N, const std::vector<u32> &bits, std::vector<u64> &out);
+void h_cdt_table(double sigma, int tail, u64 *T);
+
+// ------------------------------------------------------------ device tables
+struct Tables {
+    DevMem mc;            // ModConst[L+K]
+    DevMem tw_fwd;        // ulonglong2[L+K][N]  (psi^brv(i), shoup)
+    DevMem tw_inv;        // ulonglong2[L+K][N]  (psi^-brv(i), shoup)
+    DevMem ninv;          // ulonglong2[L+K]     N^-1
+    DevMem modup_scale;   // ulonglong2[beta][alpha][alpha]   N^-1 * Dhat_i^-1 mod q_i
+    DevMem modup_conv;    // u64[beta][alpha][alpha][L+K]     Mont(Dhat_i mod m_t)
+    DevMem moddown_scale; // ulonglong2[K]      N^-1 * Phat_k^-1 mod p_k
+    DevMem moddown_conv;  // u64[K][L]          Mont(Phat_k mod q_i)
+    DevMem pinv;          // ulonglong2[L]      P^-1 mod q_i
+    DevMem pmod;          // ulonglong2[L+K]    P mod m_t
+    DevMem rescale_inv;   // ulonglong2[L][L]   [t][i] q_t^-1 mod q_i
+    DevMem cdt;           // u64[41]
+    DevMem fft_w;         // double2[N/2]  exp(2 pi i j / (N/2))
+    DevMem fft_zeta;      // double2[N/2]  exp(pi i k / N)
+    DevMem slot_perm;     // u32[N/2]      (5^i mod 2N - 1) / 4
+};
+
+struct RotKey {
+    DevMem mem; // u64[beta][2][L+K][N], Montgomery form
+};
+
+} // namespace fheon
+
+struct fheon_ctx {
+    u32 N = 0, logN = 0, L = 0, K = 0, dnum = 0, alpha = 0, beta = 0;
+    double scale = 0;
+    u64 seed = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<u64> mod;                 // L+K moduli
+    std::vector<ModConst> mc;             // host copy
+    fheon::Tables tab;
+    std::map<u64, fheon::RotKey> keys;    // by Galois element
+    fheon::DevMem ws;                     // key-switching workspace
+    size_t ws_limbs = 0;
+    u64 enc_counter = 0;
+    std::string last_error;
+
+    // limbs of the key-switching workspace at level l
+    size_t ks_ws_limbs(u32 l) const;
+    u32 beta_at(u32 l) const { return (l + alpha - 1) / alpha; }
+    size_t limb_bytes() const { return (size_t)N * 8; }
+};
+
+struct fheon_sk {
+    fheon::DevMem s; // u64[L+K][N] evaluation form, canonical
+};
+struct fheon_pk {
+    fheon::DevMem b; // u64[2][L][N] (b, a), canonical
+};
+struct fheon_pt {
+    fheon::DevMem m; // u64[level][N] evaluation form, canonical
+    u32 level = 0;
+    double scale = 1.0;
+};
+struct fheon_ct {
+    fheon::DevMem c; // u64[2][level][N]
+    u32 level = 0;   // limbs in use
+    u32 cap = 0;     // limbs allocated per component
+    double scale = 1.0;
+    u64 *c0() const { return c.as<u64>(); }
+    u64 *c1(u32 N) const { return c.as<u64>() + (size_t)level * N; }
+};
+
+namespace fheon {
+// error helpers (set ctx->last_error and return code)
+int fail(fheon_ctx *ctx, int code, const char *fmt, ...);
+int cuda_fail(fheon_ctx *ctx, cudaError_t e, const char *where);
+#define FHEON_CUDA(ctx, expr)                                  \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return fheon::cuda_fail((ctx), _e, #expr); \
+    } while (0)
+
+// make `ct` an allocation for `level` limbs per component (keeps memory when large enough)
+int ct_reshape(fheon_ctx *ctx, fheon_ct *ct, u32 level);
+int ensure_workspace(fheon_ctx *ctx, size_t limbs);
+
+// ---------------------------------------------------------------- kernels (host launchers)
+// NTT over `n` consecutive limbs at `in` (u64[n][N]) into `out`, limb t under modulus
+// index mod0 + t (or the Q/P map below), in the evaluation convention of ntt_core.cuh.
+cudaError_t ntt_fwd_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 level, u32 first_limb,
+                          cudaStream_t st);
+cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 level, u32 first_limb,
+                          cudaStream_t st);
+
+// key switching / rotation (keyswitch.cu)
+int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out);
+int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
+
+// pointwise and rescale (arith.cu)
+cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level, u32 ct_level_out_stride);
+cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 nlimb_per_comp, u32 ncomp);
+cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level);
+int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
+cudaError_t k_decrypt(fheon_ctx *ctx, const u64 *ct, const u64 *s, u64 *m, u32 level);
+
+// sampler / keygen / encrypt (sampler.cu)
+int keygen_dev(fheon_ctx *ctx, fheon_sk *sk, fheon_pk *pk);
+int galois_key_dev(fheon_ctx *ctx, const fheon_sk *sk, u64 g, RotKey &key);
+int encrypt_dev(fheon_ctx *ctx, const fheon_pk *pk, const fheon_pt *pt, u64 nonce, fheon_ct *out);
+int plain_from_coeffs_dev(fheon_ctx *ctx, const int64_t *host_coeffs, u32 level, fheon_pt *pt);
+// device signed coefficients (N) -> evaluation-form residues over limbs 0..level-1
+int limbs_from_coeffs_dev(fheon_ctx *ctx, const long long *dev_coeffs, u32 level, u64 *out);
+cudaError_t key_from_mont(fheon_ctx *ctx, const u64 *in, u64 *out, size_t limbs_per_block, u32 blocks);
+
+// encoding (encode.cu)
+int build_fft_tables(fheon_ctx *ctx);
+int encode_dev(fheon_ctx *ctx, const double *re, const double *im, u32 n, double scale, u32 level,
+               fheon_pt *pt, int64_t *host_coeffs_out);
+int decode_dev(fheon_ctx *ctx, const fheon_pt *pt, double *re, double *im, u32 n);
+} // namespace fheon

@@ -1,0 +1,212 @@
+// layers.cu -- FHEON's special secure convolution (paper Sec. 4.3, Alg. 1-3),
+// generalised from 3x3 to any odd k with "same" padding and stride 1, as host
+// orchestration of the device operations.
+//
+// Input packing (paper Sec. 4.1, flattening): channel c, row h, column w at
+// slot c*H*W + h*W + w.  For tap (di, dj) in [-p, p]^2, p = (k-1)/2, the
+// rotated ciphertext Rot_{di*W+dj}(x) holds x[h+di][w+dj] at slot (h, w); the
+// tap plaintext is the kernel value times the boundary mask of Alg. 2/3
+// (1 where (h+di, w+dj) lies inside the input), per channel block.  The k^2
+// products are summed and rescaled once (the taps are encoded at scale
+// q_{level-1}, so the scale returns to the input's).  With C > 1 input
+// channels the channel blocks are summed by C-1 chained rotations by H*W
+// (the single W^2 key of Sec. 4.3) and masked to block 0, which costs one
+// more level.  The bias is added last.
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "internal.h"
+
+struct fheon_layer {
+    u32 in_ch = 0, k = 0, H = 0, W = 0, level = 0;
+    std::vector<fheon_pt *> taps; // k*k, row-major (di, dj)
+    fheon_pt *mask = nullptr;     // C > 1: block-0 mask at level-1
+    fheon_pt *bias = nullptr;     // at the output level
+    std::vector<bool> owned;      // which of taps are owned by the layer
+    bool own_bias = false;
+    ~fheon_layer()
+    {
+        for (size_t i = 0; i < taps.size(); i++)
+            if (owned[i]) fheon_pt_destroy(taps[i]);
+        fheon_pt_destroy(mask);
+        if (own_bias) fheon_pt_destroy(bias);
+    }
+};
+
+using namespace fheon;
+
+namespace {
+struct CtGuard {
+    fheon_ct *p = nullptr;
+    ~CtGuard() { fheon_ct_destroy(p); }
+};
+
+int make_mask(fheon_ctx *ctx, fheon_layer *ly)
+{
+    if (ly->in_ch <= 1) return FHEON_OK;
+    if (ly->level < 3) return fail(ctx, FHEON_ERR_LEVEL, "multi-channel conv needs level >= 3");
+    const u32 n = ctx->N / 2, hw = ly->H * ly->W;
+    std::vector<double> v(n, 0.0);
+    for (u32 s = 0; s < hw; s++) v[s] = 1.0;
+    const u32 lv = ly->level - 1;
+    return fheon_encode_plain(ctx, v.data(), nullptr, n, lv, (double)ctx->mod[lv - 1], &ly->mask);
+}
+} // namespace
+
+extern "C" {
+
+int fheon_conv2d_rotation_steps(uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w, int32_t *out, uint32_t *n)
+{
+    if (!n || k % 2 == 0 || in_ch == 0) return FHEON_ERR_ARG;
+    const int p = (int)(k - 1) / 2;
+    std::vector<int32_t> s;
+    for (int di = -p; di <= p; di++)
+        for (int dj = -p; dj <= p; dj++)
+            if (di || dj) s.push_back(di * (int)in_w + dj);
+    if (in_ch > 1) s.push_back((int32_t)(in_h * in_w));
+    const u32 cap = *n;
+    for (u32 i = 0; i < s.size() && i < cap; i++)
+        if (out) out[i] = s[i];
+    *n = (u32)s.size();
+    return FHEON_OK;
+}
+
+int fheon_conv2d_prepare(fheon_ctx *ctx, uint32_t in_ch, uint32_t k, uint32_t stride, uint32_t pad, uint32_t in_h,
+                         uint32_t in_w, const double *w, const double *bias, uint32_t level, double in_scale,
+                         fheon_layer **out)
+{
+    if (!ctx || !w || !out || in_ch == 0 || k == 0 || in_h == 0 || in_w == 0 || level < 2 || level > ctx->L)
+        return FHEON_ERR_ARG;
+    if (k % 2 == 0 || stride != 1 || pad != (k - 1) / 2)
+        return fail(ctx, FHEON_ERR_UNIMPLEMENTED, "only the special conv (odd k, stride 1, pad (k-1)/2) is built");
+    const u32 n = ctx->N / 2, hw = in_h * in_w;
+    if ((u64)in_ch * hw > n) return fail(ctx, FHEON_ERR_ARG, "input does not fit in %u slots", n);
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->in_ch = in_ch;
+    ly->k = k;
+    ly->H = in_h;
+    ly->W = in_w;
+    ly->level = level;
+    const int p = (int)(k - 1) / 2;
+    const double tap_scale = (double)ctx->mod[level - 1];
+    std::vector<double> v(n);
+    for (int di = -p; di <= p; di++)
+        for (int dj = -p; dj <= p; dj++) {
+            std::fill(v.begin(), v.end(), 0.0);
+            for (u32 c = 0; c < in_ch; c++) {
+                const double kv = w[((size_t)c * k + (di + p)) * k + (dj + p)];
+                for (u32 h = 0; h < in_h; h++)
+                    for (u32 x = 0; x < in_w; x++) {
+                        const int hh = (int)h + di, xx = (int)x + dj;
+                        if (hh >= 0 && hh < (int)in_h && xx >= 0 && xx < (int)in_w) v[c * hw + h * in_w + x] = kv;
+                    }
+            }
+            fheon_pt *pt = nullptr;
+            int rc = fheon_encode_plain(ctx, v.data(), nullptr, n, level, tap_scale, &pt);
+            if (rc) return rc;
+            ly->taps.push_back(pt);
+            ly->owned.push_back(true);
+        }
+    int rc = make_mask(ctx, ly.get());
+    if (rc) return rc;
+    if (bias) {
+        std::fill(v.begin(), v.end(), 0.0);
+        for (u32 s = 0; s < hw; s++) v[s] = bias[0];
+        const u32 out_level = level - (in_ch > 1 ? 2 : 1);
+        rc = fheon_encode_plain(ctx, v.data(), nullptr, n, out_level, in_scale, &ly->bias);
+        if (rc) return rc;
+        ly->own_bias = true;
+    }
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_conv2d_prepare_plain(fheon_ctx *ctx, uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w,
+                               uint32_t level, const fheon_pt *const *taps, const fheon_pt *bias, fheon_layer **out)
+{
+    if (!ctx || !taps || !out || k % 2 == 0 || in_ch == 0 || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->in_ch = in_ch;
+    ly->k = k;
+    ly->H = in_h;
+    ly->W = in_w;
+    ly->level = level;
+    for (u32 t = 0; t < k * k; t++) {
+        if (!taps[t] || taps[t]->level < level) return fail(ctx, FHEON_ERR_LEVEL, "tap %u missing or below level", t);
+        ly->taps.push_back(const_cast<fheon_pt *>(taps[t]));
+        ly->owned.push_back(false);
+    }
+    ly->bias = const_cast<fheon_pt *>(bias);
+    int rc = make_mask(ctx, ly.get());
+    if (rc) return rc;
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
+    if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "conv expects level %u, got %u", ly->level, in->level);
+    if (out == in) return fail(ctx, FHEON_ERR_ARG, "conv output must not alias its input");
+    const int p = (int)(ly->k - 1) / 2;
+    CtGuard rot, acc;
+    int rc;
+    if ((rc = fheon_ct_create(ctx, in->level, in->scale, &rot.p)) || (rc = fheon_ct_create(ctx, in->level, in->scale, &acc.p)))
+        return rc;
+    u32 t = 0;
+    for (int di = -p; di <= p; di++)
+        for (int dj = -p; dj <= p; dj++, t++) {
+            const int r = di * (int)ly->W + dj;
+            const fheon_ct *src = in;
+            if (r != 0) {
+                if ((rc = fheon_rotate(ctx, in, r, rot.p))) return rc;
+                src = rot.p;
+            }
+            if (t == 0) {
+                if ((rc = fheon_mul_plain(ctx, src, ly->taps[t], acc.p))) return rc;
+            } else {
+                if ((rc = fheon_mul_plain(ctx, src, ly->taps[t], rot.p))) return rc;
+                if ((rc = fheon_add(ctx, acc.p, rot.p, acc.p))) return rc;
+            }
+        }
+    if (ly->in_ch > 1) {
+        if ((rc = fheon_rescale(ctx, acc.p, acc.p))) return rc;
+        // channel sum: acc + Rot_{HW}(acc) + Rot_{2HW}(acc) + ..., chained on one key
+        if ((rc = fheon_drop_level(ctx, acc.p, acc.p->level, rot.p))) return rc;
+        const int32_t hw = (int32_t)(ly->H * ly->W);
+        CtGuard sum;
+        if ((rc = fheon_ct_create(ctx, acc.p->level, acc.p->scale, &sum.p))) return rc;
+        if ((rc = fheon_drop_level(ctx, acc.p, acc.p->level, sum.p))) return rc;
+        for (u32 c = 1; c < ly->in_ch; c++) {
+            if ((rc = fheon_rotate(ctx, rot.p, hw, rot.p))) return rc;
+            if ((rc = fheon_add(ctx, sum.p, rot.p, sum.p))) return rc;
+        }
+        if ((rc = fheon_mul_plain(ctx, sum.p, ly->mask, sum.p))) return rc;
+        if ((rc = fheon_rescale(ctx, sum.p, out))) return rc;
+    } else {
+        if ((rc = fheon_rescale(ctx, acc.p, out))) return rc;
+    }
+    if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
+    return FHEON_OK;
+}
+
+int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k, uint32_t stride, uint32_t pad,
+                 uint32_t in_h, uint32_t in_w, const double *w, const double *bias, fheon_ct *out)
+{
+    if (!ctx || !in) return FHEON_ERR_ARG;
+    fheon_layer *ly = nullptr;
+    int rc = fheon_conv2d_prepare(ctx, in_ch, k, stride, pad, in_h, in_w, w, bias, in->level, in->scale, &ly);
+    if (rc) return rc;
+    rc = fheon_conv2d_apply(ctx, ly, in, out);
+    fheon_layer_destroy(ly);
+    return rc;
+}
+
+int fheon_layer_destroy(fheon_layer *layer)
+{
+    delete layer;
+    return FHEON_OK;
+}
+
+} // extern "C"

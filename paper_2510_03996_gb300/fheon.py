@@ -1,0 +1,445 @@
+"""Thin Python binding of libfheon (include/fheon.h): the same call names,
+argument marshalling only.  Every step runs in the CUDA library; there is no
+Python or CPU fallback, and loading fails loudly when the library is missing.
+
+PyTorch provides the device memory (its caching allocator, installed through
+``fheon_set_allocator``) and the stream (``torch.cuda.current_stream()``).
+"""
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfheon.so")
+
+FHEON_OK = 0
+ERRORS = {-1: "FHEON_ERR_ARG", -2: "FHEON_ERR_OOM", -3: "FHEON_ERR_NO_KEY", -4: "FHEON_ERR_LEVEL",
+          -5: "FHEON_ERR_SCALE", -6: "FHEON_ERR_TIMEOUT", -7: "FHEON_ERR_CUDA", -8: "FHEON_ERR_UNIMPLEMENTED"}
+
+c_u32, c_u64, c_i32, c_dbl, c_vp, c_int, c_sz = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t)
+P = ctypes.POINTER
+c_vpp = P(c_vp)
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_vp, c_sz, c_vp, c_vp)
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_sz, c_vp, c_vp)
+
+
+class fheon_rot_item(ctypes.Structure):
+    _fields_ = [("input", c_vp), ("output", c_vp), ("step", c_i32)]
+
+
+# name -> argument types (all return int unless listed in _RESTYPE)
+SIGNATURES = {
+    "fheon_error_string": [c_int],
+    "fheon_last_error": [c_vp],
+    "fheon_set_allocator": [ALLOC_FN, FREE_FN, c_vp],
+    "fheon_ctx_create": [c_u32, P(c_u64), c_u32, P(c_u64), c_u32, c_u32, c_dbl, c_u64, c_vp, c_vpp],
+    "fheon_ctx_create_bits": [c_u32, P(c_u32), c_u32, P(c_u32), c_u32, c_u32, c_dbl, c_u64, c_vp, c_vpp],
+    "fheon_ctx_destroy": [c_vp],
+    "fheon_ctx_info": [c_vp, P(c_u32), P(c_u32), P(c_u32), P(c_u32), P(c_u32)],
+    "fheon_ctx_moduli": [c_vp, P(c_u64)],
+    "fheon_ctx_set_stream": [c_vp, c_vp],
+    "fheon_sync": [c_vp],
+    "fheon_keygen": [c_vp, c_vpp, c_vpp],
+    "fheon_sk_destroy": [c_vp],
+    "fheon_pk_destroy": [c_vp],
+    "fheon_sk_download": [c_vp, c_vp, P(c_u64)],
+    "fheon_pk_download": [c_vp, c_vp, P(c_u64)],
+    "fheon_rotkeygen": [c_vp, c_vp, P(c_i32), c_u32],
+    "fheon_galois_keygen": [c_vp, c_vp, P(c_u64), c_u32],
+    "fheon_key_erase": [c_vp, c_u64],
+    "fheon_key_stats": [c_vp, P(c_u32), P(c_u64)],
+    "fheon_key_download": [c_vp, c_u64, P(c_u64)],
+    "fheon_galois_elt": [c_vp, c_i32],
+    "fheon_encode_plain": [c_vp, P(c_dbl), P(c_dbl), c_u32, c_u32, c_dbl, c_vpp],
+    "fheon_plain_from_coeffs": [c_vp, P(ctypes.c_int64), c_u32, c_dbl, c_vpp],
+    "fheon_encode_coeffs": [c_vp, P(c_dbl), P(c_dbl), c_u32, c_dbl, P(ctypes.c_int64)],
+    "fheon_decode": [c_vp, c_vp, P(c_dbl), P(c_dbl), c_u32],
+    "fheon_pt_info": [c_vp, P(c_u32), P(c_dbl)],
+    "fheon_pt_download": [c_vp, c_vp, P(c_u64)],
+    "fheon_pt_destroy": [c_vp],
+    "fheon_encrypt": [c_vp, c_vp, c_vp, c_vpp],
+    "fheon_encrypt_seeded": [c_vp, c_vp, c_vp, c_u64, c_vpp],
+    "fheon_decrypt": [c_vp, c_vp, c_vp, c_vpp],
+    "fheon_ct_create": [c_vp, c_u32, c_dbl, c_vpp],
+    "fheon_ct_destroy": [c_vp],
+    "fheon_ct_info": [c_vp, P(c_u32), P(c_dbl)],
+    "fheon_ct_upload": [c_vp, c_vp, P(c_u64)],
+    "fheon_ct_download": [c_vp, c_vp, P(c_u64)],
+    "fheon_ct_device_ptr": [c_vp, c_vpp],
+    "fheon_rotate": [c_vp, c_vp, c_i32, c_vp],
+    "fheon_rotate_galois": [c_vp, c_vp, c_u64, c_vp],
+    "fheon_rotate_batch": [c_vp, P(fheon_rot_item), c_u32],
+    "fheon_mul_plain": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_add": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_add_plain": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_rescale": [c_vp, c_vp, c_vp],
+    "fheon_drop_level": [c_vp, c_vp, c_u32, c_vp],
+    "fheon_conv2d_rotation_steps": [c_u32, c_u32, c_u32, c_u32, P(c_i32), P(c_u32)],
+    "fheon_conv2d_prepare": [c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
+    "fheon_conv2d_prepare_plain": [c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_vp), c_vp, c_vpp],
+    "fheon_conv2d_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_conv2d": [c_vp, c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_vp],
+    "fheon_layer_destroy": [c_vp],
+    "fheon_profile_begin": [c_vp],
+    "fheon_profile_end": [c_vp, ctypes.c_char_p, c_sz],
+}
+_RESTYPE = {"fheon_error_string": ctypes.c_char_p, "fheon_last_error": ctypes.c_char_p, "fheon_galois_elt": c_u64}
+
+_lib = None
+
+
+def load():
+    """Load libfheon.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libfheon.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _RESTYPE.get(name, c_int)
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return list(SIGNATURES)
+
+
+class FheonError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def check(rc, ctx=None):
+    if rc != FHEON_OK:
+        msg = load().fheon_last_error(ctx).decode() if ctx else load().fheon_error_string(rc).decode()
+        raise FheonError(rc, msg)
+
+
+def __getattr__(name):
+    """Module-level access to every C entry point by its own name."""
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+# ---------------------------------------------------------------- allocator hook
+_hooks = None
+
+
+def use_torch_allocator():
+    """Route every device allocation of the library through torch's caching allocator."""
+    global _hooks
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0)))
+        except Exception:  # out of memory: the C side reports FHEON_ERR_OOM
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    check(load().fheon_set_allocator(_hooks[0], _hooks[1], None))
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def _u64p(a):
+    return a.ctypes.data_as(P(c_u64))
+
+
+def _dblp(a):
+    return a.ctypes.data_as(P(c_dbl)) if a is not None else None
+
+
+class Context:
+    """Owning wrapper of a fheon_ctx* with one method per C call (marshalling only)."""
+
+    def __init__(self, N, q=None, p=None, dnum=1, scale=2.0 ** 40, seed=0, stream=None, qbits=None, pbits=None):
+        L = load()
+        h = c_vp()
+        st = c_vp(stream) if stream else None
+        if qbits is not None:
+            qb = np.ascontiguousarray(qbits, dtype=np.uint32)
+            pb = np.ascontiguousarray(pbits, dtype=np.uint32)
+            rc = L.fheon_ctx_create_bits(N, qb.ctypes.data_as(P(c_u32)), len(qb), pb.ctypes.data_as(P(c_u32)),
+                                         len(pb), dnum, scale, seed, st, ctypes.byref(h))
+        else:
+            qa = np.ascontiguousarray(q, dtype=np.uint64)
+            pa = np.ascontiguousarray(p, dtype=np.uint64)
+            rc = L.fheon_ctx_create(N, _u64p(qa), len(qa), _u64p(pa), len(pa), dnum, scale, seed, st,
+                                    ctypes.byref(h))
+        check(rc)
+        self.h = h
+        info = [c_u32() for _ in range(5)]
+        check(L.fheon_ctx_info(h, *[ctypes.byref(x) for x in info]), h)
+        self.N, self.L, self.K, self.alpha, self.beta = [x.value for x in info]
+        mods = np.zeros(self.L + self.K, dtype=np.uint64)
+        check(L.fheon_ctx_moduli(h, _u64p(mods)), h)
+        self.moduli = [int(x) for x in mods]
+        self.scale = scale
+
+    def close(self):
+        if self.h:
+            load().fheon_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        # at interpreter exit torch's allocator may already be torn down: leak instead
+        if sys is None or sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        check(rc, self.h)
+
+    # streams
+    def set_stream(self, stream):
+        self._chk(load().fheon_ctx_set_stream(self.h, c_vp(stream) if stream else None))
+
+    def sync(self):
+        self._chk(load().fheon_sync(self.h))
+
+    # keys
+    def keygen(self):
+        sk, pk = c_vp(), c_vp()
+        self._chk(load().fheon_keygen(self.h, ctypes.byref(sk), ctypes.byref(pk)))
+        return Handle(sk, load().fheon_sk_destroy), Handle(pk, load().fheon_pk_destroy)
+
+    def sk_download(self, sk):
+        out = np.zeros((self.L + self.K, self.N), dtype=np.uint64)
+        self._chk(load().fheon_sk_download(self.h, sk.h, _u64p(out)))
+        return out
+
+    def pk_download(self, pk):
+        out = np.zeros((2, self.L, self.N), dtype=np.uint64)
+        self._chk(load().fheon_pk_download(self.h, pk.h, _u64p(out)))
+        return out
+
+    def rotkeygen(self, sk, steps):
+        a = np.ascontiguousarray(steps, dtype=np.int32)
+        self._chk(load().fheon_rotkeygen(self.h, sk.h, a.ctypes.data_as(P(c_i32)), len(a)))
+
+    def galois_keygen(self, sk, gs):
+        a = np.ascontiguousarray(gs, dtype=np.uint64)
+        self._chk(load().fheon_galois_keygen(self.h, sk.h, _u64p(a), len(a)))
+
+    def key_erase(self, g):
+        self._chk(load().fheon_key_erase(self.h, int(g)))
+
+    def key_stats(self):
+        n, b = c_u32(), c_u64()
+        self._chk(load().fheon_key_stats(self.h, ctypes.byref(n), ctypes.byref(b)))
+        return n.value, b.value
+
+    def key_download(self, g):
+        out = np.zeros((self.beta, 2, self.L + self.K, self.N), dtype=np.uint64)
+        self._chk(load().fheon_key_download(self.h, int(g), _u64p(out)))
+        return out
+
+    def galois_elt(self, r):
+        return int(load().fheon_galois_elt(self.h, int(r)))
+
+    # plaintexts
+    def plain_from_coeffs(self, coeffs, level, scale=1.0):
+        c = np.ascontiguousarray(coeffs, dtype=np.int64)
+        h = c_vp()
+        self._chk(load().fheon_plain_from_coeffs(self.h, c.ctypes.data_as(P(ctypes.c_int64)), level, scale,
+                                                 ctypes.byref(h)))
+        return Handle(h, load().fheon_pt_destroy)
+
+    def encode(self, z, level, scale):
+        z = np.asarray(z, dtype=np.complex128)
+        re, im = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+        h = c_vp()
+        self._chk(load().fheon_encode_plain(self.h, _dblp(re), _dblp(im), len(z), level, scale, ctypes.byref(h)))
+        return Handle(h, load().fheon_pt_destroy)
+
+    def encode_coeffs(self, z, scale):
+        z = np.asarray(z, dtype=np.complex128)
+        re, im = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+        out = np.zeros(self.N, dtype=np.int64)
+        self._chk(load().fheon_encode_coeffs(self.h, _dblp(re), _dblp(im), len(z), scale,
+                                             out.ctypes.data_as(P(ctypes.c_int64))))
+        return out
+
+    def decode(self, pt, n=None):
+        n = n or self.N // 2
+        re, im = np.zeros(n), np.zeros(n)
+        self._chk(load().fheon_decode(self.h, pt.h, _dblp(re), _dblp(im), n))
+        return re + 1j * im
+
+    def pt_download(self, pt):
+        lv = c_u32()
+        check(load().fheon_pt_info(pt.h, ctypes.byref(lv), None))
+        out = np.zeros((lv.value, self.N), dtype=np.uint64)
+        self._chk(load().fheon_pt_download(self.h, pt.h, _u64p(out)))
+        return out
+
+    # ciphertexts
+    def encrypt(self, pk, pt, nonce=None):
+        h = c_vp()
+        if nonce is None:
+            self._chk(load().fheon_encrypt(self.h, pk.h, pt.h, ctypes.byref(h)))
+        else:
+            self._chk(load().fheon_encrypt_seeded(self.h, pk.h, pt.h, int(nonce), ctypes.byref(h)))
+        return Handle(h, load().fheon_ct_destroy)
+
+    def decrypt(self, sk, ct):
+        h = c_vp()
+        self._chk(load().fheon_decrypt(self.h, sk.h, ct.h, ctypes.byref(h)))
+        return Handle(h, load().fheon_pt_destroy)
+
+    def ct_create(self, level, scale=1.0):
+        h = c_vp()
+        self._chk(load().fheon_ct_create(self.h, level, scale, ctypes.byref(h)))
+        return Handle(h, load().fheon_ct_destroy)
+
+    def ct_info(self, ct):
+        lv, sc = c_u32(), c_dbl()
+        check(load().fheon_ct_info(ct.h, ctypes.byref(lv), ctypes.byref(sc)))
+        return lv.value, sc.value
+
+    def ct_upload(self, ct, host):
+        host = np.ascontiguousarray(host, dtype=np.uint64)
+        self._chk(load().fheon_ct_upload(self.h, ct.h, _u64p(host)))
+        return host  # keep alive until synchronised when pinned/asynchronous
+
+    def ct_upload_ptr(self, ct, host_ptr):
+        self._chk(load().fheon_ct_upload(self.h, ct.h, ctypes.cast(c_vp(host_ptr), P(c_u64))))
+
+    def ct_download(self, ct):
+        lv, _ = self.ct_info(ct)
+        out = np.zeros((2, lv, self.N), dtype=np.uint64)
+        self._chk(load().fheon_ct_download(self.h, ct.h, _u64p(out)))
+        return out
+
+    def ct_download_ptr(self, ct, host_ptr):
+        self._chk(load().fheon_ct_download(self.h, ct.h, ctypes.cast(c_vp(host_ptr), P(c_u64))))
+
+    def ct_device_ptr(self, ct):
+        p = c_vp()
+        check(load().fheon_ct_device_ptr(ct.h, ctypes.byref(p)))
+        return p.value
+
+    # evaluation
+    def rotate(self, ct, step, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_rotate(self.h, ct.h, int(step), out.h))
+        return out
+
+    def rotate_galois(self, ct, g, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_rotate_galois(self.h, ct.h, int(g), out.h))
+        return out
+
+    def rotate_batch(self, ins, outs, steps):
+        items = (fheon_rot_item * len(ins))()
+        for i, (a, b, s) in enumerate(zip(ins, outs, steps)):
+            items[i].input, items[i].output, items[i].step = a.h, b.h, int(s)
+        self._chk(load().fheon_rotate_batch(self.h, items, len(ins)))
+
+    def mul_plain(self, ct, pt, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_mul_plain(self.h, ct.h, pt.h, out.h))
+        return out
+
+    def add(self, a, b, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_add(self.h, a.h, b.h, out.h))
+        return out
+
+    def add_plain(self, ct, pt, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_add_plain(self.h, ct.h, pt.h, out.h))
+        return out
+
+    def rescale(self, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_rescale(self.h, ct.h, out.h))
+        return out
+
+    def drop_level(self, ct, level, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_drop_level(self.h, ct.h, level, out.h))
+        return out
+
+    # instrumentation
+    def profile_begin(self):
+        self._chk(load().fheon_profile_begin(self.h))
+
+    def profile_end(self):
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._chk(load().fheon_profile_end(self.h, buf, len(buf)))
+        return {k: (v[0], v[1]) for k, v in json.loads(buf.value.decode()).items()}
+
+    # layers
+    def conv2d_rotation_steps(self, in_ch, k, in_h, in_w):
+        n = c_u32(64)
+        out = np.zeros(64, dtype=np.int32)
+        check(load().fheon_conv2d_rotation_steps(in_ch, k, in_h, in_w, out.ctypes.data_as(P(c_i32)), ctypes.byref(n)))
+        return [int(x) for x in out[:n.value]]
+
+    def conv2d_prepare(self, in_ch, k, stride, pad, in_h, in_w, w, bias, level, in_scale):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        h = c_vp()
+        self._chk(load().fheon_conv2d_prepare(self.h, in_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b), level,
+                                              in_scale, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def conv2d_prepare_plain(self, in_ch, k, in_h, in_w, level, taps, bias=None):
+        arr = (c_vp * len(taps))(*[t.h for t in taps])
+        h = c_vp()
+        self._chk(load().fheon_conv2d_prepare_plain(self.h, in_ch, k, in_h, in_w, level, arr,
+                                                    bias.h if bias is not None else None, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def conv2d_apply(self, layer, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_conv2d_apply(self.h, layer.h, ct.h, out.h))
+        return out
+
+    def conv2d(self, ct, in_ch, k, stride, pad, in_h, in_w, w, bias=None, out=None):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_conv2d(self.h, ct.h, in_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b), out.h))
+        return out
+
+
+class Handle:
+    """Owning pointer to a fheon_* object, destroyed with its C destructor."""
+
+    def __init__(self, h, destroy):
+        self.h = h
+        self._destroy = destroy
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            self._destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        if sys is None or sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
