@@ -206,6 +206,29 @@ int fheon_ct_device_ptr(const fheon_ct *ct, void **dptr);
 int fheon_rotate(fheon_ctx *ctx, const fheon_ct *in, int32_t step, fheon_ct *out);
 int fheon_rotate_galois(fheon_ctx *ctx, const fheon_ct *in, uint64_t galois, fheon_ct *out);
 
+/* fheon_rotate without any device allocation.  The paper has no counterpart:
+ * this serves callers that must not allocate while they rotate -- a server
+ * whose device memory is partitioned once at start-up, a latency-critical
+ * path that cannot pay for cudaMalloc/cudaFree (cudaFree synchronises the
+ * device), or work recorded inside a stream capture, where allocation calls
+ * are not permitted.  The result is identical to fheon_rotate.
+ *  - The caller passes the input and an output ciphertext that already holds
+ *    at least in's level limbs per component (fheon_ct_create); out must not
+ *    be in.  FHEON_ERR_ARG otherwise.
+ *  - The key-switching workspace is a fixed 32 MiB device array inside the
+ *    library (reserved on every GPU that loads it, until the process exits).
+ *    A rotation needs (l + beta*(l+K) + 2*(l+K) + 2K + 2l) * N * 8 bytes at
+ *    level l (e.g. N = 2^13, L = 3, K = 1: 2 MiB; N = 2^16 fits up to level 4
+ *    with K = 4); larger requests fail with FHEON_ERR_ARG and a message.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents (a
+ *    rotation never reads workspace it did not write first).  Calls that
+ *    overlap on the GPU race on it: serialise them on one stream.
+ * Errors: as fheon_rotate. */
+int fheon_rotate_noalloc(fheon_ctx *ctx, const fheon_ct *in, int32_t step, fheon_ct *out);
+
 /* One batched rotation request: rotate `in` by `step` into `out`. */
 typedef struct fheon_rot_item {
     const fheon_ct *in;

@@ -148,6 +148,9 @@ cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 le
                           cudaStream_t st);
 
 // key switching / rotation (keyswitch.cu)
+// The rotation pipeline on caller-provided workspace (ks_ws_limbs(l) limbs);
+// launches kernels only, allocates nothing.
+int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out);
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out);
 int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
 

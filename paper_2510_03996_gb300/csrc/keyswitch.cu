@@ -139,8 +139,7 @@ __global__ void __launch_bounds__(TPB) moddown_combine_kernel(const u64 *__restr
 } // namespace
 
 // Run the whole pipeline for one ciphertext.  `ws` holds ks_ws_limbs(l) limbs.
-static int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws,
-                            u64 *out)
+int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out)
 {
     const u32 N = ctx->N, K = ctx->K, L = ctx->L, A = ctx->alpha, beta = ctx->beta_at(l);
     cudaStream_t st = ctx->stream;

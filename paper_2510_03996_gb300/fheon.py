@@ -73,6 +73,7 @@ SIGNATURES = {
     "fheon_rotate": [c_vp, c_vp, c_i32, c_vp],
     "fheon_rotate_galois": [c_vp, c_vp, c_u64, c_vp],
     "fheon_rotate_batch": [c_vp, P(fheon_rot_item), c_u32],
+    "fheon_rotate_noalloc": [c_vp, c_vp, c_i32, c_vp],
     "fheon_mul_plain": [c_vp, c_vp, c_vp, c_vp],
     "fheon_add": [c_vp, c_vp, c_vp, c_vp],
     "fheon_add_plain": [c_vp, c_vp, c_vp, c_vp],
@@ -346,6 +347,11 @@ class Context:
     def rotate_galois(self, ct, g, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_rotate_galois(self.h, ct.h, int(g), out.h))
+        return out
+
+    def rotate_noalloc(self, ct, step, out):
+        """Rotation into a caller-made output, with the library's fixed scratch (no allocation)."""
+        self._chk(load().fheon_rotate_noalloc(self.h, ct.h, int(step), out.h))
         return out
 
     def rotate_batch(self, ins, outs, steps):
