@@ -225,10 +225,12 @@ def run_gpu(args, rank, world, local_rank):
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
         ctx.profile_begin()
+        torch.cuda.nvtx.range_push("timed")
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
+        torch.cuda.nvtx.range_pop()
         prof = ctx.profile_end()
         torch.cuda.synchronize()
     ms_total = ev0.elapsed_time(ev1)
