@@ -152,6 +152,7 @@ cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 le
 // launches kernels only, allocates nothing.
 int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out);
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out);
+void drop_plans(fheon_ctx *ctx); // release the cached batch plans of a context
 int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
 
 // pointwise and rescale (arith.cu)

@@ -1,5 +1,5 @@
-// jobs.cuh -- NTT job policies shared by the kernels: where a transform reads
-// its limb, which modulus a limb belongs to, and what the last pass writes.
+// jobs.cuh -- NTT job policies over plain limb arrays: where a transform reads
+// its limb, which modulus the limb belongs to, and where the result goes.
 #pragma once
 #include "internal.h"
 #include "ntt_core.cuh"
@@ -25,45 +25,46 @@ enum ScaleMode : u32 {
     SCALE_MODDOWN = 2, // N^-1 * Phat_k^-1 (P limb k)
 };
 
+__device__ __forceinline__ u32 limb_modidx(u32 t, u32 level, u32 L) { return t < level ? t : L + (t - level); }
+
+// N^-1 * Dhat_i^-1 for limb t of its digit at `level`
+__device__ __forceinline__ ulonglong2 modup_scale(const ulonglong2 *tab, u32 t, u32 level, u32 A)
+{
+    const u32 j = t / A, d = min(A, level - j * A);
+    return tab[(j * A + (d - 1)) * A + (t - j * A)];
+}
+
 // Limbs of a batch of polynomials: limb position p of polynomial `poly` sits at
 // base + poly*poly_stride + p*N; its limb index is t = p + first_t, and limb
 // index t < level is modulus q_t, otherwise special modulus p_{t-level}
-// (modulus index L + t - level).  With skip_alpha, limb t of polynomial j is
-// skipped when it belongs to digit j (those limbs need no transform).
+// (modulus index L + t - level).  The first pass writes `out` (the mid
+// buffer), the second reads and overwrites it.
 struct MapParams {
     TabPtrs tp;
     const u64 *in;
     u64 *out;
     u64 in_poly_stride, out_poly_stride;
-    u32 per_poly, first_t, level, L, alpha, skip_digit;
-    u64 gather_g;       // inverse first pass only: read in[sigma_g source] (0 = none)
-    u32 scale_mode;     // ScaleMode
+    u32 per_poly, first_t, level, L, alpha;
+    u64 gather_g;   // inverse first pass only: read in[sigma_g source] (0 = none)
+    u32 scale_mode; // ScaleMode
     const ulonglong2 *scale_tab;
 };
 
-__device__ __forceinline__ u32 limb_modidx(u32 t, u32 level, u32 L) { return t < level ? t : L + (t - level); }
-
-struct MapJob {
+struct MapJob : ntt::JobBase {
     using Params = MapParams;
     const MapParams &p;
     const u64 *in;
     u64 *out;
     u32 midx, t;
-    bool act;
-    __device__ MapJob(const MapParams &P, u32 job) : p(P)
+    __device__ MapJob(const MapParams &P, u32 task) : p(P)
     {
-        const u32 poly = job / P.per_poly, pos = job % P.per_poly;
+        const u32 poly = task / P.per_poly, pos = task % P.per_poly;
         t = pos + P.first_t;
-        act = true;
-        if (P.skip_digit) {
-            const u32 d0 = poly * P.alpha, d1 = min(d0 + P.alpha, P.level);
-            act = !(t >= d0 && t < d1);
-        }
         midx = limb_modidx(t, P.level, P.L);
         in = P.in + poly * P.in_poly_stride + (u64)pos * P.tp.N;
         out = P.out + poly * P.out_poly_stride + (u64)pos * P.tp.N;
     }
-    __device__ bool active() const { return act; }
+    __device__ bool active() const { return true; }
     __device__ ModConst mod() const { return p.tp.mc[midx]; }
     __device__ const ulonglong2 *twiddles(bool inv) const { return (inv ? p.tp.twi : p.tp.twf) + (u64)midx * p.tp.N; }
     template <bool INV> __device__ u64 load_first(u32 J) const
@@ -73,23 +74,13 @@ struct MapJob {
     }
     __device__ u64 load_mid(u32 J) const { return out[J]; }
     __device__ void store_mid(u32 J, u64 v) const { out[J] = v; }
-    template <bool INV> __device__ void store_last(u32 J, u64 v, const ModConst &m) const
+    __device__ ulonglong2 inv_scale() const
     {
-        if (!INV) {
-            out[J] = reduce4q(v, m.q);
-            return;
-        }
-        ulonglong2 s;
-        if (p.scale_mode == SCALE_MODUP) {
-            const u32 A = p.alpha, j = t / A, d = min(A, p.level - j * A);
-            s = p.scale_tab[(j * A + (d - 1)) * A + (t - j * A)];
-        } else if (p.scale_mode == SCALE_MODDOWN) {
-            s = p.scale_tab[t - p.level];
-        } else {
-            s = p.tp.ninv[midx];
-        }
-        out[J] = shoup(v, s.x, s.y, m.q);
+        if (p.scale_mode == SCALE_MODUP) return modup_scale(p.scale_tab, t, p.level, p.alpha);
+        if (p.scale_mode == SCALE_MODDOWN) return p.scale_tab[t - p.level];
+        return p.tp.ninv[midx];
     }
+    __device__ void store_last(int, u32 J, u64 v, const ModConst &) const { out[J] = v; }
 };
 
 inline MapParams map_params(const fheon_ctx *c, const u64 *in, u64 *out, u32 per_poly, u32 first_t, u32 level)
@@ -105,7 +96,6 @@ inline MapParams map_params(const fheon_ctx *c, const u64 *in, u64 *out, u32 per
     m.level = level;
     m.L = c->L;
     m.alpha = c->alpha;
-    m.skip_digit = 0;
     m.gather_g = 0;
     m.scale_mode = SCALE_NINV;
     m.scale_tab = nullptr;

@@ -1,207 +1,362 @@
 // keyswitch.cu -- the homomorphic rotation: Galois automorphism + hybrid key
 // switching (paper Sec. 2.2 rotation, Sec. 6 "4 digits"; Han-Ki hybrid key
-// switching with Cheon et al. fast base conversion).
+// switching with Cheon et al. fast base conversion), for one ciphertext or a
+// batch of ciphertexts at mixed levels and Galois elements.
 //
-// Pipeline for one ciphertext (c0, c1) at level l, Galois element g,
-// beta = ceil(l/alpha) digits, all in the evaluation domain:
-//   1  INTT of sigma_g(c1)   -- the automorphism is a gather in the first
-//                               pass's load; the last pass multiplies by
-//                               N^-1 * Dhat_i^-1, giving the ModUp inputs
-//   2  ModUp base conversion -- digit j's limbs to every other limb of Q_l u P
-//   3  NTT of the new limbs  -- beta*(l+K) - l transforms
-//   4  key inner product     -- acc_b[t] = sum_j d_j[t] * key_g[j][b][t];
-//                               digit limbs come straight from sigma_g(c1)
-//   5  INTT of acc's P limbs -- times N^-1 * Phat_k^-1
-//   6  ModDown conversion    -- P -> each q_i
-//   7  NTT of the converted limbs
-//   8  out_b = (acc_b - conv_b) * P^-1 (+ sigma_g(c0) for b = 0)
-// Workspace per ciphertext (limbs of N u64): xt[l] | ext[beta][l+K] |
-// acc[2][l+K] | pc[2][K] | conv[2][l].
+// Pipeline of one ciphertext (c0, c1) at level l, Galois element g, beta =
+// ceil(l/alpha) digits, everything in the evaluation domain.  Six launches
+// cover a whole batch; each is one NTT pass over a task list:
+//   IC   INTT of sigma_g(c1): gather on load, last pass scaled by
+//        N^-1 * Dhat_i^-1 (the ModUp input scaling)            -> xt[l]
+//   UPA  first NTT pass of every new limb of every digit; the load computes
+//        the ModUp base conversion from the digit's xt limbs    -> ext[j][t]
+//   UPB  second NTT pass, repeated over the digits j of one limb t; each
+//        result is multiplied by key_g[j][b][t] and summed in registers
+//        (digit limbs of t come straight from sigma_g(c1))      -> acc[2][l+K]
+//   DNI  INTT of the P limbs of acc, scaled N^-1 * Phat_k^-1     -> pc[2][K]
+//   DNA  first NTT pass of each q_i limb; the load computes the ModDown base
+//        conversion P -> q_i from pc                            -> conv[2][l]
+//   DNB  second pass; the store forms (acc - conv) * P^-1 and adds
+//        sigma_g(c0) to component 0                              -> out[2][l]
+// Workspace of one ciphertext (limbs of N u64):
+//   xt[l] | ext[beta][l+K] | acc[2][l+K] | pc[2][K] | conv[2][l].
+// The key is in Montgomery form, so a product with it reduces to the plain
+// residue with one REDC.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
 #include "jobs.cuh"
 
 namespace fheon {
 
 namespace {
 
-constexpr int TPB = 256;
+struct RotDesc {
+    const u64 *c0, *c1; // input components, level limbs each
+    u64 *out;           // [2][level][N]
+    const u64 *key;     // [beta_max][2][L+K][N], Montgomery form
+    u64 *ws;            // workspace (ks_ws_limbs(level) limbs)
+    u64 g;
+    u32 level, beta;
+};
 
-// Step 2.  One thread per coefficient n, blockIdx.y = digit j.
-__global__ void __launch_bounds__(TPB) modup_bconv_kernel(const u64 *__restrict__ xt, u64 *__restrict__ ext, u32 level,
-                                                          u32 K, u32 L, u32 alpha, u32 N,
-                                                          const u64 *__restrict__ conv_tab,
-                                                          const ModConst *__restrict__ mc)
+struct BatchParams {
+    TabPtrs tp;
+    const RotDesc *desc; // batch: descriptor per ciphertext (null: `one`)
+    const u32 *tasks;    // batch: (ct << 16) | sub per task (null: closed form over `one`)
+    RotDesc one;
+    u32 L, K, alpha;
+    const ulonglong2 *modup_scale;
+    const u64 *modup_conv;
+    const ulonglong2 *moddown_scale;
+    const u64 *moddown_conv;
+    const ulonglong2 *pinv;
+};
+
+enum Stage { ST_IC, ST_UPA, ST_UPB, ST_DNI, ST_DNA, ST_DNB };
+
+// (descriptor, sub-index) of a task; closed forms for a single ciphertext
+template <int STAGE>
+__device__ __forceinline__ const RotDesc &task_of(const BatchParams &P, u32 task, u32 &sub)
 {
-    const u32 n = blockIdx.x * TPB + threadIdx.x;
-    const u32 j = blockIdx.y;
-    if (n >= N) return;
-    const u32 d0 = j * alpha, d = min(alpha, level - d0), nl = level + K, nm = L + K;
-    u64 x[16];
-#pragma unroll
-    for (u32 i = 0; i < 16; i++)
-        if (i < d) x[i] = xt[(u64)(d0 + i) * N + n];
-    const u64 *tab = conv_tab + ((u64)j * alpha + (d - 1)) * alpha * nm;
-    u64 *o = ext + (u64)j * nl * N + n;
-    for (u32 t = 0; t < nl; t++) {
-        if (t >= d0 && t < d0 + d) continue;
-        const u32 m = limb_modidx(t, level, L);
-        u128acc a;
-        acc_zero(a);
-#pragma unroll
-        for (u32 i = 0; i < 16; i++)
-            if (i < d) acc_mad(a, x[i], __ldg(&tab[i * nm + m]));
-        const ModConst c = mc[m];
-        o[(u64)t * N] = redc_acc(a, c.q, c.qneg_inv);
+    if (P.tasks) {
+        const u32 w = P.tasks[task];
+        sub = w & 0xFFFFu;
+        return P.desc[w >> 16];
     }
+    const RotDesc &d = P.one;
+    const u32 l = d.level, nl = l + P.K, A = P.alpha;
+    if (STAGE == ST_UPA) {
+        // digits j < beta-1 contribute nl - alpha limbs each, the last nl - d_last
+        const u32 full = (d.beta - 1) * (nl - A);
+        const u32 j = task < full ? task / (nl - A) : d.beta - 1;
+        const u32 r = task - j * (nl - A);
+        const u32 dj = min(A, l - j * A);
+        sub = (j << 8) | (r < j * A ? r : r + dj);
+    } else {
+        sub = task;
+    }
+    return d;
 }
 
-// Step 4.  Two coefficients per thread; blockIdx.y = limb t of Q_l u P.
-__global__ void __launch_bounds__(TPB) ks_inner_kernel(const u64 *__restrict__ c1, u64 g, const u64 *__restrict__ ext,
-                                                       const u64 *__restrict__ key, u64 *__restrict__ acc, u32 level,
-                                                       u32 K, u32 L, u32 alpha, u32 N, u32 logN,
-                                                       const ModConst *__restrict__ mc)
-{
-    const u32 n = (blockIdx.x * TPB + threadIdx.x) * 2;
-    if (n >= N) return;
-    const u32 t = blockIdx.y, nl = level + K, nm = L + K;
-    const u32 m = limb_modidx(t, level, L);
-    const u32 beta = (level + alpha - 1) / alpha;
-    u128acc a0x, a0y, a1x, a1y;
-    acc_zero(a0x); acc_zero(a0y); acc_zero(a1x); acc_zero(a1y);
-    for (u32 j = 0; j < beta; j++) {
-        ulonglong2 dv;
-        if (t < level && t / alpha == j) {
-            const u64 *src = c1 + (u64)t * N;
-            dv.x = src[automorph_src(n, g, logN)];
-            dv.y = src[automorph_src(n + 1, g, logN)];
-        } else {
-            dv = *reinterpret_cast<const ulonglong2 *>(ext + ((u64)j * nl + t) * N + n);
+__device__ __forceinline__ u64 *ws_ext(const RotDesc &d, u32 N) { return d.ws + (u64)d.level * N; }
+__device__ __forceinline__ u64 *ws_acc(const RotDesc &d, u32 K, u32 N) { return ws_ext(d, N) + (u64)d.beta * (d.level + K) * N; }
+__device__ __forceinline__ u64 *ws_pc(const RotDesc &d, u32 K, u32 N) { return ws_acc(d, K, N) + (u64)2 * (d.level + K) * N; }
+__device__ __forceinline__ u64 *ws_conv(const RotDesc &d, u32 K, u32 N) { return ws_pc(d, K, N) + (u64)2 * K * N; }
+
+struct JobCommon : ntt::JobBase {
+    using Params = BatchParams;
+    const BatchParams &p;
+    const RotDesc *d;
+    u32 midx;
+    __device__ JobCommon(const BatchParams &P) : p(P) {}
+    __device__ bool active() const { return true; }
+    __device__ ModConst mod() const { return p.tp.mc[midx]; }
+    __device__ const ulonglong2 *twiddles(bool inv) const { return (inv ? p.tp.twi : p.tp.twf) + (u64)midx * p.tp.N; }
+    __device__ ulonglong2 inv_scale() const { return make_ulonglong2(0, 0); }
+};
+
+// IC: INTT of sigma_g(c1) limb t, scaled for ModUp, into xt[t]
+struct IcJob : JobCommon {
+    const u64 *in;
+    u64 *out;
+    u32 t;
+    __device__ IcJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_IC>(P, task, sub);
+        t = sub;
+        midx = t;
+        in = d->c1 + (u64)t * P.tp.N;
+        out = d->ws + (u64)t * P.tp.N;
+    }
+    template <bool INV> __device__ u64 load_first(u32 J) const { return in[automorph_src(J, d->g, p.tp.logN)]; }
+    __device__ u64 load_mid(u32 J) const { return out[J]; }
+    __device__ void store_mid(u32 J, u64 v) const { out[J] = v; }
+    __device__ ulonglong2 inv_scale() const { return modup_scale(p.modup_scale, t, d->level, p.alpha); }
+    __device__ void store_last(int, u32 J, u64 v, const ModConst &) const { out[J] = v; }
+};
+
+// UPA: first forward pass of limb t of digit j; the load is the ModUp base
+// conversion  y = sum_i xt[d0+i] * (Dhat_i mod m_t) (Montgomery constants, one REDC)
+struct UpAJob : JobCommon {
+    const u64 *src;
+    const u64 *cf;
+    u64 *mid;
+    u32 dsz;
+    __device__ UpAJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_UPA>(P, task, sub);
+        const u32 j = sub >> 8, t = sub & 0xFF, l = d->level, A = P.alpha, N = P.tp.N;
+        midx = limb_modidx(t, l, P.L);
+        const u32 d0 = j * A;
+        dsz = min(A, l - d0);
+        src = d->ws + (u64)d0 * N;
+        cf = P.modup_conv + ((u64)(j * A + (dsz - 1)) * A) * (P.L + P.K) + midx;
+        mid = ws_ext(*d, N) + ((u64)j * (l + P.K) + t) * N;
+    }
+    template <bool INV> __device__ u64 load_first(u32 J) const
+    {
+        const u32 N = p.tp.N, nm = p.L + p.K;
+        u128acc a;
+        acc_zero(a);
+        for (u32 i = 0; i < dsz; i++) acc_mad(a, src[(u64)i * N + J], __ldg(&cf[(u64)i * nm]));
+        const ModConst &m = p.tp.mc[midx];
+        return redc_acc(a, m.q, m.qneg_inv);
+    }
+    __device__ u64 load_mid(u32 J) const { return mid[J]; }
+    __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
+    __device__ void store_last(int, u32, u64, const ModConst &) const {}
+};
+
+// UPB: second forward pass of limb t for every digit j, summed against the key.
+// The two running sums of each of the thread's 16 output slots live in shared
+// memory (slot k of thread x at k*blockDim + x; only that thread touches it).
+struct UpBJob : JobCommon {
+    static constexpr int EXTRA_WORDS_PER_ELEM = 2;
+    const u64 *mid, *kb, *ka, *c1t;
+    u64 *acc0, *acc1;
+    u64 *sacc;
+    u32 t, nrep;
+    bool pass;
+    __device__ void attach(u64 *s) { sacc = s; }
+    __device__ u64 &slot(int comp, int k) const
+    {
+        return sacc[(u64)comp * ntt::R * blockDim.x + (u64)k * blockDim.x + threadIdx.x];
+    }
+    __device__ UpBJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_UPB>(P, task, sub);
+        t = sub;
+        const u32 l = d->level, N = P.tp.N;
+        midx = limb_modidx(t, l, P.L);
+        nrep = d->beta;
+        c1t = d->c1 + (u64)t * N;
+        acc0 = ws_acc(*d, P.K, N) + (u64)t * N;
+        acc1 = acc0 + (u64)(l + P.K) * N;
+    }
+    __device__ int reps() const { return (int)nrep; }
+    __device__ void begin(int j)
+    {
+        const u32 l = d->level, N = p.tp.N, nm = p.L + p.K;
+        if (j == 0) {
+#pragma unroll
+            for (int k = 0; k < ntt::R; k++) slot(0, k) = slot(1, k) = 0;
         }
-        const ulonglong2 kb = __ldg(reinterpret_cast<const ulonglong2 *>(key + (((u64)j * 2 + 0) * nm + m) * N + n));
-        const ulonglong2 ka = __ldg(reinterpret_cast<const ulonglong2 *>(key + (((u64)j * 2 + 1) * nm + m) * N + n));
-        acc_mad(a0x, dv.x, kb.x);
-        acc_mad(a0y, dv.y, kb.y);
-        acc_mad(a1x, dv.x, ka.x);
-        acc_mad(a1y, dv.y, ka.y);
+        pass = (t < l) && (t / p.alpha == (u32)j);
+        mid = ws_ext(*d, N) + ((u64)j * (l + p.K) + t) * N;
+        kb = d->key + (((u64)j * 2 + 0) * nm + midx) * N;
+        ka = d->key + (((u64)j * 2 + 1) * nm + midx) * N;
     }
-    const ModConst c = mc[m];
-    *reinterpret_cast<ulonglong2 *>(acc + ((u64)0 * nl + t) * N + n) =
-        make_ulonglong2(redc_acc(a0x, c.q, c.qneg_inv), redc_acc(a0y, c.q, c.qneg_inv));
-    *reinterpret_cast<ulonglong2 *>(acc + ((u64)1 * nl + t) * N + n) =
-        make_ulonglong2(redc_acc(a1x, c.q, c.qneg_inv), redc_acc(a1y, c.q, c.qneg_inv));
-}
+    __device__ bool passthrough() const { return pass; }
+    __device__ u64 load_passthrough(u32 J) const { return c1t[automorph_src(J, d->g, p.tp.logN)]; }
+    template <bool INV> __device__ u64 load_first(u32) const { return 0; }
+    __device__ u64 load_mid(u32 J) const { return mid[J]; }
+    __device__ void store_mid(u32, u64) const {}
+    __device__ void store_last(int k, u32 J, u64 v, const ModConst &m)
+    {
+        u64 &s0 = slot(0, k), &s1 = slot(1, k);
+        s0 = addmod(s0, mulmod_mont(v, __ldg(&kb[J]), m), m.q);
+        s1 = addmod(s1, mulmod_mont(v, __ldg(&ka[J]), m), m.q);
+    }
+    __device__ void finish(int k, u32 J, const ModConst &)
+    {
+        acc0[J] = slot(0, k);
+        acc1[J] = slot(1, k);
+    }
+};
 
-// Step 6.  One thread per coefficient; blockIdx.y = component b.
-__global__ void __launch_bounds__(TPB) moddown_bconv_kernel(const u64 *__restrict__ pc, u64 *__restrict__ conv,
-                                                            u32 level, u32 K, u32 L, u32 N,
-                                                            const u64 *__restrict__ conv_tab,
-                                                            const ModConst *__restrict__ mc)
-{
-    const u32 n = blockIdx.x * TPB + threadIdx.x;
-    if (n >= N) return;
-    const u32 b = blockIdx.y;
-    u64 x[16];
-#pragma unroll
-    for (u32 k = 0; k < 16; k++)
-        if (k < K) x[k] = pc[((u64)b * K + k) * N + n];
-    for (u32 i = 0; i < level; i++) {
+// DNI: INTT of P limb k of component b of acc, scaled N^-1 * Phat_k^-1, into pc
+struct DnIJob : JobCommon {
+    const u64 *in;
+    u64 *out;
+    u32 k;
+    __device__ DnIJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_DNI>(P, task, sub);
+        const u32 b = sub / P.K, l = d->level, N = P.tp.N;
+        k = sub % P.K;
+        midx = P.L + k;
+        in = ws_acc(*d, P.K, N) + ((u64)b * (l + P.K) + l + k) * N;
+        out = ws_pc(*d, P.K, N) + ((u64)b * P.K + k) * N;
+    }
+    template <bool INV> __device__ u64 load_first(u32 J) const { return in[J]; }
+    __device__ u64 load_mid(u32 J) const { return out[J]; }
+    __device__ void store_mid(u32 J, u64 v) const { out[J] = v; }
+    __device__ ulonglong2 inv_scale() const { return p.moddown_scale[k]; }
+    __device__ void store_last(int, u32 J, u64 v, const ModConst &) const { out[J] = v; }
+};
+
+// DNA: first forward pass of q_i limb of component b; the load is the ModDown
+// base conversion P -> q_i from pc
+struct DnAJob : JobCommon {
+    const u64 *pc;
+    u64 *mid;
+    u32 i;
+    __device__ DnAJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_DNA>(P, task, sub);
+        const u32 l = d->level, N = P.tp.N, b = sub / l;
+        i = sub % l;
+        midx = i;
+        pc = ws_pc(*d, P.K, N) + (u64)b * P.K * N;
+        mid = ws_conv(*d, P.K, N) + ((u64)b * l + i) * N;
+    }
+    template <bool INV> __device__ u64 load_first(u32 J) const
+    {
+        const u32 N = p.tp.N;
         u128acc a;
         acc_zero(a);
-#pragma unroll
-        for (u32 k = 0; k < 16; k++)
-            if (k < K) acc_mad(a, x[k], __ldg(&conv_tab[(u64)k * L + i]));
-        const ModConst c = mc[i];
-        conv[((u64)b * level + i) * N + n] = redc_acc(a, c.q, c.qneg_inv);
+        for (u32 k = 0; k < p.K; k++) acc_mad(a, pc[(u64)k * N + J], __ldg(&p.moddown_conv[(u64)k * p.L + i]));
+        const ModConst &m = p.tp.mc[i];
+        return redc_acc(a, m.q, m.qneg_inv);
     }
+    __device__ u64 load_mid(u32 J) const { return mid[J]; }
+    __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
+    __device__ void store_last(int, u32, u64, const ModConst &) const {}
+};
+
+// DNB: second forward pass; out = (acc - conv) * P^-1 (+ sigma_g(c0) for b = 0)
+struct DnBJob : JobCommon {
+    const u64 *mid, *acc, *c0i;
+    u64 *out;
+    ulonglong2 pi;
+    u32 b;
+    __device__ DnBJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_DNB>(P, task, sub);
+        const u32 l = d->level, N = P.tp.N, i = sub % l;
+        b = sub / l;
+        midx = i;
+        mid = ws_conv(*d, P.K, N) + ((u64)b * l + i) * N;
+        acc = ws_acc(*d, P.K, N) + ((u64)b * (l + P.K) + i) * N;
+        c0i = d->c0 + (u64)i * N;
+        out = d->out + ((u64)b * l + i) * N;
+        pi = P.pinv[i];
+    }
+    template <bool INV> __device__ u64 load_first(u32) const { return 0; }
+    __device__ u64 load_mid(u32 J) const { return mid[J]; }
+    __device__ void store_mid(u32, u64) const {}
+    __device__ void store_last(int, u32 J, u64 y, const ModConst &m) const
+    {
+        u64 r = shoup(acc[J] + m.q - y, pi.x, pi.y, m.q);
+        if (b == 0) r = addmod(r, c0i[automorph_src(J, d->g, p.tp.logN)], m.q);
+        out[J] = r;
+    }
+};
+
+BatchParams batch_params(const fheon_ctx *ctx)
+{
+    BatchParams P{};
+    P.tp = tab_ptrs(ctx);
+    P.L = ctx->L;
+    P.K = ctx->K;
+    P.alpha = ctx->alpha;
+    P.modup_scale = ctx->tab.modup_scale.as<ulonglong2>();
+    P.modup_conv = ctx->tab.modup_conv.as<u64>();
+    P.moddown_scale = ctx->tab.moddown_scale.as<ulonglong2>();
+    P.moddown_conv = ctx->tab.moddown_conv.as<u64>();
+    P.pinv = ctx->tab.pinv.as<ulonglong2>();
+    return P;
 }
 
-// Step 8.  out[b][i][n] = (acc[b][i][n] - conv[b][i][n]) * P^-1 (+ c0[i][src(n)] when b = 0).
-__global__ void __launch_bounds__(TPB) moddown_combine_kernel(const u64 *__restrict__ acc,
-                                                              const u64 *__restrict__ conv,
-                                                              const u64 *__restrict__ c0, u64 g,
-                                                              u64 *__restrict__ out, u32 level, u32 K, u32 N,
-                                                              u32 logN, const ulonglong2 *__restrict__ pinv,
-                                                              const ModConst *__restrict__ mc)
+struct StageCounts {
+    u32 ic = 0, upa = 0, upb = 0, dni = 0, dna = 0, dnb = 0;
+};
+
+// the six launches over `P` (tasks given explicitly or in closed form)
+int run_pipeline(fheon_ctx *ctx, BatchParams P, const StageCounts &n, const u32 *const tasks[6])
 {
-    const u64 idx = (u64)blockIdx.x * TPB + threadIdx.x;
-    const u64 per = (u64)level * N;
-    if (idx >= 2 * per) return;
-    const u32 b = (u32)(idx / per);
-    const u32 i = (u32)((idx % per) / N), n = (u32)(idx % N);
-    const u64 q = mc[i].q;
-    const u64 a = acc[((u64)b * (level + K) + i) * N + n];
-    const u64 v = conv[((u64)b * level + i) * N + n];
-    const ulonglong2 pi = pinv[i];
-    u64 r = shoup(a + q - v, pi.x, pi.y, q);
-    if (b == 0) r = addmod(r, c0[(u64)i * N + automorph_src(n, g, logN)], q);
-    out[idx] = r;
+    cudaStream_t st = ctx->stream;
+    const u32 lg = ctx->logN;
+    P.tasks = tasks[0];
+    FHEON_CUDA(ctx, (ntt::launch_pass<true, true, IcJob>(lg, P, n.ic, st, "ic_intt_rows")));
+    FHEON_CUDA(ctx, (ntt::launch_pass<true, false, IcJob>(lg, P, n.ic, st, "ic_intt_cols")));
+    P.tasks = tasks[1];
+    FHEON_CUDA(ctx, (ntt::launch_pass<false, true, UpAJob>(lg, P, n.upa, st, "up_bconv_ntt_cols")));
+    P.tasks = tasks[2];
+    FHEON_CUDA(ctx, (ntt::launch_pass<false, false, UpBJob>(lg, P, n.upb, st, "up_ntt_rows_keyip")));
+    P.tasks = tasks[3];
+    FHEON_CUDA(ctx, (ntt::launch_pass<true, true, DnIJob>(lg, P, n.dni, st, "dn_intt_rows")));
+    FHEON_CUDA(ctx, (ntt::launch_pass<true, false, DnIJob>(lg, P, n.dni, st, "dn_intt_cols")));
+    P.tasks = tasks[4];
+    FHEON_CUDA(ctx, (ntt::launch_pass<false, true, DnAJob>(lg, P, n.dna, st, "dn_bconv_ntt_cols")));
+    P.tasks = tasks[5];
+    FHEON_CUDA(ctx, (ntt::launch_pass<false, false, DnBJob>(lg, P, n.dnb, st, "dn_ntt_rows_combine")));
+    return FHEON_OK;
+}
+
+StageCounts counts_for(const fheon_ctx *ctx, u32 l)
+{
+    const u32 K = ctx->K, beta = ctx->beta_at(l);
+    StageCounts c;
+    c.ic = l;
+    c.upa = beta * (l + K) - l;
+    c.upb = l + K;
+    c.dni = 2 * K;
+    c.dna = 2 * l;
+    c.dnb = 2 * l;
+    return c;
 }
 
 } // namespace
 
-// Run the whole pipeline for one ciphertext.  `ws` holds ks_ws_limbs(l) limbs.
+// One ciphertext, closed-form tasks: no device plan, no allocation.
 int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out)
 {
-    const u32 N = ctx->N, K = ctx->K, L = ctx->L, A = ctx->alpha, beta = ctx->beta_at(l);
-    cudaStream_t st = ctx->stream;
-    u64 *xt = ws;
-    u64 *ext = xt + (u64)l * N;
-    u64 *acc = ext + (u64)beta * (l + K) * N;
-    u64 *pc = acc + (u64)2 * (l + K) * N;
-    u64 *conv = pc + (u64)2 * K * N;
-    const ModConst *mc = ctx->tab.mc.as<ModConst>();
-
-    // 1: INTT(sigma_g(c1)) scaled for ModUp
-    {
-        MapParams mp = map_params(ctx, c1, xt, l, 0, l);
-        mp.gather_g = g;
-        mp.scale_mode = SCALE_MODUP;
-        mp.scale_tab = ctx->tab.modup_scale.as<ulonglong2>();
-        FHEON_CUDA(ctx, (ntt::launch<true, MapJob>(ctx->logN, mp, l, st)));
-    }
-    // 2: ModUp base conversion
-    modup_bconv_kernel<<<dim3((N + TPB - 1) / TPB, beta), TPB, 0, st>>>(xt, ext, l, K, L, A, N,
-                                                                         ctx->tab.modup_conv.as<u64>(), mc);
-    prof_mark(st, "modup_bconv");
-    FHEON_CUDA(ctx, cudaGetLastError());
-    // 3: NTT of the converted limbs (digit limbs skipped)
-    {
-        MapParams mp = map_params(ctx, ext, ext, l + K, 0, l);
-        mp.skip_digit = 1;
-        FHEON_CUDA(ctx, (ntt::launch<false, MapJob>(ctx->logN, mp, beta * (l + K), st)));
-    }
-    // 4: inner product with the key
-    ks_inner_kernel<<<dim3((N / 2 + TPB - 1) / TPB, l + K), TPB, 0, st>>>(c1, g, ext, key, acc, l, K, L, A, N,
-                                                                          ctx->logN, mc);
-    prof_mark(st, "ks_inner");
-    FHEON_CUDA(ctx, cudaGetLastError());
-    // 5: INTT of the P limbs of both components
-    {
-        MapParams mp = map_params(ctx, acc + (u64)l * N, pc, K, l, l);
-        mp.in_poly_stride = (u64)(l + K) * N;
-        mp.out_poly_stride = (u64)K * N;
-        mp.scale_mode = SCALE_MODDOWN;
-        mp.scale_tab = ctx->tab.moddown_scale.as<ulonglong2>();
-        FHEON_CUDA(ctx, (ntt::launch<true, MapJob>(ctx->logN, mp, 2 * K, st)));
-    }
-    // 6: ModDown base conversion P -> Q_l
-    moddown_bconv_kernel<<<dim3((N + TPB - 1) / TPB, 2), TPB, 0, st>>>(pc, conv, l, K, L, N,
-                                                                       ctx->tab.moddown_conv.as<u64>(), mc);
-    prof_mark(st, "moddown_bconv");
-    FHEON_CUDA(ctx, cudaGetLastError());
-    // 7: NTT of the converted limbs
-    {
-        MapParams mp = map_params(ctx, conv, conv, l, 0, l);
-        FHEON_CUDA(ctx, (ntt::launch<false, MapJob>(ctx->logN, mp, 2 * l, st)));
-    }
-    // 8: combine
-    {
-        const u64 tot = (u64)2 * l * N;
-        moddown_combine_kernel<<<(unsigned)((tot + TPB - 1) / TPB), TPB, 0, st>>>(
-            acc, conv, c0, g, out, l, K, N, ctx->logN, ctx->tab.pinv.as<ulonglong2>(), mc);
-        prof_mark(st, "moddown_combine");
-        FHEON_CUDA(ctx, cudaGetLastError());
-    }
-    return FHEON_OK;
+    BatchParams P = batch_params(ctx);
+    P.desc = nullptr;
+    P.one = RotDesc{c0, c1, out, key, ws, g, l, ctx->beta_at(l)};
+    const u32 *none[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    return run_pipeline(ctx, P, counts_for(ctx, l), none);
 }
 
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out)
@@ -214,7 +369,6 @@ int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out)
     if (rc) return rc;
     u64 *ws = ctx->ws.as<u64>();
     const u64 *c0 = in->c0(), *c1 = in->c1(ctx->N);
-    const double sc = in->scale;
     if (out == in) {
         u64 *stage = ws + ctx->ks_ws_limbs(ctx->L) * ctx->N;
         rc = keyswitch_rotate(ctx, c0, c1, l, g, it->second.mem.as<u64>(), ws, stage);
@@ -225,18 +379,150 @@ int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out)
     }
     rc = ct_reshape(ctx, out, l);
     if (rc) return rc;
-    out->scale = sc;
+    out->scale = in->scale;
     return keyswitch_rotate(ctx, c0, c1, l, g, it->second.mem.as<u64>(), ws, out->c0());
+}
+
+// ---------------------------------------------------------------- batches
+// A plan holds the descriptors and the six task lists of one batch in device
+// memory; plans are cached by the batch's signature (buffers, levels, keys and
+// workspace), so a batch rotated repeatedly uploads its plan once.
+struct RotPlan {
+    std::vector<u64> sig;
+    DevMem mem;
+    StageCounts n;
+    const u32 *tasks[6];
+    const RotDesc *desc;
+    u64 last_use = 0;
+};
+
+static std::mutex g_plan_mu;
+static std::map<fheon_ctx *, std::vector<RotPlan>> &plan_caches()
+{
+    static auto *c = new std::map<fheon_ctx *, std::vector<RotPlan>>(); // outlives static teardown
+    return *c;
+}
+// one cache per context, kept in a side table; callers hold g_plan_mu
+static std::vector<RotPlan> &plan_cache(fheon_ctx *ctx) { return plan_caches()[ctx]; }
+
+void drop_plans(fheon_ctx *ctx)
+{
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    plan_caches().erase(ctx);
 }
 
 int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
 {
-    for (u32 i = 0; i < n; i++) {
-        if (!items[i].in || !items[i].out) return fail(ctx, FHEON_ERR_ARG, "null ciphertext in batch item %u", i);
-        int rc = fheon_rotate(ctx, items[i].in, items[i].step, items[i].out);
-        if (rc) return rc;
+    if (n == 0) return FHEON_OK;
+    if (n > 65535) {
+        for (u32 s = 0; s < n; s += 65535) {
+            int rc = rotate_many(ctx, items + s, std::min<u32>(65535, n - s));
+            if (rc) return rc;
+        }
+        return FHEON_OK;
     }
-    return FHEON_OK;
+    const u32 N = ctx->N;
+    // validate, size outputs, lay out the workspace
+    std::vector<u64> sig;
+    std::vector<size_t> ws_off(n);
+    size_t ws_total = 0;
+    std::vector<const u64 *> keyp(n);
+    for (u32 i = 0; i < n; i++) {
+        const fheon_ct *in = items[i].in;
+        fheon_ct *out = items[i].out;
+        if (!in || !out) return fail(ctx, FHEON_ERR_ARG, "null ciphertext in batch item %u", i);
+        const u64 g = fheon_galois_elt(ctx, items[i].step);
+        auto it = ctx->keys.find(g);
+        if (it == ctx->keys.end())
+            return fail(ctx, FHEON_ERR_NO_KEY, "no rotation key for step %d (batch item %u)", items[i].step, i);
+        keyp[i] = it->second.mem.as<u64>();
+        ws_off[i] = ws_total;
+        ws_total += ctx->ks_ws_limbs(in->level);
+    }
+    for (u32 i = 0; i < n; i++)
+        for (u32 k = 0; k < n; k++)
+            if (items[i].out == items[k].in)
+                return fail(ctx, FHEON_ERR_ARG, "batch output %u aliases input %u", i, k);
+    for (u32 i = 0; i < n; i++) {
+        int rc = ct_reshape(ctx, items[i].out, items[i].in->level);
+        if (rc) return rc;
+        items[i].out->scale = items[i].in->scale;
+    }
+    int rc = ensure_workspace(ctx, std::max(ws_total, ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L));
+    if (rc) return rc;
+    u64 *ws = ctx->ws.as<u64>();
+    sig.reserve(4 * n + 2);
+    sig.push_back((u64)ws);
+    sig.push_back(n);
+    for (u32 i = 0; i < n; i++) {
+        sig.push_back((u64)items[i].in->c.p ^ ((u64)items[i].in->level << 56));
+        sig.push_back((u64)items[i].out->c.p);
+        sig.push_back((u64)keyp[i]);
+        sig.push_back(fheon_galois_elt(ctx, items[i].step));
+    }
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto &cache = plan_cache(ctx);
+    static u64 tick = 0;
+    RotPlan *plan = nullptr;
+    for (auto &p : cache)
+        if (p.sig == sig) { plan = &p; break; }
+    if (!plan) {
+        std::vector<RotDesc> desc(n);
+        std::vector<u32> t[6];
+        StageCounts cnt;
+        for (u32 i = 0; i < n; i++) {
+            const fheon_ct *in = items[i].in;
+            const u32 l = in->level, K = ctx->K, A = ctx->alpha, beta = ctx->beta_at(l);
+            desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ws + ws_off[i] * N,
+                              fheon_galois_elt(ctx, items[i].step), l, beta};
+            const u32 c = i << 16;
+            for (u32 x = 0; x < l; x++) t[0].push_back(c | x);
+            for (u32 j = 0; j < beta; j++)
+                for (u32 x = 0; x < l + K; x++)
+                    if (!(x >= j * A && x < std::min(j * A + A, l))) t[1].push_back(c | (j << 8) | x);
+            for (u32 x = 0; x < l + K; x++) t[2].push_back(c | x);
+            for (u32 x = 0; x < 2 * K; x++) t[3].push_back(c | x);
+            for (u32 x = 0; x < 2 * l; x++) t[4].push_back(c | x);
+            for (u32 x = 0; x < 2 * l; x++) t[5].push_back(c | x);
+        }
+        size_t bytes = n * sizeof(RotDesc);
+        size_t off[6];
+        for (int s = 0; s < 6; s++) {
+            off[s] = bytes;
+            bytes += t[s].size() * sizeof(u32);
+        }
+        if (cache.size() >= 32) {
+            auto lru = std::min_element(cache.begin(), cache.end(),
+                                        [](const RotPlan &a, const RotPlan &b) { return a.last_use < b.last_use; });
+            cudaStreamSynchronize(ctx->stream); // the plan may be in use by queued launches
+            cache.erase(lru);
+        }
+        cache.emplace_back();
+        plan = &cache.back();
+        plan->sig = sig;
+        if (!plan->mem.alloc(bytes, ctx->stream)) {
+            cache.pop_back();
+            return fail(ctx, FHEON_ERR_OOM, "rotation plan (%zu bytes)", bytes);
+        }
+        std::vector<unsigned char> host(bytes);
+        memcpy(host.data(), desc.data(), n * sizeof(RotDesc));
+        for (int s = 0; s < 6; s++) memcpy(host.data() + off[s], t[s].data(), t[s].size() * sizeof(u32));
+        FHEON_CUDA(ctx, cudaMemcpyAsync(plan->mem.p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+        FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream)); // `host` is released on return
+        char *base = plan->mem.as<char>();
+        plan->desc = reinterpret_cast<const RotDesc *>(base);
+        for (int s = 0; s < 6; s++) plan->tasks[s] = reinterpret_cast<const u32 *>(base + off[s]);
+        plan->n.ic = (u32)t[0].size();
+        plan->n.upa = (u32)t[1].size();
+        plan->n.upb = (u32)t[2].size();
+        plan->n.dni = (u32)t[3].size();
+        plan->n.dna = (u32)t[4].size();
+        plan->n.dnb = (u32)t[5].size();
+    }
+    plan->last_use = ++tick;
+    BatchParams P = batch_params(ctx);
+    P.desc = plan->desc;
+    return run_pipeline(ctx, P, plan->n, plan->tasks);
 }
 
 } // namespace fheon

@@ -30,6 +30,7 @@ struct ModConst {
     u64 r1;       // 2^64 mod q
     u64 r1_sh;    // Shoup companion of r1: redc result times r1 = plain residue
     u64 twoq;     // 2q
+    u64 one_sh;   // floor(2^64 / q): Shoup product by 1 reduces any word to [0, 2q)
 };
 
 __device__ __forceinline__ u64 mulhi64(u64 a, u64 b) { return __umul64hi(a, b); }

@@ -5,7 +5,7 @@
 // transform writes out[j] = a(psi^(2*brv(j)+1)), i.e. the Cooley-Tukey
 // "merged" negacyclic NTT with bit-reversed output (Longa-Naehrig 2016); the
 // inverse is the Gentleman-Sande transform back to natural order times N^-1
-// (times an optional per-limb constant folded into the last multiply).
+// (times an optional per-limb constant folded into that last multiply).
 //
 // A butterfly at half-size t = 2^tau on lower index J uses twiddle number
 // 2^(logN-1-tau) + (J >> (tau+1)) of the table psi^brv(i) (forward) or
@@ -14,17 +14,32 @@
 // GB300 mapping.  One limb of N = 2^16 u64 is 512 KiB, more than a CTA's
 // shared memory, so each transform is two passes over a limb viewed as an
 // N1 x N2 matrix (J = u*N2 + c):
-//   pass A ("columns"): the butterflies on the high log2(N1) bits of J; a CTA
-//     owns SUBS adjacent columns, so warps read 128-byte row segments;
-//   pass B ("rows"):    the butterflies on the low log2(N2) bits; a CTA owns
-//     SUBS contiguous rows.
-// Forward runs A then B, inverse B then A; the second pass works in place on
-// the first pass's output (intermediate values stay lazily reduced).  Inside
-// a pass each thread keeps R = 16 elements in registers and does 4 stages per
-// round (radix 16), exchanging through shared memory between rounds; the
-// row layout is padded by one word per 16 so strided rounds are free of bank
-// conflicts.  Loads and stores of the tile go through a Job policy, which is
-// where automorphism gathers, base conversions and epilogues fuse in.
+//   pass A ("columns"): butterflies on the high log2(N1) bits of J; a CTA owns
+//     SUBS adjacent columns, so a warp touches 128-byte row segments;
+//   pass B ("rows"):    butterflies on the low log2(N2) bits; a CTA owns SUBS
+//     contiguous rows.
+// Forward runs A then B, inverse B then A; the second pass reads the first
+// pass's output (lazily reduced) from the job's mid buffer.  Each thread keeps
+// R = 16 elements in registers and does 4 stages per round (radix 16),
+// exchanging through shared memory between rounds (rows padded by one word
+// per 16: no bank conflicts).  Where a round's register layout is already
+// coalesced in global memory (forward loads, most stores), the tile moves
+// straight between registers and global memory; elsewhere it is staged
+// through shared memory.
+//
+// Reduction.  For primes below 2^54 the butterflies skip every conditional
+// subtraction: forward outputs stay below x_in + 2q (at most 35q after 17
+// stages), inverse values below 2^(s+1) q at stage s of a pass with the
+// stage constant 2^(s+1) q keeping X - Y + C non-negative; one Shoup-by-one
+// reduction at the second pass's load and at the end makes them canonical.
+// Larger primes use Harvey's lazy butterflies ([0, 4q) forward, [0, 2q)
+// inverse).
+//
+// Jobs.  Loads, stores, the limb's modulus and twiddles come from a Job
+// policy.  A job may also repeat the transform over several inputs that
+// share one output (`reps`; the key inner product sums digits this way), pass
+// an input through without transforming it, and finish with a per-element
+// epilogue.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -32,24 +47,24 @@
 
 namespace fheon {
 // Instrumentation hook: records a CUDA event named `name` on `st` after the
-// preceding launch when the calling thread's context is being profiled.
+// preceding launch while a profile is open on that stream.
 void prof_mark(cudaStream_t st, const char *name);
-}
+} // namespace fheon
 
 namespace ntt {
 
 constexpr int LOGR = 4;
 constexpr int R = 1 << LOGR;
 constexpr int TILE_ELEMS = 4096;
-constexpr int NTHREADS = 256;
+constexpr u64 LAZY_BOUND = 1ull << 54;
 
 template <int LOGN>
 struct Cfg {
-    static constexpr int B1 = LOGN / 2;      // pass A bits (high)
-    static constexpr int B2 = LOGN - B1;     // pass B bits (low)
+    static constexpr int B1 = LOGN / 2;  // pass A bits (high)
+    static constexpr int B2 = LOGN - B1; // pass B bits (low)
     static constexpr int N1 = 1 << B1, N2 = 1 << B2;
     static constexpr int TILE = (1 << LOGN) < TILE_ELEMS ? (1 << LOGN) : TILE_ELEMS;
-    static constexpr int ROW_SUBS = TILE / N2;                          // rows per CTA (pass B)
+    static constexpr int ROW_SUBS = TILE / N2;                           // rows per CTA (pass B)
     static constexpr int COL_SUBS = (TILE / N1) < N2 ? (TILE / N1) : N2; // columns per CTA (pass A)
     static constexpr int ROW_THREADS = ROW_SUBS * (N2 / R);
     static constexpr int COL_THREADS = COL_SUBS * (N1 / R);
@@ -59,139 +74,270 @@ struct Cfg {
     static constexpr int COL_SMEM = COL_SUBS * N1 * 8;
 };
 
-// One pass.  ROWS: pass B, else pass A.  FIRST: this is the first of the two
-// passes (loads through Job::load_first, stores raw to Job::mid), else the
-// second (loads Job::mid, stores through Job::store_last).
-template <int LOGN, bool INV, bool ROWS, bool FIRST, class Job>
-__global__ void __launch_bounds__(256) pass_kernel(const __grid_constant__ typename Job::Params prm)
+// Defaults for the optional parts of the Job interface.
+struct JobBase {
+    // extra shared memory the job needs, in u64 words per tile element; the
+    // kernel hands it over with attach()
+    static constexpr int EXTRA_WORDS_PER_ELEM = 0;
+    __device__ void attach(u64 *) {}
+    __device__ int reps() const { return 1; }
+    __device__ void begin(int) {}
+    __device__ bool passthrough() const { return false; }
+    __device__ u64 load_passthrough(u32) const { return 0; }
+    __device__ void finish(int, u32, const ModConst &) {}
+};
+
+// reduce v < 2^64 to [0, q) with one Shoup product by 1 and a subtraction
+__device__ __forceinline__ u64 reduce_any(u64 v, const ModConst &m)
+{
+    u64 r = v - __umul64hi(v, m.one_sh) * m.q;
+    return r >= m.q ? r - m.q : r;
+}
+__device__ __forceinline__ u64 reduce_any_lazy(u64 v, const ModConst &m) { return v - __umul64hi(v, m.one_sh) * m.q; }
+
+template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job>
+__device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile)
 {
     using C = Cfg<LOGN>;
     constexpr int LOGM = ROWS ? C::B2 : C::B1;
     constexpr int M = 1 << LOGM;
-    constexpr int G = M / R;                       // threads per sub-transform
+    constexpr int G = M / R;
     constexpr int SUBS = ROWS ? C::ROW_SUBS : C::COL_SUBS;
     constexpr int NT = SUBS * G;
-    constexpr int TILES = ROWS ? C::ROW_TILES : C::COL_TILES;
     constexpr int ROUNDS = (LOGM + LOGR - 1) / LOGR;
     constexpr int RSTRIDE = M + M / 16;
+    // round 0 of a forward pass covers the top bits: e = v*G + g, coalesced in
+    // both passes; an inverse column pass starts on the low bits of u, which
+    // are still coalesced across its lanes (lanes differ in the column).
+    constexpr bool DIRECT_LOAD = !INV || !ROWS;
+    // the last round of a forward row pass covers the low bits: a thread owns
+    // 16 consecutive words, so that store is staged; every other last round is
+    // coalesced across lanes.
+    constexpr bool DIRECT_STORE = INV || !ROWS;
 
     extern __shared__ u64 sm[];
-    const u32 job_i = blockIdx.x / TILES;
-    const u32 tile = blockIdx.x % TILES;
-    Job job(prm, job_i);
-    if (!job.active()) return;
-    const ModConst mc = job.mod();
+    job.attach(sm + (ROWS ? SUBS * RSTRIDE : SUBS * M));
     const ulonglong2 *__restrict__ tw = job.twiddles(INV);
     const u64 q = mc.q, twoq = mc.twoq;
     const int t = threadIdx.x;
-
-    // ---- load the tile (coalesced) ----
-#pragma unroll
-    for (int k = 0; k < R; k++) {
-        const int lin = t + k * NT;
-        int sub, e;
-        if (ROWS) { sub = lin / M; e = lin % M; }
-        else { sub = lin % SUBS; e = lin / SUBS; }
-        const u32 J = ROWS ? (u32)((tile * SUBS + sub) * M + e) : (u32)(e * C::N2 + tile * SUBS + sub);
-        const int s = ROWS ? sub * RSTRIDE + e + (e >> 4) : e * SUBS + sub;
-        sm[s] = FIRST ? job.template load_first<INV>(J) : job.load_mid(J);
-    }
-    __syncthreads();
-
     int sub, g;
     if (ROWS) { sub = t / G; g = t % G; }
     else { sub = t % SUBS; g = t / SUBS; }
-    const u32 row = (u32)(tile * SUBS + sub); // global row (pass B only)
+    const u32 line = (u32)(tile * SUBS + sub); // global row (pass B) or column (pass A)
 
-    u64 x[R];
-#pragma unroll
-    for (int rd = 0; rd < ROUNDS; rd++) {
+    auto gidx = [&](int sb, int e) -> u32 {
+        return ROWS ? (u32)((tile * SUBS + sb) * M + e) : (u32)(e * C::N2 + tile * SUBS + sb);
+    };
+    auto sidx = [&](int sb, int e) -> int { return ROWS ? sb * RSTRIDE + e + (e >> 4) : e * SUBS + sb; };
+    // element of register v in round rd
+    auto relem = [&](int rd, int v) -> int {
         const int lo = INV ? rd * LOGR : ((LOGM - (rd + 1) * LOGR) > 0 ? LOGM - (rd + 1) * LOGR : 0);
         const int nb = INV ? ((LOGM - lo) < LOGR ? LOGM - lo : LOGR) : (LOGM - rd * LOGR) - lo;
-        int e[R];
+        const int rest = (g << (LOGR - nb)) | (v >> nb);
+        return ((rest >> lo) << (lo + nb)) | ((v & ((1 << nb) - 1)) << lo) | (rest & ((1 << lo) - 1));
+    };
+    // element index of store slot k (register v in the last round, or the staged linear slot)
+    auto store_J = [&](int k) -> u32 {
+        if (DIRECT_STORE) return gidx(sub, relem(ROUNDS - 1, k));
+        const int lin = t + k * NT;
+        return ROWS ? gidx(lin / M, lin % M) : gidx(lin % SUBS, lin / SUBS);
+    };
+
+    const int nrep = job.reps();
+    for (int rep = 0; rep < nrep; rep++) {
+        job.begin(rep);
+        if (job.passthrough()) {
 #pragma unroll
-        for (int v = 0; v < R; v++) {
-            const int rest = (g << (LOGR - nb)) | (v >> nb);
-            const int lowp = rest & ((1 << lo) - 1);
-            const int highp = rest >> lo;
-            e[v] = (highp << (lo + nb)) | ((v & ((1 << nb) - 1)) << lo) | lowp;
-            x[v] = sm[ROWS ? sub * RSTRIDE + e[v] + (e[v] >> 4) : e[v] * SUBS + sub];
+            for (int k = 0; k < R; k++) {
+                const u32 J = store_J(k);
+                job.store_last(k, J, job.load_passthrough(J), mc);
+            }
+            continue;
         }
-#pragma unroll
-        for (int s = 0; s < nb; s++) {
-            const int vb = INV ? s : nb - 1 - s;
-            const int b = lo + vb;                       // local bit of this stage
-            const int tau = b + (ROWS ? 0 : C::B2);      // global bit
-            ulonglong2 w = make_ulonglong2(0, 0);
+        u64 x[R];
+        // ---- load ----
+        if (DIRECT_LOAD) {
 #pragma unroll
             for (int v = 0; v < R; v++) {
-                if ((v >> vb) & 1) continue;
-                if ((v & ((1 << vb) - 1)) == 0) {
-                    const u32 prefix = ROWS ? ((row << (LOGM - 1 - b)) + ((u32)e[v] >> (b + 1)))
-                                            : ((u32)e[v] >> (b + 1));
-                    w = __ldg(&tw[(1u << (LOGN - 1 - tau)) + prefix]);
+                const u32 J = gidx(sub, relem(0, v));
+                x[v] = FIRST ? job.template load_first<INV>(J) : job.load_mid(J);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const int lin = t + k * NT;
+                const int sb = ROWS ? lin / M : lin % SUBS, e = ROWS ? lin % M : lin / SUBS;
+                const u32 J = gidx(sb, e);
+                sm[sidx(sb, e)] = FIRST ? job.template load_first<INV>(J) : job.load_mid(J);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < R; v++) x[v] = sm[sidx(sub, relem(0, v))];
+        }
+        if (LAZY && INV && !FIRST) {
+#pragma unroll
+            for (int v = 0; v < R; v++) x[v] = reduce_any_lazy(x[v], mc); // < 2q
+        }
+        // ---- rounds ----
+#pragma unroll
+        for (int rd = 0; rd < ROUNDS; rd++) {
+            const int lo = INV ? rd * LOGR : ((LOGM - (rd + 1) * LOGR) > 0 ? LOGM - (rd + 1) * LOGR : 0);
+            const int nb = INV ? ((LOGM - lo) < LOGR ? LOGM - lo : LOGR) : (LOGM - rd * LOGR) - lo;
+            if (rd > 0) {
+#pragma unroll
+                for (int v = 0; v < R; v++) x[v] = sm[sidx(sub, relem(rd, v))];
+            }
+#pragma unroll
+            for (int s = 0; s < nb; s++) {
+                const int vb = INV ? s : nb - 1 - s;
+                const int b = lo + vb;                  // local bit of this stage
+                const int tau = b + (ROWS ? 0 : C::B2); // global bit
+                const int sp = INV ? rd * LOGR + s : 0; // stage index within an inverse pass
+                const u64 cst = twoq << sp;             // 2^(sp+1) q: keeps X - Y + C >= 0 (lazy inverse)
+                ulonglong2 w = make_ulonglong2(0, 0);
+#pragma unroll
+                for (int v = 0; v < R; v++) {
+                    if ((v >> vb) & 1) continue;
+                    const int e = relem(rd, v);
+                    if ((v & ((1 << vb) - 1)) == 0) {
+                        const u32 prefix = ROWS ? ((line << (LOGM - 1 - b)) + ((u32)e >> (b + 1))) : ((u32)e >> (b + 1));
+                        w = __ldg(&tw[(1u << (LOGN - 1 - tau)) + prefix]);
+                    }
+                    u64 &X = x[v], &Y = x[v | (1 << vb)];
+                    if (INV) {
+                        if (LAZY) {
+                            const u64 d = X - Y + cst;
+                            X = X + Y;
+                            Y = shoup_lazy(d, w.x, w.y, q);
+                        } else {
+                            gs_butterfly(X, Y, w.x, w.y, q, twoq);
+                        }
+                    } else {
+                        if (LAZY) {
+                            const u64 tt = shoup_lazy(Y, w.x, w.y, q);
+                            Y = X - tt + twoq;
+                            X = X + tt;
+                        } else {
+                            ct_butterfly(X, Y, w.x, w.y, q, twoq);
+                        }
+                    }
                 }
-                if (INV) gs_butterfly(x[v], x[v | (1 << vb)], w.x, w.y, q, twoq);
-                else ct_butterfly(x[v], x[v | (1 << vb)], w.x, w.y, q, twoq);
+            }
+            if (rd < ROUNDS - 1) {
+#pragma unroll
+                for (int v = 0; v < R; v++) sm[sidx(sub, relem(rd, v))] = x[v];
+                __syncthreads();
             }
         }
+        // ---- store ----
+        auto emit = [&](int k, u32 J, u64 val) {
+            if (FIRST) {
+                job.store_mid(J, val);
+            } else {
+                u64 r;
+                if (INV) {
+                    const ulonglong2 s = job.inv_scale();
+                    r = shoup(val, s.x, s.y, q); // any input < 2^64
+                } else {
+                    r = LAZY ? reduce_any(val, mc) : reduce4q(val, q);
+                }
+                job.store_last(k, J, r, mc);
+            }
+        };
+        if (DIRECT_STORE) {
 #pragma unroll
-        for (int v = 0; v < R; v++) sm[ROWS ? sub * RSTRIDE + e[v] + (e[v] >> 4) : e[v] * SUBS + sub] = x[v];
-        __syncthreads();
+            for (int v = 0; v < R; v++) emit(v, gidx(sub, relem(ROUNDS - 1, v)), x[v]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < R; v++) sm[sidx(sub, relem(ROUNDS - 1, v))] = x[v];
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const int lin = t + k * NT;
+                const int sb = ROWS ? lin / M : lin % SUBS, e = ROWS ? lin % M : lin / SUBS;
+                emit(k, gidx(sb, e), sm[sidx(sb, e)]);
+            }
+        }
+        if (nrep > 1) __syncthreads(); // the next repetition reuses shared memory
     }
-
-    // ---- store the tile (coalesced) ----
+    if (!FIRST) {
 #pragma unroll
-    for (int k = 0; k < R; k++) {
-        const int lin = t + k * NT;
-        int sb, e;
-        if (ROWS) { sb = lin / M; e = lin % M; }
-        else { sb = lin % SUBS; e = lin / SUBS; }
-        const u32 J = ROWS ? (u32)((tile * SUBS + sb) * M + e) : (u32)(e * C::N2 + tile * SUBS + sb);
-        const u64 val = sm[ROWS ? sb * RSTRIDE + e + (e >> 4) : e * SUBS + sb];
-        if (FIRST) job.store_mid(J, val);
-        else job.template store_last<INV>(J, val, mc);
+        for (int k = 0; k < R; k++) job.finish(k, store_J(k), mc);
     }
 }
 
-// Launch both passes of a forward (INV = false) or inverse transform over
-// `njobs` limbs described by Job.
-template <int LOGN, bool INV, class Job>
-inline cudaError_t launch_fixed(const typename Job::Params &prm, u32 njobs, cudaStream_t st)
+// One pass over the tiles of every task.  ROWS: pass B, else pass A.  FIRST:
+// the first pass of the transform (reads the job's input, writes its mid
+// buffer), else the second (reads mid, writes the job's output).
+template <int LOGN, bool INV, bool ROWS, bool FIRST, class Job>
+__global__ void __launch_bounds__(256, 2) pass_kernel(const __grid_constant__ typename Job::Params prm)
 {
     using C = Cfg<LOGN>;
-    if (njobs == 0) return cudaSuccess;
-    constexpr bool FIRST_ROWS = INV; // inverse starts with rows, forward with columns
-    auto k1 = pass_kernel<LOGN, INV, FIRST_ROWS, true, Job>;
-    auto k2 = pass_kernel<LOGN, INV, !FIRST_ROWS, false, Job>;
-    const int th1 = FIRST_ROWS ? C::ROW_THREADS : C::COL_THREADS;
-    const int th2 = FIRST_ROWS ? C::COL_THREADS : C::ROW_THREADS;
-    const int sm1 = FIRST_ROWS ? C::ROW_SMEM : C::COL_SMEM;
-    const int sm2 = FIRST_ROWS ? C::COL_SMEM : C::ROW_SMEM;
-    const int tl1 = FIRST_ROWS ? C::ROW_TILES : C::COL_TILES;
-    const int tl2 = FIRST_ROWS ? C::COL_TILES : C::ROW_TILES;
-    static_assert(C::ROW_SMEM <= 48 * 1024 && C::COL_SMEM <= 48 * 1024, "tile exceeds default shared memory");
-    k1<<<dim3(njobs * tl1), dim3(th1), sm1, st>>>(prm);
-    fheon::prof_mark(st, INV ? "ntt_inv_rows" : "ntt_fwd_cols");
-    k2<<<dim3(njobs * tl2), dim3(th2), sm2, st>>>(prm);
-    fheon::prof_mark(st, INV ? "ntt_inv_cols" : "ntt_fwd_rows");
+    constexpr int TILES = ROWS ? C::ROW_TILES : C::COL_TILES;
+    const u32 task = blockIdx.x / TILES;
+    const u32 tile = blockIdx.x % TILES;
+    Job job(prm, task);
+    if (!job.active()) return;
+    const ModConst mc = job.mod();
+    if (mc.q < LAZY_BOUND) pass_body<LOGN, INV, ROWS, FIRST, true>(job, mc, tile);
+    else pass_body<LOGN, INV, ROWS, FIRST, false>(job, mc, tile);
+}
+
+template <int LOGN, bool INV, bool FIRST>
+struct PassShape {
+    using C = Cfg<LOGN>;
+    static constexpr bool ROWS = (INV == FIRST); // inverse starts with rows, forward with columns
+    static constexpr int threads = ROWS ? C::ROW_THREADS : C::COL_THREADS;
+    static constexpr int smem = ROWS ? C::ROW_SMEM : C::COL_SMEM;
+    static constexpr int tiles = ROWS ? C::ROW_TILES : C::COL_TILES;
+};
+
+// Launch one pass of a transform over `ntasks` tasks.
+template <int LOGN, bool INV, bool FIRST, class Job>
+inline cudaError_t launch_pass_fixed(const typename Job::Params &prm, u32 ntasks, cudaStream_t st, const char *name)
+{
+    using S = PassShape<LOGN, INV, FIRST>;
+    constexpr int smem = S::smem + Job::EXTRA_WORDS_PER_ELEM * Cfg<LOGN>::TILE * 8;
+    static_assert(smem <= 200 * 1024, "tile exceeds shared memory");
+    if (ntasks == 0) return cudaSuccess;
+    auto kern = pass_kernel<LOGN, INV, S::ROWS, FIRST, Job>;
+    if (smem > 48 * 1024) {
+        static bool attr = false; // one instantiation per kernel: set its opt-in limit once
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+    }
+    kern<<<dim3(ntasks * S::tiles), dim3(S::threads), smem, st>>>(prm);
+    fheon::prof_mark(st, name);
     return cudaGetLastError();
 }
 
-template <bool INV, class Job>
-inline cudaError_t launch(u32 logN, const typename Job::Params &prm, u32 njobs, cudaStream_t st)
+template <bool INV, bool FIRST, class Job>
+inline cudaError_t launch_pass(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st,
+                               const char *name)
 {
     switch (logN) {
-    case 10: return launch_fixed<10, INV, Job>(prm, njobs, st);
-    case 11: return launch_fixed<11, INV, Job>(prm, njobs, st);
-    case 12: return launch_fixed<12, INV, Job>(prm, njobs, st);
-    case 13: return launch_fixed<13, INV, Job>(prm, njobs, st);
-    case 14: return launch_fixed<14, INV, Job>(prm, njobs, st);
-    case 15: return launch_fixed<15, INV, Job>(prm, njobs, st);
-    case 16: return launch_fixed<16, INV, Job>(prm, njobs, st);
-    case 17: return launch_fixed<17, INV, Job>(prm, njobs, st);
+    case 10: return launch_pass_fixed<10, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 11: return launch_pass_fixed<11, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 12: return launch_pass_fixed<12, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 13: return launch_pass_fixed<13, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 14: return launch_pass_fixed<14, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 15: return launch_pass_fixed<15, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 16: return launch_pass_fixed<16, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 17: return launch_pass_fixed<17, INV, FIRST, Job>(prm, ntasks, st, name);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// Both passes of a transform whose two passes use the same job type.
+template <bool INV, class Job>
+inline cudaError_t launch(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st)
+{
+    cudaError_t e = launch_pass<INV, true, Job>(logN, prm, ntasks, st, INV ? "ntt_inv_rows" : "ntt_fwd_cols");
+    if (e != cudaSuccess) return e;
+    return launch_pass<INV, false, Job>(logN, prm, ntasks, st, INV ? "ntt_inv_cols" : "ntt_fwd_rows");
 }
 
 } // namespace ntt

@@ -82,6 +82,7 @@ ModConst h_modconst(u64 q)
     c.r2 = h_mulmod(c.r1, c.r1, q);
     c.r1_sh = h_shoup(c.r1, q);
     c.twoq = 2 * q;
+    c.one_sh = h_shoup(1, q);
     return c;
 }
 
