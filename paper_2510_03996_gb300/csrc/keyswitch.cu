@@ -123,6 +123,7 @@ struct IcJob : JobCommon {
 // UPA: first forward pass of limb t of digit j; the load is the ModUp base
 // conversion  y = sum_i xt[d0+i] * (Dhat_i mod m_t) (Montgomery constants, one REDC)
 struct UpAJob : JobCommon {
+    static constexpr int MIN_BLOCKS = 2;
     const u64 *src;
     const u64 *cf;
     u64 *mid;
@@ -139,14 +140,24 @@ struct UpAJob : JobCommon {
         cf = P.modup_conv + ((u64)(j * A + (dsz - 1)) * A) * (P.L + P.K) + midx;
         mid = ws_ext(*d, N) + ((u64)j * (l + P.K) + t) * N;
     }
-    template <bool INV> __device__ u64 load_first(u32 J) const
+    template <bool INV> __device__ u64 load_first(u32) const { return 0; }
+    // sources outermost: one constant per source, 16 independent 128-bit sums
+    static constexpr bool TILE_LOAD = true;
+    __device__ void load_tile_first(const u32 (&J)[ntt::R], u64 (&x)[ntt::R]) const
     {
         const u32 N = p.tp.N, nm = p.L + p.K;
-        u128acc a;
-        acc_zero(a);
-        for (u32 i = 0; i < dsz; i++) acc_mad(a, src[(u64)i * N + J], __ldg(&cf[(u64)i * nm]));
+        u128acc a[ntt::R];
+#pragma unroll
+        for (int v = 0; v < ntt::R; v++) acc_zero(a[v]);
+        for (u32 i = 0; i < dsz; i++) {
+            const u64 c = __ldg(&cf[(u64)i * nm]);
+            const u64 *s = src + (u64)i * N;
+#pragma unroll
+            for (int v = 0; v < ntt::R; v++) acc_mad(a[v], s[J[v]], c);
+        }
         const ModConst &m = p.tp.mc[midx];
-        return redc_acc(a, m.q, m.qneg_inv);
+#pragma unroll
+        for (int v = 0; v < ntt::R; v++) x[v] = redc_acc(a[v], m.q, m.qneg_inv);
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
     __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
@@ -157,6 +168,7 @@ struct UpAJob : JobCommon {
 // The two running sums of each of the thread's 16 output slots live in shared
 // memory (slot k of thread x at k*blockDim + x; only that thread touches it).
 struct UpBJob : JobCommon {
+    static constexpr int MIN_BLOCKS = 2;
     static constexpr int EXTRA_WORDS_PER_ELEM = 2;
     const u64 *mid, *kb, *ka, *c1t;
     u64 *acc0, *acc1;
@@ -181,13 +193,28 @@ struct UpBJob : JobCommon {
         acc1 = acc0 + (u64)(l + P.K) * N;
     }
     __device__ int reps() const { return (int)nrep; }
-    __device__ void begin(int j)
+    // this row tile's operands of digit j into L2: the two key tiles, and the
+    // mid tile (or, for the digit holding t, the gathered block of sigma_g(c1))
+    __device__ void prefetch_rep(u32 j, u32 tile) const
+    {
+        const u32 l = d->level, N = p.tp.N, nm = p.L + p.K, te = N < 4096 ? N : 4096;
+        const u64 off = (u64)tile * te;
+        prefetch_l2(d->key + (((u64)j * 2 + 0) * nm + midx) * N + off, te * 8);
+        prefetch_l2(d->key + (((u64)j * 2 + 1) * nm + midx) * N + off, te * 8);
+        if ((t < l) && (t / p.alpha == j))
+            prefetch_l2(c1t + (automorph_src((u32)off, d->g, p.tp.logN) & ~(te - 1)), te * 8);
+        else
+            prefetch_l2(ws_ext(*d, N) + ((u64)j * (l + p.K) + t) * N + off, te * 8);
+    }
+    __device__ void begin(int j, u32 tile)
     {
         const u32 l = d->level, N = p.tp.N, nm = p.L + p.K;
         if (j == 0) {
 #pragma unroll
             for (int k = 0; k < ntt::R; k++) slot(0, k) = slot(1, k) = 0;
+            if (threadIdx.x == 0) prefetch_rep(0, tile);
         }
+        if (threadIdx.x == 0 && (u32)j + 1 < nrep) prefetch_rep(j + 1, tile);
         pass = (t < l) && (t / p.alpha == (u32)j);
         mid = ws_ext(*d, N) + ((u64)j * (l + p.K) + t) * N;
         kb = d->key + (((u64)j * 2 + 0) * nm + midx) * N;
@@ -236,6 +263,7 @@ struct DnIJob : JobCommon {
 // DNA: first forward pass of q_i limb of component b; the load is the ModDown
 // base conversion P -> q_i from pc
 struct DnAJob : JobCommon {
+    static constexpr int MIN_BLOCKS = 2;
     const u64 *pc;
     u64 *mid;
     u32 i;
@@ -249,14 +277,23 @@ struct DnAJob : JobCommon {
         pc = ws_pc(*d, P.K, N) + (u64)b * P.K * N;
         mid = ws_conv(*d, P.K, N) + ((u64)b * l + i) * N;
     }
-    template <bool INV> __device__ u64 load_first(u32 J) const
+    template <bool INV> __device__ u64 load_first(u32) const { return 0; }
+    static constexpr bool TILE_LOAD = true;
+    __device__ void load_tile_first(const u32 (&J)[ntt::R], u64 (&x)[ntt::R]) const
     {
         const u32 N = p.tp.N;
-        u128acc a;
-        acc_zero(a);
-        for (u32 k = 0; k < p.K; k++) acc_mad(a, pc[(u64)k * N + J], __ldg(&p.moddown_conv[(u64)k * p.L + i]));
+        u128acc a[ntt::R];
+#pragma unroll
+        for (int v = 0; v < ntt::R; v++) acc_zero(a[v]);
+        for (u32 k = 0; k < p.K; k++) {
+            const u64 c = __ldg(&p.moddown_conv[(u64)k * p.L + i]);
+            const u64 *s = pc + (u64)k * N;
+#pragma unroll
+            for (int v = 0; v < ntt::R; v++) acc_mad(a[v], s[J[v]], c);
+        }
         const ModConst &m = p.tp.mc[i];
-        return redc_acc(a, m.q, m.qneg_inv);
+#pragma unroll
+        for (int v = 0; v < ntt::R; v++) x[v] = redc_acc(a[v], m.q, m.qneg_inv);
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
     __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
@@ -281,6 +318,15 @@ struct DnBJob : JobCommon {
         c0i = d->c0 + (u64)i * N;
         out = d->out + ((u64)b * l + i) * N;
         pi = P.pinv[i];
+    }
+    // the row tile's acc and gathered sigma_g(c0) block into L2 while the NTT runs
+    __device__ void begin(int, u32 tile) const
+    {
+        if (threadIdx.x != 0) return;
+        const u32 N = p.tp.N, te = N < 4096 ? N : 4096;
+        const u64 off = (u64)tile * te;
+        prefetch_l2(acc + off, te * 8);
+        if (b == 0) prefetch_l2(c0i + (automorph_src((u32)off, d->g, p.tp.logN) & ~(te - 1)), te * 8);
     }
     template <bool INV> __device__ u64 load_first(u32) const { return 0; }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
@@ -308,43 +354,50 @@ BatchParams batch_params(const fheon_ctx *ctx)
     return P;
 }
 
-struct StageCounts {
-    u32 ic = 0, upa = 0, upb = 0, dni = 0, dna = 0, dnb = 0;
+// Task lists of the six stages, each split by modulus class: [s][0] tasks
+// whose prime needs Harvey butterflies, [s][1] primes below ntt::LAZY_BOUND.
+// Null lists mean closed-form tasks over BatchParams::one (class 0 only).
+struct Lists {
+    const u32 *t[6][2] = {};
+    u32 n[6][2] = {};
 };
 
-// the six launches over `P` (tasks given explicitly or in closed form)
-int run_pipeline(fheon_ctx *ctx, BatchParams P, const StageCounts &n, const u32 *const tasks[6])
+template <bool INV, bool FIRST, class Job>
+int stage(fheon_ctx *ctx, BatchParams P, const Lists &ls, int s, const char *name)
 {
-    cudaStream_t st = ctx->stream;
-    const u32 lg = ctx->logN;
-    P.tasks = tasks[0];
-    FHEON_CUDA(ctx, (ntt::launch_pass<true, true, IcJob>(lg, P, n.ic, st, "ic_intt_rows")));
-    FHEON_CUDA(ctx, (ntt::launch_pass<true, false, IcJob>(lg, P, n.ic, st, "ic_intt_cols")));
-    P.tasks = tasks[1];
-    FHEON_CUDA(ctx, (ntt::launch_pass<false, true, UpAJob>(lg, P, n.upa, st, "up_bconv_ntt_cols")));
-    P.tasks = tasks[2];
-    FHEON_CUDA(ctx, (ntt::launch_pass<false, false, UpBJob>(lg, P, n.upb, st, "up_ntt_rows_keyip")));
-    P.tasks = tasks[3];
-    FHEON_CUDA(ctx, (ntt::launch_pass<true, true, DnIJob>(lg, P, n.dni, st, "dn_intt_rows")));
-    FHEON_CUDA(ctx, (ntt::launch_pass<true, false, DnIJob>(lg, P, n.dni, st, "dn_intt_cols")));
-    P.tasks = tasks[4];
-    FHEON_CUDA(ctx, (ntt::launch_pass<false, true, DnAJob>(lg, P, n.dna, st, "dn_bconv_ntt_cols")));
-    P.tasks = tasks[5];
-    FHEON_CUDA(ctx, (ntt::launch_pass<false, false, DnBJob>(lg, P, n.dnb, st, "dn_ntt_rows_combine")));
+    for (int cls = 0; cls < 2; cls++) {
+        if (!ls.n[s][cls]) continue;
+        P.tasks = ls.t[s][cls];
+        FHEON_CUDA(ctx, (ntt::launch_pass<INV, FIRST, Job>(ctx->logN, P, ls.n[s][cls], ctx->stream, name, cls == 1)));
+    }
     return FHEON_OK;
 }
 
-StageCounts counts_for(const fheon_ctx *ctx, u32 l)
+// the pipeline's launches over `P`
+int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls)
+{
+    int rc;
+    if ((rc = stage<true, true, IcJob>(ctx, P, ls, ST_IC, "ic_intt_rows"))) return rc;
+    if ((rc = stage<true, false, IcJob>(ctx, P, ls, ST_IC, "ic_intt_cols"))) return rc;
+    if ((rc = stage<false, true, UpAJob>(ctx, P, ls, ST_UPA, "up_bconv_ntt_cols"))) return rc;
+    if ((rc = stage<false, false, UpBJob>(ctx, P, ls, ST_UPB, "up_ntt_rows_keyip"))) return rc;
+    if ((rc = stage<true, true, DnIJob>(ctx, P, ls, ST_DNI, "dn_intt_rows"))) return rc;
+    if ((rc = stage<true, false, DnIJob>(ctx, P, ls, ST_DNI, "dn_intt_cols"))) return rc;
+    if ((rc = stage<false, true, DnAJob>(ctx, P, ls, ST_DNA, "dn_bconv_ntt_cols"))) return rc;
+    return stage<false, false, DnBJob>(ctx, P, ls, ST_DNB, "dn_ntt_rows_combine");
+}
+
+Lists closed_form_lists(const fheon_ctx *ctx, u32 l)
 {
     const u32 K = ctx->K, beta = ctx->beta_at(l);
-    StageCounts c;
-    c.ic = l;
-    c.upa = beta * (l + K) - l;
-    c.upb = l + K;
-    c.dni = 2 * K;
-    c.dna = 2 * l;
-    c.dnb = 2 * l;
-    return c;
+    Lists ls;
+    ls.n[ST_IC][0] = l;
+    ls.n[ST_UPA][0] = beta * (l + K) - l;
+    ls.n[ST_UPB][0] = l + K;
+    ls.n[ST_DNI][0] = 2 * K;
+    ls.n[ST_DNA][0] = 2 * l;
+    ls.n[ST_DNB][0] = 2 * l;
+    return ls;
 }
 
 } // namespace
@@ -355,8 +408,7 @@ int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g,
     BatchParams P = batch_params(ctx);
     P.desc = nullptr;
     P.one = RotDesc{c0, c1, out, key, ws, g, l, ctx->beta_at(l)};
-    const u32 *none[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    return run_pipeline(ctx, P, counts_for(ctx, l), none);
+    return run_pipeline(ctx, P, closed_form_lists(ctx, l));
 }
 
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out)
@@ -390,8 +442,7 @@ int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out)
 struct RotPlan {
     std::vector<u64> sig;
     DevMem mem;
-    StageCounts n;
-    const u32 *tasks[6];
+    Lists lists;
     const RotDesc *desc;
     u64 last_use = 0;
 };
@@ -468,29 +519,33 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         if (p.sig == sig) { plan = &p; break; }
     if (!plan) {
         std::vector<RotDesc> desc(n);
-        std::vector<u32> t[6];
-        StageCounts cnt;
+        std::vector<u32> t[6][2];
+        const u32 L = ctx->L, K = ctx->K, A = ctx->alpha;
+        // class of a modulus index: 1 when the lazy butterflies apply
+        auto cls = [&](u32 midx) { return ctx->mod[midx] < ntt::LAZY_BOUND ? 1 : 0; };
+        auto qp = [&](u32 x, u32 l) { return x < l ? x : L + (x - l); };
         for (u32 i = 0; i < n; i++) {
             const fheon_ct *in = items[i].in;
-            const u32 l = in->level, K = ctx->K, A = ctx->alpha, beta = ctx->beta_at(l);
+            const u32 l = in->level, beta = ctx->beta_at(l);
             desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ws + ws_off[i] * N,
                               fheon_galois_elt(ctx, items[i].step), l, beta};
             const u32 c = i << 16;
-            for (u32 x = 0; x < l; x++) t[0].push_back(c | x);
+            for (u32 x = 0; x < l; x++) t[ST_IC][cls(x)].push_back(c | x);
             for (u32 j = 0; j < beta; j++)
                 for (u32 x = 0; x < l + K; x++)
-                    if (!(x >= j * A && x < std::min(j * A + A, l))) t[1].push_back(c | (j << 8) | x);
-            for (u32 x = 0; x < l + K; x++) t[2].push_back(c | x);
-            for (u32 x = 0; x < 2 * K; x++) t[3].push_back(c | x);
-            for (u32 x = 0; x < 2 * l; x++) t[4].push_back(c | x);
-            for (u32 x = 0; x < 2 * l; x++) t[5].push_back(c | x);
+                    if (!(x >= j * A && x < std::min(j * A + A, l))) t[ST_UPA][cls(qp(x, l))].push_back(c | (j << 8) | x);
+            for (u32 x = 0; x < l + K; x++) t[ST_UPB][cls(qp(x, l))].push_back(c | x);
+            for (u32 x = 0; x < 2 * K; x++) t[ST_DNI][cls(L + x % K)].push_back(c | x);
+            for (u32 x = 0; x < 2 * l; x++) t[ST_DNA][cls(x % l)].push_back(c | x);
+            for (u32 x = 0; x < 2 * l; x++) t[ST_DNB][cls(x % l)].push_back(c | x);
         }
         size_t bytes = n * sizeof(RotDesc);
-        size_t off[6];
-        for (int s = 0; s < 6; s++) {
-            off[s] = bytes;
-            bytes += t[s].size() * sizeof(u32);
-        }
+        size_t off[6][2];
+        for (int s = 0; s < 6; s++)
+            for (int k = 0; k < 2; k++) {
+                off[s][k] = bytes;
+                bytes += t[s][k].size() * sizeof(u32);
+            }
         if (cache.size() >= 32) {
             auto lru = std::min_element(cache.begin(), cache.end(),
                                         [](const RotPlan &a, const RotPlan &b) { return a.last_use < b.last_use; });
@@ -506,23 +561,23 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         }
         std::vector<unsigned char> host(bytes);
         memcpy(host.data(), desc.data(), n * sizeof(RotDesc));
-        for (int s = 0; s < 6; s++) memcpy(host.data() + off[s], t[s].data(), t[s].size() * sizeof(u32));
+        for (int s = 0; s < 6; s++)
+            for (int k = 0; k < 2; k++)
+                memcpy(host.data() + off[s][k], t[s][k].data(), t[s][k].size() * sizeof(u32));
         FHEON_CUDA(ctx, cudaMemcpyAsync(plan->mem.p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
         FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream)); // `host` is released on return
         char *base = plan->mem.as<char>();
         plan->desc = reinterpret_cast<const RotDesc *>(base);
-        for (int s = 0; s < 6; s++) plan->tasks[s] = reinterpret_cast<const u32 *>(base + off[s]);
-        plan->n.ic = (u32)t[0].size();
-        plan->n.upa = (u32)t[1].size();
-        plan->n.upb = (u32)t[2].size();
-        plan->n.dni = (u32)t[3].size();
-        plan->n.dna = (u32)t[4].size();
-        plan->n.dnb = (u32)t[5].size();
+        for (int s = 0; s < 6; s++)
+            for (int k = 0; k < 2; k++) {
+                plan->lists.t[s][k] = reinterpret_cast<const u32 *>(base + off[s][k]);
+                plan->lists.n[s][k] = (u32)t[s][k].size();
+            }
     }
     plan->last_use = ++tick;
     BatchParams P = batch_params(ctx);
     P.desc = plan->desc;
-    return run_pipeline(ctx, P, plan->n, plan->tasks);
+    return run_pipeline(ctx, P, plan->lists);
 }
 
 } // namespace fheon

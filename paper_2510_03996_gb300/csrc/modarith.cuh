@@ -52,13 +52,13 @@ struct u128acc {
     u64 lo, hi;
 };
 __device__ __forceinline__ void acc_zero(u128acc &a) { a.lo = 0; a.hi = 0; }
+// a += x * y (128-bit), with the carry chained through the PTX carry flag
 __device__ __forceinline__ void acc_mad(u128acc &a, u64 x, u64 y)
 {
-    u64 plo = x * y;
-    u64 phi = __umul64hi(x, y);
-    u64 nlo = a.lo + plo;
-    a.hi += phi + (nlo < plo ? 1ull : 0ull);
-    a.lo = nlo;
+    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
+        "madc.hi.u64 %1, %2, %3, %1;"
+        : "+l"(a.lo), "+l"(a.hi)
+        : "l"(x), "l"(y));
 }
 // REDC of (hi:lo) < q * 2^64: (hi:lo) * 2^-64 mod q, in [0, 2q).
 // lo + m*q vanishes modulo 2^64, so its carry into the high word is (lo != 0).
@@ -116,6 +116,12 @@ __device__ __forceinline__ void gs_butterfly(u64 &X, u64 &Y, u64 w, u64 wsh, u64
     u64 d = X - Y + twoq;
     X = s >= twoq ? s - twoq : s;
     Y = shoup_lazy(d, w, wsh, q);
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (address and size multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, u32 bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // bit reversal of the low `bits` bits

@@ -76,15 +76,22 @@ struct Cfg {
 
 // Defaults for the optional parts of the Job interface.
 struct JobBase {
+    // resident 256-thread CTAs per SM the register budget is sized for: 3 for
+    // plain transforms (<= 85 registers, no spills), 2 for jobs with fused
+    // base conversions or accumulations
+    static constexpr int MIN_BLOCKS = 3;
     // extra shared memory the job needs, in u64 words per tile element; the
     // kernel hands it over with attach()
     static constexpr int EXTRA_WORDS_PER_ELEM = 0;
     __device__ void attach(u64 *) {}
     __device__ int reps() const { return 1; }
-    __device__ void begin(int) {}
+    // start of repetition `rep` on tile `tile` (jobs prefetch their operands here)
+    __device__ void begin(int, u32) {}
     __device__ bool passthrough() const { return false; }
     __device__ u64 load_passthrough(u32) const { return 0; }
     __device__ void finish(int, u32, const ModConst &) {}
+    // whole-tile direct loads of the first pass (default: element by element)
+    static constexpr bool TILE_LOAD = false;
 };
 
 // reduce v < 2^64 to [0, q) with one Shoup product by 1 and a subtraction
@@ -145,7 +152,7 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
 
     const int nrep = job.reps();
     for (int rep = 0; rep < nrep; rep++) {
-        job.begin(rep);
+        job.begin(rep, tile);
         if (job.passthrough()) {
 #pragma unroll
             for (int k = 0; k < R; k++) {
@@ -156,7 +163,12 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
         }
         u64 x[R];
         // ---- load ----
-        if (DIRECT_LOAD) {
+        if constexpr (DIRECT_LOAD && FIRST && Job::TILE_LOAD) {
+            u32 Js[R];
+#pragma unroll
+            for (int v = 0; v < R; v++) Js[v] = gidx(sub, relem(0, v));
+            job.load_tile_first(Js, x);
+        } else if (DIRECT_LOAD) {
 #pragma unroll
             for (int v = 0; v < R; v++) {
                 const u32 J = gidx(sub, relem(0, v));
@@ -269,8 +281,10 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
 // One pass over the tiles of every task.  ROWS: pass B, else pass A.  FIRST:
 // the first pass of the transform (reads the job's input, writes its mid
 // buffer), else the second (reads mid, writes the job's output).
-template <int LOGN, bool INV, bool ROWS, bool FIRST, class Job>
-__global__ void __launch_bounds__(256, 2) pass_kernel(const __grid_constant__ typename Job::Params prm)
+// LAZY: every task's prime is below LAZY_BOUND (the launcher splits task
+// lists by that test); otherwise Harvey butterflies, valid for any prime.
+template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job>
+__global__ void __launch_bounds__(256, Job::MIN_BLOCKS) pass_kernel(const __grid_constant__ typename Job::Params prm)
 {
     using C = Cfg<LOGN>;
     constexpr int TILES = ROWS ? C::ROW_TILES : C::COL_TILES;
@@ -279,8 +293,7 @@ __global__ void __launch_bounds__(256, 2) pass_kernel(const __grid_constant__ ty
     Job job(prm, task);
     if (!job.active()) return;
     const ModConst mc = job.mod();
-    if (mc.q < LAZY_BOUND) pass_body<LOGN, INV, ROWS, FIRST, true>(job, mc, tile);
-    else pass_body<LOGN, INV, ROWS, FIRST, false>(job, mc, tile);
+    pass_body<LOGN, INV, ROWS, FIRST, LAZY>(job, mc, tile);
 }
 
 template <int LOGN, bool INV, bool FIRST>
@@ -293,14 +306,14 @@ struct PassShape {
 };
 
 // Launch one pass of a transform over `ntasks` tasks.
-template <int LOGN, bool INV, bool FIRST, class Job>
+template <int LOGN, bool INV, bool FIRST, bool LAZY, class Job>
 inline cudaError_t launch_pass_fixed(const typename Job::Params &prm, u32 ntasks, cudaStream_t st, const char *name)
 {
     using S = PassShape<LOGN, INV, FIRST>;
     constexpr int smem = S::smem + Job::EXTRA_WORDS_PER_ELEM * Cfg<LOGN>::TILE * 8;
     static_assert(smem <= 200 * 1024, "tile exceeds shared memory");
     if (ntasks == 0) return cudaSuccess;
-    auto kern = pass_kernel<LOGN, INV, S::ROWS, FIRST, Job>;
+    auto kern = pass_kernel<LOGN, INV, S::ROWS, FIRST, LAZY, Job>;
     if (smem > 48 * 1024) {
         static bool attr = false; // one instantiation per kernel: set its opt-in limit once
         if (!attr) {
@@ -314,21 +327,31 @@ inline cudaError_t launch_pass_fixed(const typename Job::Params &prm, u32 ntasks
     return cudaGetLastError();
 }
 
-template <bool INV, bool FIRST, class Job>
-inline cudaError_t launch_pass(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st,
-                               const char *name)
+template <bool INV, bool FIRST, bool LAZY, class Job>
+inline cudaError_t launch_pass_l(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st,
+                                 const char *name)
 {
     switch (logN) {
-    case 10: return launch_pass_fixed<10, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 11: return launch_pass_fixed<11, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 12: return launch_pass_fixed<12, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 13: return launch_pass_fixed<13, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 14: return launch_pass_fixed<14, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 15: return launch_pass_fixed<15, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 16: return launch_pass_fixed<16, INV, FIRST, Job>(prm, ntasks, st, name);
-    case 17: return launch_pass_fixed<17, INV, FIRST, Job>(prm, ntasks, st, name);
+    case 10: return launch_pass_fixed<10, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 11: return launch_pass_fixed<11, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 12: return launch_pass_fixed<12, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 13: return launch_pass_fixed<13, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 14: return launch_pass_fixed<14, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 15: return launch_pass_fixed<15, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 16: return launch_pass_fixed<16, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 17: return launch_pass_fixed<17, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// One pass; `lazy` selects the conditional-subtraction-free butterflies, valid
+// only when every task's prime is below LAZY_BOUND.
+template <bool INV, bool FIRST, class Job>
+inline cudaError_t launch_pass(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st,
+                               const char *name, bool lazy = false)
+{
+    return lazy ? launch_pass_l<INV, FIRST, true, Job>(logN, prm, ntasks, st, name)
+                : launch_pass_l<INV, FIRST, false, Job>(logN, prm, ntasks, st, name);
 }
 
 // Both passes of a transform whose two passes use the same job type.
