@@ -105,6 +105,23 @@ int fheon_ctx_info(const fheon_ctx *ctx, uint32_t *N, uint32_t *L, uint32_t *K, 
 /* The L+K moduli, Q first, into out[L+K]. */
 int fheon_ctx_moduli(const fheon_ctx *ctx, uint64_t *out);
 int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream);
+/* Key-switching schedule (results are identical under every schedule; only
+ * speed differs).  Bits: 1 = plain second NTT pass plus a streaming key
+ * inner-product kernel (else the inner product is summed inside the second
+ * pass); 2 = ModUp base conversion tiled per digit (needs alpha <= 4);
+ * 4 = ModDown base conversion tiled per component (needs K <= 4).  The
+ * default enables every bit the parameters allow.  get returns the current
+ * value; set fails with FHEON_ERR_ARG for bits the parameters do not allow. */
+int fheon_ctx_get_schedule(const fheon_ctx *ctx, int *schedule);
+int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule);
+/* Autotuner: time every schedule the parameters allow on the caller's batch
+ * (one untimed run, then `reps` timed runs of fheon_rotate_batch with CUDA
+ * events on the context's stream), keep the fastest on the context and
+ * return it in *best.  ms_per_batch, when not NULL, receives 8 entries
+ * indexed by schedule (negative for schedules not allowed).  The batch's
+ * outputs are overwritten.  Blocking. */
+int fheon_autotune_schedule(fheon_ctx *ctx, const struct fheon_rot_item *items, uint32_t n, uint32_t reps, int *best,
+                            double *ms_per_batch);
 /* Block until all work enqueued on the context's stream is done. */
 int fheon_sync(fheon_ctx *ctx);
 
@@ -283,6 +300,15 @@ int fheon_conv2d_prepare_plain(fheon_ctx *ctx, uint32_t in_ch, uint32_t k, uint3
 /* Apply: for each tap, Rot_{di*W+dj}(in) * tap plaintext, summed, one
  * rescale, channel sum by Rot_{H*W} (in_ch > 1), bias added. */
 int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
+/* fheon_conv2d_apply through a CUDA graph.  The first call for a given
+ * (input buffer, output buffer, level) runs the layer eagerly, then captures
+ * the same launch sequence on the context's stream (which must be a created
+ * stream, not the legacy default stream) into a graph kept by the layer;
+ * later calls with the same buffers replay it with one cudaGraphLaunch.
+ * Results are identical to fheon_conv2d_apply.  The graph holds the buffer
+ * addresses it was captured with: rotation keys, the layer and both
+ * ciphertexts must stay alive and in place while it is replayed. */
+int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
 /* prepare + apply + destroy in one call. */
 int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k, uint32_t stride,
                  uint32_t pad, uint32_t in_h, uint32_t in_w, const double *w, const double *bias,

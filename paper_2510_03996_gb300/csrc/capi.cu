@@ -265,6 +265,7 @@ static int ctx_create_impl(u32 N, std::vector<u64> mods, u32 nq, u32 np, u32 dnu
     ctx->dnum = dnum;
     ctx->alpha = alpha;
     ctx->beta = beta;
+    ctx->ks_schedule = 1; // fastest measured default; fheon_autotune_schedule picks per batch
     ctx->scale = scale;
     ctx->seed = seed;
     ctx->stream = (cudaStream_t)stream;
@@ -330,6 +331,57 @@ int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream)
 {
     if (!ctx) return FHEON_ERR_ARG;
     ctx->stream = (cudaStream_t)stream;
+    return FHEON_OK;
+}
+
+int fheon_ctx_get_schedule(const fheon_ctx *ctx, int *schedule)
+{
+    if (!ctx || !schedule) return FHEON_ERR_ARG;
+    *schedule = ctx->ks_schedule;
+    return FHEON_OK;
+}
+
+int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule)
+{
+    if (!ctx || schedule < 0 || schedule > 7) return FHEON_ERR_ARG;
+    if ((schedule & 2) && ctx->alpha > 4) return fail(ctx, FHEON_ERR_ARG, "tiled ModUp needs alpha <= 4");
+    if ((schedule & 4) && ctx->K > 4) return fail(ctx, FHEON_ERR_ARG, "tiled ModDown needs K <= 4");
+    ctx->ks_schedule = schedule;
+    return FHEON_OK;
+}
+
+int fheon_autotune_schedule(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, uint32_t reps, int *best,
+                            double *ms_per_batch)
+{
+    if (!ctx || !items || n == 0 || reps == 0 || !best) return FHEON_ERR_ARG;
+    const int old = ctx->ks_schedule;
+    cudaEvent_t e0, e1;
+    FHEON_CUDA(ctx, cudaEventCreate(&e0));
+    FHEON_CUDA(ctx, cudaEventCreate(&e1));
+    int pick = -1;
+    double pick_ms = 0;
+    int rc = FHEON_OK;
+    for (int s = 0; s < 8 && rc == FHEON_OK; s++) {
+        if (ms_per_batch) ms_per_batch[s] = -1.0;
+        if (fheon_ctx_set_schedule(ctx, s) != FHEON_OK) continue;
+        if ((rc = rotate_many(ctx, items, n))) break; // untimed: plans, workspace, caches
+        cudaEventRecord(e0, ctx->stream);
+        for (uint32_t r = 0; r < reps && rc == FHEON_OK; r++) rc = rotate_many(ctx, items, n);
+        cudaEventRecord(e1, ctx->stream);
+        if (rc) break;
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) { rc = cuda_fail(ctx, ce, "autotune"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / reps;
+        if (ms_per_batch) ms_per_batch[s] = per;
+        if (pick < 0 || per < pick_ms) { pick = s; pick_ms = per; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->ks_schedule = (rc == FHEON_OK && pick >= 0) ? pick : old;
+    if (rc) return rc;
+    *best = ctx->ks_schedule;
     return FHEON_OK;
 }
 

@@ -97,6 +97,11 @@ struct fheon_ctx {
     fheon::DevMem ws;                     // key-switching workspace
     size_t ws_limbs = 0;
     u64 enc_counter = 0;
+    // key-switching schedule bits: 1 = plain second pass + streaming
+    // inner-product kernel (else the inner product is fused into the NTT's
+    // second pass); 2 = tiled ModUp conversion (one task per digit and tile
+    // over all target limbs; alpha <= 4); 4 = tiled ModDown conversion (K <= 4)
+    int ks_schedule = 1;
     std::string last_error;
 
     // limbs of the key-switching workspace at level l

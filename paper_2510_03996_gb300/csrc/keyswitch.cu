@@ -56,7 +56,11 @@ struct BatchParams {
     const ulonglong2 *pinv;
 };
 
-enum Stage { ST_IC, ST_UPA, ST_UPB, ST_DNI, ST_DNA, ST_DNB };
+// ST_UPA_T / ST_DNA_T: tiled base conversions, task sub = (digit or component) << 8 | class
+enum Stage { ST_IC, ST_UPA, ST_UPB, ST_DNI, ST_DNA, ST_DNB, ST_UPA_T, ST_DNA_T, ST_COUNT };
+// class of a tiled task: 0 / 1 = targets whose prime takes Harvey / lazy
+// butterflies; CLS_ALL = every target (closed-form tasks, run with Harvey)
+constexpr u32 CLS_ALL = 2;
 
 // (descriptor, sub-index) of a task; closed forms for a single ciphertext
 template <int STAGE>
@@ -76,6 +80,8 @@ __device__ __forceinline__ const RotDesc &task_of(const BatchParams &P, u32 task
         const u32 r = task - j * (nl - A);
         const u32 dj = min(A, l - j * A);
         sub = (j << 8) | (r < j * A ? r : r + dj);
+    } else if (STAGE == ST_UPA_T || STAGE == ST_DNA_T) {
+        sub = (task << 8) | CLS_ALL; // every target of the digit | component (Harvey butterflies)
     } else {
         sub = task;
     }
@@ -143,7 +149,7 @@ struct UpAJob : JobCommon {
     template <bool INV> __device__ u64 load_first(u32) const { return 0; }
     // sources outermost: one constant per source, 16 independent 128-bit sums
     static constexpr bool TILE_LOAD = true;
-    __device__ void load_tile_first(const u32 (&J)[ntt::R], u64 (&x)[ntt::R]) const
+    __device__ void load_tile_first(const u32 (&J)[ntt::R], const int (&)[ntt::R], u64 (&x)[ntt::R]) const
     {
         const u32 N = p.tp.N, nm = p.L + p.K;
         u128acc a[ntt::R];
@@ -279,7 +285,7 @@ struct DnAJob : JobCommon {
     }
     template <bool INV> __device__ u64 load_first(u32) const { return 0; }
     static constexpr bool TILE_LOAD = true;
-    __device__ void load_tile_first(const u32 (&J)[ntt::R], u64 (&x)[ntt::R]) const
+    __device__ void load_tile_first(const u32 (&J)[ntt::R], const int (&)[ntt::R], u64 (&x)[ntt::R]) const
     {
         const u32 N = p.tp.N;
         u128acc a[ntt::R];
@@ -339,6 +345,187 @@ struct DnBJob : JobCommon {
     }
 };
 
+// Tiled base conversions: one task per (ciphertext, digit j [UP] or component
+// b [DN], prime class) and column tile, repeated over every target limb of that
+// class.  The sources (the digit's xt limbs, or the K limbs of pc[b]) are read
+// from global memory once per tile: each thread keeps its own round-0 elements
+// of every source in shared memory (slot s of source i at i*TILE + s) and only
+// ever reads its own slots back, so no barrier is needed.  At most
+// MAX_SRC sources.  Class 2 (closed-form single-ciphertext tasks) takes every
+// target.
+constexpr u32 MAX_SRC = 4;
+
+__device__ __forceinline__ bool class_ok(const BatchParams &P, u32 midx, u32 cls)
+{
+    return cls == CLS_ALL || (u32)(P.tp.mc[midx].q < ntt::LAZY_BOUND) == cls;
+}
+
+template <bool UP>
+struct TiledConvJob : JobCommon {
+    static constexpr int MIN_BLOCKS = 1;
+    static constexpr bool RUNTIME_EXTRA = true;
+    const u64 *src;  // first source limb (sources are consecutive limbs)
+    const u64 *ctab; // UP: modup_conv row of this digit size; DN: moddown_conv
+    u64 *midbase;    // UP: ext of digit j; DN: conv of component b
+    u64 *mid;
+    u64 *xs;
+    u64 cf[MAX_SRC];
+    u32 nsrc, d0, cls, nrep, cur, rep_now, tile_elems;
+    __host__ __device__ static u32 extra_words(const BatchParams &P) { return UP ? P.alpha : P.K; }
+    __device__ TiledConvJob(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<UP ? ST_UPA_T : ST_DNA_T>(P, task, sub);
+        const u32 l = d->level, N = P.tp.N, A = P.alpha, hi = sub >> 8;
+        cls = sub & 0xFF;
+        tile_elems = N < 4096 ? N : 4096;
+        if (UP) {
+            d0 = hi * A;
+            nsrc = min(A, l - d0);
+            src = d->ws + (u64)d0 * N;
+            ctab = P.modup_conv + ((u64)(hi * A + (nsrc - 1)) * A) * (P.L + P.K);
+            midbase = ws_ext(*d, N) + (u64)hi * (l + P.K) * N;
+        } else {
+            d0 = 0;
+            nsrc = P.K;
+            src = ws_pc(*d, P.K, N) + (u64)hi * P.K * N;
+            ctab = P.moddown_conv;
+            midbase = ws_conv(*d, P.K, N) + (u64)hi * l * N;
+        }
+        nrep = 0;
+        for (u32 t = 0; t < ntargets(); t++)
+            if (is_target(t)) nrep++;
+        cur = 0xFFFFFFFFu;
+        midx = 0;
+    }
+    __device__ u32 ntargets() const { return UP ? d->level + p.K : d->level; }
+    __device__ bool is_target(u32 t) const
+    {
+        const u32 l = d->level;
+        if (UP && t >= d0 && t < d0 + nsrc) return false;
+        return class_ok(p, UP ? limb_modidx(t, l, p.L) : t, cls);
+    }
+    __device__ void attach(u64 *s) { xs = s; }
+    __device__ int reps() const { return (int)nrep; }
+    __device__ void begin(int rep, u32)
+    {
+        rep_now = (u32)rep;
+        u32 t = cur + 1;
+        while (!is_target(t)) t++;
+        cur = t;
+        const u32 l = d->level, N = p.tp.N;
+        midx = UP ? limb_modidx(t, l, p.L) : t;
+        mid = midbase + (u64)t * N;
+#pragma unroll
+        for (u32 i = 0; i < MAX_SRC; i++)
+            if (i < nsrc) cf[i] = UP ? __ldg(&ctab[(u64)i * (p.L + p.K) + midx]) : __ldg(&ctab[(u64)i * p.L + t]);
+    }
+    template <bool INV> __device__ u64 load_first(u32) const { return 0; }
+    static constexpr bool TILE_LOAD = true;
+    __device__ void load_tile_first(const u32 (&J)[ntt::R], const int (&S)[ntt::R], u64 (&x)[ntt::R]) const
+    {
+        const u32 N = p.tp.N;
+        u128acc a[ntt::R];
+#pragma unroll
+        for (int v = 0; v < ntt::R; v++) acc_zero(a[v]);
+#pragma unroll
+        for (u32 i = 0; i < MAX_SRC; i++) {
+            if (i >= nsrc) break;
+            u64 *xi = xs + (u64)i * tile_elems;
+            if (rep_now == 0) {
+                const u64 *s = src + (u64)i * N;
+#pragma unroll
+                for (int v = 0; v < ntt::R; v++) {
+                    const u64 y = s[J[v]];
+                    xi[S[v]] = y;
+                    acc_mad(a[v], y, cf[i]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < ntt::R; v++) acc_mad(a[v], xi[S[v]], cf[i]);
+            }
+        }
+        const ModConst &m = p.tp.mc[midx];
+#pragma unroll
+        for (int v = 0; v < ntt::R; v++) x[v] = redc_acc(a[v], m.q, m.qneg_inv);
+    }
+    __device__ u64 load_mid(u32 J) const { return mid[J]; }
+    __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
+    __device__ void store_last(int, u32, u64, const ModConst &) const {}
+};
+
+// UPB, schedule 1: the plain second forward pass of new limb t of digit j
+// (same tasks as UPA), final values back into ext[j][t]
+struct UpB2Job : JobCommon {
+    u64 *mid;
+    __device__ UpB2Job(const BatchParams &P, u32 task) : JobCommon(P)
+    {
+        u32 sub;
+        d = &task_of<ST_UPA>(P, task, sub);
+        const u32 j = sub >> 8, t = sub & 0xFF, l = d->level, N = P.tp.N;
+        midx = limb_modidx(t, l, P.L);
+        mid = ws_ext(*d, N) + ((u64)j * (l + P.K) + t) * N;
+    }
+    template <bool INV> __device__ u64 load_first(u32) const { return 0; }
+    __device__ u64 load_mid(u32 J) const { return mid[J]; }
+    __device__ void store_mid(u32, u64) const {}
+    __device__ void store_last(int, u32 J, u64 v, const ModConst &) const { mid[J] = v; }
+};
+
+// Key inner product, schedule 1: acc_b[t] = sum_j d_j[t] * key[j][b][t] for
+// one limb t per task (UPB's tasks), 4 coefficients per thread, 16-byte
+// streams of the digits and keys, lazy 128-bit sums and one REDC each.
+constexpr int IP_TPB = 256, IP_VEC = 4;
+__global__ void __launch_bounds__(IP_TPB) ks_ip_kernel(const __grid_constant__ BatchParams P, u32 chunks)
+{
+    const u32 task = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    u32 t;
+    const RotDesc &d = task_of<ST_UPB>(P, task, t);
+    const u32 l = d.level, N = P.tp.N, nm = P.L + P.K, nl = l + P.K;
+    const u32 midx = limb_modidx(t, l, P.L);
+    const u32 n = (ch * IP_TPB + threadIdx.x) * IP_VEC;
+    if (n >= N) return;
+    u128acc a0[IP_VEC], a1[IP_VEC];
+#pragma unroll
+    for (int v = 0; v < IP_VEC; v++) { acc_zero(a0[v]); acc_zero(a1[v]); }
+    const u64 *ext = ws_ext(d, N) + (u64)t * N + n;
+    for (u32 j = 0; j < d.beta; j++) {
+        u64 x[IP_VEC];
+        if (t < l && t / P.alpha == j) {
+            const u64 *src = d.c1 + (u64)t * N;
+#pragma unroll
+            for (int v = 0; v < IP_VEC; v++) x[v] = src[automorph_src(n + v, d.g, P.tp.logN)];
+        } else {
+            const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ext + (u64)j * nl * N);
+#pragma unroll
+            for (int v = 0; v < IP_VEC / 2; v++) {
+                const ulonglong2 e = e2[v];
+                x[2 * v] = e.x;
+                x[2 * v + 1] = e.y;
+            }
+        }
+        const ulonglong2 *kb = reinterpret_cast<const ulonglong2 *>(d.key + (((u64)j * 2 + 0) * nm + midx) * N + n);
+        const ulonglong2 *ka = reinterpret_cast<const ulonglong2 *>(d.key + (((u64)j * 2 + 1) * nm + midx) * N + n);
+#pragma unroll
+        for (int v = 0; v < IP_VEC / 2; v++) {
+            const ulonglong2 b = __ldcs(kb + v), a = __ldcs(ka + v);
+            acc_mad(a0[2 * v], x[2 * v], b.x);
+            acc_mad(a0[2 * v + 1], x[2 * v + 1], b.y);
+            acc_mad(a1[2 * v], x[2 * v], a.x);
+            acc_mad(a1[2 * v + 1], x[2 * v + 1], a.y);
+        }
+    }
+    const ModConst &m = P.tp.mc[midx];
+    u64 *o0 = ws_acc(d, P.K, N) + (u64)t * N + n, *o1 = o0 + (u64)nl * N;
+#pragma unroll
+    for (int v = 0; v < IP_VEC / 2; v++) {
+        reinterpret_cast<ulonglong2 *>(o0)[v] =
+            make_ulonglong2(redc_acc(a0[2 * v], m.q, m.qneg_inv), redc_acc(a0[2 * v + 1], m.q, m.qneg_inv));
+        reinterpret_cast<ulonglong2 *>(o1)[v] =
+            make_ulonglong2(redc_acc(a1[2 * v], m.q, m.qneg_inv), redc_acc(a1[2 * v + 1], m.q, m.qneg_inv));
+    }
+}
+
 BatchParams batch_params(const fheon_ctx *ctx)
 {
     BatchParams P{};
@@ -358,8 +545,8 @@ BatchParams batch_params(const fheon_ctx *ctx)
 // whose prime needs Harvey butterflies, [s][1] primes below ntt::LAZY_BOUND.
 // Null lists mean closed-form tasks over BatchParams::one (class 0 only).
 struct Lists {
-    const u32 *t[6][2] = {};
-    u32 n[6][2] = {};
+    const u32 *t[ST_COUNT][2] = {};
+    u32 n[ST_COUNT][2] = {};
 };
 
 template <bool INV, bool FIRST, class Job>
@@ -379,11 +566,32 @@ int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls)
     int rc;
     if ((rc = stage<true, true, IcJob>(ctx, P, ls, ST_IC, "ic_intt_rows"))) return rc;
     if ((rc = stage<true, false, IcJob>(ctx, P, ls, ST_IC, "ic_intt_cols"))) return rc;
-    if ((rc = stage<false, true, UpAJob>(ctx, P, ls, ST_UPA, "up_bconv_ntt_cols"))) return rc;
-    if ((rc = stage<false, false, UpBJob>(ctx, P, ls, ST_UPB, "up_ntt_rows_keyip"))) return rc;
+    if (ctx->ks_schedule & 2) {
+        if ((rc = stage<false, true, TiledConvJob<true>>(ctx, P, ls, ST_UPA_T, "up_bconv_ntt_cols"))) return rc;
+    } else {
+        if ((rc = stage<false, true, UpAJob>(ctx, P, ls, ST_UPA, "up_bconv_ntt_cols"))) return rc;
+    }
+    if ((ctx->ks_schedule & 1) == 0) {
+        if ((rc = stage<false, false, UpBJob>(ctx, P, ls, ST_UPB, "up_ntt_rows_keyip"))) return rc;
+    } else {
+        if ((rc = stage<false, false, UpB2Job>(ctx, P, ls, ST_UPA, "up_ntt_rows"))) return rc;
+        const u32 chunks = (ctx->N + IP_TPB * IP_VEC - 1) / (IP_TPB * IP_VEC);
+        for (int cls = 0; cls < 2; cls++) {
+            if (!ls.n[ST_UPB][cls]) continue;
+            BatchParams Q = P;
+            Q.tasks = ls.t[ST_UPB][cls];
+            ks_ip_kernel<<<ls.n[ST_UPB][cls] * chunks, IP_TPB, 0, ctx->stream>>>(Q, chunks);
+            prof_mark(ctx->stream, "ks_inner");
+            FHEON_CUDA(ctx, cudaGetLastError());
+        }
+    }
     if ((rc = stage<true, true, DnIJob>(ctx, P, ls, ST_DNI, "dn_intt_rows"))) return rc;
     if ((rc = stage<true, false, DnIJob>(ctx, P, ls, ST_DNI, "dn_intt_cols"))) return rc;
-    if ((rc = stage<false, true, DnAJob>(ctx, P, ls, ST_DNA, "dn_bconv_ntt_cols"))) return rc;
+    if (ctx->ks_schedule & 4) {
+        if ((rc = stage<false, true, TiledConvJob<false>>(ctx, P, ls, ST_DNA_T, "dn_bconv_ntt_cols"))) return rc;
+    } else {
+        if ((rc = stage<false, true, DnAJob>(ctx, P, ls, ST_DNA, "dn_bconv_ntt_cols"))) return rc;
+    }
     return stage<false, false, DnBJob>(ctx, P, ls, ST_DNB, "dn_ntt_rows_combine");
 }
 
@@ -397,6 +605,8 @@ Lists closed_form_lists(const fheon_ctx *ctx, u32 l)
     ls.n[ST_DNI][0] = 2 * K;
     ls.n[ST_DNA][0] = 2 * l;
     ls.n[ST_DNB][0] = 2 * l;
+    ls.n[ST_UPA_T][0] = beta;
+    ls.n[ST_DNA_T][0] = 2;
     return ls;
 }
 
@@ -519,7 +729,7 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         if (p.sig == sig) { plan = &p; break; }
     if (!plan) {
         std::vector<RotDesc> desc(n);
-        std::vector<u32> t[6][2];
+        std::vector<u32> t[ST_COUNT][2];
         const u32 L = ctx->L, K = ctx->K, A = ctx->alpha;
         // class of a modulus index: 1 when the lazy butterflies apply
         auto cls = [&](u32 midx) { return ctx->mod[midx] < ntt::LAZY_BOUND ? 1 : 0; };
@@ -538,10 +748,24 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
             for (u32 x = 0; x < 2 * K; x++) t[ST_DNI][cls(L + x % K)].push_back(c | x);
             for (u32 x = 0; x < 2 * l; x++) t[ST_DNA][cls(x % l)].push_back(c | x);
             for (u32 x = 0; x < 2 * l; x++) t[ST_DNB][cls(x % l)].push_back(c | x);
+            // tiled conversions: one task per (digit | component, class) that has a target
+            for (u32 j = 0; j < beta; j++)
+                for (u32 k = 0; k < 2; k++) {
+                    bool any = false;
+                    for (u32 x = 0; x < l + K; x++)
+                        any = any || (!(x >= j * A && x < std::min(j * A + A, l)) && cls(qp(x, l)) == (int)k);
+                    if (any) t[ST_UPA_T][k].push_back(c | (j << 8) | k);
+                }
+            for (u32 b = 0; b < 2; b++)
+                for (u32 k = 0; k < 2; k++) {
+                    bool any = false;
+                    for (u32 x = 0; x < l; x++) any = any || cls(x) == (int)k;
+                    if (any) t[ST_DNA_T][k].push_back(c | (b << 8) | k);
+                }
         }
         size_t bytes = n * sizeof(RotDesc);
-        size_t off[6][2];
-        for (int s = 0; s < 6; s++)
+        size_t off[ST_COUNT][2];
+        for (int s = 0; s < ST_COUNT; s++)
             for (int k = 0; k < 2; k++) {
                 off[s][k] = bytes;
                 bytes += t[s][k].size() * sizeof(u32);
@@ -561,14 +785,14 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         }
         std::vector<unsigned char> host(bytes);
         memcpy(host.data(), desc.data(), n * sizeof(RotDesc));
-        for (int s = 0; s < 6; s++)
+        for (int s = 0; s < ST_COUNT; s++)
             for (int k = 0; k < 2; k++)
                 memcpy(host.data() + off[s][k], t[s][k].data(), t[s][k].size() * sizeof(u32));
         FHEON_CUDA(ctx, cudaMemcpyAsync(plan->mem.p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
         FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream)); // `host` is released on return
         char *base = plan->mem.as<char>();
         plan->desc = reinterpret_cast<const RotDesc *>(base);
-        for (int s = 0; s < 6; s++)
+        for (int s = 0; s < ST_COUNT; s++)
             for (int k = 0; k < 2; k++) {
                 plan->lists.t[s][k] = reinterpret_cast<const u32 *>(base + off[s][k]);
                 plan->lists.n[s][k] = (u32)t[s][k].size();

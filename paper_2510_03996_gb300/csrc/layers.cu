@@ -25,12 +25,24 @@ struct fheon_layer {
     fheon_pt *bias = nullptr;     // at the output level
     std::vector<bool> owned;      // which of taps are owned by the layer
     bool own_bias = false;
+    // working ciphertexts, made on the first application and reused, so that
+    // later applications (and their graph capture) allocate nothing
+    mutable fheon_ct *tmp[3] = {nullptr, nullptr, nullptr};
+    // captured applications, keyed by the buffers the captured launches use
+    struct Graph {
+        const void *in, *out, *ws;
+        u32 level;
+        cudaGraphExec_t exec;
+    };
+    mutable std::vector<Graph> graphs;
     ~fheon_layer()
     {
         for (size_t i = 0; i < taps.size(); i++)
             if (owned[i]) fheon_pt_destroy(taps[i]);
         fheon_pt_destroy(mask);
         if (own_bias) fheon_pt_destroy(bias);
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        for (fheon_ct *c : tmp) fheon_ct_destroy(c);
     }
 };
 
@@ -150,10 +162,12 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in
     if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "conv expects level %u, got %u", ly->level, in->level);
     if (out == in) return fail(ctx, FHEON_ERR_ARG, "conv output must not alias its input");
     const int p = (int)(ly->k - 1) / 2;
-    CtGuard rot, acc;
     int rc;
-    if ((rc = fheon_ct_create(ctx, in->level, in->scale, &rot.p)) || (rc = fheon_ct_create(ctx, in->level, in->scale, &acc.p)))
-        return rc;
+    for (fheon_ct *&c : ly->tmp)
+        if (!c && (rc = fheon_ct_create(ctx, ly->level, in->scale, &c))) return rc;
+    struct Ref {
+        fheon_ct *p;
+    } rot{ly->tmp[0]}, acc{ly->tmp[1]};
     u32 t = 0;
     for (int di = -p; di <= p; di++)
         for (int dj = -p; dj <= p; dj++, t++) {
@@ -175,8 +189,7 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in
         // channel sum: acc + Rot_{HW}(acc) + Rot_{2HW}(acc) + ..., chained on one key
         if ((rc = fheon_drop_level(ctx, acc.p, acc.p->level, rot.p))) return rc;
         const int32_t hw = (int32_t)(ly->H * ly->W);
-        CtGuard sum;
-        if ((rc = fheon_ct_create(ctx, acc.p->level, acc.p->scale, &sum.p))) return rc;
+        Ref sum{ly->tmp[2]};
         if ((rc = fheon_drop_level(ctx, acc.p, acc.p->level, sum.p))) return rc;
         for (u32 c = 1; c < ly->in_ch; c++) {
             if ((rc = fheon_rotate(ctx, rot.p, hw, rot.p))) return rc;
@@ -188,6 +201,40 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in
         if ((rc = fheon_rescale(ctx, acc.p, out))) return rc;
     }
     if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
+    return FHEON_OK;
+}
+
+int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
+    if (!ctx->stream) return fail(ctx, FHEON_ERR_ARG, "graph capture needs a created stream, not the legacy default stream");
+    for (auto &g : ly->graphs)
+        if (g.in == in->c.p && g.out == out->c.p && g.ws == ctx->ws.p && g.level == in->level) {
+            FHEON_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+            // the host-side metadata the captured run set
+            out->level = ly->level - (ly->in_ch > 1 ? 2 : 1);
+            out->scale = in->scale;
+            return FHEON_OK;
+        }
+    // eager run: sizes the output, the temporaries and the workspace
+    int rc = fheon_conv2d_apply(ctx, ly, in, out);
+    if (rc) return rc;
+    if (out->cap < out->level) return fail(ctx, FHEON_ERR_ARG, "output too small");
+    // capture the identical launch sequence (it allocates nothing now)
+    FHEON_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    rc = fheon_conv2d_apply(ctx, ly, in, out);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+    ly->graphs.push_back(fheon_layer::Graph{in->c.p, out->c.p, ctx->ws.p, in->level, exec});
     return FHEON_OK;
 }
 

@@ -83,6 +83,9 @@ struct JobBase {
     // extra shared memory the job needs, in u64 words per tile element; the
     // kernel hands it over with attach()
     static constexpr int EXTRA_WORDS_PER_ELEM = 0;
+    // true when the extra size depends on the launch parameters: the job then
+    // provides  static __host__ __device__ u32 extra_words(const Params &)
+    static constexpr bool RUNTIME_EXTRA = false;
     __device__ void attach(u64 *) {}
     __device__ int reps() const { return 1; }
     // start of repetition `rep` on tile `tile` (jobs prefetch their operands here)
@@ -103,7 +106,7 @@ __device__ __forceinline__ u64 reduce_any(u64 v, const ModConst &m)
 __device__ __forceinline__ u64 reduce_any_lazy(u64 v, const ModConst &m) { return v - __umul64hi(v, m.one_sh) * m.q; }
 
 template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job>
-__device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile)
+__device__ __forceinline__ void pass_body(Job &job, u32 tile)
 {
     using C = Cfg<LOGN>;
     constexpr int LOGM = ROWS ? C::B2 : C::B1;
@@ -124,8 +127,6 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
 
     extern __shared__ u64 sm[];
     job.attach(sm + (ROWS ? SUBS * RSTRIDE : SUBS * M));
-    const ulonglong2 *__restrict__ tw = job.twiddles(INV);
-    const u64 q = mc.q, twoq = mc.twoq;
     const int t = threadIdx.x;
     int sub, g;
     if (ROWS) { sub = t / G; g = t % G; }
@@ -153,6 +154,11 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
     const int nrep = job.reps();
     for (int rep = 0; rep < nrep; rep++) {
         job.begin(rep, tile);
+        // the modulus may change between repetitions (a job may run one
+        // transform per target limb over shared sources)
+        const ModConst mc = job.mod();
+        const ulonglong2 *__restrict__ tw = job.twiddles(INV);
+        const u64 q = mc.q, twoq = mc.twoq;
         if (job.passthrough()) {
 #pragma unroll
             for (int k = 0; k < R; k++) {
@@ -165,9 +171,13 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
         // ---- load ----
         if constexpr (DIRECT_LOAD && FIRST && Job::TILE_LOAD) {
             u32 Js[R];
+            int Ss[R];
 #pragma unroll
-            for (int v = 0; v < R; v++) Js[v] = gidx(sub, relem(0, v));
-            job.load_tile_first(Js, x);
+            for (int v = 0; v < R; v++) {
+                Js[v] = gidx(sub, relem(0, v));
+                Ss[v] = sidx(sub, relem(0, v));
+            }
+            job.load_tile_first(Js, Ss, x);
         } else if (DIRECT_LOAD) {
 #pragma unroll
             for (int v = 0; v < R; v++) {
@@ -274,7 +284,7 @@ __device__ __forceinline__ void pass_body(Job &job, const ModConst &mc, u32 tile
     }
     if (!FIRST) {
 #pragma unroll
-        for (int k = 0; k < R; k++) job.finish(k, store_J(k), mc);
+        for (int k = 0; k < R; k++) job.finish(k, store_J(k), job.mod());
     }
 }
 
@@ -292,8 +302,7 @@ __global__ void __launch_bounds__(256, Job::MIN_BLOCKS) pass_kernel(const __grid
     const u32 tile = blockIdx.x % TILES;
     Job job(prm, task);
     if (!job.active()) return;
-    const ModConst mc = job.mod();
-    pass_body<LOGN, INV, ROWS, FIRST, LAZY>(job, mc, tile);
+    pass_body<LOGN, INV, ROWS, FIRST, LAZY>(job, tile);
 }
 
 template <int LOGN, bool INV, bool FIRST>
@@ -310,16 +319,18 @@ template <int LOGN, bool INV, bool FIRST, bool LAZY, class Job>
 inline cudaError_t launch_pass_fixed(const typename Job::Params &prm, u32 ntasks, cudaStream_t st, const char *name)
 {
     using S = PassShape<LOGN, INV, FIRST>;
-    constexpr int smem = S::smem + Job::EXTRA_WORDS_PER_ELEM * Cfg<LOGN>::TILE * 8;
-    static_assert(smem <= 200 * 1024, "tile exceeds shared memory");
+    int extra = Job::EXTRA_WORDS_PER_ELEM;
+    if constexpr (Job::RUNTIME_EXTRA) extra = (int)Job::extra_words(prm);
+    const int smem = S::smem + extra * Cfg<LOGN>::TILE * 8;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (ntasks == 0) return cudaSuccess;
     auto kern = pass_kernel<LOGN, INV, S::ROWS, FIRST, LAZY, Job>;
     if (smem > 48 * 1024) {
-        static bool attr = false; // one instantiation per kernel: set its opt-in limit once
-        if (!attr) {
+        static int attr = 0; // one instantiation per kernel: raise its opt-in limit when needed
+        if (smem > attr) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
-            attr = true;
+            attr = smem;
         }
     }
     kern<<<dim3(ntasks * S::tiles), dim3(S::threads), smem, st>>>(prm);

@@ -42,6 +42,9 @@ SIGNATURES = {
     "fheon_ctx_info": [c_vp, P(c_u32), P(c_u32), P(c_u32), P(c_u32), P(c_u32)],
     "fheon_ctx_moduli": [c_vp, P(c_u64)],
     "fheon_ctx_set_stream": [c_vp, c_vp],
+    "fheon_ctx_get_schedule": [c_vp, P(c_int)],
+    "fheon_ctx_set_schedule": [c_vp, c_int],
+    "fheon_autotune_schedule": [c_vp, P(fheon_rot_item), c_u32, c_u32, P(c_int), P(c_dbl)],
     "fheon_sync": [c_vp],
     "fheon_keygen": [c_vp, c_vpp, c_vpp],
     "fheon_sk_destroy": [c_vp],
@@ -83,6 +86,7 @@ SIGNATURES = {
     "fheon_conv2d_prepare": [c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_conv2d_prepare_plain": [c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_vp), c_vp, c_vpp],
     "fheon_conv2d_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_conv2d_apply_graph": [c_vp, c_vp, c_vp, c_vp],
     "fheon_conv2d": [c_vp, c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_vp],
     "fheon_layer_destroy": [c_vp],
     "fheon_profile_begin": [c_vp],
@@ -215,6 +219,25 @@ class Context:
 
     def sync(self):
         self._chk(load().fheon_sync(self.h))
+
+    def get_schedule(self):
+        s = c_int()
+        self._chk(load().fheon_ctx_get_schedule(self.h, ctypes.byref(s)))
+        return s.value
+
+    def set_schedule(self, schedule):
+        self._chk(load().fheon_ctx_set_schedule(self.h, int(schedule)))
+
+    def autotune_schedule(self, ins, outs, steps, reps=2):
+        """Time every allowed key-switching schedule on this batch; keep the fastest.
+        Returns (best, {schedule: ms per batch})."""
+        items = (fheon_rot_item * len(ins))()
+        for i, (a, b, s) in enumerate(zip(ins, outs, steps)):
+            items[i].input, items[i].output, items[i].step = a.h, b.h, int(s)
+        best = c_int()
+        ms = (c_dbl * 8)()
+        self._chk(load().fheon_autotune_schedule(self.h, items, len(ins), reps, ctypes.byref(best), ms))
+        return best.value, {s: ms[s] for s in range(8) if ms[s] >= 0}
 
     # keys
     def keygen(self):
@@ -420,6 +443,11 @@ class Context:
     def conv2d_apply(self, layer, ct, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_conv2d_apply(self.h, layer.h, ct.h, out.h))
+        return out
+
+    def conv2d_apply_graph(self, layer, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_conv2d_apply_graph(self.h, layer.h, ct.h, out.h))
         return out
 
     def conv2d(self, ct, in_ch, k, stride, pad, in_h, in_w, w, bias=None, out=None):

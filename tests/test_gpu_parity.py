@@ -93,6 +93,32 @@ def test_rotate_in_place_and_batch(small):
         assert gpu_common.mismatch(small.g.ct_download(o), w) == 0
 
 
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7])
+def test_every_schedule_is_bit_exact(small, schedule):
+    """Key-switching schedules change launches and fusion only, never results:
+    single rotations (closed-form tasks) and batches at mixed levels."""
+    g = small.g
+    old = g.get_schedule()
+    g.set_schedule(schedule)
+    try:
+        ins, outs, steps, wants = [], [], [], []
+        for i, (lv, st) in enumerate([(5, 1), (3, 5), (4, -1), (1, 2047), (2, 100)]):
+            m = synth.small_int_poly(50 + schedule, i, small.N, 1 << 40)
+            c, oc = small.encrypt_both(m, nonce=700 + 10 * schedule + i, level=lv)
+            gg = g.galois_elt(st)
+            w = small.o.rotate(oc, gg, small.okeys[gg])
+            assert gpu_common.mismatch(g.ct_download(g.rotate(c, st)), w) == 0
+            ins.append(c)
+            outs.append(g.ct_create(1))
+            steps.append(st)
+            wants.append(w)
+        g.rotate_batch(ins, outs, steps)
+        for o, w in zip(outs, wants):
+            assert gpu_common.mismatch(g.ct_download(o), w) == 0
+    finally:
+        g.set_schedule(old)
+
+
 def test_missing_key_is_an_error(small):
     m = synth.small_int_poly(5, 0, small.N, 100)
     ct, _ = small.encrypt_both(m, nonce=9)
@@ -186,6 +212,35 @@ def test_conv2d_orchestration_bit_exact(conv13):
     okeys = {r: pr.okeys[pr.g.galois_elt(r)] for r in OF.conv_rotation_steps(W, k)}
     want = OF.special_conv_encrypted(pr.o, oct_, okeys, H, W, k, otaps)
     assert gpu_common.mismatch(g.ct_download(out), want) == 0
+
+
+def test_conv2d_graph_replay_bit_exact(conv13):
+    """The CUDA-graph application of a conv layer equals the eager one, on the
+    first (capturing) call and on replays with new data in the same buffers."""
+    import torch
+    pr = conv13
+    g = pr.g
+    s = torch.cuda.Stream()
+    g.set_stream(s.cuda_stream)
+    try:
+        P = pr.P
+        K = synth.conv_kernel(P["seed"], 7, (1, 5, 5))
+        layer = g.conv2d_prepare(1, 5, 1, 2, 28, 28, K, [0.25], pr.L, P["scale"])
+        ct_in = g.ct_create(pr.L, P["scale"])
+        out_graph = g.ct_create(pr.L)
+        for trial in range(3):
+            m = synth.small_int_poly(60 + trial, 0, pr.N, 1 << 40)
+            ct, _ = pr.encrypt_both(m, nonce=900 + trial)
+            host = g.ct_download(ct)
+            keep = g.ct_upload(ct_in, host)
+            g.sync()
+            eager = g.ct_download(g.conv2d_apply(layer, ct))
+            g.conv2d_apply_graph(layer, ct_in, out_graph)
+            g.sync()
+            assert gpu_common.mismatch(g.ct_download(out_graph), eager) == 0
+            del keep
+    finally:
+        g.set_stream(torch.cuda.current_stream().cuda_stream)
 
 
 def test_conv2d_matches_fp64(conv13):
