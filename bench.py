@@ -216,6 +216,9 @@ def run_gpu(args, rank, world, local_rank):
     def step():
         ctx.rotate_batch(ins, outs, steps)
 
+    # the library's autotuner picks the key-switching schedule for this batch
+    schedule, tune_ms = ctx.autotune_schedule(ins, outs, steps, reps=2)
+
     for _ in range(args.warmup):
         step()
     ctx.sync()
@@ -301,6 +304,8 @@ def run_gpu(args, rank, world, local_rank):
                 "config": {"workload": "batched rotation, N=2^16, 24x50-bit Q + 4x60-bit P, dnum 6, %d ciphertexts "
                                        "at levels U{4..24}, steps U[1,2^15), one key per step" % len(levels),
                            "keys": nkeys, "key_bytes": kbytes, "keygen_s": round(t_keys, 2),
+                           "ks_schedule": schedule,
+                           "autotune_ms_per_batch": {str(k): round(v, 3) for k, v in tune_ms.items()},
                            "mean_level": float(np.mean(levels)), "parallelism": "replicas" if world > 1 else "none",
                            "l2": "inputs larger than L2 (keys %.1f GB)" % (kbytes / 1e9)},
                 "roofline": roof, "cpu_baseline": cpu,
