@@ -42,17 +42,54 @@ def peaks():
 
 
 def algorithmic_costs(N, L, K, alpha, level):
-    """Per-rotation algorithmic work at `level` (see the design notes):
-    bytes that must cross HBM at least once, and 64-bit modular multiplies."""
+    """Algorithmic work of one rotation at `level`, in total and per kernel.
+
+    bytes: what must cross HBM at least once (key + ciphertext in and out).
+    Per kernel: 'mm' = 64-bit modular products (one per NTT butterfly, one
+    per base-conversion multiply-accumulate), or 'bytes' for the streaming
+    key inner product.  Pass A of a size-N transform covers log2(N)/2 stages
+    (floor), pass B the rest."""
     beta = (level + alpha - 1) // alpha
     limb = 8 * N
+    logN = N.bit_length() - 1
+    b1, b2 = logN // 2, logN - logN // 2
+    half = N // 2
     key_bytes = 2 * beta * (level + K) * limb
     ct_bytes = 4 * level * limb  # read (c0, c1), write (c0', c1')
-    logN = N.bit_length() - 1
-    ntt_limbs = level + (beta * (level + K) - level) + 2 * K + 2 * level
-    butterflies = ntt_limbs * (N // 2) * logN
-    return dict(bytes=key_bytes + ct_bytes, key_bytes=key_bytes, ntt_limbs=ntt_limbs, butterflies=butterflies,
-                ip_bytes=key_bytes + (beta * (level + K)) * limb + 2 * (level + K) * limb)
+    new_limbs = beta * (level + K) - level
+    digits = [min(alpha, level - j * alpha) for j in range(beta)]
+    modup_macs = N * sum(d * (level + K - d) for d in digits)
+    k = {
+        "ic_intt_rows": {"mm": level * half * b2},
+        "ic_intt_cols": {"mm": level * half * b1},
+        "up_bconv_ntt_cols": {"mm": new_limbs * half * b1 + modup_macs},
+        "up_ntt_rows": {"mm": new_limbs * half * b2},
+        "up_ntt_rows_keyip": {"mm": new_limbs * half * b2 + 2 * beta * (level + K) * N},
+        "ks_inner": {"bytes": key_bytes + beta * (level + K) * limb + 2 * (level + K) * limb},
+        "dn_intt_rows": {"mm": 2 * K * half * b2},
+        "dn_intt_cols": {"mm": 2 * K * half * b1},
+        "dn_bconv_ntt_cols": {"mm": 2 * level * half * b1 + 2 * level * K * N},
+        "dn_ntt_rows_combine": {"mm": 2 * level * half * b2},
+    }
+    return dict(bytes=key_bytes + ct_bytes, kernels=k)
+
+
+def rooflines(prof, costs, steps, hbm_peak, mm_peak):
+    """Per-kernel achieved rate against its roofline: ALU kernels in T modular
+    products/s against mm_peak, the inner product in GB/s against hbm_peak."""
+    out = {}
+    for name, (n, ms) in prof.items():
+        if ms <= 0:
+            continue
+        work = [c["kernels"].get(name, {}) for c in costs]
+        if any("bytes" in w for w in work):
+            a = sum(w.get("bytes", 0) for w in work) * steps / (ms / 1e3) / 1e9
+            out[name] = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak}
+        elif any("mm" in w for w in work):
+            a = sum(w.get("mm", 0) for w in work) * steps / (ms / 1e3) / 1e12
+            out[name] = {"bound": "alu", "achieved": a, "peak": mm_peak, "unit": "Tmodmul/s", "frac": a / mm_peak}
+        out.get(name, {}).update({"launches": n, "avg_launch_ms": ms / n})
+    return out
 
 
 class ClockSampler:
@@ -269,26 +306,19 @@ def run_gpu(args, rank, world, local_rank):
     # roofline of the dominant kernel, from the live per-launch events
     pk_, src = peaks()
     launches = sum(v[0] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
     costs = [algorithmic_costs(N, ctx.L, ctx.K, ctx.alpha, lv) for lv in levels]
-    dom_name, (dom_n, dom_ms) = dom
-    if dom_name.startswith("ntt"):
-        # one pass = half of the log2(N) butterfly stages over every transformed limb
-        tot_bfly = sum(c["butterflies"] for c in costs) * args.steps / 2
-        achieved = tot_bfly / (dom_ms / 1e3) / 1e12
-        imad_peak = 152 * 64 * float(pk_.get("sm_max_mhz", 2070.0)) * 1e6
-        peak = imad_peak / 10 / 1e12   # 10 IMAD per Shoup product (butterfly)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tbutterfly/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom_name, "launches": dom_n,
-                "avg_launch_ms": dom_ms / dom_n, "peak_source": "derived: 152 SM x 64 IMAD/clk x max clock / 10"}
-    else:
-        tot_bytes = sum(c["ip_bytes"] if dom_name == "ks_inner" else c["bytes"] for c in costs) * args.steps
-        achieved = tot_bytes / (dom_ms / 1e3) / 1e9
-        peak = float(pk_["hbm_gbs"])
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": dom_name, "launches": dom_n, "avg_launch_ms": dom_ms / dom_n,
-                "peak_source": src}
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
+    # no integer peak is measured: 152 SMs x 64 32-bit IMAD per clock x max clock,
+    # 10 IMAD per Shoup modular product
+    mm_peak = 152 * 64 * float(pk_.get("sm_max_mhz", 2070.0)) * 1e6 / 10 / 1e12
+    roofs = rooflines(prof, costs, args.steps, float(pk_["hbm_gbs"]), mm_peak)
+    dom_name = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    roof = dict(roofs[dom_name])
+    roof.update({"kernel": dom_name, "traffic": None,
+                 "peak_source": ("%s copy bandwidth" % src) if roof["bound"] == "hbm" else
+                 "derived: 152 SM x 64 IMAD/clk x %.0f MHz / 10 IMAD per modular product"
+                 % float(pk_.get("sm_max_mhz", 2070.0))})
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / sum(x[1] for x in prof.values()), 4),
+                   "frac": round(roofs.get(k, {}).get("frac", 0.0), 4), "bound": roofs.get(k, {}).get("bound")}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
     cpu = None
