@@ -129,7 +129,7 @@ struct IcJob : JobCommon {
 // UPA: first forward pass of limb t of digit j; the load is the ModUp base
 // conversion  y = sum_i xt[d0+i] * (Dhat_i mod m_t) (Montgomery constants, one REDC)
 struct UpAJob : JobCommon {
-    static constexpr int MIN_BLOCKS = 2;
+    static constexpr int MIN_BLOCKS = 3;
     const u64 *src;
     const u64 *cf;
     u64 *mid;
@@ -149,21 +149,25 @@ struct UpAJob : JobCommon {
     template <bool INV> __device__ u64 load_first(u32) const { return 0; }
     // sources outermost: one constant per source, 16 independent 128-bit sums
     static constexpr bool TILE_LOAD = true;
+    // two halves of 8 elements keep 8 (not 16) 128-bit sums live
     __device__ void load_tile_first(const u32 (&J)[ntt::R], const int (&)[ntt::R], u64 (&x)[ntt::R]) const
     {
         const u32 N = p.tp.N, nm = p.L + p.K;
-        u128acc a[ntt::R];
-#pragma unroll
-        for (int v = 0; v < ntt::R; v++) acc_zero(a[v]);
-        for (u32 i = 0; i < dsz; i++) {
-            const u64 c = __ldg(&cf[(u64)i * nm]);
-            const u64 *s = src + (u64)i * N;
-#pragma unroll
-            for (int v = 0; v < ntt::R; v++) acc_mad(a[v], s[J[v]], c);
-        }
         const ModConst &m = p.tp.mc[midx];
 #pragma unroll
-        for (int v = 0; v < ntt::R; v++) x[v] = redc_acc(a[v], m.q, m.qneg_inv);
+        for (int h = 0; h < 2; h++) {
+            u128acc a[ntt::R / 2];
+#pragma unroll
+            for (int v = 0; v < ntt::R / 2; v++) acc_zero(a[v]);
+            for (u32 i = 0; i < dsz; i++) {
+                const u64 c = __ldg(&cf[(u64)i * nm]);
+                const u64 *s = src + (u64)i * N;
+#pragma unroll
+                for (int v = 0; v < ntt::R / 2; v++) acc_mad(a[v], s[J[h * 8 + v]], c);
+            }
+#pragma unroll
+            for (int v = 0; v < ntt::R / 2; v++) x[h * 8 + v] = redc_acc(a[v], m.q, m.qneg_inv);
+        }
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
     __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
@@ -269,7 +273,7 @@ struct DnIJob : JobCommon {
 // DNA: first forward pass of q_i limb of component b; the load is the ModDown
 // base conversion P -> q_i from pc
 struct DnAJob : JobCommon {
-    static constexpr int MIN_BLOCKS = 2;
+    static constexpr int MIN_BLOCKS = 3;
     const u64 *pc;
     u64 *mid;
     u32 i;
@@ -288,18 +292,21 @@ struct DnAJob : JobCommon {
     __device__ void load_tile_first(const u32 (&J)[ntt::R], const int (&)[ntt::R], u64 (&x)[ntt::R]) const
     {
         const u32 N = p.tp.N;
-        u128acc a[ntt::R];
-#pragma unroll
-        for (int v = 0; v < ntt::R; v++) acc_zero(a[v]);
-        for (u32 k = 0; k < p.K; k++) {
-            const u64 c = __ldg(&p.moddown_conv[(u64)k * p.L + i]);
-            const u64 *s = pc + (u64)k * N;
-#pragma unroll
-            for (int v = 0; v < ntt::R; v++) acc_mad(a[v], s[J[v]], c);
-        }
         const ModConst &m = p.tp.mc[i];
 #pragma unroll
-        for (int v = 0; v < ntt::R; v++) x[v] = redc_acc(a[v], m.q, m.qneg_inv);
+        for (int h = 0; h < 2; h++) {
+            u128acc a[ntt::R / 2];
+#pragma unroll
+            for (int v = 0; v < ntt::R / 2; v++) acc_zero(a[v]);
+            for (u32 k = 0; k < p.K; k++) {
+                const u64 c = __ldg(&p.moddown_conv[(u64)k * p.L + i]);
+                const u64 *s = pc + (u64)k * N;
+#pragma unroll
+                for (int v = 0; v < ntt::R / 2; v++) acc_mad(a[v], s[J[h * 8 + v]], c);
+            }
+#pragma unroll
+            for (int v = 0; v < ntt::R / 2; v++) x[h * 8 + v] = redc_acc(a[v], m.q, m.qneg_inv);
+        }
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
     __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }
@@ -489,6 +496,7 @@ __global__ void __launch_bounds__(IP_TPB) ks_ip_kernel(const __grid_constant__ B
 #pragma unroll
     for (int v = 0; v < IP_VEC; v++) { acc_zero(a0[v]); acc_zero(a1[v]); }
     const u64 *ext = ws_ext(d, N) + (u64)t * N + n;
+#pragma unroll 2
     for (u32 j = 0; j < d.beta; j++) {
         u64 x[IP_VEC];
         if (t < l && t / P.alpha == j) {
