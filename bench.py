@@ -219,6 +219,62 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ CUDA arm
+def per_ciphertext_rate(ctx, ins, outs, steps, stream, reps=2):
+    """The same rotations issued one ciphertext per call (fheon_rotate), the
+    comparison point for the batched call."""
+    import torch
+    for c, o, r in zip(ins, outs, steps):
+        ctx.rotate(c, r, o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for c, o, r in zip(ins, outs, steps):
+            ctx.rotate(c, r, o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": reps * len(ins) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / reps}
+
+
+def conv_layer_timing(F, iters=200):
+    """Packed special conv of the 1x28x28, 5x5, pad 2 layer at N = 2^13 (24 tap
+    rotations + 25 plaintext products + one rescale), eager and as a replayed
+    CUDA graph, in microseconds per layer."""
+    import torch
+    P = synth.params("conv_n13")
+    N = 1 << P["logN"]
+    s = torch.cuda.Stream()
+    ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                    stream=s.cuda_stream)
+    H = W = 28
+    k = 5
+    sk, pk = ctx.keygen()
+    ctx.rotkeygen(sk, ctx.conv2d_rotation_steps(1, k, H, W))
+    x = np.zeros(N // 2)
+    x[:H * W] = synth.image(P["seed"], 0, (1, H, W)).reshape(-1)
+    ct = ctx.encrypt(pk, ctx.encode(x, ctx.L, P["scale"]), nonce=1)
+    layer = ctx.conv2d_prepare(1, k, 1, 2, H, W, synth.conv_kernel(P["seed"], 1, (1, k, k)), [0.0], ctx.L, P["scale"])
+    out = ctx.ct_create(ctx.L)
+    res = {}
+    for name, fn in (("eager", ctx.conv2d_apply), ("graph", ctx.conv2d_apply_graph)):
+        for _ in range(3):
+            fn(layer, ct, out)
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(iters):
+            fn(layer, ct, out)
+        e1.record(s)
+        torch.cuda.synchronize()
+        res[name + "_us_per_layer"] = 1e3 * e0.elapsed_time(e1) / iters
+    ctx.sync()
+    layer.close()
+    del out, ct, sk, pk
+    ctx.close()
+    return res
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -253,8 +309,12 @@ def run_gpu(args, rank, world, local_rank):
     def step():
         ctx.rotate_batch(ins, outs, steps)
 
-    # the library's autotuner picks the key-switching schedule for this batch
-    schedule, tune_ms = ctx.autotune_schedule(ins, outs, steps, reps=2)
+    if args.schedule < 0:
+        # the library's autotuner picks the key-switching schedule for this batch
+        schedule, tune_ms = ctx.autotune_schedule(ins, outs, steps, reps=2)
+    else:
+        ctx.set_schedule(args.schedule)
+        schedule, tune_ms = args.schedule, {}
 
     for _ in range(args.warmup):
         step()
@@ -321,6 +381,11 @@ def run_gpu(args, rank, world, local_rank):
                    "frac": round(roofs.get(k, {}).get("frac", 0.0), 4), "bound": roofs.get(k, {}).get("bound")}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
+    comparisons = None
+    if not args.no_comparisons:
+        comparisons = {"per_ciphertext_path": per_ciphertext_rate(ctx, ins, outs, steps, stream),
+                       "conv_n13_layer": conv_layer_timing(F)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, done, secs, used = OracleRunner(P, steps[0]).rate(levels, budget_s=args.cpu_budget)
@@ -340,7 +405,8 @@ def run_gpu(args, rank, world, local_rank):
                            "l2": "inputs larger than L2 (keys %.1f GB)" % (kbytes / 1e9)},
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels}
+                "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels,
+                "comparisons": comparisons}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -355,6 +421,9 @@ def main():
     ap.add_argument("--n-ct", type=int, default=256)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparisons", action="store_true")
+    ap.add_argument("--schedule", type=int, default=-1,
+                    help="key-switching schedule bits (default: the library's autotuner picks)")
     args = ap.parse_args()
     rank, world, local_rank = dist_env()
     if args.impl == "reference":

@@ -70,6 +70,7 @@ _SIGS = {
     "oracle_moddown": (None, [vp, u64p, U32, u64p]),
     "oracle_keyswitch": (None, [vp, u64p, U32, u64p, u64p]),
     "oracle_rotate": (None, [vp, u64p, U32, U64, u64p, u64p]),
+    "oracle_rotate_hoisted": (None, [vp, u64p, U32, u64p, U32, u64p, u64p]),
     "oracle_encrypt": (None, [vp, u64p, i64p, U64, u64p]),
     "oracle_plain_from_coeffs": (None, [vp, i64p, U32, u64p]),
     "oracle_decrypt": (None, [vp, u64p, u64p, U32, u64p]),

@@ -311,6 +311,19 @@ class Ctx:
         _lib.lib().oracle_rotate(self._h, _p(ct, u64p), level, int(g), _p(k, u64p), _p(out, u64p))
         return out
 
+    def rotate_hoisted(self, ct, gs, ksks):
+        """Rotations of one ciphertext by each Galois element of `gs`, sharing one
+        raising (ModUp + NTT) of c1; ksks[r] is the key of gs[r].  [n][2][level][N]."""
+        ct = _u64(ct)
+        level = ct.shape[1]
+        n = len(gs)
+        g = np.array([int(x) for x in gs], dtype=np.uint64)
+        k = _u64(np.stack([np.asarray(x, dtype=np.uint64) for x in ksks])) if n else np.zeros(1, np.uint64)
+        out = np.zeros((n, 2, level, self.N), dtype=np.uint64)
+        if n:
+            _lib.lib().oracle_rotate_hoisted(self._h, _p(ct, u64p), level, _p(g, u64p), n, _p(k, u64p), _p(out, u64p))
+        return out
+
     def mul_plain(self, ct, pt):
         ct = _u64(ct)
         level = ct.shape[1]

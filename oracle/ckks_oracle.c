@@ -640,6 +640,67 @@ void oracle_rotate(const oracle_ctx *c, const u64 *ct, u32 level, u64 g, const u
     free(sc); free(ks);
 }
 
+/* Hoisted rotations of one ciphertext (Halevi-Shoup hoisting, in the hybrid
+ * key-switching form): the digits of c1 are raised once -- coefficients, ModUp
+ * of every digit, NTT over Q_level u P -- and rotation r applies sigma_{g_r}
+ * to the raised digits in the evaluation domain, then takes the key inner
+ * product and ModDown of oracle_keyswitch: out_r = (sigma(c0) + ks_0, ks_1).
+ * sigma_g(ModUp(x)) lifts sigma_g(x) with the same digit bound, but the fast
+ * base conversion is not odd (BConv(-x) != -BConv(x)), so for g != 1 the
+ * residues differ from those of oracle_rotate.
+ * gs: [n]; ksks: [n][beta_max][2][L+K][N]; out: [n][2][level][N]. */
+void oracle_rotate_hoisted(const oracle_ctx *c, const u64 *ct, u32 level, const u64 *gs, u32 n, const u64 *ksks,
+                           u64 *out)
+{
+    u32 N = c->N, K = c->K, nl = level + K, nall = c->L + c->K;
+    u32 beta = (level + c->alpha - 1) / c->alpha;
+    size_t pl = (size_t)level * N, limbs = (size_t)nl * N, keysz = (size_t)c->beta * 2 * nall * N;
+    u64 *dc = (u64 *)malloc(sizeof(u64) * pl);
+    u64 *up = (u64 *)malloc(sizeof(u64) * limbs);
+    u64 *ext = (u64 *)malloc(sizeof(u64) * beta * limbs);
+    u64 *d = (u64 *)malloc(sizeof(u64) * limbs);
+    u64 *acc = (u64 *)malloc(sizeof(u64) * 2 * limbs);
+    u64 *accc = (u64 *)malloc(sizeof(u64) * limbs);
+    u64 *md = (u64 *)malloc(sizeof(u64) * pl);
+    u64 *ks = (u64 *)malloc(sizeof(u64) * 2 * pl);
+    u64 *sc0 = (u64 *)malloc(sizeof(u64) * pl);
+    /* the raised digits, once */
+    to_coeff(c, ct + pl, level, 0, dc);
+    for (u32 j = 0; j < beta; j++) {
+        oracle_modup(c, dc, level, j, up);
+        to_eval(c, up, level, 1, ext + j * limbs);
+    }
+    for (u32 r = 0; r < n; r++) {
+        const u64 *ksk = ksks + r * keysz;
+        memset(acc, 0, sizeof(u64) * 2 * limbs);
+        for (u32 j = 0; j < beta; j++) {
+            oracle_automorph_eval(c, ext + j * limbs, level, 1, gs[r], d);
+            for (u32 b = 0; b < 2; b++)
+                for (u32 l = 0; l < nl; l++) {
+                    u32 mi = qp_index(c, level, l);
+                    u64 m = c->mod[mi];
+                    const u64 *kk = ksk + (((size_t)j * 2 + b) * nall + mi) * N;
+                    u64 *a = acc + ((size_t)b * nl + l) * N;
+                    for (u32 k = 0; k < N; k++) a[k] = addmod(a[k], mulmod(d[(size_t)l * N + k], kk[k], m), m);
+                }
+        }
+        for (u32 b = 0; b < 2; b++) {
+            to_coeff(c, acc + (size_t)b * limbs, level, 1, accc);
+            oracle_moddown(c, accc, level, md);
+            to_eval(c, md, level, 0, ks + (size_t)b * pl);
+        }
+        oracle_automorph_eval(c, ct, level, 0, gs[r], sc0);
+        u64 *o = out + (size_t)r * 2 * pl;
+        for (u32 i = 0; i < level; i++)
+            for (u32 k = 0; k < N; k++) {
+                size_t x = (size_t)i * N + k;
+                o[x] = addmod(sc0[x], ks[x], c->mod[i]);
+                o[pl + x] = ks[pl + x];
+            }
+    }
+    free(dc); free(up); free(ext); free(d); free(acc); free(accc); free(md); free(ks); free(sc0);
+}
+
 /* pk encryption of an integer message polynomial m (coefficients), at level L:
  * v ternary (DOM_ENC_V), e0, e1 Gaussian (DOM_ENC_E0/E1), all with idx = nonce;
  * ct = (v*pk0 + e0 + m, v*pk1 + e1).  ct: [2][L][N]. */
