@@ -257,11 +257,34 @@ typedef struct fheon_rot_item {
  * sequence per ciphertext).  Bit-identical to n calls of fheon_rotate.
  * Outputs must be distinct from every input of the batch. */
 int fheon_rotate_batch(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
+/* Hoisted rotations, the "fast rotations" the paper's CKKS library provides
+ * (Sec. 2.2; Halevi-Shoup hoisting in the hybrid key-switching form):
+ * outs[i] = Rot_{steps[i]}(in) for i < n, with one INTT + ModUp + NTT of c1
+ * shared by all n.  Rotation i applies sigma_g to the raised digits in the
+ * evaluation domain (a gather inside the key inner product), takes the inner
+ * product with its own key and its own ModDown, and adds sigma_g(c0).  The
+ * results decrypt like fheon_rotate's but differ from them in the low bits
+ * for g != 1 (the fast base conversion is not odd).  Outputs must be distinct
+ * from `in` and from each other (FHEON_ERR_ARG); a missing key gives
+ * FHEON_ERR_NO_KEY before any launch; n = 0 does nothing. */
+int fheon_rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uint32_t n,
+                         fheon_ct *const *outs);
+/* fheon_rotate_batch with hoisting: items that share an input pointer share
+ * one raising (results as fheon_rotate_hoisted per input). */
+int fheon_rotate_batch_hoisted(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
 
 /* out = ct * pt slot-wise (paper Sec. 4.1, kernel-vector products); levels
  * must match (the plaintext may be at a higher level: its lowest limbs are
  * used); scale(out) = scale(ct) * scale(pt). */
 int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheon_ct *out);
+/* out = sum_t cts[t] * pts[t] slot-wise (paper Sec. 4.1: the kernel-vector
+ * products of a layer and their sum, in one pass): n >= 1 ciphertexts at one
+ * level, plaintexts at that level or above, every product at the same scale
+ * (1e-9 relative; else FHEON_ERR_SCALE); out is distinct from every input
+ * (FHEON_ERR_ARG).  Bit-identical to n fheon_mul_plain calls summed with
+ * fheon_add.  scale(out) = the products' scale. */
+int fheon_mac_plain(fheon_ctx *ctx, const fheon_ct *const *cts, const fheon_pt *const *pts, uint32_t n,
+                    fheon_ct *out);
 /* out = a + b; equal levels, scales equal to 1e-9 relative, else
  * FHEON_ERR_LEVEL / FHEON_ERR_SCALE. */
 int fheon_add(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out);

@@ -139,18 +139,29 @@ def conv_rotation_steps(W, k):
     return [di * W + dj for (di, dj) in taps(k) if (di, dj) != (0, 0)]
 
 
-def special_conv_encrypted(ctx, ct, rotkeys, H, W, k, tap_plains, bias_plain=None):
+def special_conv_encrypted(ctx, ct, rotkeys, H, W, k, tap_plains, bias_plain=None, hoisted=False):
     """Encrypted special conv of one channel (C = 1), FHEON Sec. 4.3 generalised to
     k x k: r_t = Rot_{di*W+dj}(ct) with a direct key per tap, products with the
     tap plaintexts (encoded at scale q_{level-1}), summed, one rescale, bias added.
+    hoisted: the tap rotations share one raising of c1 (the fast rotations of
+    Sec. 2.2), as ctx.rotate_hoisted computes them.
 
     rotkeys: dict step -> key-switching key; tap_plains: list of evaluation-form
     plaintexts over Q_level in taps(k) order."""
     N = ctx.N
     acc = None
+    steps = [di * W + dj for di, dj in taps(k) if di * W + dj != 0]
+    if hoisted:
+        hs = ctx.rotate_hoisted(ct, [ckks.galois_elt(r, N) for r in steps], [rotkeys[r] for r in steps])
+        rots = dict(zip(steps, hs))
     for t, (di, dj) in enumerate(taps(k)):
         r = di * W + dj
-        rt = ct if r == 0 else ctx.rotate(ct, ckks.galois_elt(r, N), rotkeys[r])
+        if r == 0:
+            rt = ct
+        elif hoisted:
+            rt = rots[r]
+        else:
+            rt = ctx.rotate(ct, ckks.galois_elt(r, N), rotkeys[r])
         prod = ctx.mul_plain(rt, tap_plains[t])
         acc = prod if acc is None else ctx.add(acc, prod)
     out = ctx.rescale(acc)

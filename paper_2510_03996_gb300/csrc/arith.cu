@@ -3,6 +3,8 @@
 // decryption, and floor rescaling by the last prime (paper Sec. 6, depth).
 // All are HBM-bound streams over u64[2][l][N]; each thread handles two
 // adjacent coefficients with 16-byte accesses.
+#include <algorithm>
+
 #include "jobs.cuh"
 
 namespace fheon {
@@ -25,6 +27,48 @@ __global__ void __launch_bounds__(TPB) mul_plain_kernel(const u64 *__restrict__ 
     const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
     const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(pt + w);
     *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(mulmod_plain(x.x, y.x, m), mulmod_plain(x.y, y.y, m));
+}
+
+// out (+)= sum_t ct_t * pt_t over both components: the products of up to 8
+// terms are summed in 128 bits (8 q^2 < q 2^64 for every q < 2^61) and
+// REDC'd, giving (sum) * 2^-64 mod q; the chunk results are added mod q and
+// multiplied back by 2^64 mod q once.  Exact, so the result equals the
+// sequence of plaintext products and additions it replaces.
+struct MacArgs {
+    const u64 *ct[MAC_MAX]; // u64[2][level][N]
+    const u64 *pt[MAC_MAX]; // u64[>= level][N]
+};
+__global__ void __launch_bounds__(TPB) mac_plain_kernel(const __grid_constant__ MacArgs A, u32 n, u64 *out, bool add_out,
+                                                        u32 level, u32 logN, const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= 2 * per) return;
+    const u64 w = idx % per;
+    const ModConst m = mc[(u32)(w >> logN)];
+    u64 s0 = 0, s1 = 0;
+    for (u32 c = 0; c < n; c += 8) {
+        u128acc a0, a1;
+        acc_zero(a0);
+        acc_zero(a1);
+        const u32 e = min(n, c + 8);
+        for (u32 t = c; t < e; t++) {
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.ct[t] + idx);
+            const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(A.pt[t] + w);
+            acc_mad(a0, x.x, y.x);
+            acc_mad(a1, x.y, y.y);
+        }
+        s0 = addmod(s0, redc_acc(a0, m.q, m.qneg_inv), m.q);
+        s1 = addmod(s1, redc_acc(a1, m.q, m.qneg_inv), m.q);
+    }
+    s0 = shoup(s0, m.r1, m.r1_sh, m.q);
+    s1 = shoup(s1, m.r1, m.r1_sh, m.q);
+    if (add_out) {
+        const ulonglong2 o = *reinterpret_cast<const ulonglong2 *>(out + idx);
+        s0 = addmod(s0, o.x, m.q);
+        s1 = addmod(s1, o.y, m.q);
+    }
+    *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(s0, s1);
 }
 
 // out = a + b over `ncomp` components of `level` limbs
@@ -121,6 +165,23 @@ cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, 
                                                                                 ctx->tab.mc.as<ModConst>());
     prof_mark(ctx->stream, "mul_plain");
     return cudaGetLastError();
+}
+cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const *pts, u32 n, u64 *out, u32 level)
+{
+    for (u32 s = 0; s < n; s += MAC_MAX) {
+        MacArgs A{};
+        const u32 m = std::min<u32>(MAC_MAX, n - s);
+        for (u32 t = 0; t < m; t++) {
+            A.ct[t] = cts[s + t];
+            A.pt[t] = pts[s + t];
+        }
+        mac_plain_kernel<<<blocks2((u64)2 * level * ctx->N), TPB, 0, ctx->stream>>>(A, m, out, s > 0, level, ctx->logN,
+                                                                                     ctx->tab.mc.as<ModConst>());
+        prof_mark(ctx->stream, "mac_plain");
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 level, u32 ncomp)
 {

@@ -635,6 +635,16 @@ int fheon_rotate_batch(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
     if (!ctx || (n && !items)) return FHEON_ERR_ARG;
     return rotate_many(ctx, items, n);
 }
+int fheon_rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uint32_t n, fheon_ct *const *outs)
+{
+    if (!ctx || !in || (n && (!steps || !outs))) return FHEON_ERR_ARG;
+    return rotate_hoisted(ctx, in, steps, n, outs);
+}
+int fheon_rotate_batch_hoisted(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
+{
+    if (!ctx || (n && !items)) return FHEON_ERR_ARG;
+    return rotate_many(ctx, items, n, true);
+}
 
 static bool scales_match(double a, double b) { return std::fabs(a - b) <= 1e-9 * std::fabs(a); }
 
@@ -649,6 +659,29 @@ int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheo
         if (rc) return rc;
     }
     FHEON_CUDA(ctx, k_mul_plain(ctx, ct->c0(), pt->m.as<u64>(), out->c0(), l, 0));
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_mac_plain(fheon_ctx *ctx, const fheon_ct *const *cts, const fheon_pt *const *pts, uint32_t n, fheon_ct *out)
+{
+    if (!ctx || !cts || !pts || !out || n == 0) return FHEON_ERR_ARG;
+    for (u32 t = 0; t < n; t++)
+        if (!cts[t] || !pts[t]) return fail(ctx, FHEON_ERR_ARG, "mac_plain: null operand %u", t);
+    const u32 l = cts[0]->level;
+    const double sc = cts[0]->scale * pts[0]->scale;
+    std::vector<const u64 *> cp(n), pp(n);
+    for (u32 t = 0; t < n; t++) {
+        if (cts[t]->level != l) return fail(ctx, FHEON_ERR_LEVEL, "mac_plain: ciphertext %u at level %u, not %u", t, cts[t]->level, l);
+        if (pts[t]->level < l) return fail(ctx, FHEON_ERR_LEVEL, "mac_plain: plaintext %u below level %u", t, l);
+        if (!scales_match(cts[t]->scale * pts[t]->scale, sc)) return fail(ctx, FHEON_ERR_SCALE, "mac_plain: product %u scale differs", t);
+        if (cts[t] == out) return fail(ctx, FHEON_ERR_ARG, "mac_plain: output aliases input %u", t);
+        cp[t] = cts[t]->c0();
+        pp[t] = pts[t]->m.as<u64>();
+    }
+    int rc = ct_reshape(ctx, out, l);
+    if (rc) return rc;
+    FHEON_CUDA(ctx, k_mac_plain(ctx, cp.data(), pp.data(), n, out->c0(), l));
     out->scale = sc;
     return FHEON_OK;
 }

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -158,10 +159,20 @@ cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 le
 int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out);
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out);
 void drop_plans(fheon_ctx *ctx); // release the cached batch plans of a context
-int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
+// hoist: items with the same input share one raising of c1 (fast rotations).
+// keep (optional) receives a reference to the device plan the launches read,
+// for callers that capture them into a graph.
+using PlanKeep = std::vector<std::shared_ptr<void>>;
+int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool hoist = false, PlanKeep *keep = nullptr);
+int rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uint32_t n, fheon_ct *const *outs,
+                   PlanKeep *keep = nullptr);
 
 // pointwise and rescale (arith.cu)
 cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level, u32 ct_level_out_stride);
+// out = sum_t cts[t] * pts[t] (ciphertexts u64[2][level][N], plaintexts' lowest
+// level limbs); out must not alias an input when n > MAC_MAX
+constexpr u32 MAC_MAX = 32;
+cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const *pts, u32 n, u64 *out, u32 level);
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 nlimb_per_comp, u32 ncomp);
 cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level);
 int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);

@@ -22,10 +22,18 @@
 //   xt[l] | ext[beta][l+K] | acc[2][l+K] | pc[2][K] | conv[2][l].
 // The key is in Montgomery form, so a product with it reduces to the plain
 // residue with one REDC.
+//
+// Hoisted rotations (the "fast rotations" of paper Sec. 2.2; Halevi-Shoup
+// hoisting): rotations of one input share IC, UPA and UPB, run once on c1
+// without the automorphism; each rotation's inner product then reads the
+// shared raised digits through the sigma_g gather (sigma_g maps every aligned
+// block of 2^s evaluation slots onto one aligned block, so the gather stays
+// coalesced), and keeps its own acc | pc | conv.
 #include <algorithm>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "jobs.cuh"
@@ -38,8 +46,12 @@ struct RotDesc {
     const u64 *c0, *c1; // input components, level limbs each
     u64 *out;           // [2][level][N]
     const u64 *key;     // [beta_max][2][L+K][N], Montgomery form
-    u64 *ws;            // workspace (ks_ws_limbs(level) limbs)
-    u64 g;
+    u64 *xt;            // INTT of c1, scaled for ModUp [level]
+    u64 *ext;           // raised digits [beta][level+K] (shared within a hoisted group)
+    u64 *acc;           // acc[2][level+K] | pc[2][K] | conv[2][level]
+    u64 g;              // the rotation's Galois element
+    u64 gi;             // element applied to c1 on its way into xt (g; 1 when hoisted)
+    u64 gx;             // element applied to ext in the inner product (0: none; g when hoisted)
     u32 level, beta;
 };
 
@@ -88,8 +100,8 @@ __device__ __forceinline__ const RotDesc &task_of(const BatchParams &P, u32 task
     return d;
 }
 
-__device__ __forceinline__ u64 *ws_ext(const RotDesc &d, u32 N) { return d.ws + (u64)d.level * N; }
-__device__ __forceinline__ u64 *ws_acc(const RotDesc &d, u32 K, u32 N) { return ws_ext(d, N) + (u64)d.beta * (d.level + K) * N; }
+__device__ __forceinline__ u64 *ws_ext(const RotDesc &d, u32) { return d.ext; }
+__device__ __forceinline__ u64 *ws_acc(const RotDesc &d, u32, u32) { return d.acc; }
 __device__ __forceinline__ u64 *ws_pc(const RotDesc &d, u32 K, u32 N) { return ws_acc(d, K, N) + (u64)2 * (d.level + K) * N; }
 __device__ __forceinline__ u64 *ws_conv(const RotDesc &d, u32 K, u32 N) { return ws_pc(d, K, N) + (u64)2 * K * N; }
 
@@ -117,9 +129,9 @@ struct IcJob : JobCommon {
         t = sub;
         midx = t;
         in = d->c1 + (u64)t * P.tp.N;
-        out = d->ws + (u64)t * P.tp.N;
+        out = d->xt + (u64)t * P.tp.N;
     }
-    template <bool INV> __device__ u64 load_first(u32 J) const { return in[automorph_src(J, d->g, p.tp.logN)]; }
+    template <bool INV> __device__ u64 load_first(u32 J) const { return in[automorph_src(J, d->gi, p.tp.logN)]; }
     __device__ u64 load_mid(u32 J) const { return out[J]; }
     __device__ void store_mid(u32 J, u64 v) const { out[J] = v; }
     __device__ ulonglong2 inv_scale() const { return modup_scale(p.modup_scale, t, d->level, p.alpha); }
@@ -142,7 +154,7 @@ struct UpAJob : JobCommon {
         midx = limb_modidx(t, l, P.L);
         const u32 d0 = j * A;
         dsz = min(A, l - d0);
-        src = d->ws + (u64)d0 * N;
+        src = d->xt + (u64)d0 * N;
         cf = P.modup_conv + ((u64)(j * A + (dsz - 1)) * A) * (P.L + P.K) + midx;
         mid = ws_ext(*d, N) + ((u64)j * (l + P.K) + t) * N;
     }
@@ -389,7 +401,7 @@ struct TiledConvJob : JobCommon {
         if (UP) {
             d0 = hi * A;
             nsrc = min(A, l - d0);
-            src = d->ws + (u64)d0 * N;
+            src = d->xt + (u64)d0 * N;
             ctab = P.modup_conv + ((u64)(hi * A + (nsrc - 1)) * A) * (P.L + P.K);
             midbase = ws_ext(*d, N) + (u64)hi * (l + P.K) * N;
         } else {
@@ -503,6 +515,11 @@ __global__ void __launch_bounds__(IP_TPB) ks_ip_kernel(const __grid_constant__ B
             const u64 *src = d.c1 + (u64)t * N;
 #pragma unroll
             for (int v = 0; v < IP_VEC; v++) x[v] = src[automorph_src(n + v, d.g, P.tp.logN)];
+        } else if (d.gx) {
+            // hoisted: sigma_g of the shared raised digit
+            const u64 *e = ext - n + (u64)j * nl * N;
+#pragma unroll
+            for (int v = 0; v < IP_VEC; v++) x[v] = e[automorph_src(n + v, d.gx, P.tp.logN)];
         } else {
             const ulonglong2 *e2 = reinterpret_cast<const ulonglong2 *>(ext + (u64)j * nl * N);
 #pragma unroll
@@ -568,8 +585,9 @@ int stage(fheon_ctx *ctx, BatchParams P, const Lists &ls, int s, const char *nam
     return FHEON_OK;
 }
 
-// the pipeline's launches over `P`
-int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls)
+// the pipeline's launches over `P`; hoisted groups need the raised digits
+// kept, so they always take the streaming inner product
+int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls, bool hoisted = false)
 {
     int rc;
     if ((rc = stage<true, true, IcJob>(ctx, P, ls, ST_IC, "ic_intt_rows"))) return rc;
@@ -579,7 +597,7 @@ int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls)
     } else {
         if ((rc = stage<false, true, UpAJob>(ctx, P, ls, ST_UPA, "up_bconv_ntt_cols"))) return rc;
     }
-    if ((ctx->ks_schedule & 1) == 0) {
+    if ((ctx->ks_schedule & 1) == 0 && !hoisted) {
         if ((rc = stage<false, false, UpBJob>(ctx, P, ls, ST_UPB, "up_ntt_rows_keyip"))) return rc;
     } else {
         if ((rc = stage<false, false, UpB2Job>(ctx, P, ls, ST_UPA, "up_ntt_rows"))) return rc;
@@ -625,7 +643,9 @@ int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g,
 {
     BatchParams P = batch_params(ctx);
     P.desc = nullptr;
-    P.one = RotDesc{c0, c1, out, key, ws, g, l, ctx->beta_at(l)};
+    const u32 beta = ctx->beta_at(l);
+    u64 *ext = ws + (size_t)l * ctx->N;
+    P.one = RotDesc{c0, c1, out, key, ws, ext, ext + (size_t)beta * (l + ctx->K) * ctx->N, g, g, 0, l, beta};
     return run_pipeline(ctx, P, closed_form_lists(ctx, l));
 }
 
@@ -656,10 +676,12 @@ int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out)
 // ---------------------------------------------------------------- batches
 // A plan holds the descriptors and the six task lists of one batch in device
 // memory; plans are cached by the batch's signature (buffers, levels, keys and
-// workspace), so a batch rotated repeatedly uploads its plan once.
+// workspace), so a batch rotated repeatedly uploads its plan once.  The memory
+// is shared with callers that keep launches referencing it (captured graphs),
+// so evicting a plan from the cache never frees memory a graph still reads.
 struct RotPlan {
     std::vector<u64> sig;
-    DevMem mem;
+    std::shared_ptr<DevMem> mem;
     Lists lists;
     const RotDesc *desc;
     u64 last_use = 0;
@@ -680,22 +702,26 @@ void drop_plans(fheon_ctx *ctx)
     plan_caches().erase(ctx);
 }
 
-int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
+int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool hoist, PlanKeep *keep)
 {
     if (n == 0) return FHEON_OK;
     if (n > 65535) {
+        // (an input whose rotations fall in two chunks is raised once per chunk)
         for (u32 s = 0; s < n; s += 65535) {
-            int rc = rotate_many(ctx, items + s, std::min<u32>(65535, n - s));
+            int rc = rotate_many(ctx, items + s, std::min<u32>(65535, n - s), hoist, keep);
             if (rc) return rc;
         }
         return FHEON_OK;
     }
     const u32 N = ctx->N;
-    // validate, size outputs, lay out the workspace
+    // validate, size outputs, lay out the workspace; lead[i] = the item whose
+    // raised digits item i reads (itself, unless it shares a hoisted input)
     std::vector<u64> sig;
     std::vector<size_t> ws_off(n);
+    std::vector<u32> lead(n);
     size_t ws_total = 0;
     std::vector<const u64 *> keyp(n);
+    std::map<const fheon_ct *, u32> first;
     for (u32 i = 0; i < n; i++) {
         const fheon_ct *in = items[i].in;
         fheon_ct *out = items[i].out;
@@ -705,13 +731,19 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         if (it == ctx->keys.end())
             return fail(ctx, FHEON_ERR_NO_KEY, "no rotation key for step %d (batch item %u)", items[i].step, i);
         keyp[i] = it->second.mem.as<u64>();
+        lead[i] = hoist ? first.emplace(in, i).first->second : i;
+        const u32 l = in->level;
         ws_off[i] = ws_total;
-        ws_total += ctx->ks_ws_limbs(in->level);
+        ws_total += ctx->ks_ws_limbs(l) - (lead[i] == i ? 0 : l + (size_t)ctx->beta_at(l) * (l + ctx->K));
     }
-    for (u32 i = 0; i < n; i++)
-        for (u32 k = 0; k < n; k++)
-            if (items[i].out == items[k].in)
-                return fail(ctx, FHEON_ERR_ARG, "batch output %u aliases input %u", i, k);
+    {
+        std::set<const fheon_ct *> ins, outs;
+        for (u32 i = 0; i < n; i++) ins.insert(items[i].in);
+        for (u32 i = 0; i < n; i++) {
+            if (ins.count(items[i].out)) return fail(ctx, FHEON_ERR_ARG, "batch output %u aliases an input", i);
+            if (!outs.insert(items[i].out).second) return fail(ctx, FHEON_ERR_ARG, "batch output %u repeated", i);
+        }
+    }
     for (u32 i = 0; i < n; i++) {
         int rc = ct_reshape(ctx, items[i].out, items[i].in->level);
         if (rc) return rc;
@@ -720,14 +752,16 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
     int rc = ensure_workspace(ctx, std::max(ws_total, ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L));
     if (rc) return rc;
     u64 *ws = ctx->ws.as<u64>();
-    sig.reserve(4 * n + 2);
+    sig.reserve(5 * n + 3);
     sig.push_back((u64)ws);
     sig.push_back(n);
+    sig.push_back(hoist);
     for (u32 i = 0; i < n; i++) {
         sig.push_back((u64)items[i].in->c.p ^ ((u64)items[i].in->level << 56));
         sig.push_back((u64)items[i].out->c.p);
         sig.push_back((u64)keyp[i]);
         sig.push_back(fheon_galois_elt(ctx, items[i].step));
+        sig.push_back(lead[i]);
     }
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto &cache = plan_cache(ctx);
@@ -745,11 +779,20 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         for (u32 i = 0; i < n; i++) {
             const fheon_ct *in = items[i].in;
             const u32 l = in->level, beta = ctx->beta_at(l);
-            desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ws + ws_off[i] * N,
-                              fheon_galois_elt(ctx, items[i].step), l, beta};
+            const u64 g = fheon_galois_elt(ctx, items[i].step);
+            u64 *w = ws + ws_off[i] * N;
+            if (lead[i] == i) {
+                u64 *ext = w + (size_t)l * N;
+                desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], w, ext,
+                                  ext + (size_t)beta * (l + K) * N, g, hoist ? 1 : g, hoist ? g : 0, l, beta};
+            } else {
+                const RotDesc &ld = desc[lead[i]];
+                desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ld.xt, ld.ext, w, g, 1, g, l, beta};
+            }
             const u32 c = i << 16;
-            for (u32 x = 0; x < l; x++) t[ST_IC][cls(x)].push_back(c | x);
-            for (u32 j = 0; j < beta; j++)
+            const bool raise = lead[i] == i;
+            for (u32 x = 0; x < l && raise; x++) t[ST_IC][cls(x)].push_back(c | x);
+            for (u32 j = 0; j < beta && raise; j++)
                 for (u32 x = 0; x < l + K; x++)
                     if (!(x >= j * A && x < std::min(j * A + A, l))) t[ST_UPA][cls(qp(x, l))].push_back(c | (j << 8) | x);
             for (u32 x = 0; x < l + K; x++) t[ST_UPB][cls(qp(x, l))].push_back(c | x);
@@ -757,7 +800,7 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
             for (u32 x = 0; x < 2 * l; x++) t[ST_DNA][cls(x % l)].push_back(c | x);
             for (u32 x = 0; x < 2 * l; x++) t[ST_DNB][cls(x % l)].push_back(c | x);
             // tiled conversions: one task per (digit | component, class) that has a target
-            for (u32 j = 0; j < beta; j++)
+            for (u32 j = 0; j < beta && raise; j++)
                 for (u32 k = 0; k < 2; k++) {
                     bool any = false;
                     for (u32 x = 0; x < l + K; x++)
@@ -787,7 +830,8 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         cache.emplace_back();
         plan = &cache.back();
         plan->sig = sig;
-        if (!plan->mem.alloc(bytes, ctx->stream)) {
+        plan->mem = std::make_shared<DevMem>();
+        if (!plan->mem->alloc(bytes, ctx->stream)) {
             cache.pop_back();
             return fail(ctx, FHEON_ERR_OOM, "rotation plan (%zu bytes)", bytes);
         }
@@ -796,9 +840,9 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
         for (int s = 0; s < ST_COUNT; s++)
             for (int k = 0; k < 2; k++)
                 memcpy(host.data() + off[s][k], t[s][k].data(), t[s][k].size() * sizeof(u32));
-        FHEON_CUDA(ctx, cudaMemcpyAsync(plan->mem.p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+        FHEON_CUDA(ctx, cudaMemcpyAsync(plan->mem->p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
         FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream)); // `host` is released on return
-        char *base = plan->mem.as<char>();
+        char *base = plan->mem->as<char>();
         plan->desc = reinterpret_cast<const RotDesc *>(base);
         for (int s = 0; s < ST_COUNT; s++)
             for (int k = 0; k < 2; k++) {
@@ -807,9 +851,18 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n)
             }
     }
     plan->last_use = ++tick;
+    if (keep) keep->push_back(plan->mem);
     BatchParams P = batch_params(ctx);
     P.desc = plan->desc;
-    return run_pipeline(ctx, P, plan->lists);
+    return run_pipeline(ctx, P, plan->lists, hoist);
+}
+
+int rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uint32_t n, fheon_ct *const *outs,
+                   PlanKeep *keep)
+{
+    std::vector<fheon_rot_item> items(n);
+    for (u32 i = 0; i < n; i++) items[i] = fheon_rot_item{in, outs[i], steps[i]};
+    return rotate_many(ctx, items.data(), n, true, keep);
 }
 
 } // namespace fheon

@@ -6,8 +6,10 @@
 // slot c*H*W + h*W + w.  For tap (di, dj) in [-p, p]^2, p = (k-1)/2, the
 // rotated ciphertext Rot_{di*W+dj}(x) holds x[h+di][w+dj] at slot (h, w); the
 // tap plaintext is the kernel value times the boundary mask of Alg. 2/3
-// (1 where (h+di, w+dj) lies inside the input), per channel block.  The k^2
-// products are summed and rescaled once (the taps are encoded at scale
+// (1 where (h+di, w+dj) lies inside the input), per channel block.  The
+// k^2 - 1 tap rotations of the input are hoisted (one raising of c1 shared by
+// all of them: the "fast rotations" of Sec. 2.2); the k^2 products are formed
+// and summed in one pass and rescaled once (the taps are encoded at scale
 // q_{level-1}, so the scale returns to the input's).  With C > 1 input
 // channels the channel blocks are summed by C-1 chained rotations by H*W
 // (the single W^2 key of Sec. 4.3) and masked to block 0, which costs one
@@ -25,16 +27,21 @@ struct fheon_layer {
     fheon_pt *bias = nullptr;     // at the output level
     std::vector<bool> owned;      // which of taps are owned by the layer
     bool own_bias = false;
-    // working ciphertexts, made on the first application and reused, so that
-    // later applications (and their graph capture) allocate nothing
+    // working ciphertexts (the k^2 - 1 tap rotations, then accumulators), made
+    // on the first application and reused, so that later applications (and
+    // their graph capture) allocate nothing
+    mutable std::vector<fheon_ct *> rot;
     mutable fheon_ct *tmp[3] = {nullptr, nullptr, nullptr};
-    // captured applications, keyed by the buffers the captured launches use
+    // captured applications, keyed by the buffers the captured launches use;
+    // `keep` holds the device rotation plans those launches read
     struct Graph {
         const void *in, *out, *ws;
         u32 level;
         cudaGraphExec_t exec;
+        fheon::PlanKeep keep;
     };
     mutable std::vector<Graph> graphs;
+    mutable fheon::PlanKeep *collect = nullptr; // set while an application is captured
     ~fheon_layer()
     {
         for (size_t i = 0; i < taps.size(); i++)
@@ -43,6 +50,7 @@ struct fheon_layer {
         if (own_bias) fheon_pt_destroy(bias);
         for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
         for (fheon_ct *c : tmp) fheon_ct_destroy(c);
+        for (fheon_ct *c : rot) fheon_ct_destroy(c);
     }
 };
 
@@ -162,28 +170,35 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in
     if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "conv expects level %u, got %u", ly->level, in->level);
     if (out == in) return fail(ctx, FHEON_ERR_ARG, "conv output must not alias its input");
     const int p = (int)(ly->k - 1) / 2;
+    const u32 kk = ly->k * ly->k;
     int rc;
     for (fheon_ct *&c : ly->tmp)
+        if (!c && (rc = fheon_ct_create(ctx, ly->level, in->scale, &c))) return rc;
+    if (ly->rot.size() != kk - 1) ly->rot.resize(kk - 1, nullptr);
+    for (fheon_ct *&c : ly->rot)
         if (!c && (rc = fheon_ct_create(ctx, ly->level, in->scale, &c))) return rc;
     struct Ref {
         fheon_ct *p;
     } rot{ly->tmp[0]}, acc{ly->tmp[1]};
-    u32 t = 0;
+    // the tap rotations, hoisted; the identity tap reads the input itself
+    std::vector<int32_t> steps;
+    std::vector<fheon_ct *> routs;
+    std::vector<const fheon_ct *> srcs;
     for (int di = -p; di <= p; di++)
-        for (int dj = -p; dj <= p; dj++, t++) {
+        for (int dj = -p; dj <= p; dj++) {
             const int r = di * (int)ly->W + dj;
-            const fheon_ct *src = in;
-            if (r != 0) {
-                if ((rc = fheon_rotate(ctx, in, r, rot.p))) return rc;
-                src = rot.p;
+            if (r == 0) {
+                srcs.push_back(in);
+                continue;
             }
-            if (t == 0) {
-                if ((rc = fheon_mul_plain(ctx, src, ly->taps[t], acc.p))) return rc;
-            } else {
-                if ((rc = fheon_mul_plain(ctx, src, ly->taps[t], rot.p))) return rc;
-                if ((rc = fheon_add(ctx, acc.p, rot.p, acc.p))) return rc;
-            }
+            if (routs.size() == ly->rot.size()) return fail(ctx, FHEON_ERR_ARG, "conv: tap rotations exceed k^2 - 1");
+            steps.push_back(r);
+            routs.push_back(ly->rot[routs.size()]);
+            srcs.push_back(routs.back());
         }
+    if ((rc = rotate_hoisted(ctx, in, steps.data(), (u32)steps.size(), routs.data(), ly->collect))) return rc;
+    // the k^2 products with the tap plaintexts, summed in one pass
+    if ((rc = fheon_mac_plain(ctx, srcs.data(), ly->taps.data(), kk, acc.p))) return rc;
     if (ly->in_ch > 1) {
         if ((rc = fheon_rescale(ctx, acc.p, acc.p))) return rc;
         // channel sum: acc + Rot_{HW}(acc) + Rot_{2HW}(acc) + ..., chained on one key
@@ -220,9 +235,13 @@ int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_
     int rc = fheon_conv2d_apply(ctx, ly, in, out);
     if (rc) return rc;
     if (out->cap < out->level) return fail(ctx, FHEON_ERR_ARG, "output too small");
-    // capture the identical launch sequence (it allocates nothing now)
+    // capture the identical launch sequence (it allocates nothing now; the
+    // rotation plans it reads are held by the graph entry)
+    PlanKeep keep;
     FHEON_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ly->collect = &keep;
     rc = fheon_conv2d_apply(ctx, ly, in, out);
+    ly->collect = nullptr;
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
     if (rc) {
@@ -234,7 +253,7 @@ int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
-    ly->graphs.push_back(fheon_layer::Graph{in->c.p, out->c.p, ctx->ws.p, in->level, exec});
+    ly->graphs.push_back(fheon_layer::Graph{in->c.p, out->c.p, ctx->ws.p, in->level, exec, std::move(keep)});
     return FHEON_OK;
 }
 

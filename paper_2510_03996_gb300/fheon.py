@@ -76,8 +76,11 @@ SIGNATURES = {
     "fheon_rotate": [c_vp, c_vp, c_i32, c_vp],
     "fheon_rotate_galois": [c_vp, c_vp, c_u64, c_vp],
     "fheon_rotate_batch": [c_vp, P(fheon_rot_item), c_u32],
+    "fheon_rotate_hoisted": [c_vp, c_vp, P(c_i32), c_u32, P(c_vp)],
+    "fheon_rotate_batch_hoisted": [c_vp, P(fheon_rot_item), c_u32],
     "fheon_rotate_noalloc": [c_vp, c_vp, c_i32, c_vp],
     "fheon_mul_plain": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_mac_plain": [c_vp, P(c_vp), P(c_vp), c_u32, c_vp],
     "fheon_add": [c_vp, c_vp, c_vp, c_vp],
     "fheon_add_plain": [c_vp, c_vp, c_vp, c_vp],
     "fheon_rescale": [c_vp, c_vp, c_vp],
@@ -377,15 +380,39 @@ class Context:
         self._chk(load().fheon_rotate_noalloc(self.h, ct.h, int(step), out.h))
         return out
 
-    def rotate_batch(self, ins, outs, steps):
+    @staticmethod
+    def _items(ins, outs, steps):
         items = (fheon_rot_item * len(ins))()
         for i, (a, b, s) in enumerate(zip(ins, outs, steps)):
             items[i].input, items[i].output, items[i].step = a.h, b.h, int(s)
-        self._chk(load().fheon_rotate_batch(self.h, items, len(ins)))
+        return items
+
+    def rotate_batch(self, ins, outs, steps):
+        self._chk(load().fheon_rotate_batch(self.h, self._items(ins, outs, steps), len(ins)))
+
+    def rotate_hoisted(self, ct, steps, outs=None):
+        """Rotations of one ciphertext by every step, sharing one raising of c1."""
+        outs = outs or [self.ct_create(1) for _ in steps]
+        st = (c_i32 * len(steps))(*[int(x) for x in steps])
+        hs = (c_vp * len(steps))(*[o.h for o in outs])
+        self._chk(load().fheon_rotate_hoisted(self.h, ct.h, st, len(steps), hs))
+        return outs
+
+    def rotate_batch_hoisted(self, ins, outs, steps):
+        self._chk(load().fheon_rotate_batch_hoisted(self.h, self._items(ins, outs, steps), len(ins)))
 
     def mul_plain(self, ct, pt, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_mul_plain(self.h, ct.h, pt.h, out.h))
+        return out
+
+    def mac_plain(self, cts, pts, out=None):
+        """out = sum_t cts[t] * pts[t] in one pass."""
+        out = out or self.ct_create(1)
+        n = len(cts)
+        ch = (c_vp * n)(*[c.h for c in cts])
+        ph = (c_vp * n)(*[p.h for p in pts])
+        self._chk(load().fheon_mac_plain(self.h, ch, ph, n, out.h))
         return out
 
     def add(self, a, b, out=None):

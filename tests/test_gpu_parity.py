@@ -196,7 +196,8 @@ def _tap_plains_int(pr, k, level, seed):
 
 def test_conv2d_orchestration_bit_exact(conv13):
     """Library special conv with caller-made integer tap plaintexts vs the
-    oracle's Sec. 4.3 orchestration on the same plaintexts (N = 2^13, 28x28, 5x5)."""
+    oracle's Sec. 4.3 orchestration on the same plaintexts (N = 2^13, 28x28, 5x5),
+    tap rotations hoisted on both sides."""
     pr = conv13
     g = pr.g
     H = W = 28
@@ -210,7 +211,7 @@ def test_conv2d_orchestration_bit_exact(conv13):
     layer = g.conv2d_prepare_plain(1, k, H, W, level, taps)
     out = g.conv2d_apply(layer, ct)
     okeys = {r: pr.okeys[pr.g.galois_elt(r)] for r in OF.conv_rotation_steps(W, k)}
-    want = OF.special_conv_encrypted(pr.o, oct_, okeys, H, W, k, otaps)
+    want = OF.special_conv_encrypted(pr.o, oct_, okeys, H, W, k, otaps, hoisted=True)
     assert gpu_common.mismatch(g.ct_download(out), want) == 0
 
 

@@ -70,8 +70,10 @@ def test_rotation_step_count():
         assert len(steps) == k * k - 1 and len(set(steps)) == k * k - 1 and 0 not in steps
 
 
-def test_encrypted_special_conv_matches_fp64():
-    """Config-1 geometry (1x28x28, 5x5, pad 2) at N = 2^11 to keep the oracle fast."""
+@pytest.mark.parametrize("hoisted", [False, True])
+def test_encrypted_special_conv_matches_fp64(hoisted):
+    """Config-1 geometry (1x28x28, 5x5, pad 2) at N = 2^11 to keep the oracle fast;
+    tap rotations one by one or hoisted."""
     P = synth.params("conv_n13")
     N = 1 << 11
     mods = ckks.gen_primes(N, P["qbits"] + P["pbits"])
@@ -87,7 +89,7 @@ def test_encrypted_special_conv_matches_fp64():
     ct = ctx.encrypt(pk, ckks.encode(x, N, P["scale"]), 0)
     keys = {r: ctx.rotkey(se, ckks.galois_elt(r, N)) for r in fheon.conv_rotation_steps(W, k)}
     taps = fheon.encode_tap_plains(ctx, H, W, K[0], k, 3)
-    out = fheon.special_conv_encrypted(ctx, ct, keys, H, W, k, taps)
+    out = fheon.special_conv_encrypted(ctx, ct, keys, H, W, k, taps, hoisted=hoisted)
     assert out.shape[1] == 2
     y = ctx.decode_ct(se, out, P["scale"]).real
     ref = fheon.conv2d_fp64(X, K, pad=2).reshape(-1)
