@@ -41,6 +41,13 @@ def peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes the kernel moved per launch over its minimum traffic (sources read
+# once, results written once), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the 16-ciphertext case of this workload; a full
+# launch's traffic is this ratio times its own minimum bytes.
+TRAFFIC_OVER_MIN = {"up_bconv_ntt_cols": 902.27 / 895.5, "ks_inner": 2599.55 / 2619.87}
+
+
 def algorithmic_costs(N, L, K, alpha, level):
     """Algorithmic work of one rotation at `level`, in total and per kernel.
 
@@ -62,10 +69,12 @@ def algorithmic_costs(N, L, K, alpha, level):
     k = {
         "ic_intt_rows": {"mm": level * half * b2},
         "ic_intt_cols": {"mm": level * half * b1},
-        "up_bconv_ntt_cols": {"mm": new_limbs * half * b1 + modup_macs},
+        # both prime-class launches read every source limb
+        "up_bconv_ntt_cols": {"mm": new_limbs * half * b1 + modup_macs, "min_bytes": (2 * level + new_limbs) * limb},
         "up_ntt_rows": {"mm": new_limbs * half * b2},
         "up_ntt_rows_keyip": {"mm": new_limbs * half * b2 + 2 * beta * (level + K) * N},
-        "ks_inner": {"bytes": key_bytes + beta * (level + K) * limb + 2 * (level + K) * limb},
+        "ks_inner": {"bytes": key_bytes + beta * (level + K) * limb + 2 * (level + K) * limb,
+                     "min_bytes": key_bytes + beta * (level + K) * limb + 2 * (level + K) * limb},
         "dn_intt_rows": {"mm": 2 * K * half * b2},
         "dn_intt_cols": {"mm": 2 * K * half * b1},
         "dn_bconv_ntt_cols": {"mm": 2 * level * half * b1 + 2 * level * K * N},
@@ -262,10 +271,12 @@ def conv_layer_timing(F, iters=200):
             fn(layer, ct, out)
         ctx.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("conv_" + name)
         e0.record(s)
         for _ in range(iters):
             fn(layer, ct, out)
         e1.record(s)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         res[name + "_us_per_layer"] = 1e3 * e0.elapsed_time(e1) / iters
     ctx.sync()
@@ -373,7 +384,13 @@ def run_gpu(args, rank, world, local_rank):
     roofs = rooflines(prof, costs, args.steps, float(pk_["hbm_gbs"]), mm_peak)
     dom_name = max(prof.items(), key=lambda kv: kv[1][1])[0]
     roof = dict(roofs[dom_name])
-    roof.update({"kernel": dom_name, "traffic": None,
+    traffic = None
+    if TRAFFIC_OVER_MIN.get(dom_name):
+        mb = sum(c["kernels"][dom_name].get("min_bytes", 0) for c in costs)
+        traffic = TRAFFIC_OVER_MIN[dom_name] * mb / (prof[dom_name][0] / args.steps)
+    roof.update({"kernel": dom_name, "traffic": traffic,
+                 "traffic_source": "ncu DRAM bytes of the 16-ciphertext case over the kernel's minimum bytes, "
+                                   "times this workload's minimum bytes per launch" if traffic else None,
                  "peak_source": ("%s copy bandwidth" % src) if roof["bound"] == "hbm" else
                  "derived: 152 SM x 64 IMAD/clk x %.0f MHz / 10 IMAD per modular product"
                  % float(pk_.get("sm_max_mhz", 2070.0))})
