@@ -155,14 +155,21 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def barrier_max(value, world):
+def barrier_max(value, world, device="cuda"):
+    """The maximum of `value` over the ranks (the slowest replica's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(units_per_rank, seconds, world, device="cuda"):
+    """Whole-job rate of `world` independent replicas that each processed
+    `units_per_rank` units: all units over the slowest replica's time."""
+    return world * units_per_rank / barrier_max(seconds, world, device)
 
 
 # ------------------------------------------------------------------ oracle timing
@@ -345,9 +352,9 @@ def run_gpu(args, rank, world, local_rank):
         prof = ctx.profile_end()
         torch.cuda.synchronize()
     ms_total = ev0.elapsed_time(ev1)
+    value = replica_rate(len(levels) * args.steps, ms_total / 1e3, world)
     ms_total = barrier_max(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * len(levels) * args.steps / (ms_total / 1e3)
 
     # e2e: host buffers (pinned) -> upload -> batched rotation -> download, every step
     host_in = [torch.empty((2, lv, N), dtype=torch.int64, pin_memory=True) for lv in levels]
@@ -371,8 +378,7 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = barrier_max(time.perf_counter() - t0, world)
-    e2e_value = world * len(levels) * e2e_steps / e2e_s
+    e2e_value = replica_rate(len(levels) * e2e_steps, time.perf_counter() - t0, world)
 
     # roofline of the dominant kernel, from the live per-launch events
     pk_, src = peaks()
