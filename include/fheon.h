@@ -109,20 +109,26 @@ int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream);
  * speed differs).  Bits: 1 = plain second NTT pass plus a streaming key
  * inner-product kernel (else the inner product is summed inside the second
  * pass); 2 = ModUp base conversion tiled per digit (needs alpha <= 4);
- * 4 = ModDown base conversion tiled per component (needs K <= 4).  The
- * default enables every bit the parameters allow.  get returns the current
- * value; set fails with FHEON_ERR_ARG for bits the parameters do not allow. */
+ * 4 = ModDown base conversion tiled per component (needs K <= 4); 8 = the
+ * streaming inner product fed by TMA bulk copies into shared memory (needs
+ * bit 1).  The default is 9.  get returns the current value; set fails with
+ * FHEON_ERR_ARG for values outside [0, FHEON_NUM_SCHEDULES) and bits the
+ * parameters do not allow. */
+#define FHEON_NUM_SCHEDULES 16
 int fheon_ctx_get_schedule(const fheon_ctx *ctx, int *schedule);
 int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule);
 /* Autotuner: time every schedule the parameters allow on the caller's batch
  * (one untimed run, then `reps` timed runs of fheon_rotate_batch with CUDA
  * events on the context's stream), keep the fastest on the context and
- * return it in *best.  ms_per_batch, when not NULL, receives 8 entries
- * indexed by schedule (negative for schedules not allowed).  The batch's
- * outputs are overwritten.  Blocking. */
+ * return it in *best.  ms_per_batch, when not NULL, receives
+ * FHEON_NUM_SCHEDULES entries indexed by schedule (negative for schedules not
+ * allowed).  The batch's outputs are overwritten.  Blocking. */
 int fheon_autotune_schedule(fheon_ctx *ctx, const struct fheon_rot_item *items, uint32_t n, uint32_t reps, int *best,
                             double *ms_per_batch);
-/* Block until all work enqueued on the context's stream is done. */
+/* Block until all work enqueued on the context's stream is done.  Returns
+ * FHEON_ERR_TIMEOUT (once) when a kernel's bounded wait on its own copies ran
+ * out since the last check; the outputs of that work are then not valid.  The
+ * download calls check the same way. */
 int fheon_sync(fheon_ctx *ctx);
 
 /* ------------------------------------------------------------------ */

@@ -233,6 +233,8 @@ static int build_tables(fheon_ctx *ctx)
     u64 cdt[41];
     h_cdt_table(3.2, 20, cdt);
     if ((rc = upload(ctx, ctx->tab.cdt, cdt, sizeof cdt))) return rc;
+    const int no_error = 0;
+    if ((rc = upload(ctx, ctx->err, &no_error, sizeof no_error))) return rc;
     return build_fft_tables(ctx);
 }
 
@@ -265,7 +267,7 @@ static int ctx_create_impl(u32 N, std::vector<u64> mods, u32 nq, u32 np, u32 dnu
     ctx->dnum = dnum;
     ctx->alpha = alpha;
     ctx->beta = beta;
-    ctx->ks_schedule = 1; // fastest measured default; fheon_autotune_schedule picks per batch
+    ctx->ks_schedule = 9; // fastest measured default; fheon_autotune_schedule picks per batch
     ctx->scale = scale;
     ctx->seed = seed;
     ctx->stream = (cudaStream_t)stream;
@@ -343,7 +345,8 @@ int fheon_ctx_get_schedule(const fheon_ctx *ctx, int *schedule)
 
 int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule)
 {
-    if (!ctx || schedule < 0 || schedule > 7) return FHEON_ERR_ARG;
+    if (!ctx || schedule < 0 || schedule >= FHEON_NUM_SCHEDULES) return FHEON_ERR_ARG;
+    if ((schedule & 8) && !(schedule & 1)) return fail(ctx, FHEON_ERR_ARG, "bulk-copy inner product needs bit 1");
     if ((schedule & 2) && ctx->alpha > 4) return fail(ctx, FHEON_ERR_ARG, "tiled ModUp needs alpha <= 4");
     if ((schedule & 4) && ctx->K > 4) return fail(ctx, FHEON_ERR_ARG, "tiled ModDown needs K <= 4");
     ctx->ks_schedule = schedule;
@@ -361,7 +364,7 @@ int fheon_autotune_schedule(fheon_ctx *ctx, const fheon_rot_item *items, uint32_
     int pick = -1;
     double pick_ms = 0;
     int rc = FHEON_OK;
-    for (int s = 0; s < 8 && rc == FHEON_OK; s++) {
+    for (int s = 0; s < FHEON_NUM_SCHEDULES && rc == FHEON_OK; s++) {
         if (ms_per_batch) ms_per_batch[s] = -1.0;
         if (fheon_ctx_set_schedule(ctx, s) != FHEON_OK) continue;
         if ((rc = rotate_many(ctx, items, n))) break; // untimed: plans, workspace, caches
@@ -385,11 +388,23 @@ int fheon_autotune_schedule(fheon_ctx *ctx, const fheon_rot_item *items, uint32_
     return FHEON_OK;
 }
 
+// after a synchronisation: the error a kernel recorded since the last check
+// (a bounded device wait that gave up), cleared once reported
+static int device_error(fheon_ctx *ctx)
+{
+    int e = 0;
+    FHEON_CUDA(ctx, cudaMemcpy(&e, ctx->err.p, sizeof e, cudaMemcpyDeviceToHost));
+    if (e == 0) return FHEON_OK;
+    const int zero = 0;
+    FHEON_CUDA(ctx, cudaMemcpy(ctx->err.p, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    return fail(ctx, e, "a kernel's bounded wait ran out; its outputs are not valid");
+}
+
 int fheon_sync(fheon_ctx *ctx)
 {
     if (!ctx) return FHEON_ERR_ARG;
     FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return FHEON_OK;
+    return device_error(ctx);
 }
 
 // ------------------------------------------------------------------ keys
@@ -415,7 +430,7 @@ static int download(fheon_ctx *ctx, const void *dev, void *host, size_t bytes)
 {
     FHEON_CUDA(ctx, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return FHEON_OK;
+    return device_error(ctx);
 }
 
 int fheon_sk_download(fheon_ctx *ctx, const fheon_sk *sk, uint64_t *host)

@@ -96,13 +96,15 @@ struct fheon_ctx {
     fheon::Tables tab;
     std::map<u64, fheon::RotKey> keys;    // by Galois element
     fheon::DevMem ws;                     // key-switching workspace
+    fheon::DevMem err;                    // int: error a kernel recorded (FHEON_ERR_TIMEOUT), 0 = none
     size_t ws_limbs = 0;
     u64 enc_counter = 0;
     // key-switching schedule bits: 1 = plain second pass + streaming
     // inner-product kernel (else the inner product is fused into the NTT's
     // second pass); 2 = tiled ModUp conversion (one task per digit and tile
-    // over all target limbs; alpha <= 4); 4 = tiled ModDown conversion (K <= 4)
-    int ks_schedule = 1;
+    // over all target limbs; alpha <= 4); 4 = tiled ModDown conversion (K <= 4);
+    // 8 = the streaming inner product fed by TMA bulk copies (with bit 1)
+    int ks_schedule = 9;
     std::string last_error;
 
     // limbs of the key-switching workspace at level l

@@ -30,6 +30,7 @@
 // block of 2^s evaluation slots onto one aligned block, so the gather stays
 // coalesced), and keeps its own acc | pc | conv.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -37,6 +38,7 @@
 #include <vector>
 
 #include "jobs.cuh"
+#include "tma.cuh"
 
 namespace fheon {
 
@@ -66,6 +68,7 @@ struct BatchParams {
     const ulonglong2 *moddown_scale;
     const u64 *moddown_conv;
     const ulonglong2 *pinv;
+    int *err; // device error word: FHEON_ERR_TIMEOUT after a wait gave up
 };
 
 // ST_UPA_T / ST_DNA_T: tiled base conversions, task sub = (digit or component) << 8 | class
@@ -551,6 +554,100 @@ __global__ void __launch_bounds__(IP_TPB) ks_ip_kernel(const __grid_constant__ B
     }
 }
 
+// Key inner product, schedule bit 8: per (task, tile of IPB_TE coefficients),
+// the operands of each digit -- the digit limb (or the sigma_g block of c1 for
+// the digit holding t, or of the shared raised digit when hoisted), and the
+// two key limbs -- arrive in shared memory by TMA bulk copies, two digits in
+// flight; each thread then sums 8 coefficients with lazy 128-bit products and
+// one REDC.  sigma_g maps an aligned block of slots onto one aligned block, so
+// a gathered operand is one contiguous copy indexed in shared memory.
+constexpr int IPB_TPB = 256, IPB_TE = 2048, IPB_PER = IPB_TE / IPB_TPB, IPB_STAGES = 2;
+constexpr u32 IPB_SMEM = IPB_STAGES * 3 * IPB_TE * 8 + 64;
+
+__global__ void __launch_bounds__(IPB_TPB, 2) ks_ip_bulk_kernel(const __grid_constant__ BatchParams P, u32 tiles)
+{
+    extern __shared__ __align__(128) u64 sm[];
+    u64 *bar = sm + IPB_STAGES * 3 * IPB_TE;
+    const u32 task = blockIdx.x / tiles, tile = blockIdx.x % tiles;
+    u32 t;
+    const RotDesc &d = task_of<ST_UPB>(P, task, t);
+    const u32 l = d.level, N = P.tp.N, nm = P.L + P.K, nl = l + P.K, logN = P.tp.logN;
+    const u32 te = N < (u32)IPB_TE ? N : (u32)IPB_TE, off = tile * te;
+    const u32 midx = limb_modidx(t, l, P.L);
+    // digit j's x operand: its limb, gather element (0: none) and source block
+    auto x_of = [&](u32 j, u64 &g, u32 &base) -> const u64 * {
+        const bool pass = t < l && t / P.alpha == j;
+        g = pass ? d.g : d.gx;
+        base = g ? (automorph_src(off, g, logN) & ~(te - 1)) : off;
+        return pass ? d.c1 + (u64)t * N : ws_ext(d, N) + ((u64)j * nl + t) * N;
+    };
+    auto issue = [&](u32 j) {
+        u64 *st = sm + (j % IPB_STAGES) * 3 * IPB_TE;
+        u64 g;
+        u32 base;
+        const u64 *x = x_of(j, g, base);
+        u64 *b = &bar[j % IPB_STAGES];
+        tma::mbar_arrive_expect_tx(b, 3 * te * 8);
+        tma::bulk_g2s(st, x + base, te * 8, b);
+        tma::bulk_g2s(st + IPB_TE, d.key + (((u64)j * 2 + 0) * nm + midx) * N + off, te * 8, b);
+        tma::bulk_g2s(st + 2 * IPB_TE, d.key + (((u64)j * 2 + 1) * nm + midx) * N + off, te * 8, b);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < IPB_STAGES; s++) tma::mbar_init(&bar[s], 1);
+        tma::fence_mbar_init();
+        for (u32 j = 0; j < d.beta && j < (u32)IPB_STAGES; j++) issue(j);
+    }
+    __syncthreads();
+    u128acc a0[IPB_PER], a1[IPB_PER];
+#pragma unroll
+    for (int k = 0; k < IPB_PER; k++) { acc_zero(a0[k]); acc_zero(a1[k]); }
+    u32 done = 0; // digits whose copies have landed
+    bool ok = true;
+    for (u32 j = 0; j < d.beta; j++) {
+        u64 *b = &bar[j % IPB_STAGES];
+        // the whole CTA agrees on a timeout, so no thread waits at a barrier alone
+        ok = __syncthreads_and(tma::mbar_wait(b, (j / IPB_STAGES) & 1));
+        if (!ok) break;
+        done = j + 1;
+        const u64 *st = sm + (j % IPB_STAGES) * 3 * IPB_TE;
+        u64 g;
+        u32 base;
+        x_of(j, g, base);
+#pragma unroll
+        for (int k = 0; k < IPB_PER; k++) {
+            const u32 nl_ = k * IPB_TPB + threadIdx.x;
+            if (nl_ >= te) break;
+            const u32 xi = g ? automorph_src(off + nl_, g, logN) - base : nl_;
+            const u64 x = st[xi];
+            acc_mad(a0[k], x, st[IPB_TE + nl_]);
+            acc_mad(a1[k], x, st[2 * IPB_TE + nl_]);
+        }
+        __syncthreads(); // stage free
+        if (threadIdx.x == 0 && j + IPB_STAGES < d.beta) {
+            tma::fence_proxy_async();
+            issue(j + IPB_STAGES);
+        }
+    }
+    if (!ok) {
+        // record the timeout, let the copies already issued land, leave the outputs
+        if (threadIdx.x == 0) {
+            atomicExch(P.err, FHEON_ERR_TIMEOUT);
+            for (u32 j = done; j < d.beta && j < done + IPB_STAGES; j++)
+                tma::mbar_wait(&bar[j % IPB_STAGES], (j / IPB_STAGES) & 1);
+        }
+        return;
+    }
+    const ModConst &m = P.tp.mc[midx];
+    u64 *o0 = ws_acc(d, P.K, N) + (u64)t * N + off, *o1 = o0 + (u64)nl * N;
+#pragma unroll
+    for (int k = 0; k < IPB_PER; k++) {
+        const u32 nl_ = k * IPB_TPB + threadIdx.x;
+        if (nl_ >= te) break;
+        o0[nl_] = redc_acc(a0[k], m.q, m.qneg_inv);
+        o1[nl_] = redc_acc(a1[k], m.q, m.qneg_inv);
+    }
+}
+
 BatchParams batch_params(const fheon_ctx *ctx)
 {
     BatchParams P{};
@@ -563,6 +660,7 @@ BatchParams batch_params(const fheon_ctx *ctx)
     P.moddown_scale = ctx->tab.moddown_scale.as<ulonglong2>();
     P.moddown_conv = ctx->tab.moddown_conv.as<u64>();
     P.pinv = ctx->tab.pinv.as<ulonglong2>();
+    P.err = ctx->err.as<int>();
     return P;
 }
 
@@ -601,12 +699,27 @@ int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls, bool hoi
         if ((rc = stage<false, false, UpBJob>(ctx, P, ls, ST_UPB, "up_ntt_rows_keyip"))) return rc;
     } else {
         if ((rc = stage<false, false, UpB2Job>(ctx, P, ls, ST_UPA, "up_ntt_rows"))) return rc;
-        const u32 chunks = (ctx->N + IP_TPB * IP_VEC - 1) / (IP_TPB * IP_VEC);
+        const bool bulk = (ctx->ks_schedule & 8) != 0;
+        const u32 chunks = bulk ? (ctx->N + IPB_TE - 1) / IPB_TE : (ctx->N + IP_TPB * IP_VEC - 1) / (IP_TPB * IP_VEC);
+        if (bulk) {
+            // the kernel's shared-memory opt-in, once per device
+            static std::atomic<u64> opted{0};
+            int dev = 0;
+            FHEON_CUDA(ctx, cudaGetDevice(&dev));
+            if (!(opted.load() >> (dev & 63) & 1)) {
+                FHEON_CUDA(ctx, cudaFuncSetAttribute(ks_ip_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)IPB_SMEM));
+                opted.fetch_or(1ull << (dev & 63));
+            }
+        }
         for (int cls = 0; cls < 2; cls++) {
             if (!ls.n[ST_UPB][cls]) continue;
             BatchParams Q = P;
             Q.tasks = ls.t[ST_UPB][cls];
-            ks_ip_kernel<<<ls.n[ST_UPB][cls] * chunks, IP_TPB, 0, ctx->stream>>>(Q, chunks);
+            if (bulk)
+                ks_ip_bulk_kernel<<<ls.n[ST_UPB][cls] * chunks, IPB_TPB, IPB_SMEM, ctx->stream>>>(Q, chunks);
+            else
+                ks_ip_kernel<<<ls.n[ST_UPB][cls] * chunks, IP_TPB, 0, ctx->stream>>>(Q, chunks);
             prof_mark(ctx->stream, "ks_inner");
             FHEON_CUDA(ctx, cudaGetLastError());
         }

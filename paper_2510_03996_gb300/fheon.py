@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libfheon.so")
 
 FHEON_OK = 0
+NUM_SCHEDULES = 16  # FHEON_NUM_SCHEDULES
 ERRORS = {-1: "FHEON_ERR_ARG", -2: "FHEON_ERR_OOM", -3: "FHEON_ERR_NO_KEY", -4: "FHEON_ERR_LEVEL",
           -5: "FHEON_ERR_SCALE", -6: "FHEON_ERR_TIMEOUT", -7: "FHEON_ERR_CUDA", -8: "FHEON_ERR_UNIMPLEMENTED"}
 
@@ -238,9 +239,9 @@ class Context:
         for i, (a, b, s) in enumerate(zip(ins, outs, steps)):
             items[i].input, items[i].output, items[i].step = a.h, b.h, int(s)
         best = c_int()
-        ms = (c_dbl * 8)()
+        ms = (c_dbl * NUM_SCHEDULES)()
         self._chk(load().fheon_autotune_schedule(self.h, items, len(ins), reps, ctypes.byref(best), ms))
-        return best.value, {s: ms[s] for s in range(8) if ms[s] >= 0}
+        return best.value, {s: ms[s] for s in range(NUM_SCHEDULES) if ms[s] >= 0}
 
     # keys
     def keygen(self):

@@ -93,7 +93,20 @@ def test_rotate_in_place_and_batch(small):
         assert gpu_common.mismatch(small.g.ct_download(o), w) == 0
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7])
+def test_schedule_range(small):
+    g = small.g
+    old = g.get_schedule()
+    try:
+        for bad in (-1, 8, 10, 16):
+            with pytest.raises(small.F.FheonError) as e:
+                g.set_schedule(bad)
+            assert e.value.code == -1
+        assert g.get_schedule() == old
+    finally:
+        g.set_schedule(old)
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15])
 def test_every_schedule_is_bit_exact(small, schedule):
     """Key-switching schedules change launches and fusion only, never results:
     single rotations (closed-form tasks) and batches at mixed levels."""
