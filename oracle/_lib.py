@@ -71,6 +71,10 @@ _SIGS = {
     "oracle_keyswitch": (None, [vp, u64p, U32, u64p, u64p]),
     "oracle_rotate": (None, [vp, u64p, U32, U64, u64p, u64p]),
     "oracle_rotate_hoisted": (None, [vp, u64p, U32, u64p, U32, u64p, u64p]),
+    "oracle_mul_relin": (None, [vp, u64p, u64p, U32, u64p, u64p]),
+    "oracle_mul_int": (None, [vp, u64p, U32, ctypes.c_int64, u64p]),
+    "oracle_add_int": (None, [vp, u64p, U32, ctypes.c_int64, u64p]),
+    "oracle_const_factor": (ctypes.c_int64, [vp, U32, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "oracle_encrypt": (None, [vp, u64p, i64p, U64, u64p]),
     "oracle_plain_from_coeffs": (None, [vp, i64p, U32, u64p]),
     "oracle_decrypt": (None, [vp, u64p, u64p, U32, u64p]),

@@ -311,6 +311,40 @@ class Ctx:
         _lib.lib().oracle_rotate(self._h, _p(ct, u64p), level, int(g), _p(k, u64p), _p(out, u64p))
         return out
 
+    def relinkey(self, s_eval):
+        """Relinearisation key: key-switching key from s^2 to s, tag 0."""
+        s_eval = _u64(s_eval)
+        sq = np.stack([np.array([(int(x) * int(x)) % m for x in s_eval[i]], dtype=np.uint64)
+                       for i, m in enumerate(self.mod)])
+        return self.keygen_ksk(s_eval, sq, tag=0)
+
+    def mul_relin(self, a, b, rlk):
+        a, b, k = _u64(a), _u64(b), _u64(rlk)
+        level = a.shape[1]
+        assert b.shape[1] == level
+        out = np.zeros_like(a)
+        _lib.lib().oracle_mul_relin(self._h, _p(a, u64p), _p(b, u64p), level, _p(k, u64p), _p(out, u64p))
+        return out
+
+    def mul_int(self, ct, v):
+        ct = _u64(ct)
+        out = np.zeros_like(ct)
+        _lib.lib().oracle_mul_int(self._h, _p(ct, u64p), ct.shape[1], int(v), _p(out, u64p))
+        return out
+
+    def add_int(self, ct, v):
+        ct = _u64(ct)
+        out = np.zeros_like(ct)
+        _lib.lib().oracle_add_int(self._h, _p(ct, u64p), ct.shape[1], int(v), _p(out, u64p))
+        return out
+
+    def const_factor(self, level, c, target, scale):
+        return int(_lib.lib().oracle_const_factor(self._h, level, float(c), float(target), float(scale)))
+
+    def mul_const_rescale(self, ct, c, target, scale):
+        """c * ct rescaled once, landing on scale `target` (ct has scale `scale`)."""
+        return self.rescale(self.mul_int(ct, self.const_factor(ct.shape[1], c, target, scale)))
+
     def rotate_hoisted(self, ct, gs, ksks):
         """Rotations of one ciphertext by each Galois element of `gs`, sharing one
         raising (ModUp + NTT) of c1; ksks[r] is the key of gs[r].  [n][2][level][N]."""

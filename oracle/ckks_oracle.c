@@ -701,6 +701,73 @@ void oracle_rotate_hoisted(const oracle_ctx *c, const u64 *ct, u32 level, const 
     free(dc); free(up); free(ext); free(d); free(acc); free(accc); free(md); free(ks); free(sc0);
 }
 
+/* Ciphertext product (the multiplications of paper Alg. 4's Chebyshev
+ * evaluation, OpenFHE's EvalMult): the tensor (d0, d1, d2) = (a0 b0,
+ * a0 b1 + a1 b0, a1 b1) decrypts under (1, s, s^2); d2 is key-switched from
+ * s^2 to s with the relinearisation key (oracle_keygen_ksk with s_from = s^2,
+ * tag 0): out = (d0 + ks_0, d1 + ks_1).  No rescale.  out: [2][level][N]. */
+void oracle_mul_relin(const oracle_ctx *c, const u64 *a, const u64 *b, u32 level, const u64 *rlk, u64 *out)
+{
+    size_t pl = (size_t)level * c->N;
+    u64 *d = (u64 *)malloc(sizeof(u64) * 3 * pl);
+    u64 *ks = (u64 *)malloc(sizeof(u64) * 2 * pl);
+    for (u32 i = 0; i < level; i++) {
+        u64 q = c->mod[i];
+        for (u32 k = 0; k < c->N; k++) {
+            size_t o = (size_t)i * c->N + k;
+            d[o] = mulmod(a[o], b[o], q);
+            d[pl + o] = addmod(mulmod(a[o], b[pl + o], q), mulmod(a[pl + o], b[o], q), q);
+            d[2 * pl + o] = mulmod(a[pl + o], b[pl + o], q);
+        }
+    }
+    oracle_keyswitch(c, d + 2 * pl, level, rlk, ks);
+    for (u32 i = 0; i < level; i++)
+        for (u32 k = 0; k < c->N; k++) {
+            size_t o = (size_t)i * c->N + k;
+            out[o] = addmod(d[o], ks[o], c->mod[i]);
+            out[pl + o] = addmod(d[pl + o], ks[pl + o], c->mod[i]);
+        }
+    free(d); free(ks);
+}
+
+/* out = v * ct for an integer v: every residue times (v mod q_i). */
+void oracle_mul_int(const oracle_ctx *c, const u64 *ct, u32 level, i64 v, u64 *out)
+{
+    size_t pl = (size_t)level * c->N;
+    for (u32 b = 0; b < 2; b++)
+        for (u32 i = 0; i < level; i++) {
+            u64 q = c->mod[i], vm = from_signed(v, q);
+            for (u32 k = 0; k < c->N; k++) {
+                size_t o = b * pl + (size_t)i * c->N + k;
+                out[o] = mulmod(ct[o], vm, q);
+            }
+        }
+}
+
+/* c0 += v: the constant polynomial v takes the value v at every evaluation
+ * point, so every residue of c0 limb i gains (v mod q_i); c1 is copied. */
+void oracle_add_int(const oracle_ctx *c, const u64 *ct, u32 level, i64 v, u64 *out)
+{
+    size_t pl = (size_t)level * c->N;
+    for (u32 i = 0; i < level; i++) {
+        u64 q = c->mod[i], vm = from_signed(v, q);
+        for (u32 k = 0; k < c->N; k++) {
+            size_t o = (size_t)i * c->N + k;
+            out[o] = addmod(ct[o], vm, q);
+            out[pl + o] = ct[pl + o];
+        }
+    }
+}
+
+/* The integer K a constant c is encoded as before a rescale by q_{level-1}, so
+ * that the rescaled product has scale `target`: a ciphertext of scale `scale`
+ * times K, divided by q_{level-1}, has scale scale * K / q ~= c * target.
+ * K = llround(((c * target) * q_{level-1}) / scale) in binary64. */
+i64 oracle_const_factor(const oracle_ctx *c, u32 level, double cval, double target, double scale)
+{
+    return llround(((cval * target) * (double)c->mod[level - 1]) / scale);
+}
+
 /* pk encryption of an integer message polynomial m (coefficients), at level L:
  * v ternary (DOM_ENC_V), e0, e1 Gaussian (DOM_ENC_E0/E1), all with idx = nonce;
  * ct = (v*pk0 + e0 + m, v*pk1 + e1).  ct: [2][L][N]. */
