@@ -154,6 +154,10 @@ int fheon_pk_download(fheon_ctx *ctx, const fheon_pk *pk, uint64_t *host);
  * (stream (seed, 5, g<<32 | j<<16)).  Keys stay resident on the device;
  * existing keys are kept. */
 int fheon_rotkeygen(fheon_ctx *ctx, const fheon_sk *sk, const int32_t *steps, uint32_t n);
+/* Relinearisation key: the key-switching key from s^2 to s (b_j = -a_j s +
+ * e_j + P [limb in digit j] s^2, streams tagged 0), kept on the context; the
+ * ciphertext product needs it.  A second call does nothing. */
+int fheon_relinkeygen(fheon_ctx *ctx, const fheon_sk *sk);
 /* Same, by Galois element (odd g < 2N; 2N-1 is complex conjugation). */
 int fheon_galois_keygen(fheon_ctx *ctx, const fheon_sk *sk, const uint64_t *galois, uint32_t n);
 /* Drop the key of Galois element g (paper Sec. 5: keys loaded and cleared
@@ -291,6 +295,28 @@ int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheo
  * fheon_add.  scale(out) = the products' scale. */
 int fheon_mac_plain(fheon_ctx *ctx, const fheon_ct *const *cts, const fheon_pt *const *pts, uint32_t n,
                     fheon_ct *out);
+/* Ciphertext product with relinearisation (the multiplications of the
+ * Chebyshev ReLU, paper Alg. 4 and Sec. 4.6): the tensor (a0 b0, a0 b1 + a1 b0,
+ * a1 b1) decrypts under (1, s, s^2); its last part is key-switched from s^2 to
+ * s on the rotation's key-switching kernels with the relinearisation key.
+ * Equal levels (else FHEON_ERR_LEVEL); FHEON_ERR_NO_KEY without
+ * fheon_relinkeygen.  scale(out) = scale(a) * scale(b); no rescale.  out may
+ * be a or b. */
+int fheon_mul_relin(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out);
+/* out = v * ct for an integer v (exact; scale unchanged). */
+int fheon_mul_int(fheon_ctx *ctx, const fheon_ct *ct, int64_t v, fheon_ct *out);
+/* out = ct + v, v an integer constant polynomial (every slot gains v / scale). */
+int fheon_add_int(fheon_ctx *ctx, const fheon_ct *ct, int64_t v, fheon_ct *out);
+/* out = ct + c in every slot: fheon_add_int with v = llround(c * scale(ct))
+ * (FHEON_ERR_ARG when |c * scale| >= 2^62). */
+int fheon_add_const(fheon_ctx *ctx, const fheon_ct *ct, double c, fheon_ct *out);
+/* out = c * ct rescaled once, landing on scale `target`: the ciphertext is
+ * multiplied by K = llround(((c * target) * q_{l-1}) / scale(ct)) (binary64,
+ * in that order) and rescaled by q_{l-1}; scale(out) = target, level l - 1.
+ * Used to scale by constants and to align levels and scales before adding
+ * (paper Alg. 4's coefficient products and its 1/beta scaling).
+ * FHEON_ERR_LEVEL below level 2, FHEON_ERR_ARG when |K| >= 2^62. */
+int fheon_mul_const_rescale(fheon_ctx *ctx, const fheon_ct *ct, double c, double target, fheon_ct *out);
 /* out = a + b; equal levels, scales equal to 1e-9 relative, else
  * FHEON_ERR_LEVEL / FHEON_ERR_SCALE. */
 int fheon_add(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out);

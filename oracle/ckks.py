@@ -48,6 +48,11 @@ def min_psi(q, N):
     return int(_lib.lib().oracle_min_psi(int(q), N))
 
 
+def llround(x):
+    """Round half away from zero (C llround) of a binary64 value."""
+    return int(_lib.lib().oracle_llround(float(x)))
+
+
 def galois_elt(r, N):
     """g = 5^r mod 2N for a slot rotation by r (slot i <- slot i+r); r may be negative."""
     n = N // 2
@@ -337,6 +342,10 @@ class Ctx:
         out = np.zeros_like(ct)
         _lib.lib().oracle_add_int(self._h, _p(ct, u64p), ct.shape[1], int(v), _p(out, u64p))
         return out
+
+    def add_const(self, ct, c, scale):
+        """ct + c in every slot: the constant llround(c * scale) added to c0."""
+        return self.add_int(ct, llround(float(c) * float(scale)))
 
     def const_factor(self, level, c, target, scale):
         return int(_lib.lib().oracle_const_factor(self._h, level, float(c), float(target), float(scale)))

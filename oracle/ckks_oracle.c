@@ -759,6 +759,10 @@ void oracle_add_int(const oracle_ctx *c, const u64 *ct, u32 level, i64 v, u64 *o
     }
 }
 
+/* round half away from zero (the encoding of a constant c at scale D is
+ * llround(c * D)) */
+i64 oracle_llround(double x) { return llround(x); }
+
 /* The integer K a constant c is encoded as before a rescale by q_{level-1}, so
  * that the rescaled product has scale `target`: a ciphertext of scale `scale`
  * times K, divided by q_{level-1}, has scale scale * K / q ~= c * target.

@@ -71,6 +71,67 @@ __global__ void __launch_bounds__(TPB) mac_plain_kernel(const __grid_constant__ 
     *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(s0, s1);
 }
 
+// the ciphertext tensor d = (a0 b0, a0 b1 + a1 b0, a1 b1); the middle term's
+// two products summed in 128 bits and reduced once
+__global__ void __launch_bounds__(TPB) tensor_kernel(const u64 *__restrict__ a, const u64 *__restrict__ b,
+                                                     u64 *__restrict__ d, u32 level, u32 logN,
+                                                     const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= per) return;
+    const ModConst m = mc[(u32)(idx >> logN)];
+    const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(a + idx), a1 = *reinterpret_cast<const ulonglong2 *>(a + per + idx);
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(b + idx), b1 = *reinterpret_cast<const ulonglong2 *>(b + per + idx);
+    u128acc x, y;
+    acc_zero(x);
+    acc_zero(y);
+    acc_mad(x, a0.x, b1.x);
+    acc_mad(x, a1.x, b0.x);
+    acc_mad(y, a0.y, b1.y);
+    acc_mad(y, a1.y, b0.y);
+    *reinterpret_cast<ulonglong2 *>(d + idx) = make_ulonglong2(mulmod_plain(a0.x, b0.x, m), mulmod_plain(a0.y, b0.y, m));
+    *reinterpret_cast<ulonglong2 *>(d + per + idx) =
+        make_ulonglong2(shoup(redc_acc(x, m.q, m.qneg_inv), m.r1, m.r1_sh, m.q), shoup(redc_acc(y, m.q, m.qneg_inv), m.r1, m.r1_sh, m.q));
+    *reinterpret_cast<ulonglong2 *>(d + 2 * per + idx) = make_ulonglong2(mulmod_plain(a1.x, b1.x, m), mulmod_plain(a1.y, b1.y, m));
+}
+
+// v mod q for a signed 64-bit v
+__device__ __forceinline__ u64 signed_mod(long long v, u64 q)
+{
+    if (v >= 0) return (u64)v % q;
+    const u64 r = (u64)(-(v + 1)) % q;
+    return q - 1 - r;
+}
+
+// out = v * ct over `ncomp` components of `level` limbs
+__global__ void __launch_bounds__(TPB) mul_int_kernel(const u64 *__restrict__ ct, long long v, u64 *__restrict__ out,
+                                                      u32 level, u32 ncomp, u32 logN, const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    if (idx >= ((u64)ncomp * level << logN)) return;
+    const ModConst m = mc[limb_of(idx, level, logN)];
+    const u64 vm = signed_mod(v, m.q);
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
+    *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(mulmod_plain(x.x, vm, m), mulmod_plain(x.y, vm, m));
+}
+
+// out = ct + v: the constant polynomial v is v at every evaluation point, so
+// component 0 gains v mod q_i everywhere; component 1 is copied
+__global__ void __launch_bounds__(TPB) add_int_kernel(const u64 *__restrict__ ct, long long v, u64 *__restrict__ out,
+                                                      u32 level, u32 logN, const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= 2 * per) return;
+    ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
+    if (idx < per) {
+        const u64 q = mc[(u32)(idx >> logN)].q, vm = signed_mod(v, q);
+        x = make_ulonglong2(addmod(x.x, vm, q), addmod(x.y, vm, q));
+    }
+    *reinterpret_cast<ulonglong2 *>(out + idx) = x;
+}
+
 // out = a + b over `ncomp` components of `level` limbs
 __global__ void __launch_bounds__(TPB) add_kernel(const u64 *__restrict__ a, const u64 *__restrict__ b,
                                                   u64 *__restrict__ out, u32 level, u32 ncomp, u32 logN,
@@ -182,6 +243,27 @@ cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const 
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+cudaError_t k_tensor(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *d, u32 level)
+{
+    tensor_kernel<<<blocks2((u64)level * ctx->N), TPB, 0, ctx->stream>>>(a, b, d, level, ctx->logN,
+                                                                          ctx->tab.mc.as<ModConst>());
+    prof_mark(ctx->stream, "tensor");
+    return cudaGetLastError();
+}
+cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level, u32 ncomp)
+{
+    mul_int_kernel<<<blocks2((u64)ncomp * level * ctx->N), TPB, 0, ctx->stream>>>(ct, (long long)v, out, level, ncomp,
+                                                                                  ctx->logN, ctx->tab.mc.as<ModConst>());
+    prof_mark(ctx->stream, "mul_int");
+    return cudaGetLastError();
+}
+cudaError_t k_add_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level)
+{
+    add_int_kernel<<<blocks2((u64)2 * level * ctx->N), TPB, 0, ctx->stream>>>(ct, (long long)v, out, level, ctx->logN,
+                                                                               ctx->tab.mc.as<ModConst>());
+    prof_mark(ctx->stream, "add_int");
+    return cudaGetLastError();
 }
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 level, u32 ncomp)
 {

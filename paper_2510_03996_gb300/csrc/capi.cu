@@ -467,6 +467,17 @@ int fheon_galois_keygen(fheon_ctx *ctx, const fheon_sk *sk, const uint64_t *galo
     return FHEON_OK;
 }
 
+int fheon_relinkeygen(fheon_ctx *ctx, const fheon_sk *sk)
+{
+    if (!ctx || !sk) return FHEON_ERR_ARG;
+    if (ctx->keys.count(0)) return FHEON_OK;
+    RotKey key;
+    int rc = galois_key_dev(ctx, sk, 0, key);
+    if (rc) return rc;
+    ctx->keys.emplace(0, std::move(key));
+    return FHEON_OK;
+}
+
 int fheon_rotkeygen(fheon_ctx *ctx, const fheon_sk *sk, const int32_t *steps, uint32_t n)
 {
     if (!ctx || !sk || (n && !steps)) return FHEON_ERR_ARG;
@@ -730,6 +741,82 @@ int fheon_add_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheo
     }
     FHEON_CUDA(ctx, k_add_plain(ctx, ct->c0(), pt->m.as<u64>(), out->c0(), l));
     out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_mul_relin(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out)
+{
+    if (!ctx || !a || !b || !out) return FHEON_ERR_ARG;
+    if (a->level != b->level) return fail(ctx, FHEON_ERR_LEVEL, "mul_relin: levels %u and %u", a->level, b->level);
+    auto it = ctx->keys.find(0);
+    if (it == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "no relinearisation key");
+    const u32 l = a->level, N = ctx->N;
+    const double sc = a->scale * b->scale;
+    int rc = ensure_workspace(ctx, ctx->ks_ws_limbs(ctx->L) + 3 * (size_t)ctx->L);
+    if (rc) return rc;
+    u64 *ws = ctx->ws.as<u64>();
+    u64 *d = ws + ctx->ks_ws_limbs(ctx->L) * N; // tensor [3][l][N] past the key-switching workspace
+    FHEON_CUDA(ctx, k_tensor(ctx, a->c0(), b->c0(), d, l));
+    if ((rc = ct_reshape(ctx, out, l))) return rc;
+    // key-switch d2 from s^2 to s (g = 1: no automorphism); d0 joins component 0, d1 component 1
+    if ((rc = keyswitch_rotate(ctx, d, d + (size_t)2 * l * N, l, 1, it->second.mem.as<u64>(), ws, out->c0(),
+                               d + (size_t)l * N)))
+        return rc;
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_mul_int(fheon_ctx *ctx, const fheon_ct *ct, int64_t v, fheon_ct *out)
+{
+    if (!ctx || !ct || !out) return FHEON_ERR_ARG;
+    const u32 l = ct->level;
+    const double sc = ct->scale;
+    int rc = out == ct ? FHEON_OK : ct_reshape(ctx, out, l);
+    if (rc) return rc;
+    FHEON_CUDA(ctx, k_mul_int(ctx, ct->c0(), v, out->c0(), l, 2));
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+int fheon_add_int(fheon_ctx *ctx, const fheon_ct *ct, int64_t v, fheon_ct *out)
+{
+    if (!ctx || !ct || !out) return FHEON_ERR_ARG;
+    const u32 l = ct->level;
+    const double sc = ct->scale;
+    int rc = out == ct ? FHEON_OK : ct_reshape(ctx, out, l);
+    if (rc) return rc;
+    FHEON_CUDA(ctx, k_add_int(ctx, ct->c0(), v, out->c0(), l));
+    out->scale = sc;
+    return FHEON_OK;
+}
+
+// llround(x) when it fits comfortably in 63 bits
+static bool round_int(double x, int64_t *v)
+{
+    if (!std::isfinite(x) || std::fabs(x) >= 4611686018427387904.0) return false; // 2^62
+    *v = (int64_t)std::llround(x);
+    return true;
+}
+
+int fheon_add_const(fheon_ctx *ctx, const fheon_ct *ct, double c, fheon_ct *out)
+{
+    if (!ctx || !ct || !out) return FHEON_ERR_ARG;
+    int64_t v;
+    if (!round_int(c * ct->scale, &v)) return fail(ctx, FHEON_ERR_ARG, "add_const: c * scale out of range");
+    return fheon_add_int(ctx, ct, v, out);
+}
+
+int fheon_mul_const_rescale(fheon_ctx *ctx, const fheon_ct *ct, double c, double target, fheon_ct *out)
+{
+    if (!ctx || !ct || !out || !(target > 0)) return FHEON_ERR_ARG;
+    if (ct->level < 2) return fail(ctx, FHEON_ERR_LEVEL, "mul_const_rescale needs level >= 2");
+    int64_t K;
+    if (!round_int(((c * target) * (double)ctx->mod[ct->level - 1]) / ct->scale, &K))
+        return fail(ctx, FHEON_ERR_ARG, "mul_const_rescale: constant factor out of range");
+    int rc = fheon_mul_int(ctx, ct, K, out);
+    if (rc) return rc;
+    if ((rc = rescale_ct(ctx, out, out))) return rc;
+    out->scale = target;
     return FHEON_OK;
 }
 

@@ -158,7 +158,10 @@ cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 le
 // key switching / rotation (keyswitch.cu)
 // The rotation pipeline on caller-provided workspace (ks_ws_limbs(l) limbs);
 // launches kernels only, allocates nothing.
-int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out);
+// c1add (optional): u64[l][N] added to the key-switched component 1
+// (relinearisation: d1; rotation: none)
+int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out,
+                     const u64 *c1add = nullptr);
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out);
 void drop_plans(fheon_ctx *ctx); // release the cached batch plans of a context
 // hoist: items with the same input share one raising of c1 (fast rotations).
@@ -176,12 +179,19 @@ cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, 
 constexpr u32 MAC_MAX = 32;
 cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const *pts, u32 n, u64 *out, u32 level);
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 nlimb_per_comp, u32 ncomp);
+// d = (a0 b0, a0 b1 + a1 b0, a1 b1) over `level` limbs: u64[3][level][N]
+cudaError_t k_tensor(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *d, u32 level);
+// out = v * ct over `ncomp` components; out = ct + v on component 0 only
+cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level, u32 ncomp);
+cudaError_t k_add_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level);
 cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level);
 int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
 cudaError_t k_decrypt(fheon_ctx *ctx, const u64 *ct, const u64 *s, u64 *m, u32 level);
 
 // sampler / keygen / encrypt (sampler.cu)
 int keygen_dev(fheon_ctx *ctx, fheon_sk *sk, fheon_pk *pk);
+// key-switching key to s from sigma_g(s) (rotation), or from s^2 when g = 0
+// (relinearisation); the sampler streams are tagged g
 int galois_key_dev(fheon_ctx *ctx, const fheon_sk *sk, u64 g, RotKey &key);
 int encrypt_dev(fheon_ctx *ctx, const fheon_pk *pk, const fheon_pt *pt, u64 nonce, fheon_ct *out);
 int plain_from_coeffs_dev(fheon_ctx *ctx, const int64_t *host_coeffs, u32 level, fheon_pt *pt);

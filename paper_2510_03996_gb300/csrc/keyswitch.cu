@@ -55,6 +55,7 @@ struct RotDesc {
     u64 gi;             // element applied to c1 on its way into xt (g; 1 when hoisted)
     u64 gx;             // element applied to ext in the inner product (0: none; g when hoisted)
     u32 level, beta;
+    const u64 *c1add;   // added to output component 1 (relinearisation: d1), or null
 };
 
 struct BatchParams {
@@ -328,9 +329,10 @@ struct DnAJob : JobCommon {
     __device__ void store_last(int, u32, u64, const ModConst &) const {}
 };
 
-// DNB: second forward pass; out = (acc - conv) * P^-1 (+ sigma_g(c0) for b = 0)
+// DNB: second forward pass; out = (acc - conv) * P^-1 (+ sigma_g(c0) for b = 0,
+// + c1add for b = 1 when given)
 struct DnBJob : JobCommon {
-    const u64 *mid, *acc, *c0i;
+    const u64 *mid, *acc, *c0i, *c1a;
     u64 *out;
     ulonglong2 pi;
     u32 b;
@@ -344,6 +346,7 @@ struct DnBJob : JobCommon {
         mid = ws_conv(*d, P.K, N) + ((u64)b * l + i) * N;
         acc = ws_acc(*d, P.K, N) + ((u64)b * (l + P.K) + i) * N;
         c0i = d->c0 + (u64)i * N;
+        c1a = (b == 1 && d->c1add) ? d->c1add + (u64)i * N : nullptr;
         out = d->out + ((u64)b * l + i) * N;
         pi = P.pinv[i];
     }
@@ -363,6 +366,7 @@ struct DnBJob : JobCommon {
     {
         u64 r = shoup(acc[J] + m.q - y, pi.x, pi.y, m.q);
         if (b == 0) r = addmod(r, c0i[automorph_src(J, d->g, p.tp.logN)], m.q);
+        else if (c1a) r = addmod(r, c1a[J], m.q);
         out[J] = r;
     }
 };
@@ -752,13 +756,14 @@ Lists closed_form_lists(const fheon_ctx *ctx, u32 l)
 } // namespace
 
 // One ciphertext, closed-form tasks: no device plan, no allocation.
-int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out)
+int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g, const u64 *key, u64 *ws, u64 *out,
+                     const u64 *c1add)
 {
     BatchParams P = batch_params(ctx);
     P.desc = nullptr;
     const u32 beta = ctx->beta_at(l);
     u64 *ext = ws + (size_t)l * ctx->N;
-    P.one = RotDesc{c0, c1, out, key, ws, ext, ext + (size_t)beta * (l + ctx->K) * ctx->N, g, g, 0, l, beta};
+    P.one = RotDesc{c0, c1, out, key, ws, ext, ext + (size_t)beta * (l + ctx->K) * ctx->N, g, g, 0, l, beta, c1add};
     return run_pipeline(ctx, P, closed_form_lists(ctx, l));
 }
 
@@ -897,10 +902,11 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool ho
             if (lead[i] == i) {
                 u64 *ext = w + (size_t)l * N;
                 desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], w, ext,
-                                  ext + (size_t)beta * (l + K) * N, g, hoist ? 1 : g, hoist ? g : 0, l, beta};
+                                  ext + (size_t)beta * (l + K) * N, g, hoist ? 1 : g, hoist ? g : 0, l, beta, nullptr};
             } else {
                 const RotDesc &ld = desc[lead[i]];
-                desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ld.xt, ld.ext, w, g, 1, g, l, beta};
+                desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ld.xt, ld.ext, w, g, 1, g, l, beta,
+                                  nullptr};
             }
             const u32 c = i << 16;
             const bool raise = lead[i] == i;

@@ -160,6 +160,16 @@ __global__ void __launch_bounds__(TPB) gather_kernel(const u64 *__restrict__ in,
     out[idx] = in[base + automorph_src((u32)(idx & ((1u << logN) - 1)), g, logN)];
 }
 
+// s^2 (pointwise in the evaluation domain) over `nlimb` limbs
+__global__ void __launch_bounds__(TPB) square_kernel(const u64 *__restrict__ in, u64 *__restrict__ out, u32 nlimb,
+                                                     u32 logN, const ModConst *__restrict__ mc)
+{
+    const u64 idx = (u64)blockIdx.x * TPB + threadIdx.x;
+    if (idx >= ((u64)nlimb << logN)) return;
+    const ModConst m = mc[idx >> logN];
+    out[idx] = mulmod_plain(in[idx], in[idx], m);
+}
+
 // ct0 = v*pb + e0 + m, ct1 = v*pa + e1 over L limbs
 __global__ void __launch_bounds__(TPB) encrypt_combine_kernel(const u64 *__restrict__ v, const u64 *__restrict__ e0,
                                                               const u64 *__restrict__ e1, const u64 *__restrict__ pk,
@@ -249,7 +259,11 @@ int galois_key_dev(fheon_ctx *ctx, const fheon_sk *sk, u64 g, RotKey &key)
         return fail(ctx, FHEON_ERR_OOM, "rotation key allocation (%zu bytes)", (size_t)B * 2 * per * 8);
     u64 *k = key.mem.as<u64>();
     const u64 *s = sk->s.as<u64>();
-    gather_kernel<<<nblk(per), TPB, 0, st>>>(s, sg.as<u64>(), g, n, ctx->logN);
+    // the source key: sigma_g(s) for a rotation, s^2 for relinearisation (g = 0)
+    if (g)
+        gather_kernel<<<nblk(per), TPB, 0, st>>>(s, sg.as<u64>(), g, n, ctx->logN);
+    else
+        square_kernel<<<nblk(per), TPB, 0, st>>>(s, sg.as<u64>(), n, ctx->logN, mc);
     // e_j into the b slots (stream idx g<<32 | j<<16), a_j into the a slots
     // (stream idx g<<32 | j<<16 | limb)
     small_kernel<true><<<dim3(nblk(N / 8), B), TPB, 0, st>>>(ctx->seed, DOM_KSK_E, g << 32, 1ull << 16, k, 2 * per, N,

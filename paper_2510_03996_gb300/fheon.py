@@ -81,6 +81,12 @@ SIGNATURES = {
     "fheon_rotate_batch_hoisted": [c_vp, P(fheon_rot_item), c_u32],
     "fheon_rotate_noalloc": [c_vp, c_vp, c_i32, c_vp],
     "fheon_mul_plain": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_mul_relin": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_mul_int": [c_vp, c_vp, ctypes.c_int64, c_vp],
+    "fheon_add_int": [c_vp, c_vp, ctypes.c_int64, c_vp],
+    "fheon_add_const": [c_vp, c_vp, c_dbl, c_vp],
+    "fheon_mul_const_rescale": [c_vp, c_vp, c_dbl, c_dbl, c_vp],
+    "fheon_relinkeygen": [c_vp, c_vp],
     "fheon_mac_plain": [c_vp, P(c_vp), P(c_vp), c_u32, c_vp],
     "fheon_add": [c_vp, c_vp, c_vp, c_vp],
     "fheon_add_plain": [c_vp, c_vp, c_vp, c_vp],
@@ -405,6 +411,34 @@ class Context:
     def mul_plain(self, ct, pt, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_mul_plain(self.h, ct.h, pt.h, out.h))
+        return out
+
+    def relinkeygen(self, sk):
+        self._chk(load().fheon_relinkeygen(self.h, sk.h))
+
+    def mul_relin(self, a, b, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_mul_relin(self.h, a.h, b.h, out.h))
+        return out
+
+    def mul_int(self, ct, v, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_mul_int(self.h, ct.h, int(v), out.h))
+        return out
+
+    def add_int(self, ct, v, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_add_int(self.h, ct.h, int(v), out.h))
+        return out
+
+    def add_const(self, ct, c, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_add_const(self.h, ct.h, float(c), out.h))
+        return out
+
+    def mul_const_rescale(self, ct, c, target, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_mul_const_rescale(self.h, ct.h, float(c), float(target), out.h))
         return out
 
     def mac_plain(self, cts, pts, out=None):
