@@ -371,6 +371,36 @@ int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k,
 int fheon_layer_destroy(fheon_layer *layer);
 
 /* ------------------------------------------------------------------ */
+/* Secure ReLU (paper Sec. 4.6, Alg. 4)                               */
+/* ------------------------------------------------------------------ */
+/* Chebyshev coefficients c_0..c_degree of f(z) = beta * max(0, z) on [-1, 1],
+ * interpolated at the degree+1 Chebyshev nodes cos(pi (k + 1/2) / (degree+1))
+ * (the zeros of T_{degree+1}; the paper prints the extrema cos(k pi / d)).
+ * out: [degree + 1].  The paper's default degree is 59. */
+int fheon_relu_coeffs(double beta, uint32_t degree, double *out);
+/* A prepared ReLU for inputs at `level`: when beta > 1 the input is first
+ * multiplied by Alg. 4's scale mask (1/beta in slots [0, n), 0 elsewhere,
+ * encoded at scale q_{level-1}) and rescaled; then the Chebyshev series of
+ * f(z) = beta * max(0, z) is evaluated: T_1 = v, T_2h = 2 T_h^2 - 1,
+ * T_2h+1 = 2 T_h+1 T_h - T_1 (products with relinearisation, rescaled), each
+ * c_d T_d rescaled onto the input's scale at one common level and summed in
+ * order of d, c_0 added.  Output: the input's scale, level - (ceil(log2
+ * degree) + 1 + [beta > 1]).  Needs the relinearisation key.  FHEON_ERR_LEVEL
+ * when the level is too low; FHEON_ERR_ARG for beta <= 0, degree outside
+ * [1, 1023] or n > N/2. */
+int fheon_relu_prepare(fheon_ctx *ctx, double beta, uint32_t degree, uint32_t n, uint32_t level,
+                       fheon_layer **out);
+/* The same with the caller's mask plaintext (at `level` or above, scale
+ * q_{level-1}; needed when beta > 1), which stays owned by the caller and
+ * must outlive the layer. */
+int fheon_relu_prepare_plain(fheon_ctx *ctx, double beta, uint32_t degree, const fheon_pt *mask, uint32_t level,
+                             fheon_layer **out);
+/* Apply a prepared ReLU; `in` at the layer's level, out distinct from in. */
+int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
+/* One-shot: prepare at in's level, apply, release. */
+int fheon_relu_approx(fheon_ctx *ctx, const fheon_ct *ct, double beta, uint32_t degree, uint32_t n, fheon_ct *out);
+
+/* ------------------------------------------------------------------ */
 /* Instrumentation (no counterpart in the paper)                      */
 /* ------------------------------------------------------------------ */
 /* Start recording a CUDA event after every kernel this library launches on

@@ -759,6 +759,27 @@ void oracle_add_int(const oracle_ctx *c, const u64 *ct, u32 level, i64 v, u64 *o
     }
 }
 
+/* Chebyshev interpolant of f(z) = beta * max(0, z) on [-1, 1] (paper Sec. 4.6
+ * and Alg. 4: the input is scaled by 1/beta first, f is evaluated by a
+ * degree-D Chebyshev series), at the D+1 Chebyshev nodes
+ * z_k = cos(theta_k), theta_k = pi (k + 1/2) / (D + 1):
+ *   c_d = (2 / (D + 1)) sum_k f(z_k) cos(d theta_k), and c_0 halved,
+ * the sums taken in order k = 0..D in binary64.  out: [D + 1]. */
+void oracle_cheb_coeffs(double beta, u32 D, double *out)
+{
+    for (u32 d = 0; d <= D; d++) {
+        double sum = 0.0;
+        for (u32 k = 0; k <= D; k++) {
+            double th = M_PI * ((double)k + 0.5) / (double)(D + 1);
+            double z = cos(th);
+            double f = z < 0.0 ? 0.0 : beta * z;
+            sum += f * cos((double)d * th);
+        }
+        out[d] = sum * 2.0 / (double)(D + 1);
+    }
+    out[0] *= 0.5;
+}
+
 /* round half away from zero (the encoding of a constant c at scale D is
  * llround(c * D)) */
 i64 oracle_llround(double x) { return llround(x); }

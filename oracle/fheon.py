@@ -177,3 +177,80 @@ def encode_tap_plains(ctx, H, W, K, k, level):
     scale = float(ctx.q[level - 1])
     return [ctx.plain_from_coeffs(ckks.encode(v, ctx.N, scale), level)
             for v in tap_vectors(n, H, W, C, K, k)]
+
+
+# ------------------------------------------------------------------ ReLU (Sec. 4.6, Alg. 4)
+RELU_DEGREE = 59  # the paper's default D
+
+
+def relu_cheb_coeffs(beta, D=RELU_DEGREE):
+    """Chebyshev coefficients c_0..c_D of f(z) = beta * max(0, z) on [-1, 1],
+    interpolated at the D+1 Chebyshev nodes (computed by the C oracle)."""
+    import ctypes
+
+    from . import _lib
+    out = (ctypes.c_double * (D + 1))()
+    _lib.lib().oracle_cheb_coeffs(float(beta), D, out)
+    return np.array(out[:], dtype=np.float64)
+
+
+def cheb_eval_fp64(c, z):
+    """sum_d c_d T_d(z) in FP64 (T by its three-term recurrence)."""
+    z = np.asarray(z, dtype=np.float64)
+    t0, t1 = np.ones_like(z), z
+    y = c[0] * t0 + (c[1] * t1 if len(c) > 1 else 0.0)
+    for d in range(2, len(c)):
+        t0, t1 = t1, 2.0 * z * t1 - t0
+        y = y + c[d] * t1
+    return y
+
+
+def relu_fp64(x, beta, D=RELU_DEGREE):
+    """The plaintext value of the approximate ReLU: the Chebyshev series of
+    beta * max(0, z) at z = x / beta."""
+    return cheb_eval_fp64(relu_cheb_coeffs(beta, D), np.asarray(x, dtype=np.float64) / beta)
+
+
+def relu_mask_values(nslots, beta, n):
+    """Alg. 4's scale mask: 1/beta in the first n slots, 0 elsewhere."""
+    v = np.zeros(nslots)
+    v[:n] = 1.0 / beta
+    return v
+
+
+def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
+    """Alg. 4 on a ciphertext of scale `scale` (returns (ct, scale)):
+    v = x * mask (rescaled; only when beta > 1), then the Chebyshev series of f
+    at v.  T_1 = v; T_2h = 2 T_h^2 - 1; T_2h+1 = 2 T_h+1 T_h - T_1 (products at
+    the lower operand level, rescaled; T_1 brought to the product's level and
+    scale by a rescaled constant product).  Every c_d T_d (d >= 1) is rescaled
+    onto `scale` at one common level and summed in order of d; c_0 is added
+    last.  The output has the input's scale, at depth ceil(log2 D) + 1 (+1
+    with the mask) below the input."""
+    q = ctx.q
+    c = relu_cheb_coeffs(beta, D)
+    lev = lambda a: a.shape[1]  # noqa: E731
+    v = ctx.rescale(ctx.mul_plain(ct, mask_plain)) if beta > 1 else ct
+    T = {1: (v, scale)}
+    for d in range(2, D + 1):
+        if d % 2 == 0:
+            A, sa = T[d // 2]
+            prod = ctx.rescale(ctx.mul_relin(ctx.mul_int(A, 2), A, rlk))
+            sc = sa * sa / float(q[lev(A) - 1])
+            T[d] = (ctx.add_const(prod, -1.0, sc), sc)
+        else:
+            (A, sa), (B, sb) = T[(d + 1) // 2], T[(d - 1) // 2]
+            lv = min(lev(A), lev(B))
+            A, B = ctx.drop_level(A, lv), ctx.drop_level(B, lv)
+            prod = ctx.rescale(ctx.mul_relin(ctx.mul_int(A, 2), B, rlk))
+            sc = sa * sb / float(q[lv - 1])
+            t1, s1 = T[1]
+            neg = ctx.mul_const_rescale(ctx.drop_level(t1, lv), -1.0, sc, s1)
+            T[d] = (ctx.add(prod, neg), sc)
+    lstar = min(lev(T[d][0]) for d in T) - 1
+    y = None
+    for d in range(1, D + 1):
+        A, sa = T[d]
+        term = ctx.mul_const_rescale(ctx.drop_level(A, lstar + 1), c[d], scale, sa)
+        y = term if y is None else ctx.add(y, term)
+    return ctx.add_const(y, c[0], scale), scale

@@ -38,7 +38,9 @@ def build(force=False, verbose=False, extra_flags=()):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", os.path.join(ROOT, "include"),
+    # host code: no floating-point contraction, so host-side binary64 formulas
+    # (constants derived from the parameters) round the same on every machine
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
               "-I", CSRC] + ARCH + list(extra_flags)
 
     def compile_one(src):

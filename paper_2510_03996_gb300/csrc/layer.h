@@ -1,0 +1,52 @@
+// layer.h -- the state behind a fheon_layer handle: one prepared layer of an
+// encrypted network (conv, approximate ReLU), its plaintexts, working
+// ciphertexts and captured graphs.
+#pragma once
+#include <vector>
+
+#include "internal.h"
+
+// kinds of layer behind the one opaque handle
+enum LayerKind : u32 { LAYER_CONV = 0, LAYER_RELU = 1 };
+
+struct fheon_layer {
+    u32 kind = LAYER_CONV;
+    u32 in_ch = 0, k = 0, H = 0, W = 0, level = 0;
+    // approximate ReLU (Alg. 4): beta, degree, Chebyshev coefficients c_0..c_D;
+    // `mask` holds the 1/beta scale mask when beta > 1
+    double beta = 1.0;
+    u32 degree = 0;
+    std::vector<double> coeffs;
+    std::vector<fheon_pt *> taps; // k*k, row-major (di, dj)
+    fheon_pt *mask = nullptr;     // conv with C > 1: block-0 mask at level-1; ReLU: the 1/beta mask
+    bool own_mask = true;
+    fheon_pt *bias = nullptr;     // at the output level
+    std::vector<bool> owned;      // which of taps are owned by the layer
+    bool own_bias = false;
+    // working ciphertexts (the k^2 - 1 tap rotations, then accumulators), made
+    // on the first application and reused, so that later applications (and
+    // their graph capture) allocate nothing
+    mutable std::vector<fheon_ct *> rot;
+    mutable fheon_ct *tmp[3] = {nullptr, nullptr, nullptr};
+    // captured applications, keyed by the buffers the captured launches use;
+    // `keep` holds the device rotation plans those launches read
+    struct Graph {
+        const void *in, *out, *ws;
+        u32 level;
+        cudaGraphExec_t exec;
+        fheon::PlanKeep keep;
+    };
+    mutable std::vector<Graph> graphs;
+    mutable fheon::PlanKeep *collect = nullptr; // set while an application is captured
+    ~fheon_layer()
+    {
+        for (size_t i = 0; i < taps.size(); i++)
+            if (owned[i]) fheon_pt_destroy(taps[i]);
+        if (own_mask) fheon_pt_destroy(mask);
+        if (own_bias) fheon_pt_destroy(bias);
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        for (fheon_ct *c : tmp) fheon_ct_destroy(c);
+        for (fheon_ct *c : rot) fheon_ct_destroy(c);
+    }
+};
+

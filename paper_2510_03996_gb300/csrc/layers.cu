@@ -18,41 +18,7 @@
 #include <memory>
 #include <vector>
 
-#include "internal.h"
-
-struct fheon_layer {
-    u32 in_ch = 0, k = 0, H = 0, W = 0, level = 0;
-    std::vector<fheon_pt *> taps; // k*k, row-major (di, dj)
-    fheon_pt *mask = nullptr;     // C > 1: block-0 mask at level-1
-    fheon_pt *bias = nullptr;     // at the output level
-    std::vector<bool> owned;      // which of taps are owned by the layer
-    bool own_bias = false;
-    // working ciphertexts (the k^2 - 1 tap rotations, then accumulators), made
-    // on the first application and reused, so that later applications (and
-    // their graph capture) allocate nothing
-    mutable std::vector<fheon_ct *> rot;
-    mutable fheon_ct *tmp[3] = {nullptr, nullptr, nullptr};
-    // captured applications, keyed by the buffers the captured launches use;
-    // `keep` holds the device rotation plans those launches read
-    struct Graph {
-        const void *in, *out, *ws;
-        u32 level;
-        cudaGraphExec_t exec;
-        fheon::PlanKeep keep;
-    };
-    mutable std::vector<Graph> graphs;
-    mutable fheon::PlanKeep *collect = nullptr; // set while an application is captured
-    ~fheon_layer()
-    {
-        for (size_t i = 0; i < taps.size(); i++)
-            if (owned[i]) fheon_pt_destroy(taps[i]);
-        fheon_pt_destroy(mask);
-        if (own_bias) fheon_pt_destroy(bias);
-        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
-        for (fheon_ct *c : tmp) fheon_ct_destroy(c);
-        for (fheon_ct *c : rot) fheon_ct_destroy(c);
-    }
-};
+#include "layer.h"
 
 using namespace fheon;
 
@@ -166,7 +132,7 @@ int fheon_conv2d_prepare_plain(fheon_ctx *ctx, uint32_t in_ch, uint32_t k, uint3
 
 int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
-    if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
+    if (!ctx || !ly || !in || !out || ly->kind != LAYER_CONV) return FHEON_ERR_ARG;
     if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "conv expects level %u, got %u", ly->level, in->level);
     if (out == in) return fail(ctx, FHEON_ERR_ARG, "conv output must not alias its input");
     const int p = (int)(ly->k - 1) / 2;
@@ -221,7 +187,7 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in
 
 int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
-    if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
+    if (!ctx || !ly || !in || !out || ly->kind != LAYER_CONV) return FHEON_ERR_ARG;
     if (!ctx->stream) return fail(ctx, FHEON_ERR_ARG, "graph capture needs a created stream, not the legacy default stream");
     for (auto &g : ly->graphs)
         if (g.in == in->c.p && g.out == out->c.p && g.ws == ctx->ws.p && g.level == in->level) {

@@ -1,0 +1,188 @@
+// relu.cu -- FHEON's secure ReLU (paper Sec. 4.6, Alg. 4) as host
+// orchestration of the device operations: the input times a 1/beta slot mask
+// (when beta > 1), then a degree-D Chebyshev series of f(z) = beta * max(0, z)
+// on [-1, 1].
+//
+// Coefficients: Chebyshev interpolation at the D+1 nodes z_k = cos(theta_k),
+// theta_k = pi (k + 1/2) / (D + 1): c_d = 2/(D+1) sum_k f(z_k) cos(d theta_k),
+// c_0 halved (summed in order k = 0..D in binary64).  The paper prints the
+// nodes as cos(k pi / d), which are the extrema of T_d; the interpolation nodes
+// are the zeros of T_{D+1}.
+//
+// Evaluation (depth ceil(log2 D) + 1, + 1 for the mask):
+//   T_1 = v; T_2h = 2 T_h^2 - 1; T_2h+1 = 2 T_h+1 T_h - T_1,
+// each product taken at the lower operand's level with relinearisation and
+// rescaled; T_1 is brought to the product's level and exact scale by a
+// rescaled constant product (c = -1).  Then every c_d T_d (d >= 1) is
+// rescaled onto the input's scale at one common level, the terms are summed
+// in order of d, and c_0 is added.  The output has the input's scale.
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "layer.h"
+
+using namespace fheon;
+
+namespace {
+
+void relu_cheb(double beta, u32 D, std::vector<double> &c)
+{
+    c.assign(D + 1, 0.0);
+    for (u32 d = 0; d <= D; d++) {
+        double acc = 0.0;
+        for (u32 k = 0; k <= D; k++) {
+            const double theta = M_PI * ((double)k + 0.5) / (double)(D + 1);
+            const double z = std::cos(theta);
+            const double fz = z < 0.0 ? 0.0 : beta * z;
+            acc += fz * std::cos((double)d * theta);
+        }
+        c[d] = acc * 2.0 / (double)(D + 1);
+    }
+    c[0] *= 0.5;
+}
+
+u32 ceil_log2(u32 x)
+{
+    u32 r = 0;
+    while ((1u << r) < x) r++;
+    return r;
+}
+
+// levels the ReLU consumes
+u32 relu_depth(double beta, u32 D) { return ceil_log2(D) + 1 + (beta > 1.0 ? 1 : 0); }
+
+int check_args(fheon_ctx *ctx, double beta, u32 D, u32 level)
+{
+    if (!(beta > 0.0) || !std::isfinite(beta) || D < 1 || D > 1023 || level > ctx->L)
+        return fail(ctx, FHEON_ERR_ARG, "relu: beta > 0, 1 <= degree <= 1023, level <= L");
+    if (level <= relu_depth(beta, D))
+        return fail(ctx, FHEON_ERR_LEVEL, "relu: needs level > %u, got %u", relu_depth(beta, D), level);
+    return FHEON_OK;
+}
+
+struct CtOwn {
+    fheon_ct *p = nullptr;
+    ~CtOwn() { fheon_ct_destroy(p); }
+};
+
+} // namespace
+
+extern "C" {
+
+int fheon_relu_coeffs(double beta, uint32_t degree, double *out)
+{
+    if (!out || !(beta > 0.0) || degree < 1 || degree > 1023) return FHEON_ERR_ARG;
+    std::vector<double> c;
+    relu_cheb(beta, degree, c);
+    for (u32 d = 0; d <= degree; d++) out[d] = c[d];
+    return FHEON_OK;
+}
+
+int fheon_relu_prepare_plain(fheon_ctx *ctx, double beta, uint32_t degree, const fheon_pt *mask, uint32_t level,
+                             fheon_layer **out)
+{
+    if (!ctx || !out) return FHEON_ERR_ARG;
+    int rc = check_args(ctx, beta, degree, level);
+    if (rc) return rc;
+    if (beta > 1.0 && (!mask || mask->level < level))
+        return fail(ctx, FHEON_ERR_ARG, "relu: beta > 1 needs a mask plaintext at level >= %u", level);
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_RELU;
+    ly->beta = beta;
+    ly->degree = degree;
+    ly->level = level;
+    relu_cheb(beta, degree, ly->coeffs);
+    ly->mask = beta > 1.0 ? const_cast<fheon_pt *>(mask) : nullptr;
+    ly->own_mask = false;
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_relu_prepare(fheon_ctx *ctx, double beta, uint32_t degree, uint32_t n, uint32_t level, fheon_layer **out)
+{
+    if (!ctx || !out || n > ctx->N / 2) return FHEON_ERR_ARG;
+    int rc = check_args(ctx, beta, degree, level);
+    if (rc) return rc;
+    fheon_pt *mask = nullptr;
+    if (beta > 1.0) {
+        // GenerateScaleMask(beta, n): 1/beta in the first n slots, at scale q_{level-1}
+        std::vector<double> v(ctx->N / 2, 0.0);
+        for (u32 i = 0; i < n; i++) v[i] = 1.0 / beta;
+        if ((rc = fheon_encode_plain(ctx, v.data(), nullptr, ctx->N / 2, level, (double)ctx->mod[level - 1], &mask)))
+            return rc;
+    }
+    rc = fheon_relu_prepare_plain(ctx, beta, degree, mask, level, out);
+    if (rc) {
+        fheon_pt_destroy(mask);
+        return rc;
+    }
+    (*out)->own_mask = true;
+    return FHEON_OK;
+}
+
+int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !ly || !in || !out || ly->kind != LAYER_RELU) return FHEON_ERR_ARG;
+    if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "relu expects level %u, got %u", ly->level, in->level);
+    if (out == in) return fail(ctx, FHEON_ERR_ARG, "relu output must not alias its input");
+    const u32 D = ly->degree;
+    const double s0 = in->scale;
+    int rc;
+    // T_1 .. T_D in layer-owned working ciphertexts (index d), plus two temporaries
+    if (ly->rot.size() != D + 3) ly->rot.resize(D + 3, nullptr);
+    for (fheon_ct *&c : ly->rot)
+        if (!c && (rc = fheon_ct_create(ctx, ly->level, s0, &c))) return rc;
+    fheon_ct **T = ly->rot.data();
+    fheon_ct *t0 = ly->rot[D + 1], *t1 = ly->rot[D + 2];
+    // v = x * mask, rescaled (scale q_{l-1} of the mask cancels)
+    if (ly->beta > 1.0) {
+        if ((rc = fheon_mul_plain(ctx, in, ly->mask, T[1]))) return rc;
+        if ((rc = fheon_rescale(ctx, T[1], T[1]))) return rc;
+        T[1]->scale = s0;
+    } else if ((rc = fheon_drop_level(ctx, in, in->level, T[1]))) {
+        return rc;
+    }
+    for (u32 d = 2; d <= D; d++) {
+        const u32 h = d / 2;
+        fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
+        const u32 lv = A->level < B->level ? A->level : B->level;
+        if ((rc = fheon_drop_level(ctx, A, lv, t0))) return rc;
+        if ((rc = fheon_mul_int(ctx, t0, 2, t0))) return rc;
+        if ((rc = fheon_drop_level(ctx, B, lv, t1))) return rc;
+        if ((rc = fheon_mul_relin(ctx, t0, t1, T[d]))) return rc;
+        if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
+        if (d % 2 == 0) {
+            if ((rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
+        } else {
+            if ((rc = fheon_drop_level(ctx, T[1], lv, t0))) return rc;
+            if ((rc = fheon_mul_const_rescale(ctx, t0, -1.0, T[d]->scale, t1))) return rc;
+            if ((rc = fheon_add(ctx, T[d], t1, T[d]))) return rc;
+        }
+    }
+    u32 lstar = T[1]->level;
+    for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
+    lstar -= 1;
+    CtOwn y;
+    if ((rc = fheon_ct_create(ctx, lstar, s0, &y.p))) return rc;
+    for (u32 d = 1; d <= D; d++) {
+        if ((rc = fheon_drop_level(ctx, T[d], lstar + 1, t0))) return rc;
+        if ((rc = fheon_mul_const_rescale(ctx, t0, ly->coeffs[d], s0, d == 1 ? y.p : t1))) return rc;
+        if (d > 1 && (rc = fheon_add(ctx, y.p, t1, y.p))) return rc;
+    }
+    if ((rc = fheon_add_const(ctx, y.p, ly->coeffs[0], out))) return rc;
+    return FHEON_OK;
+}
+
+int fheon_relu_approx(fheon_ctx *ctx, const fheon_ct *ct, double beta, uint32_t degree, uint32_t n, fheon_ct *out)
+{
+    if (!ctx || !ct) return FHEON_ERR_ARG;
+    fheon_layer *ly = nullptr;
+    int rc = fheon_relu_prepare(ctx, beta, degree, n, ct->level, &ly);
+    if (rc) return rc;
+    rc = fheon_relu_apply(ctx, ly, ct, out);
+    fheon_layer_destroy(ly);
+    return rc;
+}
+
+} // extern "C"

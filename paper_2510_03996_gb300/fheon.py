@@ -87,6 +87,11 @@ SIGNATURES = {
     "fheon_add_const": [c_vp, c_vp, c_dbl, c_vp],
     "fheon_mul_const_rescale": [c_vp, c_vp, c_dbl, c_dbl, c_vp],
     "fheon_relinkeygen": [c_vp, c_vp],
+    "fheon_relu_coeffs": [c_dbl, c_u32, P(c_dbl)],
+    "fheon_relu_prepare": [c_vp, c_dbl, c_u32, c_u32, c_u32, c_vpp],
+    "fheon_relu_prepare_plain": [c_vp, c_dbl, c_u32, c_vp, c_u32, c_vpp],
+    "fheon_relu_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_relu_approx": [c_vp, c_vp, c_dbl, c_u32, c_u32, c_vp],
     "fheon_mac_plain": [c_vp, P(c_vp), P(c_vp), c_u32, c_vp],
     "fheon_add": [c_vp, c_vp, c_vp, c_vp],
     "fheon_add_plain": [c_vp, c_vp, c_vp, c_vp],
@@ -148,6 +153,13 @@ def __getattr__(name):
 
 # ---------------------------------------------------------------- allocator hook
 _hooks = None
+
+
+def relu_coeffs(beta, degree=59):
+    """Chebyshev coefficients of f(z) = beta * max(0, z) (the library's own)."""
+    out = (c_dbl * (degree + 1))()
+    check(load().fheon_relu_coeffs(float(beta), degree, out))
+    return np.array(out[:])
 
 
 def use_torch_allocator():
@@ -439,6 +451,28 @@ class Context:
     def mul_const_rescale(self, ct, c, target, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_mul_const_rescale(self.h, ct.h, float(c), float(target), out.h))
+        return out
+
+    def relu_prepare(self, beta, degree, n, level):
+        h = c_vp()
+        self._chk(load().fheon_relu_prepare(self.h, float(beta), degree, n, level, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def relu_prepare_plain(self, beta, degree, mask, level):
+        h = c_vp()
+        self._chk(load().fheon_relu_prepare_plain(self.h, float(beta), degree, mask.h if mask is not None else None,
+                                                  level, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def relu_apply(self, layer, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_relu_apply(self.h, layer.h, ct.h, out.h))
+        return out
+
+    def relu_approx(self, ct, beta, degree=59, n=None, out=None):
+        out = out or self.ct_create(1)
+        n = self.N // 2 if n is None else n
+        self._chk(load().fheon_relu_approx(self.h, ct.h, float(beta), degree, n, out.h))
         return out
 
     def mac_plain(self, cts, pts, out=None):
