@@ -254,3 +254,156 @@ def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
         term = ctx.mul_const_rescale(ctx.drop_level(A, lstar + 1), c[d], scale, sa)
         y = term if y is None else ctx.add(y, term)
     return ctx.add_const(y, c[0], scale), scale
+
+
+# ------------------------------------------------------------------ packed network layers
+# Layout of a feature map (C, H, W) in the slots: channel c in the block at
+# offset c * block; position (i, j) at c * block + dil * (i * grid + j), where
+# `grid` is the row stride of the block's grid and `dil` the spacing of the
+# valid positions (a stride-s layer multiplies it by s instead of compacting).
+
+def map_slots(C, H, W, grid, dil, block):
+    """Slot of every (c, i, j) of a (C, H, W) map, in flatten order."""
+    return np.array([c * block + dil * (i * grid + j) for c in range(C) for i in range(H) for j in range(W)],
+                    dtype=np.int64)
+
+
+def pack_map(X, nslots, grid, dil, block):
+    v = np.zeros(nslots)
+    v[map_slots(*X.shape, grid, dil, block)] = np.asarray(X, dtype=np.float64).reshape(-1)
+    return v
+
+
+def unpack_map(v, shape, grid, dil, block):
+    return np.asarray(v)[map_slots(*shape, grid, dil, block)].reshape(shape)
+
+
+def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K):
+    """Rotation-sum plan of a stride-1 convolution (Sec. 4.1 equation, zero
+    padding `pad`) from C to F channels: tap t = (x, y) reads the input at
+    offset (x - pad, y - pad), i.e. Rot_{r_t} with r_t = dil*((x-pad)*grid +
+    (y-pad)); group delta = f - c collects, in the block of input channel c, the
+    weights K[f, c, x, y] at every output position whose tap source lies inside
+    the input; its sum is moved to block f by Rot_{-delta*block}.
+    Returns (r, [(s_g, [values_t or None])]); all-zero plaintexts are None."""
+    Ho, Wo = H + 2 * pad - k + 1, W + 2 * pad - k + 1
+    taps = [(x, y) for x in range(k) for y in range(k)]
+    r = [dil * ((x - pad) * grid + (y - pad)) for x, y in taps]
+    groups = []
+    for delta in range(-(C - 1), F):
+        vals = []
+        for x, y in taps:
+            v = np.zeros(nslots)
+            for c in range(C):
+                f = c + delta
+                if not 0 <= f < F:
+                    continue
+                for i in range(Ho):
+                    for j in range(Wo):
+                        si, sj = i + x - pad, j + y - pad
+                        if 0 <= si < H and 0 <= sj < W:
+                            v[c * block + dil * (i * grid + j)] = K[f][c][x][y]
+            vals.append(v if np.any(v != 0.0) else None)
+        if any(v is not None for v in vals):
+            groups.append((-delta * block, vals))
+    return r, groups
+
+
+def avgpool_plan(C, k, stride, H, W, grid, dil, block, nslots):
+    """Average pooling (Sec. 4.4): the window sum by the rotations
+    r_t = dil*(x*grid + y), x, y < k, times one mask holding 1/k^2 at the
+    stride-aligned outputs (the striding is the mask: the outputs stay in
+    place, at spacing dil*stride).  Returns (r, [(0, [mask] * k^2)])."""
+    Ho, Wo = (H - k) // stride + 1, (W - k) // stride + 1
+    m = np.zeros(nslots)
+    for c in range(C):
+        for i in range(Ho):
+            for j in range(Wo):
+                m[c * block + dil * stride * (i * grid + j)] = 1.0 / (k * k)
+    r = [dil * (x * grid + y) for x in range(k) for y in range(k)]
+    return r, [(0, [m] * len(r))]
+
+
+def fc_plan(Wmat, in_slots, nslots):
+    """Fully connected layer (Sec. 4.5 equation): neuron k's weight vector at
+    the input's slots (product, then the sum of all slots), and the one-hot
+    vector that places the sum in slot k.  Returns ([W_k], [E_k])."""
+    Wmat = np.asarray(Wmat, dtype=np.float64)
+    m, n = Wmat.shape
+    ws, es = [], []
+    for k in range(m):
+        w = np.zeros(nslots)
+        w[np.asarray(in_slots)] = Wmat[k]
+        e = np.zeros(nslots)
+        e[k] = 1.0
+        ws.append(w)
+        es.append(e)
+    return ws, es
+
+
+def slot_sum_steps(nslots):
+    """Rotate-and-add steps that leave the sum of all slots in every slot."""
+    return [1 << t for t in range(int(np.log2(nslots)))]
+
+
+def linear_slots(v, r, groups):
+    """FP64 slot model of a rotation-sum plan (Rot_r(v) = v shifted left by r)."""
+    out = np.zeros_like(v)
+    for s, vals in groups:
+        z = np.zeros_like(v)
+        for rt, p in zip(r, vals):
+            if p is not None:
+                z += np.roll(v, -rt) * p
+        out += np.roll(z, -s)
+    return out
+
+
+def fc_slots(v, ws, es):
+    out = np.zeros_like(v)
+    for w, e in zip(ws, es):
+        out += np.sum(v * w) * e
+    return out
+
+
+def linear_steps(r, groups):
+    """Rotation steps (keys) a rotation-sum plan uses."""
+    return sorted({x for x in r if x != 0} | {s for s, _ in groups if s != 0})
+
+
+def linear_encrypted(ctx, ct, r, groups, pts, keys):
+    """A rotation-sum plan on a ciphertext: the tap rotations hoisted from the
+    input, each group's products summed and rescaled once, moved by its own
+    (plain) rotation, the groups summed in order.  pts[g][t]: plaintext or
+    None (as in `groups`); keys: step -> key-switching key."""
+    N = ctx.N
+    steps = [x for x in r if x != 0]
+    hs = ctx.rotate_hoisted(ct, [ckks.galois_elt(x, N) for x in steps], [keys[x] for x in steps])
+    rot = dict(zip(steps, hs))
+    rot[0] = ct
+    y = None
+    for (s, _), gp in zip(groups, pts):
+        acc = None
+        for rt, p in zip(r, gp):
+            if p is not None:
+                prod = ctx.mul_plain(rot[rt], p)
+                acc = prod if acc is None else ctx.add(acc, prod)
+        acc = ctx.rescale(acc)
+        if s != 0:
+            acc = ctx.rotate(acc, ckks.galois_elt(s, N), keys[s])
+        y = acc if y is None else ctx.add(y, acc)
+    return y
+
+
+def fc_encrypted(ctx, ct, wpts, epts, keys):
+    """FC plan on a ciphertext: t_k = rescale(ct * W_k); every t_k through the
+    rotate-and-add slot sum; out = rescale(sum_k t_k * E_k)."""
+    N = ctx.N
+    ts = [ctx.rescale(ctx.mul_plain(ct, w)) for w in wpts]
+    for st in slot_sum_steps(N // 2):
+        g = ckks.galois_elt(st, N)
+        ts = [ctx.add(t, ctx.rotate(t, g, keys[st])) for t in ts]
+    y = None
+    for t, e in zip(ts, epts):
+        prod = ctx.mul_plain(t, e)
+        y = prod if y is None else ctx.add(y, prod)
+    return ctx.rescale(y)
