@@ -62,6 +62,13 @@ typedef struct fheon_pk fheon_pk;
 typedef struct fheon_pt fheon_pt;
 typedef struct fheon_ct fheon_ct;
 typedef struct fheon_layer fheon_layer;
+/* Packed layout of a feature map (C, H, W) in the slots: channel c in the
+ * block at offset c * block; position (i, j) at c*block + dil*(i*grid + j).
+ * `grid` is the row stride; `dil` the spacing of valid positions (a stride-s
+ * layer multiplies it by s, leaving its outputs in place). */
+typedef struct fheon_map {
+    uint32_t C, H, W, grid, dil, block;
+} fheon_map;
 
 /* Message for an error code (static storage). */
 const char *fheon_error_string(int code);
@@ -369,6 +376,56 @@ int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k,
                  uint32_t pad, uint32_t in_h, uint32_t in_w, const double *w, const double *bias,
                  fheon_ct *out);
 int fheon_layer_destroy(fheon_layer *layer);
+
+/* ------------------------------------------------------------------ */
+/* Packed network layers on a fheon_map (paper Sec. 4.1, 4.4, 4.5)     */
+/* ------------------------------------------------------------------ */
+/* Rotation-sum layer from the caller's plaintexts:
+ *   out = sum_g Rot_{s[g]}( rescale( sum_t Rot_{r[t]}(in) * pts[g*nt + t] ) ) (+ bias)
+ * The nt tap rotations (distinct steps; 0 = the input itself) are hoisted
+ * from the input; each group's products are summed in one pass and rescaled
+ * once; the ng group sums move by one batched rotation (s[g] = 0: none) and are
+ * added; bias (optional, level >= level-1) is added last.  pts[g*nt + t] may
+ * be NULL (no product); each group needs one.  Plaintexts at `level` or above,
+ * encoded at scale q_{level-1}; they stay owned by the caller and must outlive
+ * the layer.  Output level: level - 1. */
+int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nt, const int32_t *r, uint32_t ng, const int32_t *s,
+                               const fheon_pt *const *pts, const fheon_pt *bias, uint32_t level,
+                               fheon_layer **out);
+/* Fully connected layer from the caller's plaintexts (Sec. 4.5): t_k =
+ * rescale(in * W[k]) for each of the m neurons; each t_k summed over all N/2
+ * slots by rotate-and-add (steps 1, 2, ..., N/4, batched over the neurons);
+ * out = rescale(sum_k t_k * E[k]) (+ bias, level >= level-2).  W at `level`
+ * (scale q_{level-1}), E at level-1 (scale q_{level-2}).  Output level:
+ * level - 2.  Caller-owned plaintexts. */
+int fheon_fc_prepare_plain(fheon_ctx *ctx, uint32_t m, const fheon_pt *const *W, const fheon_pt *const *E,
+                           const fheon_pt *bias, uint32_t level, fheon_layer **out);
+/* Convolution (Sec. 4.1 equation; zero padding `pad`, stride 1) of the map
+ * `in` to F output channels, kernel K[F][C][k][k], bias[F] (or NULL): a
+ * rotation-sum layer with one group per block shift f - c.  The output map
+ * has the input's grid, dilation and block, H + 2 pad - k + 1 rows and
+ * columns.  Plaintexts encoded on the device, owned by the layer.  Output
+ * level: level - 1, scale in_scale. */
+int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t pad, const double *K,
+                       const double *bias, uint32_t level, double in_scale, fheon_layer **out);
+/* Average pooling (Sec. 4.4): the k x k window sum by k^2 hoisted rotations
+ * times one mask of 1/k^2 at the stride-aligned outputs.  The outputs stay in
+ * place: the output map's dilation is the input's times `stride`. */
+int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint32_t stride, uint32_t level,
+                          fheon_layer **out);
+/* Fully connected layer (Sec. 4.5): W[m][C*H*W] over the map's values in
+ * (c, i, j) order, bias[m] (or NULL); output: the m neurons in slots [0, m)
+ * (map {1, 1, m, m, 1, m}).  Output level: level - 2, scale in_scale. */
+int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
+                     uint32_t level, double in_scale, fheon_layer **out);
+/* Apply any prepared layer (conv2d, ReLU, rotation-sum, FC); `in` at the
+ * layer's level, out distinct from in. */
+int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
+/* Rotation steps (keys) the layer uses: *n in = capacity of out (out may be
+ * NULL to query), *n out = count; FHEON_ERR_ARG when out is too small. */
+int fheon_layer_rotation_steps(const fheon_layer *layer, int32_t *out, uint32_t *n);
+/* Output map of a conv, pooling or FC layer prepared from a map. */
+int fheon_layer_out_map(const fheon_layer *layer, fheon_map *out);
 
 /* ------------------------------------------------------------------ */
 /* Secure ReLU (paper Sec. 4.6, Alg. 4)                               */

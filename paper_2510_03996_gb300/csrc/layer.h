@@ -7,7 +7,7 @@
 #include "internal.h"
 
 // kinds of layer behind the one opaque handle
-enum LayerKind : u32 { LAYER_CONV = 0, LAYER_RELU = 1 };
+enum LayerKind : u32 { LAYER_CONV = 0, LAYER_RELU = 1, LAYER_LINEAR = 2, LAYER_FC = 3 };
 
 struct fheon_layer {
     u32 kind = LAYER_CONV;
@@ -17,6 +17,14 @@ struct fheon_layer {
     double beta = 1.0;
     u32 degree = 0;
     std::vector<double> coeffs;
+    // rotation-sum layer: tap steps r_t (hoisted from the input), group shifts
+    // s_g, plaintexts [g][t] (null: no product); FC: weight and placement
+    // plaintexts of each output neuron, the slots summed over
+    std::vector<int32_t> r, s;
+    std::vector<fheon_pt *> pts, fw, fe;   // views
+    std::vector<fheon_pt *> pt_store;       // the plaintexts the layer owns
+    u32 nslots = 0;
+    fheon_map in_map{}, out_map{};
     std::vector<fheon_pt *> taps; // k*k, row-major (di, dj)
     fheon_pt *mask = nullptr;     // conv with C > 1: block-0 mask at level-1; ReLU: the 1/beta mask
     bool own_mask = true;
@@ -27,6 +35,7 @@ struct fheon_layer {
     // on the first application and reused, so that later applications (and
     // their graph capture) allocate nothing
     mutable std::vector<fheon_ct *> rot;
+    mutable std::vector<fheon_ct *> work;
     mutable fheon_ct *tmp[3] = {nullptr, nullptr, nullptr};
     // captured applications, keyed by the buffers the captured launches use;
     // `keep` holds the device rotation plans those launches read
@@ -47,6 +56,8 @@ struct fheon_layer {
         for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
         for (fheon_ct *c : tmp) fheon_ct_destroy(c);
         for (fheon_ct *c : rot) fheon_ct_destroy(c);
+        for (fheon_ct *c : work) fheon_ct_destroy(c);
+        for (fheon_pt *p : pt_store) fheon_pt_destroy(p);
     }
 };
 

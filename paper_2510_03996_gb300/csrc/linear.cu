@@ -1,0 +1,373 @@
+// linear.cu -- the linear layers of an encrypted CNN on a packed feature map
+// (fheon_map): convolution (paper Sec. 4.1 equation; any zero padding, stride
+// 1, C input and F output channels), average pooling (Sec. 4.4: the window sum
+// times a 1/k^2 mask that also does the striding, the outputs staying at
+// stride-aligned slots) and the fully connected layer (Sec. 4.5: one product
+// per output neuron, the sum of its slots, a one-hot placement).
+//
+// Rotation-sum layer (conv, pooling):
+//   out = sum_g Rot_{s_g}( rescale( sum_t Rot_{r_t}(in) * P_{g,t} ) ) (+ bias)
+// The tap rotations r_t are hoisted from the input (one raising of c1); each
+// group's products are summed in one pass (fheon_mac_plain) and rescaled once;
+// the group sums move by one batched rotation and are added.  A conv from C to
+// F channels has one group per block shift delta = f - c: in the block of
+// input channel c it holds K[f, c, x, y] at every output position whose tap
+// source (i + x - pad, j + y - pad) lies inside the input, and s = -delta*block
+// moves that partial sum into block f.  Tap t = (x, y) reads the input at
+// r_t = dil*((x - pad)*grid + (y - pad)).
+//
+// FC: t_k = rescale(in * W_k) (W_k: row k of the weights at the input's
+// slots); every t_k through the rotate-and-add slot sum (steps 1, 2, 4, ...,
+// N/4: the total lands in every slot); out = rescale(sum_k t_k * E_k), E_k one
+// at slot k.  The output map is the compact vector of the m neurons.
+#include <cmath>
+#include <memory>
+#include <set>
+#include <vector>
+
+#include "layer.h"
+
+using namespace fheon;
+
+namespace {
+
+u32 map_slot(const fheon_map &m, u32 c, u32 i, u32 j) { return c * m.block + m.dil * (i * m.grid + j); }
+
+bool map_ok(const fheon_ctx *ctx, const fheon_map &m)
+{
+    if (!m.C || !m.H || !m.W || !m.dil || m.grid < m.W || !m.block) return false;
+    if ((u64)m.dil * ((u64)(m.H - 1) * m.grid + (m.W - 1)) >= m.block) return false;
+    return (u64)m.C * m.block <= ctx->N / 2;
+}
+
+int ensure_cts(fheon_ctx *ctx, std::vector<fheon_ct *> &v, size_t n, u32 level, double scale)
+{
+    if (v.size() < n) v.resize(n, nullptr);
+    for (size_t i = 0; i < n; i++)
+        if (!v[i]) {
+            int rc = fheon_ct_create(ctx, level, scale, &v[i]);
+            if (rc) return rc;
+        }
+    return FHEON_OK;
+}
+
+// the layer's own plaintext of `v` at `level` and `scale`; null when v is all zero
+int own_plain(fheon_ctx *ctx, fheon_layer *ly, const std::vector<double> &v, u32 level, double scale,
+              fheon_pt **out)
+{
+    *out = nullptr;
+    bool any = false;
+    for (double x : v) any = any || x != 0.0;
+    if (!any) return FHEON_OK;
+    int rc = fheon_encode_plain(ctx, v.data(), nullptr, (uint32_t)v.size(), level, scale, out);
+    if (rc) return rc;
+    ly->pt_store.push_back(*out);
+    return FHEON_OK;
+}
+
+int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    const u32 nt = (u32)ly->r.size(), ng = (u32)ly->s.size();
+    std::vector<int32_t> steps;
+    std::vector<int> idx(nt, -1);
+    for (u32 t = 0; t < nt; t++)
+        if (ly->r[t] != 0) {
+            idx[t] = (int)steps.size();
+            steps.push_back(ly->r[t]);
+        }
+    int rc;
+    if ((rc = ensure_cts(ctx, ly->rot, steps.size(), in->level, in->scale))) return rc;
+    if ((rc = ensure_cts(ctx, ly->work, 2 * (size_t)ng, in->level, in->scale))) return rc;
+    if ((rc = rotate_hoisted(ctx, in, steps.data(), (u32)steps.size(), ly->rot.data(), ly->collect))) return rc;
+    std::vector<const fheon_ct *> srcs;
+    std::vector<const fheon_pt *> ps;
+    std::vector<fheon_rot_item> moves;
+    for (u32 g = 0; g < ng; g++) {
+        srcs.clear();
+        ps.clear();
+        for (u32 t = 0; t < nt; t++) {
+            const fheon_pt *p = ly->pts[(size_t)g * nt + t];
+            if (!p) continue;
+            srcs.push_back(idx[t] < 0 ? in : ly->rot[idx[t]]);
+            ps.push_back(p);
+        }
+        if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), ly->work[g]))) return rc;
+        if ((rc = fheon_rescale(ctx, ly->work[g], ly->work[g]))) return rc;
+        if (ly->s[g] != 0) moves.push_back(fheon_rot_item{ly->work[g], ly->work[ng + g], ly->s[g]});
+    }
+    if ((rc = rotate_many(ctx, moves.data(), (u32)moves.size(), false, ly->collect))) return rc;
+    auto term = [&](u32 g) { return ly->s[g] != 0 ? ly->work[ng + g] : ly->work[g]; };
+    if (ng == 1) {
+        if ((rc = fheon_drop_level(ctx, term(0), term(0)->level, out))) return rc;
+    } else {
+        if ((rc = fheon_add(ctx, term(0), term(1), out))) return rc;
+        for (u32 g = 2; g < ng; g++)
+            if ((rc = fheon_add(ctx, out, term(g), out))) return rc;
+    }
+    if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
+    return FHEON_OK;
+}
+
+int fc_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    const u32 m = (u32)ly->fw.size();
+    int rc;
+    if ((rc = ensure_cts(ctx, ly->work, 2 * (size_t)m, in->level, in->scale))) return rc;
+    for (u32 k = 0; k < m; k++) {
+        if ((rc = fheon_mul_plain(ctx, in, ly->fw[k], ly->work[k]))) return rc;
+        if ((rc = fheon_rescale(ctx, ly->work[k], ly->work[k]))) return rc;
+    }
+    std::vector<fheon_rot_item> items(m);
+    for (u32 st = 1; st < ly->nslots; st <<= 1) {
+        for (u32 k = 0; k < m; k++) items[k] = fheon_rot_item{ly->work[k], ly->work[m + k], (int32_t)st};
+        if ((rc = rotate_many(ctx, items.data(), m, false, ly->collect))) return rc;
+        for (u32 k = 0; k < m; k++)
+            if ((rc = fheon_add(ctx, ly->work[k], ly->work[m + k], ly->work[k]))) return rc;
+    }
+    std::vector<const fheon_ct *> ts(ly->work.begin(), ly->work.begin() + m);
+    std::vector<const fheon_pt *> es(ly->fe.begin(), ly->fe.end());
+    if ((rc = fheon_mac_plain(ctx, ts.data(), es.data(), m, out))) return rc;
+    if ((rc = fheon_rescale(ctx, out, out))) return rc;
+    if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
+    return FHEON_OK;
+}
+
+int check_pt(fheon_ctx *ctx, const fheon_pt *p, u32 level, const char *what)
+{
+    if (p && p->level < level) return fail(ctx, FHEON_ERR_LEVEL, "%s below level %u", what, level);
+    return FHEON_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nt, const int32_t *r, uint32_t ng, const int32_t *s,
+                               const fheon_pt *const *pts, const fheon_pt *bias, uint32_t level, fheon_layer **out)
+{
+    if (!ctx || !out || !nt || !ng || !r || !s || !pts || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    std::set<int32_t> seen;
+    for (u32 t = 0; t < nt; t++)
+        if (!seen.insert(r[t]).second) return fail(ctx, FHEON_ERR_ARG, "linear: tap step %d repeated", r[t]);
+    int rc;
+    for (u32 g = 0; g < ng; g++) {
+        bool any = false;
+        for (u32 t = 0; t < nt; t++) {
+            const fheon_pt *p = pts[(size_t)g * nt + t];
+            any = any || p;
+            if ((rc = check_pt(ctx, p, level, "linear: plaintext"))) return rc;
+        }
+        if (!any) return fail(ctx, FHEON_ERR_ARG, "linear: group %u has no plaintext", g);
+    }
+    if ((rc = check_pt(ctx, bias, level - 1, "linear: bias"))) return rc;
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_LINEAR;
+    ly->level = level;
+    ly->r.assign(r, r + nt);
+    ly->s.assign(s, s + ng);
+    for (size_t i = 0; i < (size_t)nt * ng; i++) ly->pts.push_back(const_cast<fheon_pt *>(pts[i]));
+    ly->bias = const_cast<fheon_pt *>(bias);
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_fc_prepare_plain(fheon_ctx *ctx, uint32_t m, const fheon_pt *const *W, const fheon_pt *const *E,
+                           const fheon_pt *bias, uint32_t level, fheon_layer **out)
+{
+    if (!ctx || !out || !m || !W || !E || level < 3 || level > ctx->L) return FHEON_ERR_ARG;
+    int rc;
+    for (u32 k = 0; k < m; k++) {
+        if (!W[k] || !E[k]) return fail(ctx, FHEON_ERR_ARG, "fc: neuron %u without plaintexts", k);
+        if ((rc = check_pt(ctx, W[k], level, "fc: weights"))) return rc;
+        if ((rc = check_pt(ctx, E[k], level - 1, "fc: placement"))) return rc;
+    }
+    if ((rc = check_pt(ctx, bias, level - 2, "fc: bias"))) return rc;
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_FC;
+    ly->level = level;
+    ly->nslots = ctx->N / 2;
+    for (u32 k = 0; k < m; k++) {
+        ly->fw.push_back(const_cast<fheon_pt *>(W[k]));
+        ly->fe.push_back(const_cast<fheon_pt *>(E[k]));
+    }
+    ly->bias = const_cast<fheon_pt *>(bias);
+    ly->out_map = fheon_map{1, 1, m, m, 1, m};
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t pad, const double *K,
+                       const double *bias, uint32_t level, double in_scale, fheon_layer **out)
+{
+    if (!ctx || !in || !out || !K || !F || !k || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    const fheon_map im = *in;
+    if (!map_ok(ctx, im) || im.H + 2 * pad < k || im.W + 2 * pad < k)
+        return fail(ctx, FHEON_ERR_ARG, "conv: map does not fit the slots or the kernel");
+    const u32 C = im.C, Ho = im.H + 2 * pad - k + 1, Wo = im.W + 2 * pad - k + 1, n = ctx->N / 2;
+    const fheon_map om{F, Ho, Wo, im.grid, im.dil, im.block};
+    if (!map_ok(ctx, om)) return fail(ctx, FHEON_ERR_ARG, "conv: output map does not fit the slots");
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_LINEAR;
+    ly->level = level;
+    ly->in_map = im;
+    ly->out_map = om;
+    for (u32 x = 0; x < k; x++)
+        for (u32 y = 0; y < k; y++)
+            ly->r.push_back((int32_t)im.dil * (((int32_t)x - (int32_t)pad) * (int32_t)im.grid + ((int32_t)y - (int32_t)pad)));
+    const double ps = (double)ctx->mod[level - 1];
+    std::vector<double> v(n);
+    int rc;
+    for (int delta = -(int)(C - 1); delta < (int)F; delta++) {
+        std::vector<fheon_pt *> gp;
+        bool any = false;
+        for (u32 x = 0; x < k; x++)
+            for (u32 y = 0; y < k; y++) {
+                std::fill(v.begin(), v.end(), 0.0);
+                for (u32 c = 0; c < C; c++) {
+                    const int f = (int)c + delta;
+                    if (f < 0 || f >= (int)F) continue;
+                    const double w = K[(((size_t)f * C + c) * k + x) * k + y];
+                    for (u32 i = 0; i < Ho; i++)
+                        for (u32 j = 0; j < Wo; j++) {
+                            const int si = (int)(i + x) - (int)pad, sj = (int)(j + y) - (int)pad;
+                            if (si >= 0 && si < (int)im.H && sj >= 0 && sj < (int)im.W) v[map_slot(im, c, i, j)] = w;
+                        }
+                }
+                fheon_pt *p = nullptr;
+                if ((rc = own_plain(ctx, ly.get(), v, level, ps, &p))) return rc;
+                gp.push_back(p);
+                any = any || p;
+            }
+        if (!any) continue;
+        ly->s.push_back(-delta * (int32_t)im.block);
+        ly->pts.insert(ly->pts.end(), gp.begin(), gp.end());
+    }
+    if (bias) {
+        std::fill(v.begin(), v.end(), 0.0);
+        for (u32 f = 0; f < F; f++)
+            for (u32 i = 0; i < Ho; i++)
+                for (u32 j = 0; j < Wo; j++) v[map_slot(om, f, i, j)] = bias[f];
+        if ((rc = own_plain(ctx, ly.get(), v, level - 1, in_scale, &ly->bias))) return rc;
+    }
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint32_t stride, uint32_t level,
+                          fheon_layer **out)
+{
+    if (!ctx || !in || !out || !k || !stride || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    const fheon_map im = *in;
+    if (!map_ok(ctx, im) || im.H < k || im.W < k) return fail(ctx, FHEON_ERR_ARG, "avgpool: map does not fit");
+    const u32 Ho = (im.H - k) / stride + 1, Wo = (im.W - k) / stride + 1, n = ctx->N / 2;
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_LINEAR;
+    ly->level = level;
+    ly->in_map = im;
+    ly->out_map = fheon_map{im.C, Ho, Wo, im.grid, im.dil * stride, im.block};
+    std::vector<double> v(n, 0.0);
+    for (u32 c = 0; c < im.C; c++)
+        for (u32 i = 0; i < Ho; i++)
+            for (u32 j = 0; j < Wo; j++) v[map_slot(ly->out_map, c, i, j)] = 1.0 / ((double)k * k);
+    fheon_pt *mask = nullptr;
+    int rc = own_plain(ctx, ly.get(), v, level, (double)ctx->mod[level - 1], &mask);
+    if (rc) return rc;
+    for (u32 x = 0; x < k; x++)
+        for (u32 y = 0; y < k; y++) {
+            ly->r.push_back((int32_t)(im.dil * (x * im.grid + y)));
+            ly->pts.push_back(mask);
+        }
+    ly->s.push_back(0);
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
+                     uint32_t level, double in_scale, fheon_layer **out)
+{
+    if (!ctx || !in || !out || !W || !m || m > ctx->N / 2 || level < 3 || level > ctx->L) return FHEON_ERR_ARG;
+    const fheon_map im = *in;
+    if (!map_ok(ctx, im)) return fail(ctx, FHEON_ERR_ARG, "fc: map does not fit");
+    const u32 n = ctx->N / 2, nin = im.C * im.H * im.W;
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_FC;
+    ly->level = level;
+    ly->nslots = n;
+    ly->in_map = im;
+    ly->out_map = fheon_map{1, 1, m, m, 1, m};
+    std::vector<u32> slots;
+    for (u32 c = 0; c < im.C; c++)
+        for (u32 i = 0; i < im.H; i++)
+            for (u32 j = 0; j < im.W; j++) slots.push_back(map_slot(im, c, i, j));
+    std::vector<double> v(n);
+    int rc;
+    for (u32 k = 0; k < m; k++) {
+        std::fill(v.begin(), v.end(), 0.0);
+        for (u32 t = 0; t < nin; t++) v[slots[t]] = W[(size_t)k * nin + t];
+        fheon_pt *w = nullptr, *e = nullptr;
+        if ((rc = own_plain(ctx, ly.get(), v, level, (double)ctx->mod[level - 1], &w))) return rc;
+        std::fill(v.begin(), v.end(), 0.0);
+        v[k] = 1.0;
+        if ((rc = own_plain(ctx, ly.get(), v, level - 1, (double)ctx->mod[level - 2], &e))) return rc;
+        if (!w) return fail(ctx, FHEON_ERR_ARG, "fc: neuron %u has all-zero weights", k);
+        ly->fw.push_back(w);
+        ly->fe.push_back(e);
+    }
+    if (bias) {
+        std::fill(v.begin(), v.end(), 0.0);
+        for (u32 k = 0; k < m; k++) v[k] = bias[k];
+        if ((rc = own_plain(ctx, ly.get(), v, level - 2, in_scale, &ly->bias))) return rc;
+    }
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
+    switch (ly->kind) {
+    case LAYER_CONV: return fheon_conv2d_apply(ctx, ly, in, out);
+    case LAYER_RELU: return fheon_relu_apply(ctx, ly, in, out);
+    default: break;
+    }
+    if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "layer expects level %u, got %u", ly->level, in->level);
+    if (out == in) return fail(ctx, FHEON_ERR_ARG, "layer output must not alias its input");
+    return ly->kind == LAYER_LINEAR ? linear_apply(ctx, ly, in, out) : fc_apply(ctx, ly, in, out);
+}
+
+int fheon_layer_rotation_steps(const fheon_layer *ly, int32_t *out, uint32_t *n)
+{
+    if (!ly || !n) return FHEON_ERR_ARG;
+    std::set<int32_t> st;
+    if (ly->kind == LAYER_LINEAR) {
+        for (int32_t x : ly->r)
+            if (x) st.insert(x);
+        for (int32_t x : ly->s)
+            if (x) st.insert(x);
+    } else if (ly->kind == LAYER_FC) {
+        for (u32 x = 1; x < ly->nslots; x <<= 1) st.insert((int32_t)x);
+    } else if (ly->kind == LAYER_CONV) {
+        const int p = (int)(ly->k - 1) / 2;
+        for (int di = -p; di <= p; di++)
+            for (int dj = -p; dj <= p; dj++)
+                if (di || dj) st.insert(di * (int)ly->W + dj);
+        if (ly->in_ch > 1) st.insert((int32_t)(ly->H * ly->W));
+    }
+    const uint32_t cap = *n;
+    *n = (uint32_t)st.size();
+    if (out && cap < st.size()) return FHEON_ERR_ARG;
+    if (out) {
+        u32 i = 0;
+        for (int32_t x : st) out[i++] = x;
+    }
+    return FHEON_OK;
+}
+
+int fheon_layer_out_map(const fheon_layer *ly, fheon_map *out)
+{
+    if (!ly || !out || (ly->kind != LAYER_LINEAR && ly->kind != LAYER_FC)) return FHEON_ERR_ARG;
+    *out = ly->out_map;
+    return FHEON_OK;
+}
+
+} // extern "C"

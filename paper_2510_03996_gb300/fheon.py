@@ -28,6 +28,15 @@ ALLOC_FN = ctypes.CFUNCTYPE(c_vp, c_sz, c_vp, c_vp)
 FREE_FN = ctypes.CFUNCTYPE(None, c_vp, c_sz, c_vp, c_vp)
 
 
+class fheon_map(ctypes.Structure):
+    """Packed layout of a (C, H, W) map: channel c at c*block, (i, j) at + dil*(i*grid + j)."""
+    _fields_ = [("C", ctypes.c_uint32), ("H", ctypes.c_uint32), ("W", ctypes.c_uint32),
+                ("grid", ctypes.c_uint32), ("dil", ctypes.c_uint32), ("block", ctypes.c_uint32)]
+
+    def tup(self):
+        return (self.C, self.H, self.W, self.grid, self.dil, self.block)
+
+
 class fheon_rot_item(ctypes.Structure):
     _fields_ = [("input", c_vp), ("output", c_vp), ("step", c_i32)]
 
@@ -88,6 +97,14 @@ SIGNATURES = {
     "fheon_mul_const_rescale": [c_vp, c_vp, c_dbl, c_dbl, c_vp],
     "fheon_relinkeygen": [c_vp, c_vp],
     "fheon_relu_coeffs": [c_dbl, c_u32, P(c_dbl)],
+    "fheon_linear_prepare_plain": [c_vp, c_u32, P(c_i32), c_u32, P(c_i32), P(c_vp), c_vp, c_u32, c_vpp],
+    "fheon_fc_prepare_plain": [c_vp, c_u32, P(c_vp), P(c_vp), c_vp, c_u32, c_vpp],
+    "fheon_conv_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
+    "fheon_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_vpp],
+    "fheon_fc_prepare": [c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
+    "fheon_layer_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_layer_rotation_steps": [c_vp, P(c_i32), P(c_u32)],
+    "fheon_layer_out_map": [c_vp, P(fheon_map)],
     "fheon_relu_prepare": [c_vp, c_dbl, c_u32, c_u32, c_u32, c_vpp],
     "fheon_relu_prepare_plain": [c_vp, c_dbl, c_u32, c_vp, c_u32, c_vpp],
     "fheon_relu_apply": [c_vp, c_vp, c_vp, c_vp],
@@ -452,6 +469,74 @@ class Context:
         out = out or self.ct_create(1)
         self._chk(load().fheon_mul_const_rescale(self.h, ct.h, float(c), float(target), out.h))
         return out
+
+    @staticmethod
+    def _map(m):
+        return m if isinstance(m, fheon_map) else fheon_map(*[int(x) for x in m])
+
+    def linear_prepare_plain(self, r, s, pts, level, bias=None):
+        """pts: [len(s)][len(r)] plaintexts or None."""
+        nt, ng = len(r), len(s)
+        rr = (c_i32 * nt)(*[int(x) for x in r])
+        ss = (c_i32 * ng)(*[int(x) for x in s])
+        pp = (c_vp * (nt * ng))(*[(p.h.value if p is not None else None) for row in pts for p in row])
+        h = c_vp()
+        self._chk(load().fheon_linear_prepare_plain(self.h, nt, rr, ng, ss, pp, bias.h if bias is not None else None,
+                                                    level, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def fc_prepare_plain(self, W, E, level, bias=None):
+        m = len(W)
+        ww = (c_vp * m)(*[p.h.value for p in W])
+        ee = (c_vp * m)(*[p.h.value for p in E])
+        h = c_vp()
+        self._chk(load().fheon_fc_prepare_plain(self.h, m, ww, ee, bias.h if bias is not None else None, level,
+                                                ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def conv_prepare(self, in_map, K, pad, level, in_scale, bias=None):
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        F, C, k, _ = K.shape
+        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        h = c_vp()
+        self._chk(load().fheon_conv_prepare(self.h, ctypes.byref(self._map(in_map)), F, k, pad, _dblp(K),
+                                            _dblp(b) if b is not None else None, level, float(in_scale),
+                                            ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def avgpool_prepare(self, in_map, k, stride, level):
+        h = c_vp()
+        self._chk(load().fheon_avgpool_prepare(self.h, ctypes.byref(self._map(in_map)), k, stride, level,
+                                               ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def fc_prepare(self, in_map, W, level, in_scale, bias=None):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        h = c_vp()
+        self._chk(load().fheon_fc_prepare(self.h, ctypes.byref(self._map(in_map)), W.shape[0], _dblp(W),
+                                          _dblp(b) if b is not None else None, level, float(in_scale),
+                                          ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def layer_apply(self, layer, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_layer_apply(self.h, layer.h, ct.h, out.h))
+        return out
+
+    @staticmethod
+    def layer_rotation_steps(layer):
+        n = c_u32(0)
+        check(load().fheon_layer_rotation_steps(layer.h, None, ctypes.byref(n)))
+        out = (c_i32 * max(1, n.value))()
+        check(load().fheon_layer_rotation_steps(layer.h, out, ctypes.byref(n)))
+        return list(out[:n.value])
+
+    @staticmethod
+    def layer_out_map(layer):
+        m = fheon_map()
+        check(load().fheon_layer_out_map(layer.h, ctypes.byref(m)))
+        return m.tup()
 
     def relu_prepare(self, beta, degree, n, level):
         h = c_vp()

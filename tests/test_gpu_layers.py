@@ -1,0 +1,136 @@
+"""Packed network layers on the GPU: the rotation-sum plans (multi-channel
+conv with block shifts, average pooling on a dilated grid) and the FC plan
+against the oracle's encrypted plans from the same integer plaintexts,
+bit-exact; the layers built from weights on the device against the FP64
+layers; key and map queries."""
+import numpy as np
+import pytest
+
+import gpu_common
+from oracle import ckks
+from oracle import fheon as OF
+from paper_2510_03996_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GRID, BLOCK = 8, 64
+
+
+@pytest.fixture(scope="module")
+def pair():
+    return gpu_common.Pair("relu_n12")
+
+
+def _enc_map(pr, X, dil, nonce, level):
+    v = OF.pack_map(X, pr.N // 2, GRID, dil, BLOCK)
+    ct, oct_ = pr.encrypt_both(ckks.encode(v, pr.N, pr.P["scale"]), nonce=nonce, level=level)
+    return v, ct, oct_
+
+
+def _plains(pr, vals, level, scale):
+    """The same integer plaintext on both sides (None stays None)."""
+    g, o = [], []
+    for v in vals:
+        if v is None:
+            g.append(None)
+            o.append(None)
+            continue
+        m = ckks.encode(v, pr.N, scale)
+        g.append(pr.g.plain_from_coeffs(m, pr.L, scale))
+        o.append(pr.o.plain_from_coeffs(m, pr.L))
+    return g, o
+
+
+def _linear_pair(pr, r, groups, level):
+    scale = float(pr.g.moduli[level - 1])
+    gp, op = [], []
+    for _, vals in groups:
+        a, b = _plains(pr, vals, level, scale)
+        gp.append(a)
+        op.append(b)
+    pr.add_keys(OF.linear_steps(r, groups))
+    okeys = {s: pr.okeys[pr.g.galois_elt(s)] for s in OF.linear_steps(r, groups)}
+    layer = pr.g.linear_prepare_plain(r, [s for s, _ in groups], gp, level)
+    return layer, op, okeys, gp
+
+
+def test_conv_plan_bit_exact(pair):
+    X = synth.image(80, 0, (2, 6, 6))
+    K = synth.conv_kernel(80, 1, (3, 2, 3, 3))
+    level = 6
+    v, ct, oct_ = _enc_map(pair, X, 1, 8000, level)
+    r, groups = OF.conv_plan(2, 3, 3, 1, 6, 6, GRID, 1, BLOCK, pair.N // 2, K)
+    layer, op, okeys, keep = _linear_pair(pair, r, groups, level)
+    y = pair.g.layer_apply(layer, ct)
+    want = OF.linear_encrypted(pair.o, oct_, r, groups, op, okeys)
+    assert gpu_common.mismatch(pair.g.ct_download(y), want) == 0
+    assert sorted(pair.g.layer_rotation_steps(layer)) == OF.linear_steps(r, groups)
+
+
+def test_avgpool_plan_bit_exact(pair):
+    X = synth.image(81, 0, (3, 4, 4))
+    level = 5
+    v, ct, oct_ = _enc_map(pair, X, 2, 8100, level)
+    r, groups = OF.avgpool_plan(3, 2, 2, 4, 4, GRID, 2, BLOCK, pair.N // 2)
+    layer, op, okeys, keep = _linear_pair(pair, r, groups, level)
+    y = pair.g.layer_apply(layer, ct)
+    want = OF.linear_encrypted(pair.o, oct_, r, groups, op, okeys)
+    assert gpu_common.mismatch(pair.g.ct_download(y), want) == 0
+
+
+def test_fc_plan_bit_exact(pair):
+    X = synth.image(82, 0, (2, 3, 3))
+    level = 5
+    v, ct, oct_ = _enc_map(pair, X, 1, 8200, level)
+    slots = OF.map_slots(2, 3, 3, GRID, 1, BLOCK)
+    Wm = synth.image(82, 1, (4, len(slots)), dist="normal") * 0.2
+    ws, es = OF.fc_plan(Wm, slots, pair.N // 2)
+    gw, ow = _plains(pair, ws, level, float(pair.g.moduli[level - 1]))
+    ge, oe = _plains(pair, es, level - 1, float(pair.g.moduli[level - 2]))
+    steps = OF.slot_sum_steps(pair.N // 2)
+    pair.add_keys(steps)
+    layer = pair.g.fc_prepare_plain(gw, ge, level)
+    y = pair.g.layer_apply(layer, ct)
+    want = OF.fc_encrypted(pair.o, oct_, ow, oe, {s: pair.okeys[pair.g.galois_elt(s)] for s in steps})
+    assert gpu_common.mismatch(pair.g.ct_download(y), want) == 0
+    assert pair.g.layer_rotation_steps(layer) == steps
+
+
+def test_layers_from_weights_match_fp64(pair):
+    """conv (valid, 1 -> 2) -> avgpool 2/2 -> conv (2 -> 3) on the stride-2 grid
+    -> FC, each built from its weights on the device, decrypted against the
+    FP64 chain."""
+    g = pair.g
+    D = pair.P["scale"]
+    n = pair.N // 2
+    grid, block = 12, 144
+    X = synth.image(83, 0, (1, 12, 12))
+    K1 = synth.conv_kernel(83, 1, (2, 1, 3, 3), std=0.3)
+    b1 = np.array([0.1, -0.2])
+    K2 = synth.conv_kernel(83, 2, (3, 2, 3, 3), std=0.3)
+    Wm = synth.image(83, 3, (4, 27), dist="normal") * 0.2
+    bf = np.array([0.5, 0.0, -0.5, 1.0])
+    v = OF.pack_map(X, n, grid, 1, block)
+    ct, _ = pair.encrypt_both(ckks.encode(v, pair.N, D), nonce=8300)
+    lv = pair.L
+    m0 = (1, 12, 12, grid, 1, block)
+    L1 = g.conv_prepare(m0, K1, 0, lv, D, bias=b1)
+    m1 = g.layer_out_map(L1)
+    assert m1 == (2, 10, 10, grid, 1, block)
+    L2 = g.avgpool_prepare(m1, 2, 2, lv - 1)
+    m2 = g.layer_out_map(L2)
+    assert m2 == (2, 5, 5, grid, 2, block)
+    L3 = g.conv_prepare(m2, K2, 0, lv - 2, D)
+    m3 = g.layer_out_map(L3)
+    L4 = g.fc_prepare(m3, Wm, lv - 3, D, bias=bf)
+    for layer in (L1, L2, L3, L4):
+        pair.add_keys(g.layer_rotation_steps(layer))
+    y = ct
+    for layer in (L1, L2, L3, L4):
+        y = g.layer_apply(layer, y)
+    assert g.ct_info(y)[0] == lv - 5
+    got = np.asarray(g.decode(g.decrypt(pair.sk, y))).real
+    h = OF.conv2d_fp64(OF.avgpool_fp64(OF.conv2d_fp64(X, K1, b=b1), 2, 2), K2)
+    want = Wm @ h.reshape(-1) + bf
+    assert np.max(np.abs(got[:4] - want)) < 1e-3
+    assert np.max(np.abs(got[4:])) < 1e-3
