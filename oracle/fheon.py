@@ -407,3 +407,19 @@ def fc_encrypted(ctx, ct, wpts, epts, keys):
         prod = ctx.mul_plain(t, e)
         y = prod if y is None else ctx.add(y, prod)
     return ctx.rescale(y)
+
+
+def lenet_fp64(X, w, betas=None, D=RELU_DEGREE):
+    """LeNet-5 (paper Sec. 7 architecture) in FP64 from the plain layers; with
+    `betas`, each ReLU is the Chebyshev series of Alg. 4 with that bound."""
+    def act(v, i):
+        return np.maximum(v, 0.0) if betas is None else relu_fp64(v, betas[i], D)
+    h = avgpool_fp64(act(conv2d_fp64(X, w["conv0"][0], b=w["conv0"][1]), 0), 2, 2)
+    h = avgpool_fp64(act(conv2d_fp64(h, w["conv1"][0], b=w["conv1"][1]), 1), 2, 2)
+    h = h.reshape(-1)
+    for i in range(3):
+        W, b = w["fc%d" % i]
+        h = W @ h + b
+        if i < 2:
+            h = act(h, 2 + i)
+    return h

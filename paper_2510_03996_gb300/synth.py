@@ -30,6 +30,9 @@ def params(name):
         return dict(logN=6, qbits=[50, 40, 40, 40], pbits=[58, 58], dnum=2, scale=2.0 ** 30, seed=SEED_BASE + 7)
     if name == "small_n12":  # test-sized, spans several NTT tiles
         return dict(logN=12, qbits=[55, 45, 45, 45, 45], pbits=[60, 60], dnum=3, scale=2.0 ** 40, seed=SEED_BASE + 8)
+    if name == "lenet_n15":  # LeNet-5 without bootstrapping: 42 levels of layers + 2 to decrypt from;
+        # P (240 bits) above the largest digit (60 + 3 x 40 bits)
+        return dict(logN=15, qbits=[60] + [40] * 43, pbits=[60] * 4, dnum=11, scale=2.0 ** 40, seed=SEED_BASE + 2)
     if name == "relu_n12":  # test-sized with the depth of one approximate ReLU (8 levels) and 2 to spare;
         # P (180 bits) above the largest digit (60 + 40 + 40 bits) keeps key-switching noise small
         return dict(logN=12, qbits=[60] + [40] * 10, pbits=[60, 60, 60], dnum=4, scale=2.0 ** 40, seed=SEED_BASE + 9)
