@@ -21,9 +21,13 @@ RELU_DEGREE = 59
 # (out, in, k) of the two convolutions and (out, in) of the three FC layers
 CONVS = [(6, 1, 5), (16, 6, 5)]
 FCS = [(120, 256), (84, 120), (10, 84)]
-# levels each layer uses
+# levels each layer uses (a ReLU: ceil(log2 59) + 1, + 1 for the mask when beta > 1)
 DEPTH = {"conv": 1, "pool": 1, "fc": 2, "relu": 8}
-LEVELS = 2 * DEPTH["conv"] + 2 * DEPTH["pool"] + 3 * DEPTH["fc"] + 4 * DEPTH["relu"]
+LEVELS = 2 * DEPTH["conv"] + 2 * DEPTH["pool"] + 3 * DEPTH["fc"] + 4 * DEPTH["relu"]  # at most
+
+
+def relu_depth(beta):
+    return int(np.ceil(np.log2(RELU_DEGREE))) + 1 + (1 if beta > 1.0 else 0)
 
 
 def weights(seed):
@@ -104,7 +108,7 @@ class EncryptedLeNet:
             m = ctx.layer_out_map(conv)
             lv -= DEPTH["conv"]
             relu = ctx.relu_prepare(betas[i], RELU_DEGREE, m[0] * m[5], lv)
-            lv -= DEPTH["relu"]
+            lv -= relu_depth(betas[i])
             pool = ctx.avgpool_prepare(m, 2, 2, lv)
             m = ctx.layer_out_map(pool)
             lv -= DEPTH["pool"]
@@ -117,7 +121,7 @@ class EncryptedLeNet:
             self.layers.append(fc)
             if i < 2:
                 self.layers.append(ctx.relu_prepare(betas[2 + i], RELU_DEGREE, m[2], lv))
-                lv -= DEPTH["relu"]
+                lv -= relu_depth(betas[2 + i])
         self.out_level = lv
 
     def rotation_steps(self):
