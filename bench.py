@@ -253,6 +253,46 @@ def per_ciphertext_rate(ctx, ins, outs, steps, stream, reps=2):
     return {"value": reps * len(ins) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / reps}
 
 
+def lenet_timing(F, batch=32):
+    """LeNet-5 encrypted inference (N = 2^15, 44 levels, no bootstrapping) over a
+    batch of synthetic 1x28x28 U[0,1] inputs with random-init weights: seconds
+    per inference (CUDA events around the batch), and the largest distance of
+    the decrypted logits from the FP64 network with exact ReLUs."""
+    import torch
+    from paper_2510_03996_gb300 import lenet
+    P = synth.params("lenet_n15")
+    N = 1 << P["logN"]
+    s = torch.cuda.Stream()
+    ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                    stream=s.cuda_stream)
+    w = lenet.weights(P["seed"])
+    xs = [synth.image(P["seed"], 700 + i, (1, 28, 28)) for i in range(batch)]
+    betas = lenet.relu_bounds(xs, w)
+    sk, pk = ctx.keygen()
+    ctx.relinkeygen(sk)
+    net = lenet.EncryptedLeNet(ctx, w, betas, ctx.L, P["scale"])
+    ctx.rotkeygen(sk, net.rotation_steps())
+    cts = [ctx.encrypt(pk, ctx.encode(lenet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i)
+           for i, X in enumerate(xs)]
+    net.forward(cts[0])  # warm-up: working ciphertexts, plans
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    outs = [net.forward(ct) for ct in cts]
+    e1.record(s)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    err = 0.0
+    for X, y in zip(xs, outs):
+        got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
+        err = max(err, float(np.max(np.abs(got - lenet.forward_fp64(X, w)))))
+    nkeys, kbytes = ctx.key_stats()
+    del outs, cts, net, sk, pk
+    ctx.close()
+    return {"s_per_inference": secs / batch, "batch": batch, "keys": nkeys, "key_bytes": kbytes,
+            "max_abs_logit_vs_fp64_exact_relu": err, "relu_bounds": betas, "levels": len(P["qbits"])}
+
+
 def conv_layer_timing(F, iters=200):
     """Packed special conv of the 1x28x28, 5x5, pad 2 layer at N = 2^13 (24 tap
     rotations + 25 plaintext products + one rescale), eager and as a replayed
@@ -407,7 +447,8 @@ def run_gpu(args, rank, world, local_rank):
     comparisons = None
     if not args.no_comparisons:
         comparisons = {"per_ciphertext_path": per_ciphertext_rate(ctx, ins, outs, steps, stream),
-                       "conv_n13_layer": conv_layer_timing(F)}
+                       "conv_n13_layer": conv_layer_timing(F),
+                       "lenet5_n15": lenet_timing(F)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

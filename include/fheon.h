@@ -400,14 +400,16 @@ int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nt, const int32_t *r, ui
  * level - 2.  Caller-owned plaintexts. */
 int fheon_fc_prepare_plain(fheon_ctx *ctx, uint32_t m, const fheon_pt *const *W, const fheon_pt *const *E,
                            const fheon_pt *bias, uint32_t level, fheon_layer **out);
-/* Convolution (Sec. 4.1 equation; zero padding `pad`, stride 1) of the map
- * `in` to F output channels, kernel K[F][C][k][k], bias[F] (or NULL): a
- * rotation-sum layer with one group per block shift f - c.  The output map
- * has the input's grid, dilation and block, H + 2 pad - k + 1 rows and
- * columns.  Plaintexts encoded on the device, owned by the layer.  Output
- * level: level - 1, scale in_scale. */
-int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t pad, const double *K,
-                       const double *bias, uint32_t level, double in_scale, fheon_layer **out);
+/* Convolution (Sec. 4.1 and Sec. 4.2 equations; zero padding `pad`, stride
+ * `stride`) of the map `in` to F output channels, kernel K[F][C][k][k],
+ * bias[F] (or NULL): a rotation-sum layer with one group per block shift
+ * f - c.  Output (i, j) stays at input-grid position (stride*i, stride*j):
+ * the output map has the input's grid and block, dilation dil*stride and
+ * (H + 2 pad - k)/stride + 1 rows and columns; the striding costs no
+ * rotation and no level.  Plaintexts encoded on the device, owned by the
+ * layer.  Output level: level - 1, scale in_scale. */
+int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t stride, uint32_t pad,
+                       const double *K, const double *bias, uint32_t level, double in_scale, fheon_layer **out);
 /* Average pooling (Sec. 4.4): the k x k window sum by k^2 hoisted rotations
  * times one mask of 1/k^2 at the stride-aligned outputs.  The outputs stay in
  * place: the output map's dilation is the input's times `stride`. */

@@ -278,15 +278,17 @@ def unpack_map(v, shape, grid, dil, block):
     return np.asarray(v)[map_slots(*shape, grid, dil, block)].reshape(shape)
 
 
-def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K):
-    """Rotation-sum plan of a stride-1 convolution (Sec. 4.1 equation, zero
-    padding `pad`) from C to F channels: tap t = (x, y) reads the input at
-    offset (x - pad, y - pad), i.e. Rot_{r_t} with r_t = dil*((x-pad)*grid +
+def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K, stride=1):
+    """Rotation-sum plan of a convolution (Sec. 4.1 equation, zero padding
+    `pad`, stride `stride`) from C to F channels: tap t = (x, y) reads the input
+    at offset (x - pad, y - pad), i.e. Rot_{r_t} with r_t = dil*((x-pad)*grid +
     (y-pad)); group delta = f - c collects, in the block of input channel c, the
-    weights K[f, c, x, y] at every output position whose tap source lies inside
-    the input; its sum is moved to block f by Rot_{-delta*block}.
-    Returns (r, [(s_g, [values_t or None])]); all-zero plaintexts are None."""
-    Ho, Wo = H + 2 * pad - k + 1, W + 2 * pad - k + 1
+    weights K[f, c, x, y] at every output position -- input-grid position
+    (stride*i, stride*j), so the output dilation is dil*stride -- whose tap
+    source lies inside the input; its sum is moved to block f by
+    Rot_{-delta*block}.  Returns (r, [(s_g, [values_t or None])]); all-zero
+    plaintexts are None."""
+    Ho, Wo = (H + 2 * pad - k) // stride + 1, (W + 2 * pad - k) // stride + 1
     taps = [(x, y) for x in range(k) for y in range(k)]
     r = [dil * ((x - pad) * grid + (y - pad)) for x, y in taps]
     groups = []
@@ -300,9 +302,9 @@ def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K):
                     continue
                 for i in range(Ho):
                     for j in range(Wo):
-                        si, sj = i + x - pad, j + y - pad
+                        si, sj = stride * i + x - pad, stride * j + y - pad
                         if 0 <= si < H and 0 <= sj < W:
-                            v[c * block + dil * (i * grid + j)] = K[f][c][x][y]
+                            v[c * block + dil * stride * (i * grid + j)] = K[f][c][x][y]
             vals.append(v if np.any(v != 0.0) else None)
         if any(v is not None for v in vals):
             groups.append((-delta * block, vals))

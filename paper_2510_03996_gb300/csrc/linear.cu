@@ -1,6 +1,7 @@
 // linear.cu -- the linear layers of an encrypted CNN on a packed feature map
-// (fheon_map): convolution (paper Sec. 4.1 equation; any zero padding, stride
-// 1, C input and F output channels), average pooling (Sec. 4.4: the window sum
+// (fheon_map): convolution (paper Sec. 4.1 equation; any zero padding and
+// stride, C input and F output channels; the stride selects the output
+// positions the weights are placed at), average pooling (Sec. 4.4: the window sum
 // times a 1/k^2 mask that also does the striding, the outputs staying at
 // stride-aligned slots) and the fully connected layer (Sec. 4.5: one product
 // per output neuron, the sum of its slots, a one-hot placement).
@@ -196,15 +197,16 @@ int fheon_fc_prepare_plain(fheon_ctx *ctx, uint32_t m, const fheon_pt *const *W,
     return FHEON_OK;
 }
 
-int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t pad, const double *K,
-                       const double *bias, uint32_t level, double in_scale, fheon_layer **out)
+int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t stride, uint32_t pad,
+                       const double *K, const double *bias, uint32_t level, double in_scale, fheon_layer **out)
 {
-    if (!ctx || !in || !out || !K || !F || !k || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    if (!ctx || !in || !out || !K || !F || !k || !stride || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
     const fheon_map im = *in;
     if (!map_ok(ctx, im) || im.H + 2 * pad < k || im.W + 2 * pad < k)
         return fail(ctx, FHEON_ERR_ARG, "conv: map does not fit the slots or the kernel");
-    const u32 C = im.C, Ho = im.H + 2 * pad - k + 1, Wo = im.W + 2 * pad - k + 1, n = ctx->N / 2;
-    const fheon_map om{F, Ho, Wo, im.grid, im.dil, im.block};
+    const u32 C = im.C, Ho = (im.H + 2 * pad - k) / stride + 1, Wo = (im.W + 2 * pad - k) / stride + 1, n = ctx->N / 2;
+    // outputs at input-grid positions (stride*i, stride*j): the striding is in the weights
+    const fheon_map om{F, Ho, Wo, im.grid, im.dil * stride, im.block};
     if (!map_ok(ctx, om)) return fail(ctx, FHEON_ERR_ARG, "conv: output map does not fit the slots");
     std::unique_ptr<fheon_layer> ly(new fheon_layer());
     ly->kind = LAYER_LINEAR;
@@ -229,8 +231,8 @@ int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t
                     const double w = K[(((size_t)f * C + c) * k + x) * k + y];
                     for (u32 i = 0; i < Ho; i++)
                         for (u32 j = 0; j < Wo; j++) {
-                            const int si = (int)(i + x) - (int)pad, sj = (int)(j + y) - (int)pad;
-                            if (si >= 0 && si < (int)im.H && sj >= 0 && sj < (int)im.W) v[map_slot(im, c, i, j)] = w;
+                            const int si = (int)(stride * i + x) - (int)pad, sj = (int)(stride * j + y) - (int)pad;
+                            if (si >= 0 && si < (int)im.H && sj >= 0 && sj < (int)im.W) v[map_slot(om, c, i, j)] = w;
                         }
                 }
                 fheon_pt *p = nullptr;

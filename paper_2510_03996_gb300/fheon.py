@@ -99,7 +99,7 @@ SIGNATURES = {
     "fheon_relu_coeffs": [c_dbl, c_u32, P(c_dbl)],
     "fheon_linear_prepare_plain": [c_vp, c_u32, P(c_i32), c_u32, P(c_i32), P(c_vp), c_vp, c_u32, c_vpp],
     "fheon_fc_prepare_plain": [c_vp, c_u32, P(c_vp), P(c_vp), c_vp, c_u32, c_vpp],
-    "fheon_conv_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
+    "fheon_conv_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_vpp],
     "fheon_fc_prepare": [c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_layer_apply": [c_vp, c_vp, c_vp, c_vp],
@@ -494,12 +494,12 @@ class Context:
                                                 ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)
 
-    def conv_prepare(self, in_map, K, pad, level, in_scale, bias=None):
+    def conv_prepare(self, in_map, K, pad, level, in_scale, bias=None, stride=1):
         K = np.ascontiguousarray(K, dtype=np.float64)
         F, C, k, _ = K.shape
         b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
         h = c_vp()
-        self._chk(load().fheon_conv_prepare(self.h, ctypes.byref(self._map(in_map)), F, k, pad, _dblp(K),
+        self._chk(load().fheon_conv_prepare(self.h, ctypes.byref(self._map(in_map)), F, k, stride, pad, _dblp(K),
                                             _dblp(b) if b is not None else None, level, float(in_scale),
                                             ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)

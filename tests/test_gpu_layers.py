@@ -96,6 +96,25 @@ def test_fc_plan_bit_exact(pair):
     assert pair.g.layer_rotation_steps(layer) == steps
 
 
+def test_strided_conv_bit_exact_and_from_weights(pair):
+    X = synth.image(84, 0, (2, 7, 7))
+    K = synth.conv_kernel(84, 1, (3, 2, 3, 3), std=0.3)
+    level = 6
+    v, ct, oct_ = _enc_map(pair, X, 1, 8400, level)
+    r, groups = OF.conv_plan(2, 3, 3, 1, 7, 7, GRID, 1, BLOCK, pair.N // 2, K, stride=2)
+    layer, op, okeys, keep = _linear_pair(pair, r, groups, level)
+    y = pair.g.layer_apply(layer, ct)
+    want = OF.linear_encrypted(pair.o, oct_, r, groups, op, okeys)
+    assert gpu_common.mismatch(pair.g.ct_download(y), want) == 0
+    # built from the weights on the device
+    L = pair.g.conv_prepare((2, 7, 7, GRID, 1, BLOCK), K, 1, level, pair.P["scale"], stride=2)
+    assert pair.g.layer_out_map(L) == (3, 4, 4, GRID, 2, BLOCK)
+    pair.add_keys(pair.g.layer_rotation_steps(L))
+    got = np.asarray(pair.g.decode(pair.g.decrypt(pair.sk, pair.g.layer_apply(L, ct)))).real
+    want = OF.conv2d_fp64(X, K, stride=2, pad=1)
+    assert np.max(np.abs(OF.unpack_map(got, want.shape, GRID, 2, BLOCK) - want)) < 1e-4
+
+
 def test_layers_from_weights_match_fp64(pair):
     """conv (valid, 1 -> 2) -> avgpool 2/2 -> conv (2 -> 3) on the stride-2 grid
     -> FC, each built from its weights on the device, decrypted against the

@@ -29,6 +29,19 @@ def test_conv_plan_is_the_convolution(C, F, k, pad, H, grid, dil):
     assert np.max(np.abs(y[rest])) == 0.0
 
 
+@pytest.mark.parametrize("C,F,k,pad,stride,H,grid,dil", [
+    (2, 3, 3, 1, 2, 8, 8, 1), (1, 2, 3, 0, 2, 9, 10, 1), (2, 2, 3, 1, 2, 6, 14, 2)])
+def test_strided_conv_plan(C, F, k, pad, stride, H, grid, dil):
+    block = dil * H * grid
+    nslots = 1 << int(np.ceil(np.log2(max(C, F) * block + 1)))
+    X = synth.image(16, C, (C, H, H), dist="normal")
+    K = synth.conv_kernel(16, F, (F, C, k, k))
+    r, groups = OF.conv_plan(C, F, k, pad, H, H, grid, dil, block, nslots, K, stride=stride)
+    y = OF.linear_slots(OF.pack_map(X, nslots, grid, dil, block), r, groups)
+    want = OF.conv2d_fp64(X, K, stride=stride, pad=pad)
+    assert np.max(np.abs(OF.unpack_map(y, want.shape, grid, dil * stride, block) - want)) < 1e-12
+
+
 @pytest.mark.parametrize("C,k,stride,H,grid,dil", [(2, 2, 2, 8, 8, 1), (3, 2, 2, 4, 12, 2), (1, 3, 1, 5, 6, 1)])
 def test_avgpool_plan_is_average_pooling(C, k, stride, H, grid, dil):
     block = dil * H * grid
