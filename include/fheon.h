@@ -55,6 +55,7 @@ extern "C" {
 #define FHEON_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
 #define FHEON_ERR_CUDA (-7)          /* a CUDA runtime call failed */
 #define FHEON_ERR_UNIMPLEMENTED (-8) /* not available in this build */
+#define FHEON_PENDING 1              /* not an error: the request is still running */
 
 typedef struct fheon_ctx fheon_ctx;
 typedef struct fheon_sk fheon_sk;
@@ -62,6 +63,8 @@ typedef struct fheon_pk fheon_pk;
 typedef struct fheon_pt fheon_pt;
 typedef struct fheon_ct fheon_ct;
 typedef struct fheon_layer fheon_layer;
+typedef struct fheon_model fheon_model;
+typedef struct fheon_server fheon_server;
 /* Packed layout of a feature map (C, H, W) in the slots: channel c in the
  * block at offset c * block; position (i, j) at c*block + dil*(i*grid + j).
  * `grid` is the row stride; `dil` the spacing of valid positions (a stride-s
@@ -423,11 +426,47 @@ int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const doub
 /* Apply any prepared layer (conv2d, ReLU, rotation-sum, FC); `in` at the
  * layer's level, out distinct from in. */
 int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
+/* The layer on n inputs at once (outputs distinct from every input and each
+ * other): a rotation-sum layer runs every input's tap rotations as one
+ * hoisted batch and every group shift as one batch, an FC layer the slot
+ * sums of all neurons of all inputs together; conv2d and ReLU layers run per
+ * input.  Each output equals the one fheon_layer_apply gives for its input
+ * alone, bit for bit. */
+int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *const *ins, uint32_t n,
+                            fheon_ct *const *outs);
 /* Rotation steps (keys) the layer uses: *n in = capacity of out (out may be
  * NULL to query), *n out = count; FHEON_ERR_ARG when out is too small. */
 int fheon_layer_rotation_steps(const fheon_layer *layer, int32_t *out, uint32_t *n);
 /* Output map of a conv, pooling or FC layer prepared from a map. */
 int fheon_layer_out_map(const fheon_layer *layer, fheon_map *out);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of inference requests                 */
+/* ------------------------------------------------------------------ */
+/* A model: the ordered layers of a network on one context (the layers stay
+ * owned by the caller and must outlive the model and its requests). */
+int fheon_model_create(fheon_ctx *ctx, const fheon_layer *const *layers, uint32_t n, fheon_model **out);
+int fheon_model_destroy(fheon_model *model);
+/* A server on the context's stream.  A submitted request is admitted while
+ * fewer than max_active are in flight and the device has at least min_free
+ * bytes free (0: no memory check; the oldest waiting request is admitted when
+ * none is in flight); the others wait in arrival order. */
+int fheon_server_create(fheon_ctx *ctx, uint32_t max_active, size_t min_free, fheon_server **out);
+int fheon_server_destroy(fheon_server *server);
+/* Queue a request: the model on a copy of `in` (taken on the stream now). */
+int fheon_server_submit(fheon_server *server, const fheon_model *model, const fheon_ct *in, uint64_t *id);
+/* One scheduling step: admit what fits, take the oldest admitted request's
+ * stage (model, next layer), apply that layer to every admitted request at
+ * that stage as one batch (fheon_layer_apply_batch), advance them, and wait
+ * for the stream.  *n_done: requests that finished in this step.  A result
+ * equals the model applied to the request's input alone, bit for bit. */
+int fheon_server_step(fheon_server *server, uint32_t *n_done);
+/* The result of request `id` into out (then the request is forgotten), or
+ * FHEON_PENDING while it runs; FHEON_ERR_ARG for an unknown id. */
+int fheon_server_result(fheon_server *server, uint64_t id, fheon_ct *out);
+/* Steps taken, the largest batch so far, requests in flight and waiting. */
+int fheon_server_stats(const fheon_server *server, uint64_t *steps, uint32_t *max_batch, uint32_t *active,
+                       uint32_t *waiting);
 
 /* ------------------------------------------------------------------ */
 /* Secure ReLU (paper Sec. 4.6, Alg. 4)                               */

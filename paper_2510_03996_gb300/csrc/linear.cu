@@ -66,7 +66,10 @@ int own_plain(fheon_ctx *ctx, fheon_layer *ly, const std::vector<double> &v, u32
     return FHEON_OK;
 }
 
-int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+// n inputs at once: every input's tap rotations in one hoisted plan (grouped by
+// input), every group shift of every input in one plain batch; the result of
+// each input is the one it gets alone
+int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs)
 {
     const u32 nt = (u32)ly->r.size(), ng = (u32)ly->s.size();
     std::vector<int32_t> steps;
@@ -76,60 +79,78 @@ int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheo
             idx[t] = (int)steps.size();
             steps.push_back(ly->r[t]);
         }
+    const u32 ns = (u32)steps.size();
     int rc;
-    if ((rc = ensure_cts(ctx, ly->rot, steps.size(), in->level, in->scale))) return rc;
-    if ((rc = ensure_cts(ctx, ly->work, 2 * (size_t)ng, in->level, in->scale))) return rc;
-    if ((rc = rotate_hoisted(ctx, in, steps.data(), (u32)steps.size(), ly->rot.data(), ly->collect))) return rc;
+    if ((rc = ensure_cts(ctx, ly->rot, (size_t)n * ns, ins[0]->level, ins[0]->scale))) return rc;
+    if ((rc = ensure_cts(ctx, ly->work, (size_t)n * 2 * ng, ins[0]->level, ins[0]->scale))) return rc;
+    std::vector<fheon_rot_item> items;
+    for (u32 i = 0; i < n; i++)
+        for (u32 k = 0; k < ns; k++) items.push_back(fheon_rot_item{ins[i], ly->rot[(size_t)i * ns + k], steps[k]});
+    if ((rc = rotate_many(ctx, items.data(), (u32)items.size(), true, ly->collect))) return rc;
     std::vector<const fheon_ct *> srcs;
     std::vector<const fheon_pt *> ps;
     std::vector<fheon_rot_item> moves;
-    for (u32 g = 0; g < ng; g++) {
-        srcs.clear();
-        ps.clear();
-        for (u32 t = 0; t < nt; t++) {
-            const fheon_pt *p = ly->pts[(size_t)g * nt + t];
-            if (!p) continue;
-            srcs.push_back(idx[t] < 0 ? in : ly->rot[idx[t]]);
-            ps.push_back(p);
+    for (u32 i = 0; i < n; i++) {
+        fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * ng;
+        for (u32 g = 0; g < ng; g++) {
+            srcs.clear();
+            ps.clear();
+            for (u32 t = 0; t < nt; t++) {
+                const fheon_pt *p = ly->pts[(size_t)g * nt + t];
+                if (!p) continue;
+                srcs.push_back(idx[t] < 0 ? ins[i] : ly->rot[(size_t)i * ns + idx[t]]);
+                ps.push_back(p);
+            }
+            if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), w[g]))) return rc;
+            if ((rc = fheon_rescale(ctx, w[g], w[g]))) return rc;
+            if (ly->s[g] != 0) moves.push_back(fheon_rot_item{w[g], w[ng + g], ly->s[g]});
         }
-        if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), ly->work[g]))) return rc;
-        if ((rc = fheon_rescale(ctx, ly->work[g], ly->work[g]))) return rc;
-        if (ly->s[g] != 0) moves.push_back(fheon_rot_item{ly->work[g], ly->work[ng + g], ly->s[g]});
     }
     if ((rc = rotate_many(ctx, moves.data(), (u32)moves.size(), false, ly->collect))) return rc;
-    auto term = [&](u32 g) { return ly->s[g] != 0 ? ly->work[ng + g] : ly->work[g]; };
-    if (ng == 1) {
-        if ((rc = fheon_drop_level(ctx, term(0), term(0)->level, out))) return rc;
-    } else {
-        if ((rc = fheon_add(ctx, term(0), term(1), out))) return rc;
-        for (u32 g = 2; g < ng; g++)
-            if ((rc = fheon_add(ctx, out, term(g), out))) return rc;
+    for (u32 i = 0; i < n; i++) {
+        fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * ng;
+        auto term = [&](u32 g) { return ly->s[g] != 0 ? w[ng + g] : w[g]; };
+        fheon_ct *out = outs[i];
+        if (ng == 1) {
+            if ((rc = fheon_drop_level(ctx, term(0), term(0)->level, out))) return rc;
+        } else {
+            if ((rc = fheon_add(ctx, term(0), term(1), out))) return rc;
+            for (u32 g = 2; g < ng; g++)
+                if ((rc = fheon_add(ctx, out, term(g), out))) return rc;
+        }
+        if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
     }
-    if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
     return FHEON_OK;
 }
 
-int fc_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+// n inputs at once: the slot sums of all neurons of all inputs rotate together
+int fc_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs)
 {
     const u32 m = (u32)ly->fw.size();
+    const size_t nm = (size_t)n * m;
     int rc;
-    if ((rc = ensure_cts(ctx, ly->work, 2 * (size_t)m, in->level, in->scale))) return rc;
-    for (u32 k = 0; k < m; k++) {
-        if ((rc = fheon_mul_plain(ctx, in, ly->fw[k], ly->work[k]))) return rc;
-        if ((rc = fheon_rescale(ctx, ly->work[k], ly->work[k]))) return rc;
-    }
-    std::vector<fheon_rot_item> items(m);
+    if ((rc = ensure_cts(ctx, ly->work, 2 * nm, ins[0]->level, ins[0]->scale))) return rc;
+    fheon_ct *const *t = ly->work.data(), *const *u = ly->work.data() + nm;
+    for (u32 i = 0; i < n; i++)
+        for (u32 k = 0; k < m; k++) {
+            fheon_ct *x = t[(size_t)i * m + k];
+            if ((rc = fheon_mul_plain(ctx, ins[i], ly->fw[k], x))) return rc;
+            if ((rc = fheon_rescale(ctx, x, x))) return rc;
+        }
+    std::vector<fheon_rot_item> items(nm);
     for (u32 st = 1; st < ly->nslots; st <<= 1) {
-        for (u32 k = 0; k < m; k++) items[k] = fheon_rot_item{ly->work[k], ly->work[m + k], (int32_t)st};
-        if ((rc = rotate_many(ctx, items.data(), m, false, ly->collect))) return rc;
-        for (u32 k = 0; k < m; k++)
-            if ((rc = fheon_add(ctx, ly->work[k], ly->work[m + k], ly->work[k]))) return rc;
+        for (size_t x = 0; x < nm; x++) items[x] = fheon_rot_item{t[x], u[x], (int32_t)st};
+        if ((rc = rotate_many(ctx, items.data(), (u32)nm, false, ly->collect))) return rc;
+        for (size_t x = 0; x < nm; x++)
+            if ((rc = fheon_add(ctx, t[x], u[x], t[x]))) return rc;
     }
-    std::vector<const fheon_ct *> ts(ly->work.begin(), ly->work.begin() + m);
     std::vector<const fheon_pt *> es(ly->fe.begin(), ly->fe.end());
-    if ((rc = fheon_mac_plain(ctx, ts.data(), es.data(), m, out))) return rc;
-    if ((rc = fheon_rescale(ctx, out, out))) return rc;
-    if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
+    for (u32 i = 0; i < n; i++) {
+        std::vector<const fheon_ct *> ts(t + (size_t)i * m, t + (size_t)(i + 1) * m);
+        if ((rc = fheon_mac_plain(ctx, ts.data(), es.data(), m, outs[i]))) return rc;
+        if ((rc = fheon_rescale(ctx, outs[i], outs[i]))) return rc;
+        if (ly->bias && (rc = fheon_add_plain(ctx, outs[i], ly->bias, outs[i]))) return rc;
+    }
     return FHEON_OK;
 }
 
@@ -327,14 +348,40 @@ int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const doub
 int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
     if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
+    return fheon_layer_apply_batch(ctx, ly, &in, 1, &out);
+}
+
+int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, uint32_t n,
+                            fheon_ct *const *outs)
+{
+    if (!ctx || !ly || (n && (!ins || !outs))) return FHEON_ERR_ARG;
+    if (n == 0) return FHEON_OK;
+    std::set<const void *> in_set;
+    for (u32 i = 0; i < n; i++) {
+        if (!ins[i] || !outs[i]) return fail(ctx, FHEON_ERR_ARG, "layer batch: null ciphertext %u", i);
+        in_set.insert(ins[i]);
+    }
+    std::set<const void *> out_set;
+    for (u32 i = 0; i < n; i++) {
+        if (in_set.count(outs[i])) return fail(ctx, FHEON_ERR_ARG, "layer output %u aliases an input", i);
+        if (!out_set.insert(outs[i]).second) return fail(ctx, FHEON_ERR_ARG, "layer output %u repeated", i);
+    }
+    int rc;
     switch (ly->kind) {
-    case LAYER_CONV: return fheon_conv2d_apply(ctx, ly, in, out);
-    case LAYER_RELU: return fheon_relu_apply(ctx, ly, in, out);
+    case LAYER_CONV:
+        for (u32 i = 0; i < n; i++)
+            if ((rc = fheon_conv2d_apply(ctx, ly, ins[i], outs[i]))) return rc;
+        return FHEON_OK;
+    case LAYER_RELU:
+        for (u32 i = 0; i < n; i++)
+            if ((rc = fheon_relu_apply(ctx, ly, ins[i], outs[i]))) return rc;
+        return FHEON_OK;
     default: break;
     }
-    if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "layer expects level %u, got %u", ly->level, in->level);
-    if (out == in) return fail(ctx, FHEON_ERR_ARG, "layer output must not alias its input");
-    return ly->kind == LAYER_LINEAR ? linear_apply(ctx, ly, in, out) : fc_apply(ctx, ly, in, out);
+    for (u32 i = 0; i < n; i++)
+        if (ins[i]->level != ly->level)
+            return fail(ctx, FHEON_ERR_LEVEL, "layer expects level %u, got %u", ly->level, ins[i]->level);
+    return ly->kind == LAYER_LINEAR ? linear_apply(ctx, ly, ins, n, outs) : fc_apply(ctx, ly, ins, n, outs);
 }
 
 int fheon_layer_rotation_steps(const fheon_layer *ly, int32_t *out, uint32_t *n)

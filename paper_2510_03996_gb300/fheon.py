@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libfheon.so")
 
 FHEON_OK = 0
 NUM_SCHEDULES = 16  # FHEON_NUM_SCHEDULES
+PENDING = 1  # FHEON_PENDING
 ERRORS = {-1: "FHEON_ERR_ARG", -2: "FHEON_ERR_OOM", -3: "FHEON_ERR_NO_KEY", -4: "FHEON_ERR_LEVEL",
           -5: "FHEON_ERR_SCALE", -6: "FHEON_ERR_TIMEOUT", -7: "FHEON_ERR_CUDA", -8: "FHEON_ERR_UNIMPLEMENTED"}
 
@@ -103,6 +104,15 @@ SIGNATURES = {
     "fheon_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_vpp],
     "fheon_fc_prepare": [c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_layer_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_layer_apply_batch": [c_vp, c_vp, P(c_vp), c_u32, P(c_vp)],
+    "fheon_model_create": [c_vp, P(c_vp), c_u32, c_vpp],
+    "fheon_model_destroy": [c_vp],
+    "fheon_server_create": [c_vp, c_u32, c_sz, c_vpp],
+    "fheon_server_destroy": [c_vp],
+    "fheon_server_submit": [c_vp, c_vp, c_vp, P(c_u64)],
+    "fheon_server_step": [c_vp, P(c_u32)],
+    "fheon_server_result": [c_vp, c_u64, c_vp],
+    "fheon_server_stats": [c_vp, P(c_u64), P(c_u32), P(c_u32), P(c_u32)],
     "fheon_layer_rotation_steps": [c_vp, P(c_i32), P(c_u32)],
     "fheon_layer_out_map": [c_vp, P(fheon_map)],
     "fheon_relu_prepare": [c_vp, c_dbl, c_u32, c_u32, c_u32, c_vpp],
@@ -524,6 +534,28 @@ class Context:
         self._chk(load().fheon_layer_apply(self.h, layer.h, ct.h, out.h))
         return out
 
+    def layer_apply_batch(self, layer, cts, outs=None):
+        outs = outs or [self.ct_create(1) for _ in cts]
+        n = len(cts)
+        ii = (c_vp * n)(*[c.h.value for c in cts])
+        oo = (c_vp * n)(*[o.h.value for o in outs])
+        self._chk(load().fheon_layer_apply_batch(self.h, layer.h, ii, n, oo))
+        return outs
+
+    def model(self, layers):
+        n = len(layers)
+        arr = (c_vp * n)(*[x.h.value for x in layers])
+        h = c_vp()
+        self._chk(load().fheon_model_create(self.h, arr, n, ctypes.byref(h)))
+        m = Handle(h, load().fheon_model_destroy)
+        m.layers = list(layers)  # the layers outlive the model
+        return m
+
+    def server(self, max_active, min_free=0):
+        h = c_vp()
+        self._chk(load().fheon_server_create(self.h, max_active, min_free, ctypes.byref(h)))
+        return Server(self, Handle(h, load().fheon_server_destroy))
+
     @staticmethod
     def layer_rotation_steps(layer):
         n = c_u32(0)
@@ -637,6 +669,43 @@ class Context:
         out = out or self.ct_create(1)
         self._chk(load().fheon_conv2d(self.h, ct.h, in_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b), out.h))
         return out
+
+
+class Server:
+    """Continuous-batching server (fheon_server_*)."""
+
+    def __init__(self, ctx, handle):
+        self.ctx, self.handle = ctx, handle
+        self.models = []
+
+    def submit(self, model, ct):
+        rid = c_u64()
+        self.ctx._chk(load().fheon_server_submit(self.handle.h, model.h, ct.h, ctypes.byref(rid)))
+        self.models.append(model)
+        return rid.value
+
+    def step(self):
+        n = c_u32()
+        self.ctx._chk(load().fheon_server_step(self.handle.h, ctypes.byref(n)))
+        return n.value
+
+    def result(self, rid, out=None):
+        """The result ciphertext, or None while the request runs."""
+        out = out or self.ctx.ct_create(1)
+        rc = load().fheon_server_result(self.handle.h, rid, out.h)
+        if rc == PENDING:
+            return None
+        self.ctx._chk(rc)
+        return out
+
+    def stats(self):
+        st, mb, a, w = c_u64(), c_u32(), c_u32(), c_u32()
+        check(load().fheon_server_stats(self.handle.h, ctypes.byref(st), ctypes.byref(mb), ctypes.byref(a),
+                                        ctypes.byref(w)))
+        return {"steps": st.value, "max_batch": mb.value, "active": a.value, "waiting": w.value}
+
+    def close(self):
+        self.handle.close()
 
 
 class Handle:
