@@ -425,3 +425,77 @@ def lenet_fp64(X, w, betas=None, D=RELU_DEGREE):
         if i < 2:
             h = act(h, 2 + i)
     return h
+
+
+def fold_offsets(C, H, W, grid, dil, block):
+    """Where the fold puts channel c inside block 0: at row offset c // dil and
+    column offset c % dil of the dilation grid, so the channels interleave.
+    Only when every channel fits (C <= dil^2, dil*W <= grid) and the folded
+    region stays inside the block; else None (no fold).  Rot_{f_c} also moves
+    every other channel c' to block c' - c, which the layer never reads."""
+    if dil < 2 or C > dil * dil or dil * W > grid:
+        return None
+    off = [(c % dil) + grid * (c // dil) for c in range(C)]
+    if max(off) + dil * ((H - 1) * grid + (W - 1)) >= block:
+        return None
+    return off
+
+
+def fc_diag_plan(Wmat, C, H, W, grid, dil, block, nslots):
+    """Fully connected layer (Sec. 4.5 equation) in diagonal form.
+    Fold (when fold_offsets allows it): x' = sum_c Rot_{f_c}(x),
+    f_c = c*block - off_c, brings channel c's values (zero elsewhere) to
+    off_c + dil*(i*grid + j) in block 0.  Then y[k] = sum_d diag_d[k] x'[k + d] with
+    diag_d[k] = W[k, t] where input t sits at slot k + d; baby-step giant-step:
+    d = e_g + a (a < b, e_g = d_min + g*b), so y = sum_g Rot_{e_g}( sum_a
+    Rot_{-e_g}(diag_d) * Rot_a(x') ).  Returns (fold shifts, r, groups) with the
+    rotation-sum conventions of `conv_plan`."""
+    Wmat = np.asarray(Wmat, dtype=np.float64)
+    m, n_in = Wmat.shape
+    assert n_in == C * H * W
+    off = fold_offsets(C, H, W, grid, dil, block)
+    fold = [c * block - off[c] for c in range(C)] if off else []
+    off = off or [c * block for c in range(C)]
+    slots = [off[c] + dil * (i * grid + j) for c in range(C) for i in range(H) for j in range(W)]
+    assert len(set(slots)) == len(slots)
+    dmin = min(slots) - (m - 1)
+    dmax = max(slots)
+    span = dmax - dmin + 1
+    b = int(np.ceil(np.sqrt(span)))
+    ng = (span + b - 1) // b
+    r = list(range(b))
+    groups = []
+    for g in range(ng):
+        e = dmin + g * b
+        vals = []
+        for a in range(b):
+            d = e + a
+            diag = np.zeros(nslots)
+            for t, st in enumerate(slots):
+                k = st - d
+                if 0 <= k < m:
+                    diag[k] = Wmat[k, t]
+            vals.append(np.roll(diag, e) if np.any(diag != 0.0) else None)
+        if any(v is not None for v in vals):
+            groups.append((e, vals))
+    return fold, r, groups
+
+
+def fold_slots(v, fold):
+    if not fold:
+        return v
+    return sum(np.roll(v, -f) for f in fold)
+
+
+def fold_encrypted(ctx, ct, fold, keys):
+    """x' = sum_c Rot_{f_c}(ct), the rotations hoisted from ct, summed in order."""
+    if not fold:
+        return ct
+    N = ctx.N
+    steps = [f for f in fold if f != 0]
+    hs = dict(zip(steps, ctx.rotate_hoisted(ct, [ckks.galois_elt(f, N) for f in steps], [keys[f] for f in steps])))
+    y = None
+    for f in fold:
+        t = ct if f == 0 else hs[f]
+        y = t if y is None else ctx.add(y, t)
+    return y

@@ -70,6 +70,21 @@ def test_fc_plan_is_the_product():
     assert np.max(np.abs(t - v.sum())) < 1e-12
 
 
+@pytest.mark.parametrize("C,H,grid,dil,m", [(16, 4, 28, 4, 12), (3, 5, 12, 2, 7), (1, 10, 10, 1, 5), (5, 3, 8, 2, 4)])
+def test_fc_diag_plan_is_the_product(C, H, grid, dil, m):
+    block = dil * H * grid
+    nslots = 1 << int(np.ceil(np.log2(C * block + 1)))
+    X = synth.image(17, C, (C, H, H), dist="normal")
+    Wm = synth.image(17, 99, (m, C * H * H), dist="normal")
+    v = OF.pack_map(X, nslots, grid, dil, block)
+    fold, r, groups = OF.fc_diag_plan(Wm, C, H, H, grid, dil, block, nslots)
+    y = OF.linear_slots(OF.fold_slots(v, fold), r, groups)
+    assert np.max(np.abs(y[:m] - Wm @ X.reshape(-1))) < 1e-12
+    assert np.max(np.abs(y[m:])) < 1e-12
+    # far fewer rotations than one slot sum per neuron
+    assert len(OF.linear_steps(r, groups)) + len(fold) < m * int(np.log2(nslots))
+
+
 def test_chained_layers_on_dilated_grids():
     """conv (valid) -> avgpool 2/2 -> conv on the stride-2 grid -> FC, as the
     slot model, against the FP64 chain."""
@@ -133,3 +148,24 @@ def test_encrypted_linear_plans_match_the_slot_model(ctx11):
     got = ctx.decode_ct(se, z, D).real
     want = OF.fc_slots(OF.linear_slots(v, r, groups), ws, es)
     assert np.max(np.abs(got - want)) < 1e-4
+
+
+def test_encrypted_fc_diag_matches_the_product(ctx11):
+    ctx, P, se, pk = ctx11
+    N, n, D = ctx.N, ctx.N // 2, P["scale"]
+    C, H, grid, dil, block, m = 4, 3, 8, 2, 64, 6
+    X = synth.image(18, 0, (C, H, H))
+    Wm = synth.image(18, 1, (m, C * H * H), dist="normal") * 0.2
+    v = OF.pack_map(X, n, grid, dil, block)
+    lv = 5
+    ct = ctx.drop_level(ctx.encrypt(pk, ckks.encode(v, N, D), 5), lv)
+    fold, r, groups = OF.fc_diag_plan(Wm, C, H, H, grid, dil, block, n)
+    assert fold
+    steps = sorted(set(OF.linear_steps(r, groups)) | {f for f in fold if f})
+    keys = {s: ctx.rotkey(se, ckks.galois_elt(s, N)) for s in steps}
+    pts = [[_plain(ctx, p, lv) if p is not None else None for p in vals] for _, vals in groups]
+    y = OF.linear_encrypted(ctx, OF.fold_encrypted(ctx, ct, fold, keys), r, groups, pts, keys)
+    assert y.shape[1] == lv - 1
+    got = ctx.decode_ct(se, y, D).real
+    assert np.max(np.abs(got[:m] - Wm @ X.reshape(-1))) < 1e-4
+    assert np.max(np.abs(got[m:])) < 1e-4
