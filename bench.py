@@ -293,6 +293,61 @@ def lenet_timing(F, batch=32):
             "max_abs_logit_vs_fp64_exact_relu": err, "relu_bounds": betas, "levels": len(P["qbits"])}
 
 
+def serving_timing(F, n_req=40, rate=4.0, max_active=8):
+    """The serving workload with LeNet-5 requests: Poisson arrivals (exponential
+    gaps of mean 1/rate s from a seed), requests submitted to the
+    continuous-batching server when their arrival time has passed (host
+    clock), one server step at a time; latency = completion - arrival."""
+    import torch
+    from paper_2510_03996_gb300 import lenet
+    P = synth.params("lenet_n15")
+    N = 1 << P["logN"]
+    s = torch.cuda.Stream()
+    ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                    stream=s.cuda_stream)
+    w = lenet.weights(P["seed"])
+    xs = [synth.image(P["seed"], 800 + i, (1, 28, 28)) for i in range(n_req)]
+    betas = lenet.relu_bounds(xs, w)
+    sk, pk = ctx.keygen()
+    ctx.relinkeygen(sk)
+    net = lenet.EncryptedLeNet(ctx, w, betas, ctx.L, P["scale"])
+    ctx.rotkeygen(sk, net.rotation_steps())
+    cts = [ctx.encrypt(pk, ctx.encode(lenet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i)
+           for i, X in enumerate(xs)]
+    model = ctx.model(net.layers)
+    net.forward(cts[0])  # warm-up
+    ctx.sync()
+    gaps = synth.rng(P["seed"], 801).exponential(1.0 / rate, n_req)
+    arrive = np.cumsum(gaps) - gaps[0]
+    srv = ctx.server(max_active=max_active)
+    t0 = time.perf_counter()
+    ids, done = {}, {}
+    nxt = 0
+    while len(done) < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrive[nxt] <= now:
+            ids[nxt] = srv.submit(model, cts[nxt])
+            nxt += 1
+        if len(ids) == len(done):
+            time.sleep(max(0.0, min(0.01, arrive[nxt] - now)))
+            continue
+        if srv.step():
+            now = time.perf_counter() - t0
+            for k, rid in ids.items():
+                if k not in done and srv.result(rid) is not None:
+                    done[k] = now
+    lat = np.array([done[k] - arrive[k] for k in range(n_req)])
+    span = max(done.values()) - arrive[0]
+    st = srv.stats()
+    srv.close()
+    del cts, net, model, sk, pk
+    ctx.close()
+    return {"requests": n_req, "arrival_rate_per_s": rate, "models": "LeNet-5 (N=2^15) only",
+            "throughput_per_s": n_req / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_batch": st["max_batch"], "steps": st["steps"],
+            "max_active": max_active}
+
+
 def conv_layer_timing(F, iters=200):
     """Packed special conv of the 1x28x28, 5x5, pad 2 layer at N = 2^13 (24 tap
     rotations + 25 plaintext products + one rescale), eager and as a replayed
@@ -448,7 +503,8 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_comparisons:
         comparisons = {"per_ciphertext_path": per_ciphertext_rate(ctx, ins, outs, steps, stream),
                        "conv_n13_layer": conv_layer_timing(F),
-                       "lenet5_n15": lenet_timing(F)}
+                       "lenet5_n15": lenet_timing(F),
+                       "serving_lenet5": serving_timing(F, n_req=args.serve_requests)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -486,6 +542,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparisons", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--schedule", type=int, default=-1,
                     help="key-switching schedule bits (default: the library's autotuner picks)")
     args = ap.parse_args()

@@ -384,7 +384,8 @@ int fheon_layer_destroy(fheon_layer *layer);
 /* Packed network layers on a fheon_map (paper Sec. 4.1, 4.4, 4.5)     */
 /* ------------------------------------------------------------------ */
 /* Rotation-sum layer from the caller's plaintexts:
- *   out = sum_g Rot_{s[g]}( rescale( sum_t Rot_{r[t]}(in) * pts[g*nt + t] ) ) (+ bias)
+ *   x'  = sum_c Rot_{fold[c]}(in)   (nf > 0; the nf rotations hoisted from in)
+ *   out = sum_g Rot_{s[g]}( rescale( sum_t Rot_{r[t]}(x') * pts[g*nt + t] ) ) (+ bias)
  * The nt tap rotations (distinct steps; 0 = the input itself) are hoisted
  * from the input; each group's products are summed in one pass and rescaled
  * once; the ng group sums move by one batched rotation (s[g] = 0: none) and are
@@ -392,9 +393,9 @@ int fheon_layer_destroy(fheon_layer *layer);
  * be NULL (no product); each group needs one.  Plaintexts at `level` or above,
  * encoded at scale q_{level-1}; they stay owned by the caller and must outlive
  * the layer.  Output level: level - 1. */
-int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nt, const int32_t *r, uint32_t ng, const int32_t *s,
-                               const fheon_pt *const *pts, const fheon_pt *bias, uint32_t level,
-                               fheon_layer **out);
+int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nf, const int32_t *fold, uint32_t nt, const int32_t *r,
+                               uint32_t ng, const int32_t *s, const fheon_pt *const *pts, const fheon_pt *bias,
+                               uint32_t level, fheon_layer **out);
 /* Fully connected layer from the caller's plaintexts (Sec. 4.5): t_k =
  * rescale(in * W[k]) for each of the m neurons; each t_k summed over all N/2
  * slots by rotate-and-add (steps 1, 2, ..., N/4, batched over the neurons);
@@ -418,9 +419,13 @@ int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t
  * place: the output map's dilation is the input's times `stride`. */
 int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint32_t stride, uint32_t level,
                           fheon_layer **out);
-/* Fully connected layer (Sec. 4.5): W[m][C*H*W] over the map's values in
- * (c, i, j) order, bias[m] (or NULL); output: the m neurons in slots [0, m)
- * (map {1, 1, m, m, 1, m}).  Output level: level - 2, scale in_scale. */
+/* Fully connected layer (Sec. 4.5 equation): W[m][C*H*W] over the map's
+ * values in (c, i, j) order, bias[m] (or NULL); output: the m neurons in slots
+ * [0, m) (map {1, 1, m, m, 1, m}).  A rotation-sum layer in diagonal form:
+ * when the channels interleave on the dilation grid (C <= dil^2) they are
+ * first folded into block 0 (x' = sum_c Rot_{c*block - off_c}(in)); then
+ * y[k] = sum_d diag_d[k] x'[k + d] by baby-step giant-step over the span of
+ * d (about 2 sqrt(span) rotations).  Output level: level - 1, scale in_scale. */
 int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
                      uint32_t level, double in_scale, fheon_layer **out);
 /* Apply any prepared layer (conv2d, ReLU, rotation-sum, FC); `in` at the

@@ -21,6 +21,7 @@ struct fheon_layer {
     // s_g, plaintexts [g][t] (null: no product); FC: weight and placement
     // plaintexts of each output neuron, the slots summed over
     std::vector<int32_t> r, s;
+    std::vector<int32_t> fold; // rotation-sum layer: the input first becomes sum_c Rot_{fold[c]}(in)
     std::vector<fheon_pt *> pts, fw, fe;   // views
     std::vector<fheon_pt *> pt_store;       // the plaintexts the layer owns
     u32 nslots = 0;
@@ -35,7 +36,7 @@ struct fheon_layer {
     // on the first application and reused, so that later applications (and
     // their graph capture) allocate nothing
     mutable std::vector<fheon_ct *> rot;
-    mutable std::vector<fheon_ct *> work;
+    mutable std::vector<fheon_ct *> work, fwork;
     mutable fheon_ct *tmp[3] = {nullptr, nullptr, nullptr};
     // captured applications, keyed by the buffers the captured launches use;
     // `keep` holds the device rotation plans those launches read
@@ -57,6 +58,7 @@ struct fheon_layer {
         for (fheon_ct *c : tmp) fheon_ct_destroy(c);
         for (fheon_ct *c : rot) fheon_ct_destroy(c);
         for (fheon_ct *c : work) fheon_ct_destroy(c);
+        for (fheon_ct *c : fwork) fheon_ct_destroy(c);
         for (fheon_pt *p : pt_store) fheon_pt_destroy(p);
     }
 };

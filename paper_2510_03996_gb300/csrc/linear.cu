@@ -21,6 +21,7 @@
 // slots); every t_k through the rotate-and-add slot sum (steps 1, 2, 4, ...,
 // N/4: the total lands in every slot); out = rescale(sum_k t_k * E_k), E_k one
 // at slot k.  The output map is the compact vector of the m neurons.
+#include <algorithm>
 #include <cmath>
 #include <memory>
 #include <set>
@@ -69,9 +70,33 @@ int own_plain(fheon_ctx *ctx, fheon_layer *ly, const std::vector<double> &v, u32
 // n inputs at once: every input's tap rotations in one hoisted plan (grouped by
 // input), every group shift of every input in one plain batch; the result of
 // each input is the one it gets alone
-int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs)
+int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins_, u32 n, fheon_ct *const *outs)
 {
-    const u32 nt = (u32)ly->r.size(), ng = (u32)ly->s.size();
+    const u32 nt = (u32)ly->r.size(), ng = (u32)ly->s.size(), nf = (u32)ly->fold.size();
+    std::vector<const fheon_ct *> ins(ins_, ins_ + n);
+    int rc;
+    if (nf) {
+        // fold: x' = sum_c Rot_{fold[c]}(x), the rotations hoisted from x
+        if ((rc = ensure_cts(ctx, ly->fwork, (size_t)n * (nf + 1), ins[0]->level, ins[0]->scale))) return rc;
+        std::vector<fheon_rot_item> fi;
+        for (u32 i = 0; i < n; i++)
+            for (u32 c = 0; c < nf; c++)
+                if (ly->fold[c]) fi.push_back(fheon_rot_item{ins[i], ly->fwork[(size_t)i * (nf + 1) + c], ly->fold[c]});
+        if ((rc = rotate_many(ctx, fi.data(), (u32)fi.size(), true, ly->collect))) return rc;
+        for (u32 i = 0; i < n; i++) {
+            fheon_ct *const *fw = ly->fwork.data() + (size_t)i * (nf + 1);
+            auto part = [&](u32 c) -> const fheon_ct * { return ly->fold[c] ? fw[c] : ins[i]; };
+            fheon_ct *sum = fw[nf];
+            if (nf == 1) {
+                if ((rc = fheon_drop_level(ctx, part(0), part(0)->level, sum))) return rc;
+            } else {
+                if ((rc = fheon_add(ctx, part(0), part(1), sum))) return rc;
+                for (u32 c = 2; c < nf; c++)
+                    if ((rc = fheon_add(ctx, sum, part(c), sum))) return rc;
+            }
+            ins[i] = sum;
+        }
+    }
     std::vector<int32_t> steps;
     std::vector<int> idx(nt, -1);
     for (u32 t = 0; t < nt; t++)
@@ -80,7 +105,6 @@ int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *i
             steps.push_back(ly->r[t]);
         }
     const u32 ns = (u32)steps.size();
-    int rc;
     if ((rc = ensure_cts(ctx, ly->rot, (size_t)n * ns, ins[0]->level, ins[0]->scale))) return rc;
     if ((rc = ensure_cts(ctx, ly->work, (size_t)n * 2 * ng, ins[0]->level, ins[0]->scale))) return rc;
     std::vector<fheon_rot_item> items;
@@ -164,10 +188,12 @@ int check_pt(fheon_ctx *ctx, const fheon_pt *p, u32 level, const char *what)
 
 extern "C" {
 
-int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nt, const int32_t *r, uint32_t ng, const int32_t *s,
-                               const fheon_pt *const *pts, const fheon_pt *bias, uint32_t level, fheon_layer **out)
+int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nf, const int32_t *fold, uint32_t nt, const int32_t *r,
+                               uint32_t ng, const int32_t *s, const fheon_pt *const *pts, const fheon_pt *bias,
+                               uint32_t level, fheon_layer **out)
 {
-    if (!ctx || !out || !nt || !ng || !r || !s || !pts || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    if (!ctx || !out || !nt || !ng || !r || !s || !pts || (nf && !fold) || level < 2 || level > ctx->L)
+        return FHEON_ERR_ARG;
     std::set<int32_t> seen;
     for (u32 t = 0; t < nt; t++)
         if (!seen.insert(r[t]).second) return fail(ctx, FHEON_ERR_ARG, "linear: tap step %d repeated", r[t]);
@@ -187,6 +213,7 @@ int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nt, const int32_t *r, ui
     ly->level = level;
     ly->r.assign(r, r + nt);
     ly->s.assign(s, s + ng);
+    if (nf) ly->fold.assign(fold, fold + nf);
     for (size_t i = 0; i < (size_t)nt * ng; i++) ly->pts.push_back(const_cast<fheon_pt *>(pts[i]));
     ly->bias = const_cast<fheon_pt *>(bias);
     *out = ly.release();
@@ -308,38 +335,69 @@ int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint3
 int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
                      uint32_t level, double in_scale, fheon_layer **out)
 {
-    if (!ctx || !in || !out || !W || !m || m > ctx->N / 2 || level < 3 || level > ctx->L) return FHEON_ERR_ARG;
+    if (!ctx || !in || !out || !W || !m || m > ctx->N / 2 || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
     const fheon_map im = *in;
     if (!map_ok(ctx, im)) return fail(ctx, FHEON_ERR_ARG, "fc: map does not fit");
-    const u32 n = ctx->N / 2, nin = im.C * im.H * im.W;
+    const u32 n = ctx->N / 2, C = im.C, nin = C * im.H * im.W;
     std::unique_ptr<fheon_layer> ly(new fheon_layer());
-    ly->kind = LAYER_FC;
+    ly->kind = LAYER_LINEAR;
     ly->level = level;
-    ly->nslots = n;
     ly->in_map = im;
     ly->out_map = fheon_map{1, 1, m, m, 1, m};
-    std::vector<u32> slots;
-    for (u32 c = 0; c < im.C; c++)
+    // fold the channels into block 0 when they interleave on the dilation grid
+    std::vector<int64_t> off(C);
+    bool fold = im.dil >= 2 && C <= im.dil * im.dil && im.dil * im.W <= im.grid;
+    for (u32 c = 0; c < C && fold; c++) off[c] = (int64_t)(c % im.dil) + (int64_t)im.grid * (c / im.dil);
+    if (fold && off[C - 1] + (int64_t)im.dil * ((int64_t)(im.H - 1) * im.grid + (im.W - 1)) >= (int64_t)im.block)
+        fold = false;
+    for (u32 c = 0; c < C; c++) {
+        if (!fold) off[c] = (int64_t)c * im.block;
+        else ly->fold.push_back((int32_t)((int64_t)c * im.block - off[c]));
+    }
+    std::vector<int64_t> slot(nin);
+    for (u32 c = 0, t = 0; c < C; c++)
         for (u32 i = 0; i < im.H; i++)
-            for (u32 j = 0; j < im.W; j++) slots.push_back(map_slot(im, c, i, j));
+            for (u32 j = 0; j < im.W; j++) slot[t++] = off[c] + (int64_t)im.dil * ((int64_t)i * im.grid + j);
+    int64_t smin = slot[0], smax = slot[0];
+    for (int64_t v : slot) smin = std::min(smin, v), smax = std::max(smax, v);
+    // y[k] = sum_d diag_d[k] x'[k + d], d = e_g + a (baby steps a < b, giant steps e_g)
+    const int64_t dmin = smin - (int64_t)(m - 1), span = smax - dmin + 1;
+    const int64_t b = (int64_t)std::ceil(std::sqrt((double)span)), ng = (span + b - 1) / b;
+    for (int64_t a = 0; a < b; a++) ly->r.push_back((int32_t)a);
+    // inputs t by slot, to find the input at slot k + d
+    std::vector<int32_t> at((size_t)(smax - smin + 1), -1);
+    for (u32 t = 0; t < nin; t++) at[(size_t)(slot[t] - smin)] = (int32_t)t;
+    const double ps = (double)ctx->mod[level - 1];
     std::vector<double> v(n);
     int rc;
-    for (u32 k = 0; k < m; k++) {
-        std::fill(v.begin(), v.end(), 0.0);
-        for (u32 t = 0; t < nin; t++) v[slots[t]] = W[(size_t)k * nin + t];
-        fheon_pt *w = nullptr, *e = nullptr;
-        if ((rc = own_plain(ctx, ly.get(), v, level, (double)ctx->mod[level - 1], &w))) return rc;
-        std::fill(v.begin(), v.end(), 0.0);
-        v[k] = 1.0;
-        if ((rc = own_plain(ctx, ly.get(), v, level - 1, (double)ctx->mod[level - 2], &e))) return rc;
-        if (!w) return fail(ctx, FHEON_ERR_ARG, "fc: neuron %u has all-zero weights", k);
-        ly->fw.push_back(w);
-        ly->fe.push_back(e);
+    for (int64_t g = 0; g < ng; g++) {
+        const int64_t e = dmin + g * b;
+        std::vector<fheon_pt *> gp;
+        bool any = false;
+        for (int64_t a = 0; a < b; a++) {
+            const int64_t d = e + a;
+            std::fill(v.begin(), v.end(), 0.0);
+            for (u32 k = 0; k < m; k++) {
+                const int64_t sl = (int64_t)k + d;
+                if (sl < smin || sl > smax) continue;
+                const int32_t t = at[(size_t)(sl - smin)];
+                if (t < 0) continue;
+                // the plaintext is Rot_{-e}(diag_d): diag_d[k] lands at slot k + e
+                v[(size_t)((((int64_t)k + e) % (int64_t)n + (int64_t)n) % (int64_t)n)] = W[(size_t)k * nin + t];
+            }
+            fheon_pt *p = nullptr;
+            if ((rc = own_plain(ctx, ly.get(), v, level, ps, &p))) return rc;
+            gp.push_back(p);
+            any = any || p;
+        }
+        if (!any) continue;
+        ly->s.push_back((int32_t)e);
+        ly->pts.insert(ly->pts.end(), gp.begin(), gp.end());
     }
     if (bias) {
         std::fill(v.begin(), v.end(), 0.0);
         for (u32 k = 0; k < m; k++) v[k] = bias[k];
-        if ((rc = own_plain(ctx, ly.get(), v, level - 2, in_scale, &ly->bias))) return rc;
+        if ((rc = own_plain(ctx, ly.get(), v, level - 1, in_scale, &ly->bias))) return rc;
     }
     *out = ly.release();
     return FHEON_OK;
@@ -389,6 +447,8 @@ int fheon_layer_rotation_steps(const fheon_layer *ly, int32_t *out, uint32_t *n)
     if (!ly || !n) return FHEON_ERR_ARG;
     std::set<int32_t> st;
     if (ly->kind == LAYER_LINEAR) {
+        for (int32_t x : ly->fold)
+            if (x) st.insert(x);
         for (int32_t x : ly->r)
             if (x) st.insert(x);
         for (int32_t x : ly->s)

@@ -98,7 +98,8 @@ SIGNATURES = {
     "fheon_mul_const_rescale": [c_vp, c_vp, c_dbl, c_dbl, c_vp],
     "fheon_relinkeygen": [c_vp, c_vp],
     "fheon_relu_coeffs": [c_dbl, c_u32, P(c_dbl)],
-    "fheon_linear_prepare_plain": [c_vp, c_u32, P(c_i32), c_u32, P(c_i32), P(c_vp), c_vp, c_u32, c_vpp],
+    "fheon_linear_prepare_plain": [c_vp, c_u32, P(c_i32), c_u32, P(c_i32), c_u32, P(c_i32), P(c_vp), c_vp, c_u32,
+                                   c_vpp],
     "fheon_fc_prepare_plain": [c_vp, c_u32, P(c_vp), P(c_vp), c_vp, c_u32, c_vpp],
     "fheon_conv_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_vpp],
@@ -484,15 +485,16 @@ class Context:
     def _map(m):
         return m if isinstance(m, fheon_map) else fheon_map(*[int(x) for x in m])
 
-    def linear_prepare_plain(self, r, s, pts, level, bias=None):
+    def linear_prepare_plain(self, r, s, pts, level, bias=None, fold=()):
         """pts: [len(s)][len(r)] plaintexts or None."""
-        nt, ng = len(r), len(s)
+        nt, ng, nf = len(r), len(s), len(fold)
         rr = (c_i32 * nt)(*[int(x) for x in r])
         ss = (c_i32 * ng)(*[int(x) for x in s])
+        ff = (c_i32 * max(1, nf))(*[int(x) for x in fold])
         pp = (c_vp * (nt * ng))(*[(p.h.value if p is not None else None) for row in pts for p in row])
         h = c_vp()
-        self._chk(load().fheon_linear_prepare_plain(self.h, nt, rr, ng, ss, pp, bias.h if bias is not None else None,
-                                                    level, ctypes.byref(h)))
+        self._chk(load().fheon_linear_prepare_plain(self.h, nf, ff if nf else None, nt, rr, ng, ss, pp,
+                                                    bias.h if bias is not None else None, level, ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)
 
     def fc_prepare_plain(self, W, E, level, bias=None):

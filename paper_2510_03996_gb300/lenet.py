@@ -22,7 +22,7 @@ RELU_DEGREE = 59
 CONVS = [(6, 1, 5), (16, 6, 5)]
 FCS = [(120, 256), (84, 120), (10, 84)]
 # levels each layer uses (a ReLU: ceil(log2 59) + 1, + 1 for the mask when beta > 1)
-DEPTH = {"conv": 1, "pool": 1, "fc": 2, "relu": 8}
+DEPTH = {"conv": 1, "pool": 1, "fc": 1, "relu": 8}
 LEVELS = 2 * DEPTH["conv"] + 2 * DEPTH["pool"] + 3 * DEPTH["fc"] + 4 * DEPTH["relu"]  # at most
 
 

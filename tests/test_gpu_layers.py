@@ -115,6 +115,28 @@ def test_strided_conv_bit_exact_and_from_weights(pair):
     assert np.max(np.abs(OF.unpack_map(got, want.shape, GRID, 2, BLOCK) - want)) < 1e-4
 
 
+def test_fc_diag_bit_exact(pair):
+    """The diagonal FC with the channel fold (4 channels on the dilation-2 grid)."""
+    C, H, dil, m = 4, 3, 2, 6
+    X = synth.image(85, 0, (C, H, H))
+    Wm = synth.image(85, 1, (m, C * H * H), dist="normal") * 0.2
+    level = 5
+    v, ct, oct_ = _enc_map(pair, X, dil, 8500, level)
+    fold, r, groups = OF.fc_diag_plan(Wm, C, H, H, GRID, dil, BLOCK, pair.N // 2)
+    pair.add_keys([f for f in fold if f])
+    layer, op, okeys, keep = _linear_pair(pair, r, groups, level)
+    okeys.update({f: pair.okeys[pair.g.galois_elt(f)] for f in fold if f})
+    layer = pair.g.linear_prepare_plain(r, [s for s, _ in groups], keep, level, fold=fold)
+    y = pair.g.layer_apply(layer, ct)
+    want = OF.linear_encrypted(pair.o, OF.fold_encrypted(pair.o, oct_, fold, okeys), r, groups, op, okeys)
+    assert gpu_common.mismatch(pair.g.ct_download(y), want) == 0
+    # built from the weights on the device
+    L = pair.g.fc_prepare((C, H, H, GRID, dil, BLOCK), Wm, level, pair.P["scale"])
+    pair.add_keys(pair.g.layer_rotation_steps(L))
+    got = np.asarray(pair.g.decode(pair.g.decrypt(pair.sk, pair.g.layer_apply(L, ct)))).real
+    assert np.max(np.abs(got[:m] - Wm @ X.reshape(-1))) < 1e-4 and np.max(np.abs(got[m:])) < 1e-4
+
+
 def test_layers_from_weights_match_fp64(pair):
     """conv (valid, 1 -> 2) -> avgpool 2/2 -> conv (2 -> 3) on the stride-2 grid
     -> FC, each built from its weights on the device, decrypted against the
@@ -147,7 +169,7 @@ def test_layers_from_weights_match_fp64(pair):
     y = ct
     for layer in (L1, L2, L3, L4):
         y = g.layer_apply(layer, y)
-    assert g.ct_info(y)[0] == lv - 5
+    assert g.ct_info(y)[0] == lv - 4
     got = np.asarray(g.decode(g.decrypt(pair.sk, y))).real
     h = OF.conv2d_fp64(OF.avgpool_fp64(OF.conv2d_fp64(X, K1, b=b1), 2, 2), K2)
     want = Wm @ h.reshape(-1) + bf

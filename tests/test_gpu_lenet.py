@@ -27,8 +27,8 @@ def test_lenet_logits_match_fp64():
     ctx.relinkeygen(sk)
     net = lenet.EncryptedLeNet(ctx, w, betas, ctx.L, P["scale"])
     ctx.rotkeygen(sk, net.rotation_steps())
-    # two convs and two poolings (1 level each), three FC layers (2 each), four ReLUs
-    assert net.out_level == ctx.L - 4 - 6 - sum(lenet.relu_depth(b) for b in betas) and net.out_level >= 2
+    # two convs, two poolings and three FC layers (1 level each), four ReLUs
+    assert net.out_level == ctx.L - 7 - sum(lenet.relu_depth(b) for b in betas) and net.out_level >= 2
     for i, X in enumerate(xs):
         ct = ctx.encrypt(pk, ctx.encode(lenet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i)
         y = net.forward(ct)

@@ -29,7 +29,7 @@ def setup():
     m1 = g.layer_out_map(conv)
     relu = g.relu_prepare(2.0, 7, m1[0] * m1[5], lv - 1)         # depth 3 + 1 + 1
     pool = g.avgpool_prepare(m1, 2, 2, lv - 6)
-    fc = g.fc_prepare(g.layer_out_map(pool), Wm, lv - 7, D)
+    fc = g.fc_prepare(g.layer_out_map(pool), Wm, lv - 7, D)  # one level: ends at lv - 8
     layers = [conv, relu, pool, fc]
     for layer in layers:
         pr.add_keys(g.layer_rotation_steps(layer))
