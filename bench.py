@@ -275,21 +275,29 @@ def lenet_timing(F, batch=32):
     cts = [ctx.encrypt(pk, ctx.encode(lenet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i)
            for i, X in enumerate(xs)]
     net.forward(cts[0])  # warm-up: working ciphertexts, plans
+    net.forward_graph(cts[0])  # capture
     ctx.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s)
     outs = [net.forward(ct) for ct in cts]
     e1.record(s)
     torch.cuda.synchronize()
+    eager_secs = e0.elapsed_time(e1) / 1e3
+    e0.record(s)
+    gouts = [net.forward_graph(ct) for ct in cts]
+    e1.record(s)
+    torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
+    same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs[:2], gouts[:2]))
     err = 0.0
     for X, y in zip(xs, outs):
         got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
         err = max(err, float(np.max(np.abs(got - lenet.forward_fp64(X, w)))))
     nkeys, kbytes = ctx.key_stats()
-    del outs, cts, net, sk, pk
+    del outs, gouts, cts, net, sk, pk
     ctx.close()
-    return {"s_per_inference": secs / batch, "batch": batch, "keys": nkeys, "key_bytes": kbytes,
+    return {"s_per_inference": secs / batch, "eager_s_per_inference": eager_secs / batch,
+            "graph_equals_eager": same, "batch": batch, "keys": nkeys, "key_bytes": kbytes,
             "max_abs_logit_vs_fp64_exact_relu": err, "relu_bounds": betas, "levels": len(P["qbits"])}
 
 

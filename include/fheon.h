@@ -439,6 +439,13 @@ int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *
  * alone, bit for bit. */
 int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *const *ins, uint32_t n,
                             fheon_ct *const *outs);
+/* fheon_layer_apply replayed as a CUDA graph: the first call for a given
+ * (input buffer, output buffer, workspace, input level and scale) runs the
+ * layer eagerly, then captures the same launches on the context's stream
+ * (which must not be the legacy default stream) into a graph kept by the
+ * layer; later calls with the same key launch the graph.  Inputs with a new
+ * scale or level get their own graph. */
+int fheon_layer_apply_graph(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
 /* Rotation steps (keys) the layer uses: *n in = capacity of out (out may be
  * NULL to query), *n out = count; FHEON_ERR_ARG when out is too small. */
 int fheon_layer_rotation_steps(const fheon_layer *layer, int32_t *out, uint32_t *n);

@@ -332,6 +332,7 @@ struct DnAJob : JobCommon {
 // DNB: second forward pass; out = (acc - conv) * P^-1 (+ sigma_g(c0) for b = 0,
 // + c1add for b = 1 when given)
 struct DnBJob : JobCommon {
+    static constexpr int MIN_BLOCKS = 2;
     const u64 *mid, *acc, *c0i, *c1a;
     u64 *out;
     ulonglong2 pi;
@@ -368,6 +369,29 @@ struct DnBJob : JobCommon {
         if (b == 0) r = addmod(r, c0i[automorph_src(J, d->g, p.tp.logN)], m.q);
         else if (c1a) r = addmod(r, c1a[J], m.q);
         out[J] = r;
+    }
+    // the operands of 8 elements are loaded before any of their stores, so
+    // their latencies overlap (a store may alias a later load otherwise)
+    static constexpr bool TILE_STORE = true;
+    __device__ void store_tile_last(const u32 (&J)[ntt::R], const u64 (&y)[ntt::R], const ModConst &m) const
+    {
+        const bool add = b == 0 || c1a;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            u64 a[ntt::R / 2], c[ntt::R / 2];
+#pragma unroll
+            for (int v = 0; v < ntt::R / 2; v++) {
+                const u32 j = J[h * 8 + v];
+                a[v] = acc[j];
+                c[v] = b == 0 ? c0i[automorph_src(j, d->g, p.tp.logN)] : (c1a ? c1a[j] : 0);
+            }
+#pragma unroll
+            for (int v = 0; v < ntt::R / 2; v++) {
+                u64 r = shoup(a[v] + m.q - y[h * 8 + v], pi.x, pi.y, m.q);
+                if (add) r = addmod(r, c[v], m.q);
+                out[J[h * 8 + v]] = r;
+            }
+        }
     }
 };
 

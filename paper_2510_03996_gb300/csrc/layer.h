@@ -43,6 +43,9 @@ struct fheon_layer {
     struct Graph {
         const void *in, *out, *ws;
         u32 level;
+        double scale;           // the input's scale (captured constants depend on it)
+        u32 out_level;          // the output's metadata the captured run set
+        double out_scale;
         cudaGraphExec_t exec;
         fheon::PlanKeep keep;
     };

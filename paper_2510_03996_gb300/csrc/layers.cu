@@ -188,25 +188,30 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in
 int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
     if (!ctx || !ly || !in || !out || ly->kind != LAYER_CONV) return FHEON_ERR_ARG;
+    return fheon_layer_apply_graph(ctx, ly, in, out);
+}
+
+int fheon_layer_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
     if (!ctx->stream) return fail(ctx, FHEON_ERR_ARG, "graph capture needs a created stream, not the legacy default stream");
     for (auto &g : ly->graphs)
-        if (g.in == in->c.p && g.out == out->c.p && g.ws == ctx->ws.p && g.level == in->level) {
+        if (g.in == in->c.p && g.out == out->c.p && g.ws == ctx->ws.p && g.level == in->level && g.scale == in->scale) {
             FHEON_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
-            // the host-side metadata the captured run set
-            out->level = ly->level - (ly->in_ch > 1 ? 2 : 1);
-            out->scale = in->scale;
+            out->level = g.out_level; // the host-side metadata the captured run set
+            out->scale = g.out_scale;
             return FHEON_OK;
         }
-    // eager run: sizes the output, the temporaries and the workspace
-    int rc = fheon_conv2d_apply(ctx, ly, in, out);
+    // eager run: sizes the output, the working ciphertexts and the workspace
+    int rc = fheon_layer_apply(ctx, ly, in, out);
     if (rc) return rc;
-    if (out->cap < out->level) return fail(ctx, FHEON_ERR_ARG, "output too small");
+    const void *ws = ctx->ws.p;
     // capture the identical launch sequence (it allocates nothing now; the
     // rotation plans it reads are held by the graph entry)
     PlanKeep keep;
     FHEON_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     ly->collect = &keep;
-    rc = fheon_conv2d_apply(ctx, ly, in, out);
+    rc = fheon_layer_apply(ctx, ly, in, out);
     ly->collect = nullptr;
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
@@ -215,11 +220,16 @@ int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_
         return rc;
     }
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+    if (ctx->ws.p != ws) {
+        cudaGraphDestroy(graph);
+        return fail(ctx, FHEON_ERR_ARG, "workspace moved during capture");
+    }
     cudaGraphExec_t exec = nullptr;
     ce = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
-    ly->graphs.push_back(fheon_layer::Graph{in->c.p, out->c.p, ctx->ws.p, in->level, exec, std::move(keep)});
+    ly->graphs.push_back(fheon_layer::Graph{in->c.p, out->c.p, ctx->ws.p, in->level, in->scale, out->level,
+                                            out->scale, exec, std::move(keep)});
     return FHEON_OK;
 }
 

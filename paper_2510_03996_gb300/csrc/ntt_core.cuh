@@ -95,6 +95,10 @@ struct JobBase {
     __device__ void finish(int, u32, const ModConst &) {}
     // whole-tile direct loads of the first pass (default: element by element)
     static constexpr bool TILE_LOAD = false;
+    // whole-tile stores of the second pass: store_tile_last(J[R], value[R], mod)
+    // gets every final value of the thread at once, so a job that reads
+    // operands to combine with them can issue those loads together
+    static constexpr bool TILE_STORE = false;
 };
 
 // reduce v < 2^64 to [0, q) with one Shoup product by 1 and a subtraction
@@ -252,32 +256,50 @@ __device__ __forceinline__ void pass_body(Job &job, u32 tile)
             }
         }
         // ---- store ----
-        auto emit = [&](int k, u32 J, u64 val) {
-            if (FIRST) {
-                job.store_mid(J, val);
-            } else {
-                u64 r;
-                if (INV) {
-                    const ulonglong2 s = job.inv_scale();
-                    r = shoup(val, s.x, s.y, q); // any input < 2^64
-                } else {
-                    r = LAZY ? reduce_any(val, mc) : reduce4q(val, q);
-                }
-                job.store_last(k, J, r, mc);
+        auto final_value = [&](u64 val) -> u64 {
+            if (INV) {
+                const ulonglong2 s = job.inv_scale();
+                return shoup(val, s.x, s.y, q); // any input < 2^64
             }
+            return LAZY ? reduce_any(val, mc) : reduce4q(val, q);
         };
-        if (DIRECT_STORE) {
-#pragma unroll
-            for (int v = 0; v < R; v++) emit(v, gidx(sub, relem(ROUNDS - 1, v)), x[v]);
-        } else {
+        auto emit = [&](int k, u32 J, u64 val) {
+            if (FIRST) job.store_mid(J, val);
+            else job.store_last(k, J, final_value(val), mc);
+        };
+        if (!DIRECT_STORE) {
 #pragma unroll
             for (int v = 0; v < R; v++) sm[sidx(sub, relem(ROUNDS - 1, v))] = x[v];
             __syncthreads();
-#pragma unroll
-            for (int k = 0; k < R; k++) {
+        }
+        // element and value of store slot k
+        auto slot = [&](int k, u32 &J, u64 &val) {
+            if (DIRECT_STORE) {
+                J = gidx(sub, relem(ROUNDS - 1, k));
+                val = x[k];
+            } else {
                 const int lin = t + k * NT;
                 const int sb = ROWS ? lin / M : lin % SUBS, e = ROWS ? lin % M : lin / SUBS;
-                emit(k, gidx(sb, e), sm[sidx(sb, e)]);
+                J = gidx(sb, e);
+                val = sm[sidx(sb, e)];
+            }
+        };
+        if constexpr (!FIRST && Job::TILE_STORE) {
+            u32 Js[R];
+            u64 vs[R];
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                slot(k, Js[k], vs[k]);
+                vs[k] = final_value(vs[k]);
+            }
+            job.store_tile_last(Js, vs, mc);
+        } else {
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                u32 J;
+                u64 val;
+                slot(k, J, val);
+                emit(k, J, val);
             }
         }
         if (nrep > 1) __syncthreads(); // the next repetition reuses shared memory

@@ -61,11 +61,6 @@ int check_args(fheon_ctx *ctx, double beta, u32 D, u32 level)
     return FHEON_OK;
 }
 
-struct CtOwn {
-    fheon_ct *p = nullptr;
-    ~CtOwn() { fheon_ct_destroy(p); }
-};
-
 } // namespace
 
 extern "C" {
@@ -129,12 +124,13 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     const u32 D = ly->degree;
     const double s0 = in->scale;
     int rc;
-    // T_1 .. T_D in layer-owned working ciphertexts (index d), plus two temporaries
-    if (ly->rot.size() != D + 3) ly->rot.resize(D + 3, nullptr);
+    // T_1 .. T_D in layer-owned working ciphertexts (index d), two temporaries
+    // and the sum: nothing is allocated after the first application
+    if (ly->rot.size() != D + 4) ly->rot.resize(D + 4, nullptr);
     for (fheon_ct *&c : ly->rot)
         if (!c && (rc = fheon_ct_create(ctx, ly->level, s0, &c))) return rc;
     fheon_ct **T = ly->rot.data();
-    fheon_ct *t0 = ly->rot[D + 1], *t1 = ly->rot[D + 2];
+    fheon_ct *t0 = ly->rot[D + 1], *t1 = ly->rot[D + 2], *y = ly->rot[D + 3];
     // v = x * mask, rescaled (scale q_{l-1} of the mask cancels)
     if (ly->beta > 1.0) {
         if ((rc = fheon_mul_plain(ctx, in, ly->mask, T[1]))) return rc;
@@ -163,14 +159,12 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     u32 lstar = T[1]->level;
     for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
     lstar -= 1;
-    CtOwn y;
-    if ((rc = fheon_ct_create(ctx, lstar, s0, &y.p))) return rc;
     for (u32 d = 1; d <= D; d++) {
         if ((rc = fheon_drop_level(ctx, T[d], lstar + 1, t0))) return rc;
-        if ((rc = fheon_mul_const_rescale(ctx, t0, ly->coeffs[d], s0, d == 1 ? y.p : t1))) return rc;
-        if (d > 1 && (rc = fheon_add(ctx, y.p, t1, y.p))) return rc;
+        if ((rc = fheon_mul_const_rescale(ctx, t0, ly->coeffs[d], s0, d == 1 ? y : t1))) return rc;
+        if (d > 1 && (rc = fheon_add(ctx, y, t1, y))) return rc;
     }
-    if ((rc = fheon_add_const(ctx, y.p, ly->coeffs[0], out))) return rc;
+    if ((rc = fheon_add_const(ctx, y, ly->coeffs[0], out))) return rc;
     return FHEON_OK;
 }
 

@@ -105,6 +105,7 @@ SIGNATURES = {
     "fheon_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_vpp],
     "fheon_fc_prepare": [c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_layer_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_layer_apply_graph": [c_vp, c_vp, c_vp, c_vp],
     "fheon_layer_apply_batch": [c_vp, c_vp, P(c_vp), c_u32, P(c_vp)],
     "fheon_model_create": [c_vp, P(c_vp), c_u32, c_vpp],
     "fheon_model_destroy": [c_vp],
@@ -534,6 +535,11 @@ class Context:
     def layer_apply(self, layer, ct, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_layer_apply(self.h, layer.h, ct.h, out.h))
+        return out
+
+    def layer_apply_graph(self, layer, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_layer_apply_graph(self.h, layer.h, ct.h, out.h))
         return out
 
     def layer_apply_batch(self, layer, cts, outs=None):

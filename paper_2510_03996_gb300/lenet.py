@@ -134,3 +134,17 @@ class EncryptedLeNet:
         for layer in self.layers:
             ct = self.ctx.layer_apply(layer, ct)
         return ct
+
+    def forward_graph(self, ct):
+        """The same layers replayed as CUDA graphs on fixed buffers: the input is
+        copied into a staging ciphertext, each layer writes its own output
+        buffer (the context's stream must be a created stream).  Returns a new
+        ciphertext holding the output."""
+        ctx = self.ctx
+        if not hasattr(self, "_bufs"):
+            self._bufs = [ctx.ct_create(1) for _ in range(len(self.layers) + 1)]
+        ctx.drop_level(ct, ctx.ct_info(ct)[0], out=self._bufs[0])
+        for i, layer in enumerate(self.layers):
+            ctx.layer_apply_graph(layer, self._bufs[i], self._bufs[i + 1])
+        y = self._bufs[-1]
+        return ctx.drop_level(y, ctx.ct_info(y)[0])

@@ -18,8 +18,9 @@ def test_lenet_logits_match_fp64():
     F.use_torch_allocator()
     P = synth.params("lenet_n15")
     N = 1 << P["logN"]
+    stream = torch.cuda.Stream()  # graph capture needs a created stream
     ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
-                    stream=torch.cuda.current_stream().cuda_stream)
+                    stream=stream.cuda_stream)
     w = lenet.weights(P["seed"])
     xs = [synth.image(P["seed"], 600 + s, (1, 28, 28)) for s in range(2)]
     betas = lenet.relu_bounds(xs, w)
@@ -32,6 +33,9 @@ def test_lenet_logits_match_fp64():
     for i, X in enumerate(xs):
         ct = ctx.encrypt(pk, ctx.encode(lenet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i)
         y = net.forward(ct)
+        # the layers replayed as CUDA graphs (captured on the first input) give the same bits
+        yg = net.forward_graph(ct)
+        assert np.array_equal(ctx.ct_download(yg), ctx.ct_download(y))
         got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
         want = OF.lenet_fp64(X, w, betas)
         assert np.max(np.abs(got - want)) < 1e-2, (got, want)
