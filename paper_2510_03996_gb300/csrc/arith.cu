@@ -71,18 +71,22 @@ __global__ void __launch_bounds__(TPB) mac_plain_kernel(const __grid_constant__ 
     *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(s0, s1);
 }
 
-// the ciphertext tensor d = (a0 b0, a0 b1 + a1 b0, a1 b1); the middle term's
-// two products summed in 128 bits and reduced once
-__global__ void __launch_bounds__(TPB) tensor_kernel(const u64 *__restrict__ a, const u64 *__restrict__ b,
-                                                     u64 *__restrict__ d, u32 level, u32 logN,
+// the ciphertext tensor d = (a0 b0, a0 b1 + a1 b0, a1 b1) over the lowest
+// `level` limbs of each component (components may sit at any stride, so an
+// operand at a higher level is read in place); the middle term's two
+// products summed in 128 bits and reduced once; `twice` doubles all three
+// (the tensor of 2a and b)
+__global__ void __launch_bounds__(TPB) tensor_kernel(const u64 *__restrict__ a0p, const u64 *__restrict__ a1p,
+                                                     const u64 *__restrict__ b0p, const u64 *__restrict__ b1p,
+                                                     u64 *__restrict__ d, u32 level, bool twice, u32 logN,
                                                      const ModConst *__restrict__ mc)
 {
     const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
     const u64 per = (u64)level << logN;
     if (idx >= per) return;
     const ModConst m = mc[(u32)(idx >> logN)];
-    const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(a + idx), a1 = *reinterpret_cast<const ulonglong2 *>(a + per + idx);
-    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(b + idx), b1 = *reinterpret_cast<const ulonglong2 *>(b + per + idx);
+    const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(a0p + idx), a1 = *reinterpret_cast<const ulonglong2 *>(a1p + idx);
+    const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(b0p + idx), b1 = *reinterpret_cast<const ulonglong2 *>(b1p + idx);
     u128acc x, y;
     acc_zero(x);
     acc_zero(y);
@@ -90,29 +94,40 @@ __global__ void __launch_bounds__(TPB) tensor_kernel(const u64 *__restrict__ a, 
     acc_mad(x, a1.x, b0.x);
     acc_mad(y, a0.y, b1.y);
     acc_mad(y, a1.y, b0.y);
-    *reinterpret_cast<ulonglong2 *>(d + idx) = make_ulonglong2(mulmod_plain(a0.x, b0.x, m), mulmod_plain(a0.y, b0.y, m));
-    *reinterpret_cast<ulonglong2 *>(d + per + idx) =
-        make_ulonglong2(shoup(redc_acc(x, m.q, m.qneg_inv), m.r1, m.r1_sh, m.q), shoup(redc_acc(y, m.q, m.qneg_inv), m.r1, m.r1_sh, m.q));
-    *reinterpret_cast<ulonglong2 *>(d + 2 * per + idx) = make_ulonglong2(mulmod_plain(a1.x, b1.x, m), mulmod_plain(a1.y, b1.y, m));
+    u64 r[6] = {mulmod_plain(a0.x, b0.x, m), mulmod_plain(a0.y, b0.y, m),
+                shoup(redc_acc(x, m.q, m.qneg_inv), m.r1, m.r1_sh, m.q), shoup(redc_acc(y, m.q, m.qneg_inv), m.r1, m.r1_sh, m.q),
+                mulmod_plain(a1.x, b1.x, m), mulmod_plain(a1.y, b1.y, m)};
+    if (twice) {
+#pragma unroll
+        for (int i = 0; i < 6; i++) r[i] = addmod(r[i], r[i], m.q);
+    }
+    *reinterpret_cast<ulonglong2 *>(d + idx) = make_ulonglong2(r[0], r[1]);
+    *reinterpret_cast<ulonglong2 *>(d + per + idx) = make_ulonglong2(r[2], r[3]);
+    *reinterpret_cast<ulonglong2 *>(d + 2 * per + idx) = make_ulonglong2(r[4], r[5]);
 }
 
-// v mod q for a signed 64-bit v
-__device__ __forceinline__ u64 signed_mod(long long v, u64 q)
+// v mod q for a signed 64-bit v: REDC(v) = v 2^-64 mod q (v < q 2^64), then
+// a Montgomery product with 2^128 mod q restores v mod q
+__device__ __forceinline__ u64 signed_mod(long long v, const ModConst &m)
 {
-    if (v >= 0) return (u64)v % q;
-    const u64 r = (u64)(-(v + 1)) % q;
-    return q - 1 - r;
+    const u64 a = v >= 0 ? (u64)v : (u64)(-(v + 1)) + 1ull; // |v|, also for INT64_MIN
+    const u64 r = mulmod_mont(redc(0, a, m.q, m.qneg_inv), m.r2, m);
+    return (v >= 0 || r == 0) ? r : m.q - r;
 }
 
-// out = v * ct over `ncomp` components of `level` limbs
-__global__ void __launch_bounds__(TPB) mul_int_kernel(const u64 *__restrict__ ct, long long v, u64 *__restrict__ out,
-                                                      u32 level, u32 ncomp, u32 logN, const ModConst *__restrict__ mc)
+// out = v * ct over `ncomp` components of `level` limbs; input component c at
+// ct + c * in_stride (in_stride = level * N for a ciphertext at this level)
+__global__ void __launch_bounds__(TPB) mul_int_kernel(const u64 *__restrict__ ct, u64 in_stride, long long v,
+                                                      u64 *__restrict__ out, u32 level, u32 ncomp, u32 logN,
+                                                      const ModConst *__restrict__ mc)
 {
     const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
-    if (idx >= ((u64)ncomp * level << logN)) return;
+    const u64 per = (u64)level << logN;
+    if (idx >= ncomp * per) return;
     const ModConst m = mc[limb_of(idx, level, logN)];
-    const u64 vm = signed_mod(v, m.q);
-    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
+    const u64 vm = signed_mod(v, m);
+    const u64 comp = idx / per;
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + comp * in_stride + (idx - comp * per));
     *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(mulmod_plain(x.x, vm, m), mulmod_plain(x.y, vm, m));
 }
 
@@ -126,8 +141,9 @@ __global__ void __launch_bounds__(TPB) add_int_kernel(const u64 *__restrict__ ct
     if (idx >= 2 * per) return;
     ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ct + idx);
     if (idx < per) {
-        const u64 q = mc[(u32)(idx >> logN)].q, vm = signed_mod(v, q);
-        x = make_ulonglong2(addmod(x.x, vm, q), addmod(x.y, vm, q));
+        const ModConst m = mc[(u32)(idx >> logN)];
+        const u64 vm = signed_mod(v, m);
+        x = make_ulonglong2(addmod(x.x, vm, m.q), addmod(x.y, vm, m.q));
     }
     *reinterpret_cast<ulonglong2 *>(out + idx) = x;
 }
@@ -244,17 +260,20 @@ cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const 
     }
     return cudaSuccess;
 }
-cudaError_t k_tensor(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *d, u32 level)
+cudaError_t k_tensor(fheon_ctx *ctx, const u64 *a0, const u64 *a1, const u64 *b0, const u64 *b1, u64 *d, u32 level,
+                     bool twice)
 {
-    tensor_kernel<<<blocks2((u64)level * ctx->N), TPB, 0, ctx->stream>>>(a, b, d, level, ctx->logN,
+    tensor_kernel<<<blocks2((u64)level * ctx->N), TPB, 0, ctx->stream>>>(a0, a1, b0, b1, d, level, twice, ctx->logN,
                                                                           ctx->tab.mc.as<ModConst>());
     prof_mark(ctx->stream, "tensor");
     return cudaGetLastError();
 }
-cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level, u32 ncomp)
+cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level, u32 ncomp, u64 in_stride)
 {
-    mul_int_kernel<<<blocks2((u64)ncomp * level * ctx->N), TPB, 0, ctx->stream>>>(ct, (long long)v, out, level, ncomp,
-                                                                                  ctx->logN, ctx->tab.mc.as<ModConst>());
+    if (!in_stride) in_stride = (u64)level * ctx->N;
+    mul_int_kernel<<<blocks2((u64)ncomp * level * ctx->N), TPB, 0, ctx->stream>>>(ct, in_stride, (long long)v, out, level,
+                                                                                  ncomp, ctx->logN,
+                                                                                  ctx->tab.mc.as<ModConst>());
     prof_mark(ctx->stream, "mul_int");
     return cudaGetLastError();
 }

@@ -744,19 +744,21 @@ int fheon_add_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheo
     return FHEON_OK;
 }
 
-int fheon_mul_relin(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out)
+} // extern "C"
+
+namespace fheon {
+int mul_relin_at(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, u32 l, bool twice, fheon_ct *out)
 {
-    if (!ctx || !a || !b || !out) return FHEON_ERR_ARG;
-    if (a->level != b->level) return fail(ctx, FHEON_ERR_LEVEL, "mul_relin: levels %u and %u", a->level, b->level);
     auto it = ctx->keys.find(0);
     if (it == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "no relinearisation key");
-    const u32 l = a->level, N = ctx->N;
+    if (l < 1 || l > a->level || l > b->level) return fail(ctx, FHEON_ERR_LEVEL, "mul_relin: level %u", l);
+    const u32 N = ctx->N;
     const double sc = a->scale * b->scale;
     int rc = ensure_workspace(ctx, ctx->ks_ws_limbs(ctx->L) + 3 * (size_t)ctx->L);
     if (rc) return rc;
     u64 *ws = ctx->ws.as<u64>();
     u64 *d = ws + ctx->ks_ws_limbs(ctx->L) * N; // tensor [3][l][N] past the key-switching workspace
-    FHEON_CUDA(ctx, k_tensor(ctx, a->c0(), b->c0(), d, l));
+    FHEON_CUDA(ctx, k_tensor(ctx, a->c0(), a->c1(N), b->c0(), b->c1(N), d, l, twice));
     if ((rc = ct_reshape(ctx, out, l))) return rc;
     // key-switch d2 from s^2 to s (g = 1: no automorphism); d0 joins component 0, d1 component 1
     if ((rc = keyswitch_rotate(ctx, d, d + (size_t)2 * l * N, l, 1, it->second.mem.as<u64>(), ws, out->c0(),
@@ -764,6 +766,17 @@ int fheon_mul_relin(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_
         return rc;
     out->scale = sc;
     return FHEON_OK;
+}
+
+} // namespace fheon
+
+extern "C" {
+
+int fheon_mul_relin(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, fheon_ct *out)
+{
+    if (!ctx || !a || !b || !out) return FHEON_ERR_ARG;
+    if (a->level != b->level) return fail(ctx, FHEON_ERR_LEVEL, "mul_relin: levels %u and %u", a->level, b->level);
+    return mul_relin_at(ctx, a, b, a->level, false, out);
 }
 
 int fheon_mul_int(fheon_ctx *ctx, const fheon_ct *ct, int64_t v, fheon_ct *out)
@@ -809,16 +822,34 @@ int fheon_add_const(fheon_ctx *ctx, const fheon_ct *ct, double c, fheon_ct *out)
 int fheon_mul_const_rescale(fheon_ctx *ctx, const fheon_ct *ct, double c, double target, fheon_ct *out)
 {
     if (!ctx || !ct || !out || !(target > 0)) return FHEON_ERR_ARG;
-    if (ct->level < 2) return fail(ctx, FHEON_ERR_LEVEL, "mul_const_rescale needs level >= 2");
+    return mul_const_rescale_at(ctx, ct, ct->level, c, target, out);
+}
+
+} // extern "C"
+
+int fheon::mul_const_rescale_at(fheon_ctx *ctx, const fheon_ct *ct, u32 l, double c, double target, fheon_ct *out)
+{
+    if (l < 2 || l > ct->level) return fail(ctx, FHEON_ERR_LEVEL, "mul_const_rescale needs 2 <= level <= %u", ct->level);
     int64_t K;
-    if (!round_int(((c * target) * (double)ctx->mod[ct->level - 1]) / ct->scale, &K))
+    if (!round_int(((c * target) * (double)ctx->mod[l - 1]) / ct->scale, &K))
         return fail(ctx, FHEON_ERR_ARG, "mul_const_rescale: constant factor out of range");
-    int rc = fheon_mul_int(ctx, ct, K, out);
-    if (rc) return rc;
+    const double sc = ct->scale;
+    const u64 stride = (u64)ct->level * ctx->N;
+    const u64 *src = ct->c0();
+    int rc;
+    if (out == ct) {
+        if (l != ct->level) return fail(ctx, FHEON_ERR_ARG, "mul_const_rescale: in place needs the full level");
+    } else if ((rc = ct_reshape(ctx, out, l))) {
+        return rc;
+    }
+    FHEON_CUDA(ctx, k_mul_int(ctx, src, K, out->c0(), l, 2, stride));
+    out->scale = sc;
     if ((rc = rescale_ct(ctx, out, out))) return rc;
     out->scale = target;
     return FHEON_OK;
 }
+
+extern "C" {
 
 int fheon_rescale(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)
 {

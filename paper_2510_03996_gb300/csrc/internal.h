@@ -179,10 +179,18 @@ cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, 
 constexpr u32 MAC_MAX = 32;
 cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const *pts, u32 n, u64 *out, u32 level);
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 nlimb_per_comp, u32 ncomp);
-// d = (a0 b0, a0 b1 + a1 b0, a1 b1) over `level` limbs: u64[3][level][N]
-cudaError_t k_tensor(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *d, u32 level);
-// out = v * ct over `ncomp` components; out = ct + v on component 0 only
-cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level, u32 ncomp);
+// d = (a0 b0, a0 b1 + a1 b0, a1 b1) (doubled when `twice`) over the lowest
+// `level` limbs of each component: u64[3][level][N]
+cudaError_t k_tensor(fheon_ctx *ctx, const u64 *a0, const u64 *a1, const u64 *b0, const u64 *b1, u64 *d, u32 level,
+                     bool twice = false);
+// out = v * ct over `ncomp` components of `level` limbs (input component c at
+// ct + c * in_stride; 0 = level * N); out = ct + v on component 0 only
+cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level, u32 ncomp, u64 in_stride = 0);
+// ciphertext product with relinearisation of the lowest `level` limbs of a and
+// b (either may be at a higher level), doubled when `twice`; no rescale
+int mul_relin_at(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, u32 level, bool twice, fheon_ct *out);
+// c * (the lowest `level` limbs of ct), rescaled onto scale `target`
+int mul_const_rescale_at(fheon_ctx *ctx, const fheon_ct *ct, u32 level, double c, double target, fheon_ct *out);
 cudaError_t k_add_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level);
 cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level);
 int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);

@@ -139,20 +139,19 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     } else if ((rc = fheon_drop_level(ctx, in, in->level, T[1]))) {
         return rc;
     }
+    // operands at a higher level are read in place (their lowest limbs), and
+    // the factor 2 of 2 T_a T_b is applied inside the tensor
+    (void)t0;
     for (u32 d = 2; d <= D; d++) {
         const u32 h = d / 2;
         fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
         const u32 lv = A->level < B->level ? A->level : B->level;
-        if ((rc = fheon_drop_level(ctx, A, lv, t0))) return rc;
-        if ((rc = fheon_mul_int(ctx, t0, 2, t0))) return rc;
-        if ((rc = fheon_drop_level(ctx, B, lv, t1))) return rc;
-        if ((rc = fheon_mul_relin(ctx, t0, t1, T[d]))) return rc;
+        if ((rc = mul_relin_at(ctx, A, B, lv, true, T[d]))) return rc;
         if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
         if (d % 2 == 0) {
             if ((rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
         } else {
-            if ((rc = fheon_drop_level(ctx, T[1], lv, t0))) return rc;
-            if ((rc = fheon_mul_const_rescale(ctx, t0, -1.0, T[d]->scale, t1))) return rc;
+            if ((rc = mul_const_rescale_at(ctx, T[1], lv, -1.0, T[d]->scale, t1))) return rc;
             if ((rc = fheon_add(ctx, T[d], t1, T[d]))) return rc;
         }
     }
@@ -160,8 +159,7 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
     lstar -= 1;
     for (u32 d = 1; d <= D; d++) {
-        if ((rc = fheon_drop_level(ctx, T[d], lstar + 1, t0))) return rc;
-        if ((rc = fheon_mul_const_rescale(ctx, t0, ly->coeffs[d], s0, d == 1 ? y : t1))) return rc;
+        if ((rc = mul_const_rescale_at(ctx, T[d], lstar + 1, ly->coeffs[d], s0, d == 1 ? y : t1))) return rc;
         if (d > 1 && (rc = fheon_add(ctx, y, t1, y))) return rc;
     }
     if ((rc = fheon_add_const(ctx, y, ly->coeffs[0], out))) return rc;
