@@ -227,6 +227,13 @@ int fheon_ct_info(const fheon_ct *ct, uint32_t *level, double *scale);
  * download blocks.  Residues are not range-checked on upload. */
 int fheon_ct_upload(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host);
 int fheon_ct_download(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host);
+/* The same copies queued on `stream` (NULL: the context's stream) without
+ * waiting: the host buffer must stay valid (and, for full speed, pinned) until
+ * the stream has passed the copy; ordering against the context's work is the
+ * caller's (events), so transfers of one batch can overlap the key switching
+ * of another. */
+int fheon_ct_upload_async(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host, void *stream);
+int fheon_ct_download_async(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host, void *stream);
 /* Device address of the ciphertext's u64[2][level][N] array. */
 int fheon_ct_device_ptr(const fheon_ct *ct, void **dptr);
 

@@ -632,6 +632,20 @@ int fheon_ct_upload(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host)
                                     cudaMemcpyHostToDevice, ctx->stream));
     return FHEON_OK;
 }
+int fheon_ct_upload_async(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host, void *stream)
+{
+    if (!ctx || !ct || !host) return FHEON_ERR_ARG;
+    FHEON_CUDA(ctx, cudaMemcpyAsync(ct->c.p, host, (size_t)2 * ct->level * ctx->limb_bytes(), cudaMemcpyHostToDevice,
+                                    stream ? (cudaStream_t)stream : ctx->stream));
+    return FHEON_OK;
+}
+int fheon_ct_download_async(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host, void *stream)
+{
+    if (!ctx || !ct || !host) return FHEON_ERR_ARG;
+    FHEON_CUDA(ctx, cudaMemcpyAsync(host, ct->c.p, (size_t)2 * ct->level * ctx->limb_bytes(), cudaMemcpyDeviceToHost,
+                                    stream ? (cudaStream_t)stream : ctx->stream));
+    return FHEON_OK;
+}
 int fheon_ct_download(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host)
 {
     if (!ctx || !ct || !host) return FHEON_ERR_ARG;

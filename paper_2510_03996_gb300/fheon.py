@@ -81,6 +81,8 @@ SIGNATURES = {
     "fheon_ct_create": [c_vp, c_u32, c_dbl, c_vpp],
     "fheon_ct_destroy": [c_vp],
     "fheon_ct_info": [c_vp, P(c_u32), P(c_dbl)],
+    "fheon_ct_upload_async": [c_vp, c_vp, P(c_u64), c_vp],
+    "fheon_ct_download_async": [c_vp, c_vp, P(c_u64), c_vp],
     "fheon_ct_upload": [c_vp, c_vp, P(c_u64)],
     "fheon_ct_download": [c_vp, c_vp, P(c_u64)],
     "fheon_ct_device_ptr": [c_vp, c_vpp],
@@ -403,6 +405,12 @@ class Context:
         out = np.zeros((2, lv, self.N), dtype=np.uint64)
         self._chk(load().fheon_ct_download(self.h, ct.h, _u64p(out)))
         return out
+
+    def ct_upload_async(self, ct, host_ptr, stream=None):
+        self._chk(load().fheon_ct_upload_async(self.h, ct.h, ctypes.cast(c_vp(host_ptr), P(c_u64)), stream))
+
+    def ct_download_async(self, ct, host_ptr, stream=None):
+        self._chk(load().fheon_ct_download_async(self.h, ct.h, ctypes.cast(c_vp(host_ptr), P(c_u64)), stream))
 
     def ct_download_ptr(self, ct, host_ptr):
         self._chk(load().fheon_ct_download(self.h, ct.h, ctypes.cast(c_vp(host_ptr), P(c_u64))))
