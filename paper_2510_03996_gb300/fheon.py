@@ -281,9 +281,35 @@ class Context:
     def set_schedule(self, schedule):
         self._chk(load().fheon_ctx_set_schedule(self.h, int(schedule)))
 
-    def autotune_schedule(self, ins, outs, steps, reps=2):
+    def autotune_schedule(self, ins, outs, steps, reps=2, cache=None):
         """Time every allowed key-switching schedule on this batch; keep the fastest.
-        Returns (best, {schedule: ms per batch})."""
+        Returns (best, {schedule: ms per batch}).  With `cache` (a JSON file
+        path), a choice made before for the same parameters and batch shape
+        (count and levels) is reused without timing, and new choices are saved."""
+        key = None
+        if cache is not None:
+            import json
+            levels = sorted(self.ct_info(c)[0] for c in ins)
+            key = "N%d_L%d_K%d_a%d_n%d_l%s" % (self.N, self.L, self.K, self.alpha, len(ins),
+                                              ",".join(str(x) for x in levels))
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except (OSError, ValueError):
+                known = {}
+            if key in known:
+                self.set_schedule(int(known[key]["schedule"]))
+                return int(known[key]["schedule"]), {int(k): v for k, v in known[key]["ms"].items()}
+        best, ms = self._autotune(ins, outs, steps, reps)
+        if key is not None:
+            known[key] = {"schedule": best, "ms": {str(k): v for k, v in ms.items()}}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(known, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return best, ms
+
+    def _autotune(self, ins, outs, steps, reps):
         items = (fheon_rot_item * len(ins))()
         for i, (a, b, s) in enumerate(zip(ins, outs, steps)):
             items[i].input, items[i].output, items[i].step = a.h, b.h, int(s)

@@ -293,3 +293,26 @@ def test_rotate_full_size_sampled():
         out = pr.g.rotate(c, 12345)
         want = pr.o.rotate(oct_[:, :level], g, pr.okeys[g])
         assert gpu_common.mismatch(pr.g.ct_download(out), want) == 0
+
+
+def test_autotune_cache(small, tmp_path):
+    """The autotuner's choice is saved per parameters and batch shape and reused."""
+    import json
+    g = small.g
+    old = g.get_schedule()
+    try:
+        ins, outs, steps = [], [], []
+        for i, (lv, st) in enumerate([(5, 1), (3, -1), (4, 5)]):
+            c, _ = small.encrypt_both(synth.small_int_poly(70, i, small.N, 1 << 40), nonce=7000 + i, level=lv)
+            ins.append(c)
+            outs.append(g.ct_create(1))
+            steps.append(st)
+        path = str(tmp_path / "schedules.json")
+        best, ms = g.autotune_schedule(ins, outs, steps, reps=1, cache=path)
+        saved = json.load(open(path))
+        assert len(saved) == 1 and list(saved.values())[0]["schedule"] == best
+        g.set_schedule(0)
+        best2, ms2 = g.autotune_schedule(ins, outs, steps, reps=1, cache=path)
+        assert best2 == best and g.get_schedule() == best and ms2 == ms
+    finally:
+        g.set_schedule(old)
