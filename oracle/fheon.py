@@ -221,39 +221,38 @@ def relu_mask_values(nslots, beta, n):
 def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
     """Alg. 4 on a ciphertext of scale `scale` (returns (ct, scale)):
     v = x * mask (rescaled; only when beta > 1), then the Chebyshev series of f
-    at v.  T_1 = v; T_2h = 2 T_h^2 - 1; T_2h+1 = 2 T_h+1 T_h - T_1 (products at
-    the lower operand level, rescaled; T_1 brought to the product's level and
-    scale by a rescaled constant product).  Every c_d T_d (d >= 1) is rescaled
-    onto `scale` at one common level and summed in order of d; c_0 is added
-    last.  The output has the input's scale, at depth ceil(log2 D) + 1 (+1
-    with the mask) below the input."""
+    at v.  T_1 = v; T_2h = 2 T_h^2 - 1 (product at T_h's level, rescaled, then
+    -1 added); T_2h+1 = 2 T_h+1 T_h - T_1: the product (scale S = s_h+1 s_h,
+    at the lower operand level) plus T_1 times K = llround((-1 * S) / s_1),
+    rescaled once.  Finally y = sum_d K_d T_d (d >= 1, all at one level, K_d =
+    llround(((c_d * scale) * q) / s_d) for the prime q the sum is rescaled by),
+    rescaled once onto `scale`, plus c_0.  The output has the input's scale, at
+    depth ceil(log2 D) + 1 (+1 with the mask) below the input."""
     q = ctx.q
     c = relu_cheb_coeffs(beta, D)
     lev = lambda a: a.shape[1]  # noqa: E731
     v = ctx.rescale(ctx.mul_plain(ct, mask_plain)) if beta > 1 else ct
     T = {1: (v, scale)}
     for d in range(2, D + 1):
+        (A, sa), (B, sb) = T[d - d // 2], T[d // 2]
+        lv = min(lev(A), lev(B))
+        A, B = ctx.drop_level(A, lv), ctx.drop_level(B, lv)
+        prod = ctx.mul_relin(ctx.mul_int(A, 2), B, rlk)
+        S = sa * sb
+        sc = S / float(q[lv - 1])
         if d % 2 == 0:
-            A, sa = T[d // 2]
-            prod = ctx.rescale(ctx.mul_relin(ctx.mul_int(A, 2), A, rlk))
-            sc = sa * sa / float(q[lev(A) - 1])
-            T[d] = (ctx.add_const(prod, -1.0, sc), sc)
+            T[d] = (ctx.add_const(ctx.rescale(prod), -1.0, sc), sc)
         else:
-            (A, sa), (B, sb) = T[(d + 1) // 2], T[(d - 1) // 2]
-            lv = min(lev(A), lev(B))
-            A, B = ctx.drop_level(A, lv), ctx.drop_level(B, lv)
-            prod = ctx.rescale(ctx.mul_relin(ctx.mul_int(A, 2), B, rlk))
-            sc = sa * sb / float(q[lv - 1])
             t1, s1 = T[1]
-            neg = ctx.mul_const_rescale(ctx.drop_level(t1, lv), -1.0, sc, s1)
-            T[d] = (ctx.add(prod, neg), sc)
+            K = ckks.llround((-1.0 * S) / s1)
+            T[d] = (ctx.rescale(ctx.add(prod, ctx.mul_int(ctx.drop_level(t1, lv), K))), sc)
     lstar = min(lev(T[d][0]) for d in T) - 1
     y = None
     for d in range(1, D + 1):
         A, sa = T[d]
-        term = ctx.mul_const_rescale(ctx.drop_level(A, lstar + 1), c[d], scale, sa)
+        term = ctx.mul_int(ctx.drop_level(A, lstar + 1), ctx.const_factor(lstar + 1, c[d], scale, sa))
         y = term if y is None else ctx.add(y, term)
-    return ctx.add_const(y, c[0], scale), scale
+    return ctx.add_const(ctx.rescale(y), c[0], scale), scale
 
 
 # ------------------------------------------------------------------ packed network layers
