@@ -148,6 +148,48 @@ __global__ void __launch_bounds__(TPB) add_int_kernel(const u64 *__restrict__ ct
     *reinterpret_cast<ulonglong2 *>(out + idx) = x;
 }
 
+// out (+)= sum_t K_t * ct_t over both components, each ct_t read at its own
+// component stride (its lowest `level` limbs); the constants reduced per
+// modulus, the products summed in 128 bits in chunks of 8 as in
+// mac_plain_kernel
+struct LinArgs {
+    const u64 *ct[MAC_MAX];
+    u64 stride[MAC_MAX];
+    long long K[MAC_MAX];
+};
+__global__ void __launch_bounds__(TPB) lincomb_kernel(const __grid_constant__ LinArgs A, u32 n, u64 *out, bool add_out,
+                                                      u32 level, u32 logN, const ModConst *__restrict__ mc)
+{
+    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    const u64 per = (u64)level << logN;
+    if (idx >= 2 * per) return;
+    const u64 comp = idx / per, w = idx - comp * per;
+    const ModConst m = mc[(u32)(w >> logN)];
+    u64 s0 = 0, s1 = 0;
+    for (u32 c = 0; c < n; c += 8) {
+        u128acc a0, a1;
+        acc_zero(a0);
+        acc_zero(a1);
+        const u32 e = min(n, c + 8);
+        for (u32 t = c; t < e; t++) {
+            const u64 k = signed_mod(A.K[t], m);
+            const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(A.ct[t] + comp * A.stride[t] + w);
+            acc_mad(a0, x.x, k);
+            acc_mad(a1, x.y, k);
+        }
+        s0 = addmod(s0, redc_acc(a0, m.q, m.qneg_inv), m.q);
+        s1 = addmod(s1, redc_acc(a1, m.q, m.qneg_inv), m.q);
+    }
+    s0 = shoup(s0, m.r1, m.r1_sh, m.q);
+    s1 = shoup(s1, m.r1, m.r1_sh, m.q);
+    if (add_out) {
+        const ulonglong2 o = *reinterpret_cast<const ulonglong2 *>(out + idx);
+        s0 = addmod(s0, o.x, m.q);
+        s1 = addmod(s1, o.y, m.q);
+    }
+    *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(s0, s1);
+}
+
 // out = a + b over `ncomp` components of `level` limbs
 __global__ void __launch_bounds__(TPB) add_kernel(const u64 *__restrict__ a, const u64 *__restrict__ b,
                                                   u64 *__restrict__ out, u32 level, u32 ncomp, u32 logN,
@@ -283,6 +325,25 @@ cudaError_t k_add_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 le
                                                                                ctx->tab.mc.as<ModConst>());
     prof_mark(ctx->stream, "add_int");
     return cudaGetLastError();
+}
+cudaError_t k_lincomb(fheon_ctx *ctx, const u64 *const *cts, const u64 *strides, const int64_t *K, u32 n, u64 *out,
+                      u32 level)
+{
+    for (u32 s = 0; s < n; s += MAC_MAX) {
+        LinArgs A{};
+        const u32 m = std::min<u32>(MAC_MAX, n - s);
+        for (u32 t = 0; t < m; t++) {
+            A.ct[t] = cts[s + t];
+            A.stride[t] = strides[s + t];
+            A.K[t] = (long long)K[s + t];
+        }
+        lincomb_kernel<<<blocks2((u64)2 * level * ctx->N), TPB, 0, ctx->stream>>>(A, m, out, s > 0, level, ctx->logN,
+                                                                                   ctx->tab.mc.as<ModConst>());
+        prof_mark(ctx->stream, "lincomb");
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 level, u32 ncomp)
 {

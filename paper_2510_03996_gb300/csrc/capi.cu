@@ -817,13 +817,17 @@ int fheon_add_int(fheon_ctx *ctx, const fheon_ct *ct, int64_t v, fheon_ct *out)
     return FHEON_OK;
 }
 
+} // extern "C"
+
 // llround(x) when it fits comfortably in 63 bits
-static bool round_int(double x, int64_t *v)
+bool fheon::round_int(double x, int64_t *v)
 {
     if (!std::isfinite(x) || std::fabs(x) >= 4611686018427387904.0) return false; // 2^62
     *v = (int64_t)std::llround(x);
     return true;
 }
+
+extern "C" {
 
 int fheon_add_const(fheon_ctx *ctx, const fheon_ct *ct, double c, fheon_ct *out)
 {

@@ -189,9 +189,15 @@ cudaError_t k_mul_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 le
 // ciphertext product with relinearisation of the lowest `level` limbs of a and
 // b (either may be at a higher level), doubled when `twice`; no rescale
 int mul_relin_at(fheon_ctx *ctx, const fheon_ct *a, const fheon_ct *b, u32 level, bool twice, fheon_ct *out);
+// llround(x) into *v when x is finite and |x| < 2^62
+bool round_int(double x, int64_t *v);
 // c * (the lowest `level` limbs of ct), rescaled onto scale `target`
 int mul_const_rescale_at(fheon_ctx *ctx, const fheon_ct *ct, u32 level, double c, double target, fheon_ct *out);
 cudaError_t k_add_int(fheon_ctx *ctx, const u64 *ct, int64_t v, u64 *out, u32 level);
+// out = sum_t K[t] * (lowest `level` limbs of each component of cts[t], whose
+// components sit strides[t] words apart), both components
+cudaError_t k_lincomb(fheon_ctx *ctx, const u64 *const *cts, const u64 *strides, const int64_t *K, u32 n, u64 *out,
+                      u32 level);
 cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level);
 int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
 cudaError_t k_decrypt(fheon_ctx *ctx, const u64 *ct, const u64 *s, u64 *m, u32 level);

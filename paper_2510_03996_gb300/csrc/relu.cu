@@ -142,26 +142,42 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     // operands at a higher level are read in place (their lowest limbs), and
     // the factor 2 of 2 T_a T_b is applied inside the tensor
     (void)t0;
+    const u32 N = ctx->N;
     for (u32 d = 2; d <= D; d++) {
         const u32 h = d / 2;
         fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
         const u32 lv = A->level < B->level ? A->level : B->level;
-        if ((rc = mul_relin_at(ctx, A, B, lv, true, T[d]))) return rc;
-        if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
-        if (d % 2 == 0) {
-            if ((rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
-        } else {
-            if ((rc = mul_const_rescale_at(ctx, T[1], lv, -1.0, T[d]->scale, t1))) return rc;
-            if ((rc = fheon_add(ctx, T[d], t1, T[d]))) return rc;
+        if ((rc = mul_relin_at(ctx, A, B, lv, true, T[d]))) return rc; // scale S = s_a s_b
+        if (d % 2 == 1) {
+            // - T_1 at scale S joins the product before the shared rescale
+            int64_t K;
+            if (!round_int((-1.0 * T[d]->scale) / T[1]->scale, &K)) return fail(ctx, FHEON_ERR_ARG, "relu: constant");
+            if ((rc = ct_reshape(ctx, t1, lv))) return rc;
+            FHEON_CUDA(ctx, k_mul_int(ctx, T[1]->c0(), K, t1->c0(), lv, 2, (u64)T[1]->level * N));
+            FHEON_CUDA(ctx, k_add(ctx, T[d]->c0(), t1->c0(), T[d]->c0(), lv, 2));
         }
+        if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
+        if (d % 2 == 0 && (rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
     }
     u32 lstar = T[1]->level;
     for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
     lstar -= 1;
+    // y = sum_d K_d T_d at level lstar + 1 in one pass, rescaled once onto s0
+    std::vector<const u64 *> src(D);
+    std::vector<u64> stride(D);
+    std::vector<int64_t> K(D);
+    const double q = (double)ctx->mod[lstar];
     for (u32 d = 1; d <= D; d++) {
-        if ((rc = mul_const_rescale_at(ctx, T[d], lstar + 1, ly->coeffs[d], s0, d == 1 ? y : t1))) return rc;
-        if (d > 1 && (rc = fheon_add(ctx, y, t1, y))) return rc;
+        if (!round_int(((ly->coeffs[d] * s0) * q) / T[d]->scale, &K[d - 1]))
+            return fail(ctx, FHEON_ERR_ARG, "relu: coefficient factor out of range");
+        src[d - 1] = T[d]->c0();
+        stride[d - 1] = (u64)T[d]->level * N;
     }
+    if ((rc = ct_reshape(ctx, y, lstar + 1))) return rc;
+    FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), D, y->c0(), lstar + 1));
+    y->scale = s0 * q; // the sum's scale before the rescale (metadata)
+    if ((rc = fheon_rescale(ctx, y, y))) return rc;
+    y->scale = s0;
     if ((rc = fheon_add_const(ctx, y, ly->coeffs[0], out))) return rc;
     return FHEON_OK;
 }
