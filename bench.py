@@ -496,7 +496,8 @@ def run_gpu(args, rank, world, local_rank):
             ev_dn[k].record(s_dn)
         torch.cuda.synchronize()
 
-    e2e_steps = max(2, min(args.steps, 6))
+    # the pipeline fills and drains once per run: time enough steps to see its steady state
+    e2e_steps = max(4, 2 * args.steps)
     e2e_run(2)
     t0 = time.perf_counter()
     e2e_run(e2e_steps)
