@@ -316,3 +316,28 @@ def test_autotune_cache(small, tmp_path):
         assert best2 == best and g.get_schedule() == best and ms2 == ms
     finally:
         g.set_schedule(old)
+
+
+def test_rotate_batch_bench_configuration_sampled():
+    """The benchmark's batch itself: 256 ciphertexts at N = 2^16 (24 + 4 limbs,
+    dnum 6) at the workload's levels U{4..24}, each rotated by its own step
+    with its own key, in one fheon_rotate_batch call under the default
+    schedule; three sampled outputs (the lowest, a middle and the highest
+    level) bit-exact against the oracle's rotation of the same encryption."""
+    import oracle.ckks as O
+    P = synth.params("rot_n16")
+    levels, steps = synth.rotation_workload(P["seed"])
+    pick = [int(np.argmin(levels)), len(levels) // 2, int(np.argmax(levels))]
+    pr = gpu_common.Pair("rot_n16", rot_steps=[steps[i] for i in pick])
+    g = pr.g
+    g.galois_keygen(pr.sk, sorted({g.galois_elt(s) for s in steps}))
+    m = synth.small_int_poly(P["seed"], 21, pr.N, 1 << 40)
+    pt = g.plain_from_coeffs(m, pr.L, P["scale"])
+    ins = [g.drop_level(g.encrypt(pr.pk, pt, nonce=i), lv) for i, lv in enumerate(levels)]
+    outs = [g.ct_create(lv) for lv in levels]
+    g.rotate_batch(ins, outs, steps)
+    for i in pick:
+        oc = pr.o.drop_level(pr.o.encrypt(pr.opk, m, i), levels[i])
+        ge = O.galois_elt(steps[i], pr.N)
+        want = pr.o.rotate(oc, ge, pr.okeys[ge])
+        assert gpu_common.mismatch(g.ct_download(outs[i]), want) == 0, (i, levels[i], steps[i])
