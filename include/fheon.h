@@ -435,6 +435,24 @@ int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint3
  * d (about 2 sqrt(span) rotations).  Output level: level - 1, scale in_scale. */
 int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
                      uint32_t level, double in_scale, fheon_layer **out);
+/* Global average pooling (Sec. 4.4, used by ResNet): the mean over each
+ * channel's whole H x H map, as average pooling with k = stride = H (one
+ * value per channel, at the channel's first slot). */
+int fheon_global_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t level, fheon_layer **out);
+/* One-shot layers at ct's level and scale (prepare, apply, release). */
+int fheon_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t k, uint32_t stride, fheon_ct *out);
+int fheon_global_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, fheon_ct *out);
+/* Fully connected layer with the paper's key budget (Sec. 4.5, the number of
+ * rotation keys the system keeps): the diagonal form of fheon_fc_prepare when
+ * its rotation steps number at most max_keys (0: no limit), else the paper's
+ * form (one product per neuron, the slot sum by rotate-and-add with log2(N/2)
+ * keys, a one-hot placement; two levels); FHEON_ERR_ARG when max_keys is
+ * below log2(N/2). */
+int fheon_fc(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t m, const double *W, const double *bias,
+             uint32_t max_keys, fheon_ct *out);
+/* CKKS bootstrapping (the paper's deeper networks, Sec. 6): not part of this
+ * build; returns FHEON_ERR_UNIMPLEMENTED. */
+int fheon_bootstrap(fheon_ctx *ctx, const fheon_ct *ct, fheon_ct *out);
 /* Apply any prepared layer (conv2d, ReLU, rotation-sum, FC); `in` at the
  * layer's level, out distinct from in. */
 int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);

@@ -403,6 +403,104 @@ int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const doub
     return FHEON_OK;
 }
 
+int fheon_global_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t level, fheon_layer **out)
+{
+    if (!ctx || !in || in->H != in->W) return FHEON_ERR_ARG;
+    return fheon_avgpool_prepare(ctx, in, in->H, in->H, level, out);
+}
+
+// the FC layer as the paper states it: one product per neuron, the sum of its
+// slots by rotate-and-add, a one-hot placement (log2(N/2) keys)
+static int fc_slot_sum_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
+                               uint32_t level, double in_scale, fheon_layer **out)
+{
+    if (level < 3) return fail(ctx, FHEON_ERR_LEVEL, "fc: the slot-sum form needs level >= 3");
+    const fheon_map im = *in;
+    const u32 n = ctx->N / 2, nin = im.C * im.H * im.W;
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_FC;
+    ly->level = level;
+    ly->nslots = n;
+    ly->in_map = im;
+    ly->out_map = fheon_map{1, 1, m, m, 1, m};
+    std::vector<u32> slots;
+    for (u32 c = 0; c < im.C; c++)
+        for (u32 i = 0; i < im.H; i++)
+            for (u32 j = 0; j < im.W; j++) slots.push_back(map_slot(im, c, i, j));
+    std::vector<double> v(n);
+    int rc;
+    for (u32 k = 0; k < m; k++) {
+        std::fill(v.begin(), v.end(), 0.0);
+        for (u32 t = 0; t < nin; t++) v[slots[t]] = W[(size_t)k * nin + t];
+        fheon_pt *w = nullptr, *e = nullptr;
+        if ((rc = own_plain(ctx, ly.get(), v, level, (double)ctx->mod[level - 1], &w))) return rc;
+        if (!w) return fail(ctx, FHEON_ERR_ARG, "fc: neuron %u has all-zero weights", k);
+        std::fill(v.begin(), v.end(), 0.0);
+        v[k] = 1.0;
+        if ((rc = own_plain(ctx, ly.get(), v, level - 1, (double)ctx->mod[level - 2], &e))) return rc;
+        ly->fw.push_back(w);
+        ly->fe.push_back(e);
+    }
+    if (bias) {
+        std::fill(v.begin(), v.end(), 0.0);
+        for (u32 k = 0; k < m; k++) v[k] = bias[k];
+        if ((rc = own_plain(ctx, ly.get(), v, level - 2, in_scale, &ly->bias))) return rc;
+    }
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_fc(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t m, const double *W, const double *bias,
+             uint32_t max_keys, fheon_ct *out)
+{
+    if (!ctx || !ct || !in || !out) return FHEON_ERR_ARG;
+    fheon_layer *ly = nullptr;
+    int rc = fheon_fc_prepare(ctx, in, m, W, bias, ct->level, ct->scale, &ly);
+    if (rc) return rc;
+    uint32_t nk = 0;
+    fheon_layer_rotation_steps(ly, nullptr, &nk);
+    if (max_keys && nk > max_keys) {
+        // the paper's form needs log2(N/2) keys
+        fheon_layer_destroy(ly);
+        ly = nullptr;
+        u32 lg = 0;
+        while ((1u << lg) < ctx->N / 2) lg++;
+        if (lg > max_keys) return fail(ctx, FHEON_ERR_ARG, "fc: needs at least %u rotation keys", lg);
+        if ((rc = fc_slot_sum_prepare(ctx, in, m, W, bias, ct->level, ct->scale, &ly))) return rc;
+    }
+    rc = fheon_layer_apply(ctx, ly, ct, out);
+    fheon_layer_destroy(ly);
+    return rc;
+}
+
+int fheon_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t k, uint32_t stride, fheon_ct *out)
+{
+    if (!ctx || !ct) return FHEON_ERR_ARG;
+    fheon_layer *ly = nullptr;
+    int rc = fheon_avgpool_prepare(ctx, in, k, stride, ct->level, &ly);
+    if (rc) return rc;
+    rc = fheon_layer_apply(ctx, ly, ct, out);
+    fheon_layer_destroy(ly);
+    return rc;
+}
+
+int fheon_global_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, fheon_ct *out)
+{
+    if (!ctx || !ct) return FHEON_ERR_ARG;
+    fheon_layer *ly = nullptr;
+    int rc = fheon_global_avgpool_prepare(ctx, in, ct->level, &ly);
+    if (rc) return rc;
+    rc = fheon_layer_apply(ctx, ly, ct, out);
+    fheon_layer_destroy(ly);
+    return rc;
+}
+
+int fheon_bootstrap(fheon_ctx *ctx, const fheon_ct *ct, fheon_ct *out)
+{
+    if (!ctx || !ct || !out) return FHEON_ERR_ARG;
+    return fail(ctx, FHEON_ERR_UNIMPLEMENTED, "bootstrapping is not part of this build");
+}
+
 int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
     if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;

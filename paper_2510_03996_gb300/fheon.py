@@ -107,6 +107,11 @@ SIGNATURES = {
     "fheon_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_u32, c_u32, c_vpp],
     "fheon_fc_prepare": [c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_layer_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_global_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_vpp],
+    "fheon_avgpool": [c_vp, c_vp, P(fheon_map), c_u32, c_u32, c_vp],
+    "fheon_global_avgpool": [c_vp, c_vp, P(fheon_map), c_vp],
+    "fheon_fc": [c_vp, c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_vp],
+    "fheon_bootstrap": [c_vp, c_vp, c_vp],
     "fheon_layer_apply_graph": [c_vp, c_vp, c_vp, c_vp],
     "fheon_layer_apply_batch": [c_vp, c_vp, P(c_vp), c_u32, P(c_vp)],
     "fheon_model_create": [c_vp, P(c_vp), c_u32, c_vpp],
@@ -565,6 +570,34 @@ class Context:
                                           _dblp(b) if b is not None else None, level, float(in_scale),
                                           ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)
+
+    def global_avgpool_prepare(self, in_map, level):
+        h = c_vp()
+        self._chk(load().fheon_global_avgpool_prepare(self.h, ctypes.byref(self._map(in_map)), level, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def avgpool(self, ct, in_map, k, stride, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_avgpool(self.h, ct.h, ctypes.byref(self._map(in_map)), k, stride, out.h))
+        return out
+
+    def global_avgpool(self, ct, in_map, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_global_avgpool(self.h, ct.h, ctypes.byref(self._map(in_map)), out.h))
+        return out
+
+    def fc(self, ct, in_map, W, bias=None, max_keys=0, out=None):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_fc(self.h, ct.h, ctypes.byref(self._map(in_map)), W.shape[0], _dblp(W),
+                                  _dblp(b) if b is not None else None, max_keys, out.h))
+        return out
+
+    def bootstrap(self, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_bootstrap(self.h, ct.h, out.h))
+        return out
 
     def layer_apply(self, layer, ct, out=None):
         out = out or self.ct_create(1)

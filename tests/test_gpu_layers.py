@@ -175,3 +175,37 @@ def test_layers_from_weights_match_fp64(pair):
     want = Wm @ h.reshape(-1) + bf
     assert np.max(np.abs(got[:4] - want)) < 1e-3
     assert np.max(np.abs(got[4:])) < 1e-3
+
+
+def test_one_shot_layers_and_key_budget(pair):
+    """fheon_global_avgpool against the FP64 mean; fheon_fc within a key budget
+    that admits its diagonal form and one that forces the paper's slot-sum
+    form, both against the product; fheon_bootstrap reports unimplemented."""
+    g, D = pair.g, pair.P["scale"]
+    C, H = 3, 4
+    X = synth.image(86, 0, (C, H, H))
+    m_in = (C, H, H, GRID, 1, BLOCK)
+    v = OF.pack_map(X, pair.N // 2, GRID, 1, BLOCK)
+    ct, _ = pair.encrypt_both(ckks.encode(v, pair.N, D), nonce=8600, level=6)
+    lg = g.global_avgpool_prepare(m_in, 6)
+    pair.add_keys(g.layer_rotation_steps(lg))
+    got = np.asarray(g.decode(g.decrypt(pair.sk, g.global_avgpool(ct, m_in)))).real
+    for c in range(C):
+        assert abs(got[c * BLOCK] - X[c].mean()) < 1e-5
+    Wm = synth.image(86, 1, (5, C * H * H), dist="normal") * 0.2
+    want = Wm @ X.reshape(-1)
+    steps = OF.slot_sum_steps(pair.N // 2)
+    pair.add_keys(steps)
+    L = g.fc_prepare(m_in, Wm, 6, D)
+    pair.add_keys(g.layer_rotation_steps(L))
+    for budget in (0, len(steps)):
+        y = g.fc(ct, m_in, Wm, max_keys=budget)
+        assert g.ct_info(y)[0] == (5 if budget == 0 else 4)
+        got = np.asarray(g.decode(g.decrypt(pair.sk, y))).real
+        assert np.max(np.abs(got[:5] - want)) < 1e-4
+    with pytest.raises(pair.F.FheonError) as e:
+        g.fc(ct, m_in, Wm, max_keys=3)
+    assert e.value.code == -1
+    with pytest.raises(pair.F.FheonError) as e:
+        g.bootstrap(ct)
+    assert e.value.code == -8
