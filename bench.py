@@ -460,17 +460,21 @@ def run_gpu(args, rank, world, local_rank):
     ms_step = ms_total / args.steps
 
     # e2e: every step uploads its inputs from pinned host memory, rotates them and
-    # downloads the results, through the library's calls; transfers run on two
-    # copy streams and overlap the key switching of the neighbouring steps
-    # (double-buffered device ciphertexts, ordered by events)
-    host_in = [torch.empty((2, lv, N), dtype=torch.int64, pin_memory=True) for lv in levels]
-    host_out = [torch.empty((2, lv, N), dtype=torch.int64, pin_memory=True) for lv in levels]
-    for h, c in zip(host_in, ins):
-        ctx.ct_download_ptr(c, h.data_ptr())
-    h2d = sum(h.numel() * 8 for h in host_in)
-    d2h = sum(h.numel() * 8 for h in host_out)
-    bufs = [(ins, outs), ([ctx.ct_create(lv, P["scale"]) for lv in levels],
-                          [ctx.ct_create(lv, P["scale"]) for lv in levels])]
+    # downloads the results, through the library's calls.  The batch's
+    # ciphertexts sit back to back in one device allocation
+    # (fheon_ct_create_batch), so a step is one host-to-device and one
+    # device-to-host copy; the copies run on two copy streams and overlap the
+    # key switching of the neighbouring steps (two device batches, ordered by
+    # events).
+    words = sum(2 * lv * N for lv in levels)
+    host_in = torch.empty(words, dtype=torch.int64, pin_memory=True)
+    host_out = torch.empty(words, dtype=torch.int64, pin_memory=True)
+    bufs = [(ctx.ct_create_batch(levels, P["scale"]), ctx.ct_create_batch(levels, P["scale"])) for _ in range(2)]
+    for c, b in zip(ins, bufs[0][0]):
+        ctx.drop_level(c, ctx.ct_info(c)[0], out=b)
+    ctx.ct_download_many_async(bufs[0][0], host_in.data_ptr())
+    ctx.sync()
+    h2d = d2h = words * 8
     s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
 
     def e2e_run(nsteps):
@@ -479,8 +483,7 @@ def run_gpu(args, rank, world, local_rank):
             bi, bo = bufs[k % 2]
             if k >= 2:
                 s_up.wait_event(ev_comp[k - 2])  # the inputs of step k-2 are consumed
-            for h, c in zip(host_in, bi):
-                ctx.ct_upload_async(c, h.data_ptr(), s_up.cuda_stream)
+            ctx.ct_upload_many_async(bi, host_in.data_ptr(), s_up.cuda_stream)
             up = torch.cuda.Event()
             up.record(s_up)
             stream.wait_event(up)
@@ -490,20 +493,19 @@ def run_gpu(args, rank, world, local_rank):
             ev_comp[k] = torch.cuda.Event()
             ev_comp[k].record(stream)
             s_dn.wait_event(ev_comp[k])
-            for h, c in zip(host_out, bo):
-                ctx.ct_download_async(c, h.data_ptr(), s_dn.cuda_stream)
+            ctx.ct_download_many_async(bo, host_out.data_ptr(), s_dn.cuda_stream)
             ev_dn[k] = torch.cuda.Event()
             ev_dn[k].record(s_dn)
         torch.cuda.synchronize()
 
-    # the pipeline fills and drains once per run: time enough steps to see its steady state
     e2e_steps = max(4, 2 * args.steps)
     e2e_run(2)
     t0 = time.perf_counter()
     e2e_run(e2e_steps)
     e2e_value = replica_rate(len(levels) * e2e_steps, time.perf_counter() - t0, world)
     # the pipelined downloads are the batch's results
-    e2e_ok = bool(np.array_equal(host_out[0].numpy().view(np.uint64), ctx.ct_download(outs[0])))
+    first = host_out[:2 * levels[0] * N].numpy().view(np.uint64).reshape(2, levels[0], N)
+    e2e_ok = bool(np.array_equal(first, ctx.ct_download(outs[0])))
 
     # roofline of the dominant kernel, from the live per-launch events
     pk_, src = peaks()
@@ -555,8 +557,9 @@ def run_gpu(args, rank, world, local_rank):
                            "l2": "inputs larger than L2 (keys %.1f GB)" % (kbytes / 1e9)},
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "steps": e2e_steps, "pipelined": "uploads and downloads on two copy streams, overlapping the "
-                                                          "key switching of neighbouring steps", "result_matches": e2e_ok},
+                        "steps": e2e_steps, "pipelined": "one upload and one download per step (contiguous ciphertext "
+                                                          "batch) on two copy streams, overlapping the key switching of "
+                                                          "neighbouring steps", "result_matches": e2e_ok},
                 "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels,
                 "comparisons": comparisons}
         print(json.dumps(line), flush=True)

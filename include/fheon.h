@@ -232,6 +232,18 @@ int fheon_ct_download(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host);
  * the stream has passed the copy; ordering against the context's work is the
  * caller's (events), so transfers of one batch can overlap the key switching
  * of another. */
+/* n ciphertexts at the given levels in one device allocation, back to back
+ * (ciphertext i: 2 * levels[i] * N words), zeroed; each handle is destroyed as
+ * usual and the allocation goes with the last of them.  A batch moves to and
+ * from the host in one copy (below). */
+int fheon_ct_create_batch(fheon_ctx *ctx, const uint32_t *levels, uint32_t n, double scale, fheon_ct **out);
+/* Copies of n ciphertexts from/to `host` holding them back to back (ciphertext
+ * i: 2 * level_i * N words), queued on `stream` (NULL: the context's) without
+ * waiting: one copy when they are one batch in order at their created levels,
+ * else one copy each.  Host memory as for fheon_ct_upload_async. */
+int fheon_ct_upload_many_async(fheon_ctx *ctx, fheon_ct *const *cts, uint32_t n, const uint64_t *host, void *stream);
+int fheon_ct_download_many_async(fheon_ctx *ctx, const fheon_ct *const *cts, uint32_t n, uint64_t *host,
+                                 void *stream);
 int fheon_ct_upload_async(fheon_ctx *ctx, fheon_ct *ct, const uint64_t *host, void *stream);
 int fheon_ct_download_async(fheon_ctx *ctx, const fheon_ct *ct, uint64_t *host, void *stream);
 /* Device address of the ciphertext's u64[2][level][N] array. */

@@ -75,6 +75,7 @@ int ct_reshape(fheon_ctx *ctx, fheon_ct *ct, u32 level)
     }
     if (!ct->c.alloc((size_t)2 * level * ctx->N * 8, ctx->stream))
         return fail(ctx, FHEON_ERR_OOM, "ciphertext allocation of %u limbs failed", 2 * level);
+    ct->block.reset(); // its own memory now, not a view into a batch
     ct->cap = level;
     ct->level = level;
     return FHEON_OK;
@@ -618,6 +619,84 @@ int fheon_ct_create(fheon_ctx *ctx, uint32_t level, double scale, fheon_ct **out
     return FHEON_OK;
 }
 int fheon_ct_destroy(fheon_ct *ct) { delete ct; return FHEON_OK; }
+
+int fheon_ct_create_batch(fheon_ctx *ctx, const uint32_t *levels, uint32_t n, double scale, fheon_ct **out)
+{
+    if (!ctx || !levels || !out || !n) return FHEON_ERR_ARG;
+    size_t total = 0;
+    for (u32 i = 0; i < n; i++) {
+        if (levels[i] < 1 || levels[i] > ctx->L) return FHEON_ERR_ARG;
+        total += (size_t)2 * levels[i] * ctx->limb_bytes();
+    }
+    auto block = std::make_shared<DevMem>();
+    if (!block->alloc(total, ctx->stream)) return fail(ctx, FHEON_ERR_OOM, "ciphertext batch of %zu bytes", total);
+    FHEON_CUDA(ctx, cudaMemsetAsync(block->p, 0, total, ctx->stream));
+    char *base = block->as<char>();
+    for (u32 i = 0; i < n; i++) {
+        const size_t b = (size_t)2 * levels[i] * ctx->limb_bytes();
+        fheon_ct *ct = new fheon_ct();
+        ct->c.view(base, b);
+        ct->block = block;
+        ct->level = ct->cap = levels[i];
+        ct->scale = scale;
+        out[i] = ct;
+        base += b;
+    }
+    return FHEON_OK;
+}
+
+// true when cts[0..n) sit back to back in one batch allocation at their created levels
+static bool contiguous(const fheon_ct *const *cts, uint32_t n, size_t limb_bytes, size_t *bytes)
+{
+    const char *next = nullptr;
+    size_t total = 0;
+    for (u32 i = 0; i < n; i++) {
+        const fheon_ct *c = cts[i];
+        if (!c || !c->block || c->level != c->cap || c->block != cts[0]->block) return false;
+        if (next && (const char *)c->c.p != next) return false;
+        const size_t b = (size_t)2 * c->level * limb_bytes;
+        next = (const char *)c->c.p + b;
+        total += b;
+    }
+    *bytes = total;
+    return true;
+}
+
+int fheon_ct_upload_many_async(fheon_ctx *ctx, fheon_ct *const *cts, uint32_t n, const uint64_t *host, void *stream)
+{
+    if (!ctx || !cts || !host) return FHEON_ERR_ARG;
+    const cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    size_t bytes = 0;
+    if (n && contiguous(cts, n, ctx->limb_bytes(), &bytes)) {
+        FHEON_CUDA(ctx, cudaMemcpyAsync(cts[0]->c.p, host, bytes, cudaMemcpyHostToDevice, st));
+        return FHEON_OK;
+    }
+    for (u32 i = 0; i < n; i++) {
+        if (!cts[i]) return FHEON_ERR_ARG;
+        const size_t b = (size_t)2 * cts[i]->level * ctx->limb_bytes();
+        FHEON_CUDA(ctx, cudaMemcpyAsync(cts[i]->c.p, host, b, cudaMemcpyHostToDevice, st));
+        host += b / 8;
+    }
+    return FHEON_OK;
+}
+
+int fheon_ct_download_many_async(fheon_ctx *ctx, const fheon_ct *const *cts, uint32_t n, uint64_t *host, void *stream)
+{
+    if (!ctx || !cts || !host) return FHEON_ERR_ARG;
+    const cudaStream_t st = stream ? (cudaStream_t)stream : ctx->stream;
+    size_t bytes = 0;
+    if (n && contiguous(cts, n, ctx->limb_bytes(), &bytes)) {
+        FHEON_CUDA(ctx, cudaMemcpyAsync(host, cts[0]->c.p, bytes, cudaMemcpyDeviceToHost, st));
+        return FHEON_OK;
+    }
+    for (u32 i = 0; i < n; i++) {
+        if (!cts[i]) return FHEON_ERR_ARG;
+        const size_t b = (size_t)2 * cts[i]->level * ctx->limb_bytes();
+        FHEON_CUDA(ctx, cudaMemcpyAsync(host, cts[i]->c.p, b, cudaMemcpyDeviceToHost, st));
+        host += b / 8;
+    }
+    return FHEON_OK;
+}
 int fheon_ct_info(const fheon_ct *ct, uint32_t *level, double *scale)
 {
     if (!ct) return FHEON_ERR_ARG;

@@ -21,16 +21,33 @@ struct DevMem {
     void *p = nullptr;
     size_t bytes = 0;
     cudaStream_t st = nullptr;
+    bool owned = true; // false: a view into memory someone else releases
     DevMem() = default;
     DevMem(const DevMem &) = delete;
     DevMem &operator=(const DevMem &) = delete;
-    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes), st(o.st) { o.p = nullptr; o.bytes = 0; }
+    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes), st(o.st), owned(o.owned)
+    {
+        o.p = nullptr;
+        o.bytes = 0;
+        o.owned = true;
+    }
     DevMem &operator=(DevMem &&o) noexcept
     {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; st = o.st; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p; bytes = o.bytes; st = o.st; owned = o.owned;
+            o.p = nullptr; o.bytes = 0; o.owned = true;
+        }
         return *this;
     }
     ~DevMem() { release(); }
+    void view(void *q, size_t n)
+    {
+        release();
+        p = q;
+        bytes = n;
+        owned = false;
+    }
     bool alloc(size_t n, cudaStream_t s)
     {
         release();
@@ -43,9 +60,10 @@ struct DevMem {
     }
     void release()
     {
-        if (p) dev_free(p, bytes, st);
+        if (p && owned) dev_free(p, bytes, st);
         p = nullptr;
         bytes = 0;
+        owned = true;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
@@ -126,6 +144,7 @@ struct fheon_pt {
 };
 struct fheon_ct {
     fheon::DevMem c; // u64[2][level][N]
+    std::shared_ptr<fheon::DevMem> block; // a batch allocation c views into (null: c owns its memory)
     u32 level = 0;   // limbs in use
     u32 cap = 0;     // limbs allocated per component
     double scale = 1.0;

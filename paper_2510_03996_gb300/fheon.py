@@ -82,6 +82,9 @@ SIGNATURES = {
     "fheon_ct_destroy": [c_vp],
     "fheon_ct_info": [c_vp, P(c_u32), P(c_dbl)],
     "fheon_ct_upload_async": [c_vp, c_vp, P(c_u64), c_vp],
+    "fheon_ct_create_batch": [c_vp, P(c_u32), c_u32, c_dbl, P(c_vp)],
+    "fheon_ct_upload_many_async": [c_vp, P(c_vp), c_u32, P(c_u64), c_vp],
+    "fheon_ct_download_many_async": [c_vp, P(c_vp), c_u32, P(c_u64), c_vp],
     "fheon_ct_download_async": [c_vp, c_vp, P(c_u64), c_vp],
     "fheon_ct_upload": [c_vp, c_vp, P(c_u64)],
     "fheon_ct_download": [c_vp, c_vp, P(c_u64)],
@@ -436,6 +439,23 @@ class Context:
         out = np.zeros((2, lv, self.N), dtype=np.uint64)
         self._chk(load().fheon_ct_download(self.h, ct.h, _u64p(out)))
         return out
+
+    def ct_create_batch(self, levels, scale=1.0):
+        n = len(levels)
+        lv = (c_u32 * n)(*[int(x) for x in levels])
+        hs = (c_vp * n)()
+        self._chk(load().fheon_ct_create_batch(self.h, lv, n, float(scale), hs))
+        return [Handle(c_vp(hs[i]), load().fheon_ct_destroy) for i in range(n)]
+
+    def ct_upload_many_async(self, cts, host_ptr, stream=None):
+        arr = (c_vp * len(cts))(*[c.h.value for c in cts])
+        self._chk(load().fheon_ct_upload_many_async(self.h, arr, len(cts), ctypes.cast(c_vp(host_ptr), P(c_u64)),
+                                                    stream))
+
+    def ct_download_many_async(self, cts, host_ptr, stream=None):
+        arr = (c_vp * len(cts))(*[c.h.value for c in cts])
+        self._chk(load().fheon_ct_download_many_async(self.h, arr, len(cts), ctypes.cast(c_vp(host_ptr), P(c_u64)),
+                                                      stream))
 
     def ct_upload_async(self, ct, host_ptr, stream=None):
         self._chk(load().fheon_ct_upload_async(self.h, ct.h, ctypes.cast(c_vp(host_ptr), P(c_u64)), stream))

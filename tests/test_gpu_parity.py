@@ -341,3 +341,42 @@ def test_rotate_batch_bench_configuration_sampled():
         ge = O.galois_elt(steps[i], pr.N)
         want = pr.o.rotate(oc, ge, pr.okeys[ge])
         assert gpu_common.mismatch(g.ct_download(outs[i]), want) == 0, (i, levels[i], steps[i])
+
+
+def test_ciphertext_batch_transfers(small):
+    """A contiguous ciphertext batch: one-copy round trips through host memory,
+    rotation of batch ciphertexts equal to that of ordinary ones, and the
+    per-ciphertext fallback once a ciphertext's level changes."""
+    g = small.g
+    levels = [5, 2, 4]
+    batch = g.ct_create_batch(levels, small.P["scale"])
+    singles = []
+    for i, (lv, b) in enumerate(zip(levels, batch)):
+        c, _ = small.encrypt_both(synth.small_int_poly(71, i, small.N, 1 << 40), nonce=7100 + i, level=lv)
+        g.drop_level(c, lv, out=b)
+        singles.append(c)
+    words = sum(2 * lv * small.N for lv in levels)
+    host = np.zeros(words, dtype=np.uint64)
+    g.ct_download_many_async(batch, host.ctypes.data)
+    g.sync()
+    off = 0
+    for lv, c in zip(levels, singles):
+        n = 2 * lv * small.N
+        assert np.array_equal(host[off:off + n].reshape(2, lv, small.N), g.ct_download(c))
+        off += n
+    other = g.ct_create_batch(levels, small.P["scale"])
+    g.ct_upload_many_async(other, host.ctypes.data)
+    g.sync()
+    outs_b = g.ct_create_batch(levels, small.P["scale"])
+    g.rotate_batch(other, outs_b, [1, -1, 5])
+    outs_s = [g.ct_create(1) for _ in levels]
+    g.rotate_batch(singles, outs_s, [1, -1, 5])
+    for a, b in zip(outs_b, outs_s):
+        assert gpu_common.mismatch(g.ct_download(a), g.ct_download(b)) == 0
+    # a level change breaks contiguity: the copies go one by one and stay right
+    g.drop_level(other[0], 3, out=other[0])
+    back = np.zeros(sum(2 * g.ct_info(c)[0] * small.N for c in other), dtype=np.uint64)
+    g.ct_download_many_async(other, back.ctypes.data)
+    g.sync()
+    assert np.array_equal(back[:2 * 3 * small.N].reshape(2, 3, small.N), g.ct_download(other[0]))
+    del batch, other, outs_b
