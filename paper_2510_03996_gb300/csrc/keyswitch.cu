@@ -182,7 +182,7 @@ struct UpAJob : JobCommon {
                 for (int v = 0; v < ntt::R / 2; v++) acc_mad(a[v], s[J[h * 8 + v]], c);
             }
 #pragma unroll
-            for (int v = 0; v < ntt::R / 2; v++) x[h * 8 + v] = redc_acc(a[v], m.q, m.qneg_inv);
+            for (int v = 0; v < ntt::R / 2; v++) x[h * 8 + v] = redc_lazy(a[v].hi, a[v].lo, m.q, m.qneg_inv); // [0, 2q): the NTT takes it lazily
         }
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
@@ -321,7 +321,7 @@ struct DnAJob : JobCommon {
                 for (int v = 0; v < ntt::R / 2; v++) acc_mad(a[v], s[J[h * 8 + v]], c);
             }
 #pragma unroll
-            for (int v = 0; v < ntt::R / 2; v++) x[h * 8 + v] = redc_acc(a[v], m.q, m.qneg_inv);
+            for (int v = 0; v < ntt::R / 2; v++) x[h * 8 + v] = redc_lazy(a[v].hi, a[v].lo, m.q, m.qneg_inv); // [0, 2q): the NTT takes it lazily
         }
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
@@ -497,7 +497,7 @@ struct TiledConvJob : JobCommon {
         }
         const ModConst &m = p.tp.mc[midx];
 #pragma unroll
-        for (int v = 0; v < ntt::R; v++) x[v] = redc_acc(a[v], m.q, m.qneg_inv);
+        for (int v = 0; v < ntt::R; v++) x[v] = redc_lazy(a[v].hi, a[v].lo, m.q, m.qneg_inv); // [0, 2q)
     }
     __device__ u64 load_mid(u32 J) const { return mid[J]; }
     __device__ void store_mid(u32 J, u64 v) const { mid[J] = v; }

@@ -380,3 +380,26 @@ def test_ciphertext_batch_transfers(small):
     g.sync()
     assert np.array_equal(back[:2 * 3 * small.N].reshape(2, 3, small.N), g.ct_download(other[0]))
     del batch, other, outs_b
+
+
+def test_multichannel_special_conv_matches_fp64(conv13):
+    """The special conv with C = 2 input channels (Sec. 4.3: tap products over
+    both channel blocks, the channel sum by chained rotations of H*W, the A*
+    mask, two rescales) decrypts to the FP64 convolution summed over the
+    channels."""
+    pr = conv13
+    g = pr.g
+    P = pr.P
+    C, H, W, k = 2, 8, 8, 3
+    pr.add_keys(g.conv2d_rotation_steps(C, k, H, W))
+    X = synth.image(P["seed"], 40, (C, H, W))
+    K = synth.conv_kernel(P["seed"], 41, (1, C, k, k), std=0.3)
+    x = np.zeros(pr.N // 2)
+    x[:C * H * W] = X.reshape(-1)
+    ct = g.encrypt(pr.pk, g.encode(x, pr.L, P["scale"]), nonce=40)
+    out = g.conv2d(ct, C, k, 1, 1, H, W, K[0], bias=[0.2])
+    assert g.ct_info(out)[0] == pr.L - 2
+    y = np.asarray(g.decode(g.decrypt(pr.sk, out))).real
+    want = OF.conv2d_fp64(X, K, b=[0.2], pad=1).reshape(-1)
+    assert np.max(np.abs(y[:H * W] - want)) < 1e-4
+    assert np.max(np.abs(y[H * W:C * H * W])) < 1e-4  # the A* mask cleared the other block
