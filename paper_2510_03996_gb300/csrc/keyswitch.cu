@@ -505,8 +505,12 @@ struct TiledConvJob : JobCommon {
 };
 
 // UPB, schedule 1: the plain second forward pass of new limb t of digit j
-// (same tasks as UPA), final values back into ext[j][t]
+// (same tasks as UPA), final values back into ext[j][t].  Over a lazy prime
+// they stay unreduced (< 36q): the inner product's 128-bit sum of at most 16
+// such values times key words (< q) stays below q 2^64 for q < 2^54, so its one
+// REDC still returns canonical residues
 struct UpB2Job : JobCommon {
+    static constexpr bool LAZY_OUT = true;
     u64 *mid;
     __device__ UpB2Job(const BatchParams &P, u32 task) : JobCommon(P)
     {

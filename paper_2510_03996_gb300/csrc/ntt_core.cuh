@@ -99,6 +99,9 @@ struct JobBase {
     // gets every final value of the thread at once, so a job that reads
     // operands to combine with them can issue those loads together
     static constexpr bool TILE_STORE = false;
+    // a forward transform over a lazy prime may hand its consumer the values
+    // unreduced (below 36q for up to 17 stages from inputs below 2q)
+    static constexpr bool LAZY_OUT = false;
 };
 
 // reduce v < 2^64 to [0, q) with one Shoup product by 1 and a subtraction
@@ -261,6 +264,7 @@ __device__ __forceinline__ void pass_body(Job &job, u32 tile)
                 const ulonglong2 s = job.inv_scale();
                 return shoup(val, s.x, s.y, q); // any input < 2^64
             }
+            if (LAZY && Job::LAZY_OUT) return val;
             return LAZY ? reduce_any(val, mc) : reduce4q(val, q);
         };
         auto emit = [&](int k, u32 J, u64 val) {
