@@ -77,6 +77,7 @@ _SIGS = {
     "oracle_const_factor": (ctypes.c_int64, [vp, U32, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
     "oracle_llround": (ctypes.c_int64, [ctypes.c_double]),
     "oracle_cheb_coeffs": (None, [ctypes.c_double, U32, ctypes.POINTER(ctypes.c_double)]),
+    "oracle_cos_cheb_coeffs": (None, [ctypes.c_double, U32, U32, ctypes.POINTER(ctypes.c_double)]),
     "oracle_encrypt": (None, [vp, u64p, i64p, U64, u64p]),
     "oracle_plain_from_coeffs": (None, [vp, i64p, U32, u64p]),
     "oracle_decrypt": (None, [vp, u64p, u64p, U32, u64p]),

@@ -780,6 +780,25 @@ void oracle_cheb_coeffs(double beta, u32 D, double *out)
     out[0] *= 0.5;
 }
 
+/* Chebyshev interpolant of the scaled cosine of bootstrapping's modular
+ * reduction, f(z) = cos(2 pi (K z - 1/4) / 2^r) on [-1, 1] (so that r
+ * double-angle steps give sin(2 pi K z)), at the same D+1 nodes and with the
+ * same coefficient formula as oracle_cheb_coeffs. */
+void oracle_cos_cheb_coeffs(double K, u32 r, u32 D, double *out)
+{
+    for (u32 d = 0; d <= D; d++) {
+        double sum = 0.0;
+        for (u32 k = 0; k <= D; k++) {
+            double th = M_PI * ((double)k + 0.5) / (double)(D + 1);
+            double z = cos(th);
+            double f = cos((2.0 * M_PI) * (K * z - 0.25) / ldexp(1.0, (int)r));
+            sum += f * cos((double)d * th);
+        }
+        out[d] = sum * 2.0 / (double)(D + 1);
+    }
+    out[0] *= 0.5;
+}
+
 /* round half away from zero (the encoding of a constant c at scale D is
  * llround(c * D)) */
 i64 oracle_llround(double x) { return llround(x); }

@@ -218,20 +218,18 @@ def relu_mask_values(nslots, beta, n):
     return v
 
 
-def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
-    """Alg. 4 on a ciphertext of scale `scale` (returns (ct, scale)):
-    v = x * mask (rescaled; only when beta > 1), then the Chebyshev series of f
-    at v.  T_1 = v; T_2h = 2 T_h^2 - 1 (product at T_h's level, rescaled, then
-    -1 added); T_2h+1 = 2 T_h+1 T_h - T_1: the product (scale S = s_h+1 s_h,
-    at the lower operand level) plus T_1 times K = llround((-1 * S) / s_1),
-    rescaled once.  Finally y = sum_d K_d T_d (d >= 1, all at one level, K_d =
-    llround(((c_d * scale) * q) / s_d) for the prime q the sum is rescaled by),
-    rescaled once onto `scale`, plus c_0.  The output has the input's scale, at
-    depth ceil(log2 D) + 1 (+1 with the mask) below the input."""
+def cheb_encrypted(ctx, v, scale, c, rlk):
+    """sum_d c_d T_d(v) for a ciphertext v of scale `scale` (returns the
+    ciphertext, of scale `scale`).  T_1 = v; T_2h = 2 T_h^2 - 1 (product at
+    T_h's level, rescaled, then -1 added); T_2h+1 = 2 T_h+1 T_h - T_1: the
+    product (scale S = s_h+1 s_h, at the lower operand level) plus T_1 times
+    K = llround((-1 * S) / s_1), rescaled once.  Finally y = sum_d K_d T_d
+    (d >= 1, all at one level, K_d = llround(((c_d * scale) * q) / s_d) for the
+    prime q the sum is rescaled by), rescaled once onto `scale`, plus c_0.
+    Depth ceil(log2 D) + 1 for degree D."""
     q = ctx.q
-    c = relu_cheb_coeffs(beta, D)
+    D = len(c) - 1
     lev = lambda a: a.shape[1]  # noqa: E731
-    v = ctx.rescale(ctx.mul_plain(ct, mask_plain)) if beta > 1 else ct
     T = {1: (v, scale)}
     for d in range(2, D + 1):
         (A, sa), (B, sb) = T[d - d // 2], T[d // 2]
@@ -252,7 +250,17 @@ def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
         A, sa = T[d]
         term = ctx.mul_int(ctx.drop_level(A, lstar + 1), ctx.const_factor(lstar + 1, c[d], scale, sa))
         y = term if y is None else ctx.add(y, term)
-    return ctx.add_const(ctx.rescale(y), c[0], scale), scale
+    return ctx.add_const(ctx.rescale(y), c[0], scale)
+
+
+def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
+    """Alg. 4 on a ciphertext of scale `scale` (returns (ct, scale)):
+    v = x * mask (rescaled; only when beta > 1), then the Chebyshev series of f
+    at v (cheb_encrypted).  The output has the input's scale, at depth
+    ceil(log2 D) + 1 (+1 with the mask) below the input."""
+    c = relu_cheb_coeffs(beta, D)
+    v = ctx.rescale(ctx.mul_plain(ct, mask_plain)) if beta > 1 else ct
+    return cheb_encrypted(ctx, v, scale, c, rlk), scale
 
 
 # ------------------------------------------------------------------ packed network layers

@@ -36,6 +36,10 @@ def params(name):
     if name == "relu_n12":  # test-sized with the depth of one approximate ReLU (8 levels) and 2 to spare;
         # P (180 bits) above the largest digit (60 + 40 + 40 bits) keeps key-switching noise small
         return dict(logN=12, qbits=[60] + [40] * 10, pbits=[60, 60, 60], dnum=4, scale=2.0 ** 40, seed=SEED_BASE + 9)
+    if name == "boot_n12":  # test-sized bootstrapping: q_0 (2^12 above the scale), 2 levels left after it, SlotToCoeff 3 x 50 bits,
+        # EvalMod (degree-27 series + 7 doublings) 13 x 60 bits, CoeffToSlot 3 x 60 bits; P 6 x 60 bits
+        return dict(logN=12, qbits=[52] + [40] * 2 + [50] * 3 + [60] * 16, pbits=[60] * 6, dnum=4,
+                    scale=2.0 ** 40, seed=SEED_BASE + 10)
     raise KeyError(name)
 
 
