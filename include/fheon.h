@@ -462,11 +462,65 @@ int fheon_global_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in
  * below log2(N/2). */
 int fheon_fc(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t m, const double *W, const double *bias,
              uint32_t max_keys, fheon_ct *out);
-/* CKKS bootstrapping (the paper's deeper networks, Sec. 6): not part of this
- * build; returns FHEON_ERR_UNIMPLEMENTED. */
+/* ------------------------------------------------------------------ */
+/* CKKS bootstrapping (the paper's "Bootstrapping Layer" among its support
+ * functions, placed before the ReLUs of its deeper networks): the published
+ * full-slot method of Cheon, Han, Kim, Kim and Song (2018) with the slot
+ * transforms factored into the butterfly stages of the special FFT and
+ * applied as baby-step/giant-step rotation sums (Chen, Chillotti, Song 2019)
+ * and the modular reduction as a scaled cosine plus double-angle steps (Han,
+ * Ki 2020).  Steps: ModRaise of limb q_0 into all L primes; CoeffToSlot
+ * (cts_levels rotation-sum levels); real and imaginary parts through the
+ * conjugation (Galois element 2N - 1); EvalMod on each (the Chebyshev series
+ * of cos(2 pi (K x - 1/4) / 2^r), then r doublings c <- 2c^2 - 1);
+ * recombination; SlotToCoeff (stc_levels levels).  Consumes
+ * cts_levels + ceil(log2 degree) + 1 + doublings + stc_levels levels: a
+ * bootstrap of a context with L primes leaves the message at level
+ * L minus that.  Inputs are any ciphertext at level >= 1 whose message
+ * coefficients are small against q_0 (slots of magnitude <= 1 at a scale
+ * 2^10 or more below q_0) and whose scale is the one the layer was prepared
+ * for; the output has that scale (to 1e-9) and the same message.  Keys: the
+ * layer's rotation steps, the conjugation and the relinearisation key
+ * (fheon_bootstrap_keygen makes them all). */
+typedef struct fheon_boot_params {
+    uint32_t cts_levels; /* levels of CoeffToSlot, 1 .. log2(N/2) */
+    uint32_t stc_levels; /* levels of SlotToCoeff, 1 .. log2(N/2) */
+    uint32_t K;          /* EvalMod's range: |t / q_0| < K for the raised plaintext t */
+    uint32_t degree;     /* Chebyshev degree of the cosine */
+    uint32_t doublings;  /* double-angle steps r */
+    uint32_t baby;       /* baby steps of every BSGS level (0: fewest rotations) */
+} fheon_boot_params;
+/* Defaults for a context: 3 + 3 levels, K the power of two at or above
+ * 8 sqrt(N / 18) (eight standard deviations of t / q_0 for a uniform ternary
+ * secret), r = log2 K, degree 27. */
+int fheon_boot_params_default(const fheon_ctx *ctx, fheon_boot_params *p);
+/* EvalMod's coefficients c_0..c_degree: the Chebyshev interpolant of
+ * cos(2 pi (K z - 1/4) / 2^r) at the degree+1 nodes cos(pi (k + 1/2) / (degree + 1)). */
+int fheon_evalmod_coeffs(uint32_t K, uint32_t doublings, uint32_t degree, double *out);
+/* Prepare a bootstrap (p NULL: the defaults) for inputs of scale in_scale:
+ * the merged stage diagonals of both transforms in BSGS form, encoded on the
+ * device and owned by the layer.  FHEON_ERR_LEVEL when the context is too
+ * shallow.  Apply it with fheon_layer_apply. */
+int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p, double in_scale, fheon_layer **out);
+/* A bootstrap from caller-prepared levels (rotation-sum layers from
+ * fheon_linear_prepare_plain, without fold or bias, at levels L, L-1, ... for
+ * CoeffToSlot and from L - cts_levels - ceil(log2 degree) - 1 - doublings
+ * down for SlotToCoeff) and EvalMod coefficients (degree + 1).  The layer
+ * keeps pointers to the levels: they must outlive it. */
+int fheon_bootstrap_compose(fheon_ctx *ctx, const fheon_boot_params *p, const fheon_layer *const *cts,
+                            const fheon_layer *const *stc, const double *coeffs, double in_scale, fheon_layer **out);
+/* Generate every key a bootstrap layer uses. */
+int fheon_bootstrap_keygen(fheon_ctx *ctx, const fheon_sk *sk, const fheon_layer *layer);
+/* Output level and scale of a bootstrap layer (scale 0 for a composed one). */
+int fheon_bootstrap_info(const fheon_layer *layer, uint32_t *out_level, double *out_scale);
+/* ModRaise alone: limb q_0 of `in` (any level) to coefficients, lifted to
+ * (-q_0/2, q_0/2], into all L primes; out at level L with in's scale. */
+int fheon_mod_raise(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
+/* One-shot bootstrap with the default parameters for ct's scale (the layer
+ * is prepared on first use and kept with the context); the keys must exist. */
 int fheon_bootstrap(fheon_ctx *ctx, const fheon_ct *ct, fheon_ct *out);
-/* Apply any prepared layer (conv2d, ReLU, rotation-sum, FC); `in` at the
- * layer's level, out distinct from in. */
+/* Apply any prepared layer (conv2d, ReLU, rotation-sum, FC, bootstrap); `in`
+ * at the layer's level (a bootstrap: any level), out distinct from in. */
 int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
 /* The layer on n inputs at once (outputs distinct from every input and each
  * other): a rotation-sum layer runs every input's tap rotations as one

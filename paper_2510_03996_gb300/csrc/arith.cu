@@ -275,6 +275,27 @@ struct ReduceLoadJob : MapJob {
     }
 };
 
+// Forward NTT of the centred lift of [x]_{q_0} into each q_i (ModRaise):
+// coefficients above q_0 / 2 stand for x - q_0, whose residue is
+// x mod q_i - q_0 mod q_i (both reduced by REDC(v * (2^64 mod q_i))).
+struct CenterLoadJob : MapJob {
+    using Params = MapParams;
+    __device__ CenterLoadJob(const MapParams &P, u32 job) : MapJob(P, job)
+    {
+        in = P.in + (job / P.per_poly) * P.in_poly_stride;
+    }
+    template <bool INV> __device__ u64 load_first(u32 J) const
+    {
+        const ModConst m = p.tp.mc[midx];
+        const u64 q0 = p.tp.mc[0].q;
+        const u64 v = in[J];
+        const u64 r = redc(__umul64hi(v, m.r1), v * m.r1, m.q, m.qneg_inv);
+        if (v <= (q0 >> 1)) return r;
+        const u64 c = redc(__umul64hi(q0, m.r1), q0 * m.r1, m.q, m.qneg_inv);
+        return r >= c ? r - c : r + m.q - c;
+    }
+};
+
 inline unsigned blocks2(u64 elems) { return (unsigned)((elems / 2 + TPB - 1) / TPB); }
 } // namespace
 
@@ -375,6 +396,30 @@ cudaError_t ntt_inv_limbs(fheon_ctx *ctx, const u64 *in, u64 *out, u32 n, u32 le
 {
     MapParams mp = map_params(ctx, in, out, n, first_limb, level);
     return ntt::launch<true, MapJob>(ctx->logN, mp, n, st);
+}
+
+int mod_raise_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)
+{
+    const u32 L = ctx->L, N = ctx->N;
+    int rc = ensure_workspace(ctx, ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L);
+    if (rc) return rc;
+    cudaStream_t st = ctx->stream;
+    u64 *x0 = ctx->ws.as<u64>(); // [2][N] coefficients mod q_0
+    {
+        MapParams mp = map_params(ctx, in->c0(), x0, 1, 0, 1);
+        mp.in_poly_stride = (u64)in->level * N;
+        mp.out_poly_stride = N;
+        FHEON_CUDA(ctx, (ntt::launch<true, MapJob>(ctx->logN, mp, 2, st)));
+    }
+    if ((rc = ct_reshape(ctx, out, L))) return rc;
+    {
+        MapParams mp = map_params(ctx, x0, out->c0(), L, 0, L);
+        mp.in_poly_stride = N;
+        mp.out_poly_stride = (u64)L * N;
+        FHEON_CUDA(ctx, (ntt::launch<false, CenterLoadJob>(ctx->logN, mp, 2 * L, st)));
+    }
+    prof_mark(st, "mod_raise");
+    return FHEON_OK;
 }
 
 int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)

@@ -1,0 +1,546 @@
+// boot.cu -- CKKS bootstrapping as a layer.  The paper offers it as a layer
+// placed anywhere in a network (the "Bootstrapping Layer" among its support
+// functions; its evaluation bootstraps before every ReLU but the first two,
+// before the second pooling layer and before the global pooling) and takes
+// the algorithm from its library.  This is the published full-slot
+// bootstrapping (Cheon, Han, Kim, Kim, Song 2018) with the slot transforms
+// factored into the butterfly stages of the special FFT and applied as
+// baby-step/giant-step rotation sums (Chen, Chillotti, Song 2019), and the
+// modular reduction as a scaled cosine followed by double-angle steps (Han,
+// Ki 2020).  Every step runs on the device operations of this library:
+//
+//   1. ModRaise: limb q_0 of the input to coefficients, centred, into all L
+//      primes (mod_raise_ct); it decrypts to t = m + q_0 I, |I| < K.  The
+//      raised ciphertext is given scale q_0: its slots are F(t_lo + i t_hi)/q_0.
+//   2. CoeffToSlot: the inverse butterfly stages of F (top stages first),
+//      merged into `cts_levels` rotation-sum layers, 1/(2K) folded into the
+//      first: (t_lo + i t_hi) / (2 K q_0) in bit-reversed slot order.
+//   3. With the conjugate c' (Galois element 2N - 1): re = c + c',
+//      im = (c' - c) X^(N/2), holding t_lo / (K q_0) and t_hi / (K q_0).
+//   4. EvalMod on each: the Chebyshev series of cos(2 pi (K x - 1/4) / 2^r),
+//      then r steps c <- 2 c^2 - 1: sin(2 pi t / q_0) ~= 2 pi m / q_0.
+//   5. re + im X^(N/2).
+//   6. SlotToCoeff: the butterfly stages of F (low stages first), merged into
+//      `stc_levels` layers, q_0 / (2 pi Delta_in) folded into the first; the
+//      last is encoded so that the output lands on scale ~= Delta_in.
+//
+// Stage of half-length h of F (blocks of 2h slots, u < h the position in the
+// block, w_u = exp(2 pi i (5^u mod 8h) / 8h)):
+//   out[b+u] = in[b+u] + w_u in[b+u+h],  out[b+u+h] = in[b+u] - w_u in[b+u+h];
+// as slot diagonals (out = sum_o d_o Rot_o(in)) it has offsets 0, +h and -h.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <map>
+#include <memory>
+#include <set>
+#include <vector>
+
+#include "layer.h"
+
+using namespace fheon;
+
+namespace {
+
+using cd = std::complex<double>;
+using Diags = std::map<u32, std::vector<cd>>; // offset mod n -> diagonal
+
+u64 powmod_small(u64 b, u64 e, u64 m)
+{
+    u64 r = 1 % m;
+    b %= m;
+    while (e) {
+        if (e & 1) r = (r * b) % m;
+        b = (b * b) % m;
+        e >>= 1;
+    }
+    return r;
+}
+
+Diags stage(u32 n, u32 h, bool inverse)
+{
+    const u32 m = 2 * h;
+    std::vector<cd> d0(n), dp(n), dm(n);
+    for (u32 j = 0; j < n; j++) {
+        const u32 u = j % m;
+        const bool lo = u < h;
+        const u64 e = powmod_small(5, lo ? u : u - h, 4ull * m);
+        const double a = 2.0 * M_PI * (double)e / (double)(4ull * m);
+        const cd w(std::cos(a), std::sin(a));
+        if (!inverse) {
+            d0[j] = lo ? cd(1.0) : -w;
+            dp[j] = lo ? w : cd(0.0);
+            dm[j] = lo ? cd(0.0) : cd(1.0);
+        } else {
+            d0[j] = lo ? cd(0.5) : -0.5 / w;
+            dp[j] = lo ? cd(0.5) : cd(0.0);
+            dm[j] = lo ? cd(0.0) : 0.5 / w;
+        }
+    }
+    Diags out;
+    auto put = [&](u32 o, const std::vector<cd> &d) {
+        auto it = out.find(o);
+        if (it == out.end()) {
+            out.emplace(o, d);
+        } else {
+            for (u32 j = 0; j < n; j++) it->second[j] += d[j];
+        }
+    };
+    put(0, d0);
+    put(h % n, dp);
+    put((n - h % n) % n, dm);
+    return out;
+}
+
+// A.B (B applied first): (A B v)[j] = sum_a A_a[j] (B v)[j + a]
+Diags compose(const Diags &A, const Diags &B, u32 n)
+{
+    Diags C;
+    for (const auto &a : A)
+        for (const auto &b : B) {
+            const u32 c = (a.first + b.first) % n;
+            auto it = C.find(c);
+            if (it == C.end()) it = C.emplace(c, std::vector<cd>(n, cd(0.0))).first;
+            for (u32 j = 0; j < n; j++) it->second[j] += a.second[j] * b.second[(j + a.first) % n];
+        }
+    return C;
+}
+
+// stages 1..logn split into `levels` consecutive groups, the larger ones at the top
+std::vector<std::vector<u32>> stage_groups(u32 logn, u32 levels)
+{
+    std::vector<std::vector<u32>> g(levels);
+    const u32 base = logn / levels, extra = logn % levels;
+    u32 s = 1;
+    for (u32 i = 0; i < levels; i++) {
+        const u32 sz = base + (i >= levels - extra ? 1 : 0);
+        for (u32 k = 0; k < sz; k++) g[i].push_back(s++);
+    }
+    return g;
+}
+
+struct MergedLevel {
+    u32 stride;
+    Diags M;
+};
+
+std::vector<MergedLevel> merged_levels(u32 n, u32 levels, bool cts)
+{
+    u32 logn = 0;
+    while ((1u << logn) < n) logn++;
+    auto groups = stage_groups(logn, levels);
+    if (cts) std::reverse(groups.begin(), groups.end());
+    std::vector<MergedLevel> out;
+    for (auto &g : groups) {
+        if (cts) std::reverse(g.begin(), g.end()); // top stage of the group first
+        Diags M;
+        bool first = true;
+        for (u32 s : g) {
+            Diags S = stage(n, 1u << (s - 1), cts);
+            M = first ? S : compose(S, M, n);
+            first = false;
+        }
+        out.push_back(MergedLevel{1u << (std::min(g.front(), g.back()) - 1), std::move(M)});
+    }
+    return out;
+}
+
+int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// BSGS form of sum_o d_o Rot_o: offsets k * stride (k centred in (-M/2, M/2],
+// M = n / stride) split as k = c bs + t, 0 <= t < bs:
+//   out = sum_c Rot_{G_c}( sum_t Rot_{-G_c}(d_k) Rot_{t stride}(in) ),  G_c = c bs stride.
+// bs = `baby`, else the power of two with the fewest rotations (ties: larger).
+struct Bsgs {
+    std::vector<int32_t> r, s;
+    std::vector<std::vector<cd>> vals; // [g * r.size() + t], empty = no product
+};
+
+Bsgs bsgs(const Diags &D, u32 n, u32 stride, u32 baby)
+{
+    const int64_t M = n / stride;
+    std::map<int64_t, const std::vector<cd> *> ks;
+    for (const auto &kv : D) {
+        bool any = false;
+        for (const cd &x : kv.second) any = any || x != cd(0.0);
+        if (!any) continue;
+        int64_t k = kv.first / stride;
+        if (k > M / 2) k -= M;
+        ks[k] = &kv.second;
+    }
+    auto split = [&](int64_t bs, std::set<int64_t> &ts, std::set<int64_t> &cs) {
+        ts.clear();
+        cs.clear();
+        for (auto &kv : ks) {
+            const int64_t c = floordiv(kv.first, bs);
+            cs.insert(c);
+            ts.insert(kv.first - c * bs);
+        }
+    };
+    std::set<int64_t> ts, cs;
+    int64_t bs = baby;
+    if (!bs) {
+        int64_t best = -1;
+        for (int64_t b = 1; b <= M; b *= 2) {
+            split(b, ts, cs);
+            const int64_t cost = (int64_t)ts.size() - (int64_t)ts.count(0) + (int64_t)cs.size() - (int64_t)cs.count(0);
+            if (best < 0 || cost <= best) {
+                best = cost;
+                bs = b;
+            }
+        }
+    }
+    split(bs, ts, cs);
+    Bsgs out;
+    for (int64_t t : ts) out.r.push_back((int32_t)(t * stride));
+    for (int64_t c : cs) {
+        const int64_t G = c * bs * (int64_t)stride;
+        out.s.push_back((int32_t)G);
+        const u32 sh = (u32)(((G % (int64_t)n) + n) % n);
+        for (int64_t t : ts) {
+            auto it = ks.find(c * bs + t);
+            if (it == ks.end()) {
+                out.vals.emplace_back();
+                continue;
+            }
+            // Rot_{-G}(d)[i] = d[i - G]
+            std::vector<cd> v(n);
+            for (u32 i = 0; i < n; i++) v[i] = (*it->second)[(i + n - sh) % n];
+            out.vals.push_back(std::move(v));
+        }
+    }
+    return out;
+}
+
+// one merged level as a rotation-sum layer, its plaintexts (values times
+// `factor`, encoded at `pscale`) owned by the layer
+int level_layer(fheon_ctx *ctx, const MergedLevel &ml, cd factor, u32 baby, u32 level, double pscale,
+                fheon_layer **out)
+{
+    const u32 n = ctx->N / 2;
+    Bsgs B = bsgs(ml.M, n, ml.stride, baby);
+    const u32 nt = (u32)B.r.size(), ng = (u32)B.s.size();
+    std::vector<fheon_pt *> pts((size_t)nt * ng, nullptr);
+    std::vector<double> re(n), im(n);
+    int rc = FHEON_OK;
+    for (size_t i = 0; i < pts.size() && !rc; i++) {
+        if (B.vals[i].empty()) continue;
+        for (u32 j = 0; j < n; j++) {
+            const cd v = B.vals[i][j] * factor;
+            re[j] = v.real();
+            im[j] = v.imag();
+        }
+        rc = fheon_encode_plain(ctx, re.data(), im.data(), n, level, pscale, &pts[i]);
+    }
+    if (!rc)
+        rc = fheon_linear_prepare_plain(ctx, 0, nullptr, nt, B.r.data(), ng, B.s.data(), pts.data(), nullptr, level,
+                                        out);
+    if (rc) {
+        for (fheon_pt *p : pts) fheon_pt_destroy(p);
+        return rc;
+    }
+    for (fheon_pt *p : pts)
+        if (p) (*out)->pt_store.push_back(p);
+    return FHEON_OK;
+}
+
+u32 boot_depth(const fheon_boot_params &p) { return p.cts_levels + cheb_depth(p.degree) + p.doublings + p.stc_levels; }
+
+int check_params(fheon_ctx *ctx, const fheon_boot_params *p)
+{
+    u32 logn = ctx->logN - 1;
+    if (!p->cts_levels || !p->stc_levels || p->cts_levels > logn || p->stc_levels > logn || !p->K ||
+        p->degree < 2 || p->degree > 1023 || p->doublings > 30)
+        return fail(ctx, FHEON_ERR_ARG, "bootstrap: levels in [1, log2(N/2)], K >= 1, degree in [2, 1023]");
+    if (boot_depth(*p) > ctx->L - 1)
+        return fail(ctx, FHEON_ERR_LEVEL, "bootstrap needs %u levels above q_0, the context has %u", boot_depth(*p),
+                    ctx->L - 1);
+    return FHEON_OK;
+}
+
+// the scale the series starts on and the one SlotToCoeff starts on, in the
+// order the operations compute them
+double evalmod_end_scale(fheon_ctx *ctx, double s, u32 lv, u32 r)
+{
+    for (u32 i = 0; i < r; i++) {
+        s = (s * s) / (double)ctx->mod[lv - 1];
+        lv--;
+    }
+    return s;
+}
+
+// a default layer per context, kept for the one-shot call
+struct DefaultBoot {
+    double scale = 0;
+    fheon_layer *ly = nullptr;
+};
+std::map<const fheon_ctx *, DefaultBoot> g_default;
+
+} // namespace
+
+namespace fheon {
+
+int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
+{
+    if (in->level < 1) return fail(ctx, FHEON_ERR_LEVEL, "bootstrap: empty ciphertext");
+    if (std::fabs(in->scale - ly->in_scale) > 1e-9 * ly->in_scale)
+        return fail(ctx, FHEON_ERR_SCALE, "bootstrap prepared for scale %g, got %g", ly->in_scale, in->scale);
+    const u32 N = ctx->N, D = (u32)ly->coeffs.size() - 1;
+    int rc;
+    // working ciphertexts: 0 raised, 1-2 chain, 3 conjugate, 4 difference,
+    // 5-6 doubling ping-pong (re), 7-8 (im), 9 product
+    if (ly->work.size() < 10) ly->work.resize(10, nullptr);
+    for (fheon_ct *&c : ly->work)
+        if (!c && (rc = fheon_ct_create(ctx, 1, 1.0, &c))) return rc;
+    fheon_ct **w = ly->work.data();
+    if ((rc = mod_raise_ct(ctx, in, w[0]))) return rc;
+    w[0]->scale = (double)ctx->mod[0];
+    const fheon_ct *x = w[0];
+    for (u32 i = 0; i < ly->ncts; i++) {
+        fheon_ct *dst = w[1 + (i & 1)];
+        if ((rc = fheon_layer_apply(ctx, ly->subs[i], x, dst))) return rc;
+        x = dst;
+    }
+    // real and imaginary parts: T_1 of each part's series
+    const u32 lv = x->level;
+    if ((rc = cheb_work(ctx, ly->rot, D, lv, x->scale))) return rc;
+    if ((rc = cheb_work(ctx, ly->cheb2, D, lv, x->scale))) return rc;
+    if ((rc = fheon_rotate_galois(ctx, x, 2ull * N - 1, w[3]))) return rc;
+    if ((rc = fheon_add(ctx, x, w[3], ly->rot[1]))) return rc;
+    if ((rc = fheon_mul_int(ctx, x, -1, w[4]))) return rc;
+    if ((rc = fheon_add(ctx, w[3], w[4], w[4]))) return rc;
+    if ((rc = fheon_mul_plain(ctx, w[4], ly->mono[0], ly->cheb2[1]))) return rc;
+    fheon_ct *part[2];
+    std::vector<fheon_ct *> *works[2] = {&ly->rot, &ly->cheb2};
+    for (int k = 0; k < 2; k++) {
+        fheon_ct *a = w[5 + 2 * k], *b = w[6 + 2 * k];
+        if ((rc = cheb_series(ctx, ly->coeffs, *works[k], a))) return rc;
+        for (u32 i = 0; i < ly->boot_r; i++) {
+            // 2 c^2 - 1: the doubled product rescaled, then -1 at the new scale
+            if ((rc = mul_relin_at(ctx, a, a, a->level, true, b))) return rc;
+            if ((rc = fheon_rescale(ctx, b, b))) return rc;
+            if ((rc = fheon_add_const(ctx, b, -1.0, b))) return rc;
+            std::swap(a, b);
+        }
+        part[k] = a;
+    }
+    if ((rc = fheon_mul_plain(ctx, part[1], ly->mono[1], w[9]))) return rc;
+    if ((rc = fheon_add(ctx, part[0], w[9], w[9]))) return rc;
+    x = w[9];
+    const u32 nst = (u32)ly->subs.size() - ly->ncts;
+    for (u32 i = 0; i < nst; i++) {
+        fheon_ct *dst = i + 1 == nst ? out : w[1 + (i & 1)];
+        if ((rc = fheon_layer_apply(ctx, ly->subs[ly->ncts + i], x, dst))) return rc;
+        x = dst;
+    }
+    return FHEON_OK;
+}
+
+} // namespace fheon
+
+extern "C" {
+
+int fheon_boot_params_default(const fheon_ctx *ctx, fheon_boot_params *p)
+{
+    if (!ctx || !p) return FHEON_ERR_ARG;
+    p->cts_levels = 3;
+    p->stc_levels = 3;
+    // |t / q_0| for a uniform ternary secret: a coefficient of c_1 s sums about
+    // 2N/3 terms uniform in [-q_0/2, q_0/2), standard deviation ~ sqrt(N/18);
+    // K = the power of two at or above 8 of those
+    const double x = 8.0 * std::sqrt((double)ctx->N / 18.0);
+    u32 K = 1;
+    while ((double)K < x) K *= 2;
+    p->K = K;
+    u32 r = 0;
+    while ((1u << r) < K) r++;
+    p->doublings = r;
+    p->degree = 27;
+    p->baby = 0;
+    return FHEON_OK;
+}
+
+int fheon_evalmod_coeffs(uint32_t K, uint32_t doublings, uint32_t degree, double *out)
+{
+    if (!out || !K || degree < 1 || degree > 1023 || doublings > 30) return FHEON_ERR_ARG;
+    const u32 D = degree;
+    for (u32 d = 0; d <= D; d++) {
+        double sum = 0.0;
+        for (u32 k = 0; k <= D; k++) {
+            const double th = M_PI * ((double)k + 0.5) / (double)(D + 1);
+            const double z = std::cos(th);
+            const double f = std::cos((2.0 * M_PI) * ((double)K * z - 0.25) / std::ldexp(1.0, (int)doublings));
+            sum += f * std::cos((double)d * th);
+        }
+        out[d] = sum * 2.0 / (double)(D + 1);
+    }
+    out[0] *= 0.5;
+    return FHEON_OK;
+}
+
+int fheon_bootstrap_compose(fheon_ctx *ctx, const fheon_boot_params *p, const fheon_layer *const *cts,
+                            const fheon_layer *const *stc, const double *coeffs, double in_scale, fheon_layer **out)
+{
+    if (!ctx || !p || !cts || !stc || !coeffs || !out || !(in_scale > 0)) return FHEON_ERR_ARG;
+    int rc = check_params(ctx, p);
+    if (rc) return rc;
+    const u32 L = ctx->L;
+    u32 lv = L;
+    for (u32 i = 0; i < p->cts_levels + p->stc_levels; i++) {
+        const fheon_layer *s = i < p->cts_levels ? cts[i] : stc[i - p->cts_levels];
+        if (!s || s->kind != LAYER_LINEAR || !s->fold.empty() || s->bias)
+            return fail(ctx, FHEON_ERR_ARG, "bootstrap: level %u is not a rotation-sum layer", i);
+        if (i == p->cts_levels) lv -= cheb_depth(p->degree) + p->doublings;
+        if (s->level != lv) return fail(ctx, FHEON_ERR_LEVEL, "bootstrap: level %u at %u, expected %u", i, s->level, lv);
+        lv--;
+    }
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_BOOT;
+    ly->level = L;
+    ly->ncts = p->cts_levels;
+    for (u32 i = 0; i < p->cts_levels; i++) ly->subs.push_back(const_cast<fheon_layer *>(cts[i]));
+    for (u32 i = 0; i < p->stc_levels; i++) ly->subs.push_back(const_cast<fheon_layer *>(stc[i]));
+    ly->coeffs.assign(coeffs, coeffs + p->degree + 1);
+    ly->boot_K = p->K;
+    ly->boot_r = p->doublings;
+    ly->in_scale = in_scale;
+    ly->out_level = lv;
+    // X^(N/2) (the constant i in every slot, scale 1) where im is formed and
+    // where the parts are recombined
+    std::vector<int64_t> mono(ctx->N, 0);
+    mono[ctx->N / 2] = 1;
+    const u32 l0 = L - p->cts_levels, l1 = l0 - cheb_depth(p->degree) - p->doublings;
+    if ((rc = fheon_plain_from_coeffs(ctx, mono.data(), l0, 1.0, &ly->mono[0]))) return rc;
+    if ((rc = fheon_plain_from_coeffs(ctx, mono.data(), l1, 1.0, &ly->mono[1]))) return rc;
+    *out = ly.release();
+    return FHEON_OK;
+}
+
+int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double in_scale, fheon_layer **out)
+{
+    if (!ctx || !out || !(in_scale > 0)) return FHEON_ERR_ARG;
+    fheon_boot_params p;
+    if (p_) {
+        p = *p_;
+    } else {
+        fheon_boot_params_default(ctx, &p);
+    }
+    int rc = check_params(ctx, &p);
+    if (rc) return rc;
+    const u32 L = ctx->L, n = ctx->N / 2;
+    std::vector<double> coeffs(p.degree + 1);
+    if ((rc = fheon_evalmod_coeffs(p.K, p.doublings, p.degree, coeffs.data()))) return rc;
+    std::vector<fheon_layer *> subs;
+    auto cleanup = [&]() {
+        for (fheon_layer *l : subs) delete l;
+    };
+    u32 lv = L;
+    double s = (double)ctx->mod[0];
+    const double q0 = (double)ctx->mod[0];
+    // CoeffToSlot: 1/(2K) and the change of scale q_0 -> Delta_b in the first level
+    const double delta_b = (double)ctx->mod[L - p.cts_levels - 1];
+    auto cl = merged_levels(n, p.cts_levels, true);
+    for (u32 i = 0; i < p.cts_levels; i++) {
+        const double q = (double)ctx->mod[lv - 1];
+        const double ps = i == 0 ? q * (delta_b / q0) : q;
+        fheon_layer *l = nullptr;
+        if ((rc = level_layer(ctx, cl[i], cd(i == 0 ? 1.0 / (2.0 * (double)p.K) : 1.0), p.baby, lv, ps, &l))) {
+            cleanup();
+            return rc;
+        }
+        subs.push_back(l);
+        s = (s * ps) / q;
+        lv--;
+    }
+    lv -= cheb_depth(p.degree);
+    s = evalmod_end_scale(ctx, s, lv, p.doublings);
+    lv -= p.doublings;
+    // SlotToCoeff: q_0 / (2 pi Delta_in) in the first level, the change of
+    // scale onto Delta_in in the last
+    auto sl = merged_levels(n, p.stc_levels, false);
+    for (u32 i = 0; i < p.stc_levels; i++) {
+        const double q = (double)ctx->mod[lv - 1];
+        const double ps = i + 1 == p.stc_levels ? q * (in_scale / s) : q;
+        fheon_layer *l = nullptr;
+        const cd f(i == 0 ? q0 / (2.0 * M_PI * in_scale) : 1.0);
+        if ((rc = level_layer(ctx, sl[i], f, p.baby, lv, ps, &l))) {
+            cleanup();
+            return rc;
+        }
+        subs.push_back(l);
+        s = (s * ps) / q;
+        lv--;
+    }
+    rc = fheon_bootstrap_compose(ctx, &p, subs.data(), subs.data() + p.cts_levels, coeffs.data(), in_scale, out);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    (*out)->own_subs = true;
+    (*out)->out_scale = s;
+    return FHEON_OK;
+}
+
+int fheon_bootstrap_keygen(fheon_ctx *ctx, const fheon_sk *sk, const fheon_layer *ly)
+{
+    if (!ctx || !sk || !ly || ly->kind != LAYER_BOOT) return FHEON_ERR_ARG;
+    u32 n = 0;
+    int rc = fheon_layer_rotation_steps(ly, nullptr, &n);
+    if (rc) return rc;
+    std::vector<int32_t> st(n);
+    if ((rc = fheon_layer_rotation_steps(ly, st.data(), &n))) return rc;
+    if ((rc = fheon_rotkeygen(ctx, sk, st.data(), n))) return rc;
+    const uint64_t conj = 2ull * ctx->N - 1;
+    if ((rc = fheon_galois_keygen(ctx, sk, &conj, 1))) return rc;
+    return fheon_relinkeygen(ctx, sk);
+}
+
+int fheon_bootstrap_info(const fheon_layer *ly, uint32_t *out_level, double *out_scale)
+{
+    if (!ly || ly->kind != LAYER_BOOT) return FHEON_ERR_ARG;
+    if (out_level) *out_level = ly->out_level;
+    if (out_scale) *out_scale = ly->out_scale;
+    return FHEON_OK;
+}
+
+int fheon_mod_raise(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !in || !out || in->level < 1) return FHEON_ERR_ARG;
+    int rc = mod_raise_ct(ctx, in, out);
+    if (rc) return rc;
+    out->scale = in->scale;
+    return FHEON_OK;
+}
+
+int fheon_bootstrap(fheon_ctx *ctx, const fheon_ct *ct, fheon_ct *out)
+{
+    if (!ctx || !ct || !out) return FHEON_ERR_ARG;
+    DefaultBoot &d = g_default[ctx];
+    if (!d.ly || std::fabs(d.scale - ct->scale) > 1e-9 * ct->scale) {
+        if (d.ly) {
+            cudaStreamSynchronize(ctx->stream);
+            delete d.ly;
+            d.ly = nullptr;
+        }
+        int rc = fheon_bootstrap_prepare(ctx, nullptr, ct->scale, &d.ly);
+        if (rc) {
+            g_default.erase(ctx);
+            return rc;
+        }
+        d.scale = ct->scale;
+    }
+    return fheon_layer_apply(ctx, d.ly, ct, out);
+}
+
+} // extern "C"
+
+namespace fheon {
+// the one-shot call's cached layer of a context that is going away
+void boot_release(const fheon_ctx *ctx)
+{
+    auto it = g_default.find(ctx);
+    if (it == g_default.end()) return;
+    delete it->second.ly;
+    g_default.erase(it);
+}
+} // namespace fheon

@@ -307,6 +307,7 @@ int fheon_ctx_destroy(fheon_ctx *ctx)
 {
     if (!ctx) return FHEON_OK;
     cudaStreamSynchronize(ctx->stream);
+    boot_release(ctx);
     drop_plans(ctx);
     delete ctx;
     return FHEON_OK;

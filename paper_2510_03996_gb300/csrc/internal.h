@@ -183,6 +183,7 @@ int keyswitch_rotate(fheon_ctx *ctx, const u64 *c0, const u64 *c1, u32 l, u64 g,
                      const u64 *c1add = nullptr);
 int rotate_one(fheon_ctx *ctx, const fheon_ct *in, u64 g, fheon_ct *out);
 void drop_plans(fheon_ctx *ctx); // release the cached batch plans of a context
+void boot_release(const fheon_ctx *ctx); // release the one-shot bootstrap layer of a context
 // hoist: items with the same input share one raising of c1 (fast rotations).
 // keep (optional) receives a reference to the device plan the launches read,
 // for callers that capture them into a graph.
@@ -219,6 +220,8 @@ cudaError_t k_lincomb(fheon_ctx *ctx, const u64 *const *cts, const u64 *strides,
                       u32 level);
 cudaError_t k_add_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, u32 level);
 int rescale_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
+// ModRaise: the lowest limb (q_0) of `in`, centred, into all L primes (out at level L)
+int mod_raise_ct(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
 cudaError_t k_decrypt(fheon_ctx *ctx, const u64 *ct, const u64 *s, u64 *m, u32 level);
 
 // sampler / keygen / encrypt (sampler.cu)

@@ -7,7 +7,7 @@
 #include "internal.h"
 
 // kinds of layer behind the one opaque handle
-enum LayerKind : u32 { LAYER_CONV = 0, LAYER_RELU = 1, LAYER_LINEAR = 2, LAYER_FC = 3 };
+enum LayerKind : u32 { LAYER_CONV = 0, LAYER_RELU = 1, LAYER_LINEAR = 2, LAYER_FC = 3, LAYER_BOOT = 4 };
 
 struct fheon_layer {
     u32 kind = LAYER_CONV;
@@ -32,6 +32,17 @@ struct fheon_layer {
     fheon_pt *bias = nullptr;     // at the output level
     std::vector<bool> owned;      // which of taps are owned by the layer
     bool own_bias = false;
+    // bootstrapping: the CoeffToSlot then SlotToCoeff levels (rotation-sum
+    // layers; owned when own_subs), EvalMod's series in `coeffs` with range K
+    // and r doublings, the scale inputs must have, X^(N/2) at the two levels
+    // it multiplies at, and the output's level and scale
+    std::vector<fheon_layer *> subs;
+    u32 ncts = 0, boot_K = 0, boot_r = 0;
+    bool own_subs = false;
+    double in_scale = 0, out_scale = 0;
+    u32 out_level = 0;
+    fheon_pt *mono[2] = {nullptr, nullptr};
+    mutable std::vector<fheon_ct *> cheb2; // the second part's series working set
     // working ciphertexts (the k^2 - 1 tap rotations, then accumulators), made
     // on the first application and reused, so that later applications (and
     // their graph capture) allocate nothing
@@ -63,6 +74,20 @@ struct fheon_layer {
         for (fheon_ct *c : work) fheon_ct_destroy(c);
         for (fheon_ct *c : fwork) fheon_ct_destroy(c);
         for (fheon_pt *p : pt_store) fheon_pt_destroy(p);
+        if (own_subs)
+            for (fheon_layer *l : subs) delete l;
+        for (fheon_pt *p : mono) fheon_pt_destroy(p);
+        for (fheon_ct *c : cheb2) fheon_ct_destroy(c);
     }
 };
 
+namespace fheon {
+// Chebyshev series (relu.cu): `work` holds D + 4 working ciphertexts
+// (cheb_work makes them); work[1] = T_1 on entry, at the series' input
+// scale; out = sum_d c_d T_d at that scale, ceil(log2 D) + 1 levels below
+int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, double scale);
+int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out);
+u32 cheb_depth(u32 D);
+// bootstrapping (boot.cu)
+int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out);
+} // namespace fheon

@@ -495,12 +495,6 @@ int fheon_global_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in
     return rc;
 }
 
-int fheon_bootstrap(fheon_ctx *ctx, const fheon_ct *ct, fheon_ct *out)
-{
-    if (!ctx || !ct || !out) return FHEON_ERR_ARG;
-    return fail(ctx, FHEON_ERR_UNIMPLEMENTED, "bootstrapping is not part of this build");
-}
-
 int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
     if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
@@ -532,6 +526,10 @@ int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
         for (u32 i = 0; i < n; i++)
             if ((rc = fheon_relu_apply(ctx, ly, ins[i], outs[i]))) return rc;
         return FHEON_OK;
+    case LAYER_BOOT:
+        for (u32 i = 0; i < n; i++)
+            if ((rc = boot_apply(ctx, ly, ins[i], outs[i]))) return rc;
+        return FHEON_OK;
     default: break;
     }
     for (u32 i = 0; i < n; i++)
@@ -553,6 +551,13 @@ int fheon_layer_rotation_steps(const fheon_layer *ly, int32_t *out, uint32_t *n)
             if (x) st.insert(x);
     } else if (ly->kind == LAYER_FC) {
         for (u32 x = 1; x < ly->nslots; x <<= 1) st.insert((int32_t)x);
+    } else if (ly->kind == LAYER_BOOT) {
+        for (const fheon_layer *sub : ly->subs) {
+            for (int32_t x : sub->r)
+                if (x) st.insert(x);
+            for (int32_t x : sub->s)
+                if (x) st.insert(x);
+        }
     } else if (ly->kind == LAYER_CONV) {
         const int p = (int)(ly->k - 1) / 2;
         for (int di = -p; di <= p; di++)

@@ -9,7 +9,8 @@
 // nodes as cos(k pi / d), which are the extrema of T_d; the interpolation nodes
 // are the zeros of T_{D+1}.
 //
-// Evaluation (depth ceil(log2 D) + 1, + 1 for the mask):
+// Evaluation (cheb_series, shared with bootstrapping's EvalMod; depth
+// ceil(log2 D) + 1, + 1 for the mask):
 //   T_1 = v; T_2h = 2 T_h^2 - 1; T_2h+1 = 2 T_h+1 T_h - T_1,
 // each product taken at the lower operand's level with relinearisation and
 // rescaled; T_1 is brought to the product's level and exact scale by a
@@ -50,7 +51,7 @@ u32 ceil_log2(u32 x)
 }
 
 // levels the ReLU consumes
-u32 relu_depth(double beta, u32 D) { return ceil_log2(D) + 1 + (beta > 1.0 ? 1 : 0); }
+u32 relu_depth(double beta, u32 D) { return fheon::cheb_depth(D) + (beta > 1.0 ? 1 : 0); }
 
 int check_args(fheon_ctx *ctx, double beta, u32 D, u32 level)
 {
@@ -62,6 +63,71 @@ int check_args(fheon_ctx *ctx, double beta, u32 D, u32 level)
 }
 
 } // namespace
+
+namespace fheon {
+
+u32 cheb_depth(u32 D) { return ceil_log2(D) + 1; }
+
+int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, double scale)
+{
+    // T_1 .. T_D (index d), two temporaries and the sum: nothing is allocated
+    // after the first application
+    if (work.size() != D + 4) work.resize(D + 4, nullptr);
+    for (fheon_ct *&c : work) {
+        int rc;
+        if (!c && (rc = fheon_ct_create(ctx, level, scale, &c))) return rc;
+    }
+    return FHEON_OK;
+}
+
+int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out)
+{
+    const u32 D = (u32)coeffs.size() - 1, N = ctx->N;
+    fheon_ct **T = work.data();
+    fheon_ct *t1 = work[D + 2], *y = work[D + 3];
+    const double s0 = T[1]->scale;
+    int rc;
+    // operands at a higher level are read in place (their lowest limbs), and
+    // the factor 2 of 2 T_a T_b is applied inside the tensor
+    for (u32 d = 2; d <= D; d++) {
+        const u32 h = d / 2;
+        fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
+        const u32 lv = A->level < B->level ? A->level : B->level;
+        if ((rc = mul_relin_at(ctx, A, B, lv, true, T[d]))) return rc; // scale S = s_a s_b
+        if (d % 2 == 1) {
+            // - T_1 at scale S joins the product before the shared rescale
+            int64_t K;
+            if (!round_int((-1.0 * T[d]->scale) / T[1]->scale, &K)) return fail(ctx, FHEON_ERR_ARG, "chebyshev: constant");
+            if ((rc = ct_reshape(ctx, t1, lv))) return rc;
+            FHEON_CUDA(ctx, k_mul_int(ctx, T[1]->c0(), K, t1->c0(), lv, 2, (u64)T[1]->level * N));
+            FHEON_CUDA(ctx, k_add(ctx, T[d]->c0(), t1->c0(), T[d]->c0(), lv, 2));
+        }
+        if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
+        if (d % 2 == 0 && (rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
+    }
+    u32 lstar = T[1]->level;
+    for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
+    lstar -= 1;
+    // y = sum_d K_d T_d at level lstar + 1 in one pass, rescaled once onto s0
+    std::vector<const u64 *> src(D);
+    std::vector<u64> stride(D);
+    std::vector<int64_t> K(D);
+    const double q = (double)ctx->mod[lstar];
+    for (u32 d = 1; d <= D; d++) {
+        if (!round_int(((coeffs[d] * s0) * q) / T[d]->scale, &K[d - 1]))
+            return fail(ctx, FHEON_ERR_ARG, "chebyshev: coefficient factor out of range");
+        src[d - 1] = T[d]->c0();
+        stride[d - 1] = (u64)T[d]->level * N;
+    }
+    if ((rc = ct_reshape(ctx, y, lstar + 1))) return rc;
+    FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), D, y->c0(), lstar + 1));
+    y->scale = s0 * q; // the sum's scale before the rescale (metadata)
+    if ((rc = fheon_rescale(ctx, y, y))) return rc;
+    y->scale = s0;
+    return fheon_add_const(ctx, y, coeffs[0], out);
+}
+
+} // namespace fheon
 
 extern "C" {
 
@@ -124,62 +190,17 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     const u32 D = ly->degree;
     const double s0 = in->scale;
     int rc;
-    // T_1 .. T_D in layer-owned working ciphertexts (index d), two temporaries
-    // and the sum: nothing is allocated after the first application
-    if (ly->rot.size() != D + 4) ly->rot.resize(D + 4, nullptr);
-    for (fheon_ct *&c : ly->rot)
-        if (!c && (rc = fheon_ct_create(ctx, ly->level, s0, &c))) return rc;
-    fheon_ct **T = ly->rot.data();
-    fheon_ct *t0 = ly->rot[D + 1], *t1 = ly->rot[D + 2], *y = ly->rot[D + 3];
+    if ((rc = cheb_work(ctx, ly->rot, D, ly->level, s0))) return rc;
+    fheon_ct *T1 = ly->rot[1];
     // v = x * mask, rescaled (scale q_{l-1} of the mask cancels)
     if (ly->beta > 1.0) {
-        if ((rc = fheon_mul_plain(ctx, in, ly->mask, T[1]))) return rc;
-        if ((rc = fheon_rescale(ctx, T[1], T[1]))) return rc;
-        T[1]->scale = s0;
-    } else if ((rc = fheon_drop_level(ctx, in, in->level, T[1]))) {
+        if ((rc = fheon_mul_plain(ctx, in, ly->mask, T1))) return rc;
+        if ((rc = fheon_rescale(ctx, T1, T1))) return rc;
+        T1->scale = s0;
+    } else if ((rc = fheon_drop_level(ctx, in, in->level, T1))) {
         return rc;
     }
-    // operands at a higher level are read in place (their lowest limbs), and
-    // the factor 2 of 2 T_a T_b is applied inside the tensor
-    (void)t0;
-    const u32 N = ctx->N;
-    for (u32 d = 2; d <= D; d++) {
-        const u32 h = d / 2;
-        fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
-        const u32 lv = A->level < B->level ? A->level : B->level;
-        if ((rc = mul_relin_at(ctx, A, B, lv, true, T[d]))) return rc; // scale S = s_a s_b
-        if (d % 2 == 1) {
-            // - T_1 at scale S joins the product before the shared rescale
-            int64_t K;
-            if (!round_int((-1.0 * T[d]->scale) / T[1]->scale, &K)) return fail(ctx, FHEON_ERR_ARG, "relu: constant");
-            if ((rc = ct_reshape(ctx, t1, lv))) return rc;
-            FHEON_CUDA(ctx, k_mul_int(ctx, T[1]->c0(), K, t1->c0(), lv, 2, (u64)T[1]->level * N));
-            FHEON_CUDA(ctx, k_add(ctx, T[d]->c0(), t1->c0(), T[d]->c0(), lv, 2));
-        }
-        if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
-        if (d % 2 == 0 && (rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
-    }
-    u32 lstar = T[1]->level;
-    for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
-    lstar -= 1;
-    // y = sum_d K_d T_d at level lstar + 1 in one pass, rescaled once onto s0
-    std::vector<const u64 *> src(D);
-    std::vector<u64> stride(D);
-    std::vector<int64_t> K(D);
-    const double q = (double)ctx->mod[lstar];
-    for (u32 d = 1; d <= D; d++) {
-        if (!round_int(((ly->coeffs[d] * s0) * q) / T[d]->scale, &K[d - 1]))
-            return fail(ctx, FHEON_ERR_ARG, "relu: coefficient factor out of range");
-        src[d - 1] = T[d]->c0();
-        stride[d - 1] = (u64)T[d]->level * N;
-    }
-    if ((rc = ct_reshape(ctx, y, lstar + 1))) return rc;
-    FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), D, y->c0(), lstar + 1));
-    y->scale = s0 * q; // the sum's scale before the rescale (metadata)
-    if ((rc = fheon_rescale(ctx, y, y))) return rc;
-    y->scale = s0;
-    if ((rc = fheon_add_const(ctx, y, ly->coeffs[0], out))) return rc;
-    return FHEON_OK;
+    return cheb_series(ctx, ly->coeffs, ly->rot, out);
 }
 
 int fheon_relu_approx(fheon_ctx *ctx, const fheon_ct *ct, double beta, uint32_t degree, uint32_t n, fheon_ct *out)

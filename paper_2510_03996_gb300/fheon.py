@@ -42,6 +42,13 @@ class fheon_rot_item(ctypes.Structure):
     _fields_ = [("input", c_vp), ("output", c_vp), ("step", c_i32)]
 
 
+class fheon_boot_params(ctypes.Structure):
+    """Bootstrapping: CoeffToSlot / SlotToCoeff levels, EvalMod's range K,
+    series degree and double-angle steps, BSGS baby steps (0: fewest rotations)."""
+    _fields_ = [("cts_levels", ctypes.c_uint32), ("stc_levels", ctypes.c_uint32), ("K", ctypes.c_uint32),
+                ("degree", ctypes.c_uint32), ("doublings", ctypes.c_uint32), ("baby", ctypes.c_uint32)]
+
+
 # name -> argument types (all return int unless listed in _RESTYPE)
 SIGNATURES = {
     "fheon_error_string": [c_int],
@@ -115,6 +122,13 @@ SIGNATURES = {
     "fheon_global_avgpool": [c_vp, c_vp, P(fheon_map), c_vp],
     "fheon_fc": [c_vp, c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_vp],
     "fheon_bootstrap": [c_vp, c_vp, c_vp],
+    "fheon_boot_params_default": [c_vp, P(fheon_boot_params)],
+    "fheon_evalmod_coeffs": [c_u32, c_u32, c_u32, P(c_dbl)],
+    "fheon_bootstrap_prepare": [c_vp, P(fheon_boot_params), c_dbl, c_vpp],
+    "fheon_bootstrap_compose": [c_vp, P(fheon_boot_params), P(c_vp), P(c_vp), P(c_dbl), c_dbl, c_vpp],
+    "fheon_bootstrap_keygen": [c_vp, c_vp, c_vp],
+    "fheon_bootstrap_info": [c_vp, P(c_u32), P(c_dbl)],
+    "fheon_mod_raise": [c_vp, c_vp, c_vp],
     "fheon_layer_apply_graph": [c_vp, c_vp, c_vp, c_vp],
     "fheon_layer_apply_batch": [c_vp, c_vp, P(c_vp), c_u32, P(c_vp)],
     "fheon_model_create": [c_vp, P(c_vp), c_u32, c_vpp],
@@ -617,6 +631,49 @@ class Context:
     def bootstrap(self, ct, out=None):
         out = out or self.ct_create(1)
         self._chk(load().fheon_bootstrap(self.h, ct.h, out.h))
+        return out
+
+    def boot_params_default(self):
+        p = fheon_boot_params()
+        self._chk(load().fheon_boot_params_default(self.h, ctypes.byref(p)))
+        return p
+
+    @staticmethod
+    def evalmod_coeffs(K, doublings, degree):
+        out = (c_dbl * (degree + 1))()
+        check(load().fheon_evalmod_coeffs(K, doublings, degree, out))
+        return np.array(out[:], dtype=np.float64)
+
+    def bootstrap_prepare(self, in_scale, params=None):
+        h = c_vp()
+        self._chk(load().fheon_bootstrap_prepare(self.h, ctypes.byref(params) if params is not None else None,
+                                                 float(in_scale), ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def bootstrap_compose(self, params, cts, stc, coeffs, in_scale):
+        """cts / stc: prepared rotation-sum layers (kept alive by the result)."""
+        c = (c_vp * len(cts))(*[x.h.value for x in cts])
+        t = (c_vp * len(stc))(*[x.h.value for x in stc])
+        cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+        h = c_vp()
+        self._chk(load().fheon_bootstrap_compose(self.h, ctypes.byref(params), c, t, _dblp(cf), float(in_scale),
+                                                 ctypes.byref(h)))
+        out = Handle(h, load().fheon_layer_destroy)
+        out.levels = list(cts) + list(stc)
+        return out
+
+    def bootstrap_keygen(self, sk, layer):
+        self._chk(load().fheon_bootstrap_keygen(self.h, sk.h, layer.h))
+
+    @staticmethod
+    def bootstrap_info(layer):
+        lv, sc = c_u32(0), c_dbl(0)
+        check(load().fheon_bootstrap_info(layer.h, ctypes.byref(lv), ctypes.byref(sc)))
+        return lv.value, sc.value
+
+    def mod_raise(self, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_mod_raise(self.h, ct.h, out.h))
         return out
 
     def layer_apply(self, layer, ct, out=None):

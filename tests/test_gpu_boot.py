@@ -1,0 +1,146 @@
+"""CKKS bootstrapping on the GPU against the oracle: ModRaise and the
+conjugation bit for bit; the whole bootstrap bit for bit when it is composed
+from the oracle's integer plaintexts; the library's own prepared bootstrap
+(its own diagonals, encoded on the device) against the input message; the
+one-shot call; argument and level errors."""
+import numpy as np
+import pytest
+
+import gpu_common
+from oracle import boot as B
+from oracle import ckks
+from paper_2510_03996_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def boot():
+    pr = gpu_common.Pair("boot_n12")
+    g, o = pr.g, pr.o
+    plan = B.Plan(o, pr.P["scale"])
+    pr.add_keys(plan.steps())
+    conj = 2 * pr.N - 1
+    g.galois_keygen(pr.sk, [conj])
+    pr.oconj = o.rotkey(pr.s_eval, conj)
+    g.relinkeygen(pr.sk)
+    pr.orlk = o.relinkey(pr.s_eval)
+    pr.plan = plan
+    return pr
+
+
+def _input(pr, seed, level):
+    z = synth.uniform_slots(seed, 0, pr.N // 2)
+    m = ckks.encode(z, pr.N, pr.P["scale"])
+    ct, oct_ = pr.encrypt_both(m, nonce=seed, level=level)
+    return z, ct, oct_
+
+
+def test_mod_raise_bit_exact(boot):
+    g, o = boot.g, boot.o
+    for level in (1, 3):
+        _, ct, oct_ = _input(boot, 0xB101 + level, level)
+        r = g.mod_raise(ct)
+        assert g.ct_info(r)[0] == boot.L
+        want = B.mod_raise(o, o.drop_level(oct_, 1))
+        assert gpu_common.mismatch(g.ct_download(r), want) == 0
+
+
+def test_conjugation_bit_exact(boot):
+    g, o = boot.g, boot.o
+    _, ct, oct_ = _input(boot, 0xB102, 7)
+    y = g.rotate_galois(ct, 2 * boot.N - 1)
+    want = o.rotate(oct_, 2 * boot.N - 1, boot.oconj)
+    assert gpu_common.mismatch(g.ct_download(y), want) == 0
+
+
+def _composed(pr):
+    """The library's bootstrap over the oracle plan's integer plaintexts."""
+    g, o, plan = pr.g, pr.o, pr.plan
+    gl, opts = [], []
+    for rr, groups, ps, lv in plan.cts + plan.stc:
+        gp, op = [], []
+        for _, vals in groups:
+            grow, orow = [], []
+            for v in vals:
+                if v is None:
+                    grow.append(None)
+                    orow.append(None)
+                    continue
+                m = ckks.encode(v, pr.N, ps)
+                grow.append(g.plain_from_coeffs(m, lv, ps))
+                orow.append(o.plain_from_coeffs(m, lv))
+            gp.append(grow)
+            op.append(orow)
+        layer = g.linear_prepare_plain(rr, [G for G, _ in groups], gp, lv)
+        layer.pts = gp  # the plaintexts outlive the layer
+        gl.append(layer)
+        opts.append(op)
+    prm = pr.F.fheon_boot_params(len(plan.cts), len(plan.stc), plan.K, plan.D, plan.r, 0)
+    return g.bootstrap_compose(prm, gl[:len(plan.cts)], gl[len(plan.cts):], plan.coeffs, pr.P["scale"]), opts
+
+
+def test_bootstrap_bit_exact(boot):
+    g, o, plan = boot.g, boot.o, boot.plan
+    layer, opts = _composed(boot)
+    okeys = {st: boot.okeys[g.galois_elt(st)] for st in plan.steps()}
+    z, ct, oct_ = _input(boot, 0xB103, 2)
+    y = g.layer_apply(layer, ct)
+    want, osc = B.bootstrap_encrypted(o, oct_, plan, opts, okeys, boot.orlk, boot.oconj)
+    assert gpu_common.mismatch(g.ct_download(y), want) == 0
+    lv, sc = g.ct_info(y)
+    assert lv == plan.out_level and sc == osc
+    got = np.asarray(g.decode(g.decrypt(boot.sk, y))).real
+    assert np.max(np.abs(got - z)) < 1e-4
+
+
+def test_bootstrap_prepared_by_the_library(boot):
+    g, plan = boot.g, boot.plan
+    layer = g.bootstrap_prepare(boot.P["scale"])
+    assert sorted(g.layer_rotation_steps(layer)) == plan.steps()
+    lv, sc = g.bootstrap_info(layer)
+    assert lv == plan.out_level and abs(sc / boot.P["scale"] - 1) < 1e-9
+    g.bootstrap_keygen(boot.sk, layer)
+    z, ct, _ = _input(boot, 0xB104, 1)
+    y = g.layer_apply(layer, ct)
+    assert g.ct_info(y)[0] == plan.out_level
+    got = np.asarray(g.decode(g.decrypt(boot.sk, y))).real
+    assert np.max(np.abs(got - z)) < 1e-4
+    # the one-shot call prepares the same layer: the same ciphertext to the bit
+    y1 = g.bootstrap(ct)
+    assert gpu_common.mismatch(g.ct_download(y1), g.ct_download(y)) == 0
+    # a bootstrapped ciphertext computes on: the output times itself, rescaled
+    sq = g.rescale(g.mul_relin(y, y))
+    got2 = np.asarray(g.decode(g.decrypt(boot.sk, sq))).real
+    assert np.max(np.abs(got2 - z * z)) < 1e-3
+
+
+def test_bootstrap_errors(boot):
+    g, F = boot.g, boot.F
+    layer = g.bootstrap_prepare(boot.P["scale"])
+    _, ct, _ = _input(boot, 0xB105, 3)
+    ct2 = g.mul_const_rescale(ct, 1.0, boot.P["scale"] * 2.0)
+    with pytest.raises(F.FheonError) as e:
+        g.layer_apply(layer, ct2)                 # prepared for another scale
+    assert e.value.code == -5
+    p = g.boot_params_default()
+    assert (p.K, p.doublings, p.degree, p.cts_levels, p.stc_levels) == (plan_k(boot), boot.plan.r, 27, 3, 3)
+    p.doublings = 30                                # deeper than the context
+    with pytest.raises(F.FheonError) as e:
+        g.bootstrap_prepare(boot.P["scale"], p)
+    assert e.value.code == -4
+    small = gpu_common.Pair("relu_n12")
+    with pytest.raises(F.FheonError) as e:
+        small.g.bootstrap_prepare(small.P["scale"])
+    assert e.value.code == -4
+
+
+def plan_k(pr):
+    return pr.plan.K
+
+
+def test_evalmod_coefficients_match_the_oracle(boot):
+    for K, r, D in ((128, 7, 27), (512, 9, 27), (64, 5, 31)):
+        a = boot.g.evalmod_coeffs(K, r, D)
+        b = B.evalmod_coeffs(K, r, D)
+        assert np.array_equal(a, b)
