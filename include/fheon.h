@@ -447,6 +447,16 @@ int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint3
  * d (about 2 sqrt(span) rotations).  Output level: level - 1, scale in_scale. */
 int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
                      uint32_t level, double in_scale, fheon_layer **out);
+/* Repack a feature map into another layout of the same (C, H, W) in one
+ * level (the paper's striding by extraction, Sec. 4.2: the values a strided
+ * layer leaves at dilated positions gathered into a compact grid): out =
+ * sum_o m_o Rot_o(in), with m_o one at every destination slot whose source is
+ * o slots further on, as baby-step/giant-step rotation sums; masks at scale
+ * q_{level-1} (the output keeps the input's scale; every slot outside the
+ * output map is zero).  At most 1024 distinct shifts (split larger moves
+ * into steps). */
+int fheon_repack_prepare(fheon_ctx *ctx, const fheon_map *in, const fheon_map *out, uint32_t level,
+                         fheon_layer **layer);
 /* Global average pooling (Sec. 4.4, used by ResNet): the mean over each
  * channel's whole H x H map, as average pooling with k = stride = H (one
  * value per channel, at the channel's first slot). */
@@ -596,6 +606,12 @@ int fheon_relu_prepare(fheon_ctx *ctx, double beta, uint32_t degree, uint32_t n,
  * must outlive the layer. */
 int fheon_relu_prepare_plain(fheon_ctx *ctx, double beta, uint32_t degree, const fheon_pt *mask, uint32_t level,
                              fheon_layer **out);
+/* A Chebyshev series layer: out = sum_d c_d T_d(in) for an input in [-1, 1]
+ * (the evaluation of fheon_relu_apply without the mask; with the
+ * coefficients of fheon_relu_coeffs(beta, D) it is Alg. 4's ReLU of an input
+ * already scaled by 1/beta).  Depth ceil(log2 degree) + 1; the output keeps
+ * the input's scale. */
+int fheon_cheb_prepare(fheon_ctx *ctx, const double *coeffs, uint32_t degree, uint32_t level, fheon_layer **out);
 /* Apply a prepared ReLU; `in` at the layer's level, out distinct from in. */
 int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
 /* One-shot: prepare at in's level, apply, release. */

@@ -140,61 +140,9 @@ def cts_levels(n, levels):
     return out
 
 
-# ------------------------------------------------------------------ BSGS plans
-def bsgs_plan(diags, n, stride, baby=0):
-    """Baby-step/giant-step form of sum_o d_o Rot_o: every offset is k*stride
-    (k centred in (-M/2, M/2], M = n/stride), split as k = c*bs + t with
-    0 <= t < bs; then
-      out = sum_c Rot_{G_c}( sum_t Rot_{-G_c}(d_k) * Rot_{t stride}(in) ),  G_c = c bs stride.
-    Returns (taps r, groups [(G_c, [vector or None per tap])]) in the
-    rotation-sum form of the linear layers.  bs = `baby`, else the power of
-    two with the fewest rotations (ties: the larger bs)."""
-    M = n // stride
-    ks = {}
-    for o, d in diags.items():
-        assert o % stride == 0
-        k = o // stride
-        if k > M // 2:
-            k -= M
-        if np.any(d != 0):
-            ks[k] = d
-    def cost(bs):
-        ts = {k - (k // bs) * bs for k in ks}
-        cs = {k // bs for k in ks}
-        return len(ts - {0}) + len(cs - {0})
-    if baby:
-        bs = baby
-    else:
-        bs, best = 1, None
-        b = 1
-        while b <= M:
-            c = cost(b)
-            if best is None or c <= best:
-                bs, best = b, c
-            b *= 2
-    ts = sorted({k - (k // bs) * bs for k in ks})
-    r = [t * stride for t in ts]
-    groups = []
-    for c in sorted({k // bs for k in ks}):
-        G = c * bs * stride
-        vals = []
-        for t in ts:
-            k = c * bs + t
-            vals.append(np.roll(ks[k], G) if k in ks else None)
-        groups.append((G, vals))
-    return r, groups
-
-
-def plan_slots(v, r, groups):
-    """FP64 model of a rotation-sum plan on complex slots."""
-    out = np.zeros(len(v), dtype=np.complex128)
-    for G, vals in groups:
-        z = np.zeros(len(v), dtype=np.complex128)
-        for rt, p in zip(r, vals):
-            if p is not None:
-                z += np.roll(v, -rt) * p
-        out += np.roll(z, -G)
-    return out
+# BSGS plans of the merged levels (shared with the repacking layer)
+bsgs_plan = OF.bsgs_plan
+plan_slots = OF.plan_slots
 
 
 # ------------------------------------------------------------------ parameters

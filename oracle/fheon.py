@@ -506,3 +506,106 @@ def fold_encrypted(ctx, ct, fold, keys):
         t = ct if f == 0 else hs[f]
         y = t if y is None else ctx.add(y, t)
     return y
+
+
+# ------------------------------------------------------------------ BSGS rotation sums and repacking
+def bsgs_plan(diags, n, stride, baby=0):
+    """Baby-step/giant-step form of sum_o d_o Rot_o: every offset is k*stride
+    (k centred in (-M/2, M/2], M = n/stride), split as k = c*bs + t with
+    0 <= t < bs; then
+      out = sum_c Rot_{G_c}( sum_t Rot_{-G_c}(d_k) * Rot_{t stride}(in) ),  G_c = c bs stride.
+    Returns (taps r, groups [(G_c, [vector or None per tap])]) in the
+    rotation-sum form of the linear layers.  bs = `baby`, else the power of
+    two with the fewest rotations (ties: the larger bs)."""
+    M = n // stride
+    ks = {}
+    for o, d in diags.items():
+        assert o % stride == 0
+        k = o // stride
+        if k > M // 2:
+            k -= M
+        if np.any(d != 0):
+            ks[k] = d
+    def cost(bs):
+        ts = {k - (k // bs) * bs for k in ks}
+        cs = {k // bs for k in ks}
+        return len(ts - {0}) + len(cs - {0})
+    if baby:
+        bs = baby
+    else:
+        bs, best = 1, None
+        b = 1
+        while b <= M:
+            c = cost(b)
+            if best is None or c <= best:
+                bs, best = b, c
+            b *= 2
+    ts = sorted({k - (k // bs) * bs for k in ks})
+    r = [t * stride for t in ts]
+    groups = []
+    for c in sorted({k // bs for k in ks}):
+        G = c * bs * stride
+        vals = []
+        for t in ts:
+            k = c * bs + t
+            vals.append(np.roll(ks[k], G) if k in ks else None)
+        groups.append((G, vals))
+    return r, groups
+
+
+def plan_slots(v, r, groups):
+    """FP64 model of a rotation-sum plan on complex slots."""
+    out = np.zeros(len(v), dtype=np.complex128)
+    for G, vals in groups:
+        z = np.zeros(len(v), dtype=np.complex128)
+        for rt, p in zip(r, vals):
+            if p is not None:
+                z += np.roll(v, -rt) * p
+        out += np.roll(z, -G)
+    return out
+
+
+def repack_plan(C, H, W, src, dst, nslots):
+    """A (C, H, W) map moved from layout src = (grid, dil, block) to layout
+    dst in one level (striding by extraction, Sec. 4.2): out = sum_o m_o
+    Rot_o(in), m_o one at every destination slot whose source is o slots
+    further on; in BSGS form over the largest power-of-two stride dividing
+    every shift.  Returns (r, groups) in the rotation-sum conventions."""
+    a = map_slots(C, H, W, *src)
+    b = map_slots(C, H, W, *dst)
+    diags = {}
+    for s_, d_ in zip(a, b):
+        o = int((s_ - d_) % nslots)
+        diags.setdefault(o, np.zeros(nslots))[int(d_)] = 1.0
+    stride = nslots
+    for o in diags:
+        while stride > 1 and o % stride:
+            stride //= 2
+    return bsgs_plan(diags, nslots, stride)
+
+
+def resnet_fp64(X, w, chans, nblocks, betas=None, D=RELU_DEGREE):
+    """ResNet-20-style network (paper Sec. 7 architecture) in FP64 from the
+    plain layers: 3x3 conv + ReLU; per stage, residual blocks (3x3 conv, ReLU,
+    3x3 conv, + shortcut, ReLU) whose first block in stages 2 and 3 has stride
+    2 and a 1x1 stride-2 conv shortcut; global average pooling; FC.  With
+    `betas`, ReLU i is the Chebyshev series of Alg. 4 with bound betas[i]."""
+    idx = [0]
+
+    def act(v):
+        i = idx[0]
+        idx[0] += 1
+        return np.maximum(v, 0.0) if betas is None else relu_fp64(v, betas[i], D)
+
+    h = act(conv2d_fp64(X, w["conv0"][0], b=w["conv0"][1], pad=1))
+    for s in range(len(chans)):
+        for bk in range(nblocks):
+            name = "s%db%d" % (s, bk)
+            st = 2 if (s > 0 and bk == 0) else 1
+            t = act(conv2d_fp64(h, w[name + "_a"][0], b=w[name + "_a"][1], stride=st, pad=1))
+            t = conv2d_fp64(t, w[name + "_b"][0], b=w[name + "_b"][1], pad=1)
+            sc = conv2d_fp64(h, w[name + "_sc"][0], b=w[name + "_sc"][1], stride=2) if st == 2 else h
+            h = act(t + sc)
+    g = avgpool_fp64(h, h.shape[1], h.shape[1]).reshape(-1)
+    Wf, bf = w["fc"]
+    return Wf @ g + bf

@@ -42,9 +42,6 @@ using namespace fheon;
 
 namespace {
 
-using cd = std::complex<double>;
-using Diags = std::map<u32, std::vector<cd>>; // offset mod n -> diagonal
-
 u64 powmod_small(u64 b, u64 e, u64 m)
 {
     u64 r = 1 % m;
@@ -145,18 +142,45 @@ std::vector<MergedLevel> merged_levels(u32 n, u32 levels, bool cts)
     return out;
 }
 
-int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+u32 boot_depth(const fheon_boot_params &p) { return p.cts_levels + cheb_depth(p.degree) + p.doublings + p.stc_levels; }
 
-// BSGS form of sum_o d_o Rot_o: offsets k * stride (k centred in (-M/2, M/2],
-// M = n / stride) split as k = c bs + t, 0 <= t < bs:
-//   out = sum_c Rot_{G_c}( sum_t Rot_{-G_c}(d_k) Rot_{t stride}(in) ),  G_c = c bs stride.
-// bs = `baby`, else the power of two with the fewest rotations (ties: larger).
-struct Bsgs {
-    std::vector<int32_t> r, s;
-    std::vector<std::vector<cd>> vals; // [g * r.size() + t], empty = no product
+int check_params(fheon_ctx *ctx, const fheon_boot_params *p)
+{
+    u32 logn = ctx->logN - 1;
+    if (!p->cts_levels || !p->stc_levels || p->cts_levels > logn || p->stc_levels > logn || !p->K ||
+        p->degree < 2 || p->degree > 1023 || p->doublings > 30)
+        return fail(ctx, FHEON_ERR_ARG, "bootstrap: levels in [1, log2(N/2)], K >= 1, degree in [2, 1023]");
+    if (boot_depth(*p) > ctx->L - 1)
+        return fail(ctx, FHEON_ERR_LEVEL, "bootstrap needs %u levels above q_0, the context has %u", boot_depth(*p),
+                    ctx->L - 1);
+    return FHEON_OK;
+}
+
+// the scale the series starts on and the one SlotToCoeff starts on, in the
+// order the operations compute them
+double evalmod_end_scale(fheon_ctx *ctx, double s, u32 lv, u32 r)
+{
+    for (u32 i = 0; i < r; i++) {
+        s = (s * s) / (double)ctx->mod[lv - 1];
+        lv--;
+    }
+    return s;
+}
+
+// a default layer per context, kept for the one-shot call
+struct DefaultBoot {
+    double scale = 0;
+    fheon_layer *ly = nullptr;
 };
+std::map<const fheon_ctx *, DefaultBoot> g_default;
 
-Bsgs bsgs(const Diags &D, u32 n, u32 stride, u32 baby)
+} // namespace
+
+namespace fheon {
+
+static int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby)
 {
     const int64_t M = n / stride;
     std::map<int64_t, const std::vector<cd> *> ks;
@@ -212,13 +236,11 @@ Bsgs bsgs(const Diags &D, u32 n, u32 stride, u32 baby)
     return out;
 }
 
-// one merged level as a rotation-sum layer, its plaintexts (values times
-// `factor`, encoded at `pscale`) owned by the layer
-int level_layer(fheon_ctx *ctx, const MergedLevel &ml, cd factor, u32 baby, u32 level, double pscale,
-                fheon_layer **out)
+int diag_layer(fheon_ctx *ctx, const Diags &M, u32 stride, cd factor, u32 baby, u32 level, double pscale,
+               fheon_layer **out)
 {
     const u32 n = ctx->N / 2;
-    Bsgs B = bsgs(ml.M, n, ml.stride, baby);
+    Bsgs B = bsgs_plan(M, n, stride, baby);
     const u32 nt = (u32)B.r.size(), ng = (u32)B.s.size();
     std::vector<fheon_pt *> pts((size_t)nt * ng, nullptr);
     std::vector<double> re(n), im(n);
@@ -243,42 +265,6 @@ int level_layer(fheon_ctx *ctx, const MergedLevel &ml, cd factor, u32 baby, u32 
         if (p) (*out)->pt_store.push_back(p);
     return FHEON_OK;
 }
-
-u32 boot_depth(const fheon_boot_params &p) { return p.cts_levels + cheb_depth(p.degree) + p.doublings + p.stc_levels; }
-
-int check_params(fheon_ctx *ctx, const fheon_boot_params *p)
-{
-    u32 logn = ctx->logN - 1;
-    if (!p->cts_levels || !p->stc_levels || p->cts_levels > logn || p->stc_levels > logn || !p->K ||
-        p->degree < 2 || p->degree > 1023 || p->doublings > 30)
-        return fail(ctx, FHEON_ERR_ARG, "bootstrap: levels in [1, log2(N/2)], K >= 1, degree in [2, 1023]");
-    if (boot_depth(*p) > ctx->L - 1)
-        return fail(ctx, FHEON_ERR_LEVEL, "bootstrap needs %u levels above q_0, the context has %u", boot_depth(*p),
-                    ctx->L - 1);
-    return FHEON_OK;
-}
-
-// the scale the series starts on and the one SlotToCoeff starts on, in the
-// order the operations compute them
-double evalmod_end_scale(fheon_ctx *ctx, double s, u32 lv, u32 r)
-{
-    for (u32 i = 0; i < r; i++) {
-        s = (s * s) / (double)ctx->mod[lv - 1];
-        lv--;
-    }
-    return s;
-}
-
-// a default layer per context, kept for the one-shot call
-struct DefaultBoot {
-    double scale = 0;
-    fheon_layer *ly = nullptr;
-};
-std::map<const fheon_ctx *, DefaultBoot> g_default;
-
-} // namespace
-
-namespace fheon {
 
 int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
@@ -444,7 +430,7 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double 
         const double q = (double)ctx->mod[lv - 1];
         const double ps = i == 0 ? q * (delta_b / q0) : q;
         fheon_layer *l = nullptr;
-        if ((rc = level_layer(ctx, cl[i], cd(i == 0 ? 1.0 / (2.0 * (double)p.K) : 1.0), p.baby, lv, ps, &l))) {
+        if ((rc = diag_layer(ctx, cl[i].M, cl[i].stride, cd(i == 0 ? 1.0 / (2.0 * (double)p.K) : 1.0), p.baby, lv, ps, &l))) {
             cleanup();
             return rc;
         }
@@ -463,7 +449,7 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double 
         const double ps = i + 1 == p.stc_levels ? q * (in_scale / s) : q;
         fheon_layer *l = nullptr;
         const cd f(i == 0 ? q0 / (2.0 * M_PI * in_scale) : 1.0);
-        if ((rc = level_layer(ctx, sl[i], f, p.baby, lv, ps, &l))) {
+        if ((rc = diag_layer(ctx, sl[i].M, sl[i].stride, f, p.baby, lv, ps, &l))) {
             cleanup();
             return rc;
         }

@@ -2,6 +2,8 @@
 // encrypted network (conv, approximate ReLU), its plaintexts, working
 // ciphertexts and captured graphs.
 #pragma once
+#include <complex>
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -88,6 +90,22 @@ namespace fheon {
 int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, double scale);
 int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out);
 u32 cheb_depth(u32 D);
+// slot diagonals of a linear map on n slots: out = sum_o d_o * Rot_o(in)
+using cd = std::complex<double>;
+using Diags = std::map<u32, std::vector<cd>>; // offset mod n -> diagonal
+// BSGS form of sum_o d_o Rot_o: offsets k * stride (k centred in (-M/2, M/2],
+// M = n / stride) split as k = c bs + t, 0 <= t < bs:
+//   out = sum_c Rot_{G_c}( sum_t Rot_{-G_c}(d_k) Rot_{t stride}(in) ),  G_c = c bs stride.
+// bs = `baby`, else the power of two with the fewest rotations (ties: larger).
+struct Bsgs {
+    std::vector<int32_t> r, s;
+    std::vector<std::vector<cd>> vals; // [g * r.size() + t], empty = no product
+};
+Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby);
+// the rotation-sum layer of sum_o (factor d_o) Rot_o at `level`, its
+// plaintexts encoded at `pscale` and owned by the layer
+int diag_layer(fheon_ctx *ctx, const Diags &M, u32 stride, cd factor, u32 baby, u32 level, double pscale,
+               fheon_layer **out);
 // bootstrapping (boot.cu)
 int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out);
 } // namespace fheon

@@ -403,6 +403,40 @@ int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const doub
     return FHEON_OK;
 }
 
+int fheon_repack_prepare(fheon_ctx *ctx, const fheon_map *in, const fheon_map *out, uint32_t level,
+                         fheon_layer **layer)
+{
+    if (!ctx || !in || !out || !layer || level < 2 || level > ctx->L) return FHEON_ERR_ARG;
+    const fheon_map a = *in, b = *out;
+    if (!map_ok(ctx, a) || !map_ok(ctx, b) || a.C != b.C || a.H != b.H || a.W != b.W)
+        return fail(ctx, FHEON_ERR_ARG, "repack: maps of the same (C, H, W) that fit the slots");
+    const u32 n = ctx->N / 2;
+    // every (c, i, j) moves from its slot in `in` to its slot in `out`:
+    // out = sum_o m_o Rot_o(in), m_o one at each destination o slots before its source
+    Diags D;
+    for (u32 c = 0; c < a.C; c++)
+        for (u32 i = 0; i < a.H; i++)
+            for (u32 j = 0; j < a.W; j++) {
+                const u32 src = map_slot(a, c, i, j), dst = map_slot(b, c, i, j);
+                const u32 o = (src + n - dst) % n;
+                auto it = D.find(o);
+                if (it == D.end()) {
+                    if (D.size() == 1024)
+                        return fail(ctx, FHEON_ERR_ARG, "repack: more than 1024 distinct shifts; split it");
+                    it = D.emplace(o, std::vector<cd>(n, cd(0.0))).first;
+                }
+                it->second[dst] = cd(1.0);
+            }
+    u32 stride = n;
+    for (auto &kv : D)
+        while (stride > 1 && kv.first % stride) stride /= 2;
+    int rc = diag_layer(ctx, D, stride, cd(1.0), 0, level, (double)ctx->mod[level - 1], layer);
+    if (rc) return rc;
+    (*layer)->in_map = a;
+    (*layer)->out_map = b;
+    return FHEON_OK;
+}
+
 int fheon_global_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t level, fheon_layer **out)
 {
     if (!ctx || !in || in->H != in->W) return FHEON_ERR_ARG;

@@ -182,6 +182,21 @@ int fheon_relu_prepare(fheon_ctx *ctx, double beta, uint32_t degree, uint32_t n,
     return FHEON_OK;
 }
 
+int fheon_cheb_prepare(fheon_ctx *ctx, const double *coeffs, uint32_t degree, uint32_t level, fheon_layer **out)
+{
+    if (!ctx || !coeffs || !out || degree < 1 || degree > 1023 || level > ctx->L) return FHEON_ERR_ARG;
+    if (level <= cheb_depth(degree))
+        return fail(ctx, FHEON_ERR_LEVEL, "series: needs level > %u, got %u", cheb_depth(degree), level);
+    std::unique_ptr<fheon_layer> ly(new fheon_layer());
+    ly->kind = LAYER_RELU;
+    ly->beta = 1.0; // no mask: the input is the series' variable
+    ly->degree = degree;
+    ly->level = level;
+    ly->coeffs.assign(coeffs, coeffs + degree + 1);
+    *out = ly.release();
+    return FHEON_OK;
+}
+
 int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
     if (!ctx || !ly || !in || !out || ly->kind != LAYER_RELU) return FHEON_ERR_ARG;

@@ -118,6 +118,7 @@ SIGNATURES = {
     "fheon_fc_prepare": [c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_layer_apply": [c_vp, c_vp, c_vp, c_vp],
     "fheon_global_avgpool_prepare": [c_vp, P(fheon_map), c_u32, c_vpp],
+    "fheon_repack_prepare": [c_vp, P(fheon_map), P(fheon_map), c_u32, c_vpp],
     "fheon_avgpool": [c_vp, c_vp, P(fheon_map), c_u32, c_u32, c_vp],
     "fheon_global_avgpool": [c_vp, c_vp, P(fheon_map), c_vp],
     "fheon_fc": [c_vp, c_vp, P(fheon_map), c_u32, P(c_dbl), P(c_dbl), c_u32, c_vp],
@@ -144,6 +145,7 @@ SIGNATURES = {
     "fheon_relu_prepare": [c_vp, c_dbl, c_u32, c_u32, c_u32, c_vpp],
     "fheon_relu_prepare_plain": [c_vp, c_dbl, c_u32, c_vp, c_u32, c_vpp],
     "fheon_relu_apply": [c_vp, c_vp, c_vp, c_vp],
+    "fheon_cheb_prepare": [c_vp, P(c_dbl), c_u32, c_u32, c_vpp],
     "fheon_relu_approx": [c_vp, c_vp, c_dbl, c_u32, c_u32, c_vp],
     "fheon_mac_plain": [c_vp, P(c_vp), P(c_vp), c_u32, c_vp],
     "fheon_add": [c_vp, c_vp, c_vp, c_vp],
@@ -605,6 +607,12 @@ class Context:
                                           ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)
 
+    def repack_prepare(self, in_map, out_map, level):
+        h = c_vp()
+        self._chk(load().fheon_repack_prepare(self.h, ctypes.byref(self._map(in_map)), ctypes.byref(self._map(out_map)),
+                                              level, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
     def global_avgpool_prepare(self, in_map, level):
         h = c_vp()
         self._chk(load().fheon_global_avgpool_prepare(self.h, ctypes.byref(self._map(in_map)), level, ctypes.byref(h)))
@@ -731,6 +739,12 @@ class Context:
         h = c_vp()
         self._chk(load().fheon_relu_prepare_plain(self.h, float(beta), degree, mask.h if mask is not None else None,
                                                   level, ctypes.byref(h)))
+        return Handle(h, load().fheon_layer_destroy)
+
+    def cheb_prepare(self, coeffs, level):
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+        h = c_vp()
+        self._chk(load().fheon_cheb_prepare(self.h, _dblp(c), len(c) - 1, level, ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)
 
     def relu_apply(self, layer, ct, out=None):

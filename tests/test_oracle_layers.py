@@ -169,3 +169,17 @@ def test_encrypted_fc_diag_matches_the_product(ctx11):
     got = ctx.decode_ct(se, y, D).real
     assert np.max(np.abs(got[:m] - Wm @ X.reshape(-1))) < 1e-4
     assert np.max(np.abs(got[m:])) < 1e-4
+
+
+@pytest.mark.parametrize("src,dst", [((16, 2, 256), (8, 1, 64)), ((16, 2, 256), (8, 1, 256)), ((8, 1, 256), (8, 1, 64))])
+def test_repack_moves_every_value(src, dst):
+    """Repacking by masks and rotations: every (c, i, j) lands at its slot in
+    the new layout (brute-force pack/unpack), every other slot is zero."""
+    n, shape = 2048, (8, 8, 8)
+    X = synth.image(0xAB01, 0, shape, dist="normal")
+    r, groups = OF.repack_plan(*shape, src, dst, n)
+    out = OF.plan_slots(OF.pack_map(X, n, *src), r, groups).real
+    assert np.array_equal(OF.unpack_map(out, shape, *dst), X)
+    mask = np.ones(n, dtype=bool)
+    mask[OF.map_slots(*shape, *dst)] = False
+    assert np.all(out[mask] == 0.0)

@@ -1,0 +1,96 @@
+"""ResNet-20 host side: the package's FP64 forward pass (used to choose the
+ReLU bounds) against the oracle's plain-layer network, the slot maps, and the
+level plan of the encrypted network on a stand-in context that computes only
+levels and maps (every layer is prepared at the level its input has)."""
+import numpy as np
+import pytest
+
+from oracle import fheon as OF
+from paper_2510_03996_gb300 import resnet as R
+from paper_2510_03996_gb300 import synth
+
+MINI = dict(img=8, in_ch=3, chans=(2, 4, 8), blocks=1, classes=10)
+
+
+@pytest.mark.parametrize("arch", [MINI, dict(MINI, blocks=2)])
+def test_fp64_forward_matches_the_oracle(arch):
+    w = R.weights(0xC0, arch)
+    X = synth.image(0xC1, 0, (3, arch["img"], arch["img"]), dist="normal")
+    a = R.forward_fp64(X, w, arch)
+    b = OF.resnet_fp64(X, w, arch["chans"], arch["blocks"])
+    assert np.max(np.abs(a - b)) < 1e-10
+    betas = R.relu_bounds([X], w, arch)
+    assert len(betas) == R.n_relus(arch) == 1 + 6 * arch["blocks"]
+    a = R.forward_fp64(X, w, arch, relu=lambda v, i: OF.relu_fp64(v, betas[i]))
+    b = OF.resnet_fp64(X, w, arch["chans"], arch["blocks"], betas=betas)
+    assert np.max(np.abs(a - b)) < 1e-9
+
+
+def test_full_size_maps_fit_the_slots():
+    n = 1 << 15
+    for name, (C, H, W, grid, dil, block) in R.maps(R.FULL).items():
+        assert C * block <= n, name
+        assert dil * ((H - 1) * grid + (W - 1)) < block, name
+    assert R.n_relus(R.FULL) == 19
+
+
+class _Layer:
+    def __init__(self, kind, level, out_map=None):
+        self.kind, self.level, self.out_map = kind, level, out_map
+
+
+class FakeCtx:
+    """Levels and maps only: records every prepare call."""
+    L = 32
+
+    def __init__(self):
+        self.calls = []
+
+    def bootstrap_prepare(self, scale, params=None):
+        return _Layer("boot", None)
+
+    def bootstrap_info(self, layer):
+        return 11, 2.0 ** 40
+
+    def conv_prepare(self, m, K, pad, level, scale, bias=None, stride=1):
+        C, H, W, grid, dil, block = m
+        Fo, _, k, _ = K.shape
+        Ho, Wo = (H + 2 * pad - k) // stride + 1, (W + 2 * pad - k) // stride + 1
+        self.calls.append(("conv", level))
+        return _Layer("conv", level, (Fo, Ho, Wo, grid, dil * stride, block))
+
+    def cheb_prepare(self, coeffs, level):
+        assert level > 7
+        self.calls.append(("series", level))
+        return _Layer("series", level)
+
+    def repack_prepare(self, a, b, level):
+        assert a[:3] == b[:3]
+        self.calls.append(("repack", level))
+        return _Layer("repack", level, b)
+
+    def global_avgpool_prepare(self, m, level):
+        self.calls.append(("pool", level))
+        C, H, W, grid, dil, block = m
+        return _Layer("pool", level, (C, 1, 1, grid, dil * H, block))
+
+    def fc_prepare(self, m, W, level, scale, bias=None):
+        self.calls.append(("fc", level))
+        return _Layer("fc", level, (1, 1, W.shape[0], W.shape[0], 1, W.shape[0]))
+
+    @staticmethod
+    def layer_out_map(layer):
+        return layer.out_map
+
+
+def test_level_plan_full_size():
+    w = R.weights(0xC2, R.FULL)
+    net = R.EncryptedResNet(FakeCtx(), w, [2.0] * R.n_relus(R.FULL), 2.0 ** 40)
+    assert net.n_boot == 18 and net.in_level == 11
+    assert net.out_level >= 1
+    # every bootstrap input and every layer sits at a level >= 1
+    levels = [c[1] for c in net.ctx.calls]
+    assert min(levels) >= 2
+    assert [c[0] for c in net.ctx.calls].count("repack") == 2
+    kinds = [op[0] for op in net.plan]
+    assert kinds.count("boot") == 18 and kinds.count("add") == 9
