@@ -301,6 +301,68 @@ def lenet_timing(F, batch=32):
             "max_abs_logit_vs_fp64_exact_relu": err, "relu_bounds": betas, "levels": len(P["qbits"])}
 
 
+def resnet_timing(F, n_inputs=2):
+    """ResNet-20 encrypted inference with bootstrapping (N = 2^16, 32 primes:
+    q_0, 10 levels of layers, 21 of bootstrapping) on synthetic 3x32x32 N(0,1)
+    inputs with random-init weights: seconds per inference (CUDA events around
+    the inputs, one after another), one bootstrap alone, and the decrypted
+    logits against the FP64 network with exact ReLUs."""
+    import torch
+    from paper_2510_03996_gb300 import resnet
+    P = synth.params("resnet_n16")
+    N = 1 << P["logN"]
+    s = torch.cuda.Stream()
+    ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                    stream=s.cuda_stream)
+    w = resnet.weights(P["seed"])
+    xs = [synth.image(P["seed"], 800 + i, (3, 32, 32), dist="normal") for i in range(n_inputs)]
+    betas = resnet.relu_bounds(xs, w)
+    sk, pk = ctx.keygen()
+    t0 = time.time()
+    net = resnet.EncryptedResNet(ctx, w, betas, P["scale"])
+    net.keygen(sk)
+    ctx.sync()
+    t_prep = time.time() - t0
+    cts = [ctx.drop_level(ctx.encrypt(pk, ctx.encode(resnet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i),
+                          net.in_level) for i, X in enumerate(xs)]
+    net.forward(cts[0])  # warm-up: working ciphertexts, plans, workspace
+    net.forward_graph(cts[0])  # capture
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    outs = [net.forward(ct) for ct in cts]
+    e1.record(s)
+    torch.cuda.synchronize()
+    eager_secs = e0.elapsed_time(e1) / 1e3
+    e0.record(s)
+    gouts = [net.forward_graph(ct) for ct in cts]
+    e1.record(s)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs, gouts))
+    z = ctx.drop_level(cts[0], 1)
+    e0.record(s)
+    for _ in range(5):
+        ctx.layer_apply(net.boot, z)
+    e1.record(s)
+    torch.cuda.synchronize()
+    boot_ms = e0.elapsed_time(e1) / 5
+    err, agree = 0.0, 0
+    for X, y in zip(xs, outs):
+        got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
+        want = resnet.forward_fp64(X, w)
+        err = max(err, float(np.max(np.abs(got - want))))
+        agree += int(np.argmax(got) == np.argmax(want))
+    nkeys, kbytes = ctx.key_stats()
+    del outs, gouts, cts, net, sk, pk
+    ctx.close()
+    return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
+            "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": 18,
+            "inputs": n_inputs, "prepare_and_keygen_s": round(t_prep, 2), "keys": nkeys, "key_bytes": kbytes,
+            "max_abs_logit_vs_fp64_exact_relu": err, "argmax_agrees": "%d/%d" % (agree, n_inputs),
+            "levels": len(P["qbits"]), "paper_cpu_s_per_inference": 403}
+
+
 def serving_timing(F, n_req=40, rate=4.0, max_active=8):
     """The serving workload with LeNet-5 requests: Poisson arrivals (exponential
     gaps of mean 1/rate s from a seed), requests submitted to the
@@ -536,6 +598,7 @@ def run_gpu(args, rank, world, local_rank):
         comparisons = {"per_ciphertext_path": per_ciphertext_rate(ctx, ins, outs, steps, stream),
                        "conv_n13_layer": conv_layer_timing(F),
                        "lenet5_n15": lenet_timing(F),
+                       "resnet20_n16": resnet_timing(F),
                        "serving_lenet5": serving_timing(F, n_req=args.serve_requests)}
 
     cpu = None

@@ -282,9 +282,18 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
     if ((rc = mod_raise_ct(ctx, in, w[0]))) return rc;
     w[0]->scale = (double)ctx->mod[0];
     const fheon_ct *x = w[0];
+    // the levels' batched rotations read device plans: while this layer is
+    // captured into a graph, the graph keeps them (the levels report to the
+    // same collector)
+    auto sub_apply = [&](const fheon_layer *sub, const fheon_ct *a, fheon_ct *b) {
+        sub->collect = ly->collect;
+        const int r = fheon_layer_apply(ctx, sub, a, b);
+        sub->collect = nullptr;
+        return r;
+    };
     for (u32 i = 0; i < ly->ncts; i++) {
         fheon_ct *dst = w[1 + (i & 1)];
-        if ((rc = fheon_layer_apply(ctx, ly->subs[i], x, dst))) return rc;
+        if ((rc = sub_apply(ly->subs[i], x, dst))) return rc;
         x = dst;
     }
     // real and imaginary parts: T_1 of each part's series
@@ -316,7 +325,7 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
     const u32 nst = (u32)ly->subs.size() - ly->ncts;
     for (u32 i = 0; i < nst; i++) {
         fheon_ct *dst = i + 1 == nst ? out : w[1 + (i & 1)];
-        if ((rc = fheon_layer_apply(ctx, ly->subs[ly->ncts + i], x, dst))) return rc;
+        if ((rc = sub_apply(ly->subs[ly->ncts + i], x, dst))) return rc;
         x = dst;
     }
     return FHEON_OK;

@@ -284,3 +284,34 @@ class EncryptedResNet:
             elif kind == "boot":
                 reg[op[1]] = ctx.layer_apply(self.boot, reg[op[1]])
         return reg["x"]
+
+    def forward_graph(self, ct):
+        """The same plan with every layer (bootstraps included) replayed as a
+        CUDA graph on fixed buffers: the input is copied into a staging
+        ciphertext and every step writes its own buffer (the context's stream
+        must be a created stream).  Returns a new ciphertext holding the
+        output, bit for bit the one forward() gives."""
+        ctx = self.ctx
+        if not hasattr(self, "_bufs"):
+            self._bufs = [ctx.ct_create(1) for _ in range(3 * len(self.plan) + 1)]
+        bufs = self._bufs
+        ctx.drop_level(ct, ctx.ct_info(ct)[0], out=bufs[-1])
+        reg = {"x": bufs[-1]}
+        for k, op in enumerate(self.plan):
+            out = bufs[3 * k]
+            kind = op[0]
+            if kind == "layer":
+                _, layer, src, dst = op
+                reg[dst] = ctx.layer_apply_graph(layer, reg[src], out)
+            elif kind == "scale":
+                _, c, src, dst = op
+                reg[dst] = ctx.mul_const_rescale(reg[src], c, self.scale, out=out)
+            elif kind == "add":
+                _, lv, a, b, dst = op
+                A = ctx.drop_level(reg[a], lv, out=bufs[3 * k + 1])
+                Bc = ctx.drop_level(reg[b], lv, out=bufs[3 * k + 2])
+                reg[dst] = ctx.add(A, Bc, out=out)
+            elif kind == "boot":
+                reg[op[1]] = ctx.layer_apply_graph(self.boot, reg[op[1]], out)
+        y = reg["x"]
+        return ctx.drop_level(y, ctx.ct_info(y)[0])

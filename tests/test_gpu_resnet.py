@@ -84,3 +84,14 @@ def test_mini_resnet_matches_fp64():
     err = np.max(np.abs(logits - want))
     print("mini resnet: max |encrypted - fp64| = %.3g (logits up to %.3g)" % (err, np.max(np.abs(want))))
     assert err < 1e-2 * max(1.0, np.max(np.abs(want)))
+    # the graph replay (first call captures, second replays) gives the same
+    # ciphertext; capture needs a created stream
+    import torch
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g.set_stream(stream.cuda_stream)
+    for _ in range(2):
+        yg = net.forward_graph(ct)
+        assert gpu_common.mismatch(g.ct_download(yg), g.ct_download(y)) == 0
+    g.sync()
+    g.set_stream(torch.cuda.current_stream().cuda_stream)
