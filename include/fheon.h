@@ -612,6 +612,10 @@ int fheon_relu_prepare_plain(fheon_ctx *ctx, double beta, uint32_t degree, const
  * already scaled by 1/beta).  Depth ceil(log2 degree) + 1; the output keeps
  * the input's scale. */
 int fheon_cheb_prepare(fheon_ctx *ctx, const double *coeffs, uint32_t degree, uint32_t level, fheon_layer **out);
+/* Levels a Chebyshev series of this degree consumes (fheon_cheb_prepare, and
+ * fheon_relu_* without the mask): 6 for degree 59, 5 for 27; 0 for a degree
+ * outside [1, 1023]. */
+uint32_t fheon_cheb_depth(uint32_t degree);
 /* Apply a prepared ReLU; `in` at the layer's level, out distinct from in. */
 int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
 /* One-shot: prepare at in's level, apply, release. */

@@ -187,7 +187,7 @@ def evalmod_fp64(x, K, r, D=BOOT_DEGREE):
 
 def depth(cts, stc, D, r):
     """Levels a bootstrap consumes."""
-    return cts + (math.ceil(math.log2(D)) + 1) + r + stc
+    return cts + OF.cheb_depth(D) + r + stc
 
 
 class Plan:
@@ -233,7 +233,7 @@ class Plan:
             lv -= 1
         self.cts_scale = s
         # EvalMod: the series keeps the scale; each doubling squares it and rescales
-        lv -= math.ceil(math.log2(D)) + 1
+        lv -= OF.cheb_depth(D)
         for _ in range(self.r):
             s = (s * s) / q[lv - 1]
             lv -= 1

@@ -8,6 +8,8 @@ at slot c*H*W + h*W + w.  Rot_r moves slot i+r to slot i (r > 0 rotates left),
 which is the reading under which the nine masks of Algorithm 3 match the
 rotations of Algorithm 1.
 """
+import math
+
 import numpy as np
 
 from . import ckks
@@ -218,20 +220,103 @@ def relu_mask_values(nslots, beta, n):
     return v
 
 
+def ps_params(D):
+    """Baby-step count k = 2^ceil(log2(D+1)/2) and giant count m, the least with
+    D < k 2^m, of the baby-step/giant-step (Paterson-Stockmeyer) evaluation
+    of a degree-D Chebyshev series."""
+    k = 1 << math.ceil(math.log2(D + 1) / 2)
+    m = 0
+    while k * (1 << m) <= D:
+        m += 1
+    return k, m
+
+
+def cheb_depth(D):
+    """Levels cheb_encrypted consumes for degree D: a product lands one level
+    below the lower of its operands, a leaf one below the lowest baby it
+    reads."""
+    k, m = ps_params(D)
+    dep = {1: 0}
+    for d in range(2, min(k, D) + 1):
+        dep[d] = max(dep[d - d // 2], dep[d // 2]) + 1
+    gd = [dep[k]] if m else []
+    for _ in range(1, m):
+        gd.append(gd[-1] + 1)
+
+    def leaf(deg):
+        return max(dep[i] for i in range(1, max(deg, 1) + 1)) + 1
+
+    def depth_of(deg, j):
+        if j == 0:
+            return leaf(deg)
+        g = k << (j - 1)
+        if deg < g:
+            return depth_of(deg, j - 1)
+        return max(max(depth_of(deg - g, j - 1), gd[j - 1]) + 1, depth_of(g - 1, j - 1))
+    return depth_of(D, m)
+
+
+def cheb_split(c, g):
+    """p = r + q T_g for a series c of degree < 2g (from 2 T_g T_j = T_{g+j} +
+    T_{g-j}): q_0 = c_g, q_j = 2 c_{g+j}; r_i = c_i (i < g) less c_{g+j} at
+    i = g - j."""
+    deg = len(c) - 1
+    q = [c[g]] + [2.0 * c[g + j] for j in range(1, deg - g + 1)]
+    r = list(c[:g])
+    for j in range(1, deg - g + 1):
+        r[g - j] = r[g - j] - c[g + j]
+    return q, r
+
+
+def ps_eval_fp64(c, z):
+    """The series c at z in FP64 along the same tree as cheb_encrypted."""
+    D = len(c) - 1
+    k, m = ps_params(D)
+    z = np.asarray(z, dtype=np.float64)
+    T = {0: np.ones_like(z), 1: z}
+    for d in range(2, min(k, D) + 1):
+        h = d // 2
+        T[d] = 2.0 * T[d - h] * T[h] - (T[1] if d % 2 else 1.0)
+    G = [T[k]] if m else []
+    for _ in range(1, m):
+        G.append(2.0 * G[-1] * G[-1] - 1.0)
+
+    def ev(c, j):
+        deg = len(c) - 1
+        if j == 0:
+            return sum(c[i] * T[i] for i in range(deg + 1))
+        g = k << (j - 1)
+        if deg < g:
+            return ev(c, j - 1)
+        cq, cr = cheb_split(c, g)
+        return ev(cr, j - 1) + ev(cq, j - 1) * G[j - 1]
+    return ev(list(c), m)
+
+
 def cheb_encrypted(ctx, v, scale, c, rlk):
     """sum_d c_d T_d(v) for a ciphertext v of scale `scale` (returns the
-    ciphertext, of scale `scale`).  T_1 = v; T_2h = 2 T_h^2 - 1 (product at
-    T_h's level, rescaled, then -1 added); T_2h+1 = 2 T_h+1 T_h - T_1: the
-    product (scale S = s_h+1 s_h, at the lower operand level) plus T_1 times
-    K = llround((-1 * S) / s_1), rescaled once.  Finally y = sum_d K_d T_d
-    (d >= 1, all at one level, K_d = llround(((c_d * scale) * q) / s_d) for the
-    prime q the sum is rescaled by), rescaled once onto `scale`, plus c_0.
-    Depth ceil(log2 D) + 1 for degree D."""
+    ciphertext, of scale `scale`), by baby steps and giant steps:
+      babies T_1..T_k (k = ps_params): T_2h = 2 T_h^2 - 1 (product at T_h's
+        level, rescaled, then -1 added); T_2h+1 = 2 T_h+1 T_h - T_1 (the
+        product, scale S = s_h+1 s_h at the lower operand level, plus T_1 times
+        K = llround((-1 * S) / s_1), rescaled once);
+      giants G_0 = T_k, G_j = 2 G_j-1^2 - 1 = T_{k 2^j};
+      ev(c, j) for degree < k 2^j: a leaf (j = 0) is sum_i K_i T_i over
+        T_1..T_deg at the lowest of their levels, K_i = llround(((c_i * S_t)
+        * q) / s_i) for the prime q it is rescaled by, plus c_0: it lands on
+        the target scale S_t.  Otherwise, with g = k 2^(j-1) and p = r + q
+        T_g (cheb_split): ev(q) aimed at S_t q_p / s_G (q_p the prime of the
+        product's rescale at level l_p = min(level of ev(q), level of G)),
+        times G_j-1 at l_p, rescaled; plus ev(r) aimed at S_t; the two at
+        the lower of their levels.
+    Depth cheb_depth(D) (6 for degree 59, at most ceil(log2 D) + 1), with
+    about 2 sqrt(D) + log2 D products instead of D - 1."""
     q = ctx.q
     D = len(c) - 1
+    k, m = ps_params(D)
     lev = lambda a: a.shape[1]  # noqa: E731
     T = {1: (v, scale)}
-    for d in range(2, D + 1):
+    for d in range(2, min(k, D) + 1):
         (A, sa), (B, sb) = T[d - d // 2], T[d // 2]
         lv = min(lev(A), lev(B))
         A, B = ctx.drop_level(A, lv), ctx.drop_level(B, lv)
@@ -244,20 +329,54 @@ def cheb_encrypted(ctx, v, scale, c, rlk):
             t1, s1 = T[1]
             K = ckks.llround((-1.0 * S) / s1)
             T[d] = (ctx.rescale(ctx.add(prod, ctx.mul_int(ctx.drop_level(t1, lv), K))), sc)
-    lstar = min(lev(T[d][0]) for d in T) - 1
-    y = None
-    for d in range(1, D + 1):
-        A, sa = T[d]
-        term = ctx.mul_int(ctx.drop_level(A, lstar + 1), ctx.const_factor(lstar + 1, c[d], scale, sa))
-        y = term if y is None else ctx.add(y, term)
-    return ctx.add_const(ctx.rescale(y), c[0], scale)
+    G = [T[k]] if m else []
+    for _ in range(1, m):
+        A, sa = G[-1]
+        prod = ctx.mul_relin(ctx.mul_int(A, 2), A, rlk)
+        sc = (sa * sa) / float(q[lev(A) - 1])
+        G.append((ctx.add_const(ctx.rescale(prod), -1.0, sc), sc))
+
+    def leaf_level(deg):
+        return min(lev(T[i][0]) for i in range(1, max(deg, 1) + 1)) - 1
+
+    def out_level(deg, j):
+        if j == 0:
+            return leaf_level(deg)
+        g = k << (j - 1)
+        if deg < g:
+            return out_level(deg, j - 1)
+        return min(min(out_level(deg - g, j - 1), lev(G[j - 1][0])) - 1, out_level(g - 1, j - 1))
+
+    def ev(c, j, St):
+        deg = len(c) - 1
+        if j == 0:
+            lv = leaf_level(deg) + 1
+            y = None
+            for i in range(1, max(deg, 1) + 1):
+                A, sa = T[i]
+                term = ctx.mul_int(ctx.drop_level(A, lv), ctx.const_factor(lv, c[i] if i <= deg else 0.0, St, sa))
+                y = term if y is None else ctx.add(y, term)
+            return ctx.add_const(ctx.rescale(y), c[0], St)
+        g = k << (j - 1)
+        if deg < g:
+            return ev(c, j - 1, St)
+        cq, cr = cheb_split(c, g)
+        Gc, sg = G[j - 1]
+        lp = min(out_level(len(cq) - 1, j - 1), lev(Gc))
+        qct = ev(cq, j - 1, (St * float(q[lp - 1])) / sg)
+        prod = ctx.rescale(ctx.mul_relin(ctx.drop_level(qct, lp), ctx.drop_level(Gc, lp), rlk))
+        rct = ev(cr, j - 1, St)
+        lo = min(lev(prod), lev(rct))
+        return ctx.add(ctx.drop_level(rct, lo), ctx.drop_level(prod, lo))
+
+    return ev(list(c), m, scale)
 
 
 def relu_encrypted(ctx, ct, scale, beta, D, mask_plain, rlk):
     """Alg. 4 on a ciphertext of scale `scale` (returns (ct, scale)):
     v = x * mask (rescaled; only when beta > 1), then the Chebyshev series of f
     at v (cheb_encrypted).  The output has the input's scale, at depth
-    ceil(log2 D) + 1 (+1 with the mask) below the input."""
+    cheb_depth(D) (+1 with the mask) below the input."""
     c = relu_cheb_coeffs(beta, D)
     v = ctx.rescale(ctx.mul_plain(ct, mask_plain)) if beta > 1 else ct
     return cheb_encrypted(ctx, v, scale, c, rlk), scale

@@ -84,9 +84,9 @@ struct fheon_layer {
 };
 
 namespace fheon {
-// Chebyshev series (relu.cu): `work` holds D + 4 working ciphertexts
+// Chebyshev series (relu.cu): `work` holds the working ciphertexts
 // (cheb_work makes them); work[1] = T_1 on entry, at the series' input
-// scale; out = sum_d c_d T_d at that scale, ceil(log2 D) + 1 levels below
+// scale; out = sum_d c_d T_d at that scale, cheb_depth(D) levels below
 int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, double scale);
 int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out);
 u32 cheb_depth(u32 D);

@@ -10,13 +10,19 @@
 // are the zeros of T_{D+1}.
 //
 // Evaluation (cheb_series, shared with bootstrapping's EvalMod; depth
-// ceil(log2 D) + 1, + 1 for the mask):
-//   T_1 = v; T_2h = 2 T_h^2 - 1; T_2h+1 = 2 T_h+1 T_h - T_1,
-// each product taken at the lower operand's level with relinearisation and
-// rescaled; T_1 is brought to the product's level and exact scale by a
-// rescaled constant product (c = -1).  Then every c_d T_d (d >= 1) is
-// rescaled onto the input's scale at one common level, the terms are summed
-// in order of d, and c_0 is added.  The output has the input's scale.
+// cheb_depth(D), 6 for degree 59, + 1 for the mask), baby steps and giant
+// steps (Paterson-Stockmeyer in the Chebyshev basis):
+//   babies T_1 = v, T_2h = 2 T_h^2 - 1, T_2h+1 = 2 T_h+1 T_h - T_1 up to
+//   T_k (k = 2^ceil(log2(D+1)/2)), each product at the lower operand's level
+//   with relinearisation, rescaled (the -T_1 of an odd one joins the product
+//   before its rescale, as T_1 times K = llround(-S / s_1));
+//   giants T_k, T_2k = 2 T_k^2 - 1, ..., up to m of them (D < k 2^m);
+//   p = r + q T_g (g = k 2^(j-1), q_0 = c_g, q_j = 2 c_{g+j}, r_{g-j} -= c_{g+j})
+//   recursively: q aimed at the scale that lands the product q T_g,
+//   rescaled, on the target; a leaf (degree < k) is one integer combination
+//   of the babies, rescaled once onto its target, plus c_0.
+// The output has the input's scale; about 2 sqrt(D) + log2 D products.
+#include <algorithm>
 #include <cmath>
 #include <memory>
 #include <vector>
@@ -66,13 +72,141 @@ int check_args(fheon_ctx *ctx, double beta, u32 D, u32 level)
 
 namespace fheon {
 
-u32 cheb_depth(u32 D) { return ceil_log2(D) + 1; }
+// Baby-step/giant-step (Paterson-Stockmeyer) shape of a degree-D series:
+// k = 2^ceil(log2(D+1)/2) babies T_1..T_k, m giants T_k, T_2k, .., T_{k 2^(m-1)}
+// with D < k 2^m.
+void ps_params(u32 D, u32 &k, u32 &m)
+{
+    u32 b = 0;
+    while ((1ull << (2 * b)) < (u64)D + 1) b++; // 2b >= log2(D+1)
+    k = 1u << b;
+    m = 0;
+    while ((u64)k << m <= D) m++;
+}
+
+namespace {
+// depth of each baby (levels below T_1) and of each giant
+struct PsShape {
+    u32 k = 0, m = 0;
+    std::vector<u32> dep; // [1..min(k, D)]
+    std::vector<u32> gd;  // [0..m-1]
+};
+PsShape ps_shape(u32 D)
+{
+    PsShape P;
+    ps_params(D, P.k, P.m);
+    const u32 kb = std::min(P.k, D);
+    P.dep.assign(kb + 1, 0);
+    for (u32 d = 2; d <= kb; d++) P.dep[d] = std::max(P.dep[d - d / 2], P.dep[d / 2]) + 1;
+    if (P.m) P.gd.push_back(P.dep[P.k]);
+    for (u32 j = 1; j < P.m; j++) P.gd.push_back(P.gd.back() + 1);
+    return P;
+}
+u32 ps_depth_of(const PsShape &P, u32 deg, u32 j)
+{
+    if (j == 0) {
+        u32 d = 0;
+        for (u32 i = 1; i <= std::max(deg, 1u); i++) d = std::max(d, P.dep[i]);
+        return d + 1;
+    }
+    const u32 g = P.k << (j - 1);
+    if (deg < g) return ps_depth_of(P, deg, j - 1);
+    return std::max(std::max(ps_depth_of(P, deg - g, j - 1), P.gd[j - 1]) + 1, ps_depth_of(P, g - 1, j - 1));
+}
+
+// p = r + q T_g for a series of degree < 2g (2 T_g T_j = T_{g+j} + T_{g-j}):
+// q_0 = c_g, q_j = 2 c_{g+j}; r_i = c_i (i < g) less c_{g+j} at i = g - j
+void cheb_split(const std::vector<double> &c, u32 g, std::vector<double> &q, std::vector<double> &r)
+{
+    const u32 deg = (u32)c.size() - 1;
+    q.assign(1, c[g]);
+    for (u32 j = 1; j + g <= deg; j++) q.push_back(2.0 * c[g + j]);
+    r.assign(c.begin(), c.begin() + g);
+    for (u32 j = 1; j + g <= deg; j++) r[g - j] = r[g - j] - c[g + j];
+}
+
+struct PsEval {
+    fheon_ctx *ctx;
+    std::vector<fheon_ct *> &work;
+    u32 k, m, top;                    // top: next free working ciphertext
+    std::vector<fheon_ct *> T, G;     // babies [1..], giants [0..m-1]
+
+    u32 leaf_level(u32 deg) const
+    {
+        u32 lv = T[1]->level;
+        for (u32 i = 1; i <= std::max(deg, 1u); i++) lv = std::min(lv, T[i]->level);
+        return lv - 1;
+    }
+    u32 out_level(u32 deg, u32 j) const
+    {
+        if (j == 0) return leaf_level(deg);
+        const u32 g = k << (j - 1);
+        if (deg < g) return out_level(deg, j - 1);
+        return std::min(std::min(out_level(deg - g, j - 1), G[j - 1]->level) - 1, out_level(g - 1, j - 1));
+    }
+    // sum_i c_i T_i landing on scale St, into `out`
+    int ev(const std::vector<double> &c, u32 j, double St, fheon_ct *out)
+    {
+        const u32 deg = (u32)c.size() - 1, N = ctx->N;
+        int rc;
+        if (j == 0) {
+            const u32 lv = leaf_level(deg) + 1, n = std::max(deg, 1u);
+            const double q = (double)ctx->mod[lv - 1];
+            std::vector<const u64 *> src(n);
+            std::vector<u64> stride(n);
+            std::vector<int64_t> K(n);
+            for (u32 i = 1; i <= n; i++) {
+                const double ci = i <= deg ? c[i] : 0.0;
+                if (!round_int(((ci * St) * q) / T[i]->scale, &K[i - 1]))
+                    return fail(ctx, FHEON_ERR_ARG, "chebyshev: coefficient factor out of range");
+                src[i - 1] = T[i]->c0();
+                stride[i - 1] = (u64)T[i]->level * N;
+            }
+            if ((rc = ct_reshape(ctx, out, lv))) return rc;
+            FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), n, out->c0(), lv));
+            out->scale = St * q; // the sum's scale before the rescale (metadata)
+            if ((rc = fheon_rescale(ctx, out, out))) return rc;
+            out->scale = St;
+            return fheon_add_const(ctx, out, c[0], out);
+        }
+        const u32 g = k << (j - 1);
+        if (deg < g) return ev(c, j - 1, St, out);
+        std::vector<double> cq, cr;
+        cheb_split(c, g, cq, cr);
+        const fheon_ct *Gc = G[j - 1];
+        const u32 lp = std::min(out_level((u32)cq.size() - 1, j - 1), Gc->level);
+        if (top + 2 > work.size()) return fail(ctx, FHEON_ERR_ARG, "chebyshev: working set exhausted");
+        fheon_ct *tq = work[top], *tr = work[top + 1];
+        top += 2;
+        if ((rc = ev(cq, j - 1, (St * (double)ctx->mod[lp - 1]) / Gc->scale, tq))) return rc;
+        if ((rc = mul_relin_at(ctx, tq, Gc, lp, false, out))) return rc;
+        if ((rc = fheon_rescale(ctx, out, out))) return rc;
+        out->scale = St;
+        if ((rc = ev(cr, j - 1, St, tr))) return rc;
+        const u32 lo = std::min(out->level, tr->level);
+        if (tr->level > lo && (rc = fheon_drop_level(ctx, tr, lo, tr))) return rc;
+        if (out->level > lo && (rc = fheon_drop_level(ctx, out, lo, out))) return rc;
+        if ((rc = fheon_add(ctx, tr, out, out))) return rc;
+        top -= 2;
+        return FHEON_OK;
+    }
+};
+} // namespace
+
+u32 cheb_depth(u32 D)
+{
+    const PsShape P = ps_shape(D);
+    return ps_depth_of(P, D, P.m);
+}
 
 int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, double scale)
 {
-    // T_1 .. T_D (index d), two temporaries and the sum: nothing is allocated
-    // after the first application
-    if (work.size() != D + 4) work.resize(D + 4, nullptr);
+    // T_1 .. T_k (index d), the giants, two per level of the tree and two
+    // temporaries: nothing is allocated after the first application
+    u32 k, m;
+    ps_params(D, k, m);
+    const size_t need = (size_t)std::min(k, D) + m + 2 * (size_t)m + 4;
+    if (work.size() < need) work.resize(need, nullptr);
     for (fheon_ct *&c : work) {
         int rc;
         if (!c && (rc = fheon_ct_create(ctx, level, scale, &c))) return rc;
@@ -83,13 +217,15 @@ int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, d
 int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out)
 {
     const u32 D = (u32)coeffs.size() - 1, N = ctx->N;
+    u32 k, m;
+    ps_params(D, k, m);
+    const u32 kb = std::min(k, D);
     fheon_ct **T = work.data();
-    fheon_ct *t1 = work[D + 2], *y = work[D + 3];
-    const double s0 = T[1]->scale;
+    fheon_ct *t1 = work[kb + m + 1];
     int rc;
-    // operands at a higher level are read in place (their lowest limbs), and
-    // the factor 2 of 2 T_a T_b is applied inside the tensor
-    for (u32 d = 2; d <= D; d++) {
+    // babies: operands at a higher level are read in place (their lowest
+    // limbs), and the factor 2 of 2 T_a T_b is applied inside the tensor
+    for (u32 d = 2; d <= kb; d++) {
         const u32 h = d / 2;
         fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
         const u32 lv = A->level < B->level ? A->level : B->level;
@@ -105,31 +241,25 @@ int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<f
         if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
         if (d % 2 == 0 && (rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
     }
-    u32 lstar = T[1]->level;
-    for (u32 d = 1; d <= D; d++) lstar = T[d]->level < lstar ? T[d]->level : lstar;
-    lstar -= 1;
-    // y = sum_d K_d T_d at level lstar + 1 in one pass, rescaled once onto s0
-    std::vector<const u64 *> src(D);
-    std::vector<u64> stride(D);
-    std::vector<int64_t> K(D);
-    const double q = (double)ctx->mod[lstar];
-    for (u32 d = 1; d <= D; d++) {
-        if (!round_int(((coeffs[d] * s0) * q) / T[d]->scale, &K[d - 1]))
-            return fail(ctx, FHEON_ERR_ARG, "chebyshev: coefficient factor out of range");
-        src[d - 1] = T[d]->c0();
-        stride[d - 1] = (u64)T[d]->level * N;
+    // giants: G_0 = T_k, G_j = 2 G_j-1^2 - 1
+    PsEval E{ctx, work, k, m, kb + m + 2, {}, {}};
+    E.T.assign(T, T + kb + 1);
+    if (m) E.G.push_back(T[k]);
+    for (u32 j = 1; j < m; j++) {
+        fheon_ct *A = E.G.back(), *Gj = work[kb + j];
+        if ((rc = mul_relin_at(ctx, A, A, A->level, true, Gj))) return rc;
+        if ((rc = fheon_rescale(ctx, Gj, Gj))) return rc;
+        if ((rc = fheon_add_const(ctx, Gj, -1.0, Gj))) return rc;
+        E.G.push_back(Gj);
     }
-    if ((rc = ct_reshape(ctx, y, lstar + 1))) return rc;
-    FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), D, y->c0(), lstar + 1));
-    y->scale = s0 * q; // the sum's scale before the rescale (metadata)
-    if ((rc = fheon_rescale(ctx, y, y))) return rc;
-    y->scale = s0;
-    return fheon_add_const(ctx, y, coeffs[0], out);
+    return E.ev(coeffs, m, T[1]->scale, out);
 }
 
 } // namespace fheon
 
 extern "C" {
+
+uint32_t fheon_cheb_depth(uint32_t degree) { return degree < 1 || degree > 1023 ? 0 : cheb_depth(degree); }
 
 int fheon_relu_coeffs(double beta, uint32_t degree, double *out)
 {

@@ -146,6 +146,7 @@ SIGNATURES = {
     "fheon_relu_prepare_plain": [c_vp, c_dbl, c_u32, c_vp, c_u32, c_vpp],
     "fheon_relu_apply": [c_vp, c_vp, c_vp, c_vp],
     "fheon_cheb_prepare": [c_vp, P(c_dbl), c_u32, c_u32, c_vpp],
+    "fheon_cheb_depth": [c_u32],
     "fheon_relu_approx": [c_vp, c_vp, c_dbl, c_u32, c_u32, c_vp],
     "fheon_mac_plain": [c_vp, P(c_vp), P(c_vp), c_u32, c_vp],
     "fheon_add": [c_vp, c_vp, c_vp, c_vp],
@@ -162,7 +163,8 @@ SIGNATURES = {
     "fheon_profile_begin": [c_vp],
     "fheon_profile_end": [c_vp, ctypes.c_char_p, c_sz],
 }
-_RESTYPE = {"fheon_error_string": ctypes.c_char_p, "fheon_last_error": ctypes.c_char_p, "fheon_galois_elt": c_u64}
+_RESTYPE = {"fheon_error_string": ctypes.c_char_p, "fheon_last_error": ctypes.c_char_p, "fheon_galois_elt": c_u64,
+            "fheon_cheb_depth": c_u32}
 
 _lib = None
 
@@ -208,6 +210,14 @@ def __getattr__(name):
 
 # ---------------------------------------------------------------- allocator hook
 _hooks = None
+
+
+def cheb_depth(degree):
+    """Levels the library's Chebyshev series of this degree consumes."""
+    d = load().fheon_cheb_depth(int(degree))
+    if not d:
+        raise FheonError(FHEON_ERR_ARG, "degree outside [1, 1023]")
+    return d
 
 
 def relu_coeffs(beta, degree=59):

@@ -14,6 +14,7 @@ at stride-aligned slots (dilation 2, then 4) instead of compacting them.
 """
 import numpy as np
 
+from . import fheon as F
 from . import synth
 
 GRID, BLOCK = 28, 784
@@ -21,13 +22,17 @@ RELU_DEGREE = 59
 # (out, in, k) of the two convolutions and (out, in) of the three FC layers
 CONVS = [(6, 1, 5), (16, 6, 5)]
 FCS = [(120, 256), (84, 120), (10, 84)]
-# levels each layer uses (a ReLU: ceil(log2 59) + 1, + 1 for the mask when beta > 1)
-DEPTH = {"conv": 1, "pool": 1, "fc": 1, "relu": 8}
-LEVELS = 2 * DEPTH["conv"] + 2 * DEPTH["pool"] + 3 * DEPTH["fc"] + 4 * DEPTH["relu"]  # at most
+# levels each layer uses (a ReLU: the series' depth, + 1 for the mask when beta > 1)
+DEPTH = {"conv": 1, "pool": 1, "fc": 1}
 
 
 def relu_depth(beta):
-    return int(np.ceil(np.log2(RELU_DEGREE))) + 1 + (1 if beta > 1.0 else 0)
+    return F.cheb_depth(RELU_DEGREE) + (1 if beta > 1.0 else 0)
+
+
+def levels():
+    """The most levels the network uses (every ReLU with its mask)."""
+    return 2 * DEPTH["conv"] + 2 * DEPTH["pool"] + 3 * DEPTH["fc"] + 4 * relu_depth(2.0)
 
 
 def weights(seed):

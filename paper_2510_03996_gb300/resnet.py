@@ -20,10 +20,10 @@ The convolution in front of a ReLU carries the ReLU's 1/beta in its weights,
 so its output -- the bootstrap's input -- lies in [-1, 1]; the identity
 shortcut of a block is scaled by 1/beta with one constant product on its own
 (shallower) path.  After a bootstrap the level is B = L - (bootstrap depth);
-the ReLU series takes ceil(log2 59) + 1 = 7 levels, a convolution one, the
+the ReLU series takes 6 levels (fheon_cheb_depth(59)), a convolution one, the
 repacking two (in-block compaction, then block compaction), global pooling
 and FC one each: the deepest stretch between bootstraps -- series, the two
-repacks, the stage-3 stride-2 convolution -- needs B >= 11.
+repacks, the stage-3 stride-2 convolution -- needs B >= 10.
 
 Packing: channel c of a map in the block at c * block on a grid of row
 stride `grid`; stride-2 layers leave their outputs at dilated positions
@@ -36,7 +36,6 @@ from . import fheon as F
 from . import synth
 
 RELU_DEGREE = 59
-SERIES_DEPTH = 7  # ceil(log2 59) + 1
 
 FULL = dict(img=32, in_ch=3, chans=(16, 32, 64), blocks=3, classes=10)
 
@@ -154,7 +153,7 @@ def pack_input(X, nslots, arch=FULL):
 
 class EncryptedResNet:
     """The layers of the network prepared on a context whose bootstrap leaves
-    level B >= 11, for inputs at level B (`in_level`) at the context's scale.
+    level B >= 10, for inputs at level B (`in_level`) at the context's scale.
 
     forward(ct) runs: conv0 (x 1/beta_0) -> series_0 -> per block: conv_a
     (x 1/beta) -> [bootstrap] -> series -> conv_b (x 1/beta') + shortcut
@@ -167,8 +166,8 @@ class EncryptedResNet:
         self.L = ctx.L
         self.boot = ctx.bootstrap_prepare(scale, boot_params)
         self.B = ctx.bootstrap_info(self.boot)[0]
-        if self.B < 11:
-            raise ValueError("the bootstrap leaves level %d; the network needs 11" % self.B)
+        if self.B < 10:
+            raise ValueError("the bootstrap leaves level %d; the network needs 10" % self.B)
         self.mp = maps(arch)
         self.layers = {}
         self._series = {}
@@ -251,7 +250,7 @@ class EncryptedResNet:
             self.n_boot += 1
             lv = self.B
         self.plan.append(("layer", self._series_at(self.betas[r], lv), src, dst))
-        return lv - SERIES_DEPTH
+        return lv - F.cheb_depth(RELU_DEGREE)
 
     def rotation_steps(self):
         st = set()

@@ -37,16 +37,16 @@ def params(name):
         # P (180 bits) above the largest digit (60 + 40 + 40 bits) keeps key-switching noise small
         return dict(logN=12, qbits=[60] + [40] * 10, pbits=[60, 60, 60], dnum=4, scale=2.0 ** 40, seed=SEED_BASE + 9)
     if name == "boot_n12":  # test-sized bootstrapping: q_0 (2^12 above the scale), 2 levels left after it, SlotToCoeff 3 x 50 bits,
-        # EvalMod (degree-27 series + 7 doublings) 13 x 60 bits, CoeffToSlot 3 x 60 bits; P 6 x 60 bits
-        return dict(logN=12, qbits=[52] + [40] * 2 + [50] * 3 + [60] * 16, pbits=[60] * 6, dnum=4,
+        # EvalMod (degree-27 series in 5 levels + 7 doublings) 12 x 60 bits, CoeffToSlot 3 x 60 bits; P 6 x 60 bits
+        return dict(logN=12, qbits=[52] + [40] * 2 + [50] * 3 + [60] * 15, pbits=[60] * 6, dnum=4,
                     scale=2.0 ** 40, seed=SEED_BASE + 10)
     if name == "resnet_n16":  # ResNet-20 with bootstrapping: q_0 (2^12 above the scale), 10 levels of layers
-        # between bootstraps, SlotToCoeff 3 x 50 bits, EvalMod (degree-27 series + 9 doublings) 15 x 60 bits,
-        # CoeffToSlot 3 x 60 bits; P 8 x 60 bits above the largest digit (8 x 60 bits)
-        return dict(logN=16, qbits=[52] + [40] * 10 + [50] * 3 + [60] * 18, pbits=[60] * 8, dnum=4,
+        # between bootstraps, SlotToCoeff 3 x 50 bits, EvalMod (degree-27 series in 5 levels + 9 doublings)
+        # 14 x 60 bits, CoeffToSlot 3 x 60 bits; P 8 x 60 bits above the largest digit (8 x 60 bits)
+        return dict(logN=16, qbits=[52] + [40] * 10 + [50] * 3 + [60] * 17, pbits=[60] * 8, dnum=4,
                     scale=2.0 ** 40, seed=SEED_BASE + 3)
     if name == "resnet_n12":  # test-sized ResNet with bootstrapping: as resnet_n16 with 7 doublings
-        return dict(logN=12, qbits=[52] + [40] * 10 + [50] * 3 + [60] * 16, pbits=[60] * 8, dnum=4,
+        return dict(logN=12, qbits=[52] + [40] * 10 + [50] * 3 + [60] * 15, pbits=[60] * 8, dnum=4,
                     scale=2.0 ** 40, seed=SEED_BASE + 11)
     raise KeyError(name)
 

@@ -67,7 +67,7 @@ def test_relu_decodes_to_the_series(pair):
 def test_relu_errors(pair):
     g, F = pair.g, pair.F
     with pytest.raises(F.FheonError) as e:
-        g.relu_prepare(4.0, 59, 10, 8)  # needs level > 8
+        g.relu_prepare(4.0, 59, 10, OF.cheb_depth(59) + 1)  # needs level > depth + mask
     assert e.value.code == -4
     with pytest.raises(F.FheonError) as e:
         g.relu_prepare_plain(4.0, 59, None, pair.L)  # beta > 1 needs the mask

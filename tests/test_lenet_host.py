@@ -15,7 +15,7 @@ def test_fp64_forward_matches_the_oracle_layers():
 
 def test_level_budget_and_bounds():
     P = synth.params("lenet_n15")
-    assert lenet.LEVELS == 39 and len(P["qbits"]) >= lenet.LEVELS + 2
+    assert lenet.levels() == 7 + 4 * (OF.cheb_depth(59) + 1) and len(P["qbits"]) >= lenet.levels() + 2
     w = lenet.weights(synth.SEED_BASE + 2)
     xs = [synth.image(91, s, (1, 28, 28)) for s in range(4)]
     betas = lenet.relu_bounds(xs, w)

@@ -101,7 +101,7 @@ def test_evalmod_series_and_doublings():
 def test_default_bound_and_depth():
     assert B.default_K(1 << 12) == 128 and B.default_K(1 << 16) == 512
     assert B.default_doublings(128) == 7 and B.default_doublings(512) == 9
-    assert B.depth(3, 3, 27, 7) == 3 + 6 + 7 + 3
+    assert B.depth(3, 3, 27, 7) == 3 + B.OF.cheb_depth(27) + 7 + 3
 
 
 @pytest.fixture(scope="module")

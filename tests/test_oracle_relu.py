@@ -55,10 +55,24 @@ def test_encrypted_relu_matches_the_series(ctx10, beta):
     lvl = ct.shape[1]
     mask = ctx.plain_from_coeffs(ckks.encode(OF.relu_mask_values(N // 2, beta, n), N, float(ctx.q[lvl - 1])), lvl)
     y, sy = OF.relu_encrypted(ctx, ct, scale, beta, D, mask, rlk)
-    depth = 7 + (1 if beta > 1 else 0)
+    depth = OF.cheb_depth(D) + (1 if beta > 1 else 0)
     assert y.shape[1] == lvl - depth and sy == scale
     got = ctx.decode_ct(se, y, sy).real
     want = OF.relu_fp64(x[:n], beta, D)
     assert np.max(np.abs(got[:n] - want)) < 1e-4 * beta
     if beta > 1:  # the mask zeroed the other slots: f(0) = c-series at 0
         assert np.max(np.abs(got[n:] - OF.relu_fp64(0.0, beta, D))) < 1e-4 * beta
+
+
+def test_series_tree_and_depth():
+    """The baby-step/giant-step tree equals the plain Chebyshev sum (the
+    division p = r + q T_g), and the library's series depth is the oracle's."""
+    from paper_2510_03996_gb300 import fheon as F
+    z = np.linspace(-1, 1, 257)
+    for D in (1, 2, 3, 7, 15, 27, 31, 59, 63, 100, 255):
+        c = synth.rng(0x5E, D).normal(size=D + 1)
+        assert np.max(np.abs(OF.ps_eval_fp64(c, z) - OF.cheb_eval_fp64(c, z))) < 1e-12 * D
+    for D in range(1, 300):
+        assert F.cheb_depth(D) == OF.cheb_depth(D), D
+        assert OF.cheb_depth(D) <= int(np.ceil(np.log2(D + 1))) + 1
+    assert OF.cheb_depth(59) == 6 and OF.cheb_depth(27) == 5
