@@ -253,6 +253,17 @@ def per_ciphertext_rate(ctx, ins, outs, steps, stream, reps=2):
     return {"value": reps * len(ins) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / reps}
 
 
+def release(*ctxs):
+    """Close contexts and hand their device memory back: torch's caching
+    allocator keeps freed blocks per stream, and every context here has a
+    stream of its own."""
+    import torch
+    for c in ctxs:
+        c.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
 def lenet_timing(F, batch=32):
     """LeNet-5 encrypted inference (N = 2^15, 44 levels, no bootstrapping) over a
     batch of synthetic 1x28x28 U[0,1] inputs with random-init weights: seconds
@@ -295,7 +306,7 @@ def lenet_timing(F, batch=32):
         err = max(err, float(np.max(np.abs(got - lenet.forward_fp64(X, w)))))
     nkeys, kbytes = ctx.key_stats()
     del outs, gouts, cts, net, sk, pk
-    ctx.close()
+    release(ctx)
     return {"s_per_inference": secs / batch, "eager_s_per_inference": eager_secs / batch,
             "graph_equals_eager": same, "batch": batch, "keys": nkeys, "key_bytes": kbytes,
             "max_abs_logit_vs_fp64_exact_relu": err, "relu_bounds": betas, "levels": len(P["qbits"])}
@@ -355,7 +366,7 @@ def resnet_timing(F, n_inputs=2):
         agree += int(np.argmax(got) == np.argmax(want))
     nkeys, kbytes = ctx.key_stats()
     del outs, gouts, cts, net, sk, pk
-    ctx.close()
+    release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
             "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": 18,
             "inputs": n_inputs, "prepare_and_keygen_s": round(t_prep, 2), "keys": nkeys, "key_bytes": kbytes,
@@ -363,59 +374,98 @@ def resnet_timing(F, n_inputs=2):
             "levels": len(P["qbits"]), "paper_cpu_s_per_inference": 403}
 
 
-def serving_timing(F, n_req=40, rate=4.0, max_active=8):
-    """The serving workload with LeNet-5 requests: Poisson arrivals (exponential
-    gaps of mean 1/rate s from a seed), requests submitted to the
-    continuous-batching server when their arrival time has passed (host
-    clock), one server step at a time; latency = completion - arrival."""
+def serving_timing(F, n_req=40, rate=4.0, max_active=8, frac_resnet=0.3):
+    """The serving workload: Poisson arrivals (exponential gaps of mean 1/rate
+    s from a seed), each request LeNet-5 (N = 2^15) or, with probability
+    frac_resnet, ResNet-20 with bootstrapping (N = 2^16); one
+    continuous-batching server per context (the ResNet model is a program of
+    layer, bootstrap, add and constant steps over three registers), requests
+    submitted when their arrival time has passed (host clock), the two
+    servers stepped in turn; latency = completion - arrival."""
     import torch
-    from paper_2510_03996_gb300 import lenet
+    from paper_2510_03996_gb300 import lenet, resnet
+    kind = synth.rng(synth.SEED_BASE + 5, 802).random(n_req) < frac_resnet
+    gaps = synth.rng(synth.SEED_BASE + 5, 801).exponential(1.0 / rate, n_req)
+    arrive = np.cumsum(gaps) - gaps[0]
+    servers = []
+    # LeNet-5 on its context
     P = synth.params("lenet_n15")
     N = 1 << P["logN"]
-    s = torch.cuda.Stream()
-    ctx = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
-                    stream=s.cuda_stream)
+    s1 = torch.cuda.Stream()
+    c1 = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                   stream=s1.cuda_stream)
     w = lenet.weights(P["seed"])
     xs = [synth.image(P["seed"], 800 + i, (1, 28, 28)) for i in range(n_req)]
-    betas = lenet.relu_bounds(xs, w)
-    sk, pk = ctx.keygen()
-    ctx.relinkeygen(sk)
-    net = lenet.EncryptedLeNet(ctx, w, betas, ctx.L, P["scale"])
-    ctx.rotkeygen(sk, net.rotation_steps())
-    cts = [ctx.encrypt(pk, ctx.encode(lenet.pack_input(X, N // 2), ctx.L, P["scale"]), nonce=i)
-           for i, X in enumerate(xs)]
-    model = ctx.model(net.layers)
-    net.forward(cts[0])  # warm-up
-    ctx.sync()
-    gaps = synth.rng(P["seed"], 801).exponential(1.0 / rate, n_req)
-    arrive = np.cumsum(gaps) - gaps[0]
-    srv = ctx.server(max_active=max_active)
+    sk, pk = c1.keygen()
+    c1.relinkeygen(sk)
+    ln = lenet.EncryptedLeNet(c1, w, lenet.relu_bounds(xs, w), c1.L, P["scale"])
+    c1.rotkeygen(sk, ln.rotation_steps())
+    m1 = c1.model(ln.layers)
+    ct1 = {i: c1.encrypt(pk, c1.encode(lenet.pack_input(xs[i], N // 2), c1.L, P["scale"]), nonce=i)
+           for i in range(n_req) if not kind[i]}
+    c1.model_run(m1, next(iter(ct1.values())))  # warm-up
+    servers.append((c1, c1.server(max_active=max_active), m1, ct1))
+    # ResNet-20 on its context
+    P = synth.params("resnet_n16")
+    N = 1 << P["logN"]
+    s2 = torch.cuda.Stream()
+    c2 = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
+                   stream=s2.cuda_stream)
+    w = resnet.weights(P["seed"])
+    xs = [synth.image(P["seed"], 900 + i, (3, 32, 32), dist="normal") for i in range(n_req)]
+    sk, pk = c2.keygen()
+    rn = resnet.EncryptedResNet(c2, w, resnet.relu_bounds(xs[:4], w), P["scale"])
+    rn.keygen(sk)
+    m2 = rn.model()
+    ct2 = {i: c2.drop_level(c2.encrypt(pk, c2.encode(resnet.pack_input(xs[i], N // 2), c2.L, P["scale"]), nonce=i),
+                            rn.in_level) for i in range(n_req) if kind[i]}
+    if ct2:
+        c2.model_run(m2, next(iter(ct2.values())))  # warm-up
+    # a ResNet request in flight holds a few GB of working ciphertexts per batch slot
+    servers.append((c2, c2.server(max_active=min(max_active, 4)), m2, ct2))
+    c1.sync()
+    c2.sync()
     t0 = time.perf_counter()
     ids, done = {}, {}
+    owner = {i: int(kind[i]) for i in range(n_req)}
     nxt = 0
     while len(done) < n_req:
         now = time.perf_counter() - t0
         while nxt < n_req and arrive[nxt] <= now:
+            ctx, srv, model, cts = servers[owner[nxt]]
             ids[nxt] = srv.submit(model, cts[nxt])
             nxt += 1
         if len(ids) == len(done):
             time.sleep(max(0.0, min(0.01, arrive[nxt] - now)))
             continue
-        if srv.step():
-            now = time.perf_counter() - t0
-            for k, rid in ids.items():
-                if k not in done and srv.result(rid) is not None:
-                    done[k] = now
+        for which, (ctx, srv, model, cts) in enumerate(servers):
+            pending = [k for k in ids if k not in done and owner[k] == which]
+            if not pending:
+                continue
+            if srv.step():
+                now = time.perf_counter() - t0
+                for k in pending:
+                    if srv.result(ids[k]) is not None:
+                        done[k] = now
     lat = np.array([done[k] - arrive[k] for k in range(n_req)])
     span = max(done.values()) - arrive[0]
-    st = srv.stats()
-    srv.close()
-    del cts, net, model, sk, pk
-    ctx.close()
-    return {"requests": n_req, "arrival_rate_per_s": rate, "models": "LeNet-5 (N=2^15) only",
-            "throughput_per_s": n_req / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_batch": st["max_batch"], "steps": st["steps"],
-            "max_active": max_active}
+    out = {"requests": n_req, "arrival_rate_per_s": rate,
+           "models": "LeNet-5 (N=2^15) %d, ResNet-20 with bootstrapping (N=2^16) %d" % (n_req - kind.sum(), kind.sum()),
+           "throughput_per_s": n_req / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+           "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_active": {"lenet5": max_active,
+                                                                          "resnet20": min(max_active, 4)}}
+    for which, name in ((0, "lenet5"), (1, "resnet20")):
+        sel = np.array([owner[k] == which for k in range(n_req)])
+        if sel.any():
+            out[name + "_p50_ms"] = 1e3 * float(np.percentile(lat[sel], 50))
+            out[name + "_p99_ms"] = 1e3 * float(np.percentile(lat[sel], 99))
+        st = servers[which][1].stats()
+        out[name + "_max_batch"] = st["max_batch"]
+    for ctx, srv, model, cts in servers:
+        srv.close()
+    del servers, ct1, ct2, ln, rn, m1, m2
+    release(c1, c2)
+    return out
 
 
 def conv_layer_timing(F, iters=200):
@@ -454,7 +504,7 @@ def conv_layer_timing(F, iters=200):
     ctx.sync()
     layer.close()
     del out, ct, sk, pk
-    ctx.close()
+    release(ctx)
     return res
 
 
@@ -599,7 +649,7 @@ def run_gpu(args, rank, world, local_rank):
                        "conv_n13_layer": conv_layer_timing(F),
                        "lenet5_n15": lenet_timing(F),
                        "resnet20_n16": resnet_timing(F),
-                       "serving_lenet5": serving_timing(F, n_req=args.serve_requests)}
+                       "serving_mixed": serving_timing(F, n_req=args.serve_requests)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

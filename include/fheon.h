@@ -556,9 +556,31 @@ int fheon_layer_out_map(const fheon_layer *layer, fheon_map *out);
 /* ------------------------------------------------------------------ */
 /* Serving: continuous batching of inference requests                 */
 /* ------------------------------------------------------------------ */
-/* A model: the ordered layers of a network on one context (the layers stay
- * owned by the caller and must outlive the model and its requests). */
+/* A model: a program of steps over a request's registers on one context.
+ * Register 0 holds the input and, after the last step, the output.  A step
+ * writes register dst from:
+ *   FHEON_STEP_LAYER: a prepared layer (bootstraps included) applied to src;
+ *   FHEON_STEP_ADD:   the lowest `level` limbs of src plus those of src2;
+ *   FHEON_STEP_SCALE: c times src, rescaled onto the model's `scale`.
+ * The layers stay owned by the caller and must outlive the model and its
+ * requests. */
+#define FHEON_STEP_LAYER 0u
+#define FHEON_STEP_ADD 1u
+#define FHEON_STEP_SCALE 2u
+typedef struct fheon_step {
+    uint32_t op;
+    uint32_t src, src2, dst; /* registers */
+    uint32_t level;          /* ADD: the operands' common level */
+    const fheon_layer *layer;
+    double c;                /* SCALE: the constant */
+} fheon_step;
+int fheon_model_create_program(fheon_ctx *ctx, const fheon_step *steps, uint32_t n, uint32_t nreg, double scale,
+                               fheon_model **out);
+/* The ordered layers of a network: one layer step per layer on register 0. */
 int fheon_model_create(fheon_ctx *ctx, const fheon_layer *const *layers, uint32_t n, fheon_model **out);
+/* The model on one input, step by step on the context's stream (returns when
+ * the output is complete). */
+int fheon_model_run(fheon_ctx *ctx, const fheon_model *model, const fheon_ct *in, fheon_ct *out);
 int fheon_model_destroy(fheon_model *model);
 /* A server on the context's stream.  A submitted request is admitted while
  * fewer than max_active are in flight and the device has at least min_free
@@ -569,9 +591,9 @@ int fheon_server_destroy(fheon_server *server);
 /* Queue a request: the model on a copy of `in` (taken on the stream now). */
 int fheon_server_submit(fheon_server *server, const fheon_model *model, const fheon_ct *in, uint64_t *id);
 /* One scheduling step: admit what fits, take the oldest admitted request's
- * stage (model, next layer), apply that layer to every admitted request at
- * that stage as one batch (fheon_layer_apply_batch), advance them, and wait
- * for the stream.  *n_done: requests that finished in this step.  A result
+ * stage (model, next step), run that step for every admitted request at that
+ * stage (a layer step as one batch, fheon_layer_apply_batch), advance them,
+ * and wait for the stream.  *n_done: requests that finished in this step.  A result
  * equals the model applied to the request's input alone, bit for bit. */
 int fheon_server_step(fheon_server *server, uint32_t *n_done);
 /* The result of request `id` into out (then the request is forgotten), or

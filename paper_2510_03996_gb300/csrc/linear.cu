@@ -68,8 +68,8 @@ int own_plain(fheon_ctx *ctx, fheon_layer *ly, const std::vector<double> &v, u32
 }
 
 // n inputs at once: every input's tap rotations in one hoisted plan (grouped by
-// input), every group shift of every input in one plain batch; the result of
-// each input is the one it gets alone
+// input), the group shifts of every input in one plain batch per chunk of
+// groups; the result of each input is the one it gets alone
 int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins_, u32 n, fheon_ct *const *outs)
 {
     const u32 nt = (u32)ly->r.size(), ng = (u32)ly->s.size(), nf = (u32)ly->fold.size();
@@ -105,8 +105,13 @@ int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *i
             steps.push_back(ly->r[t]);
         }
     const u32 ns = (u32)steps.size();
+    // the groups go in chunks of GC: each chunk's sums are formed, moved by one
+    // batched rotation and added to the output in order, so the working set
+    // is bounded by the chunk and not by the layer's group count
+    constexpr u32 GC_MAX = 32;
+    const u32 GC = std::min(ng, GC_MAX);
     if ((rc = ensure_cts(ctx, ly->rot, (size_t)n * ns, ins[0]->level, ins[0]->scale))) return rc;
-    if ((rc = ensure_cts(ctx, ly->work, (size_t)n * 2 * ng, ins[0]->level, ins[0]->scale))) return rc;
+    if ((rc = ensure_cts(ctx, ly->work, (size_t)n * 2 * GC, ins[0]->level, ins[0]->scale))) return rc;
     std::vector<fheon_rot_item> items;
     for (u32 i = 0; i < n; i++)
         for (u32 k = 0; k < ns; k++) items.push_back(fheon_rot_item{ins[i], ly->rot[(size_t)i * ns + k], steps[k]});
@@ -114,36 +119,42 @@ int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *i
     std::vector<const fheon_ct *> srcs;
     std::vector<const fheon_pt *> ps;
     std::vector<fheon_rot_item> moves;
-    for (u32 i = 0; i < n; i++) {
-        fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * ng;
-        for (u32 g = 0; g < ng; g++) {
-            srcs.clear();
-            ps.clear();
-            for (u32 t = 0; t < nt; t++) {
-                const fheon_pt *p = ly->pts[(size_t)g * nt + t];
-                if (!p) continue;
-                srcs.push_back(idx[t] < 0 ? ins[i] : ly->rot[(size_t)i * ns + idx[t]]);
-                ps.push_back(p);
+    for (u32 g0 = 0; g0 < ng; g0 += GC) {
+        const u32 gn = std::min(GC, ng - g0);
+        moves.clear();
+        for (u32 i = 0; i < n; i++) {
+            fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * GC;
+            for (u32 gg = 0; gg < gn; gg++) {
+                const u32 g = g0 + gg;
+                srcs.clear();
+                ps.clear();
+                for (u32 t = 0; t < nt; t++) {
+                    const fheon_pt *p = ly->pts[(size_t)g * nt + t];
+                    if (!p) continue;
+                    srcs.push_back(idx[t] < 0 ? ins[i] : ly->rot[(size_t)i * ns + idx[t]]);
+                    ps.push_back(p);
+                }
+                if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), w[gg]))) return rc;
+                if ((rc = fheon_rescale(ctx, w[gg], w[gg]))) return rc;
+                if (ly->s[g] != 0) moves.push_back(fheon_rot_item{w[gg], w[GC + gg], ly->s[g]});
             }
-            if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), w[g]))) return rc;
-            if ((rc = fheon_rescale(ctx, w[g], w[g]))) return rc;
-            if (ly->s[g] != 0) moves.push_back(fheon_rot_item{w[g], w[ng + g], ly->s[g]});
+        }
+        if ((rc = rotate_many(ctx, moves.data(), (u32)moves.size(), false, ly->collect))) return rc;
+        for (u32 i = 0; i < n; i++) {
+            fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * GC;
+            fheon_ct *out = outs[i];
+            for (u32 gg = 0; gg < gn; gg++) {
+                const fheon_ct *term = ly->s[g0 + gg] != 0 ? w[GC + gg] : w[gg];
+                if (g0 + gg == 0) {
+                    if ((rc = fheon_drop_level(ctx, term, term->level, out))) return rc;
+                } else if ((rc = fheon_add(ctx, out, term, out))) {
+                    return rc;
+                }
+            }
         }
     }
-    if ((rc = rotate_many(ctx, moves.data(), (u32)moves.size(), false, ly->collect))) return rc;
-    for (u32 i = 0; i < n; i++) {
-        fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * ng;
-        auto term = [&](u32 g) { return ly->s[g] != 0 ? w[ng + g] : w[g]; };
-        fheon_ct *out = outs[i];
-        if (ng == 1) {
-            if ((rc = fheon_drop_level(ctx, term(0), term(0)->level, out))) return rc;
-        } else {
-            if ((rc = fheon_add(ctx, term(0), term(1), out))) return rc;
-            for (u32 g = 2; g < ng; g++)
-                if ((rc = fheon_add(ctx, out, term(g), out))) return rc;
-        }
-        if (ly->bias && (rc = fheon_add_plain(ctx, out, ly->bias, out))) return rc;
-    }
+    for (u32 i = 0; i < n; i++)
+        if (ly->bias && (rc = fheon_add_plain(ctx, outs[i], ly->bias, outs[i]))) return rc;
     return FHEON_OK;
 }
 

@@ -1,13 +1,18 @@
 // serve.cu -- continuous-batching server for encrypted inference requests.
 //
-// Requests of one or more models (ordered lists of prepared layers on one
-// context, evaluation keys resident) arrive over time.  A request is admitted
-// while fewer than `max_active` are in flight and the device has at least
-// `min_free` bytes free; the rest wait in arrival order.  Each step takes the
-// oldest admitted request's stage (model, next layer), applies that layer to
-// every admitted request at the same stage as one batch
-// (fheon_layer_apply_batch: their rotations share launches), and advances
-// them; requests past their model's last layer are done and keep their result
+// A model is a program over a request's registers (register 0 holds the
+// input and, at the end, the output): a step applies a prepared layer
+// (bootstraps included), adds two registers at a level, or multiplies one by
+// a constant rescaled onto the model's scale.  A chain of layers is the
+// program of one layer step per layer on register 0; a residual network uses
+// more registers.  Requests of one or more models on one context (evaluation
+// keys resident) arrive over time.  A request is admitted while fewer than
+// `max_active` are in flight and the device has at least `min_free` bytes
+// free; the rest wait in arrival order.  Each scheduling step takes the
+// oldest admitted request's stage (model, next step), runs that step for
+// every admitted request at the same stage -- a layer step as one batch
+// (fheon_layer_apply_batch: their rotations share launches) -- and advances
+// them; requests past their model's last step are done and keep their result
 // until it is taken.  A request's result is the one the model gives its input
 // alone, bit for bit: batching changes launches, never arithmetic.
 #include <algorithm>
@@ -22,22 +27,38 @@ using namespace fheon;
 
 struct fheon_model {
     fheon_ctx *ctx = nullptr;
-    std::vector<const fheon_layer *> layers;
+    std::vector<fheon_step> steps;
+    u32 nreg = 1;
+    double scale = 0; // target of constant steps
 };
 
 namespace {
 struct Request {
     uint64_t id = 0, seq = 0;
     const fheon_model *model = nullptr;
-    u32 next = 0; // next layer
-    fheon_ct *cur = nullptr, *nxt = nullptr;
+    u32 next = 0;                 // next step
+    std::vector<fheon_ct *> reg;  // registers
+    fheon_ct *nxt = nullptr, *aux = nullptr; // a step's output and an operand copy
     bool done = false;
     ~Request()
     {
-        fheon_ct_destroy(cur);
+        for (fheon_ct *c : reg) fheon_ct_destroy(c);
         fheon_ct_destroy(nxt);
+        fheon_ct_destroy(aux);
     }
 };
+
+// one non-layer step of one request: its output into r->nxt
+int run_step(fheon_ctx *ctx, const fheon_model *m, const fheon_step &st, Request *r)
+{
+    int rc;
+    if (st.op == FHEON_STEP_ADD) {
+        if ((rc = fheon_drop_level(ctx, r->reg[st.src], st.level, r->aux))) return rc;
+        if ((rc = fheon_drop_level(ctx, r->reg[st.src2], st.level, r->nxt))) return rc;
+        return fheon_add(ctx, r->aux, r->nxt, r->nxt);
+    }
+    return fheon_mul_const_rescale(ctx, r->reg[st.src], st.c, m->scale, r->nxt);
+}
 } // namespace
 
 struct fheon_server {
@@ -71,16 +92,62 @@ int admit(fheon_server *s)
 
 extern "C" {
 
+int fheon_model_create_program(fheon_ctx *ctx, const fheon_step *steps, uint32_t n, uint32_t nreg, double scale,
+                               fheon_model **out)
+{
+    if (!ctx || !out || !n || !steps || !nreg || nreg > 64) return FHEON_ERR_ARG;
+    for (u32 i = 0; i < n; i++) {
+        const fheon_step &st = steps[i];
+        const bool regs_ok = st.src < nreg && st.dst < nreg && (st.op != FHEON_STEP_ADD || st.src2 < nreg);
+        if (!regs_ok) return fail(ctx, FHEON_ERR_ARG, "model step %u: register out of range", i);
+        if (st.op == FHEON_STEP_LAYER && !st.layer) return fail(ctx, FHEON_ERR_ARG, "model step %u: no layer", i);
+        if (st.op == FHEON_STEP_ADD && st.level < 1) return fail(ctx, FHEON_ERR_ARG, "model step %u: level 0", i);
+        if (st.op == FHEON_STEP_SCALE && !(scale > 0)) return fail(ctx, FHEON_ERR_ARG, "model step %u: no scale", i);
+        if (st.op > FHEON_STEP_SCALE) return fail(ctx, FHEON_ERR_ARG, "model step %u: unknown op %u", i, st.op);
+    }
+    fheon_model *m = new fheon_model();
+    m->ctx = ctx;
+    m->steps.assign(steps, steps + n);
+    m->nreg = nreg;
+    m->scale = scale;
+    *out = m;
+    return FHEON_OK;
+}
+
 int fheon_model_create(fheon_ctx *ctx, const fheon_layer *const *layers, uint32_t n, fheon_model **out)
 {
     if (!ctx || !out || !n || !layers) return FHEON_ERR_ARG;
-    for (u32 i = 0; i < n; i++)
+    std::vector<fheon_step> st(n);
+    for (u32 i = 0; i < n; i++) {
         if (!layers[i]) return FHEON_ERR_ARG;
-    fheon_model *m = new fheon_model();
-    m->ctx = ctx;
-    m->layers.assign(layers, layers + n);
-    *out = m;
-    return FHEON_OK;
+        st[i] = fheon_step{FHEON_STEP_LAYER, 0, 0, 0, 0, layers[i], 0.0};
+    }
+    return fheon_model_create_program(ctx, st.data(), n, 1, 0.0, out);
+}
+
+int fheon_model_run(fheon_ctx *ctx, const fheon_model *m, const fheon_ct *in, fheon_ct *out)
+{
+    if (!ctx || !m || !in || !out || m->ctx != ctx) return FHEON_ERR_ARG;
+    Request r;
+    r.model = m;
+    r.reg.assign(m->nreg, nullptr);
+    int rc;
+    for (fheon_ct *&c : r.reg)
+        if ((rc = fheon_ct_create(ctx, in->level, in->scale, &c))) return rc;
+    if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r.nxt))) return rc;
+    if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r.aux))) return rc;
+    if ((rc = fheon_drop_level(ctx, in, in->level, r.reg[0]))) return rc;
+    for (const fheon_step &st : m->steps) {
+        if (st.op == FHEON_STEP_LAYER) {
+            if ((rc = fheon_layer_apply(ctx, st.layer, r.reg[st.src], r.nxt))) return rc;
+        } else if ((rc = run_step(ctx, m, st, &r))) {
+            return rc;
+        }
+        std::swap(r.reg[st.dst], r.nxt);
+    }
+    rc = fheon_drop_level(ctx, r.reg[0], r.reg[0]->level, out);
+    if (!rc) rc = fheon_sync(ctx); // the request's buffers go with it
+    return rc;
 }
 
 int fheon_model_destroy(fheon_model *m)
@@ -112,9 +179,12 @@ int fheon_server_submit(fheon_server *s, const fheon_model *m, const fheon_ct *i
     if (!s || !m || !in || !id || m->ctx != s->ctx) return FHEON_ERR_ARG;
     std::unique_ptr<Request> r(new Request());
     int rc;
-    if ((rc = fheon_ct_create(s->ctx, in->level, in->scale, &r->cur))) return rc;
+    r->reg.assign(m->nreg, nullptr);
+    for (fheon_ct *&c : r->reg)
+        if ((rc = fheon_ct_create(s->ctx, in->level, in->scale, &c))) return rc;
     if ((rc = fheon_ct_create(s->ctx, in->level, in->scale, &r->nxt))) return rc;
-    if ((rc = fheon_drop_level(s->ctx, in, in->level, r->cur))) return rc; // the request's own copy
+    if ((rc = fheon_ct_create(s->ctx, in->level, in->scale, &r->aux))) return rc;
+    if ((rc = fheon_drop_level(s->ctx, in, in->level, r->reg[0]))) return rc; // the request's own copy
     r->id = s->next_id++;
     r->model = m;
     *id = r->id;
@@ -137,20 +207,26 @@ int fheon_server_step(fheon_server *s, uint32_t *n_done)
     std::vector<Request *> batch;
     for (Request *r : s->active)
         if (r->model == m && r->next == stage) batch.push_back(r);
-    std::vector<const fheon_ct *> ins;
-    std::vector<fheon_ct *> outs;
-    for (Request *r : batch) {
-        ins.push_back(r->cur);
-        outs.push_back(r->nxt);
+    const fheon_step &st = m->steps[stage];
+    if (st.op == FHEON_STEP_LAYER) {
+        std::vector<const fheon_ct *> ins;
+        std::vector<fheon_ct *> outs;
+        for (Request *r : batch) {
+            ins.push_back(r->reg[st.src]);
+            outs.push_back(r->nxt);
+        }
+        if ((rc = fheon_layer_apply_batch(s->ctx, st.layer, ins.data(), (u32)batch.size(), outs.data()))) return rc;
+    } else {
+        for (Request *r : batch)
+            if ((rc = run_step(s->ctx, m, st, r))) return rc;
     }
-    if ((rc = fheon_layer_apply_batch(s->ctx, m->layers[stage], ins.data(), (u32)batch.size(), outs.data()))) return rc;
     s->steps++;
     s->max_batch = std::max<u32>(s->max_batch, (u32)batch.size());
     u32 done = 0;
     for (Request *r : batch) {
-        std::swap(r->cur, r->nxt);
+        std::swap(r->reg[st.dst], r->nxt);
         r->next++;
-        if (r->next == m->layers.size()) {
+        if (r->next == m->steps.size()) {
             r->done = true;
             done++;
         }
@@ -168,7 +244,7 @@ int fheon_server_result(fheon_server *s, uint64_t id, fheon_ct *out)
     auto it = s->all.find(id);
     if (it == s->all.end()) return fail(s->ctx, FHEON_ERR_ARG, "no request %llu", (unsigned long long)id);
     if (!it->second->done) return FHEON_PENDING;
-    const fheon_ct *r = it->second->cur;
+    const fheon_ct *r = it->second->reg[0];
     int rc = fheon_drop_level(s->ctx, r, r->level, out);
     if (rc) return rc;
     if ((rc = fheon_sync(s->ctx))) return rc;

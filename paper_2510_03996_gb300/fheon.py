@@ -42,6 +42,15 @@ class fheon_rot_item(ctypes.Structure):
     _fields_ = [("input", c_vp), ("output", c_vp), ("step", c_i32)]
 
 
+class fheon_step(ctypes.Structure):
+    """One step of a model program (FHEON_STEP_LAYER / _ADD / _SCALE)."""
+    _fields_ = [("op", ctypes.c_uint32), ("src", ctypes.c_uint32), ("src2", ctypes.c_uint32),
+                ("dst", ctypes.c_uint32), ("level", ctypes.c_uint32), ("layer", c_vp), ("c", ctypes.c_double)]
+
+
+STEP_LAYER, STEP_ADD, STEP_SCALE = 0, 1, 2
+
+
 class fheon_boot_params(ctypes.Structure):
     """Bootstrapping: CoeffToSlot / SlotToCoeff levels, EvalMod's range K,
     series degree and double-angle steps, BSGS baby steps (0: fewest rotations)."""
@@ -133,6 +142,8 @@ SIGNATURES = {
     "fheon_layer_apply_graph": [c_vp, c_vp, c_vp, c_vp],
     "fheon_layer_apply_batch": [c_vp, c_vp, P(c_vp), c_u32, P(c_vp)],
     "fheon_model_create": [c_vp, P(c_vp), c_u32, c_vpp],
+    "fheon_model_create_program": [c_vp, P(fheon_step), c_u32, c_u32, c_dbl, c_vpp],
+    "fheon_model_run": [c_vp, c_vp, c_vp, c_vp],
     "fheon_model_destroy": [c_vp],
     "fheon_server_create": [c_vp, c_u32, c_sz, c_vpp],
     "fheon_server_destroy": [c_vp],
@@ -720,6 +731,23 @@ class Context:
         m = Handle(h, load().fheon_model_destroy)
         m.layers = list(layers)  # the layers outlive the model
         return m
+
+    def model_program(self, steps, nreg, scale):
+        """steps: (op, src, src2, dst, level, layer or None, c) tuples."""
+        n = len(steps)
+        arr = (fheon_step * n)()
+        for i, (op, a, b, d, lv, layer, c) in enumerate(steps):
+            arr[i] = fheon_step(op, a, b, d, lv, layer.h.value if layer is not None else None, float(c))
+        h = c_vp()
+        self._chk(load().fheon_model_create_program(self.h, arr, n, nreg, float(scale), ctypes.byref(h)))
+        m = Handle(h, load().fheon_model_destroy)
+        m.layers = [st[5] for st in steps if st[5] is not None]  # the layers outlive the model
+        return m
+
+    def model_run(self, model, ct, out=None):
+        out = out or self.ct_create(1)
+        self._chk(load().fheon_model_run(self.h, model.h, ct.h, out.h))
+        return out
 
     def server(self, max_active, min_free=0):
         h = c_vp()

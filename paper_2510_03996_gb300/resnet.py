@@ -252,6 +252,27 @@ class EncryptedResNet:
         self.plan.append(("layer", self._series_at(self.betas[r], lv), src, dst))
         return lv - F.cheb_depth(RELU_DEGREE)
 
+    def program(self):
+        """The plan as model-program steps (fheon_step tuples) over registers
+        x = 0, h = 1, s = 2, for fheon_model_create_program."""
+        R = {"x": 0, "h": 1, "s": 2}
+        F_ = F
+        out = []
+        for op in self.plan:
+            if op[0] == "layer":
+                out.append((F_.STEP_LAYER, R[op[2]], 0, R[op[3]], 0, op[1], 0.0))
+            elif op[0] == "scale":
+                out.append((F_.STEP_SCALE, R[op[2]], 0, R[op[3]], 0, None, op[1]))
+            elif op[0] == "add":
+                out.append((F_.STEP_ADD, R[op[2]], R[op[3]], R[op[4]], op[1], None, 0.0))
+            elif op[0] == "boot":
+                out.append((F_.STEP_LAYER, R[op[1]], 0, R[op[1]], 0, self.boot, 0.0))
+        return out
+
+    def model(self):
+        """The network as a native model (fheon_model_run, the server)."""
+        return self.ctx.model_program(self.program(), 3, self.scale)
+
     def rotation_steps(self):
         st = set()
         for layer in self.layers.values():

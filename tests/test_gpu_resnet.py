@@ -95,3 +95,29 @@ def test_mini_resnet_matches_fp64():
         assert gpu_common.mismatch(g.ct_download(yg), g.ct_download(y)) == 0
     g.sync()
     g.set_stream(torch.cuda.current_stream().cuda_stream)
+    # the network as a native model program, alone and through the server
+    # mixed with a second model (the first conv and ReLU as a chain)
+    model = net.model()
+    yn = g.model_run(model, ct)
+    assert gpu_common.mismatch(g.ct_download(yn), g.ct_download(y)) == 0
+    chain = g.model([net.layers["conv0"], net._series[(betas[0], net.in_level - 1)]])
+    ct2 = g.drop_level(g.encrypt(pr.pk, g.encode(R.pack_input(X * 0.5, pr.N // 2, MINI), pr.L, pr.P["scale"]),
+                                 nonce=0xD13), net.in_level)
+    want_chain = g.ct_download(g.model_run(chain, ct2))
+    srv = g.server(max_active=4)
+    ids = [(srv.submit(model, ct), "net"), (srv.submit(chain, ct2), "chain"), (srv.submit(model, ct), "net")]
+    res = {}
+    for _ in range(500):
+        srv.step()
+        for i, (rid, _) in enumerate(ids):
+            if i not in res:
+                r = srv.result(rid)
+                if r is not None:
+                    res[i] = g.ct_download(r)
+        if len(res) == len(ids):
+            break
+    assert len(res) == 3
+    for i, (_, kind) in enumerate(ids):
+        assert gpu_common.mismatch(res[i], want_chain if kind == "chain" else g.ct_download(y)) == 0
+    assert srv.stats()["max_batch"] >= 2
+    srv.close()
