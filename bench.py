@@ -358,6 +358,13 @@ def resnet_timing(F, n_inputs=2):
     e1.record(s)
     torch.cuda.synchronize()
     boot_ms = e0.elapsed_time(e1) / 5
+    # one bootstrap launch by launch (events on the context's stream): share of each kernel
+    ctx.profile_begin()
+    ctx.layer_apply(net.boot, z)
+    bprof = ctx.profile_end()
+    btot = sum(v[1] for v in bprof.values())
+    boot_kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / btot, 4)}
+                    for k, v in sorted(bprof.items(), key=lambda kv: -kv[1][1])[:12]}
     err, agree = 0.0, 0
     for X, y in zip(xs, outs):
         got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
@@ -369,6 +376,7 @@ def resnet_timing(F, n_inputs=2):
     release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
             "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": 18,
+            "bootstrap_kernels": boot_kernels,
             "inputs": n_inputs, "prepare_and_keygen_s": round(t_prep, 2), "keys": nkeys, "key_bytes": kbytes,
             "max_abs_logit_vs_fp64_exact_relu": err, "argmax_agrees": "%d/%d" % (agree, n_inputs),
             "levels": len(P["qbits"]), "paper_cpu_s_per_inference": 403}
