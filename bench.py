@@ -652,7 +652,8 @@ def run_gpu(args, rank, world, local_rank):
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
     comparisons = None
-    if not args.no_comparisons:
+    # single-GPU diagnostics beside the timed step: each replica would only repeat them
+    if not args.no_comparisons and world == 1:
         comparisons = {"per_ciphertext_path": per_ciphertext_rate(ctx, ins, outs, steps, stream),
                        "conv_n13_layer": conv_layer_timing(F),
                        "lenet5_n15": lenet_timing(F),

@@ -121,3 +121,36 @@ def test_mini_resnet_matches_fp64():
         assert gpu_common.mismatch(res[i], want_chain if kind == "chain" else g.ct_download(y)) == 0
     assert srv.stats()["max_batch"] >= 2
     srv.close()
+
+
+def test_program_and_repack_errors(small):
+    """Argument checks of model programs, the repack layer and series layers."""
+    pr = small
+    g, F = pr.g, pr.F
+    with pytest.raises(F.FheonError) as e:          # register out of range
+        g.model_program([(F.STEP_SCALE, 0, 0, 3, 0, None, 0.5)], 2, pr.P["scale"])
+    assert e.value.code == -1
+    with pytest.raises(F.FheonError) as e:          # an add at level 0
+        g.model_program([(F.STEP_ADD, 0, 1, 0, 0, None, 0.0)], 2, pr.P["scale"])
+    assert e.value.code == -1
+    with pytest.raises(F.FheonError) as e:          # a constant step without a model scale
+        g.model_program([(F.STEP_SCALE, 0, 0, 0, 0, None, 0.5)], 1, 0.0)
+    assert e.value.code == -1
+    with pytest.raises(F.FheonError) as e:          # maps of different shapes
+        g.repack_prepare((4, 4, 4, 8, 2, 64), (4, 4, 2, 4, 1, 64), pr.L)
+    assert e.value.code == -1
+    with pytest.raises(F.FheonError) as e:          # the target layout does not fit its blocks
+        g.repack_prepare((4, 4, 4, 8, 2, 64), (4, 4, 4, 4, 1, 8), pr.L)
+    assert e.value.code == -1
+    with pytest.raises(F.FheonError) as e:          # a series deeper than the level
+        g.cheb_prepare(np.ones(60), F.cheb_depth(59))
+    assert e.value.code == -4
+    # a program of one constant step: c * x, rescaled onto the scale
+    X = synth.image(0xD20, 0, SHAPE, dist="normal")
+    n = pr.N // 2
+    ct, _ = pr.encrypt_both(ckks.encode(OF.pack_map(X, n, *SRC), pr.N, pr.P["scale"]), nonce=0xD20)
+    m = g.model_program([(F.STEP_SCALE, 0, 0, 1, 0, None, -0.5), (F.STEP_ADD, 1, 1, 0, pr.L - 1, None, 0.0)],
+                        2, pr.P["scale"])
+    y = g.model_run(m, ct)
+    v = np.asarray(g.decode(g.decrypt(pr.sk, y))).real
+    assert np.max(np.abs(OF.unpack_map(v, SHAPE, *SRC) + X)) < 1e-6   # 2 * (-0.5 x)
