@@ -848,6 +848,18 @@ void drop_plans(fheon_ctx *ctx)
     plan_caches().erase(ctx);
 }
 
+// batch plans kept per context (least recently used goes first)
+constexpr size_t PLAN_CACHE = 128;
+// a plan is written to the device in chunks carried by the launch parameters
+struct PlanChunk {
+    static constexpr u32 BYTES = 4000;
+    unsigned char b[BYTES];
+};
+__global__ void plan_write_kernel(const __grid_constant__ PlanChunk c, unsigned char *dst, u32 n)
+{
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.b[i];
+}
+
 int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool hoist, PlanKeep *keep)
 {
     if (n == 0) return FHEON_OK;
@@ -968,10 +980,13 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool ho
                 off[s][k] = bytes;
                 bytes += t[s][k].size() * sizeof(u32);
             }
-        if (cache.size() >= 32) {
+        if (cache.size() >= PLAN_CACHE) {
             auto lru = std::min_element(cache.begin(), cache.end(),
                                         [](const RotPlan &a, const RotPlan &b) { return a.last_use < b.last_use; });
-            cudaStreamSynchronize(ctx->stream); // the plan may be in use by queued launches
+            // its memory goes back stream-ordered (the caching allocator reuses it
+            // only for later work on the same stream; cudaFree waits by itself),
+            // so queued launches still read it; another stream must wait first
+            if (lru->mem && lru->mem->st != ctx->stream) cudaStreamSynchronize(lru->mem->st);
             cache.erase(lru);
         }
         cache.emplace_back();
@@ -987,8 +1002,16 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool ho
         for (int s = 0; s < ST_COUNT; s++)
             for (int k = 0; k < 2; k++)
                 memcpy(host.data() + off[s][k], t[s][k].data(), t[s][k].size() * sizeof(u32));
-        FHEON_CUDA(ctx, cudaMemcpyAsync(plan->mem->p, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
-        FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream)); // `host` is released on return
+        // written by kernels whose parameters carry the bytes: the launch copies
+        // them, so neither a staging buffer nor a wait is needed
+        for (size_t o = 0; o < bytes; o += PlanChunk::BYTES) {
+            PlanChunk c;
+            const u32 nb = (u32)std::min<size_t>(PlanChunk::BYTES, bytes - o);
+            memcpy(c.b, host.data() + o, nb);
+            plan_write_kernel<<<1, 256, 0, ctx->stream>>>(c, plan->mem->as<unsigned char>() + o, nb);
+            prof_mark(ctx->stream, "plan_write");
+            FHEON_CUDA(ctx, cudaGetLastError());
+        }
         char *base = plan->mem->as<char>();
         plan->desc = reinterpret_cast<const RotDesc *>(base);
         for (int s = 0; s < ST_COUNT; s++)
