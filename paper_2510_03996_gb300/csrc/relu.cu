@@ -314,7 +314,9 @@ int fheon_relu_prepare(fheon_ctx *ctx, double beta, uint32_t degree, uint32_t n,
 
 int fheon_cheb_prepare(fheon_ctx *ctx, const double *coeffs, uint32_t degree, uint32_t level, fheon_layer **out)
 {
-    if (!ctx || !coeffs || !out || degree < 1 || degree > 1023 || level > ctx->L) return FHEON_ERR_ARG;
+    if (!ctx || !coeffs || !out) return FHEON_ERR_ARG;
+    if (degree < 1 || degree > 1023 || level > ctx->L)
+        return fail(ctx, FHEON_ERR_ARG, "series: degree in [1, 1023] and level <= L");
     if (level <= cheb_depth(degree))
         return fail(ctx, FHEON_ERR_LEVEL, "series: needs level > %u, got %u", cheb_depth(degree), level);
     std::unique_ptr<fheon_layer> ly(new fheon_layer());

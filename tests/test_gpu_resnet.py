@@ -142,9 +142,12 @@ def test_program_and_repack_errors(small):
     with pytest.raises(F.FheonError) as e:          # the target layout does not fit its blocks
         g.repack_prepare((4, 4, 4, 8, 2, 64), (4, 4, 4, 4, 1, 8), pr.L)
     assert e.value.code == -1
-    with pytest.raises(F.FheonError) as e:          # a series deeper than the level
-        g.cheb_prepare(np.ones(60), F.cheb_depth(59))
+    with pytest.raises(F.FheonError) as e:          # a series as deep as the level
+        g.cheb_prepare(np.ones(28), F.cheb_depth(27))
     assert e.value.code == -4
+    with pytest.raises(F.FheonError) as e:          # a level above the context's
+        g.cheb_prepare(np.ones(8), pr.L + 1)
+    assert e.value.code == -1 and "level" in str(e.value)
     # a program of one constant step: c * x, rescaled onto the scale
     X = synth.image(0xD20, 0, SHAPE, dist="normal")
     n = pr.N // 2
