@@ -535,8 +535,9 @@ int fheon_layer_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *
 /* The layer on n inputs at once (outputs distinct from every input and each
  * other): a rotation-sum layer runs every input's tap rotations as one
  * hoisted batch and every group shift as one batch, an FC layer the slot
- * sums of all neurons of all inputs together; conv2d and ReLU layers run per
- * input.  Each output equals the one fheon_layer_apply gives for its input
+ * sums of all neurons of all inputs together, a ReLU layer the products of
+ * every step of all inputs' series together; conv2d and bootstrap layers run
+ * per input.  Each output equals the one fheon_layer_apply gives for its input
  * alone, bit for bit. */
 int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *const *ins, uint32_t n,
                             fheon_ct *const *outs);

@@ -305,20 +305,21 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
     if ((rc = fheon_mul_int(ctx, x, -1, w[4]))) return rc;
     if ((rc = fheon_add(ctx, w[3], w[4], w[4]))) return rc;
     if ((rc = fheon_mul_plain(ctx, w[4], ly->mono[0], ly->cheb2[1]))) return rc;
-    fheon_ct *part[2];
+    // EvalMod on both parts in lockstep: every product of a step is one batch
     std::vector<fheon_ct *> *works[2] = {&ly->rot, &ly->cheb2};
-    for (int k = 0; k < 2; k++) {
-        fheon_ct *a = w[5 + 2 * k], *b = w[6 + 2 * k];
-        if ((rc = cheb_series(ctx, ly->coeffs, *works[k], a))) return rc;
-        for (u32 i = 0; i < ly->boot_r; i++) {
-            // 2 c^2 - 1: the doubled product rescaled, then -1 at the new scale
-            if ((rc = mul_relin_at(ctx, a, a, a->level, true, b))) return rc;
-            if ((rc = fheon_rescale(ctx, b, b))) return rc;
-            if ((rc = fheon_add_const(ctx, b, -1.0, b))) return rc;
-            std::swap(a, b);
+    fheon_ct *a[2] = {w[5], w[7]}, *b[2] = {w[6], w[8]};
+    if ((rc = cheb_series_many(ctx, ly->coeffs, works, 2, a, ly->collect))) return rc;
+    for (u32 i = 0; i < ly->boot_r; i++) {
+        // 2 c^2 - 1: the doubled product rescaled, then -1 at the new scale
+        RelinItem it[2] = {RelinItem{a[0], a[0], a[0]->level, true, b[0]}, RelinItem{a[1], a[1], a[1]->level, true, b[1]}};
+        if ((rc = mul_relin_many(ctx, it, 2, ly->collect))) return rc;
+        for (int k = 0; k < 2; k++) {
+            if ((rc = fheon_rescale(ctx, b[k], b[k]))) return rc;
+            if ((rc = fheon_add_const(ctx, b[k], -1.0, b[k]))) return rc;
+            std::swap(a[k], b[k]);
         }
-        part[k] = a;
     }
+    fheon_ct *part[2] = {a[0], a[1]};
     if ((rc = fheon_mul_plain(ctx, part[1], ly->mono[1], w[9]))) return rc;
     if ((rc = fheon_add(ctx, part[0], w[9], w[9]))) return rc;
     x = w[9];

@@ -189,6 +189,28 @@ void boot_release(const fheon_ctx *ctx); // release the one-shot bootstrap layer
 // for callers that capture them into a graph.
 using PlanKeep = std::vector<std::shared_ptr<void>>;
 int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool hoist = false, PlanKeep *keep = nullptr);
+// one key switch of a batch: input components c0, c1 (u64[level][N] each;
+// c1 is switched, c0 joins component 0 of the output), optional c1add joined
+// to component 1, output u64[2][level][N], key and Galois element (1: none);
+// lead = the item whose raised digits this one reads (itself when it raises)
+struct KsItem {
+    const u64 *c0 = nullptr, *c1 = nullptr, *c1add = nullptr;
+    u64 *out = nullptr;
+    const u64 *key = nullptr;
+    u64 g = 1;
+    u32 level = 0, lead = 0;
+};
+int ks_many(fheon_ctx *ctx, const KsItem *items, uint32_t n, bool hoist, PlanKeep *keep = nullptr);
+// ciphertext products with relinearisation as one batch: out = a * b (lowest
+// `level` limbs of each, doubled when `twice`), no rescale; outputs distinct
+// from every input
+struct RelinItem {
+    const fheon_ct *a = nullptr, *b = nullptr;
+    u32 level = 0;
+    bool twice = false;
+    fheon_ct *out = nullptr;
+};
+int mul_relin_many(fheon_ctx *ctx, const RelinItem *items, uint32_t n, PlanKeep *keep = nullptr);
 int rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uint32_t n, fheon_ct *const *outs,
                    PlanKeep *keep = nullptr);
 

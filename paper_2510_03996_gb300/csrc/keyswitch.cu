@@ -860,66 +860,42 @@ __global__ void plan_write_kernel(const __grid_constant__ PlanChunk c, unsigned 
     for (u32 i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.b[i];
 }
 
-int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool hoist, PlanKeep *keep)
+// workspace limbs of a key-switching batch: each item's own, less the raised
+// digits of the items that read their leader's
+static size_t ks_ws_total(const fheon_ctx *ctx, const KsItem *items, u32 n, std::vector<size_t> *off)
+{
+    size_t total = 0;
+    for (u32 i = 0; i < n; i++) {
+        const u32 l = items[i].level;
+        if (off) (*off)[i] = total;
+        total += ctx->ks_ws_limbs(l) - (items[i].lead == i ? 0 : l + (size_t)ctx->beta_at(l) * (l + ctx->K));
+    }
+    return total;
+}
+
+int ks_many(fheon_ctx *ctx, const KsItem *items, uint32_t n, bool hoist, PlanKeep *keep)
 {
     if (n == 0) return FHEON_OK;
-    if (n > 65535) {
-        // (an input whose rotations fall in two chunks is raised once per chunk)
-        for (u32 s = 0; s < n; s += 65535) {
-            int rc = rotate_many(ctx, items + s, std::min<u32>(65535, n - s), hoist, keep);
-            if (rc) return rc;
-        }
-        return FHEON_OK;
-    }
+    if (n > 65535) return fail(ctx, FHEON_ERR_ARG, "key-switching batch of %u items", n);
     const u32 N = ctx->N;
-    // validate, size outputs, lay out the workspace; lead[i] = the item whose
-    // raised digits item i reads (itself, unless it shares a hoisted input)
-    std::vector<u64> sig;
     std::vector<size_t> ws_off(n);
-    std::vector<u32> lead(n);
-    size_t ws_total = 0;
-    std::vector<const u64 *> keyp(n);
-    std::map<const fheon_ct *, u32> first;
-    for (u32 i = 0; i < n; i++) {
-        const fheon_ct *in = items[i].in;
-        fheon_ct *out = items[i].out;
-        if (!in || !out) return fail(ctx, FHEON_ERR_ARG, "null ciphertext in batch item %u", i);
-        const u64 g = fheon_galois_elt(ctx, items[i].step);
-        auto it = ctx->keys.find(g);
-        if (it == ctx->keys.end())
-            return fail(ctx, FHEON_ERR_NO_KEY, "no rotation key for step %d (batch item %u)", items[i].step, i);
-        keyp[i] = it->second.mem.as<u64>();
-        lead[i] = hoist ? first.emplace(in, i).first->second : i;
-        const u32 l = in->level;
-        ws_off[i] = ws_total;
-        ws_total += ctx->ks_ws_limbs(l) - (lead[i] == i ? 0 : l + (size_t)ctx->beta_at(l) * (l + ctx->K));
-    }
-    {
-        std::set<const fheon_ct *> ins, outs;
-        for (u32 i = 0; i < n; i++) ins.insert(items[i].in);
-        for (u32 i = 0; i < n; i++) {
-            if (ins.count(items[i].out)) return fail(ctx, FHEON_ERR_ARG, "batch output %u aliases an input", i);
-            if (!outs.insert(items[i].out).second) return fail(ctx, FHEON_ERR_ARG, "batch output %u repeated", i);
-        }
-    }
-    for (u32 i = 0; i < n; i++) {
-        int rc = ct_reshape(ctx, items[i].out, items[i].in->level);
-        if (rc) return rc;
-        items[i].out->scale = items[i].in->scale;
-    }
+    const size_t ws_total = ks_ws_total(ctx, items, n, &ws_off);
     int rc = ensure_workspace(ctx, std::max(ws_total, ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L));
     if (rc) return rc;
     u64 *ws = ctx->ws.as<u64>();
-    sig.reserve(5 * n + 3);
+    std::vector<u64> sig;
+    sig.reserve(7 * (size_t)n + 3);
     sig.push_back((u64)ws);
     sig.push_back(n);
     sig.push_back(hoist);
     for (u32 i = 0; i < n; i++) {
-        sig.push_back((u64)items[i].in->c.p ^ ((u64)items[i].in->level << 56));
-        sig.push_back((u64)items[i].out->c.p);
-        sig.push_back((u64)keyp[i]);
-        sig.push_back(fheon_galois_elt(ctx, items[i].step));
-        sig.push_back(lead[i]);
+        sig.push_back((u64)items[i].c0 ^ ((u64)items[i].level << 56));
+        sig.push_back((u64)items[i].c1);
+        sig.push_back((u64)items[i].c1add);
+        sig.push_back((u64)items[i].out);
+        sig.push_back((u64)items[i].key);
+        sig.push_back(items[i].g);
+        sig.push_back(items[i].lead);
     }
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto &cache = plan_cache(ctx);
@@ -935,21 +911,20 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool ho
         auto cls = [&](u32 midx) { return ctx->mod[midx] < ntt::LAZY_BOUND ? 1 : 0; };
         auto qp = [&](u32 x, u32 l) { return x < l ? x : L + (x - l); };
         for (u32 i = 0; i < n; i++) {
-            const fheon_ct *in = items[i].in;
-            const u32 l = in->level, beta = ctx->beta_at(l);
-            const u64 g = fheon_galois_elt(ctx, items[i].step);
+            const KsItem &it = items[i];
+            const u32 l = it.level, beta = ctx->beta_at(l);
+            const u64 g = it.g;
             u64 *w = ws + ws_off[i] * N;
-            if (lead[i] == i) {
+            if (it.lead == i) {
                 u64 *ext = w + (size_t)l * N;
-                desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], w, ext,
-                                  ext + (size_t)beta * (l + K) * N, g, hoist ? 1 : g, hoist ? g : 0, l, beta, nullptr};
+                desc[i] = RotDesc{it.c0, it.c1, it.out, it.key, w, ext, ext + (size_t)beta * (l + K) * N, g,
+                                  hoist ? 1 : g, hoist ? g : 0, l, beta, it.c1add};
             } else {
-                const RotDesc &ld = desc[lead[i]];
-                desc[i] = RotDesc{in->c0(), in->c1(N), items[i].out->c0(), keyp[i], ld.xt, ld.ext, w, g, 1, g, l, beta,
-                                  nullptr};
+                const RotDesc &ld = desc[it.lead];
+                desc[i] = RotDesc{it.c0, it.c1, it.out, it.key, ld.xt, ld.ext, w, g, 1, g, l, beta, it.c1add};
             }
             const u32 c = i << 16;
-            const bool raise = lead[i] == i;
+            const bool raise = it.lead == i;
             for (u32 x = 0; x < l && raise; x++) t[ST_IC][cls(x)].push_back(c | x);
             for (u32 j = 0; j < beta && raise; j++)
                 for (u32 x = 0; x < l + K; x++)
@@ -1025,6 +1000,101 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool ho
     BatchParams P = batch_params(ctx);
     P.desc = plan->desc;
     return run_pipeline(ctx, P, plan->lists, hoist);
+}
+
+
+int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool hoist, PlanKeep *keep)
+{
+    if (n == 0) return FHEON_OK;
+    if (n > 65535) {
+        // (an input whose rotations fall in two chunks is raised once per chunk)
+        for (u32 s = 0; s < n; s += 65535) {
+            int rc = rotate_many(ctx, items + s, std::min<u32>(65535, n - s), hoist, keep);
+            if (rc) return rc;
+        }
+        return FHEON_OK;
+    }
+    const u32 N = ctx->N;
+    // validate and size outputs; lead = the item whose raised digits an item
+    // reads (itself, unless it shares a hoisted input)
+    std::vector<KsItem> ks(n);
+    std::map<const fheon_ct *, u32> first;
+    for (u32 i = 0; i < n; i++) {
+        const fheon_ct *in = items[i].in;
+        fheon_ct *out = items[i].out;
+        if (!in || !out) return fail(ctx, FHEON_ERR_ARG, "null ciphertext in batch item %u", i);
+        const u64 g = fheon_galois_elt(ctx, items[i].step);
+        auto it = ctx->keys.find(g);
+        if (it == ctx->keys.end())
+            return fail(ctx, FHEON_ERR_NO_KEY, "no rotation key for step %d (batch item %u)", items[i].step, i);
+        ks[i].key = it->second.mem.as<u64>();
+        ks[i].g = g;
+        ks[i].level = in->level;
+        ks[i].lead = hoist ? first.emplace(in, i).first->second : i;
+    }
+    {
+        std::set<const fheon_ct *> ins, outs;
+        for (u32 i = 0; i < n; i++) ins.insert(items[i].in);
+        for (u32 i = 0; i < n; i++) {
+            if (ins.count(items[i].out)) return fail(ctx, FHEON_ERR_ARG, "batch output %u aliases an input", i);
+            if (!outs.insert(items[i].out).second) return fail(ctx, FHEON_ERR_ARG, "batch output %u repeated", i);
+        }
+    }
+    for (u32 i = 0; i < n; i++) {
+        int rc = ct_reshape(ctx, items[i].out, items[i].in->level);
+        if (rc) return rc;
+        items[i].out->scale = items[i].in->scale;
+        ks[i].c0 = items[i].in->c0();
+        ks[i].c1 = items[i].in->c1(N);
+        ks[i].c1add = nullptr;
+        ks[i].out = items[i].out->c0();
+    }
+    return ks_many(ctx, ks.data(), n, hoist, keep);
+}
+
+int mul_relin_many(fheon_ctx *ctx, const RelinItem *items, uint32_t n, PlanKeep *keep)
+{
+    if (n == 0) return FHEON_OK;
+    if (n == 1) return mul_relin_at(ctx, items[0].a, items[0].b, items[0].level, items[0].twice, items[0].out);
+    auto kit = ctx->keys.find(0);
+    if (kit == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "no relinearisation key");
+    const u32 N = ctx->N;
+    std::vector<KsItem> ks(n);
+    size_t tens = 0;
+    for (u32 i = 0; i < n; i++) {
+        const RelinItem &r = items[i];
+        if (!r.a || !r.b || !r.out || r.out == r.a || r.out == r.b)
+            return fail(ctx, FHEON_ERR_ARG, "product batch item %u: null or aliased ciphertext", i);
+        if (r.level < 1 || r.level > r.a->level || r.level > r.b->level)
+            return fail(ctx, FHEON_ERR_LEVEL, "product batch item %u: level %u", i, r.level);
+        for (u32 j = 0; j < i; j++)
+            if (items[j].out == r.out) return fail(ctx, FHEON_ERR_ARG, "product batch output %u repeated", i);
+        ks[i].level = r.level;
+        ks[i].lead = i;
+        tens += 3 * (size_t)r.level;
+    }
+    // the tensors sit past the batch's key-switching workspace
+    const size_t base = std::max(ks_ws_total(ctx, ks.data(), n, nullptr), ctx->ks_ws_limbs(ctx->L) + 2 * (size_t)ctx->L);
+    int rc = ensure_workspace(ctx, base + tens);
+    if (rc) return rc;
+    u64 *d = ctx->ws.as<u64>() + base * N;
+    for (u32 i = 0; i < n; i++) {
+        const RelinItem &r = items[i];
+        const u32 l = r.level;
+        const double sc = r.a->scale * r.b->scale;
+        FHEON_CUDA(ctx, k_tensor(ctx, r.a->c0(), r.a->c1(N), r.b->c0(), r.b->c1(N), d, l, r.twice));
+        if ((rc = ct_reshape(ctx, r.out, l))) return rc;
+        r.out->scale = sc;
+        // key-switch d2 from s^2 to s (g = 1); d0 joins component 0, d1 component 1
+        ks[i].c0 = d;
+        ks[i].c1 = d + (size_t)2 * l * N;
+        ks[i].c1add = d + (size_t)l * N;
+        ks[i].out = r.out->c0();
+        ks[i].key = kit->second.mem.as<u64>();
+        ks[i].g = 1;
+        d += (size_t)3 * l * N;
+    }
+    return ks_many(ctx, ks.data(), n, false, keep);
 }
 
 int rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uint32_t n, fheon_ct *const *outs,

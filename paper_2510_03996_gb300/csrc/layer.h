@@ -45,6 +45,7 @@ struct fheon_layer {
     u32 out_level = 0;
     fheon_pt *mono[2] = {nullptr, nullptr};
     mutable std::vector<fheon_ct *> cheb2; // the second part's series working set
+    mutable std::vector<std::vector<fheon_ct *>> sets; // ReLU on a batch: one working set per input
     // working ciphertexts (the k^2 - 1 tap rotations, then accumulators), made
     // on the first application and reused, so that later applications (and
     // their graph capture) allocate nothing
@@ -80,6 +81,8 @@ struct fheon_layer {
             for (fheon_layer *l : subs) delete l;
         for (fheon_pt *p : mono) fheon_pt_destroy(p);
         for (fheon_ct *c : cheb2) fheon_ct_destroy(c);
+        for (auto &v : sets)
+            for (fheon_ct *c : v) fheon_ct_destroy(c);
     }
 };
 
@@ -88,7 +91,12 @@ namespace fheon {
 // (cheb_work makes them); work[1] = T_1 on entry, at the series' input
 // scale; out = sum_d c_d T_d at that scale, cheb_depth(D) levels below
 int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, double scale);
-int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out);
+int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out,
+                PlanKeep *keep = nullptr);
+// the same series on n inputs in lockstep (works[p][1] = T_1 of part p), the
+// products of each step in one batch; each output is the one cheb_series gives
+int cheb_series_many(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> *const *works, u32 n,
+                     fheon_ct *const *outs, PlanKeep *keep = nullptr);
 u32 cheb_depth(u32 D);
 // slot diagonals of a linear map on n slots: out = sum_o d_o * Rot_o(in)
 using cd = std::complex<double>;
@@ -106,6 +114,8 @@ Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby);
 // plaintexts encoded at `pscale` and owned by the layer
 int diag_layer(fheon_ctx *ctx, const Diags &M, u32 stride, cd factor, u32 baby, u32 level, double pscale,
                fheon_layer **out);
+// the ReLU layer on n inputs, their series in lockstep (relu.cu)
+int relu_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs);
 // bootstrapping (boot.cu)
 int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out);
 } // namespace fheon

@@ -568,9 +568,7 @@ int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
             if ((rc = fheon_conv2d_apply(ctx, ly, ins[i], outs[i]))) return rc;
         return FHEON_OK;
     case LAYER_RELU:
-        for (u32 i = 0; i < n; i++)
-            if ((rc = fheon_relu_apply(ctx, ly, ins[i], outs[i]))) return rc;
-        return FHEON_OK;
+        return relu_apply_batch(ctx, ly, ins, n, outs);
     case LAYER_BOOT:
         for (u32 i = 0; i < n; i++)
             if ((rc = boot_apply(ctx, ly, ins[i], outs[i]))) return rc;

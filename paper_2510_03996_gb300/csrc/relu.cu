@@ -125,68 +125,86 @@ void cheb_split(const std::vector<double> &c, u32 g, std::vector<double> &q, std
     for (u32 j = 1; j + g <= deg; j++) r[g - j] = r[g - j] - c[g + j];
 }
 
+// the tree of one series over `n` parts in lockstep (the same coefficients
+// on n inputs): every product of a step goes to the device as one batch
 struct PsEval {
     fheon_ctx *ctx;
-    std::vector<fheon_ct *> &work;
-    u32 k, m, top;                    // top: next free working ciphertext
-    std::vector<fheon_ct *> T, G;     // babies [1..], giants [0..m-1]
+    std::vector<std::vector<fheon_ct *> *> works;
+    u32 n, k, m, top;                           // top: next free working ciphertext
+    std::vector<std::vector<fheon_ct *>> T, G;  // [part] babies [1..], giants [0..m-1]
+    PlanKeep *keep;
 
-    u32 leaf_level(u32 deg) const
+    u32 leaf_level(u32 p, u32 deg) const
     {
-        u32 lv = T[1]->level;
-        for (u32 i = 1; i <= std::max(deg, 1u); i++) lv = std::min(lv, T[i]->level);
+        u32 lv = T[p][1]->level;
+        for (u32 i = 1; i <= std::max(deg, 1u); i++) lv = std::min(lv, T[p][i]->level);
         return lv - 1;
     }
-    u32 out_level(u32 deg, u32 j) const
+    u32 out_level(u32 p, u32 deg, u32 j) const
     {
-        if (j == 0) return leaf_level(deg);
+        if (j == 0) return leaf_level(p, deg);
         const u32 g = k << (j - 1);
-        if (deg < g) return out_level(deg, j - 1);
-        return std::min(std::min(out_level(deg - g, j - 1), G[j - 1]->level) - 1, out_level(g - 1, j - 1));
+        if (deg < g) return out_level(p, deg, j - 1);
+        return std::min(std::min(out_level(p, deg - g, j - 1), G[p][j - 1]->level) - 1, out_level(p, g - 1, j - 1));
     }
-    // sum_i c_i T_i landing on scale St, into `out`
-    int ev(const std::vector<double> &c, u32 j, double St, fheon_ct *out)
+    // sum_i c_i T_i of every part, landing on scale St[p], into out[p]
+    int ev(const std::vector<double> &c, u32 j, const std::vector<double> &St, const std::vector<fheon_ct *> &out)
     {
         const u32 deg = (u32)c.size() - 1, N = ctx->N;
         int rc;
         if (j == 0) {
-            const u32 lv = leaf_level(deg) + 1, n = std::max(deg, 1u);
-            const double q = (double)ctx->mod[lv - 1];
-            std::vector<const u64 *> src(n);
-            std::vector<u64> stride(n);
-            std::vector<int64_t> K(n);
-            for (u32 i = 1; i <= n; i++) {
-                const double ci = i <= deg ? c[i] : 0.0;
-                if (!round_int(((ci * St) * q) / T[i]->scale, &K[i - 1]))
-                    return fail(ctx, FHEON_ERR_ARG, "chebyshev: coefficient factor out of range");
-                src[i - 1] = T[i]->c0();
-                stride[i - 1] = (u64)T[i]->level * N;
+            for (u32 p = 0; p < n; p++) {
+                const u32 lv = leaf_level(p, deg) + 1, nt = std::max(deg, 1u);
+                const double q = (double)ctx->mod[lv - 1];
+                std::vector<const u64 *> src(nt);
+                std::vector<u64> stride(nt);
+                std::vector<int64_t> K(nt);
+                for (u32 i = 1; i <= nt; i++) {
+                    const double ci = i <= deg ? c[i] : 0.0;
+                    if (!round_int(((ci * St[p]) * q) / T[p][i]->scale, &K[i - 1]))
+                        return fail(ctx, FHEON_ERR_ARG, "chebyshev: coefficient factor out of range");
+                    src[i - 1] = T[p][i]->c0();
+                    stride[i - 1] = (u64)T[p][i]->level * N;
+                }
+                if ((rc = ct_reshape(ctx, out[p], lv))) return rc;
+                FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), nt, out[p]->c0(), lv));
+                out[p]->scale = St[p] * q; // the sum's scale before the rescale (metadata)
+                if ((rc = fheon_rescale(ctx, out[p], out[p]))) return rc;
+                out[p]->scale = St[p];
+                if ((rc = fheon_add_const(ctx, out[p], c[0], out[p]))) return rc;
             }
-            if ((rc = ct_reshape(ctx, out, lv))) return rc;
-            FHEON_CUDA(ctx, k_lincomb(ctx, src.data(), stride.data(), K.data(), n, out->c0(), lv));
-            out->scale = St * q; // the sum's scale before the rescale (metadata)
-            if ((rc = fheon_rescale(ctx, out, out))) return rc;
-            out->scale = St;
-            return fheon_add_const(ctx, out, c[0], out);
+            return FHEON_OK;
         }
         const u32 g = k << (j - 1);
         if (deg < g) return ev(c, j - 1, St, out);
         std::vector<double> cq, cr;
         cheb_split(c, g, cq, cr);
-        const fheon_ct *Gc = G[j - 1];
-        const u32 lp = std::min(out_level((u32)cq.size() - 1, j - 1), Gc->level);
-        if (top + 2 > work.size()) return fail(ctx, FHEON_ERR_ARG, "chebyshev: working set exhausted");
-        fheon_ct *tq = work[top], *tr = work[top + 1];
+        if (top + 2 > works[0]->size()) return fail(ctx, FHEON_ERR_ARG, "chebyshev: working set exhausted");
+        std::vector<fheon_ct *> tq(n), tr(n);
+        std::vector<double> Sq(n);
+        std::vector<u32> lp(n);
+        for (u32 p = 0; p < n; p++) {
+            tq[p] = (*works[p])[top];
+            tr[p] = (*works[p])[top + 1];
+            lp[p] = std::min(out_level(p, (u32)cq.size() - 1, j - 1), G[p][j - 1]->level);
+            Sq[p] = (St[p] * (double)ctx->mod[lp[p] - 1]) / G[p][j - 1]->scale;
+        }
         top += 2;
-        if ((rc = ev(cq, j - 1, (St * (double)ctx->mod[lp - 1]) / Gc->scale, tq))) return rc;
-        if ((rc = mul_relin_at(ctx, tq, Gc, lp, false, out))) return rc;
-        if ((rc = fheon_rescale(ctx, out, out))) return rc;
-        out->scale = St;
+        if ((rc = ev(cq, j - 1, Sq, tq))) return rc;
+        std::vector<RelinItem> items(n);
+        for (u32 p = 0; p < n; p++) items[p] = RelinItem{tq[p], G[p][j - 1], lp[p], false, out[p]};
+        if ((rc = mul_relin_many(ctx, items.data(), n, keep))) return rc;
+        for (u32 p = 0; p < n; p++) {
+            if ((rc = fheon_rescale(ctx, out[p], out[p]))) return rc;
+            out[p]->scale = St[p];
+        }
         if ((rc = ev(cr, j - 1, St, tr))) return rc;
-        const u32 lo = std::min(out->level, tr->level);
-        if (tr->level > lo && (rc = fheon_drop_level(ctx, tr, lo, tr))) return rc;
-        if (out->level > lo && (rc = fheon_drop_level(ctx, out, lo, out))) return rc;
-        if ((rc = fheon_add(ctx, tr, out, out))) return rc;
+        for (u32 p = 0; p < n; p++) {
+            const u32 lo = std::min(out[p]->level, tr[p]->level);
+            if (tr[p]->level > lo && (rc = fheon_drop_level(ctx, tr[p], lo, tr[p]))) return rc;
+            if (out[p]->level > lo && (rc = fheon_drop_level(ctx, out[p], lo, out[p]))) return rc;
+            if ((rc = fheon_add(ctx, tr[p], out[p], out[p]))) return rc;
+        }
         top -= 2;
         return FHEON_OK;
     }
@@ -214,45 +232,97 @@ int cheb_work(fheon_ctx *ctx, std::vector<fheon_ct *> &work, u32 D, u32 level, d
     return FHEON_OK;
 }
 
-int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out)
+int cheb_series_many(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> *const *works, u32 n,
+                     fheon_ct *const *outs, PlanKeep *keep)
 {
     const u32 D = (u32)coeffs.size() - 1, N = ctx->N;
     u32 k, m;
     ps_params(D, k, m);
     const u32 kb = std::min(k, D);
-    fheon_ct **T = work.data();
-    fheon_ct *t1 = work[kb + m + 1];
     int rc;
+    std::vector<RelinItem> items(n);
     // babies: operands at a higher level are read in place (their lowest
     // limbs), and the factor 2 of 2 T_a T_b is applied inside the tensor
     for (u32 d = 2; d <= kb; d++) {
         const u32 h = d / 2;
-        fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
-        const u32 lv = A->level < B->level ? A->level : B->level;
-        if ((rc = mul_relin_at(ctx, A, B, lv, true, T[d]))) return rc; // scale S = s_a s_b
-        if (d % 2 == 1) {
-            // - T_1 at scale S joins the product before the shared rescale
-            int64_t K;
-            if (!round_int((-1.0 * T[d]->scale) / T[1]->scale, &K)) return fail(ctx, FHEON_ERR_ARG, "chebyshev: constant");
-            if ((rc = ct_reshape(ctx, t1, lv))) return rc;
-            FHEON_CUDA(ctx, k_mul_int(ctx, T[1]->c0(), K, t1->c0(), lv, 2, (u64)T[1]->level * N));
-            FHEON_CUDA(ctx, k_add(ctx, T[d]->c0(), t1->c0(), T[d]->c0(), lv, 2));
+        for (u32 p = 0; p < n; p++) {
+            fheon_ct **T = works[p]->data();
+            fheon_ct *A = T[d - h], *B = T[h]; // d even: T_h, T_h; odd: T_h+1, T_h
+            items[p] = RelinItem{A, B, std::min(A->level, B->level), true, T[d]}; // scale S = s_a s_b
         }
-        if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
-        if (d % 2 == 0 && (rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
+        if ((rc = mul_relin_many(ctx, items.data(), n, keep))) return rc;
+        for (u32 p = 0; p < n; p++) {
+            fheon_ct **T = works[p]->data();
+            const u32 lv = items[p].level;
+            if (d % 2 == 1) {
+                // - T_1 at scale S joins the product before the shared rescale
+                fheon_ct *t1 = (*works[p])[kb + m + 1];
+                int64_t K;
+                if (!round_int((-1.0 * T[d]->scale) / T[1]->scale, &K))
+                    return fail(ctx, FHEON_ERR_ARG, "chebyshev: constant");
+                if ((rc = ct_reshape(ctx, t1, lv))) return rc;
+                FHEON_CUDA(ctx, k_mul_int(ctx, T[1]->c0(), K, t1->c0(), lv, 2, (u64)T[1]->level * N));
+                FHEON_CUDA(ctx, k_add(ctx, T[d]->c0(), t1->c0(), T[d]->c0(), lv, 2));
+            }
+            if ((rc = fheon_rescale(ctx, T[d], T[d]))) return rc;
+            if (d % 2 == 0 && (rc = fheon_add_const(ctx, T[d], -1.0, T[d]))) return rc;
+        }
     }
     // giants: G_0 = T_k, G_j = 2 G_j-1^2 - 1
-    PsEval E{ctx, work, k, m, kb + m + 2, {}, {}};
-    E.T.assign(T, T + kb + 1);
-    if (m) E.G.push_back(T[k]);
-    for (u32 j = 1; j < m; j++) {
-        fheon_ct *A = E.G.back(), *Gj = work[kb + j];
-        if ((rc = mul_relin_at(ctx, A, A, A->level, true, Gj))) return rc;
-        if ((rc = fheon_rescale(ctx, Gj, Gj))) return rc;
-        if ((rc = fheon_add_const(ctx, Gj, -1.0, Gj))) return rc;
-        E.G.push_back(Gj);
+    PsEval E{ctx, std::vector<std::vector<fheon_ct *> *>(works, works + n), n, k, m, kb + m + 2, {}, {}, keep};
+    E.T.resize(n);
+    E.G.resize(n);
+    for (u32 p = 0; p < n; p++) {
+        E.T[p].assign(works[p]->begin(), works[p]->begin() + kb + 1);
+        if (m) E.G[p].push_back((*works[p])[k]);
     }
-    return E.ev(coeffs, m, T[1]->scale, out);
+    for (u32 j = 1; j < m; j++) {
+        for (u32 p = 0; p < n; p++) {
+            fheon_ct *A = E.G[p].back();
+            items[p] = RelinItem{A, A, A->level, true, (*works[p])[kb + j]};
+        }
+        if ((rc = mul_relin_many(ctx, items.data(), n, keep))) return rc;
+        for (u32 p = 0; p < n; p++) {
+            fheon_ct *Gj = (*works[p])[kb + j];
+            if ((rc = fheon_rescale(ctx, Gj, Gj))) return rc;
+            if ((rc = fheon_add_const(ctx, Gj, -1.0, Gj))) return rc;
+            E.G[p].push_back(Gj);
+        }
+    }
+    std::vector<double> St(n);
+    for (u32 p = 0; p < n; p++) St[p] = (*works[p])[1]->scale;
+    return E.ev(coeffs, m, St, std::vector<fheon_ct *>(outs, outs + n));
+}
+
+int cheb_series(fheon_ctx *ctx, const std::vector<double> &coeffs, std::vector<fheon_ct *> &work, fheon_ct *out,
+                PlanKeep *keep)
+{
+    std::vector<fheon_ct *> *w = &work;
+    return cheb_series_many(ctx, coeffs, &w, 1, &out, keep);
+}
+
+int relu_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs)
+{
+    if (n == 1) return fheon_relu_apply(ctx, ly, ins[0], outs[0]);
+    const u32 D = ly->degree;
+    int rc;
+    if (ly->sets.size() < n) ly->sets.resize(n);
+    std::vector<std::vector<fheon_ct *> *> works(n);
+    for (u32 p = 0; p < n; p++) {
+        const fheon_ct *in = ins[p];
+        if (in->level != ly->level) return fail(ctx, FHEON_ERR_LEVEL, "relu expects level %u, got %u", ly->level, in->level);
+        if ((rc = cheb_work(ctx, ly->sets[p], D, ly->level, in->scale))) return rc;
+        fheon_ct *T1 = ly->sets[p][1];
+        if (ly->beta > 1.0) {
+            if ((rc = fheon_mul_plain(ctx, in, ly->mask, T1))) return rc;
+            if ((rc = fheon_rescale(ctx, T1, T1))) return rc;
+            T1->scale = in->scale;
+        } else if ((rc = fheon_drop_level(ctx, in, in->level, T1))) {
+            return rc;
+        }
+        works[p] = &ly->sets[p];
+    }
+    return cheb_series_many(ctx, ly->coeffs, works.data(), n, outs, ly->collect);
 }
 
 } // namespace fheon
@@ -347,7 +417,7 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, 
     } else if ((rc = fheon_drop_level(ctx, in, in->level, T1))) {
         return rc;
     }
-    return cheb_series(ctx, ly->coeffs, ly->rot, out);
+    return cheb_series(ctx, ly->coeffs, ly->rot, out, ly->collect);
 }
 
 int fheon_relu_approx(fheon_ctx *ctx, const fheon_ct *ct, double beta, uint32_t degree, uint32_t n, fheon_ct *out)
