@@ -654,7 +654,12 @@ def run_gpu(args, rank, world, local_rank):
     comparisons = None
     # single-GPU diagnostics beside the timed step: each replica would only repeat them
     if not args.no_comparisons and world == 1:
-        comparisons = {"per_ciphertext_path": per_ciphertext_rate(ctx, ins, outs, steps, stream),
+        per_ct = per_ciphertext_rate(ctx, ins, outs, steps, stream)
+        # the rotation workload's keys and batches are done with: hand their memory
+        # back before the other workloads build their own contexts
+        del ins, outs, bufs, host_in, host_out
+        release(ctx)
+        comparisons = {"per_ciphertext_path": per_ct,
                        "conv_n13_layer": conv_layer_timing(F),
                        "lenet5_n15": lenet_timing(F),
                        "resnet20_n16": resnet_timing(F),
