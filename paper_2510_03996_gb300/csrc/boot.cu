@@ -33,6 +33,7 @@
 #include <complex>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <set>
 #include <vector>
 
@@ -173,6 +174,7 @@ struct DefaultBoot {
     fheon_layer *ly = nullptr;
 };
 std::map<const fheon_ctx *, DefaultBoot> g_default;
+std::mutex g_default_mu;
 
 } // namespace
 
@@ -511,6 +513,7 @@ int fheon_mod_raise(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out)
 int fheon_bootstrap(fheon_ctx *ctx, const fheon_ct *ct, fheon_ct *out)
 {
     if (!ctx || !ct || !out) return FHEON_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_default_mu);
     DefaultBoot &d = g_default[ctx];
     if (!d.ly || std::fabs(d.scale - ct->scale) > 1e-9 * ct->scale) {
         if (d.ly) {
@@ -534,6 +537,7 @@ namespace fheon {
 // the one-shot call's cached layer of a context that is going away
 void boot_release(const fheon_ctx *ctx)
 {
+    std::lock_guard<std::mutex> lk(g_default_mu);
     auto it = g_default.find(ctx);
     if (it == g_default.end()) return;
     delete it->second.ly;

@@ -1067,8 +1067,13 @@ int mul_relin_many(fheon_ctx *ctx, const RelinItem *items, uint32_t n, PlanKeep 
             return fail(ctx, FHEON_ERR_ARG, "product batch item %u: null or aliased ciphertext", i);
         if (r.level < 1 || r.level > r.a->level || r.level > r.b->level)
             return fail(ctx, FHEON_ERR_LEVEL, "product batch item %u: level %u", i, r.level);
-        for (u32 j = 0; j < i; j++)
-            if (items[j].out == r.out) return fail(ctx, FHEON_ERR_ARG, "product batch output %u repeated", i);
+        // an output is resized before later items' operands are read: it may
+        // be no item's operand, nor another item's output
+        for (u32 j = 0; j < n; j++) {
+            if (items[j].a == r.out || items[j].b == r.out)
+                return fail(ctx, FHEON_ERR_ARG, "product batch output %u is an operand of item %u", i, j);
+            if (j < i && items[j].out == r.out) return fail(ctx, FHEON_ERR_ARG, "product batch output %u repeated", i);
+        }
         ks[i].level = r.level;
         ks[i].lead = i;
         tens += 3 * (size_t)r.level;
