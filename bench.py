@@ -313,8 +313,8 @@ def lenet_timing(F, batch=32):
 
 
 def resnet_timing(F, n_inputs=2):
-    """ResNet-20 encrypted inference with bootstrapping (N = 2^16, 32 primes:
-    q_0, 10 levels of layers, 21 of bootstrapping) on synthetic 3x32x32 N(0,1)
+    """ResNet-20 encrypted inference with bootstrapping (N = 2^16, 37 primes:
+    q_0, 16 levels of layers, 20 of bootstrapping) on synthetic 3x32x32 N(0,1)
     inputs with random-init weights: seconds per inference (CUDA events around
     the inputs, one after another), one bootstrap alone, and the decrypted
     logits against the FP64 network with exact ReLUs."""
@@ -372,10 +372,11 @@ def resnet_timing(F, n_inputs=2):
         err = max(err, float(np.max(np.abs(got - want))))
         agree += int(np.argmax(got) == np.argmax(want))
     nkeys, kbytes = ctx.key_stats()
+    n_boot = net.n_boot
     del outs, gouts, cts, net, sk, pk
     release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
-            "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": 18,
+            "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": n_boot,
             "bootstrap_kernels": boot_kernels,
             "inputs": n_inputs, "prepare_and_keygen_s": round(t_prep, 2), "keys": nkeys, "key_bytes": kbytes,
             "max_abs_logit_vs_fp64_exact_relu": err, "argmax_agrees": "%d/%d" % (agree, n_inputs),

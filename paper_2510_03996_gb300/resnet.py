@@ -197,10 +197,15 @@ class EncryptedResNet:
         m = mp["input"]
         conv, m = self._conv("conv0", m, lv, betas[r])
         self.plan.append(("layer", conv, "x", "h"))
-        lv = self._relu(r, lv - 1, "h", "x")
+        lv = self._relu(r, lv - 1, "h", "x", after=1)
         r += 1
-        for s, b, ci, co, st in blocks(self.arch):
+        bl = blocks(self.arch)
+        for bi, (s, b, ci, co, st) in enumerate(bl):
             name = "s%db%d" % (s, b)
+            # levels between this block's last ReLU and the next ReLU's input:
+            # the next conv (and the two repacks before stage 3), or pooling and FC
+            nxt = bl[bi + 1] if bi + 1 < len(bl) else None
+            after_last = 2 if nxt is None else (3 if (nxt[0] == 2 and nxt[1] == 0) else 1)
             if s == 2 and b == 0:
                 # compact stage 2's map: rows/columns within the blocks, then the blocks
                 rp1 = ctx.repack_prepare(m, mp["s1_rows"], lv)
@@ -212,7 +217,7 @@ class EncryptedResNet:
             x_level, x_map = lv, m
             conv, ma = self._conv(name + "_a", m, lv, betas[r], stride=st)
             self.plan.append(("layer", conv, "x", "h"))
-            lv = self._relu(r, lv - 1, "h", "h")
+            lv = self._relu(r, lv - 1, "h", "h", after=1)
             r += 1
             conv, mb = self._conv(name + "_b", ma, lv, betas[r])
             self.plan.append(("layer", conv, "h", "h"))
@@ -225,7 +230,7 @@ class EncryptedResNet:
                 self.plan.append(("scale", 1.0 / betas[r], "x", "s"))
             lv = min(lv, x_level - 1)
             self.plan.append(("add", lv, "h", "s", "h"))
-            lv = self._relu(r, lv, "h", "x")
+            lv = self._relu(r, lv, "h", "x", after=after_last)
             r += 1
             m = mb
         # global average pooling and FC
@@ -241,16 +246,18 @@ class EncryptedResNet:
         self.out_level = lv
         assert r == len(betas) == n_relus(self.arch)
 
-    def _relu(self, r, lv, src, dst):
+    def _relu(self, r, lv, src, dst, after):
         """The r-th ReLU of register src (at level lv, already scaled by
-        1/beta_r) into register dst, bootstrapped first from the second on;
-        returns the level after it."""
-        if r >= 1:
+        1/beta_r) into register dst; bootstrapped first when the levels left
+        would not carry the series and the `after` levels up to the next
+        ReLU's input with one level to spare.  Returns the level after it."""
+        depth = F.cheb_depth(RELU_DEGREE)
+        if lv - depth - after < 1:
             self.plan.append(("boot", src))
             self.n_boot += 1
             lv = self.B
         self.plan.append(("layer", self._series_at(self.betas[r], lv), src, dst))
-        return lv - F.cheb_depth(RELU_DEGREE)
+        return lv - depth
 
     def program(self):
         """The plan as model-program steps (fheon_step tuples) over registers

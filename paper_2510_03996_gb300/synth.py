@@ -40,10 +40,11 @@ def params(name):
         # EvalMod (degree-27 series in 5 levels + 7 doublings) 12 x 60 bits, CoeffToSlot 3 x 60 bits; P 6 x 60 bits
         return dict(logN=12, qbits=[52] + [40] * 2 + [50] * 3 + [60] * 15, pbits=[60] * 6, dnum=4,
                     scale=2.0 ** 40, seed=SEED_BASE + 10)
-    if name == "resnet_n16":  # ResNet-20 with bootstrapping: q_0 (2^12 above the scale), 10 levels of layers
-        # between bootstraps, SlotToCoeff 3 x 50 bits, EvalMod (degree-27 series in 5 levels + 9 doublings)
-        # 14 x 60 bits, CoeffToSlot 3 x 60 bits; P 8 x 60 bits above the largest digit (8 x 60 bits)
-        return dict(logN=16, qbits=[52] + [40] * 10 + [50] * 3 + [60] * 17, pbits=[60] * 8, dnum=4,
+    if name == "resnet_n16":  # ResNet-20 with bootstrapping: q_0 (2^12 above the scale), 16 levels of layers
+        # (two ReLUs and their convolutions between bootstraps), SlotToCoeff 3 x 50 bits, EvalMod (degree-27
+        # series in 5 levels + 9 doublings) 14 x 60 bits, CoeffToSlot 3 x 60 bits; P 10 x 60 bits, the size
+        # of the largest digit (10 x 60 bits)
+        return dict(logN=16, qbits=[52] + [40] * 16 + [50] * 3 + [60] * 17, pbits=[60] * 10, dnum=4,
                     scale=2.0 ** 40, seed=SEED_BASE + 3)
     if name == "resnet_n12":  # test-sized ResNet with bootstrapping: as resnet_n16 with 7 doublings
         return dict(logN=12, qbits=[52] + [40] * 10 + [50] * 3 + [60] * 15, pbits=[60] * 8, dnum=4,

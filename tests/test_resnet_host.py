@@ -94,3 +94,14 @@ def test_level_plan_full_size():
     assert [c[0] for c in net.ctx.calls].count("repack") == 2
     kinds = [op[0] for op in net.plan]
     assert kinds.count("boot") == 18 and kinds.count("add") == 9
+
+
+def test_bootstraps_only_where_levels_run_out():
+    """With 17 levels after a bootstrap, two ReLUs and their convolutions fit
+    between bootstraps: 9 instead of 18, and every layer still at level >= 2."""
+    class Deep(FakeCtx):
+        def bootstrap_info(self, layer):
+            return 17, 2.0 ** 40
+    net = R.EncryptedResNet(Deep(), R.weights(0xC3, R.FULL), [2.0] * R.n_relus(R.FULL), 2.0 ** 40)
+    assert net.n_boot == 9 and net.out_level >= 1
+    assert min(c[1] for c in net.ctx.calls) >= 2
