@@ -157,3 +157,175 @@ def test_program_and_repack_errors(small):
     y = g.model_run(m, ct)
     v = np.asarray(g.decode(g.decrypt(pr.sk, y))).real
     assert np.max(np.abs(OF.unpack_map(v, SHAPE, *SRC) + X)) < 1e-6   # 2 * (-0.5 x)
+
+
+def test_mini_resnet_bit_exact_against_the_oracle():
+    """The reduced network end to end, every layer from the oracle's plans and
+    integer plaintexts on both sides (the library through its plain-plaintext
+    layers, the oracle through its own operations), bootstraps placed by the
+    same rule: the same output ciphertext to the bit."""
+    from oracle import boot as B
+    pr = gpu_common.Pair("resnet_n12")
+    g, o = pr.g, pr.o
+    N, n, D = pr.N, pr.N // 2, pr.P["scale"]
+    q = [int(x) for x in g.moduli]
+    w = R.weights(0xD30, MINI)
+    betas = R.relu_bounds([synth.image(0xD31, i, (3, 8, 8), dist="normal") for i in range(3)], w, MINI)
+    plan = B.Plan(o, D)
+    Bl = plan.out_level
+    depth = OF.cheb_depth(R.RELU_DEGREE)
+    steps = set(plan.steps())
+    ops = []
+
+    def shared(v, lv, scale):
+        m = ckks.encode(v, N, scale)
+        return g.plain_from_coeffs(m, lv, scale), o.plain_from_coeffs(m, lv)
+
+    def linear(r, groups, lv, bias=None, fold=()):
+        gp, op = [], []
+        for _, vals in groups:
+            row = [None if v is None else shared(v, lv, float(q[lv - 1])) for v in vals]
+            gp.append([x and x[0] for x in row])
+            op.append([x and x[1] for x in row])
+        gb, ob = shared(bias, lv - 1, D) if bias is not None else (None, None)
+        layer = g.linear_prepare_plain(r, [G for G, _ in groups], gp, lv, bias=gb, fold=fold)
+        layer.keep = (gp, gb)
+        steps.update(OF.linear_steps(r, groups))
+        steps.update(f for f in fold if f)
+        ops.append(("linear", layer, (r, groups, op, ob, list(fold))))
+
+    def conv(name, m, lv, beta, stride=1, pad=1):
+        K, b = w[name]
+        C, H, W_, grid, dil, block = m
+        F_, _, k, _ = K.shape
+        r, groups = OF.conv_plan(C, F_, k, pad, H, W_, grid, dil, block, n, K / beta, stride=stride)
+        Ho, Wo = (H + 2 * pad - k) // stride + 1, (W_ + 2 * pad - k) // stride + 1
+        om = (F_, Ho, Wo, grid, dil * stride, block)
+        bias = np.zeros(n)
+        for f in range(F_):
+            bias[OF.map_slots(1, Ho, Wo, grid, dil * stride, block) + f * block] = b[f] / beta
+        linear(r, groups, lv, bias)
+        return om
+
+    def relu(i, lv, after):
+        if lv - depth - after < 1:
+            ops.append(("boot",))
+            lv = Bl
+        ops.append(("series", OF.relu_cheb_coeffs(betas[i], R.RELU_DEGREE), lv))
+        return lv - depth
+
+    mp = R.maps(MINI)
+    lv, r_i = Bl, 0
+    m = conv("conv0", mp["input"], lv, betas[0])
+    ops.append(("mov", "h", "x"))
+    lv = relu(0, lv - 1, 1)
+    r_i = 1
+    bl = R.blocks(MINI)
+    for bi, (s, b, ci, co, st) in enumerate(bl):
+        name = "s%db%d" % (s, b)
+        nxt = bl[bi + 1] if bi + 1 < len(bl) else None
+        after_last = 2 if nxt is None else (3 if (nxt[0] == 2 and nxt[1] == 0) else 1)
+        if s == 2 and b == 0:
+            for src, dst in ((m, mp["s1_rows"]), (mp["s1_rows"], mp["s1_packed"])):
+                rr, gg = OF.repack_plan(*src[:3], src[3:], dst[3:], n)
+                linear(rr, gg, lv)
+                lv -= 1
+            m = mp["s1_packed"]
+        x_level, x_map = lv, m
+        ops.append(("save_x",))
+        ma = conv(name + "_a", m, lv, betas[r_i], stride=st)
+        lv = relu(r_i, lv - 1, 1)
+        r_i += 1
+        mb = conv(name + "_b", ma, lv, betas[r_i])
+        lv -= 1
+        if st == 2:
+            ops.append(("shortcut_conv",))
+            conv(name + "_sc", x_map, x_level, betas[r_i], stride=2, pad=0)
+        else:
+            ops.append(("shortcut_scale", 1.0 / betas[r_i]))
+        lv = min(lv, x_level - 1)
+        ops.append(("add", lv))
+        lv = relu(r_i, lv, after_last)
+        r_i += 1
+        m = mb
+    C, H, W_, grid, dil, block = m
+    rr, gg = OF.avgpool_plan(C, H, H, H, W_, grid, dil, block, n)
+    linear(rr, gg, lv)
+    lv -= 1
+    pm = (C, 1, 1, grid, dil * H, block)
+    Wf, bf = w["fc"]
+    fold, rr, gg = OF.fc_diag_plan(Wf, *pm, n)
+    fb = np.zeros(n)
+    fb[:len(bf)] = bf
+    linear(rr, gg, lv, fb, fold)
+    # keys and the bootstrap (composed from the oracle plan's integers)
+    pr.add_keys(sorted(steps))
+    conj = 2 * N - 1
+    g.galois_keygen(pr.sk, [conj])
+    oconj = o.rotkey(pr.s_eval, conj)
+    g.relinkeygen(pr.sk)
+    orlk = o.relinkey(pr.s_eval)
+    okeys = {st: pr.okeys[g.galois_elt(st)] for st in steps}
+    bl_layers, bpts = [], []
+    for rr_, groups, ps, blv in plan.cts + plan.stc:
+        gp, op = [], []
+        for _, vals in groups:
+            row = [None if v is None else shared(v, blv, ps) for v in vals]
+            gp.append([x and x[0] for x in row])
+            op.append([x and x[1] for x in row])
+        layer = g.linear_prepare_plain(rr_, [G for G, _ in groups], gp, blv)
+        layer.keep = gp
+        bl_layers.append(layer)
+        bpts.append(op)
+    prm = pr.F.fheon_boot_params(len(plan.cts), len(plan.stc), plan.K, plan.D, plan.r, 0)
+    boot = g.bootstrap_compose(prm, bl_layers[:len(plan.cts)], bl_layers[len(plan.cts):], plan.coeffs, D)
+    # run both sides
+    X = synth.image(0xD32, 0, (3, 8, 8), dist="normal")
+    ct, oct_ = pr.encrypt_both(ckks.encode(R.pack_input(X, n, MINI), N, D), nonce=0xD32, level=Bl)
+    G, O = {"x": ct}, {"x": oct_}
+    cur = "x"
+    for op in ops:
+        kind = op[0]
+        if kind == "linear":
+            layer, (rr_, groups, opts, ob, fold) = op[1], op[2]
+            G["h"] = g.layer_apply(layer, G[cur])
+            y = OF.fold_encrypted(o, O[cur], fold, okeys)
+            y = OF.linear_encrypted(o, y, rr_, groups, opts, okeys)
+            O["h"] = o.add_plain(y, ob) if ob is not None else y
+            cur = "h"
+        elif kind == "series":
+            _, coeffs, slv = op
+            sc = g.ct_info(G[cur])[1]
+            lay = g.cheb_prepare(coeffs, slv)
+            G["h"] = g.layer_apply(lay, G[cur])
+            O["h"] = OF.cheb_encrypted(o, O[cur], sc, coeffs, orlk)
+            cur = "h"
+        elif kind == "boot":
+            G[cur] = g.layer_apply(boot, G[cur])
+            O[cur], _ = B.bootstrap_encrypted(o, O[cur], plan, bpts, okeys, orlk, oconj)
+        elif kind == "mov":
+            G[op[2]], O[op[2]] = G[op[1]], O[op[1]]
+        elif kind == "save_x":
+            G["x"], O["x"] = G[cur], O[cur]
+            cur = "x"
+        elif kind == "shortcut_scale":
+            sc = g.ct_info(G["x"])[1]
+            G["s"] = g.mul_const_rescale(G["x"], op[1], D)
+            O["s"] = o.mul_const_rescale(O["x"], op[1], D, sc)
+            G["main"], O["main"] = G[cur], O[cur]
+        elif kind == "shortcut_conv":
+            G["main"], O["main"] = G[cur], O[cur]
+            cur = "x"   # the next linear op is the shortcut conv on the block input
+        elif kind == "add":
+            lv_ = op[1]
+            if cur == "h" and "main" in G and G["main"] is not G["h"]:
+                G["s"], O["s"] = G["h"], O["h"]      # the shortcut conv's output
+            a_g, a_o = G["main"], O["main"]
+            G["h"] = g.add(g.drop_level(a_g, lv_), g.drop_level(G["s"], lv_))
+            O["h"] = o.add(o.drop_level(a_o, lv_), o.drop_level(O["s"], lv_))
+            G.pop("main")
+            cur = "h"
+    assert gpu_common.mismatch(g.ct_download(G[cur]), O[cur]) == 0
+    logits = np.asarray(g.decode(g.decrypt(pr.sk, G[cur]))).real[:MINI["classes"]]
+    want = OF.resnet_fp64(X, w, MINI["chans"], MINI["blocks"], betas=betas)
+    assert np.max(np.abs(logits - want)) < 1e-2 * max(1.0, np.max(np.abs(want)))
