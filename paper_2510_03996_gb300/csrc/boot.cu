@@ -157,8 +157,8 @@ int check_params(fheon_ctx *ctx, const fheon_boot_params *p)
     return FHEON_OK;
 }
 
-// the scale the series starts on and the one SlotToCoeff starts on, in the
-// order the operations compute them
+// the scale after EvalMod's r doublings (the series keeps its input scale s),
+// computed in the order the operations compute it
 double evalmod_end_scale(fheon_ctx *ctx, double s, u32 lv, u32 r)
 {
     for (u32 i = 0; i < r; i++) {
