@@ -49,13 +49,6 @@ void relu_cheb(double beta, u32 D, std::vector<double> &c)
     c[0] *= 0.5;
 }
 
-u32 ceil_log2(u32 x)
-{
-    u32 r = 0;
-    while ((1u << r) < x) r++;
-    return r;
-}
-
 // levels the ReLU consumes
 u32 relu_depth(double beta, u32 D) { return fheon::cheb_depth(D) + (beta > 1.0 ? 1 : 0); }
 
