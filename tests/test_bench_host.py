@@ -1,0 +1,51 @@
+"""Host logic of bench.py: the algorithmic bytes of a rotation against the
+closed form B(l) = 8N [2 ceil(l/alpha)(l+K) + 4l] (key read once, ciphertext
+in and out), the roofline arithmetic, and the all-cores oracle timing
+(spawned processes) on a small parameter set."""
+import math
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+from paper_2510_03996_gb300 import synth  # noqa: E402
+
+
+@pytest.mark.parametrize("level", [4, 9, 16, 24])
+def test_rotation_bytes_closed_form(level):
+    N, L, K, alpha = 1 << 16, 24, 4, 4
+    c = bench.algorithmic_costs(N, L, K, alpha, level)
+    assert c["bytes"] == 8 * N * (2 * math.ceil(level / alpha) * (level + K) + 4 * level)
+    # the inner product reads every key limb once, every raised digit once, writes two accumulators
+    beta = math.ceil(level / alpha)
+    ip = c["kernels"]["ks_inner"]["bytes"]
+    assert ip == 8 * N * (2 * beta * (level + K) + beta * (level + K) + 2 * (level + K))
+    # ModUp: new limbs = digits x (level + K) minus the digits' own limbs
+    new = beta * (level + K) - level
+    assert c["kernels"]["up_ntt_rows"]["mm"] == new * (N // 2) * 8
+
+
+def test_the_published_mean_bytes():
+    """The mean over U{4..24} of B(l) at the rotation workload's sizes is 111.6 MB."""
+    N = 1 << 16
+    mean = sum(bench.algorithmic_costs(N, 24, 4, 4, lv)["bytes"] for lv in range(4, 25)) / 21
+    assert abs(mean / 1e6 - 111.6) < 0.6
+
+
+def test_roofline_arithmetic():
+    costs = [bench.algorithmic_costs(1 << 16, 24, 4, 4, 12)]
+    prof = {"ks_inner": (2, 1.0), "up_ntt_rows": (2, 2.0), "unknown": (1, 1.0)}
+    r = bench.rooflines(prof, costs, steps=2, hbm_peak=6784.5, mm_peak=2.0)
+    ip = costs[0]["kernels"]["ks_inner"]["bytes"] * 2 / 1e-3 / 1e9
+    assert abs(r["ks_inner"]["achieved"] - ip) < 1e-6 and r["ks_inner"]["bound"] == "hbm"
+    assert abs(r["ks_inner"]["frac"] - ip / 6784.5) < 1e-12
+    assert r["up_ntt_rows"]["bound"] == "alu" and r["up_ntt_rows"]["avg_launch_ms"] == 1.0
+    assert "unknown" not in r
+
+
+def test_oracle_on_every_core():
+    P = synth.params("tiny")
+    rate, done, slowest, cores = bench.oracle_all_cores(P, 3, [2, 3, 4], per_core=2, cores=2)
+    assert cores == 2 and done == 4 and slowest > 0 and rate == pytest.approx(done / slowest)
