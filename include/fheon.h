@@ -2,13 +2,13 @@
  * fheon.h -- C ABI of the GB300 (sm_103a) RNS-CKKS rotation library behind
  * FHEON's encrypted CNN layers (arxiv 2510.03996).
  *
- * FHEON (paper Sec. 5, "Support Functions") exposes context generation,
+ * FHEON (paper Sec. 5.7, "Support Functions") exposes context generation,
  * key generation and key management, an encryption layer, the secure CNN
- * layers of Sec. 4 and bootstrapping on top of RNS-CKKS (Sec. 2.2).  This
+ * layers of Sec. 5 and bootstrapping on top of RNS-CKKS (Sec. 3.2).  This
  * library is the GPU arithmetic under those calls: the homomorphic rotation
  * (Galois automorphism + hybrid key switching) and the plaintext-multiply,
  * add and rescale steps around it, plus the packed special convolution of
- * Sec. 4.3.
+ * Sec. 5.3.
  *
  * Conventions shared by every call
  *  - Every call returns int: FHEON_OK (0) or a negative FHEON_ERR_* code;
@@ -91,7 +91,7 @@ typedef void (*fheon_free_fn)(void *ptr, size_t bytes, void *stream, void *user)
 int fheon_set_allocator(fheon_alloc_fn alloc, fheon_free_fn free_fn, void *user);
 
 /* ------------------------------------------------------------------ */
-/* Context (paper Sec. 5, context generation)                         */
+/* Context (paper Sec. 5.7, context generation)                         */
 /* ------------------------------------------------------------------ */
 /* Create a context for ring degree N with ciphertext moduli q[0..nq) and
  * special moduli p[0..np), hybrid key switching with `dnum` digits
@@ -142,7 +142,7 @@ int fheon_autotune_schedule(fheon_ctx *ctx, const struct fheon_rot_item *items, 
 int fheon_sync(fheon_ctx *ctx);
 
 /* ------------------------------------------------------------------ */
-/* Keys (paper Sec. 5, key generation and evaluation-key management)  */
+/* Keys (paper Sec. 5.7, key generation and evaluation-key management)  */
 /* ------------------------------------------------------------------ */
 /* Secret key s (ternary, stream (seed, 1, 0)) and public key
  * (b, a) = (-a*s + e, a) over Q_L; a uniform in the evaluation domain
@@ -157,7 +157,7 @@ int fheon_sk_download(fheon_ctx *ctx, const fheon_sk *sk, uint64_t *host);
 int fheon_pk_download(fheon_ctx *ctx, const fheon_pk *pk, uint64_t *host);
 
 /* Rotation keys for slot rotations steps[0..n) (Galois elements 5^r mod 2N;
- * paper Sec. 5: the rotation indices each layer needs).  A key for g is
+ * paper Sec. 5.7: the rotation indices each layer needs).  A key for g is
  * beta digits of (b_j, a_j) over Q_L u P with
  *   b_j = -a_j*s + e_j + [limb in digit j] * P * sigma_g(s),
  * a_j uniform (stream (seed, 4, g<<32 | j<<16 | limb)), e_j Gaussian
@@ -170,7 +170,7 @@ int fheon_rotkeygen(fheon_ctx *ctx, const fheon_sk *sk, const int32_t *steps, ui
 int fheon_relinkeygen(fheon_ctx *ctx, const fheon_sk *sk);
 /* Same, by Galois element (odd g < 2N; 2N-1 is complex conjugation). */
 int fheon_galois_keygen(fheon_ctx *ctx, const fheon_sk *sk, const uint64_t *galois, uint32_t n);
-/* Drop the key of Galois element g (paper Sec. 5: keys loaded and cleared
+/* Drop the key of Galois element g (paper Sec. 5.7: keys loaded and cleared
  * per block); FHEON_ERR_NO_KEY if absent. */
 int fheon_key_erase(fheon_ctx *ctx, uint64_t galois);
 /* Number of resident rotation keys and their device bytes. */
@@ -182,7 +182,7 @@ int fheon_key_download(fheon_ctx *ctx, uint64_t galois, uint64_t *host);
 uint64_t fheon_galois_elt(const fheon_ctx *ctx, int32_t r);
 
 /* ------------------------------------------------------------------ */
-/* Plaintexts (paper Sec. 2.2, encoding C^{N/2} -> R)                 */
+/* Plaintexts (paper Sec. 3.2, encoding C^{N/2} -> R)                 */
 /* ------------------------------------------------------------------ */
 /* Encode n <= N/2 complex slots (re, im; im may be NULL) at `scale` into a
  * plaintext over Q_level: coefficients m_k = round(scale * tau^-1(z)_k)
@@ -207,7 +207,7 @@ int fheon_pt_download(fheon_ctx *ctx, const fheon_pt *pt, uint64_t *host);
 int fheon_pt_destroy(fheon_pt *pt);
 
 /* ------------------------------------------------------------------ */
-/* Ciphertexts (paper Sec. 5, encryption layer)                       */
+/* Ciphertexts (paper Sec. 5.7, encryption layer)                       */
 /* ------------------------------------------------------------------ */
 /* Public-key encryption of pt (must be at level L):
  * ct = (v*b + e0 + m, v*a + e1), v ternary, e0, e1 Gaussian, drawn from
@@ -252,7 +252,7 @@ int fheon_ct_device_ptr(const fheon_ct *ct, void **dptr);
 /* ------------------------------------------------------------------ */
 /* Homomorphic evaluation                                             */
 /* ------------------------------------------------------------------ */
-/* Rotation by `step` slots (paper Sec. 2.2 rotation; Alg. 1 Rot_k):
+/* Rotation by `step` slots (paper Sec. 3.2 rotation; Alg. 1 Rot_k):
  *   (c0, c1) -> (sigma_g(c0), sigma_g(c1)) in the evaluation domain, then
  *   hybrid key switching of sigma_g(c1) from sigma_g(s) to s: INTT, ModUp
  *   of each digit by fast base conversion, NTT, inner product with the
@@ -297,7 +297,7 @@ typedef struct fheon_rot_item {
  * Outputs must be distinct from every input of the batch. */
 int fheon_rotate_batch(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
 /* Hoisted rotations, the "fast rotations" the paper's CKKS library provides
- * (Sec. 2.2; Halevi-Shoup hoisting in the hybrid key-switching form):
+ * (Sec. 3.2; Halevi-Shoup hoisting in the hybrid key-switching form):
  * outs[i] = Rot_{steps[i]}(in) for i < n, with one INTT + ModUp + NTT of c1
  * shared by all n.  Rotation i applies sigma_g to the raised digits in the
  * evaluation domain (a gather inside the key inner product), takes the inner
@@ -312,11 +312,11 @@ int fheon_rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *step
  * one raising (results as fheon_rotate_hoisted per input). */
 int fheon_rotate_batch_hoisted(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n);
 
-/* out = ct * pt slot-wise (paper Sec. 4.1, kernel-vector products); levels
+/* out = ct * pt slot-wise (paper Sec. 5.1, kernel-vector products); levels
  * must match (the plaintext may be at a higher level: its lowest limbs are
  * used); scale(out) = scale(ct) * scale(pt). */
 int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheon_ct *out);
-/* out = sum_t cts[t] * pts[t] slot-wise (paper Sec. 4.1: the kernel-vector
+/* out = sum_t cts[t] * pts[t] slot-wise (paper Sec. 5.1: the kernel-vector
  * products of a layer and their sum, in one pass): n >= 1 ciphertexts at one
  * level, plaintexts at that level or above, every product at the same scale
  * (1e-9 relative; else FHEON_ERR_SCALE); out is distinct from every input
@@ -325,7 +325,7 @@ int fheon_mul_plain(fheon_ctx *ctx, const fheon_ct *ct, const fheon_pt *pt, fheo
 int fheon_mac_plain(fheon_ctx *ctx, const fheon_ct *const *cts, const fheon_pt *const *pts, uint32_t n,
                     fheon_ct *out);
 /* Ciphertext product with relinearisation (the multiplications of the
- * Chebyshev ReLU, paper Alg. 4 and Sec. 4.6): the tensor (a0 b0, a0 b1 + a1 b0,
+ * Chebyshev ReLU, paper Alg. 4 and Sec. 5.6): the tensor (a0 b0, a0 b1 + a1 b0,
  * a1 b1) decrypts under (1, s, s^2); its last part is key-switched from s^2 to
  * s on the rotation's key-switching kernels with the relinearisation key.
  * Equal levels (else FHEON_ERR_LEVEL); FHEON_ERR_NO_KEY without
@@ -358,16 +358,16 @@ int fheon_rescale(fheon_ctx *ctx, const fheon_ct *in, fheon_ct *out);
 int fheon_drop_level(fheon_ctx *ctx, const fheon_ct *in, uint32_t level, fheon_ct *out);
 
 /* ------------------------------------------------------------------ */
-/* Secure layers (paper Sec. 4)                                       */
+/* Secure layers (paper Sec. 5)                                       */
 /* ------------------------------------------------------------------ */
 /* Rotation steps a special ("same", stride 1) k x k convolution on a
  * W-wide input needs: di*W + dj for every non-zero tap (di, dj) in
  * [-(k-1)/2, (k-1)/2]^2, plus H*W for channel summation when in_ch > 1
- * (paper Sec. 4.3 and Sec. 5 rotation-index analysis).  Writes at most
+ * (paper Sec. 5.3 and Sec. 5.7 rotation-index analysis).  Writes at most
  * *n entries, sets *n to the count. */
 int fheon_conv2d_rotation_steps(uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w, int32_t *out,
                                 uint32_t *n);
-/* Prepare a special convolution (paper Sec. 4.3, Alg. 1-3 generalised to
+/* Prepare a special convolution (paper Sec. 5.3, Alg. 1-3 generalised to
  * odd k): one output channel per layer call, in_ch input channels packed
  * at slot c*H*W + h*W + w, weights w[in_ch][k][k], optional bias.  The
  * tap vectors (weight x boundary mask of Alg. 2/3) are encoded at scale
@@ -400,7 +400,7 @@ int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k,
 int fheon_layer_destroy(fheon_layer *layer);
 
 /* ------------------------------------------------------------------ */
-/* Packed network layers on a fheon_map (paper Sec. 4.1, 4.4, 4.5)     */
+/* Packed network layers on a fheon_map (paper Sec. 5.1, 4.4, 4.5)     */
 /* ------------------------------------------------------------------ */
 /* Rotation-sum layer from the caller's plaintexts:
  *   x'  = sum_c Rot_{fold[c]}(in)   (nf > 0; the nf rotations hoisted from in)
@@ -415,7 +415,7 @@ int fheon_layer_destroy(fheon_layer *layer);
 int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nf, const int32_t *fold, uint32_t nt, const int32_t *r,
                                uint32_t ng, const int32_t *s, const fheon_pt *const *pts, const fheon_pt *bias,
                                uint32_t level, fheon_layer **out);
-/* Fully connected layer from the caller's plaintexts (Sec. 4.5): t_k =
+/* Fully connected layer from the caller's plaintexts (Sec. 5.5): t_k =
  * rescale(in * W[k]) for each of the m neurons; each t_k summed over all N/2
  * slots by rotate-and-add (steps 1, 2, ..., N/4, batched over the neurons);
  * out = rescale(sum_k t_k * E[k]) (+ bias, level >= level-2).  W at `level`
@@ -423,7 +423,7 @@ int fheon_linear_prepare_plain(fheon_ctx *ctx, uint32_t nf, const int32_t *fold,
  * level - 2.  Caller-owned plaintexts. */
 int fheon_fc_prepare_plain(fheon_ctx *ctx, uint32_t m, const fheon_pt *const *W, const fheon_pt *const *E,
                            const fheon_pt *bias, uint32_t level, fheon_layer **out);
-/* Convolution (Sec. 4.1 and Sec. 4.2 equations; zero padding `pad`, stride
+/* Convolution (Sec. 5.1 and Sec. 5.2 equations; zero padding `pad`, stride
  * `stride`) of the map `in` to F output channels, kernel K[F][C][k][k],
  * bias[F] (or NULL): a rotation-sum layer with one group per block shift
  * f - c.  Output (i, j) stays at input-grid position (stride*i, stride*j):
@@ -433,12 +433,12 @@ int fheon_fc_prepare_plain(fheon_ctx *ctx, uint32_t m, const fheon_pt *const *W,
  * layer.  Output level: level - 1, scale in_scale. */
 int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t k, uint32_t stride, uint32_t pad,
                        const double *K, const double *bias, uint32_t level, double in_scale, fheon_layer **out);
-/* Average pooling (Sec. 4.4): the k x k window sum by k^2 hoisted rotations
+/* Average pooling (Sec. 5.4): the k x k window sum by k^2 hoisted rotations
  * times one mask of 1/k^2 at the stride-aligned outputs.  The outputs stay in
  * place: the output map's dilation is the input's times `stride`. */
 int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint32_t stride, uint32_t level,
                           fheon_layer **out);
-/* Fully connected layer (Sec. 4.5 equation): W[m][C*H*W] over the map's
+/* Fully connected layer (Sec. 5.5 equation): W[m][C*H*W] over the map's
  * values in (c, i, j) order, bias[m] (or NULL); output: the m neurons in slots
  * [0, m) (map {1, 1, m, m, 1, m}).  A rotation-sum layer in diagonal form:
  * when the channels interleave on the dilation grid (C <= dil^2) they are
@@ -448,7 +448,7 @@ int fheon_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t k, uint3
 int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const double *W, const double *bias,
                      uint32_t level, double in_scale, fheon_layer **out);
 /* Repack a feature map into another layout of the same (C, H, W) in one
- * level (the paper's striding by extraction, Sec. 4.2: the values a strided
+ * level (the paper's striding by extraction, Sec. 5.2: the values a strided
  * layer leaves at dilated positions gathered into a compact grid): out =
  * sum_o m_o Rot_o(in), with m_o one at every destination slot whose source is
  * o slots further on, as baby-step/giant-step rotation sums; masks at scale
@@ -457,14 +457,14 @@ int fheon_fc_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t m, const doub
  * into steps). */
 int fheon_repack_prepare(fheon_ctx *ctx, const fheon_map *in, const fheon_map *out, uint32_t level,
                          fheon_layer **layer);
-/* Global average pooling (Sec. 4.4, used by ResNet): the mean over each
+/* Global average pooling (Sec. 5.4, used by ResNet): the mean over each
  * channel's whole H x H map, as average pooling with k = stride = H (one
  * value per channel, at the channel's first slot). */
 int fheon_global_avgpool_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t level, fheon_layer **out);
 /* One-shot layers at ct's level and scale (prepare, apply, release). */
 int fheon_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t k, uint32_t stride, fheon_ct *out);
 int fheon_global_avgpool(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, fheon_ct *out);
-/* Fully connected layer with the paper's key budget (Sec. 4.5, the number of
+/* Fully connected layer with the paper's key budget (Sec. 5.5, the number of
  * rotation keys the system keeps): the diagonal form of fheon_fc_prepare when
  * its rotation steps number at most max_keys (0: no limit), else the paper's
  * form (one product per neuron, the slot sum by rotate-and-add with log2(N/2)
@@ -605,7 +605,7 @@ int fheon_server_stats(const fheon_server *server, uint64_t *steps, uint32_t *ma
                        uint32_t *waiting);
 
 /* ------------------------------------------------------------------ */
-/* Secure ReLU (paper Sec. 4.6, Alg. 4)                               */
+/* Secure ReLU (paper Sec. 5.6, Alg. 4)                               */
 /* ------------------------------------------------------------------ */
 /* Chebyshev coefficients c_0..c_degree of f(z) = beta * max(0, z) on [-1, 1],
  * interpolated at the degree+1 Chebyshev nodes cos(pi (k + 1/2) / (degree+1))

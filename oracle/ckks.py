@@ -7,7 +7,7 @@ with the CUDA library.
 Arrays are numpy: polynomials ``uint64[n_limbs][N]`` (limb-major), ciphertexts
 ``uint64[2][level][N]`` in the evaluation domain, keys over all L+K moduli.
 The arithmetic lives in ckks_oracle.c; this module adds only marshalling and
-the exact big-integer CRT used by decoding (paper Sec. 2.2 decoding of the
+the exact big-integer CRT used by decoding (paper Sec. 3.2 decoding of the
 canonical embedding, with the centred lift modulo Q_level).
 """
 import numpy as np

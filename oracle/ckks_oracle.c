@@ -9,7 +9,7 @@
  * followed by the C `%` operator.
  *
  * What it follows.  FHEON delegates all of CKKS to OpenFHE's RNS-CKKS (paper
- * Sec. 2.2, "Cheon-Kim-Kim-Song (CKKS) Scheme") and names the full-RNS variant
+ * Sec. 3.2, "Cheon-Kim-Kim-Song (CKKS) Scheme") and names the full-RNS variant
  * of Cheon, Han, Kim, Kim and Song (SAC 2018) and hybrid key switching with
  * "4 digits" (Sec. 6, parameter paragraph).  The paper gives none of the
  * internals; the steps below are the textbook ones:
@@ -17,7 +17,7 @@
  *     output index j holding a(psi^(2*brv(j)+1)); Cooley-Tukey forward and
  *     Gentleman-Sande inverse butterflies (Longa-Naehrig 2016) for speed at
  *     large N, the O(N^2) definition beside them;
- *   - fast base conversion (Cheon et al. SAC 2018, Sec. 2.2), no correction;
+ *   - fast base conversion (Cheon et al. SAC 2018, Sec. 3.2), no correction;
  *   - hybrid key switching (Han-Ki, CT-RSA 2020): digit decomposition,
  *     ModUp, inner product with the key, ModDown;
  *   - floor rescale by the last prime;
@@ -759,7 +759,7 @@ void oracle_add_int(const oracle_ctx *c, const u64 *ct, u32 level, i64 v, u64 *o
     }
 }
 
-/* Chebyshev interpolant of f(z) = beta * max(0, z) on [-1, 1] (paper Sec. 4.6
+/* Chebyshev interpolant of f(z) = beta * max(0, z) on [-1, 1] (paper Sec. 5.6
  * and Alg. 4: the input is scaled by 1/beta first, f is evaluated by a
  * degree-D Chebyshev series), at the D+1 Chebyshev nodes
  * z_k = cos(theta_k), theta_k = pi (k + 1/2) / (D + 1):
@@ -910,7 +910,7 @@ void oracle_rescale(const oracle_ctx *c, const u64 *ct, u32 level, u64 *out)
 }
 
 /* ------------------------------------------------------------------ */
-/* Canonical embedding (paper Sec. 2.2: C^{N/2} <-> R).                */
+/* Canonical embedding (paper Sec. 3.2: C^{N/2} <-> R).                */
 /* slot i <-> evaluation at zeta^(5^i mod 2N), zeta = exp(i*pi/N).     */
 /* ------------------------------------------------------------------ */
 

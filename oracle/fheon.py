@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this module.
 
-Slot conventions (paper Sec. 4.1, input flattening): a (C, H, W) tensor sits
+Slot conventions (paper Sec. 5.1, input flattening): a (C, H, W) tensor sits
 at slot c*H*W + h*W + w.  Rot_r moves slot i+r to slot i (r > 0 rotates left),
 which is the reading under which the nine masks of Algorithm 3 match the
 rotations of Algorithm 1.
@@ -17,7 +17,7 @@ from . import ckks
 
 # ------------------------------------------------------------- FP64 CNN
 def conv2d_fp64(X, K, b=None, stride=1, pad=0):
-    """Convolution as the paper's Sec. 4.1 equation states it (cross-correlation:
+    """Convolution as the paper's Sec. 5.1 equation states it (cross-correlation:
     Y[f,h,w] = sum_c sum_i sum_j X[c, h*s+i, w*s+j] K[f,c,i,j] + b_f) on the
     zero-padded input; output size (H + 2p - k)/s + 1 per side."""
     X = np.asarray(X, dtype=np.float64)
@@ -40,7 +40,7 @@ def conv2d_fp64(X, K, b=None, stride=1, pad=0):
 
 
 def avgpool_fp64(X, k, stride):
-    """Average pooling, paper Sec. 4.4 equation: mean over each k x k window."""
+    """Average pooling, paper Sec. 5.4 equation: mean over each k x k window."""
     C, H, W = X.shape
     Ho, Wo = (H - k) // stride + 1, (W - k) // stride + 1
     Y = np.zeros((C, Ho, Wo))
@@ -104,7 +104,7 @@ def rot_slots(x, r):
 def special_conv_slots(x, H, W, C, K, k):
     """Slot-level special convolution ('same', stride 1, pad (k-1)/2), one output
     channel: sum over taps of mask_t * kernel value * Rot_{di*W+dj}(x), then the
-    channel sum by Rot_{H*W} repeated C-1 times (Sec. 4.3), channel block 0 kept."""
+    channel sum by Rot_{H*W} repeated C-1 times (Sec. 5.3), channel block 0 kept."""
     n = len(x)
     acc = np.zeros(n)
     for (di, dj) in taps(k):
@@ -142,11 +142,11 @@ def conv_rotation_steps(W, k):
 
 
 def special_conv_encrypted(ctx, ct, rotkeys, H, W, k, tap_plains, bias_plain=None, hoisted=False):
-    """Encrypted special conv of one channel (C = 1), FHEON Sec. 4.3 generalised to
+    """Encrypted special conv of one channel (C = 1), FHEON Sec. 5.3 generalised to
     k x k: r_t = Rot_{di*W+dj}(ct) with a direct key per tap, products with the
     tap plaintexts (encoded at scale q_{level-1}), summed, one rescale, bias added.
     hoisted: the tap rotations share one raising of c1 (the fast rotations of
-    Sec. 2.2), as ctx.rotate_hoisted computes them.
+    Sec. 3.2), as ctx.rotate_hoisted computes them.
 
     rotkeys: dict step -> key-switching key; tap_plains: list of evaluation-form
     plaintexts over Q_level in taps(k) order."""
@@ -181,7 +181,7 @@ def encode_tap_plains(ctx, H, W, K, k, level):
             for v in tap_vectors(n, H, W, C, K, k)]
 
 
-# ------------------------------------------------------------------ ReLU (Sec. 4.6, Alg. 4)
+# ------------------------------------------------------------------ ReLU (Sec. 5.6, Alg. 4)
 RELU_DEGREE = 59  # the paper's default D
 
 
@@ -405,7 +405,7 @@ def unpack_map(v, shape, grid, dil, block):
 
 
 def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K, stride=1):
-    """Rotation-sum plan of a convolution (Sec. 4.1 equation, zero padding
+    """Rotation-sum plan of a convolution (Sec. 5.1 equation, zero padding
     `pad`, stride `stride`) from C to F channels: tap t = (x, y) reads the input
     at offset (x - pad, y - pad), i.e. Rot_{r_t} with r_t = dil*((x-pad)*grid +
     (y-pad)); group delta = f - c collects, in the block of input channel c, the
@@ -438,7 +438,7 @@ def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K, stride=1):
 
 
 def avgpool_plan(C, k, stride, H, W, grid, dil, block, nslots):
-    """Average pooling (Sec. 4.4): the window sum by the rotations
+    """Average pooling (Sec. 5.4): the window sum by the rotations
     r_t = dil*(x*grid + y), x, y < k, times one mask holding 1/k^2 at the
     stride-aligned outputs (the striding is the mask: the outputs stay in
     place, at spacing dil*stride).  Returns (r, [(0, [mask] * k^2)])."""
@@ -453,7 +453,7 @@ def avgpool_plan(C, k, stride, H, W, grid, dil, block, nslots):
 
 
 def fc_plan(Wmat, in_slots, nslots):
-    """Fully connected layer (Sec. 4.5 equation): neuron k's weight vector at
+    """Fully connected layer (Sec. 5.5 equation): neuron k's weight vector at
     the input's slots (product, then the sum of all slots), and the one-hot
     vector that places the sum in slot k.  Returns ([W_k], [E_k])."""
     Wmat = np.asarray(Wmat, dtype=np.float64)
@@ -538,7 +538,7 @@ def fc_encrypted(ctx, ct, wpts, epts, keys):
 
 
 def lenet_fp64(X, w, betas=None, D=RELU_DEGREE):
-    """LeNet-5 (paper Sec. 7 architecture) in FP64 from the plain layers; with
+    """LeNet-5 (paper's Appendix A architecture) in FP64 from the plain layers; with
     `betas`, each ReLU is the Chebyshev series of Alg. 4 with that bound."""
     def act(v, i):
         return np.maximum(v, 0.0) if betas is None else relu_fp64(v, betas[i], D)
@@ -568,7 +568,7 @@ def fold_offsets(C, H, W, grid, dil, block):
 
 
 def fc_diag_plan(Wmat, C, H, W, grid, dil, block, nslots):
-    """Fully connected layer (Sec. 4.5 equation) in diagonal form.
+    """Fully connected layer (Sec. 5.5 equation) in diagonal form.
     Fold (when fold_offsets allows it): x' = sum_c Rot_{f_c}(x),
     f_c = c*block - off_c, brings channel c's values (zero elsewhere) to
     off_c + dil*(i*grid + j) in block 0.  Then y[k] = sum_d diag_d[k] x'[k + d] with
@@ -686,7 +686,7 @@ def plan_slots(v, r, groups):
 
 def repack_plan(C, H, W, src, dst, nslots):
     """A (C, H, W) map moved from layout src = (grid, dil, block) to layout
-    dst in one level (striding by extraction, Sec. 4.2): out = sum_o m_o
+    dst in one level (striding by extraction, Sec. 5.2): out = sum_o m_o
     Rot_o(in), m_o one at every destination slot whose source is o slots
     further on; in BSGS form over the largest power-of-two stride dividing
     every shift.  Returns (r, groups) in the rotation-sum conventions."""
@@ -704,7 +704,7 @@ def repack_plan(C, H, W, src, dst, nslots):
 
 
 def resnet_fp64(X, w, chans, nblocks, betas=None, D=RELU_DEGREE):
-    """ResNet-20-style network (paper Sec. 7 architecture) in FP64 from the
+    """ResNet-20-style network (paper's Appendix A architecture) in FP64 from the
     plain layers: 3x3 conv + ReLU; per stage, residual blocks (3x3 conv, ReLU,
     3x3 conv, + shortcut, ReLU) whose first block in stages 2 and 3 has stride
     2 and a 1x1 stride-2 conv shortcut; global average pooling; FC.  With

@@ -1,5 +1,5 @@
 // arith.cu -- slot-wise ciphertext arithmetic around the rotation: plaintext
-// products and sums (paper Sec. 4.1, kernel-vector products and their sum),
+// products and sums (paper Sec. 5.1, kernel-vector products and their sum),
 // decryption, and floor rescaling by the last prime (paper Sec. 6, depth).
 // All are HBM-bound streams over u64[2][l][N]; each thread handles two
 // adjacent coefficients with 16-byte accesses.

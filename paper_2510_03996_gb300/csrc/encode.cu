@@ -1,4 +1,4 @@
-// encode.cu -- CKKS encoding and decoding (paper Sec. 2.2: a vector of N/2
+// encode.cu -- CKKS encoding and decoding (paper Sec. 3.2: a vector of N/2
 // complex slots maps to R = Z[X]/(X^N+1)), in FP64 on the device.
 //
 // Slot i is the evaluation at zeta^(5^i mod 2N), zeta = exp(i pi / N).  With

@@ -1,5 +1,5 @@
 // keyswitch.cu -- the homomorphic rotation: Galois automorphism + hybrid key
-// switching (paper Sec. 2.2 rotation, Sec. 6 "4 digits"; Han-Ki hybrid key
+// switching (paper Sec. 3.2 rotation, Sec. 6 "4 digits"; Han-Ki hybrid key
 // switching with Cheon et al. fast base conversion), for one ciphertext or a
 // batch of ciphertexts at mixed levels and Galois elements.
 //
@@ -23,7 +23,7 @@
 // The key is in Montgomery form, so a product with it reduces to the plain
 // residue with one REDC.
 //
-// Hoisted rotations (the "fast rotations" of paper Sec. 2.2; Halevi-Shoup
+// Hoisted rotations (the "fast rotations" of paper Sec. 3.2; Halevi-Shoup
 // hoisting): rotations of one input share IC, UPA and UPB, run once on c1
 // without the automorphism; each rotation's inner product then reads the
 // shared raised digits through the sigma_g gather (sigma_g maps every aligned

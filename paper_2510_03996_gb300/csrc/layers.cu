@@ -1,18 +1,18 @@
-// layers.cu -- FHEON's special secure convolution (paper Sec. 4.3, Alg. 1-3),
+// layers.cu -- FHEON's special secure convolution (paper Sec. 5.3, Alg. 1-3),
 // generalised from 3x3 to any odd k with "same" padding and stride 1, as host
 // orchestration of the device operations.
 //
-// Input packing (paper Sec. 4.1, flattening): channel c, row h, column w at
+// Input packing (paper Sec. 5.1, flattening): channel c, row h, column w at
 // slot c*H*W + h*W + w.  For tap (di, dj) in [-p, p]^2, p = (k-1)/2, the
 // rotated ciphertext Rot_{di*W+dj}(x) holds x[h+di][w+dj] at slot (h, w); the
 // tap plaintext is the kernel value times the boundary mask of Alg. 2/3
 // (1 where (h+di, w+dj) lies inside the input), per channel block.  The
 // k^2 - 1 tap rotations of the input are hoisted (one raising of c1 shared by
-// all of them: the "fast rotations" of Sec. 2.2); the k^2 products are formed
+// all of them: the "fast rotations" of Sec. 3.2); the k^2 products are formed
 // and summed in one pass and rescaled once (the taps are encoded at scale
 // q_{level-1}, so the scale returns to the input's).  With C > 1 input
 // channels the channel blocks are summed by C-1 chained rotations by H*W
-// (the single W^2 key of Sec. 4.3) and masked to block 0, which costs one
+// (the single W^2 key of Sec. 5.3) and masked to block 0, which costs one
 // more level.  The bias is added last.
 #include <cmath>
 #include <memory>

@@ -1,9 +1,9 @@
 // linear.cu -- the linear layers of an encrypted CNN on a packed feature map
-// (fheon_map): convolution (paper Sec. 4.1 equation; any zero padding and
+// (fheon_map): convolution (paper Sec. 5.1 equation; any zero padding and
 // stride, C input and F output channels; the stride selects the output
-// positions the weights are placed at), average pooling (Sec. 4.4: the window sum
+// positions the weights are placed at), average pooling (Sec. 5.4: the window sum
 // times a 1/k^2 mask that also does the striding, the outputs staying at
-// stride-aligned slots) and the fully connected layer (Sec. 4.5: one product
+// stride-aligned slots) and the fully connected layer (Sec. 5.5: one product
 // per output neuron, the sum of its slots, a one-hot placement).
 //
 // Rotation-sum layer (conv, pooling):

@@ -1,4 +1,4 @@
-// relu.cu -- FHEON's secure ReLU (paper Sec. 4.6, Alg. 4) as host
+// relu.cu -- FHEON's secure ReLU (paper Sec. 5.6, Alg. 4) as host
 // orchestration of the device operations: the input times a 1/beta slot mask
 // (when beta > 1), then a degree-D Chebyshev series of f(z) = beta * max(0, z)
 // on [-1, 1].

@@ -1,5 +1,5 @@
 // sampler.cu -- every random draw of the scheme, on the device, and the key
-// generation / encryption built on them (paper Sec. 5: context, keys and the
+// generation / encryption built on them (paper Sec. 5.7: context, keys and the
 // encryption layer).
 //
 // Draws.  Stream (seed, domain, idx) is the ChaCha20 block function (RFC 8439

@@ -1,5 +1,5 @@
 """LeNet-5 encrypted inference on the library's packed layers (the paper's
-LeNet-5 of Sec. 7: conv 5x5 1->6, ReLU, average pooling 2/2, conv 5x5 6->16,
+LeNet-5 of Appendix A: conv 5x5 1->6, ReLU, average pooling 2/2, conv 5x5 6->16,
 ReLU, average pooling 2/2, FC 256->120, ReLU, FC 120->84, ReLU, FC 84->10).
 
 Every layer is a C-ABI layer of the library (fheon_conv_prepare,

@@ -1,5 +1,5 @@
 """ResNet-20 encrypted inference with bootstrapping on the library's layers
-(the paper's ResNet-20 of Sec. 7: a 3x3 conv 3->16 and ReLU, three stages of
+(the paper's ResNet-20 of Appendix A: a 3x3 conv 3->16 and ReLU, three stages of
 three residual blocks with 16, 32 and 64 channels, the first block of stages
 2 and 3 with stride 2 and a 1x1 stride-2 convolution on its shortcut, global
 average pooling and FC 64->10).

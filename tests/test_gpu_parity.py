@@ -209,7 +209,7 @@ def _tap_plains_int(pr, k, level, seed):
 
 def test_conv2d_orchestration_bit_exact(conv13):
     """Library special conv with caller-made integer tap plaintexts vs the
-    oracle's Sec. 4.3 orchestration on the same plaintexts (N = 2^13, 28x28, 5x5),
+    oracle's Sec. 5.3 orchestration on the same plaintexts (N = 2^13, 28x28, 5x5),
     tap rotations hoisted on both sides."""
     pr = conv13
     g = pr.g
@@ -383,7 +383,7 @@ def test_ciphertext_batch_transfers(small):
 
 
 def test_multichannel_special_conv_matches_fp64(conv13):
-    """The special conv with C = 2 input channels (Sec. 4.3: tap products over
+    """The special conv with C = 2 input channels (Sec. 5.3: tap products over
     both channel blocks, the channel sum by chained rotations of H*W, the A*
     mask, two rescales) decrypts to the FP64 convolution summed over the
     channels."""

@@ -1,4 +1,4 @@
-"""The approximate ReLU (paper Sec. 4.6, Alg. 4) on the GPU against the
+"""The approximate ReLU (paper Sec. 5.6, Alg. 4) on the GPU against the
 oracle's evaluation plan: same coefficients to the bit, same ciphertexts to the
 bit from the same integer mask plaintext and input; the decrypted output
 against the FP64 Chebyshev series; argument errors."""

@@ -64,7 +64,7 @@ def test_special_conv_slots_equals_fp64_same_conv(k, C, H, W):
 
 
 def test_rotation_step_count():
-    # one key per non-identity tap: k^2 - 1 (paper Sec. 4.1: k^2 - 1 rotations)
+    # one key per non-identity tap: k^2 - 1 (paper Sec. 5.1: k^2 - 1 rotations)
     for k in (3, 5):
         steps = fheon.conv_rotation_steps(28, k)
         assert len(steps) == k * k - 1 and len(set(steps)) == k * k - 1 and 0 not in steps

@@ -1,6 +1,6 @@
 """Pins of the oracle's packed network layers: the rotation-sum plans of
 convolution and average pooling and the FC plan, simulated exactly on FP64 slot
-vectors, against the plain FP64 layers (Sec. 4.1, 4.4, 4.5 equations), also
+vectors, against the plain FP64 layers (Sec. 5.1, 4.4, 4.5 equations), also
 chained on dilated grids; and the encrypted plans against the slot model under
 decryption."""
 import numpy as np

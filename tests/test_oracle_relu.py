@@ -1,4 +1,4 @@
-"""Pins of the oracle's approximate ReLU (paper Sec. 4.6, Alg. 4): the
+"""Pins of the oracle's approximate ReLU (paper Sec. 5.6, Alg. 4): the
 Chebyshev coefficients against numpy's Chebyshev interpolation (the same nodes,
 a library routine) and the interpolation property at the nodes; the series'
 distance to max(0, x); and the encrypted evaluation plan against the FP64
