@@ -227,7 +227,7 @@ def cheb_depth(degree):
     """Levels the library's Chebyshev series of this degree consumes."""
     d = load().fheon_cheb_depth(int(degree))
     if not d:
-        raise FheonError(FHEON_ERR_ARG, "degree outside [1, 1023]")
+        raise FheonError(-1, "degree outside [1, 1023]")
     return d
 
 

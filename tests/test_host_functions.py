@@ -1,0 +1,27 @@
+"""Host-only calls of the library (no device is touched): the ReLU's and
+EvalMod's Chebyshev coefficients are the oracle's to the bit (the integer
+constants of both sides' series derive from them), the default bootstrapping
+parameters follow the oracle's rule, and the series depth is the oracle's."""
+import numpy as np
+import pytest
+
+from oracle import boot as B
+from oracle import fheon as OF
+from paper_2510_03996_gb300 import fheon as F
+
+
+@pytest.mark.parametrize("beta,D", [(1.0, 7), (2.5, 27), (4.0, 59), (17.25, 59), (3.0, 127)])
+def test_relu_coefficients_identical(beta, D):
+    assert np.array_equal(F.relu_coeffs(beta, D), OF.relu_cheb_coeffs(beta, D))
+
+
+@pytest.mark.parametrize("K,r,D", [(128, 7, 27), (512, 9, 27), (64, 5, 31), (256, 8, 59)])
+def test_evalmod_coefficients_identical(K, r, D):
+    assert np.array_equal(F.Context.evalmod_coeffs(K, r, D), B.evalmod_coeffs(K, r, D))
+
+
+def test_series_depths():
+    for D in (1, 2, 7, 27, 59, 63, 64, 100, 1023):
+        assert F.cheb_depth(D) == OF.cheb_depth(D)
+    with pytest.raises(F.FheonError):
+        F.cheb_depth(0)
