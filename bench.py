@@ -237,30 +237,82 @@ def oracle_all_cores(P, step, levels, per_core=1, cores=None):
     return done / slowest, done, slowest, cores
 
 
+def _oracle_server(P, step, cmd, results):
+    """A reference-arm worker (a spawned process): rotates one ciphertext at
+    each level it is sent, reports the seconds; None ends it."""
+    runner = OracleRunner(P, step)
+    results.put(("ready", 0.0))
+    while True:
+        lv = cmd.get()
+        if lv is None:
+            return
+        results.put(("done", runner.rotate_seconds(lv)))
+
+
+class OraclePool:
+    """The oracle on every host core: one spawned process per core, each with
+    its own context and key; a step sends one level to every process and
+    lasts as long as the slowest."""
+
+    def __init__(self, P, step, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        self.results = ctx.Queue()
+        self.cmds = [ctx.Queue() for _ in range(self.cores)]
+        self.procs = [ctx.Process(target=_oracle_server, args=(P, step, q, self.results)) for q in self.cmds]
+        for p in self.procs:
+            p.start()
+        for _ in self.procs:
+            self.results.get()
+
+    def step(self, levels):
+        for q, lv in zip(self.cmds, levels):
+            q.put(lv)
+        return max(self.results.get()[1] for _ in levels)
+
+    def close(self):
+        for q in self.cmds:
+            q.put(None)
+        for p in self.procs:
+            p.join()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
     P = synth.params(WORKLOAD)
     levels, steps = synth.rotation_workload(P["seed"])
-    runner = OracleRunner(P, steps[0])
-    # each step rotates the next workload item on the oracle
-    for k in range(args.warmup):
-        runner.rotate_seconds(levels[k % len(levels)])
+    pool = OraclePool(P, steps[0])
+    n = pool.cores
+    # each step rotates the next `cores` workload items, one per host core, at once
+    item = 0
+
+    def next_levels():
+        nonlocal item
+        lv = [levels[(item + c) % len(levels)] for c in range(n)]
+        item += n
+        return lv
+
+    for _ in range(args.warmup):
+        pool.step(next_levels())
     t_steps, per_step = [], []
-    for k in range(args.steps):
-        lv = levels[(args.warmup + k) % len(levels)]
-        t_steps.append(runner.rotate_seconds(lv))
+    for _ in range(args.steps):
+        lv = next_levels()
+        t_steps.append(pool.step(lv))
         per_step.append(lv)
-    value = len(t_steps) / sum(t_steps)
+    pool.close()
+    value = n * len(t_steps) / sum(t_steps)
     ms = 1e3 * sum(t_steps) / len(t_steps)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "batched rotation, N=2^16, 24x50-bit Q + 4x60-bit P, dnum 6, levels U{4..24}, "
-                                   "steps U[1,2^15); reference steps rotate one ciphertext each",
+                                   "steps U[1,2^15); a reference step rotates %d ciphertexts, one per host core" % n,
                        "levels_sampled": per_step, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "one rotation per step at the workload's item levels %s" % per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
+                             "sample": "%d rotations per step, one per host core at once, at the workload's item "
+                                       "levels" % n},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

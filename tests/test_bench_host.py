@@ -49,3 +49,15 @@ def test_oracle_on_every_core():
     P = synth.params("tiny")
     rate, done, slowest, cores = bench.oracle_all_cores(P, 3, [2, 3, 4], per_core=2, cores=2)
     assert cores == 2 and done == 4 and slowest > 0 and rate == pytest.approx(done / slowest)
+
+
+def test_reference_pool_steps_every_core():
+    P = synth.params("tiny")
+    pool = bench.OraclePool(P, 3, cores=2)
+    try:
+        t = pool.step([2, 4])
+        assert t > 0
+        assert pool.step([3, 3]) > 0
+    finally:
+        pool.close()
+    assert all(p.exitcode == 0 for p in pool.procs)
