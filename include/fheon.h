@@ -7,8 +7,11 @@
  * layers of Sec. 5 and bootstrapping on top of RNS-CKKS (Sec. 3.2).  This
  * library is the GPU arithmetic under those calls: the homomorphic rotation
  * (Galois automorphism + hybrid key switching) and the plaintext-multiply,
- * add and rescale steps around it, plus the packed special convolution of
- * Sec. 5.3.
+ * add and rescale steps around it, and on top of them the secure layers as
+ * prepared handles (the special convolution of Sec. 5.3; packed convolution,
+ * pooling and FC of Sec. 5.1-5.5; the Chebyshev ReLU of Sec. 5.6; repacking),
+ * CKKS bootstrapping as a layer, model programs and a continuous-batching
+ * server.
  *
  * Conventions shared by every call
  *  - Every call returns int: FHEON_OK (0) or a negative FHEON_ERR_* code;
