@@ -647,6 +647,13 @@ int fheon_relu_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *i
 /* One-shot: prepare at in's level, apply, release. */
 int fheon_relu_approx(fheon_ctx *ctx, const fheon_ct *ct, double beta, uint32_t degree, uint32_t n, fheon_ct *out);
 
+/* Failure detection without a fault: one thread waits on a TMA barrier that
+ * nothing completes, with the library's bounded wait cut to `polls` polls
+ * (1 .. 2^22); the wait gives up and records FHEON_ERR_TIMEOUT in the
+ * context's device error word, which the next fheon_sync reports (and
+ * clears).  The context stays usable. */
+int fheon_selftest_wait(fheon_ctx *ctx, uint32_t polls);
+
 /* ------------------------------------------------------------------ */
 /* Instrumentation (no counterpart in the paper)                      */
 /* ------------------------------------------------------------------ */

@@ -1111,3 +1111,27 @@ int rotate_hoisted(fheon_ctx *ctx, const fheon_ct *in, const int32_t *steps, uin
 }
 
 } // namespace fheon
+
+namespace {
+// one thread arms a TMA barrier for 16 bytes that no copy brings, then waits
+// with the library's bounded wait: it gives up after `polls` polls and
+// records the timeout in the device error word, as the inner product does
+__global__ void wait_selftest_kernel(int *err, u32 polls)
+{
+    __shared__ __align__(8) u64 bar;
+    if (threadIdx.x != 0) return;
+    tma::mbar_init(&bar, 1);
+    tma::fence_mbar_init();
+    tma::mbar_arrive_expect_tx(&bar, 16);
+    if (!tma::mbar_wait(&bar, 0, polls)) atomicExch(err, FHEON_ERR_TIMEOUT);
+}
+} // namespace
+
+extern "C" int fheon_selftest_wait(fheon_ctx *ctx, uint32_t polls)
+{
+    if (!ctx || polls < 1 || polls > tma::WAIT_POLLS) return FHEON_ERR_ARG;
+    wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(ctx->err.as<int>(), polls);
+    FHEON_CUDA(ctx, cudaGetLastError());
+    return FHEON_OK;
+}
+

@@ -139,6 +139,7 @@ SIGNATURES = {
     "fheon_bootstrap_keygen": [c_vp, c_vp, c_vp],
     "fheon_bootstrap_info": [c_vp, P(c_u32), P(c_dbl)],
     "fheon_mod_raise": [c_vp, c_vp, c_vp],
+    "fheon_selftest_wait": [c_vp, c_u32],
     "fheon_layer_apply_graph": [c_vp, c_vp, c_vp, c_vp],
     "fheon_layer_apply_batch": [c_vp, c_vp, P(c_vp), c_u32, P(c_vp)],
     "fheon_model_create": [c_vp, P(c_vp), c_u32, c_vpp],
@@ -699,6 +700,10 @@ class Context:
         lv, sc = c_u32(0), c_dbl(0)
         check(load().fheon_bootstrap_info(layer.h, ctypes.byref(lv), ctypes.byref(sc)))
         return lv.value, sc.value
+
+    def selftest_wait(self, polls):
+        """Launch a bounded wait that runs out (see fheon_selftest_wait)."""
+        self._chk(load().fheon_selftest_wait(self.h, polls))
 
     def mod_raise(self, ct, out=None):
         out = out or self.ct_create(1)
