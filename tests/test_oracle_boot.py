@@ -171,3 +171,27 @@ def test_bootstrap_encrypted(boot_ctx):
         v = ctx.decode_ct(se, part, plan.evalmod_scale)
         assert np.max(np.abs(v.real - np.sin(2 * np.pi * brv_order(half) / q0))) < 1e-7
         assert np.max(np.abs(v.imag)) < 1e-7
+
+
+def test_slot_transform_at_the_test_size():
+    """At n = 2^11 (the N = 2^12 contexts): the butterfly stages equal the
+    oracle's decode of the real polynomial (t_lo, t_hi), and the three merged
+    levels of each transform in BSGS form (the split the bootstrap uses)
+    round-trip."""
+    n = 1 << 11
+    rng = synth.rng(0xB006, 0)
+    zp = rng.normal(size=n) + 1j * rng.normal(size=n)
+    A = brv_order(zp)
+    for s in range(1, n.bit_length()):
+        A = B.apply_diagonals(B.stage_diagonals(n, 1 << (s - 1)), A)
+    dec = ckks.decode(np.concatenate([zp.real, zp.imag]), n, 1.0)
+    assert np.max(np.abs(A - dec)) < 1e-9
+    x = brv_order(zp)
+    for stride, M in B.stc_levels(n, 3):
+        r, groups = B.bsgs_plan(M, n, stride)
+        x = B.plan_slots(x, r, groups)
+    assert np.max(np.abs(x - dec)) < 1e-9
+    for stride, M in B.cts_levels(n, 3):
+        r, groups = B.bsgs_plan(M, n, stride)
+        x = B.plan_slots(x, r, groups)
+    assert np.max(np.abs(x - brv_order(zp))) < 1e-11
