@@ -105,3 +105,14 @@ def test_bootstraps_only_where_levels_run_out():
     net = R.EncryptedResNet(Deep(), R.weights(0xC3, R.FULL), [2.0] * R.n_relus(R.FULL), 2.0 ** 40)
     assert net.n_boot == 9 and net.out_level >= 1
     assert min(c[1] for c in net.ctx.calls) >= 2
+
+
+def test_reduced_network_plan():
+    """The reduced network (one block per stage) on the test contexts' level
+    11: six bootstraps, one repack pair, every layer at level >= 2."""
+    net = R.EncryptedResNet(FakeCtx(), R.weights(0xC4, MINI), [2.0] * R.n_relus(MINI), 2.0 ** 40, MINI)
+    assert net.n_boot == 6 and net.in_level == 11
+    kinds = [op[0] for op in net.plan]
+    assert kinds.count("add") == 3 and kinds.count("scale") == 1
+    assert [c[0] for c in net.ctx.calls].count("repack") == 2
+    assert min(c[1] for c in net.ctx.calls) >= 2 and net.out_level >= 1
