@@ -90,7 +90,8 @@ typedef void *(*fheon_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*fheon_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 /* Install the process-wide allocator used for every later allocation
  * (NULL, NULL restores cudaMalloc/cudaFree).  Memory is freed through the
- * hook that allocated it. */
+ * hook that allocated it, so a free_fn (and its `user`) must stay callable
+ * until every block it allocated has been released. */
 int fheon_set_allocator(fheon_alloc_fn alloc, fheon_free_fn free_fn, void *user);
 
 /* ------------------------------------------------------------------ */

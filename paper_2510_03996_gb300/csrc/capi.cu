@@ -19,7 +19,7 @@ void *g_alloc_user = nullptr;
 }
 
 namespace fheon {
-void *dev_alloc(size_t bytes, cudaStream_t st)
+void *dev_alloc(size_t bytes, cudaStream_t st, FreeHook *hook)
 {
     fheon_alloc_fn a;
     void *u;
@@ -27,6 +27,8 @@ void *dev_alloc(size_t bytes, cudaStream_t st)
         std::lock_guard<std::mutex> lk(g_alloc_mu);
         a = g_alloc;
         u = g_alloc_user;
+        hook->fn = g_free;
+        hook->user = u;
     }
     if (a) return a(bytes, (void *)st, u);
     void *p = nullptr;
@@ -36,16 +38,9 @@ void *dev_alloc(size_t bytes, cudaStream_t st)
     }
     return p;
 }
-void dev_free(void *p, size_t bytes, cudaStream_t st)
+void dev_free(void *p, size_t bytes, cudaStream_t st, const FreeHook &hook)
 {
-    fheon_free_fn f;
-    void *u;
-    {
-        std::lock_guard<std::mutex> lk(g_alloc_mu);
-        f = g_free;
-        u = g_alloc_user;
-    }
-    if (f) f(p, bytes, (void *)st, u);
+    if (hook.fn) hook.fn(p, bytes, (void *)st, hook.user);
     else cudaFree(p);
 }
 

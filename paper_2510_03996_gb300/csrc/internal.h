@@ -14,18 +14,25 @@
 namespace fheon {
 
 // ------------------------------------------------------------ allocation
-void *dev_alloc(size_t bytes, cudaStream_t st);
-void dev_free(void *p, size_t bytes, cudaStream_t st);
+// The free half of the allocator that made a block: a block goes back
+// through it even if another allocator was installed since.
+struct FreeHook {
+    fheon_free_fn fn = nullptr; // nullptr: cudaFree
+    void *user = nullptr;
+};
+void *dev_alloc(size_t bytes, cudaStream_t st, FreeHook *hook);
+void dev_free(void *p, size_t bytes, cudaStream_t st, const FreeHook &hook);
 
 struct DevMem {
     void *p = nullptr;
     size_t bytes = 0;
     cudaStream_t st = nullptr;
     bool owned = true; // false: a view into memory someone else releases
+    FreeHook hook;
     DevMem() = default;
     DevMem(const DevMem &) = delete;
     DevMem &operator=(const DevMem &) = delete;
-    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes), st(o.st), owned(o.owned)
+    DevMem(DevMem &&o) noexcept : p(o.p), bytes(o.bytes), st(o.st), owned(o.owned), hook(o.hook)
     {
         o.p = nullptr;
         o.bytes = 0;
@@ -35,7 +42,7 @@ struct DevMem {
     {
         if (this != &o) {
             release();
-            p = o.p; bytes = o.bytes; st = o.st; owned = o.owned;
+            p = o.p; bytes = o.bytes; st = o.st; owned = o.owned; hook = o.hook;
             o.p = nullptr; o.bytes = 0; o.owned = true;
         }
         return *this;
@@ -53,14 +60,14 @@ struct DevMem {
         release();
         st = s;
         if (n == 0) return true;
-        p = dev_alloc(n, s);
+        p = dev_alloc(n, s, &hook);
         if (!p) return false;
         bytes = n;
         return true;
     }
     void release()
     {
-        if (p && owned) dev_free(p, bytes, st);
+        if (p && owned) dev_free(p, bytes, st, hook);
         p = nullptr;
         bytes = 0;
         owned = true;

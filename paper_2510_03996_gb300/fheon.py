@@ -221,7 +221,10 @@ def __getattr__(name):
 
 
 # ---------------------------------------------------------------- allocator hook
-_hooks = None
+# Every hook pair ever installed stays alive: the library frees each block
+# through the pair that allocated it.
+_hooks = []
+_hook_device = None
 
 
 def cheb_depth(degree):
@@ -240,11 +243,14 @@ def relu_coeffs(beta, degree=59):
 
 
 def use_torch_allocator():
-    """Route every device allocation of the library through torch's caching allocator."""
-    global _hooks
+    """Route every device allocation of the library through torch's caching
+    allocator of the current device (a no-op when it is installed already)."""
+    global _hook_device
     import torch
 
     dev = torch.cuda.current_device()
+    if _hook_device == dev:
+        return
 
     def _alloc(nbytes, stream, user):
         try:
@@ -255,8 +261,10 @@ def use_torch_allocator():
     def _free(ptr, nbytes, stream, user):
         torch.cuda.caching_allocator_delete(int(ptr))
 
-    _hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
-    check(load().fheon_set_allocator(_hooks[0], _hooks[1], None))
+    pair = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _hooks.append(pair)
+    check(load().fheon_set_allocator(pair[0], pair[1], None))
+    _hook_device = dev
 
 
 # ---------------------------------------------------------------- marshalling helpers
