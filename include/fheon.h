@@ -78,7 +78,10 @@ typedef struct fheon_map {
 
 /* Message for an error code (static storage). */
 const char *fheon_error_string(int code);
-/* Message of the last failing call on ctx (valid until the next call). */
+/* Message of the last failing call on ctx (valid until the next call).
+ * A call that rejects its arguments outright (a null pointer, a size out of
+ * range) returns FHEON_ERR_ARG and leaves the message as it was; every
+ * other failure sets it. */
 const char *fheon_last_error(const fheon_ctx *ctx);
 
 /* ------------------------------------------------------------------ */

@@ -209,7 +209,11 @@ class FheonError(RuntimeError):
 
 def check(rc, ctx=None):
     if rc != FHEON_OK:
-        msg = load().fheon_last_error(ctx).decode() if ctx else load().fheon_error_string(rc).decode()
+        msg = load().fheon_error_string(rc).decode()
+        if ctx:
+            last = load().fheon_last_error(ctx).decode()
+            # an argument rejected outright leaves the context's message unchanged
+            msg = "%s (last message on the context: %s)" % (msg, last) if rc == -1 else last
         raise FheonError(rc, msg)
 
 
