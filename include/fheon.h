@@ -178,13 +178,29 @@ int fheon_relinkeygen(fheon_ctx *ctx, const fheon_sk *sk);
 /* Same, by Galois element (odd g < 2N; 2N-1 is complex conjugation). */
 int fheon_galois_keygen(fheon_ctx *ctx, const fheon_sk *sk, const uint64_t *galois, uint32_t n);
 /* Drop the key of Galois element g (paper Sec. 5.7: keys loaded and cleared
- * per block); FHEON_ERR_NO_KEY if absent. */
+ * per block); FHEON_ERR_NO_KEY if absent.  Waits for the context's queued
+ * work; a layer graph captured with this key must not be replayed after. */
 int fheon_key_erase(fheon_ctx *ctx, uint64_t galois);
 /* Number of resident rotation keys and their device bytes. */
 int fheon_key_stats(const fheon_ctx *ctx, uint32_t *count, uint64_t *bytes);
 /* Blocking copy of the key of Galois element g, canonical residues,
  * u64[beta][2][L+K][N] (component 0 = b, 1 = a). */
 int fheon_key_download(fheon_ctx *ctx, uint64_t galois, uint64_t *host);
+/* Install the key of Galois element g (0 = the relinearisation key) from
+ * host limbs in the layout fheon_key_download writes: u64[beta][2][L+K][N],
+ * canonical residues (the reverse of the download: converted to Montgomery
+ * form on the device).  The load half of a key checkpoint (paper Sec. 5.7
+ * loads each block's keys from storage).  A key already present is
+ * overwritten in place, after the context's queued work, so that graphs
+ * captured with it stay valid.  FHEON_ERR_ARG for a bad element or any
+ * residue not below its limb's modulus (checked on the host before any
+ * copy); blocks until the key is on the device. */
+int fheon_key_upload(fheon_ctx *ctx, uint64_t galois, const uint64_t *host);
+/* The Galois elements of the resident keys in increasing order (0 is the
+ * relinearisation key).  With out == NULL, *n receives the count; else *n
+ * is out's capacity on entry (FHEON_ERR_ARG if too small) and the count on
+ * return. */
+int fheon_key_list(const fheon_ctx *ctx, uint64_t *out, uint32_t *n);
 /* Galois element of a slot rotation by r (negative r allowed). */
 uint64_t fheon_galois_elt(const fheon_ctx *ctx, int32_t r);
 

@@ -515,6 +515,54 @@ int fheon_key_download(fheon_ctx *ctx, uint64_t galois, uint64_t *host)
     return download(ctx, tmp.p, host, it->second.mem.bytes);
 }
 
+int fheon_key_upload(fheon_ctx *ctx, uint64_t galois, const uint64_t *host)
+{
+    if (!ctx || !host) return FHEON_ERR_ARG;
+    if (galois != 0 && ((galois & 1) == 0 || galois >= 2ull * ctx->N))
+        return fail(ctx, FHEON_ERR_ARG, "bad Galois element %llu", (unsigned long long)galois);
+    const size_t per = (size_t)(ctx->L + ctx->K), blocks = (size_t)2 * ctx->beta, N = ctx->N;
+    for (size_t b = 0; b < blocks; b++)
+        for (size_t t = 0; t < per; t++) {
+            const u64 q = ctx->mod[t];
+            const uint64_t *x = host + (b * per + t) * N;
+            for (size_t i = 0; i < N; i++)
+                if (x[i] >= q)
+                    return fail(ctx, FHEON_ERR_ARG, "key upload: residue %zu of limb %zu in block %zu is not below its modulus",
+                                i, t, b);
+        }
+    const size_t bytes = blocks * per * N * 8;
+    auto it = ctx->keys.find(galois);
+    RotKey fresh;
+    u64 *dst;
+    if (it != ctx->keys.end()) {
+        // overwritten where it is, so that captured graphs still read it;
+        // queued work may be reading the old values
+        FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        dst = it->second.mem.as<u64>();
+    } else {
+        if (!fresh.mem.alloc(bytes, ctx->stream)) return fail(ctx, FHEON_ERR_OOM, "key upload (%zu bytes)", bytes);
+        dst = fresh.mem.as<u64>();
+    }
+    FHEON_CUDA(ctx, cudaMemcpyAsync(dst, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    FHEON_CUDA(ctx, key_to_mont(ctx, dst, per, (u32)blocks));
+    FHEON_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (it == ctx->keys.end()) ctx->keys.emplace(galois, std::move(fresh));
+    return FHEON_OK;
+}
+
+int fheon_key_list(const fheon_ctx *ctx, uint64_t *out, uint32_t *n)
+{
+    if (!ctx || !n) return FHEON_ERR_ARG;
+    const u32 have = (u32)ctx->keys.size();
+    if (out) {
+        if (*n < have) return FHEON_ERR_ARG;
+        u32 i = 0;
+        for (auto &kv : ctx->keys) out[i++] = kv.first; // std::map: increasing order
+    }
+    *n = have;
+    return FHEON_OK;
+}
+
 // ------------------------------------------------------------------ plaintexts
 int fheon_plain_from_coeffs(fheon_ctx *ctx, const int64_t *coeffs, uint32_t level, double scale, fheon_pt **out)
 {

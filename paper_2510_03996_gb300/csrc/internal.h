@@ -263,6 +263,7 @@ int plain_from_coeffs_dev(fheon_ctx *ctx, const int64_t *host_coeffs, u32 level,
 // device signed coefficients (N) -> evaluation-form residues over limbs 0..level-1
 int limbs_from_coeffs_dev(fheon_ctx *ctx, const long long *dev_coeffs, u32 level, u64 *out);
 cudaError_t key_from_mont(fheon_ctx *ctx, const u64 *in, u64 *out, size_t limbs_per_block, u32 blocks);
+cudaError_t key_to_mont(fheon_ctx *ctx, u64 *x, size_t limbs_per_block, u32 blocks);
 
 // encoding (encode.cu)
 int build_fft_tables(fheon_ctx *ctx);

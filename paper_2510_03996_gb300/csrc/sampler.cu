@@ -150,6 +150,17 @@ __global__ void __launch_bounds__(TPB) from_mont_kernel(const u64 *__restrict__ 
     out[idx] = redc(0, in[idx], m.q, m.qneg_inv);
 }
 
+// x = x * 2^64 mod q in place (residues to Montgomery form), over blocks of
+// `per` limbs whose modulus index is the position within the block
+__global__ void __launch_bounds__(TPB) to_mont_kernel(u64 *x, u32 per, u64 total, u32 logN,
+                                                      const ModConst *__restrict__ mc)
+{
+    const u64 idx = (u64)blockIdx.x * TPB + threadIdx.x;
+    if (idx >= total) return;
+    const ModConst m = mc[(u32)((idx >> logN) % per)];
+    x[idx] = to_mont(x[idx], m);
+}
+
 // sigma_g gather of an evaluation-form polynomial over `nlimb` limbs
 __global__ void __launch_bounds__(TPB) gather_kernel(const u64 *__restrict__ in, u64 *__restrict__ out, u64 g,
                                                      u32 nlimb, u32 logN)
@@ -287,6 +298,14 @@ cudaError_t key_from_mont(fheon_ctx *ctx, const u64 *in, u64 *out, size_t limbs_
     const u64 total = (u64)limbs_per_block * blocks * ctx->N;
     from_mont_kernel<<<nblk(total), TPB, 0, ctx->stream>>>(in, out, (u32)limbs_per_block, total, ctx->logN,
                                                            ctx->tab.mc.as<ModConst>());
+    return cudaGetLastError();
+}
+
+cudaError_t key_to_mont(fheon_ctx *ctx, u64 *x, size_t limbs_per_block, u32 blocks)
+{
+    const u64 total = (u64)limbs_per_block * blocks * ctx->N;
+    to_mont_kernel<<<nblk(total), TPB, 0, ctx->stream>>>(x, (u32)limbs_per_block, total, ctx->logN,
+                                                         ctx->tab.mc.as<ModConst>());
     return cudaGetLastError();
 }
 

@@ -83,6 +83,8 @@ SIGNATURES = {
     "fheon_key_erase": [c_vp, c_u64],
     "fheon_key_stats": [c_vp, P(c_u32), P(c_u64)],
     "fheon_key_download": [c_vp, c_u64, P(c_u64)],
+    "fheon_key_upload": [c_vp, c_u64, P(c_u64)],
+    "fheon_key_list": [c_vp, P(c_u64), P(c_u32)],
     "fheon_galois_elt": [c_vp, c_i32],
     "fheon_encode_plain": [c_vp, P(c_dbl), P(c_dbl), c_u32, c_u32, c_dbl, c_vpp],
     "fheon_plain_from_coeffs": [c_vp, P(ctypes.c_int64), c_u32, c_dbl, c_vpp],
@@ -412,6 +414,19 @@ class Context:
         out = np.zeros((self.beta, 2, self.L + self.K, self.N), dtype=np.uint64)
         self._chk(load().fheon_key_download(self.h, int(g), _u64p(out)))
         return out
+
+    def key_upload(self, g, limbs):
+        a = np.ascontiguousarray(limbs, dtype=np.uint64)
+        if a.size != self.beta * 2 * (self.L + self.K) * self.N:
+            raise FheonError(-1, "key limbs must be u64[beta][2][L+K][N]")
+        self._chk(load().fheon_key_upload(self.h, int(g), _u64p(a)))
+
+    def key_list(self):
+        n = c_u32()
+        self._chk(load().fheon_key_list(self.h, None, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1), dtype=np.uint64)
+        self._chk(load().fheon_key_list(self.h, _u64p(out), ctypes.byref(n)))
+        return [int(x) for x in out[:n.value]]
 
     def galois_elt(self, r):
         return int(load().fheon_galois_elt(self.h, int(r)))
