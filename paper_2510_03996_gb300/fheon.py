@@ -248,6 +248,20 @@ def relu_coeffs(beta, degree=59):
     return np.array(out[:])
 
 
+def set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(nbytes, stream, user) -> address or None
+    and free(ptr, nbytes, stream, user) as the library's allocator; with
+    neither, cudaMalloc/cudaFree.  Blocks made before go back through the hook
+    that made them."""
+    global _hook_device
+    if (alloc is None) != (free is None):
+        raise FheonError(-1, "alloc and free come together")
+    pair = (ALLOC_FN(alloc), FREE_FN(free)) if alloc is not None else (ALLOC_FN(), FREE_FN())
+    _hooks.append(pair)
+    check(load().fheon_set_allocator(pair[0], pair[1], None))
+    _hook_device = None
+
+
 def use_torch_allocator():
     """Route every device allocation of the library through torch's caching
     allocator of the current device (a no-op when it is installed already)."""

@@ -1,7 +1,8 @@
 """Host-only calls of the library (no device is touched): the ReLU's and
 EvalMod's Chebyshev coefficients are the oracle's to the bit (the integer
 constants of both sides' series derive from them), the default bootstrapping
-parameters follow the oracle's rule, and the series depth is the oracle's."""
+parameters follow the oracle's rule, the series depth is the oracle's, and
+allocator hooks install and uninstall."""
 import numpy as np
 import pytest
 
@@ -25,3 +26,15 @@ def test_series_depths():
         assert F.cheb_depth(D) == OF.cheb_depth(D)
     with pytest.raises(F.FheonError):
         F.cheb_depth(0)
+
+
+def test_allocator_hooks_install_without_a_gpu():
+    """Installing hooks is host-only: a pair installs, NULL/NULL restores
+    cudaMalloc, and one hook without the other is refused."""
+    from paper_2510_03996_gb300 import fheon as F
+    L = F.load()
+    F.set_allocator(lambda n, s, u: None, lambda p, n, s, u: None)
+    F.set_allocator()
+    assert L.fheon_set_allocator(F.ALLOC_FN(lambda n, s, u: None), F.FREE_FN(), None) == -1
+    with pytest.raises(F.FheonError):
+        F.set_allocator(lambda n, s, u: None)
