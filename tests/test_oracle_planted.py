@@ -1,0 +1,235 @@
+"""The oracle's pins catch plausible mistakes: each case plants one mistake in
+the oracle (a dropped term, a wrong sign, a transposed operand, a wrong index)
+and checks that the pin written for that part fails.
+
+C mistakes are planted in a copy of ckks_oracle.c, compiled with the oracle's
+own flags into a temporary library that stands in for the oracle's for the
+duration of one test; the oracle's source is not touched.  Python mistakes are
+planted with monkeypatch.  Every planted mistake runs on the CPU."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import test_oracle_boot as TB
+import test_oracle_fheon as TF
+import test_oracle_layers as TL
+import test_oracle_mult as TM
+import test_oracle_primitives as PR
+import test_oracle_relu as TR
+import test_oracle_scheme as S
+from oracle import _lib
+from oracle import boot as B
+from oracle import ckks
+from oracle import fheon as OF
+from paper_2510_03996_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ckks_oracle.c")
+
+
+def _tiny():
+    ctx, P = S._ctx("tiny")
+    s, se = ctx.keygen_sk()
+    return ctx, P, s, se, ctx.keygen_pk(se)
+
+
+# name: (C function holding the site, exact text, planted text, the pin that must fail)
+C_PLANTS = {
+    "chacha_rotation": ("static void quarter(", "x[d] = rotl32(x[d], 16);", "x[d] = rotl32(x[d], 15);",
+                        lambda: PR.test_chacha20_rfc8439_vector()),
+    "cdt_variance": ("void oracle_cdt_table(", "(2.0 * sigma * sigma)", "(sigma * sigma)",
+                     lambda: PR.test_cdt_table_against_high_precision()),
+    "ntt_butterfly_sign": ("static void ntt_fast(", "a[j + t] = submod(U, V, q);", "a[j + t] = addmod(U, V, q);",
+                           lambda: PR.test_fast_ntt_equals_definition(6)),
+    "ntt_twiddle_order": ("static void ntt_fast(", "u64 S = tw[m + i];", "u64 S = tw[m + (m - 1 - i)];",
+                          lambda: PR.test_fast_ntt_equals_definition(6)),
+    "automorphism_wrap_sign": ("void oracle_automorph_coeff(", "else out[e - N] = submod(0, a[i] % q, q);",
+                               "else out[e - N] = a[i] % q;",
+                               lambda: PR.test_automorph_coeff_definition_and_composition()),
+    "bconv_missing_inverse": ("void oracle_bconv(", "u64 y = mulmod(in[(size_t)i * N + n], inv, from[i]);",
+                              "u64 y = in[(size_t)i * N + n] % from[i]; (void)inv;",
+                              lambda: PR.test_bconv_against_exact_crt()),
+    "modup_digit_dropped": ("void oracle_modup(",
+                            "memcpy(out + (size_t)l * N, x_coeff + (size_t)l * N, sizeof(u64) * N);",
+                            "memset(out + (size_t)l * N, 0, sizeof(u64) * N);",
+                            lambda: S.test_modup_is_crt_lift_plus_small_multiple(_tiny())),
+    "moddown_sign": ("void oracle_moddown(", "mulmod(submod(x_coeff[o], conv[o], q), Pinv, q)",
+                     "mulmod(addmod(x_coeff[o], conv[o], q), Pinv, q)",
+                     lambda: S.test_moddown_is_floor_division_minus_small(_tiny())),
+    "rescale_no_subtraction": ("void oracle_rescale_poly(", "mulmod(submod(x[o], ri[k], q), inv, q)",
+                               "mulmod(x[o], inv, q)", lambda: S.test_rescale_is_floor_division(_tiny())),
+    "ksk_missing_P": ("void oracle_keygen_ksk(", "addmod(v, mulmod(Pm, sfrom_eval[o], m), m)",
+                      "addmod(v, sfrom_eval[o], m)", lambda: S.test_keyswitch_noise_bound(_tiny())),
+    "keyswitch_key_components_swapped": ("void oracle_keyswitch(", "(((size_t)j * 2 + b) * nall + mi)",
+                                         "(((size_t)j * 2 + (1 - b)) * nall + mi)",
+                                         lambda: S.test_rotate_decrypts_to_automorphism(_tiny(), 1)),
+    "rotate_c0_dropped": ("void oracle_rotate(", "out[o] = addmod(sc[o], ks[o], c->mod[i]);", "out[o] = ks[o];",
+                          lambda: S.test_rotate_decrypts_to_automorphism(_tiny(), 3)),
+    "encrypt_message_dropped": ("void oracle_encrypt(", "addmod(addmod(mulmod(V[o], pk[o], q), E0[o], q), M[o], q)",
+                                "addmod(mulmod(V[o], pk[o], q), E0[o], q)",
+                                lambda: S.test_encrypt_decrypt_noise_bound(_tiny())),
+    "encode_conjugated": ("int oracle_encode(", "acc += zr[i] * cs[e] - zi[i] * sn[e];",
+                          "acc += zr[i] * cs[e] + zi[i] * sn[e];", lambda: S.test_encode_decode_roundtrip(64)),
+    "decode_sign": ("void oracle_decode(", "ai += m[k] * sn[e];", "ai -= m[k] * sn[e];",
+                    lambda: S.test_decode_matches_independent_fft_formulation()),
+    "tensor_cross_term_dropped": ("void oracle_mul_relin(",
+                                  "addmod(mulmod(a[o], b[pl + o], q), mulmod(a[pl + o], b[o], q), q)",
+                                  "mulmod(a[o], b[pl + o], q)",
+                                  lambda: TM.test_mul_relin_decrypts_to_the_product(_tiny(), 4)),
+    "relu_wrong_side": ("void oracle_cheb_coeffs(", "z < 0.0 ? 0.0 : beta * z", "z > 0.0 ? 0.0 : beta * z",
+                        lambda: TR.test_coeffs_are_chebyshev_interpolation(1.0, 59)),
+    "evalmod_phase_sign": ("void oracle_cos_cheb_coeffs(", "(K * z - 0.25)", "(K * z + 0.25)",
+                           lambda: TB.test_evalmod_series_and_doublings()),
+}
+
+
+def plant_c(src, func, old, new):
+    """src with `old` replaced by `new` inside the body of the C function whose
+    definition starts with `func` (the text must occur there exactly once)."""
+    start = src.index(func)
+    end = src.index("\n}\n", start)
+    body = src[start:end]
+    assert body.count(old) == 1, (func, old)
+    return src[:start] + body.replace(old, new) + src[end:]
+
+
+@pytest.fixture(scope="module")
+def mutant_dir(tmp_path_factory):
+    return tmp_path_factory.mktemp("oracle_mutants")
+
+
+def build_mutant(directory, name, source):
+    c = os.path.join(str(directory), name + ".c")
+    so = os.path.join(str(directory), "lib" + name + ".so")
+    with open(c, "w") as f:
+        f.write(source)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-ffp-contract=off",
+                    "-fno-fast-math", "-o", so, c, "-lm"], check=True)
+    L = ctypes.CDLL(so)
+    for fn, (res, args) in _lib._SIGS.items():
+        f = getattr(L, fn)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+def test_every_c_site_is_in_the_oracle():
+    src = open(SRC).read()
+    for name, (func, old, new, _) in C_PLANTS.items():
+        assert plant_c(src, func, old, new) != src, name
+
+
+@pytest.mark.parametrize("name", sorted(C_PLANTS))
+def test_planted_c_mistake_fails_its_pin(name, mutant_dir, monkeypatch):
+    func, old, new, pin = C_PLANTS[name]
+    _lib.lib()  # the oracle's own library is built and loaded first
+    L = build_mutant(mutant_dir, name, plant_c(open(SRC).read(), func, old, new))
+    monkeypatch.setattr(_lib, "_lib", L)
+    with pytest.raises(AssertionError):
+        pin()
+
+
+# ---------------------------------------------------------------- Python plants
+def _conjugated_stages(monkeypatch):
+    orig = B.stage_diagonals
+    monkeypatch.setattr(B, "stage_diagonals",
+                        lambda n, h, inverse=False: {o: np.conj(d) for o, d in orig(n, h, inverse).items()})
+
+
+def _giant_step_rotated_the_wrong_way(monkeypatch):
+    orig = B.bsgs_plan
+
+    def bad(diags, n, stride, baby=0):
+        r, groups = orig(diags, n, stride, baby)
+        return r, [(G, [None if v is None else np.roll(v, -2 * G) for v in vals]) for G, vals in groups]
+    monkeypatch.setattr(B, "bsgs_plan", bad)
+
+
+def _series_remainder_uncorrected(monkeypatch):
+    orig = OF.cheb_split
+    monkeypatch.setattr(OF, "cheb_split", lambda c, g: (orig(c, g)[0], list(c[:g])))
+
+
+def _mask_shifted(monkeypatch):
+    orig = OF.build_mask
+    monkeypatch.setattr(OF, "build_mask", lambda sp, ep, w, m, C: np.roll(orig(sp, ep, w, m, C), 1))
+
+
+def _kernel_transposed(monkeypatch):
+    orig = OF.conv_plan
+
+    def bad(*a, **kw):
+        a = list(a)
+        a[10] = np.swapaxes(np.asarray(a[10]), 2, 3)
+        return orig(*a, **kw)
+    monkeypatch.setattr(OF, "conv_plan", bad)
+
+
+def _repack_shift_reversed(monkeypatch):
+    def bad(C, H, W, src, dst, nslots):
+        a = OF.map_slots(C, H, W, *src)
+        b = OF.map_slots(C, H, W, *dst)
+        diags = {}
+        for s_, d_ in zip(a, b):
+            o = int((d_ - s_) % nslots)  # planted: the shift taken the other way
+            diags.setdefault(o, np.zeros(nslots))[int(d_)] = 1.0
+        stride = nslots
+        for o in diags:
+            while stride > 1 and o % stride:
+                stride //= 2
+        return OF.bsgs_plan(diags, nslots, stride)
+    monkeypatch.setattr(OF, "repack_plan", bad)
+
+
+def _raise_uncentred(monkeypatch):
+    def bad(ctx, ct):
+        out = np.zeros((2, ctx.L, ctx.N), dtype=np.uint64)
+        for b in range(2):
+            c = ctx.to_coeff(np.ascontiguousarray(ct[b, :1]), 1)[0].astype(np.int64)  # planted: no centring
+            res = np.stack([(c % int(qi)).astype(np.uint64) for qi in ctx.q])
+            out[b] = ctx.to_eval(res, ctx.L)
+        return out
+    monkeypatch.setattr(B, "mod_raise", bad)
+
+
+def _monomial_sign(monkeypatch):
+    orig = B.monomial
+    monkeypatch.setattr(B, "monomial", lambda ctx, level, sign=1: orig(ctx, level, -sign))
+
+
+@pytest.fixture(scope="module")
+def boot_ctx():
+    P = synth.params("boot_n12")
+    N = 1 << P["logN"]
+    L = len(P["qbits"])
+    pr = ckks.gen_primes(N, P["qbits"] + P["pbits"])
+    ctx = ckks.Ctx(N, pr[:L], pr[L:], P["dnum"], P["seed"])
+    s, se = ctx.keygen_sk()
+    return P, ctx, s, se, ctx.keygen_pk(se), B.Plan(ctx, P["scale"])
+
+
+PY_PLANTS = {
+    "stage_twiddle_conjugated": (_conjugated_stages, lambda bc: TB.test_stages_are_the_slot_transform(16)),
+    "giant_step_prerotation_sign": (_giant_step_rotated_the_wrong_way,
+                                    lambda bc: TB.test_merged_levels_in_bsgs_form(2)),
+    "series_remainder_uncorrected": (_series_remainder_uncorrected, lambda bc: TR.test_series_tree_and_depth()),
+    "alg2_mask_shifted": (_mask_shifted, lambda bc: TF.test_build_mask_worked_case()),
+    "conv_kernel_transposed": (_kernel_transposed,
+                               lambda bc: TL.test_conv_plan_is_the_convolution(1, 3, 3, 0, 6, 8, 1)),
+    "repack_shift_reversed": (_repack_shift_reversed,
+                              lambda bc: TL.test_repack_moves_every_value((16, 2, 256), (8, 1, 64))),
+    "mod_raise_uncentred": (_raise_uncentred, lambda bc: TB.test_mod_raise_is_exact(bc)),
+    "conjugation_monomial_sign": (_monomial_sign, lambda bc: TB.test_bootstrap_encrypted(bc)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PY_PLANTS))
+def test_planted_python_mistake_fails_its_pin(name, monkeypatch, request):
+    plant, pin = PY_PLANTS[name]
+    bc = request.getfixturevalue("boot_ctx") if name in ("mod_raise_uncentred", "conjugation_monomial_sign") else None
+    plant(monkeypatch)
+    with pytest.raises(AssertionError):
+        pin(bc)
