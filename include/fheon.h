@@ -614,15 +614,24 @@ int fheon_server_create(fheon_ctx *ctx, uint32_t max_active, size_t min_free, fh
 int fheon_server_destroy(fheon_server *server);
 /* Queue a request: the model on a copy of `in` (taken on the stream now). */
 int fheon_server_submit(fheon_server *server, const fheon_model *model, const fheon_ct *in, uint64_t *id);
-/* One scheduling step: admit what fits, take the oldest admitted request's
+/* One scheduling step: drop the requests past the admission timeout, admit
+ * what fits, take the oldest admitted request's
  * stage (model, next step), run that step for every admitted request at that
  * stage (a layer step as one batch, fheon_layer_apply_batch), advance them,
- * and wait for the stream.  *n_done: requests that finished in this step.  A result
+ * and wait for the stream.  *n_done: requests that finished (or were
+ * dropped) in this step.  A result
  * equals the model applied to the request's input alone, bit for bit. */
 int fheon_server_step(fheon_server *server, uint32_t *n_done);
 /* The result of request `id` into out (then the request is forgotten), or
- * FHEON_PENDING while it runs; FHEON_ERR_ARG for an unknown id. */
+ * FHEON_PENDING while it runs; FHEON_ERR_ARG for an unknown id;
+ * FHEON_ERR_TIMEOUT (then forgotten) for a request dropped because it waited
+ * longer than the admission timeout. */
 int fheon_server_result(fheon_server *server, uint64_t id, fheon_ct *out);
+/* Admission timeout: a request still waiting `seconds` after its submission
+ * (host clock) is dropped at the next scheduling step, which counts it in
+ * *n_done; its result then reports FHEON_ERR_TIMEOUT.  0 (the default): no
+ * limit.  FHEON_ERR_ARG for a negative, infinite or NaN value. */
+int fheon_server_set_admit_timeout(fheon_server *server, double seconds);
 /* Steps taken, the largest batch so far, requests in flight and waiting. */
 int fheon_server_stats(const fheon_server *server, uint64_t *steps, uint32_t *max_batch, uint32_t *active,
                        uint32_t *waiting);

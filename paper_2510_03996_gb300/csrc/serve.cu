@@ -14,8 +14,12 @@
 // (fheon_layer_apply_batch: their rotations share launches) -- and advances
 // them; requests past their model's last step are done and keep their result
 // until it is taken.  A request's result is the one the model gives its input
-// alone, bit for bit: batching changes launches, never arithmetic.
+// alone, bit for bit: batching changes launches, never arithmetic.  With an
+// admission timeout, a request still waiting that long after its submission
+// is dropped at the next admission and its result reports FHEON_ERR_TIMEOUT.
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <deque>
 #include <map>
 #include <memory>
@@ -40,6 +44,8 @@ struct Request {
     std::vector<fheon_ct *> reg;  // registers
     fheon_ct *nxt = nullptr, *aux = nullptr; // a step's output and an operand copy
     bool done = false;
+    int status = FHEON_OK; // FHEON_ERR_TIMEOUT: dropped before admission
+    std::chrono::steady_clock::time_point submitted;
     ~Request()
     {
         for (fheon_ct *c : reg) fheon_ct_destroy(c);
@@ -70,11 +76,28 @@ struct fheon_server {
     std::map<uint64_t, std::unique_ptr<Request>> all;
     uint64_t next_id = 1, next_seq = 0, steps = 0;
     u32 max_batch = 0;
+    double admit_timeout = 0; // seconds a request may wait for admission; 0: no limit
 };
 
 namespace {
-int admit(fheon_server *s)
+// drop the waiting requests past the admission timeout (counted in *expired),
+// then admit what fits
+int admit(fheon_server *s, u32 *expired)
 {
+    if (s->admit_timeout > 0) {
+        const auto now = std::chrono::steady_clock::now();
+        for (auto it = s->waiting.begin(); it != s->waiting.end();) {
+            Request *r = *it;
+            if (std::chrono::duration<double>(now - r->submitted).count() > s->admit_timeout) {
+                r->done = true;
+                r->status = FHEON_ERR_TIMEOUT;
+                ++*expired;
+                it = s->waiting.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
     while (!s->waiting.empty() && s->active.size() < s->max_active) {
         if (s->min_free) {
             size_t free_b = 0, total_b = 0;
@@ -187,6 +210,7 @@ int fheon_server_submit(fheon_server *s, const fheon_model *m, const fheon_ct *i
     if ((rc = fheon_drop_level(s->ctx, in, in->level, r->reg[0]))) return rc; // the request's own copy
     r->id = s->next_id++;
     r->model = m;
+    r->submitted = std::chrono::steady_clock::now();
     *id = r->id;
     s->waiting.push_back(r.get());
     s->all.emplace(r->id, std::move(r));
@@ -197,7 +221,9 @@ int fheon_server_step(fheon_server *s, uint32_t *n_done)
 {
     if (!s) return FHEON_ERR_ARG;
     if (n_done) *n_done = 0;
-    int rc = admit(s);
+    u32 expired = 0;
+    int rc = admit(s, &expired);
+    if (n_done) *n_done = expired;
     if (rc) return rc;
     if (s->active.empty()) return FHEON_OK;
     const Request *oldest = *std::min_element(s->active.begin(), s->active.end(),
@@ -234,7 +260,7 @@ int fheon_server_step(fheon_server *s, uint32_t *n_done)
     s->active.erase(std::remove_if(s->active.begin(), s->active.end(), [](const Request *r) { return r->done; }),
                     s->active.end());
     if ((rc = fheon_sync(s->ctx))) return rc;
-    if (n_done) *n_done = done;
+    if (n_done) *n_done = done + expired;
     return FHEON_OK;
 }
 
@@ -243,12 +269,24 @@ int fheon_server_result(fheon_server *s, uint64_t id, fheon_ct *out)
     if (!s || !out) return FHEON_ERR_ARG;
     auto it = s->all.find(id);
     if (it == s->all.end()) return fail(s->ctx, FHEON_ERR_ARG, "no request %llu", (unsigned long long)id);
+    if (it->second->status != FHEON_OK) {
+        const int st = it->second->status;
+        s->all.erase(it);
+        return fail(s->ctx, st, "request %llu waited longer than the admission timeout", (unsigned long long)id);
+    }
     if (!it->second->done) return FHEON_PENDING;
     const fheon_ct *r = it->second->reg[0];
     int rc = fheon_drop_level(s->ctx, r, r->level, out);
     if (rc) return rc;
     if ((rc = fheon_sync(s->ctx))) return rc;
     s->all.erase(it);
+    return FHEON_OK;
+}
+
+int fheon_server_set_admit_timeout(fheon_server *s, double seconds)
+{
+    if (!s || !(seconds >= 0) || std::isinf(seconds)) return FHEON_ERR_ARG;
+    s->admit_timeout = seconds;
     return FHEON_OK;
 }
 

@@ -153,6 +153,7 @@ SIGNATURES = {
     "fheon_server_submit": [c_vp, c_vp, c_vp, P(c_u64)],
     "fheon_server_step": [c_vp, P(c_u32)],
     "fheon_server_result": [c_vp, c_u64, c_vp],
+    "fheon_server_set_admit_timeout": [c_vp, c_dbl],
     "fheon_server_stats": [c_vp, P(c_u64), P(c_u32), P(c_u32), P(c_u32)],
     "fheon_layer_rotation_steps": [c_vp, P(c_i32), P(c_u32)],
     "fheon_layer_out_map": [c_vp, P(fheon_map)],
@@ -947,6 +948,9 @@ class Server:
             return None
         self.ctx._chk(rc)
         return out
+
+    def set_admit_timeout(self, seconds):
+        self.ctx._chk(load().fheon_server_set_admit_timeout(self.handle.h, float(seconds)))
 
     def stats(self):
         st, mb, a, w = c_u64(), c_u32(), c_u32(), c_u32()

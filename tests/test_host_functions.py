@@ -38,3 +38,8 @@ def test_allocator_hooks_install_without_a_gpu():
     assert L.fheon_set_allocator(F.ALLOC_FN(lambda n, s, u: None), F.FREE_FN(), None) == -1
     with pytest.raises(F.FheonError):
         F.set_allocator(lambda n, s, u: None)
+
+
+def test_server_timeout_refuses_a_null_server():
+    from paper_2510_03996_gb300 import fheon as F
+    assert F.load().fheon_server_set_admit_timeout(None, 1.0) == -1
