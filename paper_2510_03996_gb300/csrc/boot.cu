@@ -293,11 +293,15 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
         sub->collect = nullptr;
         return r;
     };
-    for (u32 i = 0; i < ly->ncts; i++) {
-        fheon_ct *dst = w[1 + (i & 1)];
-        if ((rc = sub_apply(ly->subs[i], x, dst))) return rc;
-        x = dst;
+    {
+        Range range("CoeffToSlot");
+        for (u32 i = 0; i < ly->ncts; i++) {
+            fheon_ct *dst = w[1 + (i & 1)];
+            if ((rc = sub_apply(ly->subs[i], x, dst))) return rc;
+            x = dst;
+        }
     }
+    Range phase("EvalMod");
     // real and imaginary parts: T_1 of each part's series
     const u32 lv = x->level;
     if ((rc = cheb_work(ctx, ly->rot, D, lv, x->scale))) return rc;
@@ -324,6 +328,7 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
     fheon_ct *part[2] = {a[0], a[1]};
     if ((rc = fheon_mul_plain(ctx, part[1], ly->mono[1], w[9]))) return rc;
     if ((rc = fheon_add(ctx, part[0], w[9], w[9]))) return rc;
+    phase.next("SlotToCoeff");
     x = w[9];
     const u32 nst = (u32)ly->subs.size() - ly->ncts;
     for (u32 i = 0; i < nst; i++) {

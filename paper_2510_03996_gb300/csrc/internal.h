@@ -1,6 +1,7 @@
 // internal.h -- context, handles and device tables of libfheon.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <map>
@@ -73,6 +74,23 @@ struct DevMem {
         owned = true;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// An NVTX range over a scope: names the library's phases (key-switching
+// stages, layers, the bootstrap's steps, server steps) on a profiler's
+// timeline, so that ncu --nvtx can select kernels by phase.  A no-op unless
+// a tool is attached.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    // end this range and open the next phase's
+    void next(const char *name)
+    {
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
 };
 
 // ------------------------------------------------------------ host math

@@ -707,6 +707,7 @@ struct Lists {
 template <bool INV, bool FIRST, class Job>
 int stage(fheon_ctx *ctx, BatchParams P, const Lists &ls, int s, const char *name)
 {
+    Range range(name);
     for (int cls = 0; cls < 2; cls++) {
         if (!ls.n[s][cls]) continue;
         P.tasks = ls.t[s][cls];
@@ -744,6 +745,7 @@ int run_pipeline(fheon_ctx *ctx, const BatchParams &P, const Lists &ls, bool hoi
                 opted.fetch_or(1ull << (dev & 63));
             }
         }
+        Range range("ks_inner");
         for (int cls = 0; cls < 2; cls++) {
             if (!ls.n[ST_UPB][cls]) continue;
             BatchParams Q = P;
@@ -876,6 +878,7 @@ static size_t ks_ws_total(const fheon_ctx *ctx, const KsItem *items, u32 n, std:
 int ks_many(fheon_ctx *ctx, const KsItem *items, uint32_t n, bool hoist, PlanKeep *keep)
 {
     if (n == 0) return FHEON_OK;
+    Range range(hoist ? "key_switch_batch_hoisted" : "key_switch_batch");
     if (n > 65535) return fail(ctx, FHEON_ERR_ARG, "key-switching batch of %u items", n);
     const u32 N = ctx->N;
     std::vector<size_t> ws_off(n);

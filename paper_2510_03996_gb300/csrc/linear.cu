@@ -561,6 +561,8 @@ int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
         if (in_set.count(outs[i])) return fail(ctx, FHEON_ERR_ARG, "layer output %u aliases an input", i);
         if (!out_set.insert(outs[i]).second) return fail(ctx, FHEON_ERR_ARG, "layer output %u repeated", i);
     }
+    static const char *const kind_name[] = {"layer_conv", "layer_relu", "layer_linear", "layer_fc", "layer_bootstrap"};
+    Range range(ly->kind <= LAYER_BOOT ? kind_name[ly->kind] : "layer");
     int rc;
     switch (ly->kind) {
     case LAYER_CONV:

@@ -220,6 +220,7 @@ int fheon_server_submit(fheon_server *s, const fheon_model *m, const fheon_ct *i
 int fheon_server_step(fheon_server *s, uint32_t *n_done)
 {
     if (!s) return FHEON_ERR_ARG;
+    Range range("server_step");
     if (n_done) *n_done = 0;
     u32 expired = 0;
     int rc = admit(s, &expired);
