@@ -293,6 +293,20 @@ def _u64p(a):
     return a.ctypes.data_as(P(c_u64))
 
 
+def _need(ok, what):
+    """Refuse, before any C call, an array whose size the C side would trust."""
+    if not ok:
+        raise FheonError(-1, what)
+
+
+def _bias(bias, n):
+    if bias is None:
+        return None
+    b = np.ascontiguousarray(bias, dtype=np.float64).reshape(-1)
+    _need(b.size == n, "bias needs %d values, got %d" % (n, b.size))
+    return b
+
+
 def _dblp(a):
     return a.ctypes.data_as(P(c_dbl)) if a is not None else None
 
@@ -449,6 +463,7 @@ class Context:
     # plaintexts
     def plain_from_coeffs(self, coeffs, level, scale=1.0):
         c = np.ascontiguousarray(coeffs, dtype=np.int64)
+        _need(c.size == self.N, "plain_from_coeffs needs N = %d coefficients, got %d" % (self.N, c.size))
         h = c_vp()
         self._chk(load().fheon_plain_from_coeffs(self.h, c.ctypes.data_as(P(ctypes.c_int64)), level, scale,
                                                  ctypes.byref(h)))
@@ -508,6 +523,8 @@ class Context:
 
     def ct_upload(self, ct, host):
         host = np.ascontiguousarray(host, dtype=np.uint64)
+        level = self.ct_info(ct)[0]
+        _need(host.size == 2 * level * self.N, "ct_upload needs u64[2][%d][%d]" % (level, self.N))
         self._chk(load().fheon_ct_upload(self.h, ct.h, _u64p(host)))
         return host  # keep alive until synchronised when pinned/asynchronous
 
@@ -647,9 +664,8 @@ class Context:
         return Handle(h, load().fheon_layer_destroy)
 
     def conv_prepare(self, in_map, K, pad, level, in_scale, bias=None, stride=1):
-        K = np.ascontiguousarray(K, dtype=np.float64)
+        K, b = self._conv_weights(in_map, K, bias)
         F, C, k, _ = K.shape
-        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
         h = c_vp()
         self._chk(load().fheon_conv_prepare(self.h, ctypes.byref(self._map(in_map)), F, k, stride, pad, _dblp(K),
                                             _dblp(b) if b is not None else None, level, float(in_scale),
@@ -662,9 +678,24 @@ class Context:
                                                ctypes.byref(h)))
         return Handle(h, load().fheon_layer_destroy)
 
-    def fc_prepare(self, in_map, W, level, in_scale, bias=None):
+    @staticmethod
+    def _conv_weights(in_map, K, bias):
+        K = np.ascontiguousarray(K, dtype=np.float64)
+        m = Context._map(in_map)
+        _need(K.ndim == 4 and K.shape[1] == m.C and K.shape[2] == K.shape[3],
+              "conv kernel must be K[F][%d][k][k], got shape %s" % (m.C, K.shape))
+        return K, _bias(bias, K.shape[0])
+
+    @staticmethod
+    def _fc_weights(in_map, W, bias):
         W = np.ascontiguousarray(W, dtype=np.float64)
-        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        m = Context._map(in_map)
+        _need(W.ndim == 2 and W.shape[1] == m.C * m.H * m.W,
+              "FC weights must be W[m][%d], got shape %s" % (m.C * m.H * m.W, W.shape))
+        return W, _bias(bias, W.shape[0])
+
+    def fc_prepare(self, in_map, W, level, in_scale, bias=None):
+        W, b = self._fc_weights(in_map, W, bias)
         h = c_vp()
         self._chk(load().fheon_fc_prepare(self.h, ctypes.byref(self._map(in_map)), W.shape[0], _dblp(W),
                                           _dblp(b) if b is not None else None, level, float(in_scale),
@@ -693,8 +724,7 @@ class Context:
         return out
 
     def fc(self, ct, in_map, W, bias=None, max_keys=0, out=None):
-        W = np.ascontiguousarray(W, dtype=np.float64)
-        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        W, b = self._fc_weights(in_map, W, bias)
         out = out or self.ct_create(1)
         self._chk(load().fheon_fc(self.h, ct.h, ctypes.byref(self._map(in_map)), W.shape[0], _dblp(W),
                                   _dblp(b) if b is not None else None, max_keys, out.h))
@@ -727,6 +757,7 @@ class Context:
         c = (c_vp * len(cts))(*[x.h.value for x in cts])
         t = (c_vp * len(stc))(*[x.h.value for x in stc])
         cf = np.ascontiguousarray(coeffs, dtype=np.float64)
+        _need(cf.size == params.degree + 1, "EvalMod needs degree + 1 = %d coefficients" % (params.degree + 1))
         h = c_vp()
         self._chk(load().fheon_bootstrap_compose(self.h, ctypes.byref(params), c, t, _dblp(cf), float(in_scale),
                                                  ctypes.byref(h)))
@@ -889,9 +920,14 @@ class Context:
         check(load().fheon_conv2d_rotation_steps(in_ch, k, in_h, in_w, out.ctypes.data_as(P(c_i32)), ctypes.byref(n)))
         return [int(x) for x in out[:n.value]]
 
-    def conv2d_prepare(self, in_ch, k, stride, pad, in_h, in_w, w, bias, level, in_scale):
+    @staticmethod
+    def _conv2d_weights(in_ch, k, w, bias):
         w = np.ascontiguousarray(w, dtype=np.float64)
-        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        _need(w.size == in_ch * k * k, "conv2d weights must be w[%d][%d][%d]" % (in_ch, k, k))
+        return w, _bias(bias, 1)
+
+    def conv2d_prepare(self, in_ch, k, stride, pad, in_h, in_w, w, bias, level, in_scale):
+        w, b = self._conv2d_weights(in_ch, k, w, bias)
         h = c_vp()
         self._chk(load().fheon_conv2d_prepare(self.h, in_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b), level,
                                               in_scale, ctypes.byref(h)))
@@ -915,8 +951,7 @@ class Context:
         return out
 
     def conv2d(self, ct, in_ch, k, stride, pad, in_h, in_w, w, bias=None, out=None):
-        w = np.ascontiguousarray(w, dtype=np.float64)
-        b = np.ascontiguousarray(bias, dtype=np.float64) if bias is not None else None
+        w, b = self._conv2d_weights(in_ch, k, w, bias)
         out = out or self.ct_create(1)
         self._chk(load().fheon_conv2d(self.h, ct.h, in_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b), out.h))
         return out

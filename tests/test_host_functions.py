@@ -43,3 +43,28 @@ def test_allocator_hooks_install_without_a_gpu():
 def test_server_timeout_refuses_a_null_server():
     from paper_2510_03996_gb300 import fheon as F
     assert F.load().fheon_server_set_admit_timeout(None, 1.0) == -1
+
+
+def test_binding_refuses_arrays_of_the_wrong_size():
+    """Sizes the C side would trust are checked before any call: conv kernels
+    against the map's channels, FC weights against the map's values, biases
+    against the outputs, the one-channel conv's weights."""
+    C_ = F.Context
+    m = (2, 5, 5, 8, 1, 64)
+    K, b = C_._conv_weights(m, np.zeros((3, 2, 3, 3)), [0.1, 0.2, 0.3])
+    assert K.shape == (3, 2, 3, 3) and b.size == 3
+    for bad_K, bad_b in ((np.zeros((3, 1, 3, 3)), None), (np.zeros((3, 2, 3, 2)), None),
+                         (np.zeros((3, 2, 3, 3)), [0.1, 0.2]), (np.zeros((2, 3, 3)), None)):
+        with pytest.raises(F.FheonError):
+            C_._conv_weights(m, bad_K, bad_b)
+    W, b = C_._fc_weights(m, np.zeros((4, 50)), np.zeros(4))
+    assert W.shape == (4, 50)
+    for bad_W, bad_b in ((np.zeros((4, 49)), None), (np.zeros(50), None), (np.zeros((4, 50)), np.zeros(3))):
+        with pytest.raises(F.FheonError):
+            C_._fc_weights(m, bad_W, bad_b)
+    w, b = C_._conv2d_weights(3, 5, np.zeros((3, 5, 5)), [0.25])
+    assert w.size == 75 and b.size == 1
+    with pytest.raises(F.FheonError):
+        C_._conv2d_weights(3, 5, np.zeros((2, 5, 5)), None)
+    with pytest.raises(F.FheonError):
+        C_._conv2d_weights(1, 5, np.zeros((5, 5)), [0.1, 0.2])
