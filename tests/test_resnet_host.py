@@ -1,11 +1,13 @@
 """ResNet-20 host side: the package's FP64 forward pass (used to choose the
 ReLU bounds) against the oracle's plain-layer network, the slot maps, and the
 level plan of the encrypted network on a stand-in context that computes only
-levels and maps (every layer is prepared at the level its input has)."""
+levels and maps (every layer is prepared at the level its input has) and
+passes every kernel and weight matrix through the binding's own size checks."""
 import numpy as np
 import pytest
 
 from oracle import fheon as OF
+from paper_2510_03996_gb300 import fheon as F
 from paper_2510_03996_gb300 import resnet as R
 from paper_2510_03996_gb300 import synth
 
@@ -53,6 +55,7 @@ class FakeCtx:
         return 11, 2.0 ** 40
 
     def conv_prepare(self, m, K, pad, level, scale, bias=None, stride=1):
+        F.Context._conv_weights(m, K, bias)
         C, H, W, grid, dil, block = m
         Fo, _, k, _ = K.shape
         Ho, Wo = (H + 2 * pad - k) // stride + 1, (W + 2 * pad - k) // stride + 1
@@ -75,6 +78,7 @@ class FakeCtx:
         return _Layer("pool", level, (C, 1, 1, grid, dil * H, block))
 
     def fc_prepare(self, m, W, level, scale, bias=None):
+        F.Context._fc_weights(m, W, bias)
         self.calls.append(("fc", level))
         return _Layer("fc", level, (1, 1, W.shape[0], W.shape[0], 1, W.shape[0]))
 
