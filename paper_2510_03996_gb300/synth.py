@@ -69,12 +69,6 @@ def small_int_poly(seed, stream, N, bound):
     return rng(seed, stream).integers(-bound, bound + 1, N, dtype=np.int64)
 
 
-def residues_poly(seed, stream, moduli, N):
-    """uint64[len(moduli)][N] with limb i uniform in [0, moduli[i])."""
-    g = rng(seed, stream)
-    return np.stack([g.integers(0, int(q), N, dtype=np.uint64) for q in moduli])
-
-
 def image(seed, stream, shape, dist="uniform01"):
     g = rng(seed, stream)
     if dist == "uniform01":
