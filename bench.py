@@ -148,7 +148,17 @@ class ClockSampler:
             except (ValueError, IndexError):
                 pass
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sm_min_mhz": float(min(sm)) if sm else None}
+
+
+def step_summary(ms):
+    """Median and largest of the intervals (ms) between consecutive steps'
+    completions, and the step whose completion the largest one ends at."""
+    if not ms:
+        return {}
+    k = int(np.argmax(ms))
+    return {"step_ms_median": round(float(np.median(ms)), 3), "step_ms_max": round(float(ms[k]), 3),
+            "slowest_step": k + 1}
 
 
 def dist_env():
@@ -694,19 +704,23 @@ def run_gpu(args, rank, world, local_rank):
             if k >= 2:
                 stream.wait_event(ev_dn[k - 2])  # the outputs of step k-2 are read out
             ctx.rotate_batch(bi, bo, steps)
-            ev_comp[k] = torch.cuda.Event()
+            ev_comp[k] = torch.cuda.Event(enable_timing=True)
             ev_comp[k].record(stream)
             s_dn.wait_event(ev_comp[k])
             ctx.ct_download_many_async(bo, host_out.data_ptr(), s_dn.cuda_stream)
             ev_dn[k] = torch.cuda.Event()
             ev_dn[k].record(s_dn)
         torch.cuda.synchronize()
+        # the key switching of each step ends this long after the previous one's
+        return [ev_comp[k - 1].elapsed_time(ev_comp[k]) for k in range(1, nsteps)]
 
     e2e_steps = max(4, 2 * args.steps)
     e2e_run(2)
-    t0 = time.perf_counter()
-    e2e_run(e2e_steps)
-    e2e_value = replica_rate(len(levels) * e2e_steps, time.perf_counter() - t0, world)
+    with ClockSampler(local_rank) as e2e_clk:
+        t0 = time.perf_counter()
+        e2e_ms = e2e_run(e2e_steps)
+        e2e_secs = time.perf_counter() - t0
+    e2e_value = replica_rate(len(levels) * e2e_steps, e2e_secs, world)
     # the pipelined downloads are the batch's results
     first = host_out[:2 * levels[0] * N].numpy().view(np.uint64).reshape(2, levels[0], N)
     e2e_ok = bool(np.array_equal(first, ctx.ct_download(outs[0])))
@@ -773,7 +787,8 @@ def run_gpu(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps, "pipelined": "one upload and one download per step (contiguous ciphertext "
                                                           "batch) on two copy streams, overlapping the key switching of "
-                                                          "neighbouring steps", "result_matches": e2e_ok},
+                                                          "neighbouring steps", "result_matches": e2e_ok,
+                        "steps_ms": step_summary(e2e_ms), "clocks": e2e_clk.summary()},
                 "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels,
                 "comparisons": comparisons}
         print(json.dumps(line), flush=True)

@@ -61,3 +61,16 @@ def test_reference_pool_steps_every_core():
     finally:
         pool.close()
     assert all(p.exitcode == 0 for p in pool.procs)
+
+
+def test_step_summary_and_clock_summary():
+    s = bench.step_summary([37.5, 37.4, 150.2, 37.6])
+    assert s == {"step_ms_median": 37.55, "step_ms_max": 150.2, "slowest_step": 3}
+    assert bench.step_summary([]) == {}
+    c = bench.ClockSampler(0)
+    c.rows = [["0", "2070", "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+              ["0", "1500", "2070", "1400", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+              ["0", "2070", "2070", "950", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    out = c.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_min_mhz"] == 1500.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
