@@ -68,3 +68,47 @@ def test_binding_refuses_arrays_of_the_wrong_size():
         C_._conv2d_weights(3, 5, np.zeros((2, 5, 5)), None)
     with pytest.raises(F.FheonError):
         C_._conv2d_weights(1, 5, np.zeros((5, 5)), [0.1, 0.2])
+
+
+@pytest.mark.parametrize("C,k,H,W", [(1, 3, 6, 6), (1, 5, 28, 28), (3, 5, 7, 9), (16, 3, 32, 32)])
+def test_conv_rotation_steps_are_the_oracle_taps(C, k, H, W):
+    """The special conv's key list: one step per non-identity tap (the oracle's
+    list, the same set), plus H*W for the channel sum when C > 1."""
+    import ctypes
+    L = F.load()
+    n = ctypes.c_uint32(0)
+    assert L.fheon_conv2d_rotation_steps(C, k, H, W, None, ctypes.byref(n)) == 0
+    out = (ctypes.c_int32 * n.value)()
+    assert L.fheon_conv2d_rotation_steps(C, k, H, W, out, ctypes.byref(n)) == 0
+    want = set(OF.conv_rotation_steps(W, k)) | ({H * W} if C > 1 else set())
+    assert sorted(out) == sorted(want) and len(out) == len(want)
+    assert L.fheon_conv2d_rotation_steps(C, 4, H, W, out, ctypes.byref(n)) == -1  # even kernel
+
+
+def test_context_arguments_refused_before_any_device_work():
+    """fheon_ctx_create's documented argument rules (checked on the host, so
+    they run without a GPU): N a power of two in [2^10, 2^17], moduli prime,
+    = 1 mod 2N, distinct and below 2^60, 1 <= dnum <= nq, digits at most 16."""
+    import ctypes
+    from oracle import ckks as O
+    L = F.load()
+    N = 1 << 12
+    good = O.gen_primes(N, [50, 50, 50, 60])
+    h = ctypes.c_void_p()
+
+    def create(N, q, p, dnum):
+        qa = (ctypes.c_uint64 * len(q))(*q)
+        pa = (ctypes.c_uint64 * len(p))(*p)
+        return L.fheon_ctx_create(N, qa, len(q), pa, len(p), dnum, 2.0 ** 40, 1, None, ctypes.byref(h))
+
+    assert create(N + 1, good[:3], good[3:], 1) == -1                  # not a power of two
+    assert create(1 << 9, good[:3], good[3:], 1) == -1                 # below 2^10
+    assert create(N, good[:3], good[3:], 4) == -1                      # dnum > nq
+    assert create(N, good[:3], good[3:], 0) == -1                      # dnum 0
+    assert create(N, [good[0], good[0], good[1]], good[3:], 1) == -1   # repeated modulus
+    composite = 3 * 2 * N + 1                                          # 24577 = 7 * 3511, = 1 mod 2N
+    assert composite % (2 * N) == 1 and not O.is_prime(composite)
+    assert create(N, [good[0], composite], good[3:], 1) == -1          # not prime
+    big = O.gen_primes(N, [61])
+    assert create(N, good[:2], big, 1) == -1                           # a modulus above 2^60
+    assert create(N, [good[0] + 1], good[3:], 1) == -1                 # even, not 1 mod 2N
