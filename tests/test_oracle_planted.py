@@ -15,6 +15,7 @@ import pytest
 
 import test_oracle_boot as TB
 import test_oracle_fheon as TF
+import test_oracle_hoisted as TH
 import test_oracle_layers as TL
 import test_oracle_mult as TM
 import test_oracle_primitives as PR
@@ -34,6 +35,11 @@ def _tiny():
     ctx, P = S._ctx("tiny")
     s, se = ctx.keygen_sk()
     return ctx, P, s, se, ctx.keygen_pk(se)
+
+
+def _tiny4():
+    ctx, P, s, se, pk = _tiny()
+    return ctx, P, se, pk
 
 
 # name: (C function holding the site, exact text, planted text, the pin that must fail)
@@ -83,6 +89,39 @@ C_PLANTS = {
                         lambda: TR.test_coeffs_are_chebyshev_interpolation(1.0, 59)),
     "evalmod_phase_sign": ("void oracle_cos_cheb_coeffs(", "(K * z - 0.25)", "(K * z + 0.25)",
                            lambda: TB.test_evalmod_series_and_doublings()),
+    "intt_butterfly_sign": ("static void intt_fast(", "mulmod(submod(U, V, q), S, q)", "mulmod(addmod(U, V, q), S, q)",
+                            lambda: PR.test_fast_ntt_equals_definition(6)),
+    "psi_not_minimal": ("u64 oracle_min_psi(", "if (cur < best) best = cur;", "if (cur > best) best = cur;",
+                        lambda: PR.test_min_psi_brute_force(97, 16)),
+    "prime_not_largest": ("int oracle_gen_primes(", "u64 cand = top - ((top - 1) % twoN);",
+                          "u64 cand = top - ((top - 1) % twoN) - twoN;",
+                          lambda: PR.test_gen_primes_are_the_largest_ntt_primes(13, [60, 40, 40, 60])),
+    "ternary_two_values": ("void oracle_sample_ternary(", "% 3) - 1", "% 2) - 1",
+                           lambda: PR.test_samplers_statistics()),
+    "gauss_index_shifted": ("void oracle_sample_gauss(", "out[n] = k;", "out[n] = k + 1;",
+                            lambda: PR.test_samplers_statistics()),
+    "uniform_words_swapped": ("void oracle_sample_uniform(", "(((u128)hi << 64) | lo) % q",
+                              "(((u128)lo << 64) | hi) % q", lambda: PR.test_samplers_statistics()),
+    "automorphism_element_conjugated": ("void oracle_automorph_eval(", "oracle_automorph_coeff(t, N, c->mod[mi], g, t2);",
+                                        "oracle_automorph_coeff(t, N, c->mod[mi], 2ull * N - g, t2);",
+                                        lambda: S.test_rotate_decrypts_to_automorphism(_tiny(), 1)),
+    "hoisted_c0_not_permuted": ("void oracle_rotate_hoisted(", "oracle_automorph_eval(c, ct, level, 0, gs[r], sc0);",
+                                "memcpy(sc0, ct, sizeof(u64) * pl);",
+                                lambda: TH.test_constant_c1_equals_plain_rotation_for_every_g(_tiny4(), 4)),
+    "hoisted_digits_not_permuted": ("void oracle_rotate_hoisted(",
+                                    "oracle_automorph_eval(c, ext + j * limbs, level, 1, gs[r], d);",
+                                    "memcpy(d, ext + j * limbs, sizeof(u64) * limbs);",
+                                    lambda: TH.test_decrypts_to_automorphism_and_differs_from_plain(_tiny4())),
+    "decrypt_sign": ("void oracle_decrypt(", "m[o] = addmod(ct[o], mulmod(", "m[o] = submod(ct[o], mulmod(",
+                     lambda: S.test_encrypt_decrypt_noise_bound(_tiny())),
+    "public_key_sign": ("void oracle_keygen_pk(", "addmod(submod(0, mulmod(a[k], s_eval[(size_t)i * N + k], q), q)",
+                        "addmod(mulmod(a[k], s_eval[(size_t)i * N + k], q)",
+                        lambda: S.test_public_key_relation(_tiny())),
+    "mul_int_sign": ("void oracle_mul_int(", "vm = from_signed(v, q);", "vm = from_signed(-v, q);",
+                     lambda: TM.test_mul_int_and_add_int_are_exact(_tiny())),
+    "add_int_into_c1": ("void oracle_add_int(", "out[o] = addmod(ct[o], vm, q);\n            out[pl + o] = ct[pl + o];",
+                        "out[o] = ct[o];\n            out[pl + o] = addmod(ct[pl + o], vm, q);",
+                        lambda: TM.test_mul_int_and_add_int_are_exact(_tiny())),
 }
 
 
@@ -195,6 +234,20 @@ def _raise_uncentred(monkeypatch):
     monkeypatch.setattr(B, "mod_raise", bad)
 
 
+def _pool_mask_one_over_k(monkeypatch):
+    orig = OF.avgpool_plan
+
+    def bad(C, k, stride, H, W, grid, dil, block, nslots):
+        r, groups = orig(C, k, stride, H, W, grid, dil, block, nslots)
+        return r, [(G, [None if v is None else v * k for v in vals]) for G, vals in groups]  # 1/k, not 1/k^2
+    monkeypatch.setattr(OF, "avgpool_plan", bad)
+
+
+def _fold_rotated_the_wrong_way(monkeypatch):
+    orig = OF.fold_slots
+    monkeypatch.setattr(OF, "fold_slots", lambda v, fold: orig(v, [-f for f in fold]))
+
+
 def _monomial_sign(monkeypatch):
     orig = B.monomial
     monkeypatch.setattr(B, "monomial", lambda ctx, level, sign=1: orig(ctx, level, -sign))
@@ -222,6 +275,10 @@ PY_PLANTS = {
     "repack_shift_reversed": (_repack_shift_reversed,
                               lambda bc: TL.test_repack_moves_every_value((16, 2, 256), (8, 1, 64))),
     "mod_raise_uncentred": (_raise_uncentred, lambda bc: TB.test_mod_raise_is_exact(bc)),
+    "pool_mask_one_over_k": (_pool_mask_one_over_k,
+                             lambda bc: TL.test_avgpool_plan_is_average_pooling(2, 2, 2, 8, 8, 1)),
+    "fold_rotation_sign": (_fold_rotated_the_wrong_way,
+                           lambda bc: TL.test_fc_diag_plan_is_the_product(16, 4, 28, 4, 12)),
     "conjugation_monomial_sign": (_monomial_sign, lambda bc: TB.test_bootstrap_encrypted(bc)),
 }
 
