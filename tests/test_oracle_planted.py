@@ -248,6 +248,40 @@ def _fold_rotated_the_wrong_way(monkeypatch):
     monkeypatch.setattr(OF, "fold_slots", lambda v, fold: orig(v, [-f for f in fold]))
 
 
+def _kernel_read_transposed(monkeypatch):
+    def bad(x, H, W, C, K, k):
+        n = len(x)
+        p = (k - 1) // 2
+        acc = np.zeros(n)
+        for (di, dj) in OF.taps(k):
+            vec = np.zeros(n)
+            for c in range(C):  # planted: the kernel read at (dj, di)
+                vec[c * H * W:(c + 1) * H * W] = K[c, dj + p, di + p] * OF.tap_mask(H, W, 1, di, dj)
+            acc += vec * OF.rot_slots(x, di * W + dj)
+        tot, cur = acc.copy(), acc
+        for _ in range(C - 1):
+            cur = OF.rot_slots(cur, H * W)
+            tot = tot + cur
+        out = np.zeros(n)
+        out[:H * W] = tot[:H * W]
+        return out
+    monkeypatch.setattr(OF, "special_conv_slots", bad)
+
+
+def _doubling_without_minus_one(monkeypatch):
+    def bad(x, K, r, D=B.BOOT_DEGREE):
+        c = OF.cheb_eval_fp64(B.evalmod_coeffs(K, r, D), x)
+        for _ in range(r):
+            c = 2.0 * c * c  # planted: the -1 of cos(2a) = 2 cos(a)^2 - 1 dropped
+        return c
+    monkeypatch.setattr(B, "evalmod_fp64", bad)
+
+
+def _stage_groups_reversed(monkeypatch):
+    orig = B.stage_groups
+    monkeypatch.setattr(B, "stage_groups", lambda logn, levels: list(reversed(orig(logn, levels))))
+
+
 def _monomial_sign(monkeypatch):
     orig = B.monomial
     monkeypatch.setattr(B, "monomial", lambda ctx, level, sign=1: orig(ctx, level, -sign))
@@ -272,6 +306,11 @@ PY_PLANTS = {
     "alg2_mask_shifted": (_mask_shifted, lambda bc: TF.test_build_mask_worked_case()),
     "conv_kernel_transposed": (_kernel_transposed,
                                lambda bc: TL.test_conv_plan_is_the_convolution(1, 3, 3, 0, 6, 8, 1)),
+    "special_conv_kernel_transposed": (_kernel_read_transposed,
+                                     lambda bc: TF.test_special_conv_slots_equals_fp64_same_conv(5, 3, 7, 9)),
+    "evalmod_doubling_minus_one_dropped": (_doubling_without_minus_one,
+                                           lambda bc: TB.test_evalmod_series_and_doublings()),
+    "stage_groups_out_of_order": (_stage_groups_reversed, lambda bc: TB.test_stage_groups_cover_every_stage()),
     "repack_shift_reversed": (_repack_shift_reversed,
                               lambda bc: TL.test_repack_moves_every_value((16, 2, 256), (8, 1, 64))),
     "mod_raise_uncentred": (_raise_uncentred, lambda bc: TB.test_mod_raise_is_exact(bc)),
