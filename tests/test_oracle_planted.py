@@ -119,6 +119,21 @@ C_PLANTS = {
                         lambda: S.test_public_key_relation(_tiny())),
     "mul_int_sign": ("void oracle_mul_int(", "vm = from_signed(v, q);", "vm = from_signed(-v, q);",
                      lambda: TM.test_mul_int_and_add_int_are_exact(_tiny())),
+    "ntt_definition_natural_order": ("void oracle_ntt_def(", "powmod(psi, 2ull * brv(j, logn) + 1, q)",
+                                     "powmod(psi, 2ull * j + 1, q)",
+                                     lambda: PR.test_ntt_definition_brute_force(97, 16)),
+    "schoolbook_wrap_sign": ("void oracle_negacyclic_mul(", "else out[i + j - N] = submod(out[i + j - N], p, q);",
+                             "else out[i + j - N] = addmod(out[i + j - N], p, q);",
+                             lambda: PR.test_convolution_theorem()),
+    "draw_block_counter": ("u64 oracle_draw64(", "(u32)(n / 8)", "(u32)(n / 16)",
+                           lambda: PR.test_draw64_is_word_pair_of_block()),
+    "secret_key_one_modulus": ("void oracle_keygen_sk(", "midx[i] = i;", "midx[i] = 0;",
+                               lambda: S.test_secret_key_is_ternary_and_consistent(_tiny())),
+    "mul_plain_c1_skipped": ("void oracle_mul_plain(", "out[b * pl + o] = mulmod(ct[b * pl + o], pt[o], c->mod[i]);",
+                             "out[b * pl + o] = b ? ct[b * pl + o] : mulmod(ct[b * pl + o], pt[o], c->mod[i]);",
+                             lambda: S.test_add_and_mul_plain_exact(_tiny())),
+    "add_subtracts": ("void oracle_add(", "out[o] = addmod(x[o], y[o], c->mod[i]);",
+                      "out[o] = submod(x[o], y[o], c->mod[i]);", lambda: S.test_add_and_mul_plain_exact(_tiny())),
     "add_int_into_c1": ("void oracle_add_int(", "out[o] = addmod(ct[o], vm, q);\n            out[pl + o] = ct[pl + o];",
                         "out[o] = ct[o];\n            out[pl + o] = addmod(ct[pl + o], vm, q);",
                         lambda: TM.test_mul_int_and_add_int_are_exact(_tiny())),
