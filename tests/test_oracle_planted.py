@@ -134,6 +134,14 @@ C_PLANTS = {
                              lambda: S.test_add_and_mul_plain_exact(_tiny())),
     "add_subtracts": ("void oracle_add(", "out[o] = addmod(x[o], y[o], c->mod[i]);",
                       "out[o] = submod(x[o], y[o], c->mod[i]);", lambda: S.test_add_and_mul_plain_exact(_tiny())),
+    "miller_rabin_one_base": ("int oracle_is_prime(", "for (int i = 0; i < 12; i++) {\n        u64 x",
+                              "for (int i = 0; i < 1; i++) {\n        u64 x", lambda: PR.test_is_prime_against_sympy()),
+    "add_plain_into_c1": ("void oracle_add_plain(",
+                          "out[o] = addmod(ct[o], pt[o], c->mod[i]);\n            out[pl + o] = ct[pl + o];",
+                          "out[o] = ct[o];\n            out[pl + o] = addmod(ct[pl + o], pt[o], c->mod[i]);",
+                          lambda: S.test_add_and_mul_plain_exact(_tiny())),
+    "tensor_d0_dropped": ("void oracle_mul_relin(", "d[o] = mulmod(a[o], b[o], q);", "d[o] = 0;",
+                          lambda: TM.test_mul_relin_decrypts_to_the_product(_tiny(), 3)),
     "add_int_into_c1": ("void oracle_add_int(", "out[o] = addmod(ct[o], vm, q);\n            out[pl + o] = ct[pl + o];",
                         "out[o] = ct[o];\n            out[pl + o] = addmod(ct[pl + o], vm, q);",
                         lambda: TM.test_mul_int_and_add_int_are_exact(_tiny())),
