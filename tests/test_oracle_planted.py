@@ -77,6 +77,8 @@ C_PLANTS = {
     "encrypt_message_dropped": ("void oracle_encrypt(", "addmod(addmod(mulmod(V[o], pk[o], q), E0[o], q), M[o], q)",
                                 "addmod(mulmod(V[o], pk[o], q), E0[o], q)",
                                 lambda: S.test_encrypt_decrypt_noise_bound(_tiny())),
+    "encode_truncates": ("int oracle_encode(", "double r = round(v);", "double r = trunc(v);",
+                         lambda: S.test_encode_rounds_half_away_from_zero()),
     "encode_conjugated": ("int oracle_encode(", "acc += zr[i] * cs[e] - zi[i] * sn[e];",
                           "acc += zr[i] * cs[e] + zi[i] * sn[e];", lambda: S.test_encode_decode_roundtrip(64)),
     "decode_sign": ("void oracle_decode(", "ai += m[k] * sn[e];", "ai -= m[k] * sn[e];",

@@ -279,6 +279,16 @@ def test_encode_decode_roundtrip(N):
     assert np.max(np.abs(back - z)) <= N / 2 / scale
 
 
+def test_encode_rounds_half_away_from_zero():
+    """A constant slot vector z encodes to m_0 = scale * z exactly (every other
+    coefficient 0), so the rounding rule shows: half away from zero (2.5 -> 3,
+    -2.5 -> -3), to nearest otherwise (2.7 -> 3, 2.4 -> 2, -2.7 -> -3)."""
+    N = 64
+    for v, want in ((2.5, 3), (-2.5, -3), (2.7, 3), (2.4, 2), (-2.7, -3), (0.5, 1), (-0.5, -1)):
+        m = ckks.encode(np.full(N // 2, v), N, 1.0)
+        assert int(m[0]) == want and np.all(m[1:] == 0), (v, m[0])
+
+
 def test_encode_constant_and_partial_slots():
     N = 128
     m = ckks.encode(np.full(N // 2, 0.75), N, 2.0 ** 20)
