@@ -307,6 +307,26 @@ def _stage_groups_reversed(monkeypatch):
     monkeypatch.setattr(B, "stage_groups", lambda logn, levels: list(reversed(orig(logn, levels))))
 
 
+def _crt_not_centred(monkeypatch):
+    def bad(residues, moduli):
+        Q = 1
+        for q in moduli:
+            Q *= int(q)
+        out = []
+        for k in range(residues.shape[1]):
+            x = 0
+            for q, row in zip(moduli, residues):
+                Qh = Q // int(q)
+                x += int(row[k]) * Qh * pow(Qh, -1, int(q))
+            out.append(x % Q)  # planted: the lift left in [0, Q), not centred
+        return out
+    monkeypatch.setattr(ckks, "crt_centered", bad)
+
+
+def _galois_generator_3(monkeypatch):
+    monkeypatch.setattr(ckks, "galois_elt", lambda r, N: pow(3, r % (N // 2), 2 * N))
+
+
 def _monomial_sign(monkeypatch):
     orig = B.monomial
     monkeypatch.setattr(B, "monomial", lambda ctx, level, sign=1: orig(ctx, level, -sign))
@@ -336,6 +356,8 @@ PY_PLANTS = {
     "evalmod_doubling_minus_one_dropped": (_doubling_without_minus_one,
                                            lambda bc: TB.test_evalmod_series_and_doublings()),
     "stage_groups_out_of_order": (_stage_groups_reversed, lambda bc: TB.test_stage_groups_cover_every_stage()),
+    "crt_lift_not_centred": (_crt_not_centred, lambda bc: S.test_encrypt_decrypt_noise_bound(_tiny())),
+    "galois_generator_3": (_galois_generator_3, lambda bc: S.test_rotate_moves_slots()),
     "repack_shift_reversed": (_repack_shift_reversed,
                               lambda bc: TL.test_repack_moves_every_value((16, 2, 256), (8, 1, 64))),
     "mod_raise_uncentred": (_raise_uncentred, lambda bc: TB.test_mod_raise_is_exact(bc)),
