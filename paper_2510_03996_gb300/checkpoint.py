@@ -64,6 +64,20 @@ def read_header(path):
     return meta, len(MAGIC) + 8 + n
 
 
+def _write_atomically(path, body):
+    """body(f) writes the file through a temporary beside it, which replaces
+    `path` only when body returns; on any error it is removed."""
+    tmp = path + ".tmp"
+    try:
+        with open(tmp, "wb") as f:
+            body(f)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.remove(tmp)
+        raise
+
+
 def key_shape(meta):
     return (meta["beta"], 2, meta["L"] + meta["K"], meta["N"])
 
@@ -90,8 +104,8 @@ def write_keys(path, meta, items):
     generator, and its Galois elements are listed in `meta["galois"]`."""
     meta = dict(meta, kind="keys")
     shape = key_shape(meta)
-    tmp = path + ".tmp"
-    with open(tmp, "wb") as f:
+
+    def body(f):
         write_header(f, meta)
         seen = []
         for g, a in items:
@@ -100,10 +114,9 @@ def write_keys(path, meta, items):
                 raise CheckpointError("key %d has shape %s, not %s" % (g, a.shape, shape))
             f.write(a.tobytes())
             seen.append(int(g))
-    if seen != [int(g) for g in meta["galois"]]:
-        os.remove(tmp)
-        raise CheckpointError("keys written %s differ from the header's list %s" % (seen, meta["galois"]))
-    os.replace(tmp, path)
+        if seen != [int(g) for g in meta["galois"]]:
+            raise CheckpointError("keys written %s differ from the header's list %s" % (seen, meta["galois"]))
+    _write_atomically(path, body)
 
 
 def iter_keys(path, moduli=None):
@@ -129,11 +142,11 @@ def write_ct(path, meta, limbs):
     meta = dict(meta, kind="ciphertext")
     if a.shape != (2, meta["level"], meta["N"]):
         raise CheckpointError("ciphertext shape %s, header says (2, %d, %d)" % (a.shape, meta["level"], meta["N"]))
-    tmp = path + ".tmp"
-    with open(tmp, "wb") as f:
+
+    def body(f):
         write_header(f, meta)
         f.write(a.tobytes())
-    os.replace(tmp, path)
+    _write_atomically(path, body)
 
 
 def read_ct(path):

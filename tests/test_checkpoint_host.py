@@ -3,6 +3,8 @@ bit for bit, the payload is 8-byte aligned, and corrupt, truncated or
 foreign files are refused (residue at or above its modulus, bad magic,
 short payload, another context's moduli).  The context is a stand-in that
 stores keys in a dict, so the save/load logic runs without a GPU."""
+import os
+
 import numpy as np
 import pytest
 
@@ -132,3 +134,16 @@ def test_ciphertext_round_trip(tmp_path):
     CK.write_ct(path, {"N": 16, "level": 2, "scale": scale, "moduli": MODS[:2]}, limbs)
     with pytest.raises(CK.CheckpointError):
         CK.read_ct(path)
+
+
+def test_a_failed_save_leaves_no_file(tmp_path):
+    ctx = FakeCtx()
+    ctx.keys[5] = random_limbs(4, (ctx.beta, 2, ctx.L + ctx.K, ctx.N), MODS, 2)
+
+    def broken(g):
+        raise RuntimeError("download failed")
+    ctx.key_download = broken
+    path = str(tmp_path / "k.ck")
+    with pytest.raises(RuntimeError):
+        CK.save_keys(ctx, path)
+    assert os.listdir(str(tmp_path)) == []
