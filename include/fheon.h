@@ -116,6 +116,20 @@ int fheon_ctx_create_bits(uint32_t N, const uint32_t *qbits, uint32_t nq, const 
                           uint32_t np, uint32_t dnum, double scale, uint64_t seed, void *stream,
                           fheon_ctx **out);
 int fheon_ctx_destroy(fheon_ctx *ctx);
+/* Host-only parameter calls (no device, no context).  The moduli
+ * fheon_ctx_create_bits picks for these bit sizes, in order, into out[n]:
+ * for each size, the largest unused prime below 2^bits that is 1 mod 2N.
+ * FHEON_ERR_ARG for N outside the supported powers of two, a size outside
+ * [20, 61], or a size with no such prime. */
+int fheon_pick_primes(uint32_t N, const uint32_t *bits, uint32_t n, uint64_t *out);
+/* The NTT's root for modulus q: the smallest primitive 2N-th root of unity
+ * mod q (the minimum over the odd powers of any one).  0 when q is not a
+ * prime = 1 mod 2N or N not a power of two. */
+uint64_t fheon_min_root(uint64_t q, uint32_t N);
+/* The discrete Gaussian sampler's table (sigma 3.2, tail 20): out[k + 20] =
+ * floor(2^64 * sum_{i <= k} rho(i) / sum rho) for k < 20, rho(k) =
+ * exp(-k^2 / (2 sigma^2)) in binary64, out[40] = 0; n must be 41. */
+int fheon_gaussian_cdt(uint64_t *out, uint32_t n);
 /* N, L (= nq), K (= np), alpha (limbs per digit), beta (digits at level L). */
 int fheon_ctx_info(const fheon_ctx *ctx, uint32_t *N, uint32_t *L, uint32_t *K, uint32_t *alpha,
                    uint32_t *beta);

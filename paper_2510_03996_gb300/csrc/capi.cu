@@ -122,6 +122,33 @@ int fheon_set_allocator(fheon_alloc_fn alloc, fheon_free_fn free_fn, void *user)
     return FHEON_OK;
 }
 
+// ------------------------------------------------------------------ parameters (host only)
+int fheon_pick_primes(uint32_t N, const uint32_t *bits, uint32_t n, uint64_t *out)
+{
+    if (!bits || !out || !n || N < 1024 || N > (1u << 17) || (N & (N - 1))) return FHEON_ERR_ARG;
+    std::vector<u32> b(bits, bits + n);
+    std::vector<u64> m;
+    if (!h_pick_primes(N, b, m)) return FHEON_ERR_ARG;
+    for (u32 i = 0; i < n; i++) out[i] = m[i];
+    return FHEON_OK;
+}
+
+uint64_t fheon_min_root(uint64_t q, uint32_t N)
+{
+    // the search below ends only for a prime q = 1 mod 2N
+    if (N < 2 || (N & (N - 1)) || q < 3 || q % (2ull * N) != 1 || !h_is_prime(q)) return 0;
+    return h_min_root(q, N);
+}
+
+int fheon_gaussian_cdt(uint64_t *out, uint32_t n)
+{
+    if (!out || n != 41) return FHEON_ERR_ARG;
+    u64 T[41];
+    h_cdt_table(3.2, 20, T);
+    for (u32 i = 0; i < 41; i++) out[i] = T[i];
+    return FHEON_OK;
+}
+
 // ------------------------------------------------------------------ context
 static int upload(fheon_ctx *ctx, DevMem &m, const void *host, size_t bytes)
 {

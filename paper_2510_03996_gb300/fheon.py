@@ -66,6 +66,9 @@ SIGNATURES = {
     "fheon_ctx_create": [c_u32, P(c_u64), c_u32, P(c_u64), c_u32, c_u32, c_dbl, c_u64, c_vp, c_vpp],
     "fheon_ctx_create_bits": [c_u32, P(c_u32), c_u32, P(c_u32), c_u32, c_u32, c_dbl, c_u64, c_vp, c_vpp],
     "fheon_ctx_destroy": [c_vp],
+    "fheon_pick_primes": [c_u32, P(c_u32), c_u32, P(c_u64)],
+    "fheon_min_root": [c_u64, c_u32],
+    "fheon_gaussian_cdt": [P(c_u64), c_u32],
     "fheon_ctx_info": [c_vp, P(c_u32), P(c_u32), P(c_u32), P(c_u32), P(c_u32)],
     "fheon_ctx_moduli": [c_vp, P(c_u64)],
     "fheon_ctx_set_stream": [c_vp, c_vp],
@@ -179,6 +182,7 @@ SIGNATURES = {
     "fheon_profile_end": [c_vp, ctypes.c_char_p, c_sz],
 }
 _RESTYPE = {"fheon_error_string": ctypes.c_char_p, "fheon_last_error": ctypes.c_char_p, "fheon_galois_elt": c_u64,
+            "fheon_min_root": c_u64,
             "fheon_cheb_depth": c_u32}
 
 _lib = None
@@ -232,6 +236,25 @@ def __getattr__(name):
 # through the pair that allocated it.
 _hooks = []
 _hook_device = None
+
+
+def pick_primes(N, bits):
+    """The moduli a context of these bit sizes gets (host only)."""
+    b = np.ascontiguousarray(bits, dtype=np.uint32)
+    out = np.zeros(len(b), dtype=np.uint64)
+    check(load().fheon_pick_primes(int(N), b.ctypes.data_as(P(c_u32)), len(b), _u64p(out)))
+    return [int(x) for x in out]
+
+
+def min_root(q, N):
+    """The NTT's root for modulus q (0: q is not a prime = 1 mod 2N)."""
+    return int(load().fheon_min_root(int(q), int(N)))
+
+
+def gaussian_cdt():
+    out = np.zeros(41, dtype=np.uint64)
+    check(load().fheon_gaussian_cdt(_u64p(out), 41))
+    return out
 
 
 def cheb_depth(degree):

@@ -112,3 +112,37 @@ def test_context_arguments_refused_before_any_device_work():
     big = O.gen_primes(N, [61])
     assert create(N, good[:2], big, 1) == -1                           # a modulus above 2^60
     assert create(N, [good[0] + 1], good[3:], 1) == -1                 # even, not 1 mod 2N
+
+
+@pytest.mark.parametrize("name", ["small_n12", "relu_n12", "boot_n12", "conv_n13", "lenet_n15", "rot_n16",
+                                  "resnet_n16"])
+def test_parameters_picked_on_the_host_are_the_oracles(name):
+    """Every parameter set: the library's moduli and NTT roots (host code,
+    no device) equal the oracle's, which are written independently."""
+    from oracle import ckks as O
+    from paper_2510_03996_gb300 import synth
+    P = synth.params(name)
+    N = 1 << P["logN"]
+    bits = P["qbits"] + P["pbits"]
+    mods = F.pick_primes(N, bits)
+    assert mods == [int(x) for x in O.gen_primes(N, bits)]
+    for q in mods[:6] + mods[-2:]:
+        assert F.min_root(q, N) == O.min_psi(q, N)
+
+
+def test_root_and_prime_arguments():
+    from oracle import ckks as O
+    N = 1 << 12
+    q = F.pick_primes(N, [50])[0]
+    assert F.min_root(q + 2 * N, N) == 0 or O.is_prime(q + 2 * N)   # not prime: refused, no search
+    assert F.min_root(q + 2, N) == 0                                 # not 1 mod 2N
+    assert F.min_root(q, N + 1) == 0
+    with pytest.raises(F.FheonError):
+        F.pick_primes(N + 1, [50])
+    with pytest.raises(F.FheonError):
+        F.pick_primes(N, [62])
+
+
+def test_gaussian_table_is_the_oracles():
+    from oracle import ckks as O
+    assert np.array_equal(F.gaussian_cdt(), np.asarray(O.cdt_table(3.2, 20), dtype=np.uint64))
