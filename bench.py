@@ -48,44 +48,60 @@ def peaks():
 TRAFFIC_OVER_MIN = {"up_bconv_ntt_cols": 899.91 / 895.5}
 
 
-def algorithmic_costs(N, L, K, alpha, level):
+def algorithmic_costs(N, L, K, alpha, level, q_lazy=True, p_lazy=False):
     """Algorithmic work of one rotation at `level`, in total and per kernel.
 
     bytes: what must cross HBM at least once (key + ciphertext in and out).
-    Per kernel: 'mm' = 64-bit modular products (one per NTT butterfly, one
-    per base-conversion multiply-accumulate), or 'bytes' for the streaming
-    key inner product.  Pass A of a size-N transform covers log2(N)/2 stages
+    Per kernel: 'mm' = 64-bit modular products by kind (one per NTT butterfly
+    -- forward 'ct' or inverse 'gs', 'lazy' on primes below 2^54 (q_lazy for
+    the Q primes, p_lazy for the P primes) else 'harvey' -- and one 'mac' per
+    base-conversion multiply-accumulate), or 'bytes' for the streaming key
+    inner product.  Pass A of a size-N transform covers log2(N)/2 stages
     (floor), pass B the rest."""
     beta = (level + alpha - 1) // alpha
     limb = 8 * N
     logN = N.bit_length() - 1
     b1, b2 = logN // 2, logN - logN // 2
     half = N // 2
+    qk, pk = ("lazy" if q_lazy else "harvey"), ("lazy" if p_lazy else "harvey")
     key_bytes = 2 * beta * (level + K) * limb
     ct_bytes = 4 * level * limb  # read (c0, c1), write (c0', c1')
-    new_limbs = beta * (level + K) - level
+    new_q = beta * level - level  # raised Q limbs (every digit's other Q limbs)
+    new_p = beta * K              # raised P limbs
+    new_limbs = new_q + new_p
     digits = [min(alpha, level - j * alpha) for j in range(beta)]
     modup_macs = N * sum(d * (level + K - d) for d in digits)
+
+    def mm(**kw):
+        return {k: v for k, v in kw.items() if v}
+
     k = {
-        "ic_intt_rows": {"mm": level * half * b2},
-        "ic_intt_cols": {"mm": level * half * b1},
+        "ic_intt_rows": {"mm": mm(**{"gs_" + qk: level * half * b2})},
+        "ic_intt_cols": {"mm": mm(**{"gs_" + qk: level * half * b1})},
         # both prime-class launches read every source limb
-        "up_bconv_ntt_cols": {"mm": new_limbs * half * b1 + modup_macs, "min_bytes": (2 * level + new_limbs) * limb},
-        "up_ntt_rows": {"mm": new_limbs * half * b2},
-        "up_ntt_rows_keyip": {"mm": new_limbs * half * b2 + 2 * beta * (level + K) * N},
+        "up_bconv_ntt_cols": {"mm": mm(**{"ct_" + qk: new_q * half * b1}, **{"ct_" + pk: new_p * half * b1},
+                                       mac=modup_macs) if qk != pk else
+                              mm(**{"ct_" + qk: new_limbs * half * b1}, mac=modup_macs),
+                              "min_bytes": (2 * level + new_limbs) * limb},
+        "up_ntt_rows": {"mm": mm(**{"ct_" + qk: new_q * half * b2}, **{"ct_" + pk: new_p * half * b2})
+                        if qk != pk else mm(**{"ct_" + qk: new_limbs * half * b2})},
         "ks_inner": {"bytes": key_bytes + beta * (level + K) * limb + 2 * (level + K) * limb,
                      "min_bytes": key_bytes + beta * (level + K) * limb + 2 * (level + K) * limb},
-        "dn_intt_rows": {"mm": 2 * K * half * b2},
-        "dn_intt_cols": {"mm": 2 * K * half * b1},
-        "dn_bconv_ntt_cols": {"mm": 2 * level * half * b1 + 2 * level * K * N},
-        "dn_ntt_rows_combine": {"mm": 2 * level * half * b2},
+        "dn_intt_rows": {"mm": mm(**{"gs_" + pk: 2 * K * half * b2})},
+        "dn_intt_cols": {"mm": mm(**{"gs_" + pk: 2 * K * half * b1})},
+        "dn_bconv_ntt_cols": {"mm": mm(**{"ct_" + qk: 2 * level * half * b1}, mac=2 * level * K * N)},
+        "dn_ntt_rows_combine": {"mm": mm(**{"ct_" + qk: 2 * level * half * b2})},
     }
     return dict(bytes=key_bytes + ct_bytes, kernels=k)
 
 
-def rooflines(prof, costs, steps, hbm_peak, mm_peak):
-    """Per-kernel achieved rate against its roofline: ALU kernels in T modular
-    products/s against mm_peak, the inner product in GB/s against hbm_peak."""
+def rooflines(prof, costs, steps, hbm_peak, alu_rates):
+    """Per-kernel achieved rate against its roofline.  The inner product: GB/s
+    against hbm_peak.  ALU kernels: their modular products by kind; the
+    shortest time they can take is sum_kind n_kind / rate_kind at the
+    measured rates (alu_rates, steps/s), so frac = that time / the measured
+    time, achieved = products / measured time and peak = products / shortest
+    time, both in T modular products/s."""
     out = {}
     for name, (n, ms) in prof.items():
         if ms <= 0:
@@ -95,8 +111,16 @@ def rooflines(prof, costs, steps, hbm_peak, mm_peak):
             a = sum(w.get("bytes", 0) for w in work) * steps / (ms / 1e3) / 1e9
             out[name] = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak}
         elif any("mm" in w for w in work):
-            a = sum(w.get("mm", 0) for w in work) * steps / (ms / 1e3) / 1e12
-            out[name] = {"bound": "alu", "achieved": a, "peak": mm_peak, "unit": "Tmodmul/s", "frac": a / mm_peak}
+            tot = {}
+            for w in work:
+                for kind, v in w.get("mm", {}).items():
+                    tot[kind] = tot.get(kind, 0) + v * steps
+            prods = sum(tot.values())
+            t_min = sum(v / alu_rates[kind] for kind, v in tot.items())
+            a = prods / (ms / 1e3) / 1e12
+            peak = prods / t_min / 1e12
+            out[name] = {"bound": "alu", "achieved": a, "peak": peak, "unit": "Tmodmul/s", "frac": a / peak,
+                         "mix": {k: round(v / prods, 4) for k, v in sorted(tot.items())}}
         out.get(name, {}).update({"launches": n, "avg_launch_ms": ms / n})
     return out
 
@@ -644,6 +668,10 @@ def run_gpu(args, rank, world, local_rank):
     def step():
         ctx.rotate_batch(ins, outs, steps)
 
+    # integer peaks of this GPU: the rate of each modular step the ALU-bound
+    # kernels are built from (fheon_alu_peak), the denominators of their rooflines
+    alu_rates = {k: ctx.alu_peak(k) for k in F.Context.PEAK_KINDS}
+
     if args.schedule < 0:
         # the library's autotuner picks the key-switching schedule for this batch
         schedule, tune_ms = ctx.autotune_schedule(ins, outs, steps, reps=2)
@@ -659,16 +687,27 @@ def run_gpu(args, rank, world, local_rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         torch.cuda.synchronize()
-        ctx.profile_begin()
         torch.cuda.nvtx.range_push("timed")
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         torch.cuda.nvtx.range_pop()
-        prof = ctx.profile_end()
         torch.cuda.synchronize()
     ms_total = ev0.elapsed_time(ev1)
+    # per-kernel times: the same steps once more, with a CUDA event recorded
+    # after every launch on the launching stream (the headline above runs
+    # without that instrumentation)
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ctx.profile_begin()
+    ev2.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev3.record(stream)
+    prof = ctx.profile_end()
+    torch.cuda.synchronize()
+    ms_profiled = ev2.elapsed_time(ev3)
     value = replica_rate(len(levels) * args.steps, ms_total / 1e3, world)
     ms_total = barrier_max(ms_total, world)
     ms_step = ms_total / args.steps
@@ -728,11 +767,10 @@ def run_gpu(args, rank, world, local_rank):
     # roofline of the dominant kernel, from the live per-launch events
     pk_, src = peaks()
     launches = sum(v[0] for v in prof.values())
-    costs = [algorithmic_costs(N, ctx.L, ctx.K, ctx.alpha, lv) for lv in levels]
-    # no integer peak is measured: 152 SMs x 64 32-bit IMAD per clock x max clock,
-    # 10 IMAD per Shoup modular product
-    mm_peak = 152 * 64 * float(pk_.get("sm_max_mhz", 2070.0)) * 1e6 / 10 / 1e12
-    roofs = rooflines(prof, costs, args.steps, float(pk_["hbm_gbs"]), mm_peak)
+    mods = ctx.moduli
+    costs = [algorithmic_costs(N, ctx.L, ctx.K, ctx.alpha, lv, q_lazy=max(mods[:ctx.L]) < (1 << 54),
+                               p_lazy=max(mods[ctx.L:]) < (1 << 54)) for lv in levels]
+    roofs = rooflines(prof, costs, args.steps, float(pk_["hbm_gbs"]), alu_rates)
     dom_name = max(prof.items(), key=lambda kv: kv[1][1])[0]
     roof = dict(roofs[dom_name])
     traffic = None
@@ -743,8 +781,10 @@ def run_gpu(args, rank, world, local_rank):
                  "traffic_source": "ncu DRAM bytes of the 16-ciphertext case over the kernel's minimum bytes, "
                                    "times this workload's minimum bytes per launch" if traffic else None,
                  "peak_source": ("%s copy bandwidth" % src) if roof["bound"] == "hbm" else
-                 "derived: 152 SM x 64 IMAD/clk x %.0f MHz / 10 IMAD per modular product"
-                 % float(pk_.get("sm_max_mhz", 2070.0))})
+                 "measured in this run (fheon_alu_peak): the kernel's mix of butterflies and conversion "
+                 "multiply-accumulates at their measured rates",
+                 "kernel_times": "CUDA events after every launch, in a pass of the same %d steps right after "
+                                 "the timed region (%.2f ms per step there)" % (args.steps, ms_profiled / args.steps)})
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / sum(x[1] for x in prof.values()), 4),
                    "frac": round(roofs.get(k, {}).get("frac", 0.0), 4), "bound": roofs.get(k, {}).get("bound")}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -790,6 +830,7 @@ def run_gpu(args, rank, world, local_rank):
                                                           "neighbouring steps", "result_matches": e2e_ok,
                         "steps_ms": step_summary(e2e_ms), "clocks": e2e_clk.summary()},
                 "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels,
+                "alu_peaks_tmodmul_s": {k: round(v / 1e12, 4) for k, v in alu_rates.items()},
                 "comparisons": comparisons}
         print(json.dumps(line), flush=True)
     if world > 1:

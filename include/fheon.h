@@ -709,6 +709,26 @@ int fheon_profile_begin(fheon_ctx *ctx);
  * FHEON_ERR_ARG if cap is too small. */
 int fheon_profile_end(fheon_ctx *ctx, char *out, size_t cap);
 
+/* Measured integer peaks: the rate of one modular step of the rotation's
+ * ALU-bound kernels, run alone on every SM at those kernels' occupancy (three
+ * 256-thread CTAs per SM), the step in the form those kernels use it, on one
+ * of the context's primes of the right class.  Kinds: */
+#define FHEON_PEAK_CT_LAZY 0   /* forward butterfly, no conditional subtraction (q < 2^54) */
+#define FHEON_PEAK_GS_LAZY 1   /* inverse butterfly, same primes */
+#define FHEON_PEAK_CT_HARVEY 2 /* forward butterfly with Harvey's reductions */
+#define FHEON_PEAK_GS_HARVEY 3 /* inverse butterfly with Harvey's reductions */
+#define FHEON_PEAK_MAC 4       /* 128-bit multiply-accumulate of a base conversion */
+#define FHEON_PEAK_KINDS 5
+/* Each thread runs `rounds` rounds of 32 steps (a radix-16 round of four
+ * butterfly stages with its 15 twiddle reads; or four source words times
+ * eight accumulators, each reduced once per round); the fastest of `reps`
+ * launches, timed with CUDA events on the context's stream after one
+ * untimed launch, gives *per_s = steps per second.  Blocking; allocates a
+ * few KiB through the allocator hook.  FHEON_ERR_ARG for an unknown kind,
+ * rounds outside [1, 2^20], reps outside [1, 100], N < 256, or a lazy kind
+ * on a context without a prime below 2^54. */
+int fheon_alu_peak(fheon_ctx *ctx, uint32_t kind, uint32_t rounds, uint32_t reps, double *per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,7 @@ SIGNATURES = {
     "fheon_rotate_batch": [c_vp, P(fheon_rot_item), c_u32],
     "fheon_rotate_hoisted": [c_vp, c_vp, P(c_i32), c_u32, P(c_vp)],
     "fheon_rotate_batch_hoisted": [c_vp, P(fheon_rot_item), c_u32],
+    "fheon_alu_peak": [c_vp, c_u32, c_u32, c_u32, P(c_dbl)],
     "fheon_rotate_noalloc": [c_vp, c_vp, c_i32, c_vp],
     "fheon_mul_plain": [c_vp, c_vp, c_vp, c_vp],
     "fheon_mul_relin": [c_vp, c_vp, c_vp, c_vp],
@@ -935,6 +936,15 @@ class Context:
         buf = ctypes.create_string_buffer(1 << 16)
         self._chk(load().fheon_profile_end(self.h, buf, len(buf)))
         return {k: (v[0], v[1]) for k, v in json.loads(buf.value.decode()).items()}
+
+    PEAK_KINDS = {"ct_lazy": 0, "gs_lazy": 1, "ct_harvey": 2, "gs_harvey": 3, "mac": 4}
+
+    def alu_peak(self, kind, rounds=2048, reps=5):
+        """Measured rate (steps/s) of one modular step (see fheon_alu_peak):
+        kind is one of PEAK_KINDS."""
+        v = c_dbl(0.0)
+        self._chk(load().fheon_alu_peak(self.h, self.PEAK_KINDS[kind], rounds, reps, ctypes.byref(v)))
+        return v.value
 
     # layers
     def conv2d_rotation_steps(self, in_ch, k, in_h, in_w):

@@ -24,7 +24,14 @@ def test_rotation_bytes_closed_form(level):
     assert ip == 8 * N * (2 * beta * (level + K) + beta * (level + K) + 2 * (level + K))
     # ModUp: new limbs = digits x (level + K) minus the digits' own limbs
     new = beta * (level + K) - level
-    assert c["kernels"]["up_ntt_rows"]["mm"] == new * (N // 2) * 8
+    up = c["kernels"]["up_ntt_rows"]["mm"]
+    assert sum(up.values()) == new * (N // 2) * 8
+    # 50-bit Q primes take the lazy butterflies, 60-bit P primes Harvey's
+    assert up.get("ct_lazy", 0) == (beta * level - level) * (N // 2) * 8 and up["ct_harvey"] == beta * K * (N // 2) * 8
+    # ModUp's conversions: digit j of d_j limbs feeds the level + K - d_j other limbs
+    digits = [min(alpha, level - j * alpha) for j in range(beta)]
+    assert c["kernels"]["up_bconv_ntt_cols"]["mm"]["mac"] == N * sum(d * (level + K - d) for d in digits)
+    assert c["kernels"]["dn_intt_rows"]["mm"] == {"gs_harvey": 2 * K * (N // 2) * 8}
 
 
 def test_the_published_mean_bytes():
@@ -37,11 +44,19 @@ def test_the_published_mean_bytes():
 def test_roofline_arithmetic():
     costs = [bench.algorithmic_costs(1 << 16, 24, 4, 4, 12)]
     prof = {"ks_inner": (2, 1.0), "up_ntt_rows": (2, 2.0), "unknown": (1, 1.0)}
-    r = bench.rooflines(prof, costs, steps=2, hbm_peak=6784.5, mm_peak=2.0)
+    rates = {"ct_lazy": 2e12, "gs_lazy": 2e12, "ct_harvey": 1e12, "gs_harvey": 1e12, "mac": 4e12}
+    r = bench.rooflines(prof, costs, steps=2, hbm_peak=6784.5, alu_rates=rates)
     ip = costs[0]["kernels"]["ks_inner"]["bytes"] * 2 / 1e-3 / 1e9
     assert abs(r["ks_inner"]["achieved"] - ip) < 1e-6 and r["ks_inner"]["bound"] == "hbm"
     assert abs(r["ks_inner"]["frac"] - ip / 6784.5) < 1e-12
-    assert r["up_ntt_rows"]["bound"] == "alu" and r["up_ntt_rows"]["avg_launch_ms"] == 1.0
+    up = r["up_ntt_rows"]
+    assert up["bound"] == "alu" and up["avg_launch_ms"] == 1.0
+    # frac = the shortest time at the measured rates over the measured time
+    mm = costs[0]["kernels"]["up_ntt_rows"]["mm"]
+    t_min = 2 * sum(v / rates[k] for k, v in mm.items())
+    assert up["frac"] == pytest.approx(t_min / 2e-3)
+    assert up["achieved"] == pytest.approx(2 * sum(mm.values()) / 2e-3 / 1e12)
+    assert up["peak"] == pytest.approx(2 * sum(mm.values()) / t_min / 1e12)
     assert "unknown" not in r
 
 
