@@ -18,6 +18,7 @@ import test_oracle_fheon as TF
 import test_oracle_hoisted as TH
 import test_oracle_layers as TL
 import test_oracle_mult as TM
+import test_oracle_paper_layers as TP
 import test_oracle_primitives as PR
 import test_oracle_relu as TR
 import test_oracle_scheme as S
@@ -25,6 +26,7 @@ from oracle import _lib
 from oracle import boot as B
 from oracle import ckks
 from oracle import fheon as OF
+from oracle import paper_layers as PL
 from paper_2510_03996_gb300 import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -332,6 +334,15 @@ def _monomial_sign(monkeypatch):
     monkeypatch.setattr(B, "monomial", lambda ctx, level, sign=1: orig(ctx, level, -sign))
 
 
+def _rotation_remapped(remap):
+    """A paper-form layer that rotates by remap(r) where it means r (a wrong
+    shift in one of its steps)."""
+    def plant(monkeypatch):
+        orig = PL.Counter.rot
+        monkeypatch.setattr(PL.Counter, "rot", lambda self, x, r: orig(self, x, remap(r)))
+    return plant
+
+
 @pytest.fixture(scope="module")
 def boot_ctx():
     P = synth.params("boot_n12")
@@ -366,6 +377,19 @@ PY_PLANTS = {
     "fold_rotation_sign": (_fold_rotated_the_wrong_way,
                            lambda bc: TL.test_fc_diag_plan_is_the_product(16, 4, 28, 4, 12)),
     "conjugation_monomial_sign": (_monomial_sign, lambda bc: TB.test_bootstrap_encrypted(bc)),
+    # the paper's own layer algorithms (Sec. 5.1, 5.2, 5.4, 5.5)
+    "paper_pad_row_gap_P": (_rotation_remapped(lambda r: -1 if r == -2 else r),
+                            lambda bc: TP.test_padding_by_rotations(3, 5, 5, 1)),
+    "paper_channel_sum_by_W": (_rotation_remapped(lambda r: 6 if r == 36 else r),
+                               lambda bc: TP.test_conv_is_the_convolution_with_k_plus_f_keys(2, 3, 3, 6, 6)),
+    "paper_extraction_one_too_far": (_rotation_remapped(lambda r: 3 if r == 2 else r),
+                                     lambda bc: TP.test_conv_is_the_convolution_with_k_plus_f_keys(1, 1, 3, 6, 6)),
+    "paper_stride_compaction_by_S": (_rotation_remapped(lambda r: 2 * r if r in (1, 2) else r),
+                                     lambda bc: TP.test_striding_key_and_rotation_counts(8, 3, 2)),
+    "paper_fc_merge_sign": (_rotation_remapped(lambda r: -r if -5 < r < 0 else r),
+                            lambda bc: TP.test_fc_with_merge_budget(5, None)),
+    "paper_global_pool_merge_by_block": (_rotation_remapped(lambda r: 64 if r == 63 else r),
+                                         lambda bc: TP.test_global_avgpool(3, 8)),
 }
 
 
