@@ -377,6 +377,13 @@ int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule)
     return FHEON_OK;
 }
 
+int fheon_ctx_set_batching(fheon_ctx *ctx, int on)
+{
+    if (!ctx || (on != 0 && on != 1)) return FHEON_ERR_ARG;
+    ctx->batching = on != 0;
+    return FHEON_OK;
+}
+
 int fheon_autotune_schedule(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, uint32_t reps, int *best,
                             double *ms_per_batch)
 {

@@ -148,6 +148,10 @@ struct fheon_ctx {
     // over all target limbs; alpha <= 4); 4 = tiled ModDown conversion (K <= 4);
     // 8 = the streaming inner product fed by TMA bulk copies (with bit 1)
     int ks_schedule = 9;
+    // false: every batched rotation and product runs one ciphertext at a time,
+    // each through its own launch sequence and without hoisting (the plain
+    // path batched results are compared with; fheon_ctx_set_batching)
+    bool batching = true;
     std::string last_error;
 
     // limbs of the key-switching workspace at level l

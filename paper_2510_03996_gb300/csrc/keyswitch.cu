@@ -121,10 +121,13 @@ struct JobCommon : ntt::JobBase {
     __device__ ulonglong2 inv_scale() const { return make_ulonglong2(0, 0); }
 };
 
-// IC: INTT of sigma_g(c1) limb t, scaled for ModUp, into xt[t]
+// IC: INTT of sigma_g(c1) limb t, scaled for ModUp, into xt[t].  The first
+// (row) pass reads the tile's sources, one aligned tile of c1, in order and
+// places each at its destination in shared memory (GATHER_LOAD)
 struct IcJob : JobCommon {
     const u64 *in;
     u64 *out;
+    u64 ginv;
     u32 t;
     __device__ IcJob(const BatchParams &P, u32 task) : JobCommon(P)
     {
@@ -134,8 +137,13 @@ struct IcJob : JobCommon {
         midx = t;
         in = d->c1 + (u64)t * P.tp.N;
         out = d->xt + (u64)t * P.tp.N;
+        ginv = inv_odd(d->gi);
     }
     template <bool INV> __device__ u64 load_first(u32 J) const { return in[automorph_src(J, d->gi, p.tp.logN)]; }
+    static constexpr bool GATHER_LOAD = true;
+    __device__ u32 gather_src(u32 J) const { return automorph_src(J, d->gi, p.tp.logN); }
+    __device__ u32 gather_dst(u32 s) const { return automorph_src(s, ginv, p.tp.logN); }
+    __device__ u64 load_src(u32 s) const { return in[s]; }
     __device__ u64 load_mid(u32 J) const { return out[J]; }
     __device__ void store_mid(u32 J, u64 v) const { out[J] = v; }
     __device__ ulonglong2 inv_scale() const { return modup_scale(p.modup_scale, t, d->level, p.alpha); }
@@ -1043,6 +1051,14 @@ int rotate_many(fheon_ctx *ctx, const fheon_rot_item *items, uint32_t n, bool ho
             if (!outs.insert(items[i].out).second) return fail(ctx, FHEON_ERR_ARG, "batch output %u repeated", i);
         }
     }
+    if (!ctx->batching) {
+        // the plain path: one rotation at a time, none hoisted
+        for (u32 i = 0; i < n; i++) {
+            int rc = rotate_one(ctx, items[i].in, ks[i].g, items[i].out);
+            if (rc) return rc;
+        }
+        return FHEON_OK;
+    }
     for (u32 i = 0; i < n; i++) {
         int rc = ct_reshape(ctx, items[i].out, items[i].in->level);
         if (rc) return rc;
@@ -1059,6 +1075,16 @@ int mul_relin_many(fheon_ctx *ctx, const RelinItem *items, uint32_t n, PlanKeep 
 {
     if (n == 0) return FHEON_OK;
     if (n == 1) return mul_relin_at(ctx, items[0].a, items[0].b, items[0].level, items[0].twice, items[0].out);
+    if (!ctx->batching) {
+        for (u32 i = 0; i < n; i++) {
+            const RelinItem &r = items[i];
+            if (!r.a || !r.b || !r.out || r.out == r.a || r.out == r.b)
+                return fail(ctx, FHEON_ERR_ARG, "product batch item %u: null or aliased ciphertext", i);
+            int rc = mul_relin_at(ctx, r.a, r.b, r.level, r.twice, r.out);
+            if (rc) return rc;
+        }
+        return FHEON_OK;
+    }
     auto kit = ctx->keys.find(0);
     if (kit == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "no relinearisation key");
     const u32 N = ctx->N;

@@ -124,11 +124,25 @@ __device__ __forceinline__ void prefetch_l2(const void *p, u32 bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// inverse of an odd g modulo 2^64 (Newton's iteration x <- x (2 - g x) doubles
+// the number of correct low bits; x = g is right to 3 bits)
+__device__ __forceinline__ u64 inv_odd(u64 g)
+{
+    u64 x = g;
+#pragma unroll
+    for (int i = 0; i < 5; i++) x *= 2 - g * x;
+    return x;
+}
+
 // bit reversal of the low `bits` bits
 __device__ __forceinline__ u32 brev_bits(u32 x, u32 bits) { return __brev(x) >> (32 - bits); }
 
 // Evaluation-domain Galois automorphism: index j of sigma_g(a) holds index
-// src of a, where 2*brv(src)+1 = (2*brv(j)+1) * g mod 2N.
+// src of a, where 2*brv(src)+1 = (2*brv(j)+1) * g mod 2N.  The map by g^-1 is
+// its inverse.  It takes an aligned block of 2^b indices (fixed high bits)
+// onto an aligned block: the low logN - b bits of brv(j) are fixed, odd
+// multiples keep them fixed modulo 2^(logN-b+1), so the high bits of src are
+// fixed too.
 __device__ __forceinline__ u32 automorph_src(u32 j, u64 g, u32 logN)
 {
     u32 k = brev_bits(j, logN);

@@ -102,6 +102,12 @@ struct JobBase {
     // a forward transform over a lazy prime may hand its consumer the values
     // unreduced (below 36q for up to 17 stages from inputs below 2q)
     static constexpr bool LAZY_OUT = false;
+    // a first row pass whose input is a Galois image sigma_g(in): the job gives
+    // gather_src(J) (the input index element J reads) and gather_dst(s) (its
+    // inverse) and load_src(s) = in[s]; the tile's sources are one aligned
+    // tile of `in`, read in order (coalesced) and placed in shared memory at
+    // their destinations
+    static constexpr bool GATHER_LOAD = false;
 };
 
 // reduce v < 2^64 to [0, q) with one Shoup product by 1 and a subtraction
@@ -191,6 +197,21 @@ __device__ __forceinline__ void pass_body(Job &job, u32 tile)
                 const u32 J = gidx(sub, relem(0, v));
                 x[v] = FIRST ? job.template load_first<INV>(J) : job.load_mid(J);
             }
+        } else if constexpr (FIRST && Job::GATHER_LOAD) {
+            static_assert(ROWS, "a gathered load needs the row pass: a tile of consecutive elements");
+            const u32 t0 = tile * (u32)(SUBS * M);
+            const u32 s0 = job.gather_src(t0) & ~(u32)(SUBS * M - 1);
+            u64 v_[R];
+#pragma unroll
+            for (int k = 0; k < R; k++) v_[k] = job.load_src(s0 + (u32)(t + k * NT));
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                const u32 loc = job.gather_dst(s0 + (u32)(t + k * NT)) - t0;
+                sm[sidx((int)(loc / M), (int)(loc % M))] = v_[k];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int v = 0; v < R; v++) x[v] = sm[sidx(sub, relem(0, v))];
         } else {
 #pragma unroll
             for (int k = 0; k < R; k++) {
