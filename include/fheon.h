@@ -148,6 +148,15 @@ int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream);
 #define FHEON_NUM_SCHEDULES 16
 int fheon_ctx_get_schedule(const fheon_ctx *ctx, int *schedule);
 int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule);
+/* Batching switch.  on = 1 (the default): batched rotations and products
+ * (fheon_rotate_batch, the layers, series and bootstraps built on them) run
+ * as one launch sequence over the whole batch, with the rotations of one
+ * input hoisted.  on = 0: the plain one-ciphertext-per-launch path, every
+ * rotation and product of a batch through its own launch sequence, none
+ * hoisted (its results are the plain rotation's; a hoisted rotation differs
+ * from it in the low bits).  For measuring what batching gains.
+ * FHEON_ERR_ARG for other values. */
+int fheon_ctx_set_batching(fheon_ctx *ctx, int on);
 /* Autotuner: time every schedule the parameters allow on the caller's batch
  * (one untimed run, then `reps` timed runs of fheon_rotate_batch with CUDA
  * events on the context's stream), keep the fastest on the context and
@@ -311,8 +320,9 @@ int fheon_rotate_galois(fheon_ctx *ctx, const fheon_ct *in, uint64_t galois, fhe
  *  - The key-switching workspace is a fixed 32 MiB device array inside the
  *    library (reserved on every GPU that loads it, until the process exits).
  *    A rotation needs (l + beta*(l+K) + 2*(l+K) + 2K + 2l) * N * 8 bytes at
- *    level l (e.g. N = 2^13, L = 3, K = 1: 2 MiB; N = 2^16 fits up to level 4
- *    with K = 4); larger requests fail with FHEON_ERR_ARG and a message.
+ *    level l (e.g. N = 2^13, L = 3, K = 1: 2 MiB; N = 2^16 with K = 4 and
+ *    four limbs per digit fits up to level 5, 29.5 MiB); larger requests fail
+ *    with FHEON_ERR_ARG and a message.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
  *    before any stream capture.
@@ -397,13 +407,19 @@ int fheon_drop_level(fheon_ctx *ctx, const fheon_ct *in, uint32_t level, fheon_c
 /* ------------------------------------------------------------------ */
 /* Secure layers (paper Sec. 5)                                       */
 /* ------------------------------------------------------------------ */
-/* Rotation steps a special ("same", stride 1) k x k convolution on a
- * W-wide input needs: di*W + dj for every non-zero tap (di, dj) in
- * [-(k-1)/2, (k-1)/2]^2, plus H*W for channel summation when in_ch > 1
- * (paper Sec. 5.3 and Sec. 5.7 rotation-index analysis).  Writes at most
- * *n entries, sets *n to the count. */
-int fheon_conv2d_rotation_steps(uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w, int32_t *out,
-                                uint32_t *n);
+/* Rotation steps fheon_conv2d needs on a ring of degree N for this shape
+ * (host only, no context): for the special convolution (in_ch = out_ch = 1,
+ * odd k, stride 1, pad (k-1)/2) di*W + dj for every non-zero tap (di, dj) in
+ * [-(k-1)/2, (k-1)/2]^2 (paper Sec. 5.3 and the rotation-index analysis of
+ * Sec. 5.7); otherwise the tap steps (x - pad)*W + (y - pad), the block
+ * shifts -delta*H*W (delta = f - c != 0) and, when the outputs need
+ * compacting, the repack's steps.  Sorted, distinct.  With out == NULL only
+ * *n is set (the count); else *n is out's capacity on entry (FHEON_ERR_ARG if
+ * too small) and the count on return.  FHEON_ERR_ARG for a zero size, N not
+ * a power of two, a kernel larger than the padded input, or maps that do not
+ * fit N/2 slots. */
+int fheon_conv2d_rotation_steps(uint32_t N, uint32_t in_ch, uint32_t out_ch, uint32_t k, uint32_t stride,
+                                uint32_t pad, uint32_t in_h, uint32_t in_w, int32_t *out, uint32_t *n);
 /* Prepare a special convolution (paper Sec. 5.3, Alg. 1-3 generalised to
  * odd k): one output channel per layer call, in_ch input channels packed
  * at slot c*H*W + h*W + w, weights w[in_ch][k][k], optional bias.  The
@@ -430,10 +446,23 @@ int fheon_conv2d_apply(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct 
  * addresses it was captured with: rotation keys, the layer and both
  * ciphertexts must stay alive and in place while it is replayed. */
 int fheon_conv2d_apply_graph(fheon_ctx *ctx, const fheon_layer *layer, const fheon_ct *in, fheon_ct *out);
-/* prepare + apply + destroy in one call. */
-int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k, uint32_t stride,
-                 uint32_t pad, uint32_t in_h, uint32_t in_w, const double *w, const double *bias,
-                 fheon_ct *out);
+/* Convolution in one call (paper Sec. 5.1 equation with padding and stride,
+ * Sec. 5.2 output size): the input ciphertext holds the flattened
+ * (in_ch, in_h, in_w) map at slot c*H*W + h*W + w (Sec. 5.1 flattening); w is
+ * w[out_ch][in_ch][k][k] (row-major, cross-correlation as in Sec. 5.1), bias
+ * b[out_ch] or NULL.  The output holds the flattened (out_ch, Ho, Wo) map at
+ * f*Ho*Wo + i*Wo + j, Ho = (in_h + 2 pad - k)/stride + 1 (likewise Wo), zero in
+ * every other slot.  One output channel from one input channel with odd k,
+ * stride 1 and pad (k-1)/2 is the special convolution of Sec. 5.3 (one
+ * level); every other shape is the rotation-sum convolution of
+ * fheon_conv_prepare on that map (one level), followed, when its outputs are
+ * not already compact (stride > 1, or an output smaller than the input), by
+ * one repack layer (one more level).  Needs the rotation keys of
+ * fheon_conv2d_rotation_steps.  Errors: FHEON_ERR_ARG for zero sizes or maps
+ * that do not fit N/2 slots; FHEON_ERR_NO_KEY; FHEON_ERR_LEVEL when the input
+ * has too few levels.  Asynchronous on the context's stream. */
+int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t out_ch, uint32_t k, uint32_t stride,
+                 uint32_t pad, uint32_t in_h, uint32_t in_w, const double *w, const double *bias, fheon_ct *out);
 int fheon_layer_destroy(fheon_layer *layer);
 
 /* ------------------------------------------------------------------ */
@@ -590,6 +619,45 @@ int fheon_layer_apply_graph(fheon_ctx *ctx, const fheon_layer *layer, const fheo
 int fheon_layer_rotation_steps(const fheon_layer *layer, int32_t *out, uint32_t *n);
 /* Output map of a conv, pooling or FC layer prepared from a map. */
 int fheon_layer_out_map(const fheon_layer *layer, fheon_map *out);
+
+/* Introspection of a prepared layer, so that a caller (or a test) can check
+ * what a builder made against an independent construction: its plan and
+ * every plaintext it encoded.  Blocking only where a download is.
+ * Kinds of layer: */
+#define FHEON_LAYER_SPECIAL_CONV 0 /* fheon_conv2d_prepare */
+#define FHEON_LAYER_RELU 1         /* fheon_relu_prepare, fheon_cheb_prepare */
+#define FHEON_LAYER_ROTSUM 2       /* rotation-sum: conv, pooling, diagonal FC, repack, slot-transform levels */
+#define FHEON_LAYER_FC_SLOTSUM 3   /* fheon_fc_prepare_plain, the paper's per-neuron FC */
+#define FHEON_LAYER_BOOTSTRAP 4    /* fheon_bootstrap_prepare / _compose */
+/* Kind, level (the input level the layer expects; a bootstrap: L) and
+ * counts: a rotation-sum layer has nf fold shifts, nt tap steps and ng
+ * groups; a slot-sum FC ng neurons; a special conv nt = k^2 taps and ng = 1;
+ * a bootstrap nt CoeffToSlot and ng SlotToCoeff levels; others 0.  Any
+ * pointer may be NULL. */
+int fheon_layer_plan_info(const fheon_layer *layer, uint32_t *kind, uint32_t *level, uint32_t *nf, uint32_t *nt,
+                          uint32_t *ng);
+/* A rotation-sum layer's fold shifts fold[nf], tap steps r[nt] and group
+ * shifts s[ng] (arrays sized from fheon_layer_plan_info; any may be NULL):
+ * out = sum_g Rot_{s_g}(rescale(sum_t Rot_{r_t}(x) * P_{g,t})) + bias, with
+ * x = sum_c Rot_{fold_c}(in) when nf > 0.  FHEON_ERR_ARG for other kinds. */
+int fheon_layer_plan(const fheon_layer *layer, int32_t *fold, int32_t *r, int32_t *s);
+/* Borrow one of a layer's plaintexts (valid while the layer lives; the
+ * caller must not destroy it); *out = NULL where the layer has none (a
+ * group's tap without a product, no bias).  which: */
+#define FHEON_PLAIN_PRODUCT 0 /* rotation-sum P_{g,t}; slot-sum FC weights of neuron g (t = 0); special conv tap t */
+#define FHEON_PLAIN_PLACE 1   /* slot-sum FC: the one-hot placement of neuron g */
+#define FHEON_PLAIN_BIAS 2    /* the bias (g = t = 0) */
+#define FHEON_PLAIN_MASK 3    /* ReLU: the 1/beta mask; special conv with C > 1: the block-0 mask */
+#define FHEON_PLAIN_MONO 4    /* bootstrap: X^(N/2) where the parts split (g = 0) and join (g = 1) */
+/* FHEON_ERR_ARG for an index out of range or a kind without that plaintext. */
+int fheon_layer_plain(const fheon_layer *layer, uint32_t which, uint32_t g, uint32_t t, const fheon_pt **out);
+/* Level i of a bootstrap layer: CoeffToSlot levels first (i < nt), then
+ * SlotToCoeff (rotation-sum layers, borrowed like plaintexts). */
+int fheon_layer_sub(const fheon_layer *layer, uint32_t i, const fheon_layer **out);
+/* The series coefficients c_0..c_D of a ReLU / Chebyshev layer or of a
+ * bootstrap's EvalMod; with out == NULL only *n (the count) is set, else *n
+ * is the capacity on entry (FHEON_ERR_ARG if too small). */
+int fheon_layer_coeffs(const fheon_layer *layer, double *out, uint32_t *n);
 
 /* ------------------------------------------------------------------ */
 /* Serving: continuous batching of inference requests                 */

@@ -182,33 +182,23 @@ namespace fheon {
 
 static int64_t floordiv(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
-Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby)
+void bsgs_split(const std::set<int64_t> &ks, int64_t M, u32 baby, int64_t &bs, std::set<int64_t> &ts,
+                std::set<int64_t> &cs)
 {
-    const int64_t M = n / stride;
-    std::map<int64_t, const std::vector<cd> *> ks;
-    for (const auto &kv : D) {
-        bool any = false;
-        for (const cd &x : kv.second) any = any || x != cd(0.0);
-        if (!any) continue;
-        int64_t k = kv.first / stride;
-        if (k > M / 2) k -= M;
-        ks[k] = &kv.second;
-    }
-    auto split = [&](int64_t bs, std::set<int64_t> &ts, std::set<int64_t> &cs) {
+    auto split = [&](int64_t b) {
         ts.clear();
         cs.clear();
-        for (auto &kv : ks) {
-            const int64_t c = floordiv(kv.first, bs);
+        for (int64_t k : ks) {
+            const int64_t c = floordiv(k, b);
             cs.insert(c);
-            ts.insert(kv.first - c * bs);
+            ts.insert(k - c * b);
         }
     };
-    std::set<int64_t> ts, cs;
-    int64_t bs = baby;
+    bs = baby;
     if (!bs) {
         int64_t best = -1;
         for (int64_t b = 1; b <= M; b *= 2) {
-            split(b, ts, cs);
+            split(b);
             const int64_t cost = (int64_t)ts.size() - (int64_t)ts.count(0) + (int64_t)cs.size() - (int64_t)cs.count(0);
             if (best < 0 || cost <= best) {
                 best = cost;
@@ -216,7 +206,42 @@ Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby)
             }
         }
     }
-    split(bs, ts, cs);
+    split(bs);
+}
+
+std::set<int64_t> bsgs_offsets(const std::set<u32> &offsets, u32 n, u32 stride)
+{
+    const int64_t M = n / stride;
+    std::set<int64_t> ks;
+    for (u32 o : offsets) {
+        int64_t k = o / stride;
+        if (k > M / 2) k -= M;
+        ks.insert(k);
+    }
+    return ks;
+}
+
+Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby)
+{
+    std::set<u32> offs;
+    std::map<int64_t, const std::vector<cd> *> byk;
+    for (const auto &kv : D) {
+        bool any = false;
+        for (const cd &x : kv.second) any = any || x != cd(0.0);
+        if (!any) continue;
+        offs.insert(kv.first);
+    }
+    const std::set<int64_t> ks = bsgs_offsets(offs, n, stride);
+    for (const auto &kv : D)
+        if (offs.count(kv.first)) {
+            const int64_t M = n / stride;
+            int64_t k = kv.first / stride;
+            if (k > M / 2) k -= M;
+            byk[k] = &kv.second;
+        }
+    int64_t bs = 0;
+    std::set<int64_t> ts, cs;
+    bsgs_split(ks, (int64_t)(n / stride), baby, bs, ts, cs);
     Bsgs out;
     for (int64_t t : ts) out.r.push_back((int32_t)(t * stride));
     for (int64_t c : cs) {
@@ -224,8 +249,8 @@ Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby)
         out.s.push_back((int32_t)G);
         const u32 sh = (u32)(((G % (int64_t)n) + n) % n);
         for (int64_t t : ts) {
-            auto it = ks.find(c * bs + t);
-            if (it == ks.end()) {
+            auto it = byk.find(c * bs + t);
+            if (it == byk.end()) {
                 out.vals.emplace_back();
                 continue;
             }

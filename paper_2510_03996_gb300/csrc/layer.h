@@ -4,6 +4,7 @@
 #pragma once
 #include <complex>
 #include <map>
+#include <set>
 #include <vector>
 
 #include "internal.h"
@@ -110,6 +111,16 @@ struct Bsgs {
     std::vector<std::vector<cd>> vals; // [g * r.size() + t], empty = no product
 };
 Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby);
+// the split alone, from the nonzero offsets: k = o / stride centred in
+// (-M/2, M/2] (bsgs_offsets), then the baby-step size bs over b = 1, 2, ..
+// <= M (fewest rotations, ties: the larger), the baby steps ts and giant
+// steps cs; r = ts * stride, s = cs * bs * stride
+std::set<int64_t> bsgs_offsets(const std::set<u32> &offsets, u32 n, u32 stride);
+void bsgs_split(const std::set<int64_t> &ks, int64_t M, u32 baby, int64_t &bs, std::set<int64_t> &ts,
+                std::set<int64_t> &cs);
+// rotation steps of the repack layer from map a to map b (the plan of
+// fheon_repack_prepare, without encoding it); FHEON_ERR_ARG as that call
+int repack_steps(u32 n, const fheon_map &a, const fheon_map &b, std::vector<int32_t> &steps);
 // the rotation-sum layer of sum_o (factor d_o) Rot_o at `level`, its
 // plaintexts encoded at `pscale` and owned by the layer
 int diag_layer(fheon_ctx *ctx, const Diags &M, u32 stride, cd factor, u32 baby, u32 level, double pscale,

@@ -14,8 +14,10 @@
 // channels the channel blocks are summed by C-1 chained rotations by H*W
 // (the single W^2 key of Sec. 5.3) and masked to block 0, which costs one
 // more level.  The bias is added last.
+#include <algorithm>
 #include <cmath>
 #include <memory>
+#include <set>
 #include <vector>
 
 #include "layer.h"
@@ -27,6 +29,27 @@ struct CtGuard {
     fheon_ct *p = nullptr;
     ~CtGuard() { fheon_ct_destroy(p); }
 };
+
+bool conv2d_is_special(u32 in_ch, u32 out_ch, u32 k, u32 stride, u32 pad)
+{
+    return in_ch == 1 && out_ch == 1 && k % 2 == 1 && stride == 1 && pad == (k - 1) / 2;
+}
+
+bool same_map(const fheon_map &a, const fheon_map &b)
+{
+    return a.C == b.C && a.H == b.H && a.W == b.W && a.grid == b.grid && a.dil == b.dil && a.block == b.block;
+}
+
+// the output map of the rotation-sum conv on the compact (C, H, W) input (its
+// outputs at the stride-aligned slots of the input grid) and the compact
+// output map (F, Ho, Wo) the one-shot call returns
+void conv2d_maps(u32 C, u32 F, u32 k, u32 stride, u32 pad, u32 H, u32 W, fheon_map &om, fheon_map &cm)
+{
+    const u32 Ho = (H + 2 * pad - k) / stride + 1, Wo = (W + 2 * pad - k) / stride + 1;
+    (void)C;
+    om = fheon_map{F, Ho, Wo, W, stride, H * W};
+    cm = fheon_map{F, Ho, Wo, Wo, 1, Ho * Wo};
+}
 
 int make_mask(fheon_ctx *ctx, fheon_layer *ly)
 {
@@ -42,19 +65,45 @@ int make_mask(fheon_ctx *ctx, fheon_layer *ly)
 
 extern "C" {
 
-int fheon_conv2d_rotation_steps(uint32_t in_ch, uint32_t k, uint32_t in_h, uint32_t in_w, int32_t *out, uint32_t *n)
+int fheon_conv2d_rotation_steps(uint32_t N, uint32_t in_ch, uint32_t out_ch, uint32_t k, uint32_t stride,
+                                uint32_t pad, uint32_t in_h, uint32_t in_w, int32_t *out, uint32_t *n)
 {
-    if (!n || k % 2 == 0 || in_ch == 0) return FHEON_ERR_ARG;
-    const int p = (int)(k - 1) / 2;
-    std::vector<int32_t> s;
-    for (int di = -p; di <= p; di++)
-        for (int dj = -p; dj <= p; dj++)
-            if (di || dj) s.push_back(di * (int)in_w + dj);
-    if (in_ch > 1) s.push_back((int32_t)(in_h * in_w));
+    if (!n || in_ch == 0 || out_ch == 0 || k == 0 || stride == 0 || in_h == 0 || in_w == 0 || N < 2 || (N & (N - 1)))
+        return FHEON_ERR_ARG;
+    if (in_h + 2 * pad < k || in_w + 2 * pad < k) return FHEON_ERR_ARG;
+    std::set<int32_t> s;
+    if (conv2d_is_special(in_ch, out_ch, k, stride, pad)) {
+        const int p = (int)(k - 1) / 2;
+        for (int di = -p; di <= p; di++)
+            for (int dj = -p; dj <= p; dj++)
+                if (di || dj) s.insert(di * (int)in_w + dj);
+    } else {
+        // the rotation-sum conv on the compact map (taps, block shifts), then the
+        // repack of its output to the compact (F, Ho, Wo) layout when needed
+        const u32 nsl = N / 2, block = in_h * in_w;
+        if ((u64)std::max(in_ch, out_ch) * block > nsl) return FHEON_ERR_ARG;
+        for (u32 x = 0; x < k; x++)
+            for (u32 y = 0; y < k; y++) {
+                const int32_t r = ((int32_t)x - (int32_t)pad) * (int32_t)in_w + ((int32_t)y - (int32_t)pad);
+                if (r) s.insert(r);
+            }
+        for (int delta = -(int)(in_ch - 1); delta < (int)out_ch; delta++)
+            if (delta) s.insert(-delta * (int32_t)block);
+        fheon_map om, cm;
+        conv2d_maps(in_ch, out_ch, k, stride, pad, in_h, in_w, om, cm);
+        if (!same_map(om, cm)) {
+            std::vector<int32_t> rs;
+            if (repack_steps(nsl, om, cm, rs)) return FHEON_ERR_ARG;
+            s.insert(rs.begin(), rs.end());
+        }
+    }
     const u32 cap = *n;
-    for (u32 i = 0; i < s.size() && i < cap; i++)
-        if (out) out[i] = s[i];
     *n = (u32)s.size();
+    if (out && cap < s.size()) return FHEON_ERR_ARG;
+    if (out) {
+        u32 i = 0;
+        for (int32_t x : s) out[i++] = x;
+    }
     return FHEON_OK;
 }
 
@@ -233,21 +282,134 @@ int fheon_layer_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
     return FHEON_OK;
 }
 
-int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t k, uint32_t stride, uint32_t pad,
-                 uint32_t in_h, uint32_t in_w, const double *w, const double *bias, fheon_ct *out)
+int fheon_conv2d(fheon_ctx *ctx, const fheon_ct *in, uint32_t in_ch, uint32_t out_ch, uint32_t k, uint32_t stride,
+                 uint32_t pad, uint32_t in_h, uint32_t in_w, const double *w, const double *bias, fheon_ct *out)
 {
-    if (!ctx || !in) return FHEON_ERR_ARG;
-    fheon_layer *ly = nullptr;
-    int rc = fheon_conv2d_prepare(ctx, in_ch, k, stride, pad, in_h, in_w, w, bias, in->level, in->scale, &ly);
-    if (rc) return rc;
-    rc = fheon_conv2d_apply(ctx, ly, in, out);
-    fheon_layer_destroy(ly);
+    if (!ctx || !in || !out || !w || in_ch == 0 || out_ch == 0 || k == 0 || stride == 0 || in_h == 0 || in_w == 0)
+        return FHEON_ERR_ARG;
+    int rc;
+    if (conv2d_is_special(in_ch, out_ch, k, stride, pad)) {
+        fheon_layer *ly = nullptr;
+        if ((rc = fheon_conv2d_prepare(ctx, in_ch, k, stride, pad, in_h, in_w, w, bias, in->level, in->scale, &ly)))
+            return rc;
+        rc = fheon_conv2d_apply(ctx, ly, in, out);
+        fheon_layer_destroy(ly);
+        return rc;
+    }
+    const fheon_map im{in_ch, in_h, in_w, in_w, 1, in_h * in_w};
+    fheon_map om, cm;
+    conv2d_maps(in_ch, out_ch, k, stride, pad, in_h, in_w, om, cm);
+    fheon_layer *conv = nullptr;
+    if ((rc = fheon_conv_prepare(ctx, &im, out_ch, k, stride, pad, w, bias, in->level, in->scale, &conv))) return rc;
+    if (same_map(om, cm)) {
+        rc = fheon_layer_apply(ctx, conv, in, out);
+        fheon_layer_destroy(conv);
+        return rc;
+    }
+    // the outputs sit at the stride-aligned slots of the input grid: one repack
+    // makes them the compact (F, Ho, Wo) map
+    CtGuard mid;
+    fheon_layer *rp = nullptr;
+    if ((rc = fheon_ct_create(ctx, 1, in->scale, &mid.p)) || (rc = fheon_layer_apply(ctx, conv, in, mid.p))) {
+        fheon_layer_destroy(conv);
+        return rc;
+    }
+    fheon_layer_destroy(conv);
+    if (mid.p->level < 2) return fail(ctx, FHEON_ERR_LEVEL, "conv2d: the compaction needs one more level");
+    if ((rc = fheon_repack_prepare(ctx, &om, &cm, mid.p->level, &rp))) return rc;
+    rc = fheon_layer_apply(ctx, rp, mid.p, out);
+    fheon_layer_destroy(rp);
     return rc;
 }
 
 int fheon_layer_destroy(fheon_layer *layer)
 {
     delete layer;
+    return FHEON_OK;
+}
+
+int fheon_layer_plan_info(const fheon_layer *ly, uint32_t *kind, uint32_t *level, uint32_t *nf, uint32_t *nt,
+                          uint32_t *ng)
+{
+    if (!ly) return FHEON_ERR_ARG;
+    u32 f = 0, t = 0, g = 0;
+    switch (ly->kind) {
+    case LAYER_LINEAR: f = (u32)ly->fold.size(); t = (u32)ly->r.size(); g = (u32)ly->s.size(); break;
+    case LAYER_FC: g = (u32)ly->fw.size(); break;
+    case LAYER_CONV: t = (u32)ly->taps.size(); g = 1; break;
+    case LAYER_BOOT: t = ly->ncts; g = (u32)ly->subs.size() - ly->ncts; break;
+    default: break;
+    }
+    if (kind) *kind = ly->kind;
+    if (level) *level = ly->level;
+    if (nf) *nf = f;
+    if (nt) *nt = t;
+    if (ng) *ng = g;
+    return FHEON_OK;
+}
+
+int fheon_layer_plan(const fheon_layer *ly, int32_t *fold, int32_t *r, int32_t *s)
+{
+    if (!ly || ly->kind != LAYER_LINEAR) return FHEON_ERR_ARG;
+    if (fold) std::copy(ly->fold.begin(), ly->fold.end(), fold);
+    if (r) std::copy(ly->r.begin(), ly->r.end(), r);
+    if (s) std::copy(ly->s.begin(), ly->s.end(), s);
+    return FHEON_OK;
+}
+
+int fheon_layer_plain(const fheon_layer *ly, uint32_t which, uint32_t g, uint32_t t, const fheon_pt **out)
+{
+    if (!ly || !out) return FHEON_ERR_ARG;
+    *out = nullptr;
+    switch (which) {
+    case FHEON_PLAIN_PRODUCT:
+        if (ly->kind == LAYER_LINEAR) {
+            if (g >= ly->s.size() || t >= ly->r.size()) return FHEON_ERR_ARG;
+            *out = ly->pts[(size_t)g * ly->r.size() + t];
+        } else if (ly->kind == LAYER_FC) {
+            if (g >= ly->fw.size() || t) return FHEON_ERR_ARG;
+            *out = ly->fw[g];
+        } else if (ly->kind == LAYER_CONV) {
+            if (g || t >= ly->taps.size()) return FHEON_ERR_ARG;
+            *out = ly->taps[t];
+        } else {
+            return FHEON_ERR_ARG;
+        }
+        return FHEON_OK;
+    case FHEON_PLAIN_PLACE:
+        if (ly->kind != LAYER_FC || g >= ly->fe.size() || t) return FHEON_ERR_ARG;
+        *out = ly->fe[g];
+        return FHEON_OK;
+    case FHEON_PLAIN_BIAS:
+        if (g || t) return FHEON_ERR_ARG;
+        *out = ly->bias;
+        return FHEON_OK;
+    case FHEON_PLAIN_MASK:
+        if (g || t) return FHEON_ERR_ARG;
+        *out = ly->mask;
+        return FHEON_OK;
+    case FHEON_PLAIN_MONO:
+        if (ly->kind != LAYER_BOOT || g > 1 || t) return FHEON_ERR_ARG;
+        *out = ly->mono[g];
+        return FHEON_OK;
+    default: return FHEON_ERR_ARG;
+    }
+}
+
+int fheon_layer_sub(const fheon_layer *ly, uint32_t i, const fheon_layer **out)
+{
+    if (!ly || !out || ly->kind != LAYER_BOOT || i >= ly->subs.size()) return FHEON_ERR_ARG;
+    *out = ly->subs[i];
+    return FHEON_OK;
+}
+
+int fheon_layer_coeffs(const fheon_layer *ly, double *out, uint32_t *n)
+{
+    if (!ly || !n || (ly->kind != LAYER_RELU && ly->kind != LAYER_BOOT)) return FHEON_ERR_ARG;
+    const u32 cap = *n;
+    *n = (u32)ly->coeffs.size();
+    if (out && cap < ly->coeffs.size()) return FHEON_ERR_ARG;
+    if (out) std::copy(ly->coeffs.begin(), ly->coeffs.end(), out);
     return FHEON_OK;
 }
 

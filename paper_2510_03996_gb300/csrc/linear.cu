@@ -189,6 +189,34 @@ int fc_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, 
     return FHEON_OK;
 }
 
+// the largest power of two (at most n) dividing every offset
+u32 common_stride(u32 n, const std::set<u32> &offs)
+{
+    u32 stride = n;
+    for (u32 o : offs)
+        while (stride > 1 && o % stride) stride /= 2;
+    return stride;
+}
+
+// where every (c, i, j) of map a moves to reach its slot in map b: offset o
+// = (src - dst) mod n, the destination slots of each offset
+bool repack_offsets(u32 n, const fheon_map &a, const fheon_map &b, std::map<u32, std::vector<u32>> &dst_of)
+{
+    for (u32 c = 0; c < a.C; c++)
+        for (u32 i = 0; i < a.H; i++)
+            for (u32 j = 0; j < a.W; j++) {
+                const u32 src = map_slot(a, c, i, j), dst = map_slot(b, c, i, j);
+                const u32 o = (src + n - dst) % n;
+                auto it = dst_of.find(o);
+                if (it == dst_of.end()) {
+                    if (dst_of.size() == 1024) return false;
+                    it = dst_of.emplace(o, std::vector<u32>()).first;
+                }
+                it->second.push_back(dst);
+            }
+    return true;
+}
+
 int check_pt(fheon_ctx *ctx, const fheon_pt *p, u32 level, const char *what)
 {
     if (p && p->level < level) return fail(ctx, FHEON_ERR_LEVEL, "%s below level %u", what, level);
@@ -196,6 +224,27 @@ int check_pt(fheon_ctx *ctx, const fheon_pt *p, u32 level, const char *what)
 }
 
 } // namespace
+
+namespace fheon {
+int repack_steps(u32 n, const fheon_map &a, const fheon_map &b, std::vector<int32_t> &steps)
+{
+    std::map<u32, std::vector<u32>> dst_of;
+    if (!repack_offsets(n, a, b, dst_of)) return FHEON_ERR_ARG;
+    std::set<u32> offs;
+    for (auto &kv : dst_of) offs.insert(kv.first);
+    const u32 stride = common_stride(n, offs);
+    int64_t bs = 0;
+    std::set<int64_t> ts, cs;
+    bsgs_split(bsgs_offsets(offs, n, stride), (int64_t)(n / stride), 0, bs, ts, cs);
+    std::set<int32_t> st;
+    for (int64_t t : ts)
+        if (t) st.insert((int32_t)(t * stride));
+    for (int64_t c : cs)
+        if (c) st.insert((int32_t)(c * bs * (int64_t)stride));
+    steps.assign(st.begin(), st.end());
+    return FHEON_OK;
+}
+} // namespace fheon
 
 extern "C" {
 
@@ -424,24 +473,17 @@ int fheon_repack_prepare(fheon_ctx *ctx, const fheon_map *in, const fheon_map *o
     const u32 n = ctx->N / 2;
     // every (c, i, j) moves from its slot in `in` to its slot in `out`:
     // out = sum_o m_o Rot_o(in), m_o one at each destination o slots before its source
+    std::map<u32, std::vector<u32>> dst_of;
+    if (!repack_offsets(n, a, b, dst_of))
+        return fail(ctx, FHEON_ERR_ARG, "repack: more than 1024 distinct shifts; split it");
     Diags D;
-    for (u32 c = 0; c < a.C; c++)
-        for (u32 i = 0; i < a.H; i++)
-            for (u32 j = 0; j < a.W; j++) {
-                const u32 src = map_slot(a, c, i, j), dst = map_slot(b, c, i, j);
-                const u32 o = (src + n - dst) % n;
-                auto it = D.find(o);
-                if (it == D.end()) {
-                    if (D.size() == 1024)
-                        return fail(ctx, FHEON_ERR_ARG, "repack: more than 1024 distinct shifts; split it");
-                    it = D.emplace(o, std::vector<cd>(n, cd(0.0))).first;
-                }
-                it->second[dst] = cd(1.0);
-            }
-    u32 stride = n;
-    for (auto &kv : D)
-        while (stride > 1 && kv.first % stride) stride /= 2;
-    int rc = diag_layer(ctx, D, stride, cd(1.0), 0, level, (double)ctx->mod[level - 1], layer);
+    std::set<u32> offs;
+    for (auto &kv : dst_of) {
+        std::vector<cd> &d = D.emplace(kv.first, std::vector<cd>(n, cd(0.0))).first->second;
+        for (u32 dst : kv.second) d[dst] = cd(1.0);
+        offs.insert(kv.first);
+    }
+    int rc = diag_layer(ctx, D, common_stride(n, offs), cd(1.0), 0, level, (double)ctx->mod[level - 1], layer);
     if (rc) return rc;
     (*layer)->in_map = a;
     (*layer)->out_map = b;

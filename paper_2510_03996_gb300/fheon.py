@@ -74,6 +74,7 @@ SIGNATURES = {
     "fheon_ctx_set_stream": [c_vp, c_vp],
     "fheon_ctx_get_schedule": [c_vp, P(c_int)],
     "fheon_ctx_set_schedule": [c_vp, c_int],
+    "fheon_ctx_set_batching": [c_vp, c_int],
     "fheon_autotune_schedule": [c_vp, P(fheon_rot_item), c_u32, c_u32, P(c_int), P(c_dbl)],
     "fheon_sync": [c_vp],
     "fheon_keygen": [c_vp, c_vpp, c_vpp],
@@ -116,6 +117,11 @@ SIGNATURES = {
     "fheon_rotate_hoisted": [c_vp, c_vp, P(c_i32), c_u32, P(c_vp)],
     "fheon_rotate_batch_hoisted": [c_vp, P(fheon_rot_item), c_u32],
     "fheon_alu_peak": [c_vp, c_u32, c_u32, c_u32, P(c_dbl)],
+    "fheon_layer_plan_info": [c_vp, P(c_u32), P(c_u32), P(c_u32), P(c_u32), P(c_u32)],
+    "fheon_layer_plan": [c_vp, P(c_i32), P(c_i32), P(c_i32)],
+    "fheon_layer_plain": [c_vp, c_u32, c_u32, c_u32, c_vpp],
+    "fheon_layer_sub": [c_vp, c_u32, c_vpp],
+    "fheon_layer_coeffs": [c_vp, P(c_dbl), P(c_u32)],
     "fheon_rotate_noalloc": [c_vp, c_vp, c_i32, c_vp],
     "fheon_mul_plain": [c_vp, c_vp, c_vp, c_vp],
     "fheon_mul_relin": [c_vp, c_vp, c_vp, c_vp],
@@ -172,12 +178,12 @@ SIGNATURES = {
     "fheon_add_plain": [c_vp, c_vp, c_vp, c_vp],
     "fheon_rescale": [c_vp, c_vp, c_vp],
     "fheon_drop_level": [c_vp, c_vp, c_u32, c_vp],
-    "fheon_conv2d_rotation_steps": [c_u32, c_u32, c_u32, c_u32, P(c_i32), P(c_u32)],
+    "fheon_conv2d_rotation_steps": [c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_i32), P(c_u32)],
     "fheon_conv2d_prepare": [c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_u32, c_dbl, c_vpp],
     "fheon_conv2d_prepare_plain": [c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_vp), c_vp, c_vpp],
     "fheon_conv2d_apply": [c_vp, c_vp, c_vp, c_vp],
     "fheon_conv2d_apply_graph": [c_vp, c_vp, c_vp, c_vp],
-    "fheon_conv2d": [c_vp, c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_vp],
+    "fheon_conv2d": [c_vp, c_vp, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, c_u32, P(c_dbl), P(c_dbl), c_vp],
     "fheon_layer_destroy": [c_vp],
     "fheon_profile_begin": [c_vp],
     "fheon_profile_end": [c_vp, ctypes.c_char_p, c_sz],
@@ -394,6 +400,10 @@ class Context:
     def set_schedule(self, schedule):
         self._chk(load().fheon_ctx_set_schedule(self.h, int(schedule)))
 
+    def set_batching(self, on):
+        """False: the plain one-ciphertext-per-launch path (fheon_ctx_set_batching)."""
+        self._chk(load().fheon_ctx_set_batching(self.h, 1 if on else 0))
+
     def autotune_schedule(self, ins, outs, steps, reps=2, cache=None):
         """Time every allowed key-switching schedule on this batch; keep the fastest.
         Returns (best, {schedule: ms per batch}).  With `cache` (a JSON file
@@ -539,6 +549,11 @@ class Context:
         h = c_vp()
         self._chk(load().fheon_ct_create(self.h, level, scale, ctypes.byref(h)))
         return Handle(h, load().fheon_ct_destroy)
+
+    def pt_info(self, pt):
+        lv, sc = c_u32(), c_dbl()
+        check(load().fheon_pt_info(pt.h, ctypes.byref(lv), ctypes.byref(sc)))
+        return lv.value, sc.value
 
     def ct_info(self, ct):
         lv, sc = c_u32(), c_dbl()
@@ -864,6 +879,51 @@ class Context:
         check(load().fheon_layer_rotation_steps(layer.h, out, ctypes.byref(n)))
         return list(out[:n.value])
 
+    PLAIN = {"product": 0, "place": 1, "bias": 2, "mask": 3, "mono": 4}
+
+    @staticmethod
+    def layer_plan(layer):
+        """{'kind', 'level', 'fold', 'r', 's'} of a prepared layer (fold/r/s for
+        rotation-sum layers; counts only otherwise)."""
+        v = [c_u32(0) for _ in range(5)]
+        check(load().fheon_layer_plan_info(layer.h, *[ctypes.byref(x) for x in v]))
+        kind, level, nf, nt, ng = [x.value for x in v]
+        out = {"kind": kind, "level": level, "nf": nf, "nt": nt, "ng": ng}
+        if kind == 2:
+            f, r, s = (c_i32 * max(1, nf))(), (c_i32 * max(1, nt))(), (c_i32 * max(1, ng))()
+            check(load().fheon_layer_plan(layer.h, f, r, s))
+            out.update(fold=list(f[:nf]), r=list(r[:nt]), s=list(s[:ng]))
+        return out
+
+    @staticmethod
+    def layer_plain(layer, which, g=0, t=0):
+        """A borrowed plaintext of the layer (None where it has none); it keeps
+        the layer alive."""
+        h = c_vp()
+        check(load().fheon_layer_plain(layer.h, Context.PLAIN[which], g, t, ctypes.byref(h)))
+        if not h.value:
+            return None
+        pt = Handle(h, lambda _h: None)
+        pt.owner = layer
+        return pt
+
+    @staticmethod
+    def layer_sub(layer, i):
+        """Level i of a bootstrap layer (borrowed; keeps the bootstrap alive)."""
+        h = c_vp()
+        check(load().fheon_layer_sub(layer.h, i, ctypes.byref(h)))
+        sub = Handle(h, lambda _h: None)
+        sub.owner = layer
+        return sub
+
+    @staticmethod
+    def layer_coeffs(layer):
+        n = c_u32(0)
+        check(load().fheon_layer_coeffs(layer.h, None, ctypes.byref(n)))
+        out = (c_dbl * max(1, n.value))()
+        check(load().fheon_layer_coeffs(layer.h, out, ctypes.byref(n)))
+        return np.array(out[:n.value])
+
     @staticmethod
     def layer_out_map(layer):
         m = fheon_map()
@@ -947,10 +1007,14 @@ class Context:
         return v.value
 
     # layers
-    def conv2d_rotation_steps(self, in_ch, k, in_h, in_w):
-        n = c_u32(64)
-        out = np.zeros(64, dtype=np.int32)
-        check(load().fheon_conv2d_rotation_steps(in_ch, k, in_h, in_w, out.ctypes.data_as(P(c_i32)), ctypes.byref(n)))
+    def conv2d_rotation_steps(self, in_ch, out_ch, k, stride, pad, in_h, in_w):
+        """Rotation keys fheon_conv2d needs for this shape on this ring."""
+        n = c_u32(0)
+        check(load().fheon_conv2d_rotation_steps(self.N, in_ch, out_ch, k, stride, pad, in_h, in_w, None,
+                                                 ctypes.byref(n)))
+        out = np.zeros(max(1, n.value), dtype=np.int32)
+        check(load().fheon_conv2d_rotation_steps(self.N, in_ch, out_ch, k, stride, pad, in_h, in_w,
+                                                 out.ctypes.data_as(P(c_i32)), ctypes.byref(n)))
         return [int(x) for x in out[:n.value]]
 
     @staticmethod
@@ -983,10 +1047,15 @@ class Context:
         self._chk(load().fheon_conv2d_apply_graph(self.h, layer.h, ct.h, out.h))
         return out
 
-    def conv2d(self, ct, in_ch, k, stride, pad, in_h, in_w, w, bias=None, out=None):
-        w, b = self._conv2d_weights(in_ch, k, w, bias)
+    def conv2d(self, ct, in_ch, out_ch, k, stride, pad, in_h, in_w, w, bias=None, out=None):
+        """w: w[out_ch][in_ch][k][k]; bias: out_ch values or None (fheon_conv2d)."""
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        _need(w.size == out_ch * in_ch * k * k,
+              "conv2d weights must be w[%d][%d][%d][%d], got %d values" % (out_ch, in_ch, k, k, w.size))
+        b = _bias(bias, out_ch)
         out = out or self.ct_create(1)
-        self._chk(load().fheon_conv2d(self.h, ct.h, in_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b), out.h))
+        self._chk(load().fheon_conv2d(self.h, ct.h, in_ch, out_ch, k, stride, pad, in_h, in_w, _dblp(w), _dblp(b),
+                                      out.h))
         return out
 
 

@@ -210,3 +210,50 @@ def test_one_shot_layers_and_key_budget(pair):
     with pytest.raises(pair.F.FheonError) as e:
         g.bootstrap(ct)
     assert e.value.code == -4
+
+
+@pytest.mark.parametrize("C,F,k,s,p,H,levels", [(3, 4, 3, 2, 1, 8, 2), (1, 6, 5, 1, 0, 12, 2), (2, 3, 3, 1, 1, 8, 1)])
+def test_conv2d_one_shot_general(pair, C, F, k, s, p, H, levels):
+    """fheon_conv2d(in_ch, out_ch, k, stride, pad) on the flattened (C, H, W)
+    map (Sec. 5.1-5.2): the compact (F, Ho, Wo) output within 1e-4 of the FP64
+    convolution (decryption noise at scale 2^40 is ~1e-7), zero elsewhere; and
+    the same ciphertext, bit for bit, as the two prepared layers it is made of
+    (the rotation-sum conv, then the repack to the compact map when needed)."""
+    pr = pair
+    g = pr.g
+    level = 8
+    X = synth.image(95, C, (C, H, H))
+    K = synth.conv_kernel(95, F, (F, C, k, k), std=0.3)
+    b = synth.image(95, 99, (F,), dist="normal") * 0.1
+    n = pr.N // 2
+    x = np.zeros(n)
+    x[:X.size] = X.reshape(-1)
+    pr.add_keys(g.conv2d_rotation_steps(C, F, k, s, p, H, H))
+    ct = g.drop_level(g.encrypt(pr.pk, g.encode(x, pr.L, pr.P["scale"]), nonce=9500 + C), level)
+    out = g.conv2d(ct, C, F, k, s, p, H, H, K, bias=b)
+    assert g.ct_info(out)[0] == level - levels
+    want = OF.conv2d_fp64(X, K, b=b, stride=s, pad=p)
+    y = np.asarray(g.decode(g.decrypt(pr.sk, out))).real
+    assert np.max(np.abs(y[:want.size] - want.reshape(-1))) < 1e-4
+    assert np.max(np.abs(y[want.size:])) < 1e-4
+    # the composition of prepared layers
+    conv = g.conv_prepare((C, H, H, H, 1, H * H), K, p, level, pr.P["scale"], bias=b, stride=s)
+    mid = g.layer_apply(conv, ct)
+    Ho = (H + 2 * p - k) // s + 1
+    if levels == 2:
+        rp = g.repack_prepare(g.layer_out_map(conv), (F, Ho, Ho, Ho, 1, Ho * Ho), level - 1)
+        mid = g.layer_apply(rp, mid)
+    assert gpu_common.mismatch(g.ct_download(out), g.ct_download(mid)) == 0
+
+
+def test_conv2d_refuses_what_it_cannot_compute(pair):
+    """A kernel larger than the padded input is refused by the key list and
+    by the call, before any device work."""
+    g = pair.g
+    with pytest.raises(pair.F.FheonError) as e:
+        g.conv2d_rotation_steps(1, 1, 9, 1, 0, 4, 4)
+    assert e.value.code == -1
+    ct = g.encrypt(pair.pk, g.encode(np.zeros(16), pair.L, pair.P["scale"]), nonce=9600)
+    with pytest.raises(pair.F.FheonError) as e:
+        g.conv2d(ct, 1, 2, 9, 1, 0, 4, 4, np.zeros((2, 1, 9, 9)))
+    assert e.value.code == -1

@@ -270,7 +270,7 @@ def test_conv2d_matches_fp64(conv13):
     x = np.zeros(pr.N // 2)
     x[:H * W] = X.reshape(-1)
     ct = g.encrypt(pr.pk, g.encode(x, pr.L, P["scale"]), nonce=1)
-    out = g.conv2d(ct, 1, 5, 1, 2, H, W, K[0])
+    out = g.conv2d(ct, 1, 1, 5, 1, 2, H, W, K)
     lv, sc = g.ct_info(out)
     assert lv == 2 and abs(sc - P["scale"]) / P["scale"] < 1e-12
     y = g.decode(g.decrypt(pr.sk, out)).real
@@ -391,13 +391,14 @@ def test_multichannel_special_conv_matches_fp64(conv13):
     g = pr.g
     P = pr.P
     C, H, W, k = 2, 8, 8, 3
-    pr.add_keys(g.conv2d_rotation_steps(C, k, H, W))
+    pr.add_keys(OF.conv_rotation_steps(W, k) + [H * W])
     X = synth.image(P["seed"], 40, (C, H, W))
     K = synth.conv_kernel(P["seed"], 41, (1, C, k, k), std=0.3)
     x = np.zeros(pr.N // 2)
     x[:C * H * W] = X.reshape(-1)
     ct = g.encrypt(pr.pk, g.encode(x, pr.L, P["scale"]), nonce=40)
-    out = g.conv2d(ct, C, k, 1, 1, H, W, K[0], bias=[0.2])
+    layer = g.conv2d_prepare(C, k, 1, 1, H, W, K[0], [0.2], pr.L, P["scale"])
+    out = g.conv2d_apply(layer, ct)
     assert g.ct_info(out)[0] == pr.L - 2
     y = np.asarray(g.decode(g.decrypt(pr.sk, out))).real
     want = OF.conv2d_fp64(X, K, b=[0.2], pad=1).reshape(-1)

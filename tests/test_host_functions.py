@@ -70,19 +70,47 @@ def test_binding_refuses_arrays_of_the_wrong_size():
         C_._conv2d_weights(1, 5, np.zeros((5, 5)), [0.1, 0.2])
 
 
-@pytest.mark.parametrize("C,k,H,W", [(1, 3, 6, 6), (1, 5, 28, 28), (3, 5, 7, 9), (16, 3, 32, 32)])
-def test_conv_rotation_steps_are_the_oracle_taps(C, k, H, W):
+@pytest.mark.parametrize("k,H,W", [(3, 6, 6), (5, 28, 28), (5, 7, 9)])
+def test_special_conv_rotation_steps_are_the_oracle_taps(k, H, W):
     """The special conv's key list: one step per non-identity tap (the oracle's
-    list, the same set), plus H*W for the channel sum when C > 1."""
+    list, the same set)."""
     import ctypes
     L = F.load()
     n = ctypes.c_uint32(0)
-    assert L.fheon_conv2d_rotation_steps(C, k, H, W, None, ctypes.byref(n)) == 0
+    pad = (k - 1) // 2
+    assert L.fheon_conv2d_rotation_steps(1 << 13, 1, 1, k, 1, pad, H, W, None, ctypes.byref(n)) == 0
     out = (ctypes.c_int32 * n.value)()
-    assert L.fheon_conv2d_rotation_steps(C, k, H, W, out, ctypes.byref(n)) == 0
-    want = set(OF.conv_rotation_steps(W, k)) | ({H * W} if C > 1 else set())
+    assert L.fheon_conv2d_rotation_steps(1 << 13, 1, 1, k, 1, pad, H, W, out, ctypes.byref(n)) == 0
+    want = set(OF.conv_rotation_steps(W, k))
     assert sorted(out) == sorted(want) and len(out) == len(want)
-    assert L.fheon_conv2d_rotation_steps(C, 4, H, W, out, ctypes.byref(n)) == -1  # even kernel
+    small = (ctypes.c_int32 * 1)()
+    n = ctypes.c_uint32(1)
+    assert L.fheon_conv2d_rotation_steps(1 << 13, 1, 1, k, 1, pad, H, W, small, ctypes.byref(n)) == -1  # no room
+    assert L.fheon_conv2d_rotation_steps(1000, 1, 1, k, 1, pad, H, W, None, ctypes.byref(n)) == -1  # N not 2^k
+
+
+@pytest.mark.parametrize("C,Fo,k,s,pad,H", [(3, 4, 3, 2, 1, 8), (2, 3, 5, 1, 0, 12), (16, 16, 3, 1, 1, 32),
+                                           (1, 6, 5, 1, 0, 28)])
+def test_general_conv_rotation_steps_are_the_oracle_plans(C, Fo, k, s, pad, H):
+    """The general conv's key list: the oracle's rotation-sum plan of the
+    convolution (taps and block shifts) and, when the outputs are not compact,
+    the oracle's repack plan to the compact map."""
+    import ctypes
+    N = 1 << 16
+    n = N // 2
+    L = F.load()
+    cnt = ctypes.c_uint32(0)
+    assert L.fheon_conv2d_rotation_steps(N, C, Fo, k, s, pad, H, H, None, ctypes.byref(cnt)) == 0
+    out = (ctypes.c_int32 * cnt.value)()
+    assert L.fheon_conv2d_rotation_steps(N, C, Fo, k, s, pad, H, H, out, ctypes.byref(cnt)) == 0
+    K = np.ones((Fo, C, k, k))
+    r, groups = OF.conv_plan(C, Fo, k, pad, H, H, H, 1, H * H, n, K, stride=s)
+    want = set(OF.linear_steps(r, groups))
+    Ho = (H + 2 * pad - k) // s + 1
+    if s > 1 or Ho != H:
+        rr, gg = OF.repack_plan(Fo, Ho, Ho, (H, s, H * H), (Ho, 1, Ho * Ho), n)
+        want |= set(OF.linear_steps(rr, gg))
+    assert sorted(out) == sorted(want)
 
 
 def test_context_arguments_refused_before_any_device_work():
