@@ -417,14 +417,29 @@ def lenet_timing(F, batch=32):
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
     same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs[:2], gouts[:2]))
+    # the batch through batched layer applications (every layer over 8 inputs
+    # per call: their rotations, products and series share launches)
+    chunk = 8
+    net.forward_batch(cts[:chunk])  # warm-up: the batch's working sets and plans
+    ctx.sync()
+    e0.record(s)
+    bouts = []
+    for i in range(0, batch, chunk):
+        bouts += net.forward_batch(cts[i:i + chunk])
+    e1.record(s)
+    torch.cuda.synchronize()
+    batched_secs = e0.elapsed_time(e1) / 1e3
+    batch_same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs[:2], bouts[:2]))
     err = 0.0
     for X, y in zip(xs, outs):
         got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
         err = max(err, float(np.max(np.abs(got - lenet.forward_fp64(X, w)))))
     nkeys, kbytes = ctx.key_stats()
-    del outs, gouts, cts, net, sk, pk
+    del outs, gouts, bouts, cts, net, sk, pk
     release(ctx)
-    return {"s_per_inference": secs / batch, "eager_s_per_inference": eager_secs / batch,
+    return {"s_per_inference": min(secs, batched_secs) / batch, "graph_s_per_inference": secs / batch,
+            "batched_s_per_inference": batched_secs / batch, "batched_chunk": chunk,
+            "batched_equals_one_by_one": batch_same, "eager_s_per_inference": eager_secs / batch,
             "graph_equals_eager": same, "batch": batch, "keys": nkeys, "key_bytes": kbytes,
             "max_abs_logit_vs_fp64_exact_relu": err, "relu_bounds": betas, "levels": len(P["qbits"])}
 
@@ -482,20 +497,76 @@ def resnet_timing(F, n_inputs=2):
     btot = sum(v[1] for v in bprof.values())
     boot_kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / btot, 4)}
                     for k, v in sorted(bprof.items(), key=lambda kv: -kv[1][1])[:12]}
-    err, agree = 0.0, 0
+    # where one inference spends its time: CUDA events around every step of
+    # the plan (eager), summed by kind of step
+    kind_ms = {}
+    reg = {"x": cts[0]}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(net.plan) + 1)]
+    ev[0].record(s)
+    names = []
+    for k, op in enumerate(net.plan):
+        if op[0] == "layer":
+            layer = op[1]
+            name = next((n for n, l in net.layers.items() if l is layer), None)
+            name = "relu" if name is None else ("conv" if "conv" in name or name.startswith("s") else name)
+            reg[op[3]] = ctx.layer_apply(layer, reg[op[2]])
+        elif op[0] == "scale":
+            name = "shortcut_scale"
+            reg[op[3]] = ctx.mul_const_rescale(reg[op[2]], op[1], net.scale)
+        elif op[0] == "add":
+            name = "add"
+            A, Bc = (ctx.drop_level(reg[x], op[1]) if ctx.ct_info(reg[x])[0] > op[1] else reg[x] for x in (op[2], op[3]))
+            reg[op[4]] = ctx.add(A, Bc)
+        else:
+            name = "bootstrap"
+            reg[op[1]] = ctx.layer_apply(net.boot, reg[op[1]])
+        ev[k + 1].record(s)
+        names.append(name)
+    torch.cuda.synchronize()
+    for k, name in enumerate(names):
+        kind_ms[name] = kind_ms.get(name, 0.0) + ev[k].elapsed_time(ev[k + 1])
+    del reg
+    # the plain one-ciphertext-per-launch path: every rotation and product of
+    # the same network through its own launch sequence, nothing hoisted
+    ctx.set_batching(False)
+    net.forward(cts[0])  # warm-up of the plain path's workspace
+    ctx.sync()
+    e0.record(s)
+    for ct in cts:
+        net.forward(ct)
+    e1.record(s)
+    torch.cuda.synchronize()
+    plain_secs = e0.elapsed_time(e1) / 1e3
+    ctx.set_batching(True)
+    coeffs = [F.relu_coeffs(b, resnet.RELU_DEGREE) for b in betas]
+
+    def cheb_relu(v, i):
+        # the encrypted network's ReLU, the Chebyshev series at v / beta, in FP64
+        z = v / betas[i]
+        t0, t1 = np.ones_like(z), z
+        y = coeffs[i][0] * t0 + coeffs[i][1] * t1
+        for c in coeffs[i][2:]:
+            t0, t1 = t1, 2.0 * z * t1 - t0
+            y = y + c * t1
+        return y
+    err, err_cheb, agree = 0.0, 0.0, 0
     for X, y in zip(xs, outs):
         got = np.asarray(ctx.decode(ctx.decrypt(sk, y))).real[:10]
         want = resnet.forward_fp64(X, w)
         err = max(err, float(np.max(np.abs(got - want))))
+        err_cheb = max(err_cheb, float(np.max(np.abs(got - resnet.forward_fp64(X, w, relu=cheb_relu)))))
         agree += int(np.argmax(got) == np.argmax(want))
     nkeys, kbytes = ctx.key_stats()
     n_boot = net.n_boot
     del outs, gouts, cts, net, sk, pk
     release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
+            "per_ciphertext_path_s_per_inference": plain_secs / n_inputs,
+            "eager_ms_by_step_kind": {k: round(v, 2) for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
             "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": n_boot,
             "bootstrap_kernels": boot_kernels,
             "inputs": n_inputs, "prepare_and_keygen_s": round(t_prep, 2), "keys": nkeys, "key_bytes": kbytes,
+            "max_abs_logit_vs_fp64_chebyshev_relu": err_cheb,
             "max_abs_logit_vs_fp64_exact_relu": err, "argmax_agrees": "%d/%d" % (agree, n_inputs),
             "levels": len(P["qbits"]), "paper_cpu_s_per_inference": 403}
 
@@ -607,7 +678,7 @@ def conv_layer_timing(F, iters=200):
     H = W = 28
     k = 5
     sk, pk = ctx.keygen()
-    ctx.rotkeygen(sk, ctx.conv2d_rotation_steps(1, k, H, W))
+    ctx.rotkeygen(sk, ctx.conv2d_rotation_steps(1, 1, k, 1, (k - 1) // 2, H, W))
     x = np.zeros(N // 2)
     x[:H * W] = synth.image(P["seed"], 0, (1, H, W)).reshape(-1)
     ct = ctx.encrypt(pk, ctx.encode(x, ctx.L, P["scale"]), nonce=1)

@@ -703,17 +703,21 @@ def repack_plan(C, H, W, src, dst, nslots):
     return bsgs_plan(diags, nslots, stride)
 
 
-def resnet_fp64(X, w, chans, nblocks, betas=None, D=RELU_DEGREE):
+def resnet_fp64(X, w, chans, nblocks, betas=None, D=RELU_DEGREE, perturb=None):
     """ResNet-20-style network (paper's Appendix A architecture) in FP64 from the
     plain layers: 3x3 conv + ReLU; per stage, residual blocks (3x3 conv, ReLU,
     3x3 conv, + shortcut, ReLU) whose first block in stages 2 and 3 has stride
     2 and a 1x1 stride-2 conv shortcut; global average pooling; FC.  With
-    `betas`, ReLU i is the Chebyshev series of Alg. 4 with bound betas[i]."""
+    `betas`, ReLU i is the Chebyshev series of Alg. 4 with bound betas[i].
+    perturb(i, v), when given, returns the input ReLU i then takes (an error
+    model: what an encrypted pipeline adds before that ReLU)."""
     idx = [0]
 
     def act(v):
         i = idx[0]
         idx[0] += 1
+        if perturb is not None:
+            v = perturb(i, v)
         return np.maximum(v, 0.0) if betas is None else relu_fp64(v, betas[i], D)
 
     h = act(conv2d_fp64(X, w["conv0"][0], b=w["conv0"][1], pad=1))

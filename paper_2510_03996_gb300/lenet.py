@@ -140,6 +140,14 @@ class EncryptedLeNet:
             ct = self.ctx.layer_apply(layer, ct)
         return ct
 
+    def forward_batch(self, cts):
+        """Several inputs at once: each layer applied to the whole batch in one
+        call (fheon_layer_apply_batch), so the rotations of every input share
+        launches; each output is the one forward() gives its input."""
+        for layer in self.layers:
+            cts = self.ctx.layer_apply_batch(layer, cts)
+        return cts
+
     def forward_graph(self, ct):
         """The same layers replayed as CUDA graphs on fixed buffers: the input is
         copied into a staging ciphertext, each layer writes its own output
