@@ -65,12 +65,17 @@ def read_header(path):
 
 
 def _write_atomically(path, body):
-    """body(f) writes the file through a temporary beside it, which replaces
-    `path` only when body returns; on any error it is removed."""
-    tmp = path + ".tmp"
+    """body(f) writes the file through a temporary of its own beside it
+    (a unique name, so concurrent saves do not meet), flushed to the disk
+    before it replaces `path`, only when body returns; on any error it is
+    removed."""
+    import tempfile
+    fd, tmp = tempfile.mkstemp(dir=os.path.dirname(os.path.abspath(path)), prefix=os.path.basename(path) + ".")
     try:
-        with open(tmp, "wb") as f:
+        with os.fdopen(fd, "wb") as f:
             body(f)
+            f.flush()
+            os.fsync(f.fileno())
         os.replace(tmp, path)
     except BaseException:
         if os.path.exists(tmp):
@@ -190,13 +195,18 @@ def load_keys(ctx, path, galois=None):
     meta, _ = read_header(path)
     _match(ctx, meta, ("N", "L", "K", "alpha", "beta", "moduli"))
     want = None if galois is None else {int(g) for g in galois}
+    # all or nothing: every selected key is read and checked before the first
+    # is installed
+    have = [int(g) for g in meta["galois"]]
+    if want is not None and want - set(have):
+        raise CheckpointError("%s has no key for %s" % (path, sorted(want - set(have))))
+    for g, _ in iter_keys(path, ctx.moduli):
+        pass  # iter_keys checks every residue of every key
     done = []
     for g, a in iter_keys(path, ctx.moduli):
         if want is None or g in want:
             ctx.key_upload(g, a)
             done.append(g)
-    if want is not None and want - set(done):
-        raise CheckpointError("%s has no key for %s" % (path, sorted(want - set(done))))
     return done
 
 
