@@ -404,36 +404,77 @@ def unpack_map(v, shape, grid, dil, block):
     return np.asarray(v)[map_slots(*shape, grid, dil, block)].reshape(shape)
 
 
-def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K, stride=1):
+def conv_baby(k, C, F):
+    """Baby steps B of the block shifts: the B minimising B k^2 - 1 + 2 ceil(G/B),
+    G = C + F - 1 (the hoisted tap rotations, plus the giant steps counted at
+    twice a hoisted rotation), the smaller on ties."""
+    G = C + F - 1
+    best, cost = 1, None
+    for B in range(1, G + 1):
+        c = k * k * B - 1 + 2 * (-(-G // B))
+        if cost is None or c < cost:
+            best, cost = B, c
+    return best
+
+
+def conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K, stride=1, baby=None):
     """Rotation-sum plan of a convolution (Sec. 5.1 equation, zero padding
-    `pad`, stride `stride`) from C to F channels: tap t = (x, y) reads the input
-    at offset (x - pad, y - pad), i.e. Rot_{r_t} with r_t = dil*((x-pad)*grid +
-    (y-pad)); group delta = f - c collects, in the block of input channel c, the
-    weights K[f, c, x, y] at every output position -- input-grid position
-    (stride*i, stride*j), so the output dilation is dil*stride -- whose tap
-    source lies inside the input; its sum is moved to block f by
-    Rot_{-delta*block}.  Returns (r, [(s_g, [values_t or None])]); all-zero
-    plaintexts are None."""
+    `pad`, stride `stride`) from C to F channels.  Tap (x, y) reads the input
+    at offset (x - pad, y - pad), i.e. Rot_r with r = dil*((x-pad)*grid +
+    (y-pad)).  Block shift delta = f - c collects, in the block of input
+    channel c, the weights K[f, c, x, y] at every output position --
+    input-grid position (stride*i, stride*j), so the output dilation is
+    dil*stride -- whose tap source lies inside the input; it moves to block f
+    by Rot_{-delta*block}.  The shifts go by baby steps and giant steps:
+    delta = a + B b (0 <= a < B = conv_baby unless `baby` is given) and
+      Rot_{-delta block}(P * Rot_r(x)) = Rot_{-B b block}(Rot_{-a block}(P) * Rot_{r - a block}(x)),
+    so the taps are r - a*block (a-major, then (x, y); a step shared by two
+    pairs appears once, with their vectors summed) and group b shifts by
+    -B*b*block with the vectors moved by a*block.  Returns (r, [(s_g, [values_t
+    or None])]); all-zero plaintexts are None, groups without any are left out."""
     Ho, Wo = (H + 2 * pad - k) // stride + 1, (W + 2 * pad - k) // stride + 1
+    B = conv_baby(k, C, F) if baby is None else baby
     taps = [(x, y) for x in range(k) for y in range(k)]
-    r = [dil * ((x - pad) * grid + (y - pad)) for x, y in taps]
-    groups = []
-    for delta in range(-(C - 1), F):
-        vals = []
+    # each step once: where the taps span more than a block, pairs (a, tap)
+    # can share a step, and their vectors are summed (in (a, tap) order)
+    r, index = [], []
+    for a in range(B):
         for x, y in taps:
-            v = np.zeros(nslots)
-            for c in range(C):
-                f = c + delta
-                if not 0 <= f < F:
-                    continue
-                for i in range(Ho):
-                    for j in range(Wo):
-                        si, sj = stride * i + x - pad, stride * j + y - pad
-                        if 0 <= si < H and 0 <= sj < W:
-                            v[c * block + dil * stride * (i * grid + j)] = K[f][c][x][y]
-            vals.append(v if np.any(v != 0.0) else None)
+            st = dil * ((x - pad) * grid + (y - pad)) - a * block
+            if st not in r:
+                r.append(st)
+            index.append(r.index(st))
+
+    def add_vec(acc, delta, x, y, a):
+        any_ = False
+        for c in range(C):
+            f = c + delta
+            if not 0 <= f < F or K[f][c][x][y] == 0.0:
+                continue
+            for i in range(Ho):
+                for j in range(Wo):
+                    si, sj = stride * i + x - pad, stride * j + y - pad
+                    if 0 <= si < H and 0 <= sj < W:
+                        s_ = (c * block + dil * stride * (i * grid + j) + a * block) % nslots
+                        acc[s_] = acc[s_] + K[f][c][x][y]
+                        any_ = True
+        return any_
+
+    groups = []
+    for b in range((-(C - 1)) // B, (F - 1) // B + 1):
+        acc = [np.zeros(nslots) for _ in r]
+        used = [False] * len(r)
+        for a in range(B):
+            delta = a + B * b
+            if not -(C - 1) <= delta <= F - 1:
+                continue
+            for ti, (x, y) in enumerate(taps):
+                t = index[a * len(taps) + ti]
+                if add_vec(acc[t], delta, x, y, a):
+                    used[t] = True
+        vals = [v if u and np.any(v != 0.0) else None for v, u in zip(acc, used)]
         if any(v is not None for v in vals):
-            groups.append((-delta * block, vals))
+            groups.append((-B * b * block, vals))
     return r, groups
 
 

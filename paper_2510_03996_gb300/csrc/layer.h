@@ -118,6 +118,10 @@ Bsgs bsgs_plan(const Diags &D, u32 n, u32 stride, u32 baby);
 std::set<int64_t> bsgs_offsets(const std::set<u32> &offsets, u32 n, u32 stride);
 void bsgs_split(const std::set<int64_t> &ks, int64_t M, u32 baby, int64_t &bs, std::set<int64_t> &ts,
                 std::set<int64_t> &cs);
+// baby steps B of a C -> F convolution with a k x k kernel: the B minimising
+// B k^2 - 1 + 2 ceil((C + F - 1) / B) (hoisted tap rotations, plus the giant
+// steps at twice a hoisted rotation's cost), the smaller on ties
+u32 conv_baby(u32 k, u32 C, u32 F);
 // rotation steps of the repack layer from map a to map b (the plan of
 // fheon_repack_prepare, without encoding it); FHEON_ERR_ARG as that call
 int repack_steps(u32 n, const fheon_map &a, const fheon_map &b, std::vector<int32_t> &steps);

@@ -82,13 +82,18 @@ int fheon_conv2d_rotation_steps(uint32_t N, uint32_t in_ch, uint32_t out_ch, uin
         // repack of its output to the compact (F, Ho, Wo) layout when needed
         const u32 nsl = N / 2, block = in_h * in_w;
         if ((u64)std::max(in_ch, out_ch) * block > nsl) return FHEON_ERR_ARG;
-        for (u32 x = 0; x < k; x++)
-            for (u32 y = 0; y < k; y++) {
-                const int32_t r = ((int32_t)x - (int32_t)pad) * (int32_t)in_w + ((int32_t)y - (int32_t)pad);
-                if (r) s.insert(r);
-            }
-        for (int delta = -(int)(in_ch - 1); delta < (int)out_ch; delta++)
-            if (delta) s.insert(-delta * (int32_t)block);
+        // the plan's hoisted taps r - a*block (a < B) and giant steps -B*b*block
+        const u32 B = conv_baby(k, in_ch, out_ch);
+        for (u32 a = 0; a < B; a++)
+            for (u32 x = 0; x < k; x++)
+                for (u32 y = 0; y < k; y++) {
+                    const int32_t r = ((int32_t)x - (int32_t)pad) * (int32_t)in_w + ((int32_t)y - (int32_t)pad) -
+                                      (int32_t)(a * block);
+                    if (r) s.insert(r);
+                }
+        auto fdiv = [](int x, int d) { return x >= 0 ? x / d : -((-x + d - 1) / d); };
+        for (int b = fdiv(-(int)(in_ch - 1), (int)B); b <= fdiv((int)out_ch - 1, (int)B); b++)
+            if (b) s.insert(-b * (int32_t)B * (int32_t)block);
         fheon_map om, cm;
         conv2d_maps(in_ch, out_ch, k, stride, pad, in_h, in_w, om, cm);
         if (!same_map(om, cm)) {

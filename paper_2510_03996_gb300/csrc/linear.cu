@@ -11,11 +11,16 @@
 // The tap rotations r_t are hoisted from the input (one raising of c1); each
 // group's products are summed in one pass (fheon_mac_plain) and rescaled once;
 // the group sums move by one batched rotation and are added.  A conv from C to
-// F channels has one group per block shift delta = f - c: in the block of
-// input channel c it holds K[f, c, x, y] at every output position whose tap
-// source (i + x - pad, j + y - pad) lies inside the input, and s = -delta*block
-// moves that partial sum into block f.  Tap t = (x, y) reads the input at
-// r_t = dil*((x - pad)*grid + (y - pad)).
+// F channels sums, for every block shift delta = f - c, the products that in
+// the block of input channel c hold K[f, c, x, y] at every output position
+// whose tap source (i + x - pad, j + y - pad) lies inside the input, moved to
+// block f by Rot_{-delta*block}.  Tap (x, y) reads the input at
+// r = dil*((x - pad)*grid + (y - pad)).  The shifts go by baby steps and giant
+// steps: delta = a + B*b, Rot_{-delta*block}(P * Rot_r(x)) =
+// Rot_{-B*b*block}(Rot_{-a*block}(P) * Rot_{r - a*block}(x)), so the layer's
+// taps are the B*k^2 hoisted rotations r - a*block and its groups the giant
+// steps b, with B (conv_baby) the fewest rotations when a plain rotation costs
+// two hoisted ones: B k^2 - 1 + 2 ceil((C + F - 1)/B).
 //
 // FC: t_k = rescale(in * W_k) (W_k: row k of the weights at the input's
 // slots); every t_k through the rotate-and-add slot sum (steps 1, 2, 4, ...,
@@ -226,6 +231,21 @@ int check_pt(fheon_ctx *ctx, const fheon_pt *p, u32 level, const char *what)
 } // namespace
 
 namespace fheon {
+u32 conv_baby(u32 k, u32 C, u32 F)
+{
+    const u64 G = (u64)C + F - 1, taps = (u64)k * k;
+    u32 best = 1;
+    u64 best_cost = ~0ull;
+    for (u64 B = 1; B <= G; B++) {
+        const u64 cost = taps * B - 1 + 2 * ((G + B - 1) / B);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = (u32)B;
+        }
+    }
+    return best;
+}
+
 int repack_steps(u32 n, const fheon_map &a, const fheon_map &b, std::vector<int32_t> &steps)
 {
     std::map<u32, std::vector<u32>> dst_of;
@@ -321,35 +341,74 @@ int fheon_conv_prepare(fheon_ctx *ctx, const fheon_map *in, uint32_t F, uint32_t
     ly->level = level;
     ly->in_map = im;
     ly->out_map = om;
+    // block shift delta = a + B*b: baby a in [0, B) taken by the hoisted tap
+    // rotations r_t - a*block, giant b by the group's rotation -B*b*block
+    const u32 B = fheon::conv_baby(k, C, F);
+    std::vector<int32_t> tap;
     for (u32 x = 0; x < k; x++)
         for (u32 y = 0; y < k; y++)
-            ly->r.push_back((int32_t)im.dil * (((int32_t)x - (int32_t)pad) * (int32_t)im.grid + ((int32_t)y - (int32_t)pad)));
+            tap.push_back((int32_t)im.dil * (((int32_t)x - (int32_t)pad) * (int32_t)im.grid + ((int32_t)y - (int32_t)pad)));
+    // the layer's tap steps r - a*block, each once: on a map whose taps span
+    // more than a block, two (a, tap) pairs can share a step, and their vectors
+    // are summed (in (a, tap) order) into that step's plaintext
+    std::vector<u32> tix; // (a, tap) -> index into ly->r
+    for (u32 a = 0; a < B; a++)
+        for (int32_t r : tap) {
+            const int32_t st = r - (int32_t)(a * im.block);
+            auto it = std::find(ly->r.begin(), ly->r.end(), st);
+            tix.push_back((u32)(it - ly->r.begin()));
+            if (it == ly->r.end()) ly->r.push_back(st);
+        }
+    const u32 nt = (u32)ly->r.size();
     const double ps = (double)ctx->mod[level - 1];
     std::vector<double> v(n);
-    int rc;
-    for (int delta = -(int)(C - 1); delta < (int)F; delta++) {
-        std::vector<fheon_pt *> gp;
+    // adds the weights of block shift delta, tap (x, y), in the input channels'
+    // blocks, moved by a*block (Rot_{-a*block}), into acc; true when any is nonzero
+    auto add_group_vec = [&](int delta, u32 x, u32 y, u32 a, std::vector<double> &acc) {
         bool any = false;
-        for (u32 x = 0; x < k; x++)
-            for (u32 y = 0; y < k; y++) {
-                std::fill(v.begin(), v.end(), 0.0);
-                for (u32 c = 0; c < C; c++) {
-                    const int f = (int)c + delta;
-                    if (f < 0 || f >= (int)F) continue;
-                    const double w = K[(((size_t)f * C + c) * k + x) * k + y];
-                    for (u32 i = 0; i < Ho; i++)
-                        for (u32 j = 0; j < Wo; j++) {
-                            const int si = (int)(stride * i + x) - (int)pad, sj = (int)(stride * j + y) - (int)pad;
-                            if (si >= 0 && si < (int)im.H && sj >= 0 && sj < (int)im.W) v[map_slot(om, c, i, j)] = w;
-                        }
+        for (u32 c = 0; c < C; c++) {
+            const int f = (int)c + delta;
+            if (f < 0 || f >= (int)F) continue;
+            const double w = K[(((size_t)f * C + c) * k + x) * k + y];
+            if (w == 0.0) continue;
+            for (u32 i = 0; i < Ho; i++)
+                for (u32 j = 0; j < Wo; j++) {
+                    const int si = (int)(stride * i + x) - (int)pad, sj = (int)(stride * j + y) - (int)pad;
+                    if (si >= 0 && si < (int)im.H && sj >= 0 && sj < (int)im.W) {
+                        double &d = acc[(map_slot(om, c, i, j) + (size_t)a * im.block) % n];
+                        d = d + w;
+                        any = true;
+                    }
                 }
-                fheon_pt *p = nullptr;
-                if ((rc = own_plain(ctx, ly.get(), v, level, ps, &p))) return rc;
-                gp.push_back(p);
-                any = any || p;
-            }
+        }
+        return any;
+    };
+    const int dmin = -(int)(C - 1), dmax = (int)F - 1;
+    auto fdiv = [](int x, int d) { return x >= 0 ? x / d : -((-x + d - 1) / d); };
+    std::vector<std::vector<double>> acc(nt, std::vector<double>(n));
+    std::vector<char> used(nt);
+    int rc;
+    for (int b = fdiv(dmin, (int)B); b <= fdiv(dmax, (int)B); b++) {
+        for (auto &w : acc) std::fill(w.begin(), w.end(), 0.0);
+        std::fill(used.begin(), used.end(), 0);
+        for (u32 a = 0; a < B; a++) {
+            const int delta = (int)a + (int)B * b;
+            if (delta < dmin || delta > dmax) continue;
+            for (u32 x = 0; x < k; x++)
+                for (u32 y = 0; y < k; y++) {
+                    const u32 t = tix[(size_t)a * k * k + x * k + y];
+                    if (add_group_vec(delta, x, y, a, acc[t])) used[t] = 1;
+                }
+        }
+        std::vector<fheon_pt *> gp(nt, nullptr);
+        bool any = false;
+        for (u32 t = 0; t < nt; t++) {
+            if (!used[t]) continue;
+            if ((rc = own_plain(ctx, ly.get(), acc[t], level, ps, &gp[t]))) return rc;
+            any = any || gp[t];
+        }
         if (!any) continue;
-        ly->s.push_back(-delta * (int32_t)im.block);
+        ly->s.push_back(-b * (int32_t)B * (int32_t)im.block);
         ly->pts.insert(ly->pts.end(), gp.begin(), gp.end());
     }
     if (bias) {

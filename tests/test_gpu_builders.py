@@ -123,11 +123,17 @@ def enc_map(pr, X, grid, dil, block, nonce, level):
     return ct, oct_
 
 
-def test_conv_builder(pair):
-    """fheon_conv_prepare: 3 -> 4 channels, 3x3, stride 2, pad 1, with bias."""
+@pytest.mark.parametrize("C,F,k,s,p,H,grid,dil,block,babies", [
+    (3, 4, 3, 2, 1, 8, 8, 1, 64, 1), (8, 8, 3, 1, 1, 4, 4, 1, 16, 2), (4, 8, 1, 2, 0, 8, 8, 1, 64, 4),
+    (8, 8, 3, 1, 1, 2, 4, 2, 16, 2)])
+def test_conv_builder(pair, C, F, k, s, p, H, grid, dil, block, babies):
+    """fheon_conv_prepare: 3 -> 4 channels, 3x3, stride 2, pad 1, with bias;
+    8 -> 8 channels (block shifts by baby steps of 2 and giant steps); a 1x1
+    stride-2 convolution 4 -> 8 (baby steps of 4); 8 -> 8 on a dilated map
+    whose taps span more than a block (shared baby-step taps merged)."""
     pr = pair
-    C, F, k, s, p, H = 3, 4, 3, 2, 1, 8
-    grid, dil, block, level = 8, 1, 64, 6
+    level = 6
+    assert OF.conv_baby(k, C, F) == babies
     X = synth.image(90, 0, (C, H, H))
     K = synth.conv_kernel(90, 1, (F, C, k, k), std=0.3)
     b = synth.image(90, 2, (F,), dist="normal") * 0.1

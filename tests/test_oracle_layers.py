@@ -19,14 +19,27 @@ def test_conv_plan_is_the_convolution(C, F, k, pad, H, grid, dil):
     nslots = 1 << int(np.ceil(np.log2(max(C, F) * block + 1)))
     X = synth.image(11, C, (C, H, W), dist="normal")
     K = synth.conv_kernel(11, F, (F, C, k, k))
-    r, groups = OF.conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K)
-    y = OF.linear_slots(OF.pack_map(X, nslots, grid, dil, block), r, groups)
     want = OF.conv2d_fp64(X, K, pad=pad)
-    assert np.max(np.abs(OF.unpack_map(y, want.shape, grid, dil, block) - want)) < 1e-12
-    # nothing outside the output map
     rest = np.ones(nslots, bool)
     rest[OF.map_slots(*want.shape, grid, dil, block)] = False
-    assert np.max(np.abs(y[rest])) == 0.0
+    # every split of the block shifts into baby and giant steps is the same map
+    for baby in (None, 1, 2, 3, C + F - 1):
+        r, groups = OF.conv_plan(C, F, k, pad, H, W, grid, dil, block, nslots, K, baby=baby)
+        y = OF.linear_slots(OF.pack_map(X, nslots, grid, dil, block), r, groups)
+        assert np.max(np.abs(OF.unpack_map(y, want.shape, grid, dil, block) - want)) < 1e-12
+        # nothing outside the output map
+        assert np.max(np.abs(y[rest])) < 1e-12
+        B = OF.conv_baby(k, C, F) if baby is None else baby
+        assert len(r) == B * k * k and len(groups) <= -(-(C + F - 1) // B) + 1
+
+
+def test_conv_baby_is_the_fewest_rotations():
+    """B minimises B k^2 - 1 + 2 ceil((C + F - 1)/B), found by brute force."""
+    for k in (1, 3, 5):
+        for C, F in ((1, 6), (6, 16), (16, 16), (16, 32), (64, 64), (3, 4)):
+            G = C + F - 1
+            costs = [k * k * B - 1 + 2 * (-(-G // B)) for B in range(1, G + 1)]
+            assert OF.conv_baby(k, C, F) == 1 + int(np.argmin(costs))
 
 
 @pytest.mark.parametrize("C,F,k,pad,stride,H,grid,dil", [
@@ -183,3 +196,20 @@ def test_repack_moves_every_value(src, dst):
     mask = np.ones(n, dtype=bool)
     mask[OF.map_slots(*shape, *dst)] = False
     assert np.all(out[mask] == 0.0)
+
+
+@pytest.mark.parametrize("baby", [None, 2, 3])
+def test_conv_plan_with_shared_tap_steps(baby):
+    """A dilated map whose taps span more than a block (8 channels of 2x2 on
+    a 4-wide grid, dilation 2, blocks of 16 slots): baby steps r - a*block of
+    different taps coincide and are merged; the plan is still the convolution."""
+    C, F, k, pad, H, grid, dil, block = 8, 8, 3, 1, 2, 4, 2, 16
+    nslots = 256
+    X = synth.image(18, C, (C, H, H), dist="normal")
+    K = synth.conv_kernel(18, F, (F, C, k, k))
+    r, groups = OF.conv_plan(C, F, k, pad, H, H, grid, dil, block, nslots, K, baby=baby)
+    B = OF.conv_baby(k, C, F) if baby is None else baby
+    assert B > 1 and len(set(r)) == len(r) < B * k * k
+    y = OF.linear_slots(OF.pack_map(X, nslots, grid, dil, block), r, groups)
+    want = OF.conv2d_fp64(X, K, pad=pad)
+    assert np.max(np.abs(OF.unpack_map(y, want.shape, grid, dil, block) - want)) < 1e-12
