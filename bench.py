@@ -571,20 +571,22 @@ def resnet_timing(F, n_inputs=2):
             "levels": len(P["qbits"]), "paper_cpu_s_per_inference": 403}
 
 
-def serving_timing(F, n_req=40, rate=4.0, max_active=8, frac_resnet=0.3):
+def serving_timing(F, n_req=200, rate=4.0, max_active=12, frac_resnet=0.3):
     """The serving workload: Poisson arrivals (exponential gaps of mean 1/rate
     s from a seed), each request LeNet-5 (N = 2^15) or, with probability
-    frac_resnet, ResNet-20 with bootstrapping (N = 2^16); one
-    continuous-batching server per context (the ResNet model is a program of
-    layer, bootstrap, add and constant steps over three registers), requests
-    submitted when their arrival time has passed (host clock), the two
-    servers stepped in turn; latency = completion - arrival."""
+    frac_resnet, ResNet-20 with bootstrapping (N = 2^16), both models on one
+    continuous-batching server (fheon_server_*: each context on its own
+    stream, their batches overlapping on the device; the ResNet model is a
+    program of layer, bootstrap, add and constant steps over three registers).
+    Admission by memory: the budget holds the footprints of 8 LeNet-5 and 3
+    ResNet-20 requests (fheon_model_footprint).  Requests are submitted when
+    their arrival time has passed (host clock); latency = completion -
+    arrival."""
     import torch
     from paper_2510_03996_gb300 import lenet, resnet
     kind = synth.rng(synth.SEED_BASE + 5, 802).random(n_req) < frac_resnet
     gaps = synth.rng(synth.SEED_BASE + 5, 801).exponential(1.0 / rate, n_req)
     arrive = np.cumsum(gaps) - gaps[0]
-    servers = []
     # LeNet-5 on its context
     P = synth.params("lenet_n15")
     N = 1 << P["logN"]
@@ -592,16 +594,15 @@ def serving_timing(F, n_req=40, rate=4.0, max_active=8, frac_resnet=0.3):
     c1 = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
                    stream=s1.cuda_stream)
     w = lenet.weights(P["seed"])
-    xs = [synth.image(P["seed"], 800 + i, (1, 28, 28)) for i in range(n_req)]
+    xs = [synth.image(P["seed"], 800 + i, (1, 28, 28)) for i in range(16)]
     sk, pk = c1.keygen()
     c1.relinkeygen(sk)
     ln = lenet.EncryptedLeNet(c1, w, lenet.relu_bounds(xs, w), c1.L, P["scale"])
     c1.rotkeygen(sk, ln.rotation_steps())
     m1 = c1.model(ln.layers)
-    ct1 = {i: c1.encrypt(pk, c1.encode(lenet.pack_input(xs[i], N // 2), c1.L, P["scale"]), nonce=i)
-           for i in range(n_req) if not kind[i]}
-    c1.model_run(m1, next(iter(ct1.values())))  # warm-up
-    servers.append((c1, c1.server(max_active=max_active), m1, ct1))
+    ct1 = [c1.encrypt(pk, c1.encode(lenet.pack_input(X, N // 2), c1.L, P["scale"]), nonce=i)
+           for i, X in enumerate(xs)]
+    c1.model_run(m1, ct1[0])  # warm-up
     # ResNet-20 on its context
     P = synth.params("resnet_n16")
     N = 1 << P["logN"]
@@ -609,17 +610,24 @@ def serving_timing(F, n_req=40, rate=4.0, max_active=8, frac_resnet=0.3):
     c2 = F.Context(N, qbits=P["qbits"], pbits=P["pbits"], dnum=P["dnum"], scale=P["scale"], seed=P["seed"],
                    stream=s2.cuda_stream)
     w = resnet.weights(P["seed"])
-    xs = [synth.image(P["seed"], 900 + i, (3, 32, 32), dist="normal") for i in range(n_req)]
+    xs = [synth.image(P["seed"], 900 + i, (3, 32, 32), dist="normal") for i in range(4)]
     sk, pk = c2.keygen()
-    rn = resnet.EncryptedResNet(c2, w, resnet.relu_bounds(xs[:4], w), P["scale"])
+    rn = resnet.EncryptedResNet(c2, w, resnet.relu_bounds(xs, w), P["scale"])
     rn.keygen(sk)
     m2 = rn.model()
-    ct2 = {i: c2.drop_level(c2.encrypt(pk, c2.encode(resnet.pack_input(xs[i], N // 2), c2.L, P["scale"]), nonce=i),
-                            rn.in_level) for i in range(n_req) if kind[i]}
-    if ct2:
-        c2.model_run(m2, next(iter(ct2.values())))  # warm-up
-    # a ResNet request in flight holds a few GB of working ciphertexts per batch slot
-    servers.append((c2, c2.server(max_active=min(max_active, 4)), m2, ct2))
+    ct2 = [c2.drop_level(c2.encrypt(pk, c2.encode(resnet.pack_input(X, N // 2), c2.L, P["scale"]), nonce=i),
+                         rn.in_level) for i, X in enumerate(xs)]
+    c2.model_run(m2, ct2[0])  # warm-up
+    models = [(c1, m1, ct1), (c2, m2, ct2)]
+    fp = [F.Context.model_footprint(m1, c1.ct_info(ct1[0])[0]), F.Context.model_footprint(m2, rn.in_level)]
+    # the device memory left once both models' keys are resident (free, plus
+    # what torch's cache holds unused), less a margin, bounded by 8 LeNet-5 and
+    # 3 ResNet-20 requests
+    torch.cuda.synchronize()
+    free_b, _ = torch.cuda.mem_get_info()
+    avail = free_b + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+    budget = int(min(8 * fp[0] + 3 * fp[1], 0.8 * avail))
+    srv = c1.server(max_active=max_active, mem_budget=budget)
     c1.sync()
     c2.sync()
     t0 = time.perf_counter()
@@ -629,38 +637,35 @@ def serving_timing(F, n_req=40, rate=4.0, max_active=8, frac_resnet=0.3):
     while len(done) < n_req:
         now = time.perf_counter() - t0
         while nxt < n_req and arrive[nxt] <= now:
-            ctx, srv, model, cts = servers[owner[nxt]]
-            ids[nxt] = srv.submit(model, cts[nxt])
+            ctx, model, cts = models[owner[nxt]]
+            ids[nxt] = srv.submit(model, cts[nxt % len(cts)])
             nxt += 1
         if len(ids) == len(done):
             time.sleep(max(0.0, min(0.01, arrive[nxt] - now)))
             continue
-        for which, (ctx, srv, model, cts) in enumerate(servers):
-            pending = [k for k in ids if k not in done and owner[k] == which]
-            if not pending:
-                continue
-            if srv.step():
-                now = time.perf_counter() - t0
-                for k in pending:
-                    if srv.result(ids[k]) is not None:
-                        done[k] = now
+        if srv.step():
+            now = time.perf_counter() - t0
+            for k in list(ids):
+                if k not in done and srv.result(ids[k]) is not None:
+                    done[k] = now
     lat = np.array([done[k] - arrive[k] for k in range(n_req)])
     span = max(done.values()) - arrive[0]
     out = {"requests": n_req, "arrival_rate_per_s": rate,
            "models": "LeNet-5 (N=2^15) %d, ResNet-20 with bootstrapping (N=2^16) %d" % (n_req - kind.sum(), kind.sum()),
+           "server": "one server over both contexts, their batches overlapping on two streams",
            "throughput_per_s": n_req / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-           "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_active": {"lenet5": max_active,
-                                                                          "resnet20": min(max_active, 4)}}
-    for which, name in ((0, "lenet5"), (1, "resnet20")):
+           "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_active": max_active,
+           "mem_budget_bytes": budget, "device_bytes_available": avail,
+           "footprint_bytes": {"lenet5": fp[0], "resnet20": fp[1]},
+           "mem_waits": srv.model_stats(m1)["mem_waits"], "steps": srv.stats()["steps"]}
+    for which, name, m in ((0, "lenet5", m1), (1, "resnet20", m2)):
         sel = np.array([owner[k] == which for k in range(n_req)])
         if sel.any():
             out[name + "_p50_ms"] = 1e3 * float(np.percentile(lat[sel], 50))
             out[name + "_p99_ms"] = 1e3 * float(np.percentile(lat[sel], 99))
-        st = servers[which][1].stats()
-        out[name + "_max_batch"] = st["max_batch"]
-    for ctx, srv, model, cts in servers:
-        srv.close()
-    del servers, ct1, ct2, ln, rn, m1, m2
+        out[name + "_max_batch"] = srv.model_stats(m)["max_batch"]
+    srv.close()
+    del models, ct1, ct2, ln, rn, m1, m2
     release(c1, c2)
     return out
 
@@ -793,7 +798,8 @@ def run_gpu(args, rank, world, local_rank):
     words = sum(2 * lv * N for lv in levels)
     host_in = torch.empty(words, dtype=torch.int64, pin_memory=True)
     host_out = torch.empty(words, dtype=torch.int64, pin_memory=True)
-    bufs = [(ctx.ct_create_batch(levels, P["scale"]), ctx.ct_create_batch(levels, P["scale"])) for _ in range(2)]
+    depth = args.e2e_depth
+    bufs = [(ctx.ct_create_batch(levels, P["scale"]), ctx.ct_create_batch(levels, P["scale"])) for _ in range(depth)]
     for c, b in zip(ins, bufs[0][0]):
         ctx.drop_level(c, ctx.ct_info(c)[0], out=b)
     ctx.ct_download_many_async(bufs[0][0], host_in.data_ptr())
@@ -804,15 +810,15 @@ def run_gpu(args, rank, world, local_rank):
     def e2e_run(nsteps):
         ev_comp, ev_dn = {}, {}
         for k in range(nsteps):
-            bi, bo = bufs[k % 2]
-            if k >= 2:
-                s_up.wait_event(ev_comp[k - 2])  # the inputs of step k-2 are consumed
+            bi, bo = bufs[k % depth]
+            if k >= depth:
+                s_up.wait_event(ev_comp[k - depth])  # the inputs of step k-depth are consumed
             ctx.ct_upload_many_async(bi, host_in.data_ptr(), s_up.cuda_stream)
             up = torch.cuda.Event()
             up.record(s_up)
             stream.wait_event(up)
-            if k >= 2:
-                stream.wait_event(ev_dn[k - 2])  # the outputs of step k-2 are read out
+            if k >= depth:
+                stream.wait_event(ev_dn[k - depth])  # the outputs of step k-depth are read out
             ctx.rotate_batch(bi, bo, steps)
             ev_comp[k] = torch.cuda.Event(enable_timing=True)
             ev_comp[k].record(stream)
@@ -825,7 +831,7 @@ def run_gpu(args, rank, world, local_rank):
         return [ev_comp[k - 1].elapsed_time(ev_comp[k]) for k in range(1, nsteps)]
 
     e2e_steps = max(4, 2 * args.steps)
-    e2e_run(2)
+    e2e_run(depth)  # warm-up: every device batch once (its rotation plan is made then)
     with ClockSampler(local_rank) as e2e_clk:
         t0 = time.perf_counter()
         e2e_ms = e2e_run(e2e_steps)
@@ -898,7 +904,8 @@ def run_gpu(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e2e_steps, "pipelined": "one upload and one download per step (contiguous ciphertext "
                                                           "batch) on two copy streams, overlapping the key switching of "
-                                                          "neighbouring steps", "result_matches": e2e_ok,
+                                                          "neighbouring steps; %d device batches in flight" % depth,
+                        "result_matches": e2e_ok,
                         "steps_ms": step_summary(e2e_ms), "clocks": e2e_clk.summary()},
                 "clocks": clk.summary(), "gpu_launches": launches, "kernels": kernels,
                 "alu_peaks_tmodmul_s": {k: round(v / 1e12, 4) for k, v in alu_rates.items()},
@@ -918,7 +925,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparisons", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--e2e-depth", type=int, default=4,
+                    help="device batches of the end-to-end pipeline (uploads run up to depth-1 steps ahead)")
     ap.add_argument("--schedule", type=int, default=-1,
                     help="key-switching schedule bits (default: the library's autotuner picks)")
     args = ap.parse_args()

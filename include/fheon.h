@@ -688,21 +688,33 @@ int fheon_model_create(fheon_ctx *ctx, const fheon_layer *const *layers, uint32_
  * the output is complete). */
 int fheon_model_run(fheon_ctx *ctx, const fheon_model *model, const fheon_ct *in, fheon_ct *out);
 int fheon_model_destroy(fheon_model *model);
-/* A server on the context's stream.  A submitted request is admitted while
- * fewer than max_active are in flight and the device has at least min_free
- * bytes free (0: no memory check; the oldest waiting request is admitted when
- * none is in flight); the others wait in arrival order. */
-int fheon_server_create(fheon_ctx *ctx, uint32_t max_active, size_t min_free, fheon_server **out);
+/* Device bytes one request of the model adds in flight with its input at
+ * `level`: its registers and step buffers, the working ciphertexts one more
+ * input adds to each distinct layer of the model (a layer keeps one set per
+ * input of the largest batch it has run), and the largest key-switching
+ * workspace one input of a layer's batch needs.  Keys are not included (they
+ * are resident before serving).  FHEON_ERR_ARG for a level outside [1, L]. */
+int fheon_model_footprint(const fheon_model *model, uint32_t level, size_t *bytes);
+/* A server for requests of models on any contexts (each context runs its
+ * requests on its own stream; ctx is the context errors are reported on).
+ * A submitted request is admitted, in arrival order, while fewer than
+ * max_active are in flight and the footprints (fheon_model_footprint) of the
+ * admitted requests plus its own fit mem_budget bytes (0: no memory limit);
+ * a request that does not fit holds back the later requests of its model,
+ * not those of other models; with nothing in flight the oldest waiting
+ * request is admitted whatever its size. */
+int fheon_server_create(fheon_ctx *ctx, uint32_t max_active, size_t mem_budget, fheon_server **out);
 int fheon_server_destroy(fheon_server *server);
 /* Queue a request: the model on a copy of `in` (taken on the stream now). */
 int fheon_server_submit(fheon_server *server, const fheon_model *model, const fheon_ct *in, uint64_t *id);
 /* One scheduling step: drop the requests past the admission timeout, admit
- * what fits, take the oldest admitted request's
- * stage (model, next step), run that step for every admitted request at that
- * stage (a layer step as one batch, fheon_layer_apply_batch), advance them,
- * and wait for the stream.  *n_done: requests that finished (or were
- * dropped) in this step.  A result
- * equals the model applied to the request's input alone, bit for bit. */
+ * what fits, then on every context with requests in flight take its oldest
+ * request's stage (model, next step) and run that step for every admitted
+ * request at that stage (a layer step as one batch, fheon_layer_apply_batch)
+ * on the context's stream; the contexts' batches are enqueued one after the
+ * other, so they overlap on the device, and then waited for.  *n_done:
+ * requests that finished (or were dropped) in this step.  A result equals
+ * the model applied to the request's input alone, bit for bit. */
 int fheon_server_step(fheon_server *server, uint32_t *n_done);
 /* The result of request `id` into out (then the request is forgotten), or
  * FHEON_PENDING while it runs; FHEON_ERR_ARG for an unknown id;
@@ -717,6 +729,11 @@ int fheon_server_set_admit_timeout(fheon_server *server, double seconds);
 /* Steps taken, the largest batch so far, requests in flight and waiting. */
 int fheon_server_stats(const fheon_server *server, uint64_t *steps, uint32_t *max_batch, uint32_t *active,
                        uint32_t *waiting);
+/* The largest batch of one model so far, the admissions the memory budget
+ * has deferred (each time a request did not fit), and the footprint bytes the
+ * admitted requests hold now.  Any pointer may be NULL. */
+int fheon_server_model_stats(const fheon_server *server, const fheon_model *model, uint32_t *max_batch,
+                             uint64_t *mem_waits, size_t *held);
 
 /* ------------------------------------------------------------------ */
 /* Secure ReLU (paper Sec. 5.6, Alg. 4)                               */

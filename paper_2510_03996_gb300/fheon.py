@@ -158,6 +158,8 @@ SIGNATURES = {
     "fheon_model_create_program": [c_vp, P(fheon_step), c_u32, c_u32, c_dbl, c_vpp],
     "fheon_model_run": [c_vp, c_vp, c_vp, c_vp],
     "fheon_model_destroy": [c_vp],
+    "fheon_model_footprint": [c_vp, c_u32, P(c_sz)],
+    "fheon_server_model_stats": [c_vp, c_vp, P(c_u32), P(c_u64), P(c_sz)],
     "fheon_server_create": [c_vp, c_u32, c_sz, c_vpp],
     "fheon_server_destroy": [c_vp],
     "fheon_server_submit": [c_vp, c_vp, c_vp, P(c_u64)],
@@ -866,10 +868,17 @@ class Context:
         self._chk(load().fheon_model_run(self.h, model.h, ct.h, out.h))
         return out
 
-    def server(self, max_active, min_free=0):
+    def server(self, max_active, mem_budget=0):
+        """A server (fheon_server_create); it takes models of other contexts too."""
         h = c_vp()
-        self._chk(load().fheon_server_create(self.h, max_active, min_free, ctypes.byref(h)))
+        self._chk(load().fheon_server_create(self.h, max_active, int(mem_budget), ctypes.byref(h)))
         return Server(self, Handle(h, load().fheon_server_destroy))
+
+    @staticmethod
+    def model_footprint(model, level):
+        b = c_sz(0)
+        check(load().fheon_model_footprint(model.h, level, ctypes.byref(b)))
+        return b.value
 
     @staticmethod
     def layer_rotation_steps(layer):
@@ -1094,6 +1103,12 @@ class Server:
         check(load().fheon_server_stats(self.handle.h, ctypes.byref(st), ctypes.byref(mb), ctypes.byref(a),
                                         ctypes.byref(w)))
         return {"steps": st.value, "max_batch": mb.value, "active": a.value, "waiting": w.value}
+
+    def model_stats(self, model):
+        mb, mw, held = c_u32(), c_u64(), c_sz()
+        check(load().fheon_server_model_stats(self.handle.h, model.h, ctypes.byref(mb), ctypes.byref(mw),
+                                              ctypes.byref(held)))
+        return {"max_batch": mb.value, "mem_waits": mw.value, "held": held.value}
 
     def close(self):
         self.handle.close()

@@ -94,3 +94,57 @@ def test_server_mixes_requests_bit_exactly(setup):
     with pytest.raises(pr.F.FheonError):
         srv.result(ids[0])                        # taken already
     srv.close()
+
+
+def test_one_server_two_contexts_memory_admission(setup):
+    """One server takes the models of two contexts (each on its own stream):
+    the results are the models' alone, bit for bit; a memory budget of one
+    footprint per model keeps one request of each in flight, defers the rest
+    (counted), and admits them as the earlier ones finish."""
+    import torch
+    pr, layers, cts, alone = setup
+    g = pr.g
+    model_a = g.model(layers)
+    other = gpu_common.Pair("relu_n12")
+    g2 = other.g
+    stream = torch.cuda.Stream()
+    g2.set_stream(stream.cuda_stream)
+    K = synth.conv_kernel(96, 0, (1, 1, 3, 3), std=0.3)
+    conv = g2.conv_prepare((1, 6, 6, GRID, 1, BLOCK), K, 1, other.L, other.P["scale"])
+    other.add_keys(g2.layer_rotation_steps(conv))
+    model_b = g2.model([conv])
+    cts_b = []
+    for i in range(2):
+        X = synth.image(96, 10 + i, (1, 6, 6))
+        v = OF.pack_map(X, other.N // 2, GRID, 1, BLOCK)
+        cts_b.append(other.encrypt_both(ckks.encode(v, other.N, other.P["scale"]), nonce=9600 + i)[0])
+    alone_b = [g2.ct_download(g2.model_run(model_b, c)) for c in cts_b]
+    fa = g.model_footprint(model_a, g.ct_info(cts[0])[0])
+    fb = g2.model_footprint(model_b, g2.ct_info(cts_b[0])[0])
+    assert fa > fb > 0  # so that two requests of model a never fit the budget together
+    srv = g.server(max_active=8, mem_budget=fa + fb)
+    ids = [(srv.submit(model_a, cts[k]), "a", k) for k in range(3)] + \
+          [(srv.submit(model_b, cts_b[k]), "b", k) for k in range(2)]
+    res = {}
+    for _ in range(200):
+        srv.step()
+        st = srv.model_stats(model_a)
+        assert st["held"] <= fa + fb
+        for rid, kind, k in ids:
+            if (kind, k) not in res:
+                r = srv.result(rid)
+                if r is not None:
+                    res[(kind, k)] = (g if kind == "a" else g2).ct_download(r)
+        if len(res) == len(ids):
+            break
+    assert len(res) == 5
+    for k in range(3):
+        assert gpu_common.mismatch(res[("a", k)], alone[k]) == 0
+    for k in range(2):
+        assert gpu_common.mismatch(res[("b", k)], alone_b[k]) == 0
+    sa, sb = srv.model_stats(model_a), srv.model_stats(model_b)
+    assert sa["max_batch"] == 1 and sb["max_batch"] == 1   # one footprint each fits the budget
+    assert sa["mem_waits"] > 0 and sa["held"] == 0
+    srv.close()
+    g2.sync()
+    g2.set_stream(torch.cuda.current_stream().cuda_stream)
