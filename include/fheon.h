@@ -142,10 +142,12 @@ int fheon_ctx_set_stream(fheon_ctx *ctx, void *stream);
  * pass); 2 = ModUp base conversion tiled per digit (needs alpha <= 4);
  * 4 = ModDown base conversion tiled per component (needs K <= 4); 8 = the
  * streaming inner product fed by TMA bulk copies into shared memory (needs
- * bit 1).  The default is 9.  get returns the current value; set fails with
- * FHEON_ERR_ARG for values outside [0, FHEON_NUM_SCHEDULES) and bits the
- * parameters do not allow. */
-#define FHEON_NUM_SCHEDULES 16
+ * bit 1); 16 = the NTT's row passes at radix 8 on 2048-element tiles (half
+ * the registers a thread, one more CTA per SM) instead of radix 16 on
+ * 4096-element tiles (needs bit 1).  The default is 9.  get returns the
+ * current value; set fails with FHEON_ERR_ARG for values outside
+ * [0, FHEON_NUM_SCHEDULES) and bits the parameters do not allow. */
+#define FHEON_NUM_SCHEDULES 32
 int fheon_ctx_get_schedule(const fheon_ctx *ctx, int *schedule);
 int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule);
 /* Batching switch.  on = 1 (the default): batched rotations and products

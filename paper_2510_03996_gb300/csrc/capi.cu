@@ -371,6 +371,7 @@ int fheon_ctx_set_schedule(fheon_ctx *ctx, int schedule)
 {
     if (!ctx || schedule < 0 || schedule >= FHEON_NUM_SCHEDULES) return FHEON_ERR_ARG;
     if ((schedule & 8) && !(schedule & 1)) return fail(ctx, FHEON_ERR_ARG, "bulk-copy inner product needs bit 1");
+    if ((schedule & 16) && !(schedule & 1)) return fail(ctx, FHEON_ERR_ARG, "radix-8 row passes need bit 1");
     if ((schedule & 2) && ctx->alpha > 4) return fail(ctx, FHEON_ERR_ARG, "tiled ModUp needs alpha <= 4");
     if ((schedule & 4) && ctx->K > 4) return fail(ctx, FHEON_ERR_ARG, "tiled ModDown needs K <= 4");
     ctx->ks_schedule = schedule;

@@ -35,6 +35,7 @@
 #include <map>
 #include <mutex>
 #include <set>
+#include <type_traits>
 #include <vector>
 
 #include "jobs.cuh"
@@ -240,7 +241,7 @@ struct UpBJob : JobCommon {
         else
             prefetch_l2(ws_ext(*d, N) + ((u64)j * (l + p.K) + t) * N + off, te * 8);
     }
-    __device__ void begin(int j, u32 tile)
+    __device__ void begin(int j, u32 tile, u32)
     {
         const u32 l = d->level, N = p.tp.N, nm = p.L + p.K;
         if (j == 0) {
@@ -360,10 +361,9 @@ struct DnBJob : JobCommon {
         pi = P.pinv[i];
     }
     // the row tile's acc and gathered sigma_g(c0) block into L2 while the NTT runs
-    __device__ void begin(int, u32 tile) const
+    __device__ void begin(int, u32 tile, u32 te) const
     {
         if (threadIdx.x != 0) return;
-        const u32 N = p.tp.N, te = N < 4096 ? N : 4096;
         const u64 off = (u64)tile * te;
         prefetch_l2(acc + off, te * 8);
         if (b == 0) prefetch_l2(c0i + (automorph_src((u32)off, d->g, p.tp.logN) & ~(te - 1)), te * 8);
@@ -381,20 +381,21 @@ struct DnBJob : JobCommon {
     // the operands of 8 elements are loaded before any of their stores, so
     // their latencies overlap (a store may alias a later load otherwise)
     static constexpr bool TILE_STORE = true;
-    __device__ void store_tile_last(const u32 (&J)[ntt::R], const u64 (&y)[ntt::R], const ModConst &m) const
+    template <int RR>
+    __device__ void store_tile_last(const u32 (&J)[RR], const u64 (&y)[RR], const ModConst &m) const
     {
         const bool add = b == 0 || c1a;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            u64 a[ntt::R / 2], c[ntt::R / 2];
+        for (int h = 0; h < RR / 8; h++) {
+            u64 a[8], c[8];
 #pragma unroll
-            for (int v = 0; v < ntt::R / 2; v++) {
+            for (int v = 0; v < 8; v++) {
                 const u32 j = J[h * 8 + v];
                 a[v] = acc[j];
                 c[v] = b == 0 ? c0i[automorph_src(j, d->g, p.tp.logN)] : (c1a ? c1a[j] : 0);
             }
 #pragma unroll
-            for (int v = 0; v < ntt::R / 2; v++) {
+            for (int v = 0; v < 8; v++) {
                 u64 r = shoup(a[v] + m.q - y[h * 8 + v], pi.x, pi.y, m.q);
                 if (add) r = addmod(r, c[v], m.q);
                 out[J[h * 8 + v]] = r;
@@ -465,7 +466,7 @@ struct TiledConvJob : JobCommon {
     }
     __device__ void attach(u64 *s) { xs = s; }
     __device__ int reps() const { return (int)nrep; }
-    __device__ void begin(int rep, u32)
+    __device__ void begin(int rep, u32, u32)
     {
         rep_now = (u32)rep;
         u32 t = cur + 1;
@@ -712,14 +713,26 @@ struct Lists {
     u32 n[ST_COUNT][2] = {};
 };
 
+// One stage of the pipeline over both prime classes.  Schedule bit 16 runs
+// the row passes at radix 8 (the fused inner product of schedule bit 1 = 0
+// keeps radix 16)
 template <bool INV, bool FIRST, class Job>
 int stage(fheon_ctx *ctx, BatchParams P, const Lists &ls, int s, const char *name)
 {
     Range range(name);
+    constexpr bool R8_OK = (INV == FIRST) && !std::is_same<Job, UpBJob>::value; // a row pass
+    const bool r8 = R8_OK && (ctx->ks_schedule & 16);
     for (int cls = 0; cls < 2; cls++) {
         if (!ls.n[s][cls]) continue;
         P.tasks = ls.t[s][cls];
-        FHEON_CUDA(ctx, (ntt::launch_pass<INV, FIRST, Job>(ctx->logN, P, ls.n[s][cls], ctx->stream, name, cls == 1)));
+        cudaError_t e;
+        if constexpr (R8_OK) {
+            e = r8 ? ntt::launch_pass<INV, FIRST, Job, 3>(ctx->logN, P, ls.n[s][cls], ctx->stream, name, cls == 1)
+                   : ntt::launch_pass<INV, FIRST, Job, 4>(ctx->logN, P, ls.n[s][cls], ctx->stream, name, cls == 1);
+        } else {
+            e = ntt::launch_pass<INV, FIRST, Job>(ctx->logN, P, ls.n[s][cls], ctx->stream, name, cls == 1);
+        }
+        FHEON_CUDA(ctx, e);
     }
     return FHEON_OK;
 }

@@ -53,20 +53,27 @@ void prof_mark(cudaStream_t st, const char *name);
 
 namespace ntt {
 
-constexpr int LOGR = 4;
+constexpr int LOGR = 4; // radix of the column passes, and the default of the row passes
 constexpr int R = 1 << LOGR;
 constexpr int TILE_ELEMS = 4096;
 constexpr u64 LAZY_BOUND = 1ull << 54;
 
-template <int LOGN>
+// LOGR_ROWS: radix of the row passes (4: radix 16, 4096-element tiles; 3:
+// radix 8, 2048-element tiles, still 256 threads a CTA and half the registers
+// a thread).  The column passes are radix 16 either way: a radix-8 column
+// tile would read 64-byte instead of 128-byte row segments.
+template <int LOGN, int LOGR_ROWS = LOGR>
 struct Cfg {
     static constexpr int B1 = LOGN / 2;  // pass A bits (high)
     static constexpr int B2 = LOGN - B1; // pass B bits (low)
     static constexpr int N1 = 1 << B1, N2 = 1 << B2;
+    static constexpr int RR = 1 << LOGR_ROWS;
     static constexpr int TILE = (1 << LOGN) < TILE_ELEMS ? (1 << LOGN) : TILE_ELEMS;
-    static constexpr int ROW_SUBS = TILE / N2;                           // rows per CTA (pass B)
+    static constexpr int ROW_TILE_ELEMS = 256 * RR;
+    static constexpr int ROW_TILE = (1 << LOGN) < ROW_TILE_ELEMS ? (1 << LOGN) : ROW_TILE_ELEMS;
+    static constexpr int ROW_SUBS = ROW_TILE / N2;                       // rows per CTA (pass B)
     static constexpr int COL_SUBS = (TILE / N1) < N2 ? (TILE / N1) : N2; // columns per CTA (pass A)
-    static constexpr int ROW_THREADS = ROW_SUBS * (N2 / R);
+    static constexpr int ROW_THREADS = ROW_SUBS * (N2 / RR);
     static constexpr int COL_THREADS = COL_SUBS * (N1 / R);
     static constexpr int ROW_TILES = N1 / ROW_SUBS;
     static constexpr int COL_TILES = N2 / COL_SUBS;
@@ -88,16 +95,18 @@ struct JobBase {
     static constexpr bool RUNTIME_EXTRA = false;
     __device__ void attach(u64 *) {}
     __device__ int reps() const { return 1; }
-    // start of repetition `rep` on tile `tile` (jobs prefetch their operands here)
-    __device__ void begin(int, u32) {}
+    // start of repetition `rep` on tile `tile` of `te` consecutive elements of
+    // the pass's grid (jobs prefetch their operands here)
+    __device__ void begin(int, u32, u32) {}
     __device__ bool passthrough() const { return false; }
     __device__ u64 load_passthrough(u32) const { return 0; }
     __device__ void finish(int, u32, const ModConst &) {}
     // whole-tile direct loads of the first pass (default: element by element)
     static constexpr bool TILE_LOAD = false;
-    // whole-tile stores of the second pass: store_tile_last(J[R], value[R], mod)
-    // gets every final value of the thread at once, so a job that reads
-    // operands to combine with them can issue those loads together
+    // whole-tile stores of the second pass: store_tile_last(J[RR], value[RR],
+    // mod) gets every final value of the thread at once (RR: the pass's radix),
+    // so a job that reads operands to combine with them can issue those loads
+    // together
     static constexpr bool TILE_STORE = false;
     // a forward transform over a lazy prime may hand its consumer the values
     // unreduced (below 36q for up to 17 stages from inputs below 2q)
@@ -118,10 +127,12 @@ __device__ __forceinline__ u64 reduce_any(u64 v, const ModConst &m)
 }
 __device__ __forceinline__ u64 reduce_any_lazy(u64 v, const ModConst &m) { return v - __umul64hi(v, m.one_sh) * m.q; }
 
-template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job>
+template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job, int LOGR_ROWS = LOGR>
 __device__ __forceinline__ void pass_body(Job &job, u32 tile)
 {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, LOGR_ROWS>;
+    constexpr int LOGR = ROWS ? LOGR_ROWS : ntt::LOGR; // this pass's radix
+    constexpr int R = 1 << LOGR;
     constexpr int LOGM = ROWS ? C::B2 : C::B1;
     constexpr int M = 1 << LOGM;
     constexpr int G = M / R;
@@ -166,7 +177,7 @@ __device__ __forceinline__ void pass_body(Job &job, u32 tile)
 
     const int nrep = job.reps();
     for (int rep = 0; rep < nrep; rep++) {
-        job.begin(rep, tile);
+        job.begin(rep, tile, (u32)(SUBS * M));
         // the modulus may change between repetitions (a job may run one
         // transform per target limb over shared sources)
         const ModConst mc = job.mod();
@@ -340,38 +351,44 @@ __device__ __forceinline__ void pass_body(Job &job, u32 tile)
 // buffer), else the second (reads mid, writes the job's output).
 // LAZY: every task's prime is below LAZY_BOUND (the launcher splits task
 // lists by that test); otherwise Harvey butterflies, valid for any prime.
-template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job>
-__global__ void __launch_bounds__(256, Job::MIN_BLOCKS) pass_kernel(const __grid_constant__ typename Job::Params prm)
+// a radix-8 row pass holds half the registers a thread: one more CTA per SM
+template <class Job, int LOGR_ROWS>
+constexpr int min_blocks() { return LOGR_ROWS < LOGR ? Job::MIN_BLOCKS + 1 : Job::MIN_BLOCKS; }
+
+template <int LOGN, bool INV, bool ROWS, bool FIRST, bool LAZY, class Job, int LOGR_ROWS = LOGR>
+__global__ void __launch_bounds__(256, (min_blocks<Job, LOGR_ROWS>()))
+    pass_kernel(const __grid_constant__ typename Job::Params prm)
 {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, LOGR_ROWS>;
     constexpr int TILES = ROWS ? C::ROW_TILES : C::COL_TILES;
     const u32 task = blockIdx.x / TILES;
     const u32 tile = blockIdx.x % TILES;
     Job job(prm, task);
     if (!job.active()) return;
-    pass_body<LOGN, INV, ROWS, FIRST, LAZY>(job, tile);
+    pass_body<LOGN, INV, ROWS, FIRST, LAZY, Job, LOGR_ROWS>(job, tile);
 }
 
-template <int LOGN, bool INV, bool FIRST>
+template <int LOGN, bool INV, bool FIRST, int LOGR_ROWS = LOGR>
 struct PassShape {
-    using C = Cfg<LOGN>;
+    using C = Cfg<LOGN, LOGR_ROWS>;
     static constexpr bool ROWS = (INV == FIRST); // inverse starts with rows, forward with columns
     static constexpr int threads = ROWS ? C::ROW_THREADS : C::COL_THREADS;
     static constexpr int smem = ROWS ? C::ROW_SMEM : C::COL_SMEM;
     static constexpr int tiles = ROWS ? C::ROW_TILES : C::COL_TILES;
+    static constexpr int tile_elems = ROWS ? C::ROW_TILE : C::TILE;
 };
 
 // Launch one pass of a transform over `ntasks` tasks.
-template <int LOGN, bool INV, bool FIRST, bool LAZY, class Job>
+template <int LOGN, bool INV, bool FIRST, bool LAZY, class Job, int LOGR_ROWS = LOGR>
 inline cudaError_t launch_pass_fixed(const typename Job::Params &prm, u32 ntasks, cudaStream_t st, const char *name)
 {
-    using S = PassShape<LOGN, INV, FIRST>;
+    using S = PassShape<LOGN, INV, FIRST, LOGR_ROWS>;
     int extra = Job::EXTRA_WORDS_PER_ELEM;
     if constexpr (Job::RUNTIME_EXTRA) extra = (int)Job::extra_words(prm);
-    const int smem = S::smem + extra * Cfg<LOGN>::TILE * 8;
+    const int smem = S::smem + extra * S::tile_elems * 8;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     if (ntasks == 0) return cudaSuccess;
-    auto kern = pass_kernel<LOGN, INV, S::ROWS, FIRST, LAZY, Job>;
+    auto kern = pass_kernel<LOGN, INV, S::ROWS, FIRST, LAZY, Job, LOGR_ROWS>;
     if (smem > 48 * 1024) {
         static int attr = 0; // one instantiation per kernel: raise its opt-in limit when needed
         if (smem > attr) {
@@ -385,31 +402,32 @@ inline cudaError_t launch_pass_fixed(const typename Job::Params &prm, u32 ntasks
     return cudaGetLastError();
 }
 
-template <bool INV, bool FIRST, bool LAZY, class Job>
+template <bool INV, bool FIRST, bool LAZY, class Job, int LOGR_ROWS>
 inline cudaError_t launch_pass_l(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st,
                                  const char *name)
 {
     switch (logN) {
-    case 10: return launch_pass_fixed<10, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 11: return launch_pass_fixed<11, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 12: return launch_pass_fixed<12, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 13: return launch_pass_fixed<13, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 14: return launch_pass_fixed<14, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 15: return launch_pass_fixed<15, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 16: return launch_pass_fixed<16, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
-    case 17: return launch_pass_fixed<17, INV, FIRST, LAZY, Job>(prm, ntasks, st, name);
+    case 10: return launch_pass_fixed<10, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 11: return launch_pass_fixed<11, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 12: return launch_pass_fixed<12, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 13: return launch_pass_fixed<13, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 14: return launch_pass_fixed<14, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 15: return launch_pass_fixed<15, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 16: return launch_pass_fixed<16, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
+    case 17: return launch_pass_fixed<17, INV, FIRST, LAZY, Job, LOGR_ROWS>(prm, ntasks, st, name);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // One pass; `lazy` selects the conditional-subtraction-free butterflies, valid
-// only when every task's prime is below LAZY_BOUND.
-template <bool INV, bool FIRST, class Job>
+// only when every task's prime is below LAZY_BOUND.  LOGR_ROWS: the radix of a
+// row pass (3 or 4; a column pass is radix 16 either way).
+template <bool INV, bool FIRST, class Job, int LOGR_ROWS = LOGR>
 inline cudaError_t launch_pass(u32 logN, const typename Job::Params &prm, u32 ntasks, cudaStream_t st,
                                const char *name, bool lazy = false)
 {
-    return lazy ? launch_pass_l<INV, FIRST, true, Job>(logN, prm, ntasks, st, name)
-                : launch_pass_l<INV, FIRST, false, Job>(logN, prm, ntasks, st, name);
+    return lazy ? launch_pass_l<INV, FIRST, true, Job, LOGR_ROWS>(logN, prm, ntasks, st, name)
+                : launch_pass_l<INV, FIRST, false, Job, LOGR_ROWS>(logN, prm, ntasks, st, name);
 }
 
 // Both passes of a transform whose two passes use the same job type.

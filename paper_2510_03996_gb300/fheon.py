@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libfheon.so")
 
 FHEON_OK = 0
-NUM_SCHEDULES = 16  # FHEON_NUM_SCHEDULES
+NUM_SCHEDULES = 32  # FHEON_NUM_SCHEDULES
 PENDING = 1  # FHEON_PENDING
 ERRORS = {-1: "FHEON_ERR_ARG", -2: "FHEON_ERR_OOM", -3: "FHEON_ERR_NO_KEY", -4: "FHEON_ERR_LEVEL",
           -5: "FHEON_ERR_SCALE", -6: "FHEON_ERR_TIMEOUT", -7: "FHEON_ERR_CUDA", -8: "FHEON_ERR_UNIMPLEMENTED"}

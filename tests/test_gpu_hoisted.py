@@ -37,7 +37,7 @@ def test_hoisted_bit_exact(small, level):
     assert gpu_common.mismatch(small.g.ct_download(one), want[2]) == 0
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15, 17, 25, 31])
 def test_hoisted_every_schedule(small, schedule):
     g = small.g
     old = g.get_schedule()

@@ -106,7 +106,7 @@ def test_schedule_range(small):
         g.set_schedule(old)
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15, 17, 25, 31])
 def test_every_schedule_is_bit_exact(small, schedule):
     """Key-switching schedules change launches and fusion only, never results:
     single rotations (closed-form tasks) and batches at mixed levels."""
@@ -289,10 +289,12 @@ def test_rotate_full_size_sampled():
     m = synth.small_int_poly(13, 0, pr.N, 1 << 40)
     ct, oct_ = pr.encrypt_both(m, nonce=3)
     for level in (24, 9):
-        c = pr.g.drop_level(ct, level)
-        out = pr.g.rotate(c, 12345)
         want = pr.o.rotate(oct_[:, :level], g, pr.okeys[g])
-        assert gpu_common.mismatch(pr.g.ct_download(out), want) == 0
+        c = pr.g.drop_level(ct, level)
+        for schedule in (9, 25):  # row passes at radix 16 and at radix 8
+            pr.g.set_schedule(schedule)
+            out = pr.g.rotate(c, 12345)
+            assert gpu_common.mismatch(pr.g.ct_download(out), want) == 0, schedule
 
 
 def test_autotune_cache(small, tmp_path):

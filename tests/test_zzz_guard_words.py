@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 GUARD, BYTE = 4096, 0xA5
 STEPS = [1, -1, 7, 100]
-SCHEDULES = (0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15)
+SCHEDULES = (0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 15, 17, 25, 31)
 
 
 class GuardedBlocks:
