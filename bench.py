@@ -483,6 +483,16 @@ def resnet_timing(F, n_inputs=2):
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
     same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs, gouts))
+    # the inputs as one batch: every layer and bootstrap over both at once
+    net.forward_batch(cts)  # warm-up: the batch's working sets
+    ctx.sync()
+    e0.record(s)
+    bouts = net.forward_batch(cts)
+    e1.record(s)
+    torch.cuda.synchronize()
+    batch_secs = e0.elapsed_time(e1) / 1e3
+    batch_same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs, bouts))
+    del bouts
     z = ctx.drop_level(cts[0], 1)
     e0.record(s)
     for _ in range(5):
@@ -562,6 +572,7 @@ def resnet_timing(F, n_inputs=2):
     release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
             "per_ciphertext_path_s_per_inference": plain_secs / n_inputs,
+            "batched_s_per_inference": batch_secs / n_inputs, "batched_equals_one_by_one": batch_same,
             "eager_ms_by_step_kind": {k: round(v, 2) for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
             "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": n_boot,
             "bootstrap_kernels": boot_kernels,

@@ -364,6 +364,108 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
     return FHEON_OK;
 }
 
+int boot_apply_many(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs)
+{
+    const u32 N = ctx->N, D = (u32)ly->coeffs.size() - 1;
+    int rc;
+    for (u32 p = 0; p < n; p++) {
+        if (ins[p]->level < 1) return fail(ctx, FHEON_ERR_LEVEL, "bootstrap: empty ciphertext");
+        if (std::fabs(ins[p]->scale - ly->in_scale) > 1e-9 * ly->in_scale)
+            return fail(ctx, FHEON_ERR_SCALE, "bootstrap prepared for scale %g, got %g", ly->in_scale, ins[p]->scale);
+    }
+    auto conj = ctx->keys.find(2ull * N - 1);
+    if (conj == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "bootstrap: no conjugation key");
+    if (ly->bsets.size() < n) ly->bsets.resize(n);
+    // per input: 0 raised, 1-2 chain, 3 conjugate, 4 difference, 5-8 doubling
+    // ping-pong (re, im), 9 recombined
+    for (u32 p = 0; p < n; p++) {
+        auto &w = ly->bsets[p].w;
+        if (w.size() < 10) w.resize(10, nullptr);
+        for (fheon_ct *&c : w)
+            if (!c && (rc = fheon_ct_create(ctx, 1, 1.0, &c))) return rc;
+    }
+    auto W = [&](u32 p, u32 i) { return ly->bsets[p].w[i]; };
+    std::vector<const fheon_ct *> xs(n);
+    std::vector<fheon_ct *> dsts(n);
+    for (u32 p = 0; p < n; p++) {
+        if ((rc = mod_raise_ct(ctx, ins[p], W(p, 0)))) return rc;
+        W(p, 0)->scale = (double)ctx->mod[0];
+        xs[p] = W(p, 0);
+    }
+    auto sub_apply = [&](const fheon_layer *sub, fheon_ct *const *to) {
+        sub->collect = ly->collect;
+        const int r = fheon_layer_apply_batch(ctx, sub, xs.data(), n, to);
+        sub->collect = nullptr;
+        return r;
+    };
+    {
+        Range range("CoeffToSlot");
+        for (u32 i = 0; i < ly->ncts; i++) {
+            for (u32 p = 0; p < n; p++) dsts[p] = W(p, 1 + (i & 1));
+            if ((rc = sub_apply(ly->subs[i], dsts.data()))) return rc;
+            for (u32 p = 0; p < n; p++) xs[p] = dsts[p];
+        }
+    }
+    Range phase("EvalMod");
+    // the conjugates of every input as one key-switching batch
+    std::vector<KsItem> ks(n);
+    for (u32 p = 0; p < n; p++) {
+        const fheon_ct *x = xs[p];
+        if ((rc = ct_reshape(ctx, W(p, 3), x->level))) return rc;
+        W(p, 3)->scale = x->scale;
+        ks[p].c0 = x->c0();
+        ks[p].c1 = x->c1(N);
+        ks[p].out = W(p, 3)->c0();
+        ks[p].key = conj->second.mem.as<u64>();
+        ks[p].g = 2ull * N - 1;
+        ks[p].level = x->level;
+        ks[p].lead = p;
+    }
+    if ((rc = ks_many(ctx, ks.data(), n, false, ly->collect))) return rc;
+    std::vector<std::vector<fheon_ct *> *> works(2 * n);
+    std::vector<fheon_ct *> a(2 * n), b(2 * n);
+    for (u32 p = 0; p < n; p++) {
+        const fheon_ct *x = xs[p];
+        auto &bs = ly->bsets[p];
+        if ((rc = cheb_work(ctx, bs.re, D, x->level, x->scale))) return rc;
+        if ((rc = cheb_work(ctx, bs.im, D, x->level, x->scale))) return rc;
+        if ((rc = fheon_add(ctx, x, W(p, 3), bs.re[1]))) return rc;
+        if ((rc = fheon_mul_int(ctx, x, -1, W(p, 4)))) return rc;
+        if ((rc = fheon_add(ctx, W(p, 3), W(p, 4), W(p, 4)))) return rc;
+        if ((rc = fheon_mul_plain(ctx, W(p, 4), ly->mono[0], bs.im[1]))) return rc;
+        works[2 * p] = &bs.re;
+        works[2 * p + 1] = &bs.im;
+        a[2 * p] = W(p, 5);
+        a[2 * p + 1] = W(p, 7);
+        b[2 * p] = W(p, 6);
+        b[2 * p + 1] = W(p, 8);
+    }
+    if ((rc = cheb_series_many(ctx, ly->coeffs, works.data(), 2 * n, a.data(), ly->collect))) return rc;
+    std::vector<RelinItem> it(2 * n);
+    for (u32 i = 0; i < ly->boot_r; i++) {
+        for (u32 k = 0; k < 2 * n; k++) it[k] = RelinItem{a[k], a[k], a[k]->level, true, b[k]};
+        if ((rc = mul_relin_many(ctx, it.data(), 2 * n, ly->collect))) return rc;
+        for (u32 k = 0; k < 2 * n; k++) {
+            if ((rc = fheon_rescale(ctx, b[k], b[k]))) return rc;
+            if ((rc = fheon_add_const(ctx, b[k], -1.0, b[k]))) return rc;
+            std::swap(a[k], b[k]);
+        }
+    }
+    for (u32 p = 0; p < n; p++) {
+        if ((rc = fheon_mul_plain(ctx, a[2 * p + 1], ly->mono[1], W(p, 9)))) return rc;
+        if ((rc = fheon_add(ctx, a[2 * p], W(p, 9), W(p, 9)))) return rc;
+        xs[p] = W(p, 9);
+    }
+    phase.next("SlotToCoeff");
+    const u32 nst = (u32)ly->subs.size() - ly->ncts;
+    for (u32 i = 0; i < nst; i++) {
+        for (u32 p = 0; p < n; p++) dsts[p] = i + 1 == nst ? outs[p] : W(p, 1 + (i & 1));
+        if ((rc = sub_apply(ly->subs[ly->ncts + i], dsts.data()))) return rc;
+        for (u32 p = 0; p < n; p++) xs[p] = dsts[p];
+    }
+    return FHEON_OK;
+}
+
 } // namespace fheon
 
 extern "C" {

@@ -47,6 +47,12 @@ struct fheon_layer {
     fheon_pt *mono[2] = {nullptr, nullptr};
     mutable std::vector<fheon_ct *> cheb2; // the second part's series working set
     mutable std::vector<std::vector<fheon_ct *>> sets; // ReLU on a batch: one working set per input
+    // bootstrapping a batch: per input, its 10 working ciphertexts and the two
+    // series working sets (the single-input path uses work, rot and cheb2)
+    struct BootSet {
+        std::vector<fheon_ct *> w, re, im;
+    };
+    mutable std::vector<BootSet> bsets;
     // working ciphertexts (the k^2 - 1 tap rotations, then accumulators), made
     // on the first application and reused, so that later applications (and
     // their graph capture) allocate nothing
@@ -84,6 +90,9 @@ struct fheon_layer {
         for (fheon_ct *c : cheb2) fheon_ct_destroy(c);
         for (auto &v : sets)
             for (fheon_ct *c : v) fheon_ct_destroy(c);
+        for (auto &b : bsets)
+            for (auto *v : {&b.w, &b.re, &b.im})
+                for (fheon_ct *c : *v) fheon_ct_destroy(c);
     }
 };
 
@@ -133,4 +142,7 @@ int diag_layer(fheon_ctx *ctx, const Diags &M, u32 stride, cd factor, u32 baby, 
 int relu_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs);
 // bootstrapping (boot.cu)
 int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out);
+// n inputs at once: every level, the conjugations, the series and the
+// doublings of all of them as batches; each output is the one boot_apply gives
+int boot_apply_many(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs);
 } // namespace fheon

@@ -673,9 +673,7 @@ int fheon_layer_apply_batch(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
     case LAYER_RELU:
         return relu_apply_batch(ctx, ly, ins, n, outs);
     case LAYER_BOOT:
-        for (u32 i = 0; i < n; i++)
-            if ((rc = boot_apply(ctx, ly, ins[i], outs[i]))) return rc;
-        return FHEON_OK;
+        return n == 1 ? boot_apply(ctx, ly, ins[0], outs[0]) : boot_apply_many(ctx, ly, ins, n, outs);
     default: break;
     }
     for (u32 i = 0; i < n; i++)

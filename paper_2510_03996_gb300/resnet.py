@@ -312,6 +312,33 @@ class EncryptedResNet:
                 reg[op[1]] = ctx.layer_apply(self.boot, reg[op[1]])
         return reg["x"]
 
+    def forward_batch(self, cts):
+        """Several inputs through the same plan at once: every layer (bootstraps
+        included) applied to the whole batch in one call (fheon_layer_apply_batch),
+        so their rotations, products and series share launches; each output is
+        the one forward() gives its input."""
+        ctx = self.ctx
+        reg = {"x": list(cts)}
+        for op in self.plan:
+            kind = op[0]
+            if kind == "layer":
+                _, layer, src, dst = op
+                reg[dst] = ctx.layer_apply_batch(layer, reg[src])
+            elif kind == "scale":
+                _, c, src, dst = op
+                reg[dst] = [ctx.mul_const_rescale(x, c, self.scale) for x in reg[src]]
+            elif kind == "add":
+                _, lv, a, b, dst = op
+                out = []
+                for A, Bc in zip(reg[a], reg[b]):
+                    A = ctx.drop_level(A, lv) if ctx.ct_info(A)[0] > lv else A
+                    Bc = ctx.drop_level(Bc, lv) if ctx.ct_info(Bc)[0] > lv else Bc
+                    out.append(ctx.add(A, Bc))
+                reg[dst] = out
+            elif kind == "boot":
+                reg[op[1]] = ctx.layer_apply_batch(self.boot, reg[op[1]])
+        return reg["x"]
+
     def forward_graph(self, ct):
         """The same plan with every layer (bootstraps included) replayed as a
         CUDA graph on fixed buffers: the input is copied into a staging

@@ -144,3 +144,21 @@ def test_evalmod_coefficients_match_the_oracle(boot):
         a = boot.g.evalmod_coeffs(K, r, D)
         b = B.evalmod_coeffs(K, r, D)
         assert np.array_equal(a, b)
+
+
+def test_bootstrap_batch_equals_one_by_one(boot):
+    """Two inputs bootstrapped as one batch (every level, the conjugations,
+    the series and the doublings batched) give each the ciphertext the
+    bootstrap gives it alone, bit for bit."""
+    g = boot.g
+    layer = g.bootstrap_prepare(boot.P["scale"])
+    g.bootstrap_keygen(boot.sk, layer)
+    cts = [_input(boot, 0xB106 + i, 1 + i)[1] for i in range(2)]
+    alone = [g.ct_download(g.layer_apply(layer, c)) for c in cts]
+    outs = g.layer_apply_batch(layer, cts)
+    for o, a in zip(outs, alone):
+        assert gpu_common.mismatch(g.ct_download(o), a) == 0
+    # and once more (the batch's working sets are kept and reused)
+    outs = g.layer_apply_batch(layer, cts[::-1])
+    for o, a in zip(outs, alone[::-1]):
+        assert gpu_common.mismatch(g.ct_download(o), a) == 0
