@@ -559,7 +559,21 @@ int fheon_fc(fheon_ctx *ctx, const fheon_ct *ct, const fheon_map *in, uint32_t m
  * 2^10 or more below q_0) and whose scale is the one the layer was prepared
  * for; the output has that scale (to 1e-9) and the same message.  Keys: the
  * layer's rotation steps, the conjugation and the relinearisation key
- * (fheon_bootstrap_keygen makes them all). */
+ * (fheon_bootstrap_keygen makes them all).
+ *
+ * Sparse bootstrap (slots = n_s <= N/4; OpenFHE, which the paper runs, does
+ * the same for a message of fewer than N/2 slots): the input, at level >= 2,
+ * is multiplied by the mask of slots [0, n_s) (one level, the mask encoded
+ * at scale q_1 so the scale is kept) and repeated in every copy of n_s slots
+ * (x + Rot_{n_s 2^j}(x) at level 1), so that its polynomial lies in
+ * Z[X^(N / 2 n_s)].  After ModRaise the trace (the same sums at level L)
+ * keeps the coefficients of that subring; CoeffToSlot is the n_s-slot
+ * transform in every copy and ends in the factor 1 on even copies and -i on
+ * odd ones, so that c + conj(c) holds the low coefficients in the even copies
+ * and the high ones in the odd copies: ONE EvalMod instead of two.
+ * SlotToCoeff starts with the map (a, b) -> a + i b in every copy.  The
+ * output holds slots [0, n_s) of the input in every copy of n_s slots.
+ * Levels consumed above q_0 are the same as the full bootstrap's. */
 typedef struct fheon_boot_params {
     uint32_t cts_levels; /* levels of CoeffToSlot, 1 .. log2(N/2) */
     uint32_t stc_levels; /* levels of SlotToCoeff, 1 .. log2(N/2) */
@@ -567,6 +581,8 @@ typedef struct fheon_boot_params {
     uint32_t degree;     /* Chebyshev degree of the cosine */
     uint32_t doublings;  /* double-angle steps r */
     uint32_t baby;       /* baby steps of every BSGS level (0: fewest rotations) */
+    uint32_t slots;      /* 0 or N/2: every slot; a power of two in [2, N/4]: the
+                          * sparse bootstrap of slots [0, slots) (below) */
 } fheon_boot_params;
 /* Defaults for a context: 3 + 3 levels, K the power of two at or above
  * 8 sqrt(N / 18) (eight standard deviations of t / q_0 for a uniform ternary
@@ -587,6 +603,11 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p, double i
  * keeps pointers to the levels: they must outlive it. */
 int fheon_bootstrap_compose(fheon_ctx *ctx, const fheon_boot_params *p, const fheon_layer *const *cts,
                             const fheon_layer *const *stc, const double *coeffs, double in_scale, fheon_layer **out);
+/* Sparse bootstrap: replace the input mask the layer encoded (slots
+ * [0, n_s) at level 2, scale q_1) by the caller's plaintext, which must
+ * outlive the layer (for checking the layer against an independent encoder).
+ * FHEON_ERR_ARG for a full bootstrap or a plaintext below level 2. */
+int fheon_bootstrap_set_mask(fheon_ctx *ctx, fheon_layer *layer, const fheon_pt *mask);
 /* Generate every key a bootstrap layer uses. */
 int fheon_bootstrap_keygen(fheon_ctx *ctx, const fheon_sk *sk, const fheon_layer *layer);
 /* Output level and scale of a bootstrap layer (scale 0 for a composed one). */
@@ -651,6 +672,7 @@ int fheon_layer_plan(const fheon_layer *layer, int32_t *fold, int32_t *r, int32_
 #define FHEON_PLAIN_BIAS 2    /* the bias (g = t = 0) */
 #define FHEON_PLAIN_MASK 3    /* ReLU: the 1/beta mask; special conv with C > 1: the block-0 mask */
 #define FHEON_PLAIN_MONO 4    /* bootstrap: X^(N/2) where the parts split (g = 0) and join (g = 1) */
+#define FHEON_PLAIN_BOOT_MASK 5 /* sparse bootstrap: the input mask of slots [0, n_s) */
 /* FHEON_ERR_ARG for an index out of range or a kind without that plaintext. */
 int fheon_layer_plain(const fheon_layer *layer, uint32_t which, uint32_t g, uint32_t t, const fheon_pt **out);
 /* Level i of a bootstrap layer: CoeffToSlot levels first (i < nt), then

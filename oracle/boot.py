@@ -31,6 +31,24 @@ scaled cosine followed by double-angle steps (Han and Ki, CT-RSA 2020):
      with the factor q_0 / (2 pi Delta) folded into the first, give back the
      slots of m / Delta = the input's message.
 
+Sparse bootstrap (a message in slots [0, ns), ns <= N/4; the library the
+paper runs does the same for fewer than N/2 slots): with copies = N / (2 ns),
+  0. the input (level >= 2) times the mask of slots [0, ns), rescaled, then
+     repeated in every copy of ns slots by x += Rot_{ns 2^j}(x): its
+     polynomial now lies in Z[X^copies];
+  1. ModRaise as above, then the trace x += Rot_{ns 2^j}(x), which keeps
+     copies times the coefficients of X^(copies k) of t and drops the rest;
+  2. CoeffToSlot: the ns-slot transform of that subring in every copy (its
+     slots are the ns-slot ring's slots of T(Y) = t(X), Y = X^copies),
+     1 / copies folded into the first level and the copy factor (1 on even
+     copies, -i on odd ones) into the last, so that y + conj(y) holds
+     T_lo / (K q_0) in the even copies and T_hi / (K q_0) in the odd ones;
+  3. ONE EvalMod on y + conj(y);
+  4. SlotToCoeff: the map (a, b) -> a + i b in every copy (diagonals
+     {0: (1, i), ns: (i, 1)}), composed into the first level, then the
+     ns-slot transform in every copy.
+The output holds the input's slots [0, ns) in every copy.
+
 Slot convention: slot j is the evaluation at zeta^(5^j mod 2N), zeta =
 exp(i pi / N); Rot_k moves slot j + k to slot j.
 """
@@ -126,6 +144,34 @@ def stc_levels(n, levels):
     return out
 
 
+def replicate(M, ns, n):
+    """Diagonals of an ns-slot map as an n-slot map for inputs of period ns
+    (ns divides n): every vector tiled n/ns times, offset o in [0, ns) taken
+    as o or o - ns, whichever is nearer to 0, modulo n.  On an input whose
+    slots repeat every ns it computes the ns-slot map in every copy."""
+    out = {}
+    for o, d in M.items():
+        oo = (o if o <= ns // 2 else o - ns) % n
+        out[oo] = out.get(oo, 0j) + np.tile(d, n // ns)
+    return out
+
+
+def copy_factor(ns, n):
+    """1 on the even copies of ns slots, -i on the odd ones.  CoeffToSlot of a
+    sparse bootstrap ends with it: with y = f * u (u repeated), y + conj(y)
+    holds 2 Re u in the even copies and 2 Im u in the odd ones."""
+    return np.tile(np.concatenate([np.ones(ns), np.full(ns, -1j)]), n // (2 * ns))
+
+
+def join_map(ns, n):
+    """Diagonals {0: P1, ns: P2} of the map from w = (a, b) (period 2 ns, real
+    a and b) to a + i b repeated every ns slots: P1 = (1, i), P2 = (i, 1), so
+    that copy 2c gets a + i b and copy 2c + 1 gets i b + a."""
+    one, im = np.ones(ns), np.full(ns, 1j)
+    return {0: np.tile(np.concatenate([one, im]), n // (2 * ns)),
+            ns % n: np.tile(np.concatenate([im, one]), n // (2 * ns))}
+
+
 def cts_levels(n, levels):
     """Merged CoeffToSlot groups in the order they are applied (top stages
     first): each the product of its stages' inverse diagonals."""
@@ -137,6 +183,25 @@ def cts_levels(n, levels):
             S = stage_diagonals(n, 1 << (s - 1), inverse=True)
             M = S if M is None else compose(S, M, n)
         out.append((1 << (g[0] - 1), M))
+    return out
+
+
+def cts_levels_sparse(n, ns, levels):
+    """CoeffToSlot of the sparse bootstrap on n slots: the ns-slot levels in
+    every copy (replicate), the last one times the copy factor (1, -i)."""
+    out = [(stride, replicate(M, ns, n)) for stride, M in cts_levels(ns, levels)]
+    stride, M = out[-1]
+    f = copy_factor(ns, n)
+    out[-1] = (stride, {o: d * f for o, d in M.items()})
+    return out
+
+
+def stc_levels_sparse(n, ns, levels):
+    """SlotToCoeff of the sparse bootstrap on n slots: the join map from
+    (a, b) to a + i b, then the ns-slot levels in every copy."""
+    out = [(stride, replicate(M, ns, n)) for stride, M in stc_levels(ns, levels)]
+    _, M = out[0]
+    out[0] = (1, compose(M, join_map(ns, n), n))
     return out
 
 
@@ -205,10 +270,15 @@ class Plan:
     is small against the message.  The output then has scale ~= Delta_in and
     the input's message."""
 
-    def __init__(self, ctx, in_scale, cts=3, stc=3, K=None, r=None, D=BOOT_DEGREE, baby=0):
+    def __init__(self, ctx, in_scale, cts=3, stc=3, K=None, r=None, D=BOOT_DEGREE, baby=0, slots=None):
         N, L = ctx.N, ctx.L
         n = N // 2
+        ns = n if not slots else int(slots)
+        if ns > n or ns < 2 or ns & (ns - 1):
+            raise ValueError("slots: a power of two in [2, N/2]")
         self.N, self.n, self.in_scale = N, n, float(in_scale)
+        # sparse (ns < N/2): the message lives in slots [0, ns); copies = n / ns
+        self.ns, self.copies = ns, n // ns
         self.K = K or default_K(N)
         self.r = default_doublings(self.K) if r is None else r
         self.D, self.ncts, self.nstc = D, cts, stc
@@ -217,13 +287,14 @@ class Plan:
         if depth(cts, stc, D, self.r) > L - 1:
             raise ValueError("bootstrap needs %d levels above q_0" % depth(cts, stc, D, self.r))
         lv = L
-        # CoeffToSlot
+        # CoeffToSlot (sparse: the ns-slot transform in every copy, after the
+        # trace summed the copies, which multiplied the message by `copies`)
         self.cts = []
         s = float(ctx.q[0])
         delta_b = q[L - cts - 1]
-        for i, (stride, M) in enumerate(cts_levels(n, cts)):
+        for i, (stride, M) in enumerate(cts_levels(n, cts) if ns == n else cts_levels_sparse(n, ns, cts)):
             if i == 0:
-                M = {o: d * (1.0 / (2.0 * self.K)) for o, d in M.items()}
+                M = {o: d * (1.0 / (2.0 * self.K * self.copies)) for o, d in M.items()}
                 ps = q[lv - 1] * (delta_b / float(ctx.q[0]))
             else:
                 ps = q[lv - 1]
@@ -238,9 +309,10 @@ class Plan:
             s = (s * s) / q[lv - 1]
             lv -= 1
         self.evalmod_scale = s
-        # SlotToCoeff
+        # SlotToCoeff (sparse: the first level starts with the join map from
+        # the real parts (a, b) to a + i b in every copy)
         self.stc = []
-        for i, (stride, M) in enumerate(stc_levels(n, stc)):
+        for i, (stride, M) in enumerate(stc_levels(n, stc) if ns == n else stc_levels_sparse(n, ns, stc)):
             if i == 0:
                 M = {o: d * (float(ctx.q[0]) / (2.0 * math.pi * self.in_scale)) for o, d in M.items()}
             ps = q[lv - 1] * (self.in_scale / s) if i == stc - 1 else q[lv - 1]
@@ -250,9 +322,19 @@ class Plan:
             lv -= 1
         self.out_scale, self.out_level = s, lv
 
+    def trace_steps(self):
+        """Rotation steps of the trace over the copies (ns, 2 ns, ...): sparse only."""
+        return [self.ns << j for j in range(self.copies.bit_length() - 1)]
+
+    def mask_slots(self):
+        """The sparse bootstrap's input mask: 1 in slots [0, ns), 0 elsewhere."""
+        v = np.zeros(self.n)
+        v[:self.ns] = 1.0
+        return v
+
     def steps(self):
         """Rotation steps of the plan's keys (besides the conjugation)."""
-        st = set()
+        st = set(self.trace_steps()) if self.ns < self.n else set()
         for rr, groups, _, _ in self.cts + self.stc:
             st |= set(OF.linear_steps(rr, groups))
         return sorted(st)
@@ -264,6 +346,11 @@ class Plan:
             out.append([[None if v is None else ctx.plain_from_coeffs(ckks.encode(v, self.N, ps), lv)
                          for v in vals] for _, vals in groups])
         return out
+
+    def encode_mask(self, ctx):
+        """The sparse input mask as a plaintext at level 2, scale q_1 (the
+        prime its rescale drops, so the scale is kept)."""
+        return ctx.plain_from_coeffs(ckks.encode(self.mask_slots(), self.N, float(ctx.q[1])), 2)
 
 
 def mod_raise(ctx, ct):
@@ -295,14 +382,42 @@ def double_angle(ctx, c, scale, rlk):
     return ctx.add_const(ctx.rescale(prod), -1.0, sc), sc
 
 
-def bootstrap_encrypted(ctx, ct, plan, pts, keys, rlk, conj_key, trace=None):
+def bootstrap_encrypted(ctx, ct, plan, pts, keys, rlk, conj_key, trace=None, mask=None):
     """The six steps on a ciphertext of scale plan.in_scale at any level >= 1
     (returns (ct, scale)).  pts: plan.encode(ctx); keys: step -> key;
-    trace (optional dict) receives the intermediate ciphertexts."""
+    trace (optional dict) receives the intermediate ciphertexts.
+
+    Sparse plans (plan.ns < N/2; the input at level >= 2, mask =
+    plan.encode_mask(ctx)) take the message of slots [0, ns) only and
+    return it in every copy of ns slots: the input is masked to those slots
+    and repeated in every copy (so its polynomial lies in Z[X^copies]);
+    after ModRaise the trace (the sum of the copies' rotations) removes the
+    other coefficients of q_0 I; CoeffToSlot is the ns-slot transform of
+    that subring, ending in the copy factor (1, -i); one EvalMod runs on
+    y + conj(y) = (T_lo, T_hi) / (K q_0); SlotToCoeff starts with the join
+    map back to T_lo + i T_hi in every copy."""
     N = ctx.N
-    x = mod_raise(ctx, ctx.drop_level(ct, 1))
+    sparse = plan.ns < plan.n
+    if sparse:
+        # slots [0, ns) kept, repeated in every copy: the message then lies in
+        # the subring the trace below projects onto
+        x = ctx.rescale(ctx.mul_plain(ctx.drop_level(ct, 2), mask))
+        for st in plan.trace_steps():
+            x = ctx.add(x, ctx.rotate(x, ckks.galois_elt(st, N), keys[st]))
+        if trace is not None:
+            trace["repeated"] = x
+        x = mod_raise(ctx, x)
+    else:
+        x = mod_raise(ctx, ctx.drop_level(ct, 1))
     if trace is not None:
         trace["raised"] = x
+    if sparse:
+        # the trace: the sum of the copies' automorphisms, which keeps the
+        # coefficients of X^(copies j) (times copies) and drops the others
+        for st in plan.trace_steps():
+            x = ctx.add(x, ctx.rotate(x, ckks.galois_elt(st, N), keys[st]))
+        if trace is not None:
+            trace["traced"] = x
     s = float(ctx.q[0])
     levels = plan.cts + plan.stc
     for i, (rr, groups, ps, lv) in enumerate(plan.cts):
@@ -312,6 +427,21 @@ def bootstrap_encrypted(ctx, ct, plan, pts, keys, rlk, conj_key, trace=None):
         trace["cts"] = x
     xc = ctx.rotate(x, 2 * N - 1, conj_key)
     lv = x.shape[1]
+    if sparse:
+        # one part: 2 Re u in the even copies, 2 Im u in the odd ones
+        c = OF.cheb_encrypted(ctx, ctx.add(x, xc), s, plan.coeffs, rlk)
+        sc = s
+        for _ in range(plan.r):
+            c, sc = double_angle(ctx, c, sc, rlk)
+        s = sc
+        if trace is not None:
+            trace["evalmod"] = [c]
+        y = c
+        for i, (rr, groups, ps, lv) in enumerate(plan.stc):
+            y = OF.linear_encrypted(ctx, y, rr, groups, pts[len(plan.cts) + i], keys)
+            s = (s * ps) / float(ctx.q[lv - 1])
+        assert len(levels) == len(pts)
+        return y, s
     re = ctx.add(x, xc)
     im = ctx.mul_plain(ctx.add(xc, ctx.mul_int(x, -1)), monomial(ctx, lv))
     parts = []

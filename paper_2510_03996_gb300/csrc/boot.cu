@@ -24,6 +24,15 @@
 //      `stc_levels` layers, q_0 / (2 pi Delta_in) folded into the first; the
 //      last is encoded so that the output lands on scale ~= Delta_in.
 //
+// Sparse bootstrap (slots [0, n_s), n_s <= N/4, copies = N / (2 n_s)): the
+// input is masked to those slots at level 2 and repeated in every copy of
+// n_s slots (its polynomial then lies in Z[X^copies]); after ModRaise the
+// trace (the sum of the copies' rotations) keeps copies x the coefficients of
+// that subring; CoeffToSlot is the n_s-slot transform in every copy, ending
+// in the factor 1 / -i on even / odd copies, so y + conj(y) carries the low
+// and the high coefficients in one ciphertext: one EvalMod; SlotToCoeff
+// starts with (a, b) -> a + i b in every copy.
+//
 // Stage of half-length h of F (blocks of 2h slots, u < h the position in the
 // block, w_u = exp(2 pi i (5^u mod 8h) / 8h)):
 //   out[b+u] = in[b+u] + w_u in[b+u+h],  out[b+u+h] = in[b+u] - w_u in[b+u+h];
@@ -143,14 +152,65 @@ std::vector<MergedLevel> merged_levels(u32 n, u32 levels, bool cts)
     return out;
 }
 
+// An n_s-slot map as an n-slot map for inputs that repeat every n_s slots:
+// every diagonal tiled n / n_s times, offset o taken as o or o - n_s (the
+// nearer to 0) modulo n.  On such an input it is the n_s-slot map in every copy.
+Diags replicate(const Diags &M, u32 ns, u32 n)
+{
+    Diags out;
+    for (const auto &kv : M) {
+        const u32 o = kv.first <= ns / 2 ? kv.first : (u32)((kv.first + n - ns) % n);
+        std::vector<cd> d(n);
+        for (u32 j = 0; j < n; j++) d[j] = kv.second[j % ns];
+        auto it = out.find(o);
+        if (it == out.end()) {
+            out.emplace(o, std::move(d));
+        } else {
+            for (u32 j = 0; j < n; j++) it->second[j] += d[j];
+        }
+    }
+    return out;
+}
+
+// the sparse CoeffToSlot's last factor: 1 on even copies of n_s slots, -i on
+// odd ones; with y = f u (u repeated), y + conj(y) = 2 Re u on the even
+// copies and 2 Im u on the odd ones
+void times_copy_factor(Diags &M, u32 ns)
+{
+    for (auto &kv : M)
+        for (u32 j = 0; j < kv.second.size(); j++)
+            if ((j / ns) & 1) kv.second[j] *= cd(0.0, -1.0);
+}
+
+// {0: (1, i), n_s: (i, 1)} (period 2 n_s): (a, b) -> a + i b in every copy
+Diags join_map(u32 ns, u32 n)
+{
+    std::vector<cd> p1(n), p2(n);
+    for (u32 j = 0; j < n; j++) {
+        const bool odd = (j / ns) & 1;
+        p1[j] = odd ? cd(0.0, 1.0) : cd(1.0);
+        p2[j] = odd ? cd(1.0) : cd(0.0, 1.0);
+    }
+    Diags out;
+    out.emplace(0u, std::move(p1));
+    out.emplace(ns % n, std::move(p2));
+    return out;
+}
+
+u32 boot_slots(const fheon_ctx *ctx, const fheon_boot_params &p) { return p.slots ? p.slots : ctx->N / 2; }
+
 u32 boot_depth(const fheon_boot_params &p) { return p.cts_levels + cheb_depth(p.degree) + p.doublings + p.stc_levels; }
 
 int check_params(fheon_ctx *ctx, const fheon_boot_params *p)
 {
-    u32 logn = ctx->logN - 1;
+    const u32 ns = boot_slots(ctx, *p);
+    if (ns < 2 || ns > ctx->N / 2 || (ns & (ns - 1)))
+        return fail(ctx, FHEON_ERR_ARG, "bootstrap: slots 0 or a power of two in [2, N/2]");
+    u32 logn = 0;
+    while ((1u << logn) < ns) logn++;
     if (!p->cts_levels || !p->stc_levels || p->cts_levels > logn || p->stc_levels > logn || !p->K ||
         p->degree < 2 || p->degree > 1023 || p->doublings > 30)
-        return fail(ctx, FHEON_ERR_ARG, "bootstrap: levels in [1, log2(N/2)], K >= 1, degree in [2, 1023]");
+        return fail(ctx, FHEON_ERR_ARG, "bootstrap: levels in [1, log2(slots)], K >= 1, degree in [2, 1023]");
     if (boot_depth(*p) > ctx->L - 1)
         return fail(ctx, FHEON_ERR_LEVEL, "bootstrap needs %u levels above q_0, the context has %u", boot_depth(*p),
                     ctx->L - 1);
@@ -293,8 +353,149 @@ int diag_layer(fheon_ctx *ctx, const Diags &M, u32 stride, cd factor, u32 baby, 
     return FHEON_OK;
 }
 
+// x_p <- x_p + sigma_g(x_p) for every input p, the n automorphisms as one
+// key-switching batch (sigma_g(x_p) lands in tmp_p)
+static int add_automorph_many(fheon_ctx *ctx, fheon_ct *const *xs, fheon_ct *const *tmp, u32 n, u64 g, PlanKeep *keep)
+{
+    auto key = ctx->keys.find(g);
+    if (key == ctx->keys.end())
+        return fail(ctx, FHEON_ERR_NO_KEY, "bootstrap: no key for Galois element %llu", (unsigned long long)g);
+    std::vector<KsItem> ks(n);
+    int rc;
+    for (u32 p = 0; p < n; p++) {
+        const fheon_ct *x = xs[p];
+        if ((rc = ct_reshape(ctx, tmp[p], x->level))) return rc;
+        tmp[p]->scale = x->scale;
+        ks[p].c0 = x->c0();
+        ks[p].c1 = x->c1(ctx->N);
+        ks[p].out = tmp[p]->c0();
+        ks[p].key = key->second.mem.as<u64>();
+        ks[p].g = g;
+        ks[p].level = x->level;
+        ks[p].lead = p;
+    }
+    if ((rc = ks_many(ctx, ks.data(), n, false, keep))) return rc;
+    for (u32 p = 0; p < n; p++)
+        if ((rc = fheon_add(ctx, xs[p], tmp[p], xs[p]))) return rc;
+    return FHEON_OK;
+}
+
+// The sparse bootstrap of n inputs (slots [0, n_s); every step of all inputs
+// as one batch): mask and repeat at the bottom, ModRaise, the trace, the
+// n_s-slot CoeffToSlot, y + conj(y), one EvalMod, SlotToCoeff.
+static int boot_sparse_many(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n,
+                            fheon_ct *const *outs)
+{
+    const u32 N = ctx->N, D = (u32)ly->coeffs.size() - 1, ns = ly->boot_ns;
+    int rc;
+    for (u32 p = 0; p < n; p++) {
+        if (ins[p]->level < 2) return fail(ctx, FHEON_ERR_LEVEL, "sparse bootstrap: input at level %u, needs >= 2", ins[p]->level);
+        if (std::fabs(ins[p]->scale - ly->in_scale) > 1e-9 * ly->in_scale)
+            return fail(ctx, FHEON_ERR_SCALE, "bootstrap prepared for scale %g, got %g", ly->in_scale, ins[p]->scale);
+    }
+    auto conj = ctx->keys.find(2ull * N - 1);
+    if (conj == ctx->keys.end()) return fail(ctx, FHEON_ERR_NO_KEY, "bootstrap: no conjugation key");
+    if (ly->bsets.size() < n) ly->bsets.resize(n);
+    // per input: 0 raised, 1-2 chain, 3 automorphism, 4 masked and repeated,
+    // 5-6 doubling ping-pong, 7 the input at level 2
+    for (u32 p = 0; p < n; p++) {
+        auto &w = ly->bsets[p].w;
+        if (w.size() < 8) w.resize(8, nullptr);
+        for (fheon_ct *&c : w)
+            if (!c && (rc = fheon_ct_create(ctx, 1, 1.0, &c))) return rc;
+    }
+    auto W = [&](u32 p, u32 i) { return ly->bsets[p].w[i]; };
+    std::vector<fheon_ct *> xs(n), tmp(n), dsts(n);
+    for (u32 p = 0; p < n; p++) {
+        if ((rc = fheon_drop_level(ctx, ins[p], 2, W(p, 7)))) return rc;
+        if ((rc = fheon_mul_plain(ctx, W(p, 7), ly->boot_mask, W(p, 4)))) return rc;
+        if ((rc = fheon_rescale(ctx, W(p, 4), W(p, 4)))) return rc;
+        xs[p] = W(p, 4);
+        tmp[p] = W(p, 3);
+    }
+    // the copies' automorphisms: Rot_{n_s}, Rot_{2 n_s}, ...
+    std::vector<u64> gs;
+    for (u32 st = ns; st < N / 2; st <<= 1) gs.push_back(fheon_galois_elt(ctx, (int32_t)st));
+    for (u64 g : gs)
+        if ((rc = add_automorph_many(ctx, xs.data(), tmp.data(), n, g, ly->collect))) return rc;
+    for (u32 p = 0; p < n; p++) {
+        if ((rc = mod_raise_ct(ctx, W(p, 4), W(p, 0)))) return rc;
+        W(p, 0)->scale = (double)ctx->mod[0];
+        xs[p] = W(p, 0);
+    }
+    {
+        Range range("Trace");
+        for (u64 g : gs)
+            if ((rc = add_automorph_many(ctx, xs.data(), tmp.data(), n, g, ly->collect))) return rc;
+    }
+    std::vector<const fheon_ct *> cx(xs.begin(), xs.end());
+    auto sub_apply = [&](const fheon_layer *sub, fheon_ct *const *to) {
+        sub->collect = ly->collect;
+        const int r = fheon_layer_apply_batch(ctx, sub, cx.data(), n, to);
+        sub->collect = nullptr;
+        return r;
+    };
+    {
+        Range range("CoeffToSlot");
+        for (u32 i = 0; i < ly->ncts; i++) {
+            for (u32 p = 0; p < n; p++) dsts[p] = W(p, 1 + (i & 1));
+            if ((rc = sub_apply(ly->subs[i], dsts.data()))) return rc;
+            for (u32 p = 0; p < n; p++) cx[p] = dsts[p];
+        }
+    }
+    Range phase("EvalMod");
+    // y + conj(y): the low coefficients in the even copies, the high ones in
+    // the odd copies -- EvalMod's one input
+    std::vector<KsItem> ks(n);
+    for (u32 p = 0; p < n; p++) {
+        const fheon_ct *x = cx[p];
+        if ((rc = ct_reshape(ctx, W(p, 3), x->level))) return rc;
+        W(p, 3)->scale = x->scale;
+        ks[p].c0 = x->c0();
+        ks[p].c1 = x->c1(N);
+        ks[p].out = W(p, 3)->c0();
+        ks[p].key = conj->second.mem.as<u64>();
+        ks[p].g = 2ull * N - 1;
+        ks[p].level = x->level;
+        ks[p].lead = p;
+    }
+    if ((rc = ks_many(ctx, ks.data(), n, false, ly->collect))) return rc;
+    std::vector<std::vector<fheon_ct *> *> works(n);
+    std::vector<fheon_ct *> a(n), b(n);
+    for (u32 p = 0; p < n; p++) {
+        const fheon_ct *x = cx[p];
+        auto &bs = ly->bsets[p];
+        if ((rc = cheb_work(ctx, bs.re, D, x->level, x->scale))) return rc;
+        if ((rc = fheon_add(ctx, x, W(p, 3), bs.re[1]))) return rc;
+        works[p] = &bs.re;
+        a[p] = W(p, 5);
+        b[p] = W(p, 6);
+    }
+    if ((rc = cheb_series_many(ctx, ly->coeffs, works.data(), n, a.data(), ly->collect))) return rc;
+    std::vector<RelinItem> it(n);
+    for (u32 i = 0; i < ly->boot_r; i++) {
+        for (u32 k = 0; k < n; k++) it[k] = RelinItem{a[k], a[k], a[k]->level, true, b[k]};
+        if ((rc = mul_relin_many(ctx, it.data(), n, ly->collect))) return rc;
+        for (u32 k = 0; k < n; k++) {
+            if ((rc = fheon_rescale(ctx, b[k], b[k]))) return rc;
+            if ((rc = fheon_add_const(ctx, b[k], -1.0, b[k]))) return rc;
+            std::swap(a[k], b[k]);
+        }
+    }
+    for (u32 p = 0; p < n; p++) cx[p] = a[p];
+    phase.next("SlotToCoeff");
+    const u32 nst = (u32)ly->subs.size() - ly->ncts;
+    for (u32 i = 0; i < nst; i++) {
+        for (u32 p = 0; p < n; p++) dsts[p] = i + 1 == nst ? outs[p] : W(p, 1 + (i & 1));
+        if ((rc = sub_apply(ly->subs[ly->ncts + i], dsts.data()))) return rc;
+        for (u32 p = 0; p < n; p++) cx[p] = dsts[p];
+    }
+    return FHEON_OK;
+}
+
 int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *out)
 {
+    if (ly->boot_ns) return boot_sparse_many(ctx, ly, &in, 1, &out);
     if (in->level < 1) return fail(ctx, FHEON_ERR_LEVEL, "bootstrap: empty ciphertext");
     if (std::fabs(in->scale - ly->in_scale) > 1e-9 * ly->in_scale)
         return fail(ctx, FHEON_ERR_SCALE, "bootstrap prepared for scale %g, got %g", ly->in_scale, in->scale);
@@ -366,6 +567,7 @@ int boot_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_
 
 int boot_apply_many(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *ins, u32 n, fheon_ct *const *outs)
 {
+    if (ly->boot_ns) return boot_sparse_many(ctx, ly, ins, n, outs);
     const u32 N = ctx->N, D = (u32)ly->coeffs.size() - 1;
     int rc;
     for (u32 p = 0; p < n; p++) {
@@ -487,6 +689,7 @@ int fheon_boot_params_default(const fheon_ctx *ctx, fheon_boot_params *p)
     p->doublings = r;
     p->degree = 27;
     p->baby = 0;
+    p->slots = 0;
     return FHEON_OK;
 }
 
@@ -535,6 +738,22 @@ int fheon_bootstrap_compose(fheon_ctx *ctx, const fheon_boot_params *p, const fh
     ly->boot_r = p->doublings;
     ly->in_scale = in_scale;
     ly->out_level = lv;
+    const u32 n = ctx->N / 2, ns = boot_slots(ctx, *p);
+    if (ns < n) {
+        // the input mask: 1 in slots [0, n_s), at level 2 and scale q_1, the
+        // prime its rescale drops
+        if (L < 2) return fail(ctx, FHEON_ERR_LEVEL, "sparse bootstrap: the context needs 2 primes");
+        std::vector<double> re(n, 0.0), im(n, 0.0);
+        for (u32 j = 0; j < ns; j++) re[j] = 1.0;
+        fheon_pt *mask = nullptr;
+        if ((rc = fheon_encode_plain(ctx, re.data(), im.data(), n, 2, (double)ctx->mod[1], &mask))) return rc;
+        ly->boot_ns = ns;
+        ly->nslots = n;
+        ly->boot_mask = mask;
+        ly->own_boot_mask = true;
+        *out = ly.release();
+        return FHEON_OK;
+    }
     // X^(N/2) (the constant i in every slot, scale 1) where im is formed and
     // where the parts are recombined
     std::vector<int64_t> mono(ctx->N, 0);
@@ -567,14 +786,20 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double 
     u32 lv = L;
     double s = (double)ctx->mod[0];
     const double q0 = (double)ctx->mod[0];
-    // CoeffToSlot: 1/(2K) and the change of scale q_0 -> Delta_b in the first level
+    // CoeffToSlot: 1/(2K) and the change of scale q_0 -> Delta_b in the first
+    // level.  Sparse: the n_s-slot transform in every copy, 1/copies in the
+    // first level (the trace summed the copies), the copy factor in the last
+    const u32 ns = boot_slots(ctx, p), copies = n / ns;
     const double delta_b = (double)ctx->mod[L - p.cts_levels - 1];
-    auto cl = merged_levels(n, p.cts_levels, true);
+    auto cl = merged_levels(ns, p.cts_levels, true);
     for (u32 i = 0; i < p.cts_levels; i++) {
         const double q = (double)ctx->mod[lv - 1];
         const double ps = i == 0 ? q * (delta_b / q0) : q;
         fheon_layer *l = nullptr;
-        if ((rc = diag_layer(ctx, cl[i].M, cl[i].stride, cd(i == 0 ? 1.0 / (2.0 * (double)p.K) : 1.0), p.baby, lv, ps, &l))) {
+        Diags M = ns < n ? replicate(cl[i].M, ns, n) : std::move(cl[i].M);
+        if (ns < n && i + 1 == p.cts_levels) times_copy_factor(M, ns);
+        const cd f(i == 0 ? 1.0 / (2.0 * (double)p.K * (double)copies) : 1.0);
+        if ((rc = diag_layer(ctx, M, cl[i].stride, f, p.baby, lv, ps, &l))) {
             cleanup();
             return rc;
         }
@@ -587,13 +812,20 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double 
     lv -= p.doublings;
     // SlotToCoeff: q_0 / (2 pi Delta_in) in the first level, the change of
     // scale onto Delta_in in the last
-    auto sl = merged_levels(n, p.stc_levels, false);
+    // (sparse: the n_s-slot transform in every copy, the join map first)
+    auto sl = merged_levels(ns, p.stc_levels, false);
     for (u32 i = 0; i < p.stc_levels; i++) {
         const double q = (double)ctx->mod[lv - 1];
         const double ps = i + 1 == p.stc_levels ? q * (in_scale / s) : q;
         fheon_layer *l = nullptr;
         const cd f(i == 0 ? q0 / (2.0 * M_PI * in_scale) : 1.0);
-        if ((rc = diag_layer(ctx, sl[i].M, sl[i].stride, f, p.baby, lv, ps, &l))) {
+        Diags M = ns < n ? replicate(sl[i].M, ns, n) : std::move(sl[i].M);
+        u32 stride = sl[i].stride;
+        if (ns < n && i == 0) {
+            M = compose(M, join_map(ns, n), n);
+            stride = 1;
+        }
+        if ((rc = diag_layer(ctx, M, stride, f, p.baby, lv, ps, &l))) {
             cleanup();
             return rc;
         }
@@ -608,6 +840,17 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double 
     }
     (*out)->own_subs = true;
     (*out)->out_scale = s;
+    return FHEON_OK;
+}
+
+int fheon_bootstrap_set_mask(fheon_ctx *ctx, fheon_layer *ly, const fheon_pt *mask)
+{
+    if (!ctx || !ly || !mask || ly->kind != LAYER_BOOT) return FHEON_ERR_ARG;
+    if (!ly->boot_ns) return fail(ctx, FHEON_ERR_ARG, "set_mask: not a sparse bootstrap");
+    if (mask->level < 2) return fail(ctx, FHEON_ERR_ARG, "set_mask: the mask must be at level >= 2");
+    if (ly->own_boot_mask) fheon_pt_destroy(const_cast<fheon_pt *>(ly->boot_mask));
+    ly->boot_mask = mask;
+    ly->own_boot_mask = false;
     return FHEON_OK;
 }
 

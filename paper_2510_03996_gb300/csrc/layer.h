@@ -45,6 +45,11 @@ struct fheon_layer {
     double in_scale = 0, out_scale = 0;
     u32 out_level = 0;
     fheon_pt *mono[2] = {nullptr, nullptr};
+    // sparse bootstrap: the message slots n_s (0: every slot) and the input
+    // mask of slots [0, n_s) at level 2, scale q_1 (owned unless set by the caller)
+    u32 boot_ns = 0;
+    const fheon_pt *boot_mask = nullptr;
+    bool own_boot_mask = false;
     mutable std::vector<fheon_ct *> cheb2; // the second part's series working set
     mutable std::vector<std::vector<fheon_ct *>> sets; // ReLU on a batch: one working set per input
     // bootstrapping a batch: per input, its 10 working ciphertexts and the two
@@ -87,6 +92,7 @@ struct fheon_layer {
         if (own_subs)
             for (fheon_layer *l : subs) delete l;
         for (fheon_pt *p : mono) fheon_pt_destroy(p);
+        if (own_boot_mask) fheon_pt_destroy(const_cast<fheon_pt *>(boot_mask));
         for (fheon_ct *c : cheb2) fheon_ct_destroy(c);
         for (auto &v : sets)
             for (fheon_ct *c : v) fheon_ct_destroy(c);

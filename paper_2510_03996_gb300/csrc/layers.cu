@@ -397,6 +397,10 @@ int fheon_layer_plain(const fheon_layer *ly, uint32_t which, uint32_t g, uint32_
         if (ly->kind != LAYER_BOOT || g > 1 || t) return FHEON_ERR_ARG;
         *out = ly->mono[g];
         return FHEON_OK;
+    case FHEON_PLAIN_BOOT_MASK:
+        if (ly->kind != LAYER_BOOT || g || t) return FHEON_ERR_ARG;
+        *out = ly->boot_mask;
+        return FHEON_OK;
     default: return FHEON_ERR_ARG;
     }
 }

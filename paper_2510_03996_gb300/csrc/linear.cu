@@ -696,6 +696,9 @@ int fheon_layer_rotation_steps(const fheon_layer *ly, int32_t *out, uint32_t *n)
     } else if (ly->kind == LAYER_FC) {
         for (u32 x = 1; x < ly->nslots; x <<= 1) st.insert((int32_t)x);
     } else if (ly->kind == LAYER_BOOT) {
+        // sparse: the copies' rotations n_s, 2 n_s, ... (repetition and trace)
+        if (ly->boot_ns)
+            for (u32 x = ly->boot_ns; x < ly->nslots; x <<= 1) st.insert((int32_t)x);
         for (const fheon_layer *sub : ly->subs) {
             for (int32_t x : sub->r)
                 if (x) st.insert(x);

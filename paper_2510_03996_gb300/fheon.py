@@ -53,9 +53,11 @@ STEP_LAYER, STEP_ADD, STEP_SCALE = 0, 1, 2
 
 class fheon_boot_params(ctypes.Structure):
     """Bootstrapping: CoeffToSlot / SlotToCoeff levels, EvalMod's range K,
-    series degree and double-angle steps, BSGS baby steps (0: fewest rotations)."""
+    series degree and double-angle steps, BSGS baby steps (0: fewest rotations),
+    message slots (0: all N/2; fewer: the sparse bootstrap)."""
     _fields_ = [("cts_levels", ctypes.c_uint32), ("stc_levels", ctypes.c_uint32), ("K", ctypes.c_uint32),
-                ("degree", ctypes.c_uint32), ("doublings", ctypes.c_uint32), ("baby", ctypes.c_uint32)]
+                ("degree", ctypes.c_uint32), ("doublings", ctypes.c_uint32), ("baby", ctypes.c_uint32),
+                ("slots", ctypes.c_uint32)]
 
 
 # name -> argument types (all return int unless listed in _RESTYPE)
@@ -149,6 +151,7 @@ SIGNATURES = {
     "fheon_bootstrap_prepare": [c_vp, P(fheon_boot_params), c_dbl, c_vpp],
     "fheon_bootstrap_compose": [c_vp, P(fheon_boot_params), P(c_vp), P(c_vp), P(c_dbl), c_dbl, c_vpp],
     "fheon_bootstrap_keygen": [c_vp, c_vp, c_vp],
+    "fheon_bootstrap_set_mask": [c_vp, c_vp, c_vp],
     "fheon_bootstrap_info": [c_vp, P(c_u32), P(c_dbl)],
     "fheon_mod_raise": [c_vp, c_vp, c_vp],
     "fheon_selftest_wait": [c_vp, c_u32],
@@ -809,6 +812,12 @@ class Context:
     def bootstrap_keygen(self, sk, layer):
         self._chk(load().fheon_bootstrap_keygen(self.h, sk.h, layer.h))
 
+    def bootstrap_set_mask(self, layer, mask):
+        """Sparse bootstrap: use the plaintext `mask` (kept alive by the layer)
+        as the input mask."""
+        self._chk(load().fheon_bootstrap_set_mask(self.h, layer.h, mask.h))
+        layer.mask_ref = mask
+
     @staticmethod
     def bootstrap_info(layer):
         lv, sc = c_u32(0), c_dbl(0)
@@ -888,7 +897,7 @@ class Context:
         check(load().fheon_layer_rotation_steps(layer.h, out, ctypes.byref(n)))
         return list(out[:n.value])
 
-    PLAIN = {"product": 0, "place": 1, "bias": 2, "mask": 3, "mono": 4}
+    PLAIN = {"product": 0, "place": 1, "bias": 2, "mask": 3, "mono": 4, "boot_mask": 5}
 
     @staticmethod
     def layer_plan(layer):

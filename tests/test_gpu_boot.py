@@ -54,9 +54,10 @@ def test_conjugation_bit_exact(boot):
     assert gpu_common.mismatch(g.ct_download(y), want) == 0
 
 
-def _composed(pr):
+def _composed(pr, plan=None):
     """The library's bootstrap over the oracle plan's integer plaintexts."""
-    g, o, plan = pr.g, pr.o, pr.plan
+    g, o = pr.g, pr.o
+    plan = plan or pr.plan
     gl, opts = [], []
     for rr, groups, ps, lv in plan.cts + plan.stc:
         gp, op = [], []
@@ -76,7 +77,8 @@ def _composed(pr):
         layer.pts = gp  # the plaintexts outlive the layer
         gl.append(layer)
         opts.append(op)
-    prm = pr.F.fheon_boot_params(len(plan.cts), len(plan.stc), plan.K, plan.D, plan.r, 0)
+    prm = pr.F.fheon_boot_params(len(plan.cts), len(plan.stc), plan.K, plan.D, plan.r, 0,
+                                 0 if plan.ns == plan.n else plan.ns)
     return g.bootstrap_compose(prm, gl[:len(plan.cts)], gl[len(plan.cts):], plan.coeffs, pr.P["scale"]), opts
 
 
@@ -162,3 +164,70 @@ def test_bootstrap_batch_equals_one_by_one(boot):
     outs = g.layer_apply_batch(layer, cts[::-1])
     for o, a in zip(outs, alone[::-1]):
         assert gpu_common.mismatch(g.ct_download(o), a) == 0
+
+
+# ---------------------------------------------------------------- sparse bootstrap
+@pytest.fixture(scope="module")
+def sparse(boot):
+    """The sparse bootstrap of slots [0, N/4) on the same context."""
+    boot.splan = B.Plan(boot.o, boot.P["scale"], slots=boot.N // 4)
+    boot.add_keys(boot.splan.steps())
+    return boot
+
+
+def test_sparse_bootstrap_bit_exact(sparse):
+    """Composed from the oracle's integer plaintexts and its input mask: the
+    same ciphertext to the bit as the oracle's sparse bootstrap, and the
+    message of slots [0, N/4) in both copies."""
+    g, o, plan = sparse.g, sparse.o, sparse.splan
+    layer, opts = _composed(sparse, plan)
+    mc = ckks.encode(plan.mask_slots(), sparse.N, float(o.q[1]))
+    mask = g.plain_from_coeffs(mc, 2, float(o.q[1]))
+    m = o.plain_from_coeffs(mc, 2)
+    g.bootstrap_set_mask(layer, mask)
+    assert sorted(g.layer_rotation_steps(layer)) == plan.steps()
+    okeys = {st: sparse.okeys[g.galois_elt(st)] for st in plan.steps()}
+    z, ct, oct_ = _input(sparse, 0xB201, 3)
+    y = g.layer_apply(layer, ct)
+    want, osc = B.bootstrap_encrypted(o, oct_, plan, opts, okeys, sparse.orlk, sparse.oconj, mask=m)
+    assert gpu_common.mismatch(g.ct_download(y), want) == 0
+    assert g.ct_info(y) == (plan.out_level, osc)
+    got = np.asarray(g.decode(g.decrypt(sparse.sk, y))).real
+    ns = plan.ns
+    assert np.max(np.abs(got - np.tile(z[:ns], 2))) < 1e-4
+
+
+def test_sparse_bootstrap_prepared_by_the_library(sparse):
+    """The library's own sparse bootstrap: the oracle plan's keys, the input's
+    slots [0, N/4) in both copies within 1e-4, whatever the other slots held;
+    a batch equal to one by one bit for bit; an input at level 1 refused."""
+    g, F, plan = sparse.g, sparse.F, sparse.splan
+    p = g.boot_params_default()
+    p.slots = sparse.N // 4
+    layer = g.bootstrap_prepare(sparse.P["scale"], p)
+    assert sorted(g.layer_rotation_steps(layer)) == plan.steps()
+    assert g.bootstrap_info(layer)[0] == plan.out_level
+    g.bootstrap_keygen(sparse.sk, layer)
+    ns = plan.ns
+    cts, zs = [], []
+    for i in range(2):
+        z, ct, _ = _input(sparse, 0xB202 + i, 2 + i)
+        cts.append(ct)
+        zs.append(z)
+    alone = []
+    for z, ct in zip(zs, cts):
+        y = g.layer_apply(layer, ct)
+        got = np.asarray(g.decode(g.decrypt(sparse.sk, y))).real
+        assert np.max(np.abs(got - np.tile(z[:ns], 2))) < 1e-4
+        alone.append(g.ct_download(y))
+    outs = g.layer_apply_batch(layer, cts)
+    for y, a in zip(outs, alone):
+        assert gpu_common.mismatch(g.ct_download(y), a) == 0
+    _, ct1, _ = _input(sparse, 0xB204, 1)
+    with pytest.raises(F.FheonError) as e:
+        g.layer_apply(layer, ct1)
+    assert e.value.code == -4
+    p.slots = 3
+    with pytest.raises(F.FheonError) as e:
+        g.bootstrap_prepare(sparse.P["scale"], p)
+    assert e.value.code == -1

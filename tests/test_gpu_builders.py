@@ -253,3 +253,39 @@ def test_bootstrap_builder(boot):
                                       pr.o.rotkey(pr.s_eval, conj))
     assert gpu_common.mismatch(g.ct_download(y), want) == 0
     assert g.ct_info(y) == (plan.out_level, osc)
+
+
+def test_sparse_bootstrap_builder(boot):
+    """fheon_bootstrap_prepare with slots = N/4: every CoeffToSlot and
+    SlotToCoeff level (the N/4-slot transform in both copies, the copy factor
+    in the last CoeffToSlot level, the join map in the first SlotToCoeff
+    level) and the input mask against the oracle's sparse plan, then the run
+    from the library-built plaintexts against the oracle over the same
+    integers, bit for bit."""
+    pr = boot
+    g, o = pr.g, pr.o
+    plan = B.Plan(o, pr.P["scale"], slots=pr.N // 4)
+    p = g.boot_params_default()
+    p.slots = pr.N // 4
+    layer = g.bootstrap_prepare(pr.P["scale"], p)
+    info = g.layer_plan(layer)
+    assert (info["nt"], info["ng"]) == (len(plan.cts), len(plan.stc))
+    assert g.bootstrap_info(layer)[0] == plan.out_level
+    opts = []
+    for i, (rr, groups, ps, lv) in enumerate(plan.cts + plan.stc):
+        opts.append(check_rotsum(pr, g.layer_sub(layer, i), rr, groups, lv, ps))
+    q1 = float(o.q[1])
+    mm = check_plain(pr, g.layer_plain(layer, "boot_mask"), plan.mask_slots(), 2, q1)
+    assert g.layer_plain(layer, "mono", 0) is None
+    pr.add_keys(plan.steps())
+    conj = 2 * pr.N - 1
+    g.galois_keygen(pr.sk, [conj])
+    g.relinkeygen(pr.sk)
+    okeys = {st: pr.okeys[g.galois_elt(st)] for st in plan.steps()}
+    z = synth.uniform_slots(0xB1E, 0, pr.N // 2)
+    ct, oct_ = pr.encrypt_both(ckks.encode(z, pr.N, pr.P["scale"]), nonce=0xB1E, level=3)
+    y = g.layer_apply(layer, ct)
+    want, osc = B.bootstrap_encrypted(o, oct_, plan, opts, okeys, o.relinkey(pr.s_eval), o.rotkey(pr.s_eval, conj),
+                                      mask=o.plain_from_coeffs(mm, 2))
+    assert gpu_common.mismatch(g.ct_download(y), want) == 0
+    assert g.ct_info(y) == (plan.out_level, osc)

@@ -195,3 +195,89 @@ def test_slot_transform_at_the_test_size():
         r, groups = B.bsgs_plan(M, n, stride)
         x = B.plan_slots(x, r, groups)
     assert np.max(np.abs(x - brv_order(zp))) < 1e-11
+
+
+# ---------------------------------------------------------------- sparse bootstrap
+def subring_poly(T, copies):
+    """The polynomial T(X^copies) of degree < copies * len(T)."""
+    t = np.zeros(copies * len(T))
+    t[::copies] = T
+    return t
+
+
+@pytest.mark.parametrize("n,ns", [(64, 32), (64, 16), (256, 32)])
+def test_sparse_transforms_on_the_subring(n, ns):
+    """For a real T with 2 ns coefficients, the N-ring polynomial T(X^(n/ns))
+    has the slots of T in its own ring repeated in every copy (decode on
+    both sides).  The sparse CoeffToSlot levels take those slots to
+    u = brv(T_lo + i T_hi) in even copies and -i u in odd ones, so that
+    y + conj(y) = 2 (brv T_lo, brv T_hi); the sparse SlotToCoeff levels take
+    (brv T_lo, brv T_hi) back to the slots."""
+    rng = synth.rng(0xB00C, n + ns)
+    T = rng.normal(size=2 * ns)
+    copies = n // ns
+    slots = ckks.decode(subring_poly(T, copies), n, 1.0)
+    own = ckks.decode(T, ns, 1.0)
+    assert np.max(np.abs(slots - np.tile(own, copies))) < 1e-9
+    x = slots
+    for stride, M in B.cts_levels_sparse(n, ns, 3 if ns >= 8 else 1):
+        r, groups = B.bsgs_plan(M, n, stride)
+        x = B.plan_slots(x, r, groups)
+    u = brv_order(T[:ns] + 1j * T[ns:])
+    want = np.tile(np.concatenate([u, -1j * u]), n // (2 * ns))
+    assert np.max(np.abs(x - want)) < 1e-9
+    w = x + np.conj(x)
+    assert np.max(np.abs(w - np.tile(2 * np.concatenate([brv_order(T[:ns]), brv_order(T[ns:])]), n // (2 * ns)))) < 1e-9
+    v = np.tile(np.concatenate([brv_order(T[:ns]), brv_order(T[ns:])]), n // (2 * ns)).astype(np.complex128)
+    for stride, M in B.stc_levels_sparse(n, ns, 3 if ns >= 8 else 1):
+        r, groups = B.bsgs_plan(M, n, stride)
+        v = B.plan_slots(v, r, groups)
+    assert np.max(np.abs(v - slots)) < 1e-9
+
+
+def test_sparse_plan_levels_keys_and_scales(boot_ctx):
+    P, ctx, s, se, pk, plan = boot_ctx
+    sp = B.Plan(ctx, P["scale"], slots=ctx.N // 4)
+    assert sp.out_level == plan.out_level and abs(sp.out_scale / P["scale"] - 1) < 1e-12
+    assert sp.trace_steps() == [ctx.N // 4]
+    assert ctx.N // 4 in sp.steps() and 0 not in sp.steps()
+    assert np.array_equal(sp.mask_slots(), np.concatenate([np.ones(ctx.N // 4), np.zeros(ctx.N // 4)]))
+
+
+def test_sparse_bootstrap_encrypted(boot_ctx):
+    """The encrypted sparse bootstrap: the input's slots [0, N/4) come back in
+    both copies (whatever the other slots held); the traced plaintext is
+    `copies` times an element of Z[X^copies] up to key-switching noise; the
+    CoeffToSlot output is (u, -i u) with u = brv(T_lo + i T_hi) / (2 K q_0)
+    for T the subring coefficients / copies; EvalMod's output is
+    sin(2 pi (brv T_lo, brv T_hi) / q_0)."""
+    P, ctx, s, se, pk, plan = boot_ctx
+    N, n = ctx.N, ctx.N // 2
+    sp = B.Plan(ctx, P["scale"], slots=N // 4)
+    ns, copies = sp.ns, sp.copies
+    keys = {st: ctx.rotkey(se, ckks.galois_elt(st, N)) for st in sp.steps()}
+    pts = sp.encode(ctx)
+    z = synth.uniform_slots(0xB00D, 0, n)
+    ct = ctx.drop_level(ctx.encrypt(pk, ckks.encode(z, N, P["scale"]), 13), 3)
+    tr = {}
+    y, sc = B.bootstrap_encrypted(ctx, ct, sp, pts, keys, ctx.relinkey(se), ctx.rotkey(se, 2 * N - 1), trace=tr,
+                                  mask=sp.encode_mask(ctx))
+    assert y.shape == (2, sp.out_level, N) and sc == sp.out_scale
+    out = ctx.decode_ct(se, y, sc)
+    assert np.max(np.abs(out - np.tile(z[:ns], 2))) < 1e-4
+    # the repeated input: slots [0, ns) in both copies
+    rep = ctx.decode_ct(se, tr["repeated"], P["scale"])
+    assert np.max(np.abs(rep - np.tile(z[:ns], 2))) < 1e-6
+    q0 = float(ctx.q[0])
+    t = np.array([float(v) for v in ctx.decrypt_coeffs(se, tr["traced"])])
+    off = np.delete(t, np.arange(0, N, copies))
+    assert np.max(np.abs(off)) < 2.0 ** 20 < q0 / 2.0 ** 20
+    T = t[::copies] / copies
+    u = brv_order((T[:ns] + 1j * T[ns:]) / (2 * sp.K * q0))
+    got = ctx.decode_ct(se, tr["cts"], sp.cts_scale)
+    assert np.max(np.abs(got - np.concatenate([u, -1j * u]))) < 1e-10
+    (part,) = tr["evalmod"]
+    v = ctx.decode_ct(se, part, sp.evalmod_scale)
+    want = np.sin(2 * np.pi * np.concatenate([brv_order(T[:ns]), brv_order(T[ns:])]) / q0)
+    assert np.max(np.abs(v.real - want)) < 1e-7
+    assert np.max(np.abs(v.imag)) < 1e-7

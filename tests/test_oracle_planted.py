@@ -334,6 +334,30 @@ def _monomial_sign(monkeypatch):
     monkeypatch.setattr(B, "monomial", lambda ctx, level, sign=1: orig(ctx, level, -sign))
 
 
+def _copy_factor_conjugated(monkeypatch):
+    orig = B.copy_factor
+    monkeypatch.setattr(B, "copy_factor", lambda ns, n: np.conj(orig(ns, n)))
+
+
+def _join_map_swapped(monkeypatch):
+    orig = B.join_map
+
+    def bad(ns, n):
+        d = orig(ns, n)
+        return {0: d[ns % n], ns % n: d[0]}
+    monkeypatch.setattr(B, "join_map", bad)
+
+
+def _trace_skipped(monkeypatch):
+    orig = B.mod_raise
+
+    def bad(ctx, ct):
+        r = orig(ctx, ct)
+        monkeypatch.setattr(B.Plan, "trace_steps", lambda self: [])  # planted: no trace after ModRaise
+        return r
+    monkeypatch.setattr(B, "mod_raise", bad)
+
+
 def _rotation_remapped(remap):
     """A paper-form layer that rotates by remap(r) where it means r (a wrong
     shift in one of its steps)."""
@@ -377,6 +401,11 @@ PY_PLANTS = {
     "fold_rotation_sign": (_fold_rotated_the_wrong_way,
                            lambda bc: TL.test_fc_diag_plan_is_the_product(16, 4, 28, 4, 12)),
     "conjugation_monomial_sign": (_monomial_sign, lambda bc: TB.test_bootstrap_encrypted(bc)),
+    # the sparse bootstrap
+    "sparse_copy_factor_conjugated": (_copy_factor_conjugated,
+                                      lambda bc: TB.test_sparse_transforms_on_the_subring(64, 16)),
+    "sparse_join_map_swapped": (_join_map_swapped, lambda bc: TB.test_sparse_transforms_on_the_subring(64, 32)),
+    "sparse_trace_skipped": (_trace_skipped, lambda bc: TB.test_sparse_bootstrap_encrypted(bc)),
     # the paper's own layer algorithms (Sec. 5.1, 5.2, 5.4, 5.5)
     "paper_pad_row_gap_P": (_rotation_remapped(lambda r: -1 if r == -2 else r),
                             lambda bc: TP.test_padding_by_rotations(3, 5, 5, 1)),
@@ -396,7 +425,8 @@ PY_PLANTS = {
 @pytest.mark.parametrize("name", sorted(PY_PLANTS))
 def test_planted_python_mistake_fails_its_pin(name, monkeypatch, request):
     plant, pin = PY_PLANTS[name]
-    bc = request.getfixturevalue("boot_ctx") if name in ("mod_raise_uncentred", "conjugation_monomial_sign") else None
+    bc = (request.getfixturevalue("boot_ctx")
+          if name in ("mod_raise_uncentred", "conjugation_monomial_sign", "sparse_trace_skipped") else None)
     plant(monkeypatch)
     with pytest.raises(AssertionError):
         pin(bc)
