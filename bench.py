@@ -493,13 +493,19 @@ def resnet_timing(F, n_inputs=2):
     batch_secs = e0.elapsed_time(e1) / 1e3
     batch_same = all(np.array_equal(ctx.ct_download(a), ctx.ct_download(b)) for a, b in zip(outs, bouts))
     del bouts
-    z = ctx.drop_level(cts[0], 1)
-    e0.record(s)
-    for _ in range(5):
-        ctx.layer_apply(net.boot, z)
-    e1.record(s)
-    torch.cuda.synchronize()
-    boot_ms = e0.elapsed_time(e1) / 5
+    # one bootstrap alone: the sparse one (slots [0, N/4), one EvalMod) the
+    # network mostly uses, and the full one
+    z = ctx.drop_level(cts[0], 2)
+    boot_ms_by = {}
+    for slots, layer in sorted(net._boots.items()):
+        ctx.layer_apply(layer, z)
+        e0.record(s)
+        for _ in range(5):
+            ctx.layer_apply(layer, z)
+        e1.record(s)
+        torch.cuda.synchronize()
+        boot_ms_by["sparse_%d_slots" % slots if slots else "full"] = e0.elapsed_time(e1) / 5
+    boot_ms = boot_ms_by.get("sparse_%d_slots" % (N // 4), boot_ms_by.get("full"))
     # one bootstrap launch by launch (events on the context's stream): share of each kernel
     ctx.profile_begin()
     ctx.layer_apply(net.boot, z)
@@ -529,7 +535,7 @@ def resnet_timing(F, n_inputs=2):
             reg[op[4]] = ctx.add(A, Bc)
         else:
             name = "bootstrap"
-            reg[op[1]] = ctx.layer_apply(net.boot, reg[op[1]])
+            reg[op[1]] = ctx.layer_apply(op[2], reg[op[1]])
         ev[k + 1].record(s)
         names.append(name)
     torch.cuda.synchronize()
@@ -568,13 +574,15 @@ def resnet_timing(F, n_inputs=2):
         agree += int(np.argmax(got) == np.argmax(want))
     nkeys, kbytes = ctx.key_stats()
     n_boot = net.n_boot
+    n_sparse = sum(1 for op in net.plan if op[0] == "boot" and op[2] is not net._boots.get(0))
     del outs, gouts, cts, net, sk, pk
     release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
             "per_ciphertext_path_s_per_inference": plain_secs / n_inputs,
             "batched_s_per_inference": batch_secs / n_inputs, "batched_equals_one_by_one": batch_same,
             "eager_ms_by_step_kind": {k: round(v, 2) for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
-            "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstraps_per_inference": n_boot,
+            "graph_equals_eager": same, "bootstrap_ms": boot_ms, "bootstrap_ms_by_kind": boot_ms_by,
+            "bootstraps_per_inference": n_boot, "sparse_bootstraps_per_inference": n_sparse,
             "bootstrap_kernels": boot_kernels,
             "inputs": n_inputs, "prepare_and_keygen_s": round(t_prep, 2), "keys": nkeys, "key_bytes": kbytes,
             "max_abs_logit_vs_fp64_chebyshev_relu": err_cheb,

@@ -12,23 +12,29 @@ architecture, seeded random-init weights, the FP64 forward pass that sets
 each ReLU's input bound beta (Alg. 4 leaves beta to an analysis of the data)
 and the level plan.
 
-Placement of bootstraps: before every ReLU but the first (the paper skips
-the first two; here the primes above the bootstrap's output level are the
-bootstrap's own, 50 to 60 bits against a 2^40 scale, so inputs are encrypted
-at that output level and only the first ReLU runs without a bootstrap).
-The convolution in front of a ReLU carries the ReLU's 1/beta in its weights,
-so its output -- the bootstrap's input -- lies in [-1, 1]; the identity
-shortcut of a block is scaled by 1/beta with one constant product on its own
-(shallower) path.  After a bootstrap the level is B = L - (bootstrap depth);
-the ReLU series takes 6 levels (fheon_cheb_depth(59)), a convolution one, the
-repacking two (in-block compaction, then block compaction), global pooling
-and FC one each: the deepest stretch between bootstraps -- series, the two
-repacks, the stage-3 stride-2 convolution -- needs B >= 10.
+Placement of bootstraps: before a ReLU exactly when the levels left would
+not carry its series and the layers up to the next ReLU's input with one
+level to spare (the paper bootstraps before every ReLU but the first two; a
+context with 16 levels of layers after a bootstrap needs one every other
+ReLU).  Inputs are encrypted at the bootstrap's output level, so the first
+ReLU runs without one.  The convolution in front of a ReLU carries the
+ReLU's 1/beta in its weights, so its output -- the bootstrap's input -- lies
+in [-1, 1]; the identity shortcut of a block is scaled by 1/beta with one
+constant product on its own (shallower) path.  After a bootstrap the level
+is B = L - (bootstrap depth); the ReLU series takes 6 levels
+(fheon_cheb_depth(59)), a convolution one, the repacking two (in-block
+compaction, then block compaction), global pooling and FC one each: the
+deepest stretch between bootstraps -- series, the stage-2 stride-2
+convolution, the two repacks -- needs B >= 10.
 
 Packing: channel c of a map in the block at c * block on a grid of row
 stride `grid`; stride-2 layers leave their outputs at dilated positions
-(fheon_map dil 2) and the maps of stage 2 are compacted once before stage 3
-so that its 64 channels fit the slots.
+(fheon_map dil 2).  Stage 2's map is compacted once, in its first block
+right after the strided convolutions (on the residual path and on the
+shortcut), so that every map from there on -- and stage 3's 64 channels --
+fits slots [0, N/4).  A bootstrap of such a map is the sparse one (one
+EvalMod instead of two); one whose input arrives at level 1 (the sparse
+bootstrap's mask needs a level) is the full one.
 """
 import numpy as np
 
@@ -161,13 +167,19 @@ class EncryptedResNet:
     x 1/beta') -> [bootstrap] -> series; the two repacks after stage 2; global
     pooling; FC.  The first ReLU runs without a bootstrap."""
 
-    def __init__(self, ctx, w, betas, scale, arch=FULL, boot_params=None):
+    def __init__(self, ctx, w, betas, scale, arch=FULL, boot_params=None, sparse=True):
         self.ctx, self.w, self.betas, self.scale, self.arch = ctx, w, list(betas), float(scale), arch
         self.L = ctx.L
-        self.boot = ctx.bootstrap_prepare(scale, boot_params)
+        self.nslots = ctx.N // 2
+        self.sparse = bool(sparse)
+        self._boots = {}
+        # the bootstrap of feature maps within slots [0, N/4) (sparse: one
+        # EvalMod), and the full one for maps beyond
+        self.boot = self._boot(self.nslots // 2 if self.sparse else 0, boot_params)
         self.B = ctx.bootstrap_info(self.boot)[0]
         if self.B < 10:
             raise ValueError("the bootstrap leaves level %d; the network needs 10" % self.B)
+        self._boot_params = boot_params
         self.mp = maps(arch)
         self.layers = {}
         self._series = {}
@@ -176,6 +188,20 @@ class EncryptedResNet:
         self._build()
 
     # -- preparation -------------------------------------------------------
+    def _boot(self, slots, params=None):
+        if slots not in self._boots:
+            p = None
+            if slots or params is not None:
+                p = params if params is not None else self.ctx.boot_params_default()
+                p = type(p).from_buffer_copy(p)
+                p.slots = slots
+            self._boots[slots] = self.ctx.bootstrap_prepare(self.scale, p)
+        return self._boots[slots]
+
+    def boot_layers(self):
+        """The bootstrap layers the plan uses."""
+        return list(self._boots.values())
+
     def _series_at(self, beta, level):
         key = (beta, level)
         if key not in self._series:
@@ -188,6 +214,16 @@ class EncryptedResNet:
         self.layers[name] = layer
         return layer, self.ctx.layer_out_map(layer)
 
+    def _compact(self, reg, m, lv, tag):
+        """Stage 2's strided map into its compact layout (rows and columns
+        within the blocks, then the blocks: two repack layers, two levels)."""
+        mp = self.mp
+        rp1 = self.ctx.repack_prepare(m, mp["s1_rows"], lv)
+        rp2 = self.ctx.repack_prepare(mp["s1_rows"], mp["s1_packed"], lv - 1)
+        self.layers["repack1" + tag], self.layers["repack2" + tag] = rp1, rp2
+        self.plan += [("layer", rp1, reg, reg), ("layer", rp2, reg, reg)]
+        return lv - 2
+
     def _build(self):
         # registers: x = the current feature map (a block's input and output),
         # h = the residual branch, s = the shortcut
@@ -197,40 +233,44 @@ class EncryptedResNet:
         m = mp["input"]
         conv, m = self._conv("conv0", m, lv, betas[r])
         self.plan.append(("layer", conv, "x", "h"))
-        lv = self._relu(r, lv - 1, "h", "x", after=1)
+        lv = self._relu(r, lv - 1, "h", "x", after=1, m=m)
         r += 1
         bl = blocks(self.arch)
         for bi, (s, b, ci, co, st) in enumerate(bl):
             name = "s%db%d" % (s, b)
-            # levels between this block's last ReLU and the next ReLU's input:
-            # the next conv (and the two repacks before stage 3), or pooling and FC
+            # stage 2's first block compacts its strided map (both paths)
+            # before its first ReLU: levels between this block's last ReLU and
+            # the next ReLU's input are the next conv (and those two repacks),
+            # or pooling and FC
+            compact = s == 1 and b == 0
             nxt = bl[bi + 1] if bi + 1 < len(bl) else None
-            after_last = 2 if nxt is None else (3 if (nxt[0] == 2 and nxt[1] == 0) else 1)
-            if s == 2 and b == 0:
-                # compact stage 2's map: rows/columns within the blocks, then the blocks
-                rp1 = ctx.repack_prepare(m, mp["s1_rows"], lv)
-                rp2 = ctx.repack_prepare(mp["s1_rows"], mp["s1_packed"], lv - 1)
-                self.layers["repack1"], self.layers["repack2"] = rp1, rp2
-                self.plan += [("layer", rp1, "x", "x"), ("layer", rp2, "x", "x")]
-                lv -= 2
-                m = mp["s1_packed"]
+            after_last = 2 if nxt is None else (3 if (nxt[0] == 1 and nxt[1] == 0) else 1)
             x_level, x_map = lv, m
             conv, ma = self._conv(name + "_a", m, lv, betas[r], stride=st)
             self.plan.append(("layer", conv, "x", "h"))
-            lv = self._relu(r, lv - 1, "h", "h", after=1)
+            lv -= 1
+            if compact:
+                lv = self._compact("h", ma, lv, "")
+                ma = mp["s1_packed"]
+            lv = self._relu(r, lv, "h", "h", after=1, m=ma)
             r += 1
             conv, mb = self._conv(name + "_b", ma, lv, betas[r])
             self.plan.append(("layer", conv, "h", "h"))
             lv -= 1
             if st == 2:
                 sc, msc = self._conv(name + "_sc", x_map, x_level, betas[r], stride=2, pad=0)
-                assert tuple(msc) == tuple(mb), (msc, mb)
                 self.plan.append(("layer", sc, "x", "s"))
+                sl = x_level - 1
+                if compact:
+                    sl = self._compact("s", msc, sl, "_sc")
+                    msc = mp["s1_packed"]
+                assert tuple(msc) == tuple(mb), (msc, mb)
             else:
                 self.plan.append(("scale", 1.0 / betas[r], "x", "s"))
-            lv = min(lv, x_level - 1)
+                sl = x_level - 1
+            lv = min(lv, sl)
             self.plan.append(("add", lv, "h", "s", "h"))
-            lv = self._relu(r, lv, "h", "x", after=after_last)
+            lv = self._relu(r, lv, "h", "x", after=after_last, m=mb)
             r += 1
             m = mb
         # global average pooling and FC
@@ -246,14 +286,18 @@ class EncryptedResNet:
         self.out_level = lv
         assert r == len(betas) == n_relus(self.arch)
 
-    def _relu(self, r, lv, src, dst, after):
+    def _relu(self, r, lv, src, dst, after, m):
         """The r-th ReLU of register src (at level lv, already scaled by
-        1/beta_r) into register dst; bootstrapped first when the levels left
-        would not carry the series and the `after` levels up to the next
-        ReLU's input with one level to spare.  Returns the level after it."""
+        1/beta_r, feature map m) into register dst; bootstrapped first when
+        the levels left would not carry the series and the `after` levels up
+        to the next ReLU's input with one level to spare.  A map within slots
+        [0, N/4) at level 2 or more (the input mask takes a level) takes the
+        sparse bootstrap, any other the full one.  Returns the level after it."""
         depth = F.cheb_depth(RELU_DEGREE)
         if lv - depth - after < 1:
-            self.plan.append(("boot", src))
+            C, H, W, grid, dil, block = m
+            fits = self.sparse and C * block <= self.nslots // 2 and lv >= 2
+            self.plan.append(("boot", src, self._boot(self.nslots // 2 if fits else 0, self._boot_params)))
             self.n_boot += 1
             lv = self.B
         self.plan.append(("layer", self._series_at(self.betas[r], lv), src, dst))
@@ -273,7 +317,7 @@ class EncryptedResNet:
             elif op[0] == "add":
                 out.append((F_.STEP_ADD, R[op[2]], R[op[3]], R[op[4]], op[1], None, 0.0))
             elif op[0] == "boot":
-                out.append((F_.STEP_LAYER, R[op[1]], 0, R[op[1]], 0, self.boot, 0.0))
+                out.append((F_.STEP_LAYER, R[op[1]], 0, R[op[1]], 0, op[2], 0.0))
         return out
 
     def model(self):
@@ -289,7 +333,8 @@ class EncryptedResNet:
     def keygen(self, sk):
         ctx = self.ctx
         ctx.relinkeygen(sk)
-        ctx.bootstrap_keygen(sk, self.boot)
+        for b in self.boot_layers():
+            ctx.bootstrap_keygen(sk, b)
         ctx.galois_keygen(sk, sorted({ctx.galois_elt(s) for s in self.rotation_steps()}))
 
     # -- inference ---------------------------------------------------------
@@ -309,7 +354,7 @@ class EncryptedResNet:
                 A, Bc = (ctx.drop_level(reg[k], lv) if ctx.ct_info(reg[k])[0] > lv else reg[k] for k in (a, b))
                 reg[dst] = ctx.add(A, Bc)
             elif kind == "boot":
-                reg[op[1]] = ctx.layer_apply(self.boot, reg[op[1]])
+                reg[op[1]] = ctx.layer_apply(op[2], reg[op[1]])
         return reg["x"]
 
     def forward_batch(self, cts):
@@ -336,7 +381,7 @@ class EncryptedResNet:
                     out.append(ctx.add(A, Bc))
                 reg[dst] = out
             elif kind == "boot":
-                reg[op[1]] = ctx.layer_apply_batch(self.boot, reg[op[1]])
+                reg[op[1]] = ctx.layer_apply_batch(op[2], reg[op[1]])
         return reg["x"]
 
     def forward_graph(self, ct):
@@ -366,6 +411,6 @@ class EncryptedResNet:
                 Bc = ctx.drop_level(reg[b], lv, out=bufs[3 * k + 2])
                 reg[dst] = ctx.add(A, Bc, out=out)
             elif kind == "boot":
-                reg[op[1]] = ctx.layer_apply_graph(self.boot, reg[op[1]], out)
+                reg[op[1]] = ctx.layer_apply_graph(op[2], reg[op[1]], out)
         y = reg["x"]
         return ctx.drop_level(y, ctx.ct_info(y)[0])

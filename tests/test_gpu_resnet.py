@@ -172,9 +172,11 @@ def test_mini_resnet_bit_exact_against_the_oracle():
     w = R.weights(0xD30, MINI)
     betas = R.relu_bounds([synth.image(0xD31, i, (3, 8, 8), dist="normal") for i in range(3)], w, MINI)
     plan = B.Plan(o, D)
+    splan = B.Plan(o, D, slots=N // 4)
     Bl = plan.out_level
+    assert splan.out_level == Bl
     depth = OF.cheb_depth(R.RELU_DEGREE)
-    steps = set(plan.steps())
+    steps = set(plan.steps()) | set(splan.steps())
     ops = []
 
     def shared(v, lv, scale):
@@ -207,45 +209,58 @@ def test_mini_resnet_bit_exact_against_the_oracle():
         linear(r, groups, lv, bias)
         return om
 
-    def relu(i, lv, after):
+    def relu(i, lv, after, m):
+        # a map within slots [0, N/4) at level >= 2 takes the sparse bootstrap
         if lv - depth - after < 1:
-            ops.append(("boot",))
+            C_, _, _, _, _, block_ = m
+            ops.append(("boot", C_ * block_ <= N // 4 and lv >= 2))
             lv = Bl
         ops.append(("series", OF.relu_cheb_coeffs(betas[i], R.RELU_DEGREE), lv))
         return lv - depth
 
     mp = R.maps(MINI)
+
+    def compact(src, lv):
+        # stage 2's strided map into its compact layout: two repack levels
+        for a, b in ((src, mp["s1_rows"]), (mp["s1_rows"], mp["s1_packed"])):
+            rr, gg = OF.repack_plan(*a[:3], a[3:], b[3:], n)
+            linear(rr, gg, lv)
+            lv -= 1
+        return lv
+
     lv, r_i = Bl, 0
     m = conv("conv0", mp["input"], lv, betas[0])
     ops.append(("mov", "h", "x"))
-    lv = relu(0, lv - 1, 1)
+    lv = relu(0, lv - 1, 1, m)
     r_i = 1
     bl = R.blocks(MINI)
     for bi, (s, b, ci, co, st) in enumerate(bl):
         name = "s%db%d" % (s, b)
         nxt = bl[bi + 1] if bi + 1 < len(bl) else None
-        after_last = 2 if nxt is None else (3 if (nxt[0] == 2 and nxt[1] == 0) else 1)
-        if s == 2 and b == 0:
-            for src, dst in ((m, mp["s1_rows"]), (mp["s1_rows"], mp["s1_packed"])):
-                rr, gg = OF.repack_plan(*src[:3], src[3:], dst[3:], n)
-                linear(rr, gg, lv)
-                lv -= 1
-            m = mp["s1_packed"]
+        after_last = 2 if nxt is None else (3 if (nxt[0] == 1 and nxt[1] == 0) else 1)
+        packs = s == 1 and b == 0   # stage 2's first block compacts both paths
         x_level, x_map = lv, m
         ops.append(("save_x",))
         ma = conv(name + "_a", m, lv, betas[r_i], stride=st)
-        lv = relu(r_i, lv - 1, 1)
+        lv -= 1
+        if packs:
+            lv = compact(ma, lv)
+            ma = mp["s1_packed"]
+        lv = relu(r_i, lv, 1, ma)
         r_i += 1
         mb = conv(name + "_b", ma, lv, betas[r_i])
         lv -= 1
+        sl = x_level - 1
         if st == 2:
             ops.append(("shortcut_conv",))
-            conv(name + "_sc", x_map, x_level, betas[r_i], stride=2, pad=0)
+            msc = conv(name + "_sc", x_map, x_level, betas[r_i], stride=2, pad=0)
+            if packs:
+                sl = compact(msc, sl)
         else:
             ops.append(("shortcut_scale", 1.0 / betas[r_i]))
-        lv = min(lv, x_level - 1)
+        lv = min(lv, sl)
         ops.append(("add", lv))
-        lv = relu(r_i, lv, after_last)
+        lv = relu(r_i, lv, after_last, mb)
         r_i += 1
         m = mb
     C, H, W_, grid, dil, block = m
@@ -266,19 +281,27 @@ def test_mini_resnet_bit_exact_against_the_oracle():
     g.relinkeygen(pr.sk)
     orlk = o.relinkey(pr.s_eval)
     okeys = {st: pr.okeys[g.galois_elt(st)] for st in steps}
-    bl_layers, bpts = [], []
-    for rr_, groups, ps, blv in plan.cts + plan.stc:
-        gp, op = [], []
-        for _, vals in groups:
-            row = [None if v is None else shared(v, blv, ps) for v in vals]
-            gp.append([x and x[0] for x in row])
-            op.append([x and x[1] for x in row])
-        layer = g.linear_prepare_plain(rr_, [G for G, _ in groups], gp, blv)
-        layer.keep = gp
-        bl_layers.append(layer)
-        bpts.append(op)
-    prm = pr.F.fheon_boot_params(len(plan.cts), len(plan.stc), plan.K, plan.D, plan.r, 0)
-    boot = g.bootstrap_compose(prm, bl_layers[:len(plan.cts)], bl_layers[len(plan.cts):], plan.coeffs, D)
+    boots = {}
+    for sparse, pl in ((False, plan), (True, splan)):
+        bl_layers, bpts = [], []
+        for rr_, groups, ps, blv in pl.cts + pl.stc:
+            gp, op = [], []
+            for _, vals in groups:
+                row = [None if v is None else shared(v, blv, ps) for v in vals]
+                gp.append([x and x[0] for x in row])
+                op.append([x and x[1] for x in row])
+            layer = g.linear_prepare_plain(rr_, [G for G, _ in groups], gp, blv)
+            layer.keep = gp
+            bl_layers.append(layer)
+            bpts.append(op)
+        prm = pr.F.fheon_boot_params(len(pl.cts), len(pl.stc), pl.K, pl.D, pl.r, 0, pl.ns if sparse else 0)
+        boot = g.bootstrap_compose(prm, bl_layers[:len(pl.cts)], bl_layers[len(pl.cts):], pl.coeffs, D)
+        omask = None
+        if sparse:
+            gm, omask = shared(pl.mask_slots(), 2, float(q[1]))
+            g.bootstrap_set_mask(boot, gm)
+        boots[sparse] = (boot, pl, bpts, omask)
+    assert any(op[0] == "boot" and op[1] for op in ops)
     # run both sides
     X = synth.image(0xD32, 0, (3, 8, 8), dist="normal")
     ct, oct_ = pr.encrypt_both(ckks.encode(R.pack_input(X, n, MINI), N, D), nonce=0xD32, level=Bl)
@@ -301,8 +324,9 @@ def test_mini_resnet_bit_exact_against_the_oracle():
             O["h"] = OF.cheb_encrypted(o, O[cur], sc, coeffs, orlk)
             cur = "h"
         elif kind == "boot":
+            boot, pl, bpts, omask = boots[op[1]]
             G[cur] = g.layer_apply(boot, G[cur])
-            O[cur], _ = B.bootstrap_encrypted(o, O[cur], plan, bpts, okeys, orlk, oconj)
+            O[cur], _ = B.bootstrap_encrypted(o, O[cur], pl, bpts, okeys, orlk, oconj, mask=omask)
         elif kind == "mov":
             G[op[2]], O[op[2]] = G[op[1]], O[op[1]]
         elif kind == "save_x":

@@ -44,12 +44,16 @@ class _Layer:
 class FakeCtx:
     """Levels and maps only: records every prepare call."""
     L = 32
+    N = 1 << 16
 
     def __init__(self):
         self.calls = []
 
     def bootstrap_prepare(self, scale, params=None):
-        return _Layer("boot", None)
+        return _Layer("boot", None, params.slots if params is not None else 0)
+
+    def boot_params_default(self):
+        return F.fheon_boot_params(3, 3, 512, 27, 9, 0, 0)
 
     def bootstrap_info(self, layer):
         return 11, 2.0 ** 40
@@ -95,7 +99,8 @@ def test_level_plan_full_size():
     # every bootstrap input and every layer sits at a level >= 1
     levels = [c[1] for c in net.ctx.calls]
     assert min(levels) >= 2
-    assert [c[0] for c in net.ctx.calls].count("repack") == 2
+    # stage 2's map compacted once, on the residual path and on the shortcut
+    assert [c[0] for c in net.ctx.calls].count("repack") == 4
     kinds = [op[0] for op in net.plan]
     assert kinds.count("boot") == 18 and kinds.count("add") == 9
 
@@ -109,6 +114,12 @@ def test_bootstraps_only_where_levels_run_out():
     net = R.EncryptedResNet(Deep(), R.weights(0xC3, R.FULL), [2.0] * R.n_relus(R.FULL), 2.0 ** 40)
     assert net.n_boot == 9 and net.out_level >= 1
     assert min(c[1] for c in net.ctx.calls) >= 2
+    # every bootstrap input within slots [0, N/4) at level >= 2 takes the
+    # sparse bootstrap: all of them but the one whose input is at level 1
+    slots = [op[2].out_map for op in net.plan if op[0] == "boot"]
+    assert slots.count(Deep.N // 4) == 8 and slots.count(0) == 1
+    full = R.EncryptedResNet(Deep(), R.weights(0xC3, R.FULL), [2.0] * R.n_relus(R.FULL), 2.0 ** 40, sparse=False)
+    assert full.n_boot == 9 and all(op[2].out_map == 0 for op in full.plan if op[0] == "boot")
 
 
 def test_reduced_network_plan():
@@ -118,5 +129,5 @@ def test_reduced_network_plan():
     assert net.n_boot == 6 and net.in_level == 11
     kinds = [op[0] for op in net.plan]
     assert kinds.count("add") == 3 and kinds.count("scale") == 1
-    assert [c[0] for c in net.ctx.calls].count("repack") == 2
+    assert [c[0] for c in net.ctx.calls].count("repack") == 4
     assert min(c[1] for c in net.ctx.calls) >= 2 and net.out_level >= 1
