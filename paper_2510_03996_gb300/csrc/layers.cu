@@ -249,13 +249,22 @@ int fheon_layer_apply_graph(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
 {
     if (!ctx || !ly || !in || !out) return FHEON_ERR_ARG;
     if (!ctx->stream) return fail(ctx, FHEON_ERR_ARG, "graph capture needs a created stream, not the legacy default stream");
-    for (auto &g : ly->graphs)
+    for (auto it = ly->graphs.begin(); it != ly->graphs.end(); ++it) {
+        auto &g = *it;
         if (g.in == in->c.p && g.out == out->c.p && g.ws == ctx->ws.p && g.level == in->level && g.scale == in->scale) {
+            if (out->cap < g.out_level) {
+                // the output buffer at this address is a newer, smaller
+                // allocation than the one captured: drop the entry, capture anew
+                cudaGraphExecDestroy(g.exec);
+                ly->graphs.erase(it);
+                break;
+            }
             FHEON_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
             out->level = g.out_level; // the host-side metadata the captured run set
             out->scale = g.out_scale;
             return FHEON_OK;
         }
+    }
     // eager run: sizes the output, the working ciphertexts and the workspace
     int rc = fheon_layer_apply(ctx, ly, in, out);
     if (rc) return rc;

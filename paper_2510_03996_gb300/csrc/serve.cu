@@ -119,6 +119,28 @@ void layer_cost(const fheon_ctx *ctx, const fheon_layer *ly, size_t *work, size_
 } // namespace
 
 namespace {
+// a request's buffers: its registers, a step's output and an operand copy;
+// `order` remembers the registers' first assignment (steps swap them), so a
+// set handed on to a later request starts from the same buffers
+struct RegSet {
+    std::vector<fheon_ct *> reg;
+    fheon_ct *nxt = nullptr, *aux = nullptr;
+    std::vector<fheon_ct *> order;
+    void restore()
+    {
+        for (size_t i = 0; i < reg.size(); i++) reg[i] = order[i];
+        nxt = order[reg.size()];
+    }
+    void destroy()
+    {
+        for (fheon_ct *c : order) fheon_ct_destroy(c);
+        fheon_ct_destroy(aux);
+        reg.clear();
+        order.clear();
+        nxt = aux = nullptr;
+    }
+};
+
 struct Request {
     uint64_t id = 0, seq = 0;
     const fheon_model *model = nullptr;
@@ -126,13 +148,21 @@ struct Request {
     u32 next = 0;                 // next step
     std::vector<fheon_ct *> reg;  // registers
     fheon_ct *nxt = nullptr, *aux = nullptr; // a step's output and an operand copy
+    std::vector<fheon_ct *> order; // the buffers' first assignment (reg then nxt)
     bool done = false;
     int status = FHEON_OK; // FHEON_ERR_TIMEOUT: dropped before admission
     std::chrono::steady_clock::time_point submitted;
+    RegSet take()
+    {
+        RegSet r{reg, nxt, aux, order};
+        reg.clear();
+        order.clear();
+        nxt = aux = nullptr;
+        return r;
+    }
     ~Request()
     {
-        for (fheon_ct *c : reg) fheon_ct_destroy(c);
-        fheon_ct_destroy(nxt);
+        for (fheon_ct *c : order) fheon_ct_destroy(c);
         fheon_ct_destroy(aux);
     }
 };
@@ -162,6 +192,17 @@ struct fheon_server {
     u32 max_batch = 0;
     std::map<const fheon_model *, u32> model_max_batch;
     double admit_timeout = 0; // seconds a request may wait for admission; 0: no limit
+    // graph replay: a layer step of one request runs as the layer's captured
+    // graph on that request's buffers, which go back to a per-model pool when
+    // the result is taken, so the next request of the model replays them
+    bool graphs = false;
+    std::map<const fheon_model *, std::vector<RegSet>> pool;
+    uint64_t replays = 0;
+    ~fheon_server()
+    {
+        for (auto &kv : pool)
+            for (RegSet &r : kv.second) r.destroy();
+    }
 };
 
 namespace {
@@ -247,9 +288,12 @@ int fheon_model_run(fheon_ctx *ctx, const fheon_model *m, const fheon_ct *in, fh
     r.model = m;
     r.reg.assign(m->nreg, nullptr);
     int rc;
-    for (fheon_ct *&c : r.reg)
+    for (fheon_ct *&c : r.reg) {
         if ((rc = fheon_ct_create(ctx, in->level, in->scale, &c))) return rc;
+        r.order.push_back(c);
+    }
     if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r.nxt))) return rc;
+    r.order.push_back(r.nxt);
     if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r.aux))) return rc;
     if ((rc = fheon_drop_level(ctx, in, in->level, r.reg[0]))) return rc;
     for (const fheon_step &st : m->steps) {
@@ -322,11 +366,24 @@ int fheon_server_submit(fheon_server *s, const fheon_model *m, const fheon_ct *i
     std::unique_ptr<Request> r(new Request());
     int rc;
     if ((rc = fheon_model_footprint(m, in->level, &r->footprint))) return rc;
-    r->reg.assign(m->nreg, nullptr);
-    for (fheon_ct *&c : r->reg)
-        if ((rc = fheon_ct_create(ctx, in->level, in->scale, &c))) return rc;
-    if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r->nxt))) return rc;
-    if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r->aux))) return rc;
+    auto pit = s->pool.find(m);
+    if (s->graphs && pit != s->pool.end() && !pit->second.empty()) {
+        RegSet set = pit->second.back();
+        pit->second.pop_back();
+        r->reg = set.reg;
+        r->nxt = set.nxt;
+        r->aux = set.aux;
+        r->order = set.order;
+    } else {
+        r->reg.assign(m->nreg, nullptr);
+        for (fheon_ct *&c : r->reg) {
+            if ((rc = fheon_ct_create(ctx, in->level, in->scale, &c))) return rc;
+            r->order.push_back(c);
+        }
+        if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r->nxt))) return rc;
+        r->order.push_back(r->nxt);
+        if ((rc = fheon_ct_create(ctx, in->level, in->scale, &r->aux))) return rc;
+    }
     if ((rc = fheon_drop_level(ctx, in, in->level, r->reg[0]))) return rc; // the request's own copy
     r->id = s->next_id++;
     r->model = m;
@@ -362,7 +419,10 @@ int fheon_server_step(fheon_server *s, uint32_t *n_done)
             if (r->model == m && r->next == stage) batch.push_back(r);
         fheon_ctx *ctx = kv.first;
         const fheon_step &st = m->steps[stage];
-        if (st.op == FHEON_STEP_LAYER) {
+        if (st.op == FHEON_STEP_LAYER && s->graphs && batch.size() == 1) {
+            rc = fheon_layer_apply_graph(ctx, st.layer, batch[0]->reg[st.src], batch[0]->nxt);
+            s->replays++;
+        } else if (st.op == FHEON_STEP_LAYER) {
             std::vector<const fheon_ct *> ins;
             std::vector<fheon_ct *> outs;
             for (Request *r : batch) {
@@ -421,7 +481,36 @@ int fheon_server_result(fheon_server *s, uint64_t id, fheon_ct *out)
     int rc = fheon_drop_level(ctx, r, r->level, out);
     if (rc) return rc;
     if ((rc = fheon_sync(ctx))) return rc;
+    if (s->graphs) {
+        // the buffers serve the model's next request (its graphs replay on them)
+        RegSet set = it->second->take();
+        set.restore();
+        s->pool[it->second->model].push_back(set);
+    }
     s->all.erase(it);
+    return FHEON_OK;
+}
+
+int fheon_server_set_graphs(fheon_server *s, int on)
+{
+    if (!s) return FHEON_ERR_ARG;
+    std::set<fheon_ctx *> ctxs{s->ctx};
+    for (auto &kv : s->all) ctxs.insert(kv.second->model->ctx);
+    for (fheon_ctx *c : ctxs)
+        if (on && c && !c->stream)
+            return fail(s->ctx, FHEON_ERR_ARG, "graph replay needs created streams, not the legacy default stream");
+    if (!on)
+        for (auto &kv : s->pool)
+            for (RegSet &r : kv.second) r.destroy();
+    if (!on) s->pool.clear();
+    s->graphs = on != 0;
+    return FHEON_OK;
+}
+
+int fheon_server_graph_replays(const fheon_server *s, uint64_t *replays)
+{
+    if (!s || !replays) return FHEON_ERR_ARG;
+    *replays = s->replays;
     return FHEON_OK;
 }
 

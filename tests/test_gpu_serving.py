@@ -148,3 +148,43 @@ def test_one_server_two_contexts_memory_admission(setup):
     srv.close()
     g2.sync()
     g2.set_stream(torch.cuda.current_stream().cuda_stream)
+
+
+def test_server_graph_replay_bit_exact(setup):
+    """With graph replay on, a request stepping alone runs each layer as a
+    captured CUDA graph on its own buffers; finished requests hand their
+    buffers to the model's next request, whose steps then replay those
+    graphs.  Every result is the model's on its input alone, bit for bit;
+    a context on the legacy default stream is refused."""
+    import torch
+    pr, layers, cts, alone = setup
+    g = pr.g
+    model = g.model(layers)
+    srv = g.server(max_active=1)
+    srv.submit(model, cts[0])
+    with pytest.raises(pr.F.FheonError) as e:   # the context runs on the legacy default stream
+        srv.set_graphs(True)
+    assert e.value.code == -1
+    srv.close()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g.set_stream(stream.cuda_stream)
+    try:
+        srv = g.server(max_active=1)
+        srv.set_graphs(True)
+        for rnd in range(2):                      # the second round reuses the pooled buffers
+            for k in range(len(cts)):
+                rid = srv.submit(model, cts[k])
+                out = None
+                for _ in range(50):
+                    srv.step()
+                    out = srv.result(rid)
+                    if out is not None:
+                        break
+                assert out is not None
+                assert gpu_common.mismatch(g.ct_download(out), alone[k]) == 0, (rnd, k)
+        assert srv.graph_replays() == 2 * len(cts) * len(layers)
+        srv.close()
+    finally:
+        g.sync()
+        g.set_stream(torch.cuda.current_stream().cuda_stream)
