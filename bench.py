@@ -497,14 +497,15 @@ def resnet_timing(F, n_inputs=2):
     # network mostly uses, and the full one
     z = ctx.drop_level(cts[0], 2)
     boot_ms_by = {}
-    for slots, layer in sorted(net._boots.items()):
+    for (slots, unmasked), layer in sorted(net._boots.items()):
         ctx.layer_apply(layer, z)
         e0.record(s)
         for _ in range(5):
             ctx.layer_apply(layer, z)
         e1.record(s)
         torch.cuda.synchronize()
-        boot_ms_by["sparse_%d_slots" % slots if slots else "full"] = e0.elapsed_time(e1) / 5
+        name = ("sparse_%d_slots" % slots + ("_unmasked" if unmasked else "")) if slots else "full"
+        boot_ms_by[name] = e0.elapsed_time(e1) / 5
     boot_ms = boot_ms_by.get("sparse_%d_slots" % (N // 4), boot_ms_by.get("full"))
     # one bootstrap launch by launch (events on the context's stream): share of each kernel
     ctx.profile_begin()
@@ -574,7 +575,7 @@ def resnet_timing(F, n_inputs=2):
         agree += int(np.argmax(got) == np.argmax(want))
     nkeys, kbytes = ctx.key_stats()
     n_boot = net.n_boot
-    n_sparse = sum(1 for op in net.plan if op[0] == "boot" and op[2] is not net._boots.get(0))
+    n_sparse = sum(1 for op in net.plan if op[0] == "boot" and op[2] is not net._boots.get((0, False)))
     del outs, gouts, cts, net, sk, pk
     release(ctx)
     return {"s_per_inference": secs / n_inputs, "eager_s_per_inference": eager_secs / n_inputs,
@@ -595,8 +596,10 @@ def serving_timing(F, n_req=200, rate=4.0, max_active=12, frac_resnet=0.3):
     s from a seed), each request LeNet-5 (N = 2^15) or, with probability
     frac_resnet, ResNet-20 with bootstrapping (N = 2^16), both models on one
     continuous-batching server (fheon_server_*: each context on its own
-    stream, their batches overlapping on the device; the ResNet model is a
-    program of layer, bootstrap, add and constant steps over three registers).
+    stream, their batches overlapping on the device, a layer step of one
+    request alone replayed as a CUDA graph on pooled request buffers; the
+    ResNet model is a program of layer, bootstrap, add and constant steps
+    over three registers).
     Admission by memory: the budget holds the footprints of 8 LeNet-5 and 3
     ResNet-20 requests (fheon_model_footprint).  Requests are submitted when
     their arrival time has passed (host clock); latency = completion -
@@ -647,6 +650,7 @@ def serving_timing(F, n_req=200, rate=4.0, max_active=12, frac_resnet=0.3):
     avail = free_b + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
     budget = int(min(8 * fp[0] + 3 * fp[1], 0.8 * avail))
     srv = c1.server(max_active=max_active, mem_budget=budget)
+    srv.set_graphs(True)  # single-request layer steps replay captured graphs on pooled buffers
     c1.sync()
     c2.sync()
     t0 = time.perf_counter()
@@ -676,7 +680,8 @@ def serving_timing(F, n_req=200, rate=4.0, max_active=12, frac_resnet=0.3):
            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "max_active": max_active,
            "mem_budget_bytes": budget, "device_bytes_available": avail,
            "footprint_bytes": {"lenet5": fp[0], "resnet20": fp[1]},
-           "mem_waits": srv.model_stats(m1)["mem_waits"], "steps": srv.stats()["steps"]}
+           "mem_waits": srv.model_stats(m1)["mem_waits"], "steps": srv.stats()["steps"],
+           "graph_replayed_layer_steps": srv.graph_replays()}
     for which, name, m in ((0, "lenet5", m1), (1, "resnet20", m2)):
         sel = np.array([owner[k] == which for k in range(n_req)])
         if sel.any():

@@ -583,6 +583,9 @@ typedef struct fheon_boot_params {
     uint32_t baby;       /* baby steps of every BSGS level (0: fewest rotations) */
     uint32_t slots;      /* 0 or N/2: every slot; a power of two in [2, N/4]: the
                           * sparse bootstrap of slots [0, slots) (below) */
+    uint32_t unmasked;   /* sparse only, 1: inputs are zero outside slots
+                          * [0, slots) (a convolution's output, say), so the
+                          * mask is left out and inputs at level 1 are taken */
 } fheon_boot_params;
 /* Defaults for a context: 3 + 3 levels, K the power of two at or above
  * 8 sqrt(N / 18) (eight standard deviations of t / q_0 for a uniform ternary
@@ -750,6 +753,20 @@ int fheon_server_result(fheon_server *server, uint64_t id, fheon_ct *out);
  * *n_done; its result then reports FHEON_ERR_TIMEOUT.  0 (the default): no
  * limit.  FHEON_ERR_ARG for a negative, infinite or NaN value. */
 int fheon_server_set_admit_timeout(fheon_server *server, double seconds);
+/* Graph replay (on = 1): a layer step the scheduler runs for one request
+ * alone runs as the layer's captured CUDA graph (fheon_layer_apply_graph) on
+ * that request's buffers.  A request's buffers go back to a pool of its model
+ * when its result is taken, and the model's next request takes them, so its
+ * steps replay the graphs captured before (launch gaps between a layer's
+ * kernels disappear).  Pooled buffers are outside the memory budget.  Every
+ * context of the server's models must run on a created stream, not the
+ * legacy default stream: FHEON_ERR_ARG here for the contexts of requests
+ * already submitted, and from fheon_server_step otherwise.  Off (the
+ * default) frees the pool.  Results are the same bits either way. */
+int fheon_server_set_graphs(fheon_server *server, int on);
+/* Layer steps that ran as graph replays (their first run, which captures,
+ * included). */
+int fheon_server_graph_replays(const fheon_server *server, uint64_t *replays);
 /* Steps taken, the largest batch so far, requests in flight and waiting. */
 int fheon_server_stats(const fheon_server *server, uint64_t *steps, uint32_t *max_batch, uint32_t *active,
                        uint32_t *waiting);

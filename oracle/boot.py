@@ -270,15 +270,18 @@ class Plan:
     is small against the message.  The output then has scale ~= Delta_in and
     the input's message."""
 
-    def __init__(self, ctx, in_scale, cts=3, stc=3, K=None, r=None, D=BOOT_DEGREE, baby=0, slots=None):
+    def __init__(self, ctx, in_scale, cts=3, stc=3, K=None, r=None, D=BOOT_DEGREE, baby=0, slots=None,
+                 masked=True):
         N, L = ctx.N, ctx.L
         n = N // 2
         ns = n if not slots else int(slots)
         if ns > n or ns < 2 or ns & (ns - 1):
             raise ValueError("slots: a power of two in [2, N/2]")
         self.N, self.n, self.in_scale = N, n, float(in_scale)
-        # sparse (ns < N/2): the message lives in slots [0, ns); copies = n / ns
+        # sparse (ns < N/2): the message lives in slots [0, ns); copies = n / ns;
+        # unmasked (masked=False): the inputs are zero outside those slots
         self.ns, self.copies = ns, n // ns
+        self.masked = bool(masked) or ns == n
         self.K = K or default_K(N)
         self.r = default_doublings(self.K) if r is None else r
         self.D, self.ncts, self.nstc = D, cts, stc
@@ -388,7 +391,8 @@ def bootstrap_encrypted(ctx, ct, plan, pts, keys, rlk, conj_key, trace=None, mas
     trace (optional dict) receives the intermediate ciphertexts.
 
     Sparse plans (plan.ns < N/2; the input at level >= 2, mask =
-    plan.encode_mask(ctx)) take the message of slots [0, ns) only and
+    plan.encode_mask(ctx); unmasked plans: inputs zero outside slots [0, ns),
+    at level >= 1, no mask) take the message of slots [0, ns) only and
     return it in every copy of ns slots: the input is masked to those slots
     and repeated in every copy (so its polynomial lies in Z[X^copies]);
     after ModRaise the trace (the sum of the copies' rotations) removes the
@@ -400,8 +404,12 @@ def bootstrap_encrypted(ctx, ct, plan, pts, keys, rlk, conj_key, trace=None, mas
     sparse = plan.ns < plan.n
     if sparse:
         # slots [0, ns) kept, repeated in every copy: the message then lies in
-        # the subring the trace below projects onto
-        x = ctx.rescale(ctx.mul_plain(ctx.drop_level(ct, 2), mask))
+        # the subring the trace below projects onto (an unmasked plan's inputs
+        # are zero outside those slots already)
+        if plan.masked:
+            x = ctx.rescale(ctx.mul_plain(ctx.drop_level(ct, 2), mask))
+        else:
+            x = ctx.drop_level(ct, 1)
         for st in plan.trace_steps():
             x = ctx.add(x, ctx.rotate(x, ckks.galois_elt(st, N), keys[st]))
         if trace is not None:

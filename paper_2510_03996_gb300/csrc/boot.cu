@@ -206,6 +206,8 @@ int check_params(fheon_ctx *ctx, const fheon_boot_params *p)
     const u32 ns = boot_slots(ctx, *p);
     if (ns < 2 || ns > ctx->N / 2 || (ns & (ns - 1)))
         return fail(ctx, FHEON_ERR_ARG, "bootstrap: slots 0 or a power of two in [2, N/2]");
+    if (p->unmasked > 1 || (p->unmasked && ns == ctx->N / 2))
+        return fail(ctx, FHEON_ERR_ARG, "bootstrap: unmasked is 0 or 1, and 1 only with slots < N/2");
     u32 logn = 0;
     while ((1u << logn) < ns) logn++;
     if (!p->cts_levels || !p->stc_levels || p->cts_levels > logn || p->stc_levels > logn || !p->K ||
@@ -388,8 +390,10 @@ static int boot_sparse_many(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
 {
     const u32 N = ctx->N, D = (u32)ly->coeffs.size() - 1, ns = ly->boot_ns;
     int rc;
+    const u32 min_level = ly->boot_unmasked ? 1 : 2;
     for (u32 p = 0; p < n; p++) {
-        if (ins[p]->level < 2) return fail(ctx, FHEON_ERR_LEVEL, "sparse bootstrap: input at level %u, needs >= 2", ins[p]->level);
+        if (ins[p]->level < min_level)
+            return fail(ctx, FHEON_ERR_LEVEL, "sparse bootstrap: input at level %u, needs >= %u", ins[p]->level, min_level);
         if (std::fabs(ins[p]->scale - ly->in_scale) > 1e-9 * ly->in_scale)
             return fail(ctx, FHEON_ERR_SCALE, "bootstrap prepared for scale %g, got %g", ly->in_scale, ins[p]->scale);
     }
@@ -407,9 +411,13 @@ static int boot_sparse_many(fheon_ctx *ctx, const fheon_layer *ly, const fheon_c
     auto W = [&](u32 p, u32 i) { return ly->bsets[p].w[i]; };
     std::vector<fheon_ct *> xs(n), tmp(n), dsts(n);
     for (u32 p = 0; p < n; p++) {
-        if ((rc = fheon_drop_level(ctx, ins[p], 2, W(p, 7)))) return rc;
-        if ((rc = fheon_mul_plain(ctx, W(p, 7), ly->boot_mask, W(p, 4)))) return rc;
-        if ((rc = fheon_rescale(ctx, W(p, 4), W(p, 4)))) return rc;
+        if (ly->boot_unmasked) {
+            if ((rc = fheon_drop_level(ctx, ins[p], 1, W(p, 4)))) return rc;
+        } else {
+            if ((rc = fheon_drop_level(ctx, ins[p], 2, W(p, 7)))) return rc;
+            if ((rc = fheon_mul_plain(ctx, W(p, 7), ly->boot_mask, W(p, 4)))) return rc;
+            if ((rc = fheon_rescale(ctx, W(p, 4), W(p, 4)))) return rc;
+        }
         xs[p] = W(p, 4);
         tmp[p] = W(p, 3);
     }
@@ -690,6 +698,7 @@ int fheon_boot_params_default(const fheon_ctx *ctx, fheon_boot_params *p)
     p->degree = 27;
     p->baby = 0;
     p->slots = 0;
+    p->unmasked = 0;
     return FHEON_OK;
 }
 
@@ -739,6 +748,13 @@ int fheon_bootstrap_compose(fheon_ctx *ctx, const fheon_boot_params *p, const fh
     ly->in_scale = in_scale;
     ly->out_level = lv;
     const u32 n = ctx->N / 2, ns = boot_slots(ctx, *p);
+    if (ns < n && p->unmasked) {
+        ly->boot_ns = ns;
+        ly->nslots = n;
+        ly->boot_unmasked = true;
+        *out = ly.release();
+        return FHEON_OK;
+    }
     if (ns < n) {
         // the input mask: 1 in slots [0, n_s), at level 2 and scale q_1, the
         // prime its rescale drops
@@ -846,7 +862,7 @@ int fheon_bootstrap_prepare(fheon_ctx *ctx, const fheon_boot_params *p_, double 
 int fheon_bootstrap_set_mask(fheon_ctx *ctx, fheon_layer *ly, const fheon_pt *mask)
 {
     if (!ctx || !ly || !mask || ly->kind != LAYER_BOOT) return FHEON_ERR_ARG;
-    if (!ly->boot_ns) return fail(ctx, FHEON_ERR_ARG, "set_mask: not a sparse bootstrap");
+    if (!ly->boot_ns || ly->boot_unmasked) return fail(ctx, FHEON_ERR_ARG, "set_mask: not a masked sparse bootstrap");
     if (mask->level < 2) return fail(ctx, FHEON_ERR_ARG, "set_mask: the mask must be at level >= 2");
     if (ly->own_boot_mask) fheon_pt_destroy(const_cast<fheon_pt *>(ly->boot_mask));
     ly->boot_mask = mask;

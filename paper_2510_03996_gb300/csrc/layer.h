@@ -48,6 +48,7 @@ struct fheon_layer {
     // sparse bootstrap: the message slots n_s (0: every slot) and the input
     // mask of slots [0, n_s) at level 2, scale q_1 (owned unless set by the caller)
     u32 boot_ns = 0;
+    bool boot_unmasked = false; // inputs zero outside [0, n_s): no mask, level 1 taken
     const fheon_pt *boot_mask = nullptr;
     bool own_boot_mask = false;
     mutable std::vector<fheon_ct *> cheb2; // the second part's series working set

@@ -54,10 +54,11 @@ STEP_LAYER, STEP_ADD, STEP_SCALE = 0, 1, 2
 class fheon_boot_params(ctypes.Structure):
     """Bootstrapping: CoeffToSlot / SlotToCoeff levels, EvalMod's range K,
     series degree and double-angle steps, BSGS baby steps (0: fewest rotations),
-    message slots (0: all N/2; fewer: the sparse bootstrap)."""
+    message slots (0: all N/2; fewer: the sparse bootstrap), and whether a
+    sparse bootstrap's inputs are known to be zero outside those slots (no mask)."""
     _fields_ = [("cts_levels", ctypes.c_uint32), ("stc_levels", ctypes.c_uint32), ("K", ctypes.c_uint32),
                 ("degree", ctypes.c_uint32), ("doublings", ctypes.c_uint32), ("baby", ctypes.c_uint32),
-                ("slots", ctypes.c_uint32)]
+                ("slots", ctypes.c_uint32), ("unmasked", ctypes.c_uint32)]
 
 
 # name -> argument types (all return int unless listed in _RESTYPE)
@@ -169,6 +170,8 @@ SIGNATURES = {
     "fheon_server_step": [c_vp, P(c_u32)],
     "fheon_server_result": [c_vp, c_u64, c_vp],
     "fheon_server_set_admit_timeout": [c_vp, c_dbl],
+    "fheon_server_set_graphs": [c_vp, c_int],
+    "fheon_server_graph_replays": [c_vp, P(c_u64)],
     "fheon_server_stats": [c_vp, P(c_u64), P(c_u32), P(c_u32), P(c_u32)],
     "fheon_layer_rotation_steps": [c_vp, P(c_i32), P(c_u32)],
     "fheon_layer_out_map": [c_vp, P(fheon_map)],
@@ -1106,6 +1109,15 @@ class Server:
 
     def set_admit_timeout(self, seconds):
         self.ctx._chk(load().fheon_server_set_admit_timeout(self.handle.h, float(seconds)))
+
+    def set_graphs(self, on=True):
+        """Single-request layer steps as replayed CUDA graphs on pooled buffers."""
+        self.ctx._chk(load().fheon_server_set_graphs(self.handle.h, 1 if on else 0))
+
+    def graph_replays(self):
+        n = c_u64()
+        check(load().fheon_server_graph_replays(self.handle.h, ctypes.byref(n)))
+        return n.value
 
     def stats(self):
         st, mb, a, w = c_u64(), c_u32(), c_u32(), c_u32()

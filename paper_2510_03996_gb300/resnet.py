@@ -188,15 +188,17 @@ class EncryptedResNet:
         self._build()
 
     # -- preparation -------------------------------------------------------
-    def _boot(self, slots, params=None):
-        if slots not in self._boots:
+    def _boot(self, slots, params=None, unmasked=False):
+        key = (slots, bool(unmasked))
+        if key not in self._boots:
             p = None
             if slots or params is not None:
                 p = params if params is not None else self.ctx.boot_params_default()
                 p = type(p).from_buffer_copy(p)
                 p.slots = slots
-            self._boots[slots] = self.ctx.bootstrap_prepare(self.scale, p)
-        return self._boots[slots]
+                p.unmasked = 1 if unmasked else 0
+            self._boots[key] = self.ctx.bootstrap_prepare(self.scale, p)
+        return self._boots[key]
 
     def boot_layers(self):
         """The bootstrap layers the plan uses."""
@@ -233,7 +235,7 @@ class EncryptedResNet:
         m = mp["input"]
         conv, m = self._conv("conv0", m, lv, betas[r])
         self.plan.append(("layer", conv, "x", "h"))
-        lv = self._relu(r, lv - 1, "h", "x", after=1, m=m)
+        lv = self._relu(r, lv - 1, "h", "x", after=1, m=m, clean=True)
         r += 1
         bl = blocks(self.arch)
         for bi, (s, b, ci, co, st) in enumerate(bl):
@@ -252,7 +254,7 @@ class EncryptedResNet:
             if compact:
                 lv = self._compact("h", ma, lv, "")
                 ma = mp["s1_packed"]
-            lv = self._relu(r, lv, "h", "h", after=1, m=ma)
+            lv = self._relu(r, lv, "h", "h", after=1, m=ma, clean=True)
             r += 1
             conv, mb = self._conv(name + "_b", ma, lv, betas[r])
             self.plan.append(("layer", conv, "h", "h"))
@@ -270,7 +272,9 @@ class EncryptedResNet:
                 sl = x_level - 1
             lv = min(lv, sl)
             self.plan.append(("add", lv, "h", "s", "h"))
-            lv = self._relu(r, lv, "h", "x", after=after_last, m=mb)
+            # a convolution's output is zero outside its map; an identity
+            # shortcut carries the previous ReLU's values there
+            lv = self._relu(r, lv, "h", "x", after=after_last, m=mb, clean=st == 2)
             r += 1
             m = mb
         # global average pooling and FC
@@ -286,18 +290,21 @@ class EncryptedResNet:
         self.out_level = lv
         assert r == len(betas) == n_relus(self.arch)
 
-    def _relu(self, r, lv, src, dst, after, m):
+    def _relu(self, r, lv, src, dst, after, m, clean=False):
         """The r-th ReLU of register src (at level lv, already scaled by
-        1/beta_r, feature map m) into register dst; bootstrapped first when
-        the levels left would not carry the series and the `after` levels up
-        to the next ReLU's input with one level to spare.  A map within slots
-        [0, N/4) at level 2 or more (the input mask takes a level) takes the
-        sparse bootstrap, any other the full one.  Returns the level after it."""
+        1/beta_r, feature map m; `clean`: zero outside the map) into register
+        dst; bootstrapped first when the levels left would not carry the
+        series and the `after` levels up to the next ReLU's input with one
+        level to spare.  A map within slots [0, N/4) takes the sparse
+        bootstrap: unmasked when the input is clean, masked when it is at
+        level 2 or more (the mask takes a level); any other the full one.
+        Returns the level after it."""
         depth = F.cheb_depth(RELU_DEGREE)
         if lv - depth - after < 1:
             C, H, W, grid, dil, block = m
-            fits = self.sparse and C * block <= self.nslots // 2 and lv >= 2
-            self.plan.append(("boot", src, self._boot(self.nslots // 2 if fits else 0, self._boot_params)))
+            fits = self.sparse and C * block <= self.nslots // 2 and (clean or lv >= 2)
+            layer = self._boot(self.nslots // 2 if fits else 0, self._boot_params, unmasked=fits and clean)
+            self.plan.append(("boot", src, layer))
             self.n_boot += 1
             lv = self.B
         self.plan.append(("layer", self._series_at(self.betas[r], lv), src, dst))

@@ -78,7 +78,7 @@ def _composed(pr, plan=None):
         gl.append(layer)
         opts.append(op)
     prm = pr.F.fheon_boot_params(len(plan.cts), len(plan.stc), plan.K, plan.D, plan.r, 0,
-                                 0 if plan.ns == plan.n else plan.ns)
+                                 0 if plan.ns == plan.n else plan.ns, 0 if plan.masked else 1)
     return g.bootstrap_compose(prm, gl[:len(plan.cts)], gl[len(plan.cts):], plan.coeffs, pr.P["scale"]), opts
 
 
@@ -228,6 +228,35 @@ def test_sparse_bootstrap_prepared_by_the_library(sparse):
         g.layer_apply(layer, ct1)
     assert e.value.code == -4
     p.slots = 3
+    with pytest.raises(F.FheonError) as e:
+        g.bootstrap_prepare(sparse.P["scale"], p)
+    assert e.value.code == -1
+
+
+def test_sparse_unmasked_bootstrap(sparse):
+    """The unmasked sparse bootstrap (inputs zero outside slots [0, N/4), no
+    mask, level 1 taken): composed from the oracle's plaintexts, bit-exact
+    against the oracle; prepared by the library, the input's slots back in
+    both copies within 1e-4."""
+    g, o, F = sparse.g, sparse.o, sparse.F
+    plan = B.Plan(o, sparse.P["scale"], slots=sparse.N // 4, masked=False)
+    layer, opts = _composed(sparse, plan)
+    with pytest.raises(F.FheonError):               # no mask to replace
+        g.bootstrap_set_mask(layer, g.plain_from_coeffs(np.zeros(sparse.N, dtype=np.int64), 2))
+    ns = plan.ns
+    z = synth.uniform_slots(0xB205, 0, sparse.N // 2)
+    z[ns:] = 0.0
+    ct, oct_ = sparse.encrypt_both(ckks.encode(z, sparse.N, sparse.P["scale"]), nonce=0xB205, level=1)
+    okeys = {st: sparse.okeys[g.galois_elt(st)] for st in plan.steps()}
+    y = g.layer_apply(layer, ct)
+    want, osc = B.bootstrap_encrypted(o, oct_, plan, opts, okeys, sparse.orlk, sparse.oconj)
+    assert gpu_common.mismatch(g.ct_download(y), want) == 0
+    p = g.boot_params_default()
+    p.slots, p.unmasked = ns, 1
+    lib = g.bootstrap_prepare(sparse.P["scale"], p)
+    got = np.asarray(g.decode(g.decrypt(sparse.sk, g.layer_apply(lib, ct)))).real
+    assert np.max(np.abs(got - np.tile(z[:ns], 2))) < 1e-4
+    p.slots = 0                                     # unmasked needs a sparse bootstrap
     with pytest.raises(F.FheonError) as e:
         g.bootstrap_prepare(sparse.P["scale"], p)
     assert e.value.code == -1

@@ -171,12 +171,14 @@ def test_mini_resnet_bit_exact_against_the_oracle():
     q = [int(x) for x in g.moduli]
     w = R.weights(0xD30, MINI)
     betas = R.relu_bounds([synth.image(0xD31, i, (3, 8, 8), dist="normal") for i in range(3)], w, MINI)
-    plan = B.Plan(o, D)
-    splan = B.Plan(o, D, slots=N // 4)
-    Bl = plan.out_level
-    assert splan.out_level == Bl
+    plans = {"full": B.Plan(o, D), "masked": B.Plan(o, D, slots=N // 4),
+             "unmasked": B.Plan(o, D, slots=N // 4, masked=False)}
+    Bl = plans["full"].out_level
+    assert all(p_.out_level == Bl for p_ in plans.values())
     depth = OF.cheb_depth(R.RELU_DEGREE)
-    steps = set(plan.steps()) | set(splan.steps())
+    steps = set()
+    for p_ in plans.values():
+        steps |= set(p_.steps())
     ops = []
 
     def shared(v, lv, scale):
@@ -209,11 +211,13 @@ def test_mini_resnet_bit_exact_against_the_oracle():
         linear(r, groups, lv, bias)
         return om
 
-    def relu(i, lv, after, m):
-        # a map within slots [0, N/4) at level >= 2 takes the sparse bootstrap
+    def relu(i, lv, after, m, clean):
+        # a map within slots [0, N/4) takes the sparse bootstrap: unmasked on
+        # a convolution's output (zero outside its map), masked at level >= 2
         if lv - depth - after < 1:
             C_, _, _, _, _, block_ = m
-            ops.append(("boot", C_ * block_ <= N // 4 and lv >= 2))
+            fits = C_ * block_ <= N // 4
+            ops.append(("boot", "unmasked" if fits and clean else ("masked" if fits and lv >= 2 else "full")))
             lv = Bl
         ops.append(("series", OF.relu_cheb_coeffs(betas[i], R.RELU_DEGREE), lv))
         return lv - depth
@@ -231,7 +235,7 @@ def test_mini_resnet_bit_exact_against_the_oracle():
     lv, r_i = Bl, 0
     m = conv("conv0", mp["input"], lv, betas[0])
     ops.append(("mov", "h", "x"))
-    lv = relu(0, lv - 1, 1, m)
+    lv = relu(0, lv - 1, 1, m, True)
     r_i = 1
     bl = R.blocks(MINI)
     for bi, (s, b, ci, co, st) in enumerate(bl):
@@ -246,7 +250,7 @@ def test_mini_resnet_bit_exact_against_the_oracle():
         if packs:
             lv = compact(ma, lv)
             ma = mp["s1_packed"]
-        lv = relu(r_i, lv, 1, ma)
+        lv = relu(r_i, lv, 1, ma, True)
         r_i += 1
         mb = conv(name + "_b", ma, lv, betas[r_i])
         lv -= 1
@@ -260,7 +264,7 @@ def test_mini_resnet_bit_exact_against_the_oracle():
             ops.append(("shortcut_scale", 1.0 / betas[r_i]))
         lv = min(lv, sl)
         ops.append(("add", lv))
-        lv = relu(r_i, lv, after_last, mb)
+        lv = relu(r_i, lv, after_last, mb, st == 2)
         r_i += 1
         m = mb
     C, H, W_, grid, dil, block = m
@@ -282,7 +286,8 @@ def test_mini_resnet_bit_exact_against_the_oracle():
     orlk = o.relinkey(pr.s_eval)
     okeys = {st: pr.okeys[g.galois_elt(st)] for st in steps}
     boots = {}
-    for sparse, pl in ((False, plan), (True, splan)):
+    for kind, pl in plans.items():
+        sparse = pl.ns < pl.n
         bl_layers, bpts = [], []
         for rr_, groups, ps, blv in pl.cts + pl.stc:
             gp, op = [], []
@@ -294,14 +299,16 @@ def test_mini_resnet_bit_exact_against_the_oracle():
             layer.keep = gp
             bl_layers.append(layer)
             bpts.append(op)
-        prm = pr.F.fheon_boot_params(len(pl.cts), len(pl.stc), pl.K, pl.D, pl.r, 0, pl.ns if sparse else 0)
+        prm = pr.F.fheon_boot_params(len(pl.cts), len(pl.stc), pl.K, pl.D, pl.r, 0, pl.ns if sparse else 0,
+                                     0 if pl.masked else 1)
         boot = g.bootstrap_compose(prm, bl_layers[:len(pl.cts)], bl_layers[len(pl.cts):], pl.coeffs, D)
         omask = None
-        if sparse:
+        if sparse and pl.masked:
             gm, omask = shared(pl.mask_slots(), 2, float(q[1]))
             g.bootstrap_set_mask(boot, gm)
-        boots[sparse] = (boot, pl, bpts, omask)
-    assert any(op[0] == "boot" and op[1] for op in ops)
+        boots[kind] = (boot, pl, bpts, omask)
+    used = [op[1] for op in ops if op[0] == "boot"]
+    assert len(used) == 6 and "full" not in used and "unmasked" in used and "masked" in used
     # run both sides
     X = synth.image(0xD32, 0, (3, 8, 8), dist="normal")
     ct, oct_ = pr.encrypt_both(ckks.encode(R.pack_input(X, n, MINI), N, D), nonce=0xD32, level=Bl)

@@ -1,5 +1,5 @@
-"""ResNet-20 at full size on the GPU (N = 2^16, 37 primes, 9 bootstraps, 8 of
-them sparse, the ResNet-20 workload's parameters), one CIFAR-shaped
+"""ResNet-20 at full size on the GPU (N = 2^16, 37 primes, 9 sparse
+bootstraps, the ResNet-20 workload's parameters), one CIFAR-shaped
 synthetic input:
 the decrypted logits against the FP64 network with the same Chebyshev ReLUs
 (oracle), within a tolerance derived from the bootstrap's measured precision.
@@ -73,9 +73,13 @@ def test_resnet20_full_size_within_the_bootstrap_tolerance():
     z = synth.uniform_slots(P["seed"], 802, N // 2)
     zc = ctx.drop_level(ctx.encrypt(pk, ctx.encode(z, ctx.L, P["scale"]), nonce=2), 2)
     e_b = 0.0
-    for slots, layer in net._boots.items():
-        want_b = np.tile(z[:slots], N // 2 // slots) if slots else z
-        got_b = np.asarray(ctx.decode(ctx.decrypt(sk, ctx.layer_apply(layer, zc)))).real
+    z0 = z.copy()
+    z0[N // 4:] = 0.0       # the unmasked sparse bootstrap's inputs are zero outside its slots
+    zc0 = ctx.drop_level(ctx.encrypt(pk, ctx.encode(z0, ctx.L, P["scale"]), nonce=3), 1)
+    for (slots, unmasked), layer in net._boots.items():
+        v, c = (z0, zc0) if unmasked else (z, zc)
+        want_b = np.tile(v[:slots], N // 2 // slots) if slots else v
+        got_b = np.asarray(ctx.decode(ctx.decrypt(sk, ctx.layer_apply(layer, c)))).real
         e_b = max(e_b, float(np.max(np.abs(got_b - want_b))))
 
     # the oracle's FP64 network with the same Chebyshev ReLUs, and its response

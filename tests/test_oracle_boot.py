@@ -281,3 +281,20 @@ def test_sparse_bootstrap_encrypted(boot_ctx):
     want = np.sin(2 * np.pi * np.concatenate([brv_order(T[:ns]), brv_order(T[ns:])]) / q0)
     assert np.max(np.abs(v.real - want)) < 1e-7
     assert np.max(np.abs(v.imag)) < 1e-7
+
+
+def test_sparse_unmasked_bootstrap_encrypted(boot_ctx):
+    """An unmasked sparse plan on an input that is zero outside slots
+    [0, N/4), at level 1 (no level for a mask): those slots come back in
+    both copies."""
+    P, ctx, s, se, pk, plan = boot_ctx
+    N, n = ctx.N, ctx.N // 2
+    sp = B.Plan(ctx, P["scale"], slots=N // 4, masked=False)
+    assert not sp.masked and sp.steps() == B.Plan(ctx, P["scale"], slots=N // 4).steps()
+    keys = {st: ctx.rotkey(se, ckks.galois_elt(st, N)) for st in sp.steps()}
+    z = synth.uniform_slots(0xB00E, 0, n)
+    z[N // 4:] = 0.0
+    ct = ctx.drop_level(ctx.encrypt(pk, ckks.encode(z, N, P["scale"]), 14), 1)
+    y, sc = B.bootstrap_encrypted(ctx, ct, sp, sp.encode(ctx), keys, ctx.relinkey(se), ctx.rotkey(se, 2 * N - 1))
+    out = ctx.decode_ct(se, y, sc)
+    assert np.max(np.abs(out - np.tile(z[:N // 4], 2))) < 1e-4

@@ -50,7 +50,7 @@ class FakeCtx:
         self.calls = []
 
     def bootstrap_prepare(self, scale, params=None):
-        return _Layer("boot", None, params.slots if params is not None else 0)
+        return _Layer("boot", None, (params.slots, params.unmasked) if params is not None else (0, 0))
 
     def boot_params_default(self):
         return F.fheon_boot_params(3, 3, 512, 27, 9, 0, 0)
@@ -114,12 +114,15 @@ def test_bootstraps_only_where_levels_run_out():
     net = R.EncryptedResNet(Deep(), R.weights(0xC3, R.FULL), [2.0] * R.n_relus(R.FULL), 2.0 ** 40)
     assert net.n_boot == 9 and net.out_level >= 1
     assert min(c[1] for c in net.ctx.calls) >= 2
-    # every bootstrap input within slots [0, N/4) at level >= 2 takes the
-    # sparse bootstrap: all of them but the one whose input is at level 1
-    slots = [op[2].out_map for op in net.plan if op[0] == "boot"]
-    assert slots.count(Deep.N // 4) == 8 and slots.count(0) == 1
+    # every bootstrap input within slots [0, N/4) takes the sparse bootstrap:
+    # unmasked where it is a convolution's output (zero outside its map: here
+    # the second ReLU of the two blocks with a convolution on the shortcut,
+    # one of them at level 1), masked otherwise (its input at level >= 2)
+    kinds = [op[2].out_map for op in net.plan if op[0] == "boot"]
+    assert all(k[0] == Deep.N // 4 for k in kinds)
+    assert kinds.count((Deep.N // 4, 1)) == 2 and kinds.count((Deep.N // 4, 0)) == 7
     full = R.EncryptedResNet(Deep(), R.weights(0xC3, R.FULL), [2.0] * R.n_relus(R.FULL), 2.0 ** 40, sparse=False)
-    assert full.n_boot == 9 and all(op[2].out_map == 0 for op in full.plan if op[0] == "boot")
+    assert full.n_boot == 9 and all(op[2].out_map == (0, 0) for op in full.plan if op[0] == "boot")
 
 
 def test_reduced_network_plan():
