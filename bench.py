@@ -600,8 +600,9 @@ def serving_timing(F, n_req=200, rate=4.0, max_active=12, frac_resnet=0.3):
     request alone replayed as a CUDA graph on pooled request buffers; the
     ResNet model is a program of layer, bootstrap, add and constant steps
     over three registers).
-    Admission by memory: the budget holds the footprints of 8 LeNet-5 and 3
-    ResNet-20 requests (fheon_model_footprint).  Requests are submitted when
+    Admission by memory: the budget holds the footprints of one ResNet-20 and
+    three LeNet-5 requests (fheon_model_footprint), less than two ResNet-20
+    footprints.  Requests are submitted when
     their arrival time has passed (host clock); latency = completion -
     arrival."""
     import torch
@@ -643,12 +644,13 @@ def serving_timing(F, n_req=200, rate=4.0, max_active=12, frac_resnet=0.3):
     models = [(c1, m1, ct1), (c2, m2, ct2)]
     fp = [F.Context.model_footprint(m1, c1.ct_info(ct1[0])[0]), F.Context.model_footprint(m2, rn.in_level)]
     # the device memory left once both models' keys are resident (free, plus
-    # what torch's cache holds unused), less a margin, bounded by 8 LeNet-5 and
-    # 3 ResNet-20 requests
+    # what torch's cache holds unused), less a margin, bounded by one ResNet-20
+    # and three LeNet-5 requests: below two ResNet-20 footprints, so that
+    # ResNet-20 requests never take all of it and LeNet-5 requests keep flowing
     torch.cuda.synchronize()
     free_b, _ = torch.cuda.mem_get_info()
     avail = free_b + torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
-    budget = int(min(8 * fp[0] + 3 * fp[1], 0.8 * avail))
+    budget = int(min(3 * fp[0] + fp[1], 0.8 * avail))
     srv = c1.server(max_active=max_active, mem_budget=budget)
     srv.set_graphs(True)  # single-request layer steps replay captured graphs on pooled buffers
     c1.sync()

@@ -249,6 +249,14 @@ cudaError_t k_mul_plain(fheon_ctx *ctx, const u64 *ct, const u64 *pt, u64 *out, 
 // level limbs); out must not alias an input when n > MAC_MAX
 constexpr u32 MAC_MAX = 32;
 cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const *pts, u32 n, u64 *out, u32 level);
+// the sums of several groups over one set of taps: outs[g] = sum_t cts[t] *
+// pts[g * nt + t] (null plaintexts skipped; every group at least one), all
+// ciphertexts u64[2][level][N]; each launch reads the taps once for up to
+// MACG_SUB groups.  Bit-identical to k_mac_plain per group.  nt <= MACG_TAPS,
+// ng <= MACG_GROUPS; outputs distinct from the taps
+constexpr u32 MACG_TAPS = 64, MACG_GROUPS = 32, MACG_SUB = 2;
+cudaError_t k_mac_groups(fheon_ctx *ctx, const u64 *const *cts, u32 nt, const u64 *const *pts, u32 ng,
+                         u64 *const *outs, u32 level);
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 nlimb_per_comp, u32 ncomp);
 // d = (a0 b0, a0 b1 + a1 b0, a1 b1) (doubled when `twice`) over the lowest
 // `level` limbs of each component: u64[3][level][N]

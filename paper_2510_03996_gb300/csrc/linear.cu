@@ -72,6 +72,70 @@ int own_plain(fheon_ctx *ctx, fheon_layer *ly, const std::vector<double> &v, u32
     return FHEON_OK;
 }
 
+// groups g0 .. g0 + gn - 1 of a rotation-sum layer on one input: w[gg] = sum_t
+// tap_t * P_{g0+gg, t} (tap_t = Rot_{r_t}(in): rot[idx[t]], or in itself for
+// r_t = 0).  The taps any of these groups uses are read once per MACG_SUB
+// groups (k_mac_groups); more taps than it takes, or products of different
+// scales, go group by group through fheon_mac_plain (which reports the error)
+int group_sums(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *const *rot,
+               const std::vector<int> &idx, u32 g0, u32 gn, fheon_ct *const *w)
+{
+    const u32 nt = (u32)ly->r.size();
+    std::vector<u32> used;
+    for (u32 t = 0; t < nt; t++)
+        for (u32 gg = 0; gg < gn; gg++)
+            if (ly->pts[(size_t)(g0 + gg) * nt + t]) {
+                used.push_back(t);
+                break;
+            }
+    auto tap = [&](u32 t) -> const fheon_ct * { return idx[t] < 0 ? in : rot[idx[t]]; };
+    const u32 l = in->level;
+    bool grouped = !used.empty() && used.size() <= MACG_TAPS && gn <= MACG_GROUPS;
+    std::vector<double> sc(gn, 0.0);
+    for (u32 gg = 0; gg < gn && grouped; gg++) {
+        for (u32 t : used) {
+            const fheon_pt *p = ly->pts[(size_t)(g0 + gg) * nt + t];
+            if (!p) continue;
+            const double x = tap(t)->scale * p->scale;
+            if (tap(t)->level != l || p->level < l || (sc[gg] != 0.0 && std::fabs(x - sc[gg]) > 1e-9 * sc[gg]))
+                grouped = false;
+            if (sc[gg] == 0.0) sc[gg] = x;
+        }
+        grouped = grouped && sc[gg] != 0.0;
+    }
+    int rc;
+    if (grouped) {
+        std::vector<const u64 *> cts, pts;
+        std::vector<u64 *> outs;
+        for (u32 t : used) cts.push_back(tap(t)->c0());
+        for (u32 gg = 0; gg < gn; gg++) {
+            for (u32 t : used) {
+                const fheon_pt *p = ly->pts[(size_t)(g0 + gg) * nt + t];
+                pts.push_back(p ? p->m.as<u64>() : nullptr);
+            }
+            if ((rc = ct_reshape(ctx, w[gg], l))) return rc;
+            w[gg]->scale = sc[gg];
+            outs.push_back(w[gg]->c0());
+        }
+        FHEON_CUDA(ctx, k_mac_groups(ctx, cts.data(), (u32)cts.size(), pts.data(), gn, outs.data(), l));
+        return FHEON_OK;
+    }
+    std::vector<const fheon_ct *> srcs;
+    std::vector<const fheon_pt *> ps;
+    for (u32 gg = 0; gg < gn; gg++) {
+        srcs.clear();
+        ps.clear();
+        for (u32 t = 0; t < nt; t++) {
+            const fheon_pt *p = ly->pts[(size_t)(g0 + gg) * nt + t];
+            if (!p) continue;
+            srcs.push_back(tap(t));
+            ps.push_back(p);
+        }
+        if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), w[gg]))) return rc;
+    }
+    return FHEON_OK;
+}
+
 // n inputs at once: every input's tap rotations in one hoisted plan (grouped by
 // input), the group shifts of every input in one plain batch per chunk of
 // groups; the result of each input is the one it gets alone
@@ -121,25 +185,15 @@ int linear_apply(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *const *i
     for (u32 i = 0; i < n; i++)
         for (u32 k = 0; k < ns; k++) items.push_back(fheon_rot_item{ins[i], ly->rot[(size_t)i * ns + k], steps[k]});
     if ((rc = rotate_many(ctx, items.data(), (u32)items.size(), true, ly->collect))) return rc;
-    std::vector<const fheon_ct *> srcs;
-    std::vector<const fheon_pt *> ps;
     std::vector<fheon_rot_item> moves;
     for (u32 g0 = 0; g0 < ng; g0 += GC) {
         const u32 gn = std::min(GC, ng - g0);
         moves.clear();
         for (u32 i = 0; i < n; i++) {
             fheon_ct *const *w = ly->work.data() + (size_t)i * 2 * GC;
+            if ((rc = group_sums(ctx, ly, ins[i], ly->rot.data() + (size_t)i * ns, idx, g0, gn, w))) return rc;
             for (u32 gg = 0; gg < gn; gg++) {
                 const u32 g = g0 + gg;
-                srcs.clear();
-                ps.clear();
-                for (u32 t = 0; t < nt; t++) {
-                    const fheon_pt *p = ly->pts[(size_t)g * nt + t];
-                    if (!p) continue;
-                    srcs.push_back(idx[t] < 0 ? ins[i] : ly->rot[(size_t)i * ns + idx[t]]);
-                    ps.push_back(p);
-                }
-                if ((rc = fheon_mac_plain(ctx, srcs.data(), ps.data(), (u32)srcs.size(), w[gg]))) return rc;
                 if ((rc = fheon_rescale(ctx, w[gg], w[gg]))) return rc;
                 if (ly->s[g] != 0) moves.push_back(fheon_rot_item{w[gg], w[GC + gg], ly->s[g]});
             }
