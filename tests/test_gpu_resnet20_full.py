@@ -9,8 +9,8 @@ noise (about 1e-7 of the message at scale 2^40), the encrypted network
 differs from the FP64 one by each bootstrap's error: a bootstrap returns its
 input (in [-1, 1]: the ReLU's 1/beta is folded into the conv before it) up to
 an error d, measured here on a uniform [-1, 1] vector x and split in three
-parts: its mean mu over the slots (a shift of every slot alike: the floor
-roundings of rescaling and of ModDown collect in the constant coefficient),
+parts: its mean mu over the slots (a shift of every slot alike, carried by
+the output's constant coefficient),
 a change of scale rho (the least-squares fit d - mu ~ rho x) and a residual
 of at most e_r per slot.  The coherent parts are what the layers after a
 bootstrap amplify most: a shift of every slot by e_r moves the logits about
