@@ -71,74 +71,66 @@ __global__ void __launch_bounds__(TPB) mac_plain_kernel(const __grid_constant__ 
     *reinterpret_cast<ulonglong2 *>(out + idx) = make_ulonglong2(s0, s1);
 }
 
-// several groups' sums over one set of taps: outs[g0 + k] = sum_t ct_t *
-// pt[g0 + k][t] for k < gn <= SUB.  Each tap's two coefficients are read once
-// and multiplied into every group's 128-bit sums (at most 8 products each
-// between reductions, as in mac_plain_kernel), so the taps cross HBM once per
-// SUB groups instead of once per group.  Measured on a 64-channel ResNet-20
-// convolution at N = 2^16: SUB = 2 takes 14 % less time than one group per
-// pass; SUB = 4 and 8 hold 78 and 128 registers a thread and are slower.
+// several groups' sums over one set of taps: outs[g] = sum_t ct_t * pt[g][t].
+// A block is GB groups x (TPB / GB) coefficient pairs: each warp sums one
+// group over 32 consecutive pairs (the same per-thread work as
+// mac_plain_kernel, coalesced), and the GB warps of a block that read the
+// same tap coefficients share them through L1, so the taps cross HBM about
+// once per GB groups instead of once per group.  Measured on a 64-channel
+// ResNet-20 convolution at N = 2^16 (45 taps, 26 groups, level 11): GB = 4
+// takes 3.34 ms (2: 3.53, 8: 3.40) against 4.70 ms group by group; one thread
+// holding the sums of two groups took 4.06 ms, of four or eight (78 and 128
+// registers a thread) 4.86 and 6.50 ms.
 struct MacGroupArgs {
     const u64 *ct[MACG_TAPS];              // u64[2][level][N]
     const u64 *pt[MACG_GROUPS][MACG_TAPS]; // u64[>= level][N]; null: no product
     u64 *out[MACG_GROUPS];
 };
-template <u32 SUB>
-__global__ void __launch_bounds__(TPB) mac_groups_kernel(const __grid_constant__ MacGroupArgs A, u32 nt, u32 g0, u32 gn,
+template <u32 GB>
+__global__ void __launch_bounds__(TPB) mac_groups_kernel(const __grid_constant__ MacGroupArgs A, u32 nt, u32 ng,
                                                          u32 level, u32 logN, const ModConst *__restrict__ mc)
 {
-    // this launch's pointers in shared memory: the loop below indexes them by
-    // tap and group, which from the parameter bank would serialise on its cache
+    // the block's pointers in shared memory (indexed by tap and group, the
+    // parameter bank's cache would serialise)
     __shared__ const u64 *sct[MACG_TAPS];
-    __shared__ const u64 *spt[SUB][MACG_TAPS];
+    __shared__ const u64 *spt[GB][MACG_TAPS];
+    const u32 g0 = blockIdx.y * GB;
     for (u32 i = threadIdx.x; i < nt; i += TPB) sct[i] = A.ct[i];
-    for (u32 i = threadIdx.x; i < gn * nt; i += TPB) spt[i / nt][i % nt] = A.pt[g0 + i / nt][i % nt];
+    for (u32 i = threadIdx.x; i < GB * nt; i += TPB)
+        spt[i / nt][i % nt] = g0 + i / nt < ng ? A.pt[g0 + i / nt][i % nt] : nullptr;
     __syncthreads();
-    const u64 idx = ((u64)blockIdx.x * TPB + threadIdx.x) * 2;
+    constexpr u32 PAIRS = TPB / GB;
+    const u32 k = threadIdx.x / PAIRS;
+    const u64 idx = ((u64)blockIdx.x * PAIRS + threadIdx.x % PAIRS) * 2;
     const u64 per = (u64)level << logN;
-    if (idx >= 2 * per) return;
+    if (idx >= 2 * per || g0 + k >= ng) return;
     const u64 w = idx % per;
     const ModConst m = mc[(u32)(w >> logN)];
-    u64 s[SUB][2];
-    u128acc a[SUB][2];
-#pragma unroll
-    for (u32 k = 0; k < SUB; k++) {
-        s[k][0] = s[k][1] = 0;
-        acc_zero(a[k][0]);
-        acc_zero(a[k][1]);
-    }
+    u64 s0 = 0, s1 = 0;
+    u128acc a0, a1;
+    acc_zero(a0);
+    acc_zero(a1);
+    u32 cnt = 0;
     for (u32 t = 0; t < nt; t++) {
+        const u64 *p = spt[k][t];
+        if (!p) continue;
         const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(sct[t] + idx);
-#pragma unroll
-        for (u32 k = 0; k < SUB; k++) {
-            if (k < gn) {
-                const u64 *p = spt[k][t];
-                if (p) {
-                    const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(p + w);
-                    acc_mad(a[k][0], x.x, y.x);
-                    acc_mad(a[k][1], x.y, y.y);
-                }
-            }
-        }
-        if ((t & 7) == 7 || t + 1 == nt) {
-#pragma unroll
-            for (u32 k = 0; k < SUB; k++) {
-                if (k < gn) {
-                    s[k][0] = addmod(s[k][0], redc_acc(a[k][0], m.q, m.qneg_inv), m.q);
-                    s[k][1] = addmod(s[k][1], redc_acc(a[k][1], m.q, m.qneg_inv), m.q);
-                    acc_zero(a[k][0]);
-                    acc_zero(a[k][1]);
-                }
-            }
+        const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(p + w);
+        acc_mad(a0, x.x, y.x);
+        acc_mad(a1, x.y, y.y);
+        if (++cnt == 8) { // at most 8 products between reductions (8 q^2 < q 2^64)
+            s0 = addmod(s0, redc_acc(a0, m.q, m.qneg_inv), m.q);
+            s1 = addmod(s1, redc_acc(a1, m.q, m.qneg_inv), m.q);
+            acc_zero(a0);
+            acc_zero(a1);
+            cnt = 0;
         }
     }
-#pragma unroll
-    for (u32 k = 0; k < SUB; k++) {
-        if (k < gn) {
-            const u64 r0 = shoup(s[k][0], m.r1, m.r1_sh, m.q), r1 = shoup(s[k][1], m.r1, m.r1_sh, m.q);
-            *reinterpret_cast<ulonglong2 *>(A.out[g0 + k] + idx) = make_ulonglong2(r0, r1);
-        }
-    }
+    s0 = addmod(s0, redc_acc(a0, m.q, m.qneg_inv), m.q);
+    s1 = addmod(s1, redc_acc(a1, m.q, m.qneg_inv), m.q);
+    s0 = shoup(s0, m.r1, m.r1_sh, m.q);
+    s1 = shoup(s1, m.r1, m.r1_sh, m.q);
+    *reinterpret_cast<ulonglong2 *>(A.out[g0 + k] + idx) = make_ulonglong2(s0, s1);
 }
 
 // the ciphertext tensor d = (a0 b0, a0 b1 + a1 b0, a1 b1) over the lowest
@@ -403,10 +395,11 @@ cudaError_t k_mac_groups(fheon_ctx *ctx, const u64 *const *cts, u32 nt, const u6
         A.out[g] = outs[g];
         for (u32 t = 0; t < nt; t++) A.pt[g][t] = pts[(size_t)g * nt + t];
     }
-    for (u32 g0 = 0; g0 < ng; g0 += MACG_SUB) {
-        const u32 gn = std::min<u32>(MACG_SUB, ng - g0);
-        mac_groups_kernel<MACG_SUB><<<blocks2((u64)2 * level * ctx->N), TPB, 0, ctx->stream>>>(
-            A, nt, g0, gn, level, ctx->logN, ctx->tab.mc.as<ModConst>());
+    {
+        constexpr u32 GB = MACG_BLOCK_GROUPS;
+        const u64 pairs = (u64)level * ctx->N;
+        const dim3 grid((unsigned)((pairs + TPB / GB - 1) / (TPB / GB)), (ng + GB - 1) / GB);
+        mac_groups_kernel<GB><<<grid, TPB, 0, ctx->stream>>>(A, nt, ng, level, ctx->logN, ctx->tab.mc.as<ModConst>());
         prof_mark(ctx->stream, "mac_groups");
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -251,10 +251,11 @@ constexpr u32 MAC_MAX = 32;
 cudaError_t k_mac_plain(fheon_ctx *ctx, const u64 *const *cts, const u64 *const *pts, u32 n, u64 *out, u32 level);
 // the sums of several groups over one set of taps: outs[g] = sum_t cts[t] *
 // pts[g * nt + t] (null plaintexts skipped; every group at least one), all
-// ciphertexts u64[2][level][N]; each launch reads the taps once for up to
-// MACG_SUB groups.  Bit-identical to k_mac_plain per group.  nt <= MACG_TAPS,
-// ng <= MACG_GROUPS; outputs distinct from the taps
-constexpr u32 MACG_TAPS = 64, MACG_GROUPS = 32, MACG_SUB = 2;
+// ciphertexts u64[2][level][N]; the warps of a block sum MACG_BLOCK_GROUPS
+// groups over the same coefficients, so each tap crosses HBM about once per
+// that many groups.  Bit-identical to k_mac_plain per group.  nt <=
+// MACG_TAPS, ng <= MACG_GROUPS; outputs distinct from the taps
+constexpr u32 MACG_TAPS = 64, MACG_GROUPS = 32, MACG_BLOCK_GROUPS = 4;
 cudaError_t k_mac_groups(fheon_ctx *ctx, const u64 *const *cts, u32 nt, const u64 *const *pts, u32 ng,
                          u64 *const *outs, u32 level);
 cudaError_t k_add(fheon_ctx *ctx, const u64 *a, const u64 *b, u64 *out, u32 nlimb_per_comp, u32 ncomp);

@@ -74,9 +74,10 @@ int own_plain(fheon_ctx *ctx, fheon_layer *ly, const std::vector<double> &v, u32
 
 // groups g0 .. g0 + gn - 1 of a rotation-sum layer on one input: w[gg] = sum_t
 // tap_t * P_{g0+gg, t} (tap_t = Rot_{r_t}(in): rot[idx[t]], or in itself for
-// r_t = 0).  The taps any of these groups uses are read once per MACG_SUB
-// groups (k_mac_groups); more taps than it takes, or products of different
-// scales, go group by group through fheon_mac_plain (which reports the error)
+// r_t = 0), all in one pass over the taps any of them uses (k_mac_groups: a
+// tap crosses HBM about once per MACG_BLOCK_GROUPS groups); more taps than it
+// takes, or products of different scales, go group by group through
+// fheon_mac_plain (which reports the error)
 int group_sums(fheon_ctx *ctx, const fheon_layer *ly, const fheon_ct *in, fheon_ct *const *rot,
                const std::vector<int> &idx, u32 g0, u32 gn, fheon_ct *const *w)
 {
